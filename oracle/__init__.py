@@ -60,14 +60,20 @@ def _load():
         _lib.orc_row_weights.argtypes = [C.c_int, D, C.c_double, C.c_int, D]
         _lib.orc_axis_tables.argtypes = [C.c_int, D, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, C.c_double,
-                                         D, D, D, D, I, I, D, D]
+                                         D, D, D, D, I, I, D, D, I]
         _lib.orc_axis_tables.restype = C.c_int
         _lib.orc_locate.argtypes = [C.c_int, D, C.c_int, D, C.c_int, D, C.c_int,
                                     C.c_int, C.c_int, C.c_int, D, I, D]
         _lib.orc_locate.restype = C.c_int
         _lib.orc_forward.argtypes = [C.POINTER(_Problem)]
         _lib.orc_forward.restype = C.c_int
+        _lib.orc_threads.restype = C.c_int
     return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return int(_load().orc_threads())
 
 
 def _dp(a: Optional[np.ndarray]):
@@ -121,12 +127,12 @@ def axis_tables(x, rd: int, nb: int, ne: int, vmax: float = 1.0,
     out = dict(X=np.zeros(npad + 1), Xh=np.zeros(npad), cp=np.zeros((npad, m)),
                cm=np.zeros((npad, m)), slab=np.zeros(npad, np.int32),
                slabh=np.zeros(npad, np.int32),
-               pml=np.zeros((4, 2 * nb)), dmax=np.zeros(1))
+               pml=np.zeros((4, 2 * nb)), dmax=np.zeros(1), ranges=np.zeros(4, np.int32))
     code = _load().orc_axis_tables(n, _dp(x), rd, nb, ne, vmax, fmax, dt,
                                    _dp(out["X"]), _dp(out["Xh"]), _dp(out["cp"]),
                                    _dp(out["cm"]), _ip(out["slab"]), _ip(out["slabh"]),
                                    _dp(out["pml"]),
-                                   _dp(out["dmax"]))
+                                   _dp(out["dmax"]), _ip(out["ranges"]))
     _check(code, "axis_tables")
     out["dmax"] = float(out["dmax"][0])
     return out
@@ -163,6 +169,8 @@ class _Problem(C.Structure):
         ("rec_G", C.POINTER(C.c_double)), ("rec_acc", C.POINTER(C.c_double)),
         ("jhat", C.POINTER(C.c_double)), ("vol_G", C.POINTER(C.c_double)),
         ("info", C.POINTER(C.c_double)),
+        ("nvs", C.c_int), ("vs_idx", C.POINTER(C.c_longlong)),
+        ("vs_G", C.POINTER(C.c_double)),
     ]
 
 
@@ -172,11 +180,14 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
             sigma_min: float = 0.0, dt: float = 0.0, volume: bool = False,
             convergence: bool = False, inject: bool = True, pml: bool = True,
             init_fields: Optional[np.ndarray] = None,
-            want_fields: bool = False) -> Dict[str, object]:
+            want_fields: bool = False,
+            vol_samples: Optional[np.ndarray] = None) -> Dict[str, object]:
     """Run the FP64 oracle.  ``sigma`` is [3][n3][n2][n1] (staggered sigma_xx,
     sigma_yy, sigma_zz).  Returns a dict with ``G`` [nrec][6][nfreq] complex,
     ``acc`` (raw DTFT), ``jhat`` [nfreq], optional ``vol`` [6][nfreq][n3][n2][n1]
-    and ``fields`` [6][n3p][n2p][n1p], plus ``dt``, ``vmax``, ``nt``, ``eta``."""
+    and ``fields`` [6][n3p][n2p][n1p], plus ``dt``, ``vmax``, ``nt``, ``eta``.
+    ``vol_samples`` (flat indices into [6][n3][n2][n1]) gives ``vol_samples_G``
+    [nvs][nfreq]: the volume Green's functions at those samples only."""
     lib = _load()
     xs = [_f64(x), _f64(y), _f64(z)]
     n = [len(a) for a in xs]
@@ -215,6 +226,13 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     vol = np.zeros((6, nf, n[2], n[1], n[0], 2)) if volume else None
     info = np.zeros(4)
     P.rec_G, P.rec_acc, P.jhat, P.vol_G, P.info = _dp(G), _dp(acc), _dp(jh), _dp(vol), _dp(info)
+    vsG = None
+    if vol_samples is not None:
+        vs = np.ascontiguousarray(vol_samples, dtype=np.int64)
+        P.nvs = len(vs)
+        P.vs_idx = vs.ctypes.data_as(C.POINTER(C.c_longlong))
+        vsG = np.zeros((len(vs), max(nf, 1), 2))
+        P.vs_G = _dp(vsG)
     code = lib.orc_forward(C.byref(P))
     _check(code, "forward")
     cplx = lambda a: a[..., 0] + 1j * a[..., 1]
@@ -224,6 +242,8 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
         out["vol"] = cplx(vol)
     if want_fields:
         out["fields"] = fields
+    if vsG is not None:
+        out["vol_samples_G"] = cplx(vsG)[:, :nf]
     return out
 
 

@@ -33,6 +33,9 @@
  */
 #include <complex.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -40,6 +43,16 @@
 #define ORC_MAXK 8              /* 2r knots, r <= 4 */
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EOUTSIDE = 3 };
+
+/* Number of OpenMP threads the loops below use. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Vandermonde inversion (Sec. 3.1, Eq. 9-11)                               */
@@ -217,7 +230,7 @@ int orc_axis_tables(int n, const double *x, int rd, int nb, int ne,
                     double vmax, double fmax, double dt,
                     double *X, double *Xh, double *cp, double *cm, int *slab, int *slabh,
                     double *pml /* [4][2nb]: a_int, b_int, a_half, b_half */,
-                    double *dmax)
+                    double *dmax, int *ranges /* [4]: first/last D+ row, first/last D- row */)
 {
   orc_axis ax;
   int st = orc_axis_nodes(&ax, n, x, rd, nb, ne);
@@ -238,6 +251,7 @@ int orc_axis_tables(int n, const double *x, int rd, int nb, int ne,
     memcpy(pml + 3 * 2 * nb, ax.pb_h, sizeof(double) * 2 * nb);
   }
   if (dmax) *dmax = orc_axis_dmax(&ax);
+  if (ranges) { ranges[0] = rd - 1; ranges[1] = np - 1 - rd; ranges[2] = rd; ranges[3] = np - 1 - rd; }
   orc_axis_free(&ax);
   return ORC_OK;
 }
@@ -320,6 +334,10 @@ typedef struct {
   double *jhat;              /* [nfreq][2] source spectrum */
   double *vol_G;             /* [6][nfreq][n3][n2][n1][2] Green's functions on the interior */
   double *info;              /* [4]: dt, vmax, nt actually run, eta */
+  /* optional sampled volume DTFT: flat indices into [6][n3][n2][n1] */
+  int nvs;
+  const long long *vs_idx;
+  double *vs_G;              /* [nvs][nfreq][2] Green's functions at those samples */
 } orc_problem;
 
 typedef struct {
@@ -629,6 +647,8 @@ int orc_forward(orc_problem *P)
   double complex *jh = calloc(nf > 0 ? nf : 1, sizeof(double complex));
   double *rval = calloc((size_t)(nrec > 0 ? nrec : 1) * 6, sizeof(double));
   double complex *vol = NULL;
+  double complex *vsa = NULL;
+  if (P->nvs > 0) vsa = calloc((size_t)P->nvs * nf, sizeof(double complex));
   if (P->want_volume) {
     vol = calloc(6 * (size_t)nf * nint, sizeof(double complex));
     if (!vol) { free(rst); free(wp); free(acc); free(jh); free(rval); orc_state_free(st); return ORC_ENOMEM; }
@@ -677,6 +697,15 @@ int orc_forward(orc_problem *P)
                 vc[((size_t)k * P->n[1] + j) * P->n[0] + i] += fac * Fc[IDX(st, k + nbe, j + nbe, i + nbe)];
         }
       }
+      if (vsa) {
+        for (int q = 0; q < P->nvs; ++q) {
+          long long fi = P->vs_idx[q];
+          int c = (int)(fi / (long long)nint);
+          long long rem = fi % (long long)nint;
+          int i = (int)(rem % P->n[0]), j = (int)((rem / P->n[0]) % P->n[1]), k = (int)(rem / ((long long)P->n[0] * P->n[1]));
+          vsa[(size_t)q * nf + f] += (c < 3 ? fE : fH) * st->F[c][IDX(st, k + nbe, j + nbe, i + nbe)];
+        }
+      }
       if (P->convergence && f == flo) {
         for (int q = 0; q < 8; ++q) {
           int ci = nbe + ((q & 1) ? P->n[0] - 1 : 0);
@@ -718,6 +747,13 @@ int orc_forward(orc_problem *P)
         if (P->rec_G) { P->rec_G[2 * o] = creal(g); P->rec_G[2 * o + 1] = cimag(g); }
         if (P->rec_acc) { P->rec_acc[2 * o] = creal(acc[o]); P->rec_acc[2 * o + 1] = cimag(acc[o]); }
       }
+    if (vsa && P->vs_G)
+      for (int q = 0; q < P->nvs; ++q) {
+        int c = (int)(P->vs_idx[q] / (long long)nint);
+        double complex g = (c < 3 ? sE : 1.0) * vsa[(size_t)q * nf + f] / jh[f];
+        P->vs_G[2 * ((size_t)q * nf + f)] = creal(g);
+        P->vs_G[2 * ((size_t)q * nf + f) + 1] = cimag(g);
+      }
     if (vol && P->vol_G)
       for (int c = 0; c < 6; ++c) {
         double complex fac = (c < 3 ? sE : 1.0) / jh[f];
@@ -733,7 +769,7 @@ int orc_forward(orc_problem *P)
     for (int c = 0; c < 6; ++c) memcpy(P->final_fields + c * st->ncell, st->F[c], sizeof(double) * st->ncell);
   if (P->info) { P->info[0] = dt; P->info[1] = vmax; P->info[2] = nt_run; P->info[3] = eta; }
 
-  free(vol); free(acc); free(jh); free(wp); free(rst); free(rval);
+  free(vsa); free(vol); free(acc); free(jh); free(wp); free(rst); free(rval);
   for (int c = 0; c < 3; ++c) free(jw[c]);
   orc_state_free(st);
   return ORC_OK;
