@@ -1,0 +1,304 @@
+"""Benchmark of the fictitious-wave FDTD forward solve on B300.
+
+One benchmark step = one complete forward solve (every leapfrog step of the
+time loop, CPML, source injection, receiver DTFT, Green's functions) of the
+marine 1-D VTI workload on its 128 x 128 x 96-node non-uniform grid
+(162 x 162 x 130 padded samples, 4th order, 3 frequencies, 64 receivers).
+The metric is padded cell-steps per second (Gcell-steps/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own
+transmitter position (sources are independent problems, weak scaling); the
+only collective is the max over ranks of the timed duration.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on the
+host cores, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2304_00233_b300 import workloads as W  # noqa: E402
+
+WORKLOAD = "marine_1d_128x128x96"
+
+
+def _slab_cells(wl):
+    np1, np2, np3 = wl.npad
+    nb2 = 2 * wl.nb
+    return nb2 * np2 * np3 + np1 * nb2 * np3 + np1 * np2 * nb2
+
+
+def algorithmic_bytes(wl):
+    """Bytes per leapfrog step the method must move at minimum (FP32):
+    6 fields read + written and 3 dt/eps read = 60 B per padded cell, plus
+    4 CPML memory arrays read + written (32 B) per cell and per axis whose
+    slab it lies in, plus 32 B per compensated volume-DTFT accumulator."""
+    cells = int(np.prod(wl.npad))
+    b = 60 * cells + 32 * _slab_cells(wl)
+    if wl.volume:
+        b += 32 * 6 * len(wl.freqs) * int(np.prod(wl.shape))
+    return b
+
+
+def per_kernel_bytes(wl):
+    """Minimal bytes of each half-step launch of the two-launch step:
+    E launch reads H, E, dt/eps and writes E (48 B/cell); H launch reads E, H
+    and writes H (36 B/cell); each has 2 CPML arrays per slab axis."""
+    cells = int(np.prod(wl.npad))
+    vol = 32 * 3 * len(wl.freqs) * int(np.prod(wl.shape)) if wl.volume else 0
+    return 48 * cells + 16 * _slab_cells(wl) + vol, 36 * cells + 16 * _slab_cells(wl) + vol
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(wl, nt):
+    """Wall time of `nt` oracle steps (setup subtracted)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.forward_workload(wl, nt=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.forward_workload(wl, nt=nt)
+    return max(time.perf_counter() - t0 - t_setup, 1e-9)
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    import oracle
+    threads = oracle.threads()
+    probe_nt = 4
+    t = oracle_sample(wl, probe_nt)
+    nt = int(min(400, max(8, budget_s / (t / probe_nt))))
+    t = oracle_sample(wl, nt)
+    cells = int(np.prod(wl.npad))
+    return {"value": cells * nt / t / 1e9, "unit": "Gcell-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{nt} leapfrog steps of {wl.name} (FP64 oracle, {threads} OpenMP threads), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, each step a
+    bounded sample (a fixed number of leapfrog steps) of the same workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    wl = W.WORKLOADS[args.workload]()
+    threads = oracle.threads()
+    cells = int(np.prod(wl.npad))
+    probe = oracle_sample(wl, 2) / 2
+    # each step: enough leapfrog steps for ~90 s over the whole run
+    nt = int(min(400, max(2, 90.0 / max(1, args.steps + args.warmup) / probe)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, nt)
+    times = [oracle_sample(wl, nt) for _ in range(args.steps)]
+    tot = sum(times)
+    value = cells * nt * args.steps / tot / 1e9
+    line = {"metric": "FDTD forward Gcell-steps/s", "value": value, "unit": "Gcell-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "padded_cells": cells, "timesteps_per_step": nt,
+                       "note": "each step is a bounded sample of the solve's leapfrog steps"},
+            "cpu_baseline": {"value": value, "unit": "Gcell-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{nt} leapfrog steps of {wl.name} per step"},
+            "e2e": {"value": value, "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timesteps", type=int, default=0,
+                    help="override the leapfrog steps per solve (short profiling runs only)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2304_00233_b300 as emm
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    wl = W.WORKLOADS[args.workload]()
+    # weak scaling: rank r solves the transmitter shifted 200 m along the tow line
+    wl.src = wl.src + np.array([200.0 * rank, 0.0, 0.0])
+    grid = emm.grid_for(wl)
+    nt = args.timesteps if args.timesteps > 0 else emm.steps_for(wl, grid)
+    survey = emm.survey_for(wl, nt=nt)
+    cells = grid.cells
+    sigma_host = torch.from_numpy(wl.sigma.astype(np.float32)).pin_memory()
+    sigma = sigma_host.cuda()
+    work = emm.Workspace(grid, survey)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        emm.forward_async(grid, survey, sigma, work)
+    torch.cuda.synchronize()
+    assert emm.status(work) == emm.EMM_OK
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- timed region: K device-resident solves ----
+    e_ms, h_ms = [], []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            t = emm.forward_timed(grid, survey, sigma, work, every=64)
+            e_ms.append(t["e_ms"])
+            h_ms.append(t["h_ms"])
+        ev1.record(stream)
+        barrier()
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    clocks = clk.summary()
+    value = world * cells * nt * args.steps / elapsed / 1e9
+
+    # ---- e2e: pinned host sigma in, receiver Green's functions out ----
+    rec_host = torch.empty(work.rec.shape, dtype=work.rec.dtype).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sig_dev = sigma_host.to("cuda", non_blocking=True)
+        emm.forward_async(grid, survey, sig_dev, work)
+        rec_host.copy_(work.rec, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e_value = world * cells * nt * args.steps / e2e_s / 1e9
+
+    peak, peak_kind = measured_peaks()
+    e_mean, h_mean = float(np.mean(e_ms)), float(np.mean(h_ms))
+    alg = algorithmic_bytes(wl)
+    be, bh = per_kernel_bytes(wl)
+    step_s = (e_mean + h_mean) / 1e3
+    achieved = alg / step_s / 1e9
+    kernel_launches = args.steps * (1 + 2 * nt + (1 if survey.nrec else 0) + (1 if survey.volume else 0))
+    line = {
+        "metric": "FDTD forward Gcell-steps/s", "value": value, "unit": "Gcell-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "grid_nodes": list(wl.shape), "padded": list(grid.npad),
+                   "padded_cells": cells, "rd": wl.rd, "timesteps_per_solve": nt,
+                   "nfreq": len(wl.freqs), "nrec": survey.nrec, "volume_dtft": bool(wl.volume),
+                   "parallelism": f"{world} independent transmitters" if world > 1 else "single GPU",
+                   "l2": "no flush: per-solve working set (fields, 1/eps, CPML) exceeds the 126 MB L2"},
+        "roofline": {"bound": "hbm", "kernel": "leapfrog step = k_update_E + k_update_H",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": ("of measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                                   if peak_kind == "measured" else "of fallback 6.4 TB/s"),
+                     "algorithmic_bytes_per_step": alg, "step_ms": 1e3 * step_s, "traffic": None,
+                     "kernels": {"k_update_E": {"ms": e_mean, "min_bytes": be, "gbs": be / e_mean / 1e6},
+                                 "k_update_H": {"ms": h_mean, "min_bytes": bh, "gbs": bh / h_mean / 1e6}}},
+        "e2e": {"value": e2e_value, "unit": "Gcell-steps/s",
+                "h2d_bytes_per_step": int(sigma_host.numel() * 4),
+                "d2h_bytes_per_step": int(rec_host.numel() * 8)},
+        "gpu_launches": kernel_launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W.WORKLOADS[args.workload]())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

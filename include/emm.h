@@ -1,0 +1,198 @@
+/*
+ * emm.h -- C ABI of the B300 fictitious-wave-domain FDTD library (libemm).
+ *
+ * The library advances the diffusive Maxwell equations transformed to the
+ * fictitious wave domain (Yang, libEMM, arXiv 2304.00233, Sec. 2.2 Eq. 3-5)
+ * with a 2r-th order staggered leapfrog on a non-uniform rectilinear grid
+ * (Sec. 3.1 Eq. 8, 12-13), CPML absorbing layers (Sec. 3.4 Eq. 16-18), an
+ * electric dipole source, and an on-the-fly DTFT (Sec. 3.5 Eq. 19) that yields
+ * frequency-domain Green's functions (Sec. 2.2 Eq. 7) at receivers and,
+ * optionally, over the model volume.  The time loop runs in CUDA kernels on
+ * one GPU (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *   - Axes are x, y, z (index 0, 1, 2); z is positive down.  Every 3-D array
+ *     is C order [n3][n2][n1] with x fastest (Sec. 3.8).
+ *   - Field components are numbered 0..5 = Ex, Ey, Ez, Hx, Hy, Hz on the Yee
+ *     grid: Ex at (x_{i+1/2}, y_j, z_k), Ey at (x_i, y_{j+1/2}, z_k),
+ *     Ez at (x_i, y_j, z_{k+1/2}), Hx at (x_i, y_{j+1/2}, z_{k+1/2}),
+ *     Hy at (x_{i+1/2}, y_j, z_{k+1/2}), Hz at (x_{i+1/2}, y_{j+1/2}, z_k).
+ *   - The model (n1 x n2 x n3 nodes) is padded with ne buffer layers and nb
+ *     CPML layers on every face: npad = n + 2 (nb + ne) (Sec. 3.4).  Pads
+ *     repeat the edge spacing; half nodes are midpoints.  The grid holds
+ *     integer samples 0..npad-1 and half samples 0..npad-2.
+ *   - All functions return EMM_OK (0) or one of the EMM_E* codes below.  No
+ *     C++ exception crosses the ABI.  Functions are thread-safe for distinct
+ *     grids and distinct workspaces.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory owned by the caller.  The library never
+ *     allocates or frees device memory.
+ */
+#ifndef EMM_H
+#define EMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define EMM_OK 0
+#define EMM_EINVAL 1      /* invalid argument (sizes, ranges, NULL, non-monotone nodes) */
+#define EMM_ENOMEM 2      /* host allocation failed */
+#define EMM_EOUTSIDE 3    /* a source/receiver stencil leaves the non-CPML region */
+#define EMM_ECFL 4        /* dt > 1/eta: the leapfrog would be unstable (Sec. 3.2) */
+#define EMM_ECUDA 5       /* a CUDA runtime call or kernel launch failed */
+#define EMM_EWORKSPACE 6  /* workspace too small or misaligned */
+#define EMM_EDEVICE 7     /* the device flagged a bad input (see emm_status) */
+
+/* Opaque grid handle: padded nodes, half nodes, FD tables (host, FP64).
+ * Immutable after emm_make_grid; owns no device memory. */
+typedef struct emm_grid emm_grid;
+
+/* CUDA stream handle (layout-compatible with cudaStream_t); NULL = default stream. */
+typedef struct CUstream_st *emm_stream;
+
+typedef struct {
+  int n[3];            /* interior node counts along x, y, z; each >= 2 */
+  const double *x[3];  /* host: strictly ascending node coordinates (m), n[a] each */
+  int rd;              /* FD half length r, order 2r: 1..4 (Sec. 3.1, 5.7) */
+  int nb;              /* CPML layers per face, rd <= nb */
+  int ne;              /* buffer layers between CPML and model, >= 0 */
+} emm_grid_desc;
+
+typedef struct {
+  int n[3];            /* interior node counts */
+  int npad[3];         /* padded sample counts n + 2 (nb + ne) */
+  int rd, nb, ne;
+  size_t cells;        /* npad[0] * npad[1] * npad[2] */
+} emm_grid_info;
+
+/* Build a grid: pads the nodes (Sec. 3.4), forms half nodes, and tabulates
+ * the D+ / D- rows of every sample (row 1 of [V^T]^{-1}, Sec. 3.1 Eq. 9-13).
+ * desc (host, read only during the call).  *out receives a handle that the
+ * caller releases with emm_free_grid.  EMM_EINVAL for bad sizes, rd outside
+ * 1..4, nb < rd, ne < 0, or non-ascending nodes; EMM_ENOMEM. */
+int emm_make_grid(const emm_grid_desc *desc, emm_grid **out);
+
+/* Release a grid (NULL is a no-op). */
+void emm_free_grid(emm_grid *grid);
+
+/* Sizes of a grid.  EMM_EINVAL on NULL arguments. */
+int emm_grid_query(const emm_grid *grid, emm_grid_info *info);
+
+/* Table kinds for emm_grid_tables. */
+#define EMM_TAB_NODES 0      /* coef[npad+1]: padded integer nodes X (X[npad] only bounds the last half cell) */
+#define EMM_TAB_HALF 1       /* coef[npad]: half nodes Xh[i] = (X[i] + X[i+1]) / 2 */
+#define EMM_TAB_DPLUS 2      /* coef[npad][2rd]: D+ rows at Xh[i] over F[i-rd+1 .. i+rd] (Eq. 12);
+                                idx[npad]: first tap i-rd+1, or -1 where the row is off the grid */
+#define EMM_TAB_DMINUS 3     /* coef[npad][2rd]: D- rows at X[i] over half samples F[i-rd .. i+rd-1] (Eq. 13);
+                                idx[npad]: first tap i-rd, or -1 */
+#define EMM_TAB_SLAB_INT 4   /* idx[npad]: CPML slab entry 0..2nb-1 of integer sample i, or -1 */
+#define EMM_TAB_SLAB_HALF 5  /* idx[npad]: CPML slab entry 0..2nb-1 of half sample i, or -1 */
+
+/* Copy one table of axis `axis` (0..2) into host arrays (either may be NULL
+ * when the kind does not fill it).  Used by the index-map parity tests.
+ * EMM_EINVAL on a bad axis or kind. */
+int emm_grid_tables(const emm_grid *grid, int axis, int kind, double *coef, int *idx);
+
+/* Time step of the stability condition (Sec. 3.2 Eq. 14-15):
+ * vmax = sqrt(2 omega0 / (mu0 sigma_min)), eta = vmax/2 sqrt(sum_a Dmax_a^2),
+ * Dmax_a = largest absolute row sum of the D+ and D- tables of axis a.
+ * *dt = 0.99 / eta; *eta and *vmax (both may be NULL) receive the others.
+ * EMM_EINVAL if sigma_min or omega0 is not positive. */
+int emm_time_step(const emm_grid *grid, double sigma_min, double omega0,
+                  double *dt, double *eta, double *vmax);
+
+/* CPML coefficients of axis `axis` for a given vmax, fmax and dt (Eq. 17-18,
+ * kappa = 1, profile d = d0 (xi/L)^2 with d0 = -3 vmax ln(1e-3) / (2L),
+ * alpha = pi fmax (1 - xi/L)); ab (host) receives [4][2nb]:
+ * a at integer samples, b at integer samples, a at half samples, b at half
+ * samples, indexed by slab entry (EMM_TAB_SLAB_*).  EMM_EINVAL on bad input. */
+int emm_cpml_tables(const emm_grid *grid, int axis, double vmax, double fmax,
+                    double dt, double *ab);
+
+/* Stencil of a point source/receiver for component comp (0..5) at pos[3]
+ * (m): along each axis, on the component's own node array P, i = max{i :
+ * P[i] <= p}; knots i-rd+1 .. i+rd; start[a] = i-rd+1; w (host, [3][2rd])
+ * receives the Lagrange interpolation weights (row 0 of [V^T]^{-1}, Sec. 3.1).
+ * EMM_EOUTSIDE if a knot falls in a CPML slab or off the grid. */
+int emm_locate(const emm_grid *grid, int comp, const double pos[3], int start[3], double *w);
+
+/* One transmitter and its receivers. */
+typedef struct {
+  double omega0;        /* rad/s, > 0: fictitious permittivity eps = sigma / (2 omega0) (Eq. 3) */
+  double fmax;          /* Hz, > 0: Gaussian wavelet exp(-(pi fmax (t - 1.5/fmax))^2) and CPML alpha */
+  double sigma_min;     /* S/m, > 0: smallest conductivity in the model (sets vmax) */
+  double dt;            /* s: time step; <= 0 selects 0.99/eta; > 1/eta is EMM_ECFL */
+  int nt;               /* number of leapfrog steps, >= 0 */
+  double src[3];        /* source position (m) */
+  double src_az;        /* rad: azimuth of the electric dipole */
+  double src_dip;       /* rad: dip; direction (cos dip cos az, cos dip sin az, sin dip) */
+  double moment;        /* A m: dipole moment (Green's functions do not depend on it) */
+  int nrec;             /* >= 0 */
+  const double *rec;    /* host [nrec][3] receiver positions (m) */
+  int nfreq;            /* >= 1 */
+  const double *freqs;  /* host [nfreq] frequencies (Hz, > 0) */
+  int volume;           /* 1: also accumulate the DTFT of all six components on
+                           every interior sample (the n1 x n2 x n3 samples of each
+                           component's own staggered positions) */
+} emm_survey;
+
+/* Device workspace bytes emm_forward needs for this grid and survey
+ * (fields, CPML memory, 1/eps, tables).  EMM_EINVAL on bad input. */
+int emm_workspace_size(const emm_grid *grid, const emm_survey *survey, size_t *bytes);
+
+/* Run the forward time loop (Algorithm 1 without the airwave step) on
+ * `stream` and write the Green's functions.
+ *   sigma    device float [3][n3][n2][n1]: staggered sigma_xx at Ex, sigma_yy
+ *            at Ey, sigma_zz at Ez positions of the interior (Sec. 5.5); the
+ *            pads replicate the edge values.  Every value must be finite,
+ *            positive and >= survey->sigma_min (else the device status word
+ *            reports EMM_EDEVICE and the outputs are undefined).
+ *   ws       device workspace of at least emm_workspace_size bytes, 256-byte
+ *            aligned; its contents on entry do not matter.
+ *   rec_out  device double [nrec][6][nfreq][2]: (re, im) of G^EE (V/m per
+ *            A m) for components 0..2 and G^HE (A/m per A m) for 3..5 (Eq. 7).
+ *   vol_out  device double [6][nfreq][n3][n2][n1][2] when survey->volume, else
+ *            ignored (may be NULL).
+ * The call validates on the host, uploads tables with cudaMemcpyAsync, and
+ * enqueues every kernel asynchronously; it returns before the GPU finishes.
+ * Host-detected errors (EMM_EINVAL, EMM_EOUTSIDE, EMM_ECFL, EMM_EWORKSPACE)
+ * enqueue nothing; EMM_ECUDA reports a failed runtime call or launch. */
+int emm_forward(const emm_grid *grid, const emm_survey *survey, const float *sigma,
+                void *ws, size_t ws_bytes, double *rec_out, double *vol_out,
+                emm_stream stream);
+
+/* Per-kernel timing of a forward run (the per-phase breakdown of Sec. 6,
+ * Table 1, measured on the device). */
+typedef struct {
+  int every;       /* in: time the launches of every `every`-th step (>= 1) */
+  int samples;     /* out: number of steps timed */
+  double e_ms;     /* out: mean duration (ms) of one E half-step launch */
+  double h_ms;     /* out: mean duration (ms) of one H half-step launch */
+  double total_ms; /* out: duration (ms) of the whole enqueued forward run */
+} emm_timing;
+
+/* emm_forward, with CUDA events recorded on `stream` around the E and H
+ * launches of every timing->every-th step and around the whole run.  Same
+ * arguments, outputs and errors as emm_forward; in addition it synchronises
+ * `stream` before returning and fills *timing (host).  EMM_EINVAL if timing
+ * is NULL or timing->every < 1. */
+int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const float *sigma,
+                      void *ws, size_t ws_bytes, double *rec_out, double *vol_out,
+                      emm_stream stream, emm_timing *timing);
+
+/* Read the device status word of a workspace after emm_forward: synchronises
+ * `stream`, then *status = EMM_OK or EMM_EDEVICE (a sigma value was not
+ * finite, not positive, or below sigma_min).  EMM_ECUDA if the copy fails. */
+int emm_status(const void *ws, int *status, emm_stream stream);
+
+/* Static description of an error code (never NULL). */
+const char *emm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMM_H */

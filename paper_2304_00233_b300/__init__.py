@@ -1,0 +1,361 @@
+"""B300-native fictitious-wave FDTD (libEMM's method, Yang, arXiv 2304.00233).
+
+Thin Python binding of the C ABI in ``include/emm.h`` (``libemm.so``): the
+functions below only marshal arguments through ctypes.  Every step of the time
+loop runs in the library's CUDA kernels; PyTorch provides device memory and
+streams.  There is no CPU fallback: if ``libemm.so`` is missing or cannot be
+loaded, every call raises.
+
+    grid = make_grid(x, y, z, rd=2, nb=10, ne=7)
+    survey = Survey(omega0=2*pi, fmax=1.0, sigma_min=0.02, nt=7000,
+                    src=(0, 0, 950), rec=rec_xyz, freqs=[0.25, 0.75, 1.25])
+    G, vol = forward(grid, survey, sigma)     # sigma: [3][n3][n2][n1] float32
+
+``G`` is complex128 [nrec][6][nfreq]: G^EE (components 0..2) and G^HE (3..5)
+of Eq. 7; ``vol`` is [6][nfreq][n3][n2][n1] when ``survey.volume``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "libemm.so")
+
+EMM_OK, EMM_EINVAL, EMM_ENOMEM, EMM_EOUTSIDE, EMM_ECFL, EMM_ECUDA, EMM_EWORKSPACE, EMM_EDEVICE = range(8)
+TAB_NODES, TAB_HALF, TAB_DPLUS, TAB_DMINUS, TAB_SLAB_INT, TAB_SLAB_HALF = range(6)
+COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
+EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",
+            "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
+            "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror")
+
+
+class EmmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+class _GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("x", _D * 3), ("rd", C.c_int), ("nb", C.c_int), ("ne", C.c_int)]
+
+
+class _GridInfo(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("npad", C.c_int * 3), ("rd", C.c_int), ("nb", C.c_int),
+                ("ne", C.c_int), ("cells", C.c_size_t)]
+
+
+class _Timing(C.Structure):
+    _fields_ = [("every", C.c_int), ("samples", C.c_int), ("e_ms", C.c_double),
+                ("h_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class _Survey(C.Structure):
+    _fields_ = [("omega0", C.c_double), ("fmax", C.c_double), ("sigma_min", C.c_double),
+                ("dt", C.c_double), ("nt", C.c_int), ("src", C.c_double * 3),
+                ("src_az", C.c_double), ("src_dip", C.c_double), ("moment", C.c_double),
+                ("nrec", C.c_int), ("rec", _D), ("nfreq", C.c_int), ("freqs", _D),
+                ("volume", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
+    """Load libemm.so (built by ``python -m paper_2304_00233_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libemm.so not found at {path}: build it with "
+                           "`python -m paper_2304_00233_b300.build` (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    V = C.c_void_p
+    sig = {
+        "emm_make_grid": ([C.POINTER(_GridDesc), C.POINTER(V)], C.c_int),
+        "emm_free_grid": ([V], None),
+        "emm_grid_query": ([V, C.POINTER(_GridInfo)], C.c_int),
+        "emm_grid_tables": ([V, C.c_int, C.c_int, _D, _I], C.c_int),
+        "emm_time_step": ([V, C.c_double, C.c_double, _D, _D, _D], C.c_int),
+        "emm_cpml_tables": ([V, C.c_int, C.c_double, C.c_double, C.c_double, _D], C.c_int),
+        "emm_locate": ([V, C.c_int, _D, _I, _D], C.c_int),
+        "emm_workspace_size": ([V, C.POINTER(_Survey), C.POINTER(C.c_size_t)], C.c_int),
+        "emm_forward": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V], C.c_int),
+        "emm_forward_timed": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V,
+                               C.POINTER(_Timing)], C.c_int),
+        "emm_status": ([V, _I, V], C.c_int),
+        "emm_strerror": ([C.c_int], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load_library().emm_strerror(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != EMM_OK:
+        raise EmmError(code, what)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+class Grid:
+    """Handle of an ``emm_grid`` (padded nodes, half nodes, FD rows)."""
+
+    def __init__(self, x, y, z, rd: int = 2, nb: int = 10, ne: Optional[int] = None):
+        lib = load_library()
+        self._axes = [_f64(x), _f64(y), _f64(z)]
+        self.rd, self.nb = int(rd), int(nb)
+        self.ne = int(rd + 5 if ne is None else ne)
+        d = _GridDesc()
+        d.n = (C.c_int * 3)(*[len(a) for a in self._axes])
+        d.x = (_D * 3)(*[_dp(a) for a in self._axes])
+        d.rd, d.nb, d.ne = self.rd, self.nb, self.ne
+        h = C.c_void_p()
+        _check(lib.emm_make_grid(C.byref(d), C.byref(h)), "emm_make_grid")
+        self._h = h
+        info = _GridInfo()
+        _check(lib.emm_grid_query(h, C.byref(info)), "emm_grid_query")
+        self.n = tuple(info.n)
+        self.npad = tuple(info.npad)
+        self.cells = int(info.cells)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.emm_free_grid(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def table(self, axis: int, kind: int):
+        """Test hook: ``emm_grid_tables`` as numpy arrays (coef, idx)."""
+        np_ = self.npad[axis]
+        m = 2 * self.rd
+        coef = idx = None
+        if kind == TAB_NODES:
+            coef = np.zeros(np_ + 1)
+        elif kind == TAB_HALF:
+            coef = np.zeros(np_)
+        elif kind in (TAB_DPLUS, TAB_DMINUS):
+            coef, idx = np.zeros((np_, m)), np.zeros(np_, np.int32)
+        else:
+            idx = np.zeros(np_, np.int32)
+        _check(load_library().emm_grid_tables(self._h, axis, kind, _dp(coef),
+                                              None if idx is None else idx.ctypes.data_as(_I)),
+               "emm_grid_tables")
+        return coef, idx
+
+    def time_step(self, sigma_min: float, omega0: float) -> Tuple[float, float, float]:
+        """(dt, eta, vmax) of Sec. 3.2."""
+        dt, eta, vmax = C.c_double(), C.c_double(), C.c_double()
+        _check(load_library().emm_time_step(self._h, sigma_min, omega0, C.byref(dt), C.byref(eta),
+                                            C.byref(vmax)), "emm_time_step")
+        return dt.value, eta.value, vmax.value
+
+    def cpml_tables(self, axis: int, vmax: float, fmax: float, dt: float) -> np.ndarray:
+        ab = np.zeros((4, 2 * self.nb))
+        _check(load_library().emm_cpml_tables(self._h, axis, vmax, fmax, dt, _dp(ab)), "emm_cpml_tables")
+        return ab
+
+    def locate(self, comp: int, pos) -> Tuple[np.ndarray, np.ndarray]:
+        pos = _f64(pos)
+        start = np.zeros(3, np.int32)
+        w = np.zeros((3, 2 * self.rd))
+        _check(load_library().emm_locate(self._h, comp, _dp(pos), start.ctypes.data_as(_I), _dp(w)),
+               "emm_locate")
+        return start, w
+
+
+def make_grid(x, y, z, rd: int = 2, nb: int = 10, ne: Optional[int] = None) -> Grid:
+    return Grid(x, y, z, rd, nb, ne)
+
+
+@dataclasses.dataclass
+class Survey:
+    """One transmitter, its receivers and the frequencies (``emm_survey``)."""
+    omega0: float
+    fmax: float
+    sigma_min: float
+    nt: int
+    src: Sequence[float] = (0.0, 0.0, 0.0)
+    rec: Optional[np.ndarray] = None
+    freqs: Sequence[float] = (1.0,)
+    dt: float = 0.0
+    src_az: float = 0.0
+    src_dip: float = 0.0
+    moment: float = 1.0
+    volume: bool = False
+
+    def _c(self) -> Tuple[_Survey, list]:
+        rec = _f64(np.zeros((0, 3)) if self.rec is None else self.rec).reshape(-1, 3)
+        freqs = _f64(self.freqs)
+        s = _Survey()
+        s.omega0, s.fmax, s.sigma_min, s.dt = self.omega0, self.fmax, self.sigma_min, self.dt
+        s.nt = int(self.nt)
+        s.src = (C.c_double * 3)(*[float(v) for v in self.src])
+        s.src_az, s.src_dip, s.moment = self.src_az, self.src_dip, self.moment
+        s.nrec = rec.shape[0]
+        s.rec = _dp(rec) if rec.shape[0] else None
+        s.nfreq = len(freqs)
+        s.freqs = _dp(freqs) if len(freqs) else None
+        s.volume = int(bool(self.volume))
+        return s, [rec, freqs]   # the arrays must outlive every use of the struct
+
+    @property
+    def nrec(self) -> int:
+        return 0 if self.rec is None else int(np.asarray(self.rec).reshape(-1, 3).shape[0])
+
+
+def workspace_size(grid: Grid, survey: Survey) -> int:
+    s, keep = survey._c()
+    out = C.c_size_t()
+    _check(load_library().emm_workspace_size(grid.handle, C.byref(s), C.byref(out)), "emm_workspace_size")
+    return int(out.value)
+
+
+class Workspace:
+    """Device buffers of one forward configuration, reusable across calls."""
+
+    def __init__(self, grid: Grid, survey: Survey, device=None):
+        import torch
+        self.device = torch.device("cuda" if device is None else device)
+        self.bytes = workspace_size(grid, survey)
+        self.ws = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ptr = self.ws.data_ptr() + off
+        nf = len(survey.freqs)
+        self.rec = torch.zeros((max(survey.nrec, 1), 6, nf, 2), dtype=torch.float64, device=self.device)
+        self.vol = None
+        if survey.volume:
+            n1, n2, n3 = grid.n
+            self.vol = torch.empty((6, nf, n3, n2, n1, 2), dtype=torch.float64, device=self.device)
+
+
+def _check_sigma(grid: Grid, sigma):
+    import torch
+    if not (isinstance(sigma, torch.Tensor) and sigma.is_cuda and sigma.dtype == torch.float32
+            and sigma.is_contiguous()):
+        raise TypeError("sigma must be a contiguous CUDA float32 tensor [3][n3][n2][n1]")
+    n1, n2, n3 = grid.n
+    if tuple(sigma.shape) != (3, n3, n2, n1):
+        raise ValueError(f"sigma shape {tuple(sigma.shape)} != (3, {n3}, {n2}, {n1})")
+
+
+def forward_async(grid: Grid, survey: Survey, sigma, work: Workspace, stream=None) -> None:
+    """Enqueue ``emm_forward`` on ``stream`` (default: torch's current stream)
+    using the buffers of ``work``; ``sigma`` is a CUDA float32 tensor
+    [3][n3][n2][n1]."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    s, keep = survey._c()
+    code = load_library().emm_forward(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(work.ptr),
+        C.c_size_t(work.bytes), C.c_void_p(work.rec.data_ptr()),
+        C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream))
+    _check(code, "emm_forward")
+
+
+def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int = 64,
+                  stream=None) -> dict:
+    """``emm_forward_timed``: like ``forward_async`` but synchronises and
+    returns the mean device duration of the E and H launches (sampled every
+    ``every`` steps) and of the whole run, in ms."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    s, keep = survey._c()
+    t = _Timing()
+    t.every = int(every)
+    code = load_library().emm_forward_timed(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(work.ptr),
+        C.c_size_t(work.bytes), C.c_void_p(work.rec.data_ptr()),
+        C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream),
+        C.byref(t))
+    _check(code, "emm_forward_timed")
+    return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, total_ms=t.total_ms)
+
+
+def status(work: Workspace, stream=None) -> int:
+    """Device status word of the last forward run on ``work`` (synchronises)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(work.device)
+    st = C.c_int()
+    _check(load_library().emm_status(C.c_void_p(work.ptr), C.byref(st), C.c_void_p(stream.cuda_stream)),
+           "emm_status")
+    return int(st.value)
+
+
+def forward(grid: Grid, survey: Survey, sigma, work: Optional[Workspace] = None, check: bool = True):
+    """Run one forward solve and return (G, vol) as complex128 torch tensors on
+    the GPU (``vol`` is None unless ``survey.volume``).  ``sigma`` may be a
+    numpy array or a CPU tensor; it is copied to the GPU first."""
+    import torch
+    if not isinstance(sigma, torch.Tensor):
+        sigma = torch.from_numpy(np.ascontiguousarray(sigma, dtype=np.float32))
+    if not sigma.is_cuda:
+        sigma = sigma.to(device="cuda", dtype=torch.float32, non_blocking=True)
+    sigma = sigma.contiguous()
+    if work is None:
+        work = Workspace(grid, survey, sigma.device)
+    forward_async(grid, survey, sigma, work)
+    if check:
+        st = status(work)
+        if st != EMM_OK:
+            raise EmmError(st, "emm_forward (device status)")
+    G = torch.view_as_complex(work.rec)[: survey.nrec]
+    vol = None if work.vol is None else torch.view_as_complex(work.vol)
+    return G, vol
+
+
+def survey_for(workload, nt: Optional[int] = None, dt: float = 0.0, **kw) -> Survey:
+    """Survey of a :class:`workloads.Workload` (sigma_min from its model)."""
+    nt = workload.nt if nt is None else nt
+    if nt is None:
+        raise ValueError("nt required (the workload fixes only t_max)")
+    args = dict(omega0=workload.omega0, fmax=workload.fmax,
+                sigma_min=float(np.min(workload.sigma)), nt=int(nt), src=tuple(workload.src),
+                rec=workload.rec, freqs=tuple(workload.freqs), dt=dt, src_az=workload.src_az,
+                src_dip=workload.src_dip, moment=workload.moment, volume=workload.volume)
+    args.update(kw)
+    return Survey(**args)
+
+
+def grid_for(workload) -> Grid:
+    return Grid(workload.x, workload.y, workload.z, workload.rd, workload.nb, workload.ne)
+
+
+def steps_for(workload, grid: Optional[Grid] = None) -> int:
+    """ceil(t_max / dt) with dt = 0.99/eta of the workload's grid and model."""
+    if workload.nt is not None:
+        return int(workload.nt)
+    grid = grid_for(workload) if grid is None else grid
+    dt, _, _ = grid.time_step(float(np.min(workload.sigma)), workload.omega0)
+    return int(math.ceil(workload.t_max / dt))

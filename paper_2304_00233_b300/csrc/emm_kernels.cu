@@ -1,0 +1,800 @@
+// emm_kernels.cu -- sm_103a kernels of the fictitious-wave FDTD time loop and
+// the emm_forward / emm_forward_timed / emm_workspace_size / emm_status
+// entry points.
+//
+// One leapfrog step (Algorithm 1 without the airwave step) is two launches:
+//
+//   k_update_E<R>  curl H with D- rows and CPML memory (Eq. 13, 16-18), the
+//                  electric source at t_{n+1/2}, E += dt/eps (curl H - J)
+//                  (Eq. 8); extra CTAs accumulate the receiver DTFT of
+//                  H^{n+1/2} (Eq. 19), which this launch only reads; interior
+//                  threads accumulate the volume DTFT of H^{n+1/2}.
+//   k_update_H<R>  curl E with D+ rows and CPML memory (Eq. 12, 16-18),
+//                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
+//                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
+//
+// Each stencil CTA owns a TX x TY tile of (i, j) columns and marches z over a
+// chunk of planes.  The z taps of the two fields differentiated along z sit
+// in a per-thread register queue of 2R planes; the current plane of the three
+// fields is staged in shared memory with the x/y halos.  Fields are FP32,
+// the receiver DTFT accumulates in FP64 and the volume DTFT in compensated
+// FP32 (hi + lo pairs).  No device transcendentals: every exp/sin/cos comes
+// from FP64 host tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "emm_internal.h"
+
+namespace emm {
+namespace {
+
+constexpr int TX = 32;  // tile width (x, one warp)
+constexpr int TY = 8;   // tile height (y)
+constexpr int NT = TX * TY;
+
+__device__ __forceinline__ int slab_int(int i, int np, int nb) {
+  return i < nb ? i : (i >= np - nb ? nb + np - 1 - i : -1);
+}
+__device__ __forceinline__ int slab_half(int i, int np, int nb) {
+  return i < nb ? i : ((i >= np - 1 - nb && i <= np - 2) ? nb + np - 2 - i : -1);
+}
+
+// CPML memory array of a derivative along axis a: the slab (2nb entries)
+// replaces that axis.  x: [np2][np1][2nb], y: [np2][2nb][np0], z: [2nb][np1][np0].
+__device__ __forceinline__ size_t psi_at(int a, int s, int i, int j, int k, const int *np, int nb2) {
+  if (a == 0) return (static_cast<size_t>(k) * np[1] + j) * nb2 + s;
+  if (a == 1) return (static_cast<size_t>(k) * nb2 + s) * np[0] + i;
+  return (static_cast<size_t>(s) * np[1] + j) * np[0] + i;
+}
+
+// psi <- b psi + a d ; return d + psi   (Eq. 16-17, kappa = 1)
+__device__ __forceinline__ float cpml(float d, float *psi, size_t idx, const float *tab, int s, int nb,
+                                      bool half) {
+  const float a = tab[(half ? 4 : 0) * nb + s];
+  const float b = tab[(half ? 6 : 2) * nb + s];
+  const float v = fmaf(b, psi[idx], a * d);
+  psi[idx] = v;
+  return d + v;
+}
+
+// Error-free accumulation (hi, lo) += v  (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+  const float t = hi + v;
+  const float bp = t - hi;
+  const float err = (hi - (t - bp)) + (v - bp);
+  hi = t;
+  lo += err;
+}
+
+__device__ __forceinline__ void volume_accumulate(const DevParams &p, int comp, int lin, size_t nint,
+                                                  const float *fac, float v) {
+  for (int f = 0; f < p.nf; ++f) {
+    float4 *a = p.vacc + (static_cast<size_t>(comp) * p.nf + f) * nint + lin;
+    float4 acc = *a;
+    two_sum_add(acc.x, acc.y, fac[2 * f] * v);
+    two_sum_add(acc.z, acc.w, fac[2 * f + 1] * v);
+    *a = acc;
+  }
+}
+
+// One warp per (receiver, component): (2R)^3 weighted gather in FP64, warp
+// shuffle reduction, then acc += factor * value for every frequency.
+template <int R>
+__device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, const double *fac, int block) {
+  constexpr int M = 2 * R;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = block * (NT / 32) + warp;
+  if (item >= p.nrec * 3) return;
+  const int rec = item / 3, c = comp0 + item % 3;
+  const int *st = p.rec_start + (rec * 6 + c) * 3;
+  const double *w = p.rec_w + static_cast<size_t>(rec * 6 + c) * 3 * M;
+  const float *f = F[c - comp0];
+  double s = 0.0;
+  for (int t = lane; t < M * M * M; t += 32) {
+    const int q1 = t % M, q2 = (t / M) % M, q3 = t / (M * M);
+    const size_t id = (static_cast<size_t>(st[2] + q3) * p.np[1] + (st[1] + q2)) * p.np[0] + (st[0] + q1);
+    s += w[q1] * w[M + q2] * w[2 * M + q3] * static_cast<double>(f[id]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double *acc = p.rec_acc + static_cast<size_t>(rec * 6 + c) * p.nf * 2;
+    for (int q = 0; q < p.nf; ++q) {
+      acc[2 * q] += fac[2 * q] * s;
+      acc[2 * q + 1] += fac[2 * q + 1] * s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(NT) k_update_E(const DevParams p, const int n) {
+  constexpr int M = 2 * R;
+  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
+    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
+    return;
+  }
+  __shared__ float sHz[TY + 2 * R][TX + 2 * R];  // plane k, x and y halo
+  __shared__ float sHy[TY][TX + 2 * R];          // plane k, x halo
+  __shared__ float sHx[TY + 2 * R][TX];          // plane k, y halo
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const int b = blockIdx.x;
+  const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const size_t plane = static_cast<size_t>(np0) * np1;
+  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
+  const bool in_ij = i < np0 && j < np1;
+  const size_t col = static_cast<size_t>(j) * np0 + i;
+  const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
+  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
+  float cx[M], cy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    cx[q] = dm_i ? p.cm[0][i * M + q] : 0.f;
+    cy[q] = dm_j ? p.cm[1][j * M + q] : 0.f;
+  }
+  const float amp = p.amp[n];
+  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+  const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+  const int ii = i - p.nbe, jj = j - p.nbe;
+  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+
+  float qx[M], qy[M];  // Hx, Hy at planes k-R .. k+R-1 of this column
+#pragma unroll
+  for (int q = 0; q < M - 1; ++q) {
+    const int kk = k0 - R + q;
+    const bool ok = in_ij && kk >= 0 && kk < np2;
+    qx[q] = ok ? p.H[0][kk * plane + col] : 0.f;
+    qy[q] = ok ? p.H[1][kk * plane + col] : 0.f;
+  }
+  for (int k = k0; k < k1; ++k) {
+    {
+      const int kk = k + R - 1;
+      const bool ok = in_ij && kk < np2;
+      qx[M - 1] = ok ? p.H[0][kk * plane + col] : 0.f;
+      qy[M - 1] = ok ? p.H[1][kk * plane + col] : 0.f;
+    }
+    const float *Hx = p.H[0] + k * plane, *Hy = p.H[1] + k * plane, *Hz = p.H[2] + k * plane;
+    for (int t = threadIdx.x; t < (TY + 2 * R) * (TX + 2 * R); t += NT) {
+      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
+      const int y = j0 - R + r, x = i0 - R + c;
+      sHz[r][c] = (y >= 0 && y < np1 && x >= 0 && x < np0) ? Hz[y * np0 + x] : 0.f;
+    }
+    for (int t = threadIdx.x; t < TY * (TX + 2 * R); t += NT) {
+      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
+      const int y = j0 + r, x = i0 - R + c;
+      sHy[r][c] = (y < np1 && x >= 0 && x < np0) ? Hy[y * np0 + x] : 0.f;
+    }
+    for (int t = threadIdx.x; t < (TY + 2 * R) * TX; t += NT) {
+      const int r = t / TX, c = t % TX;
+      const int y = j0 - R + r, x = i0 + c;
+      sHx[r][c] = (y >= 0 && y < np1 && x < np0) ? Hx[y * np0 + x] : 0.f;
+    }
+    __syncthreads();
+    if (in_ij) {
+      const bool dm_k = k >= R && k <= np2 - 1 - R;
+      const int sk = slab_int(k, np2, nb);
+      float cz[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) cz[q] = dm_k ? p.cm[2][k * M + q] : 0.f;
+      const size_t id = k * plane + col;
+      // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+      if (i <= np0 - 2 && dm_j && dm_k) {
+        float dy = 0.f, dz = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dy = fmaf(cy[q], sHz[ty + q][tx + R], dy);
+          dz = fmaf(cz[q], qy[q], dz);
+        }
+        if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+        if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+        float curl = dy - dz;
+        if (p.src_on[0]) {
+          const int a = i - p.src_start[0][0], bb = j - p.src_start[0][1], c = k - p.src_start[0][2];
+          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[0][(c * M + bb) * M + a];
+        }
+        p.E[0][id] = fmaf(p.ie[0][id], curl, p.E[0][id]);
+      }
+      // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+      if (j <= np1 - 2 && dm_i && dm_k) {
+        float dz = 0.f, dx = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dz = fmaf(cz[q], qx[q], dz);
+          dx = fmaf(cx[q], sHz[ty + R][tx + q], dx);
+        }
+        if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+        if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+        float curl = dz - dx;
+        if (p.src_on[1]) {
+          const int a = i - p.src_start[1][0], bb = j - p.src_start[1][1], c = k - p.src_start[1][2];
+          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[1][(c * M + bb) * M + a];
+        }
+        p.E[1][id] = fmaf(p.ie[1][id], curl, p.E[1][id]);
+      }
+      // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+      if (k <= np2 - 2 && dm_i && dm_j) {
+        float dx = 0.f, dy = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dx = fmaf(cx[q], sHy[ty][tx + q], dx);
+          dy = fmaf(cy[q], sHx[ty + q][tx], dy);
+        }
+        if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+        if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+        float curl = dx - dy;
+        if (p.src_on[2]) {
+          const int a = i - p.src_start[2][0], bb = j - p.src_start[2][1], c = k - p.src_start[2][2];
+          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[2][(c * M + bb) * M + a];
+        }
+        p.E[2][id] = fmaf(p.ie[2][id], curl, p.E[2][id]);
+      }
+      // volume DTFT of H^{n+1/2} (centre values of plane k)
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 3, lin, nint, facH, qx[R]);
+        volume_accumulate(p, 4, lin, nint, facH, qy[R]);
+        volume_accumulate(p, 5, lin, nint, facH, sHz[ty + R][tx + R]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < M - 1; ++q) {
+      qx[q] = qx[q + 1];
+      qy[q] = qy[q + 1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(NT) k_update_H(const DevParams p, const int n) {
+  constexpr int M = 2 * R;
+  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
+    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
+    return;
+  }
+  __shared__ float sEz[TY + 2 * R][TX + 2 * R];  // plane k, x and y halo
+  __shared__ float sEy[TY][TX + 2 * R];          // plane k, x halo
+  __shared__ float sEx[TY + 2 * R][TX];          // plane k, y halo
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const int b = blockIdx.x;
+  const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const size_t plane = static_cast<size_t>(np0) * np1;
+  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
+  const bool in_ij = i < np0 && j < np1;
+  const size_t col = static_cast<size_t>(j) * np0 + i;
+  const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
+  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
+  float cx[M], cy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    cx[q] = dp_i ? p.cp[0][i * M + q] : 0.f;
+    cy[q] = dp_j ? p.cp[1][j * M + q] : 0.f;
+  }
+  const float dt_mu = p.dt_mu;
+  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+  const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
+  const int ii = i - p.nbe, jj = j - p.nbe;
+  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+
+  float qx[M], qy[M];  // Ex, Ey at planes k-R+1 .. k+R of this column
+#pragma unroll
+  for (int q = 0; q < M - 1; ++q) {
+    const int kk = k0 - R + 1 + q;
+    const bool ok = in_ij && kk >= 0 && kk < np2;
+    qx[q] = ok ? p.E[0][kk * plane + col] : 0.f;
+    qy[q] = ok ? p.E[1][kk * plane + col] : 0.f;
+  }
+  for (int k = k0; k < k1; ++k) {
+    {
+      const int kk = k + R;
+      const bool ok = in_ij && kk < np2;
+      qx[M - 1] = ok ? p.E[0][kk * plane + col] : 0.f;
+      qy[M - 1] = ok ? p.E[1][kk * plane + col] : 0.f;
+    }
+    const float *Ex = p.E[0] + k * plane, *Ey = p.E[1] + k * plane, *Ez = p.E[2] + k * plane;
+    for (int t = threadIdx.x; t < (TY + 2 * R) * (TX + 2 * R); t += NT) {
+      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
+      const int y = j0 - R + r, x = i0 - R + c;
+      sEz[r][c] = (y >= 0 && y < np1 && x >= 0 && x < np0) ? Ez[y * np0 + x] : 0.f;
+    }
+    for (int t = threadIdx.x; t < TY * (TX + 2 * R); t += NT) {
+      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
+      const int y = j0 + r, x = i0 - R + c;
+      sEy[r][c] = (y < np1 && x >= 0 && x < np0) ? Ey[y * np0 + x] : 0.f;
+    }
+    for (int t = threadIdx.x; t < (TY + 2 * R) * TX; t += NT) {
+      const int r = t / TX, c = t % TX;
+      const int y = j0 - R + r, x = i0 + c;
+      sEx[r][c] = (y >= 0 && y < np1 && x < np0) ? Ex[y * np0 + x] : 0.f;
+    }
+    __syncthreads();
+    if (in_ij) {
+      const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
+      const int sk = slab_half(k, np2, nb);
+      float cz[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) cz[q] = dp_k ? p.cp[2][k * M + q] : 0.f;
+      const size_t id = k * plane + col;
+      // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+      if (dp_j && dp_k) {
+        float dy = 0.f, dz = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dy = fmaf(cy[q], sEz[ty + 1 + q][tx + R], dy);
+          dz = fmaf(cz[q], qy[q], dz);
+        }
+        if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+        if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+        p.H[0][id] = fmaf(-dt_mu, dy - dz, p.H[0][id]);
+      }
+      // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+      if (dp_i && dp_k) {
+        float dz = 0.f, dx = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dz = fmaf(cz[q], qx[q], dz);
+          dx = fmaf(cx[q], sEz[ty + R][tx + 1 + q], dx);
+        }
+        if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+        if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+        p.H[1][id] = fmaf(-dt_mu, dz - dx, p.H[1][id]);
+      }
+      // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+      if (dp_i && dp_j) {
+        float dx = 0.f, dy = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dx = fmaf(cx[q], sEy[ty][tx + 1 + q], dx);
+          dy = fmaf(cy[q], sEx[ty + 1 + q][tx], dy);
+        }
+        if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+        if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+        p.H[2][id] = fmaf(-dt_mu, dx - dy, p.H[2][id]);
+      }
+      // volume DTFT of E^{n+1} (centre values of plane k)
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
+        volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
+        volume_accumulate(p, 2, lin, nint, facE, sEz[ty + R][tx + R]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < M - 1; ++q) {
+      qx[q] = qx[q + 1];
+      qy[q] = qy[q + 1];
+    }
+  }
+}
+
+// dt/eps on the padded grid from the interior staggered conductivity, with
+// the pads replicating the edge (model extension, Sec. 3.4), and the input
+// check (finite, positive, >= sigma_min).
+__global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie1, float *ie2, int n0,
+                          int n1, int n2, int np0, int np1, int np2, int nbe, double two_w0_dt,
+                          double sigma_min, int *status) {
+  const size_t cells = static_cast<size_t>(np0) * np1 * np2;
+  const size_t nint = static_cast<size_t>(n0) * n1 * n2;
+  float *ie[3] = {ie0, ie1, ie2};
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < 3 * cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(t / cells);
+    const size_t r = t % cells;
+    const int i = static_cast<int>(r % np0), j = static_cast<int>((r / np0) % np1),
+              k = static_cast<int>(r / (static_cast<size_t>(np0) * np1));
+    const int a = min(max(i - nbe, 0), n0 - 1), b = min(max(j - nbe, 0), n1 - 1),
+              cc = min(max(k - nbe, 0), n2 - 1);
+    const float s = sigma[c * nint + (static_cast<size_t>(cc) * n1 + b) * n0 + a];
+    if (!(s > 0.f) || !isfinite(s) || static_cast<double>(s) < sigma_min) {
+      atomicExch(status, EMM_EDEVICE);
+      ie[c][r] = 0.f;
+    } else {
+      ie[c][r] = static_cast<float>(two_w0_dt / static_cast<double>(s));
+    }
+  }
+}
+
+// Green's functions at receivers, in place: G = norm[c][f] * acc  (Eq. 7)
+__global__ void k_finalize_rec(double *acc, const double *norm, int nrec, int nf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrec * 6 * nf) return;
+  const int f = t % nf, c = (t / nf) % 6;
+  const double nr = norm[(c < 3 ? 0 : 1) * nf * 2 + 2 * f], ni = norm[(c < 3 ? 0 : 1) * nf * 2 + 2 * f + 1];
+  const double ar = acc[2 * t], ai = acc[2 * t + 1];
+  acc[2 * t] = nr * ar - ni * ai;
+  acc[2 * t + 1] = nr * ai + ni * ar;
+}
+
+// Volume Green's functions: vol[c][f][..] = norm[c][f] * (hi + lo)
+__global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *norm, size_t nint, int nf) {
+  const size_t total = 6 * static_cast<size_t>(nf) * nint;
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int cf = static_cast<int>(t / nint);
+    const int f = cf % nf, c = cf / nf;
+    const double nr = norm[(c < 3 ? 0 : 1) * nf * 2 + 2 * f], ni = norm[(c < 3 ? 0 : 1) * nf * 2 + 2 * f + 1];
+    const float4 a = vacc[t];
+    const double ar = static_cast<double>(a.x) + a.y, ai = static_cast<double>(a.z) + a.w;
+    vol[2 * t] = nr * ar - ni * ai;
+    vol[2 * t + 1] = nr * ai + ni * ar;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side of emm_forward
+// ---------------------------------------------------------------------------
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Byte layout of the device workspace.
+struct Layout {
+  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], vacc, zero_end;
+  size_t cm[3], cp[3], pml[3], jw[3], amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
+};
+
+size_t psi_elems(const emm_grid *g, int axis) {
+  const size_t nb2 = 2 * static_cast<size_t>(g->nb);
+  const size_t p0 = g->ax[0].npad, p1 = g->ax[1].npad, p2 = g->ax[2].npad;
+  if (axis == 0) return p2 * p1 * nb2;
+  if (axis == 1) return p2 * nb2 * p0;
+  return nb2 * p1 * p0;
+}
+
+// Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
+inline int psi_axis(int c) { return (c % 2 == 0) ? (c / 2 + 1) % 3 : (c / 2 + 2) % 3; }
+
+Layout plan(const emm_grid *g, const emm_survey *s) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t cells = static_cast<size_t>(g->ax[0].npad) * g->ax[1].npad * g->ax[2].npad;
+  const size_t nint = static_cast<size_t>(g->ax[0].n) * g->ax[1].n * g->ax[2].n;
+  const size_t m = 2 * static_cast<size_t>(g->rd), nf = s->nfreq;
+  const size_t nt = s->nt > 0 ? s->nt : 1, nrec = s->nrec > 0 ? s->nrec : 1;
+  L.status = take(sizeof(int));
+  for (int c = 0; c < 3; ++c) L.E[c] = take(cells * 4);
+  for (int c = 0; c < 3; ++c) L.H[c] = take(cells * 4);
+  for (int c = 0; c < 6; ++c) L.psiE[c] = take(psi_elems(g, psi_axis(c)) * 4);
+  for (int c = 0; c < 6; ++c) L.psiH[c] = take(psi_elems(g, psi_axis(c)) * 4);
+  L.vacc = take(s->volume ? 6 * nf * nint * sizeof(float4) : 0);
+  L.zero_end = off;
+  for (int c = 0; c < 3; ++c) L.ie[c] = take(cells * 4);
+  for (int a = 0; a < 3; ++a) L.cm[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  for (int a = 0; a < 3; ++a) L.cp[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  for (int a = 0; a < 3; ++a) L.pml[a] = take(8 * static_cast<size_t>(g->nb) * 4);
+  for (int c = 0; c < 3; ++c) L.jw[c] = take(m * m * m * 4);
+  L.amp = take(nt * 4);
+  L.rec_start = take(nrec * 18 * sizeof(int));
+  L.rec_w = take(nrec * 18 * m * sizeof(double));
+  L.fE = take(nt * nf * 2 * sizeof(double));
+  L.fH = take(nt * nf * 2 * sizeof(double));
+  L.fE32 = take(nt * nf * 2 * sizeof(float));
+  L.fH32 = take(nt * nf * 2 * sizeof(float));
+  L.norm = take(2 * nf * 2 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+int check_survey(const emm_grid *g, const emm_survey *s) {
+  if (!g || !s) return EMM_EINVAL;
+  if (!(s->omega0 > 0) || !(s->fmax > 0) || !(s->sigma_min > 0) || !std::isfinite(s->sigma_min)) return EMM_EINVAL;
+  if (s->nt < 0 || s->nfreq < 1 || !s->freqs || s->nrec < 0 || (s->nrec > 0 && !s->rec)) return EMM_EINVAL;
+  for (int f = 0; f < s->nfreq; ++f)
+    if (!(s->freqs[f] > 0) || !std::isfinite(s->freqs[f])) return EMM_EINVAL;
+  if (!std::isfinite(s->moment) || !std::isfinite(s->src_az) || !std::isfinite(s->src_dip)) return EMM_EINVAL;
+  return EMM_OK;
+}
+
+// Optional per-launch timing: events before/after the E and H launches of
+// every `every`-th step (3 events per timed step).
+struct StepEvents {
+  int every = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+template <int R>
+cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st, StepEvents *te) {
+  size_t used = 0;
+  for (int n = 0; n < nt; ++n) {
+    const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
+    if (timed) cudaEventRecord(te->ev[used], st);
+    k_update_E<R><<<blocks, NT, 0, st>>>(p, n);
+    if (timed) cudaEventRecord(te->ev[used + 1], st);
+    k_update_H<R><<<blocks, NT, 0, st>>>(p, n);
+    if (timed) {
+      cudaEventRecord(te->ev[used + 2], st);
+      used += 3;
+    }
+  }
+  return cudaGetLastError();
+}
+
+int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                 double *rec_out, double *vol_out, emm_stream stream, StepEvents *te) {
+  int st = check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
+  const Layout L = plan(g, s);
+  if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int rd = g->rd, m = 2 * rd, nf = s->nfreq, nt = s->nt, nb = g->nb;
+  const int nbe = g->nb + g->ne;
+
+  // time step (Sec. 3.2) and vmax
+  double dt_max, eta, vmax;
+  st = emm_time_step(g, s->sigma_min, s->omega0, &dt_max, &eta, &vmax);
+  if (st != EMM_OK) return st;
+  const double dt = (s->dt > 0) ? s->dt : dt_max;
+  if (dt * eta > 1.0) return EMM_ECFL;
+
+  // ---- host tables, packed at their workspace offsets ----
+  const size_t tab0 = L.cm[0];
+  std::vector<unsigned char> blob;
+  try {
+    blob.assign(L.total - tab0, 0);
+  } catch (const std::bad_alloc &) {
+    return EMM_ENOMEM;
+  }
+  auto at = [&](size_t off) { return blob.data() + (off - tab0); };
+  for (int a = 0; a < 3; ++a) {
+    const Axis &ax = g->ax[a];
+    float *cm = reinterpret_cast<float *>(at(L.cm[a]));
+    float *cp = reinterpret_cast<float *>(at(L.cp[a]));
+    for (size_t q = 0; q < ax.cm.size(); ++q) cm[q] = static_cast<float>(ax.cm[q]);
+    for (size_t q = 0; q < ax.cp.size(); ++q) cp[q] = static_cast<float>(ax.cp[q]);
+    std::vector<double> ab(8 * static_cast<size_t>(nb));
+    cpml_axis(g, a, vmax, s->fmax, dt, ab.data());
+    float *pm = reinterpret_cast<float *>(at(L.pml[a]));
+    for (size_t q = 0; q < ab.size(); ++q) pm[q] = static_cast<float>(ab[q]);
+  }
+  // source: J_node = moment s(t) dir_c w_node / V_node, V = dual-cell volume
+  const double dir[3] = {std::cos(s->src_dip) * std::cos(s->src_az), std::cos(s->src_dip) * std::sin(s->src_az),
+                         std::sin(s->src_dip)};
+  DevParams p{};
+  for (int c = 0; c < 3; ++c) {
+    p.src_on[c] = 0;
+    if (dir[c] == 0.0) continue;
+    int start[3];
+    double w[3][2 * kMaxRd];
+    for (int a = 0; a < 3; ++a) {
+      st = locate_axis(g, a, kHalf[c][a], s->src[a], &start[a], w[a]);
+      if (st != EMM_OK) return st;
+    }
+    float *jw = reinterpret_cast<float *>(at(L.jw[c]));
+    for (int q3 = 0; q3 < m; ++q3)
+      for (int q2 = 0; q2 < m; ++q2)
+        for (int q1 = 0; q1 < m; ++q1) {
+          const int idx[3] = {start[0] + q1, start[1] + q2, start[2] + q3};
+          double vol = 1.0;
+          for (int a = 0; a < 3; ++a) {
+            const Axis &ax = g->ax[a];
+            vol *= kHalf[c][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+          }
+          jw[(q3 * m + q2) * m + q1] = static_cast<float>(dir[c] * w[0][q1] * w[1][q2] * w[2][q3] / vol);
+        }
+    p.src_on[c] = 1;
+    for (int a = 0; a < 3; ++a) p.src_start[c][a] = start[a];
+  }
+  // receivers: stencils of all six components
+  int *rs = reinterpret_cast<int *>(at(L.rec_start));
+  double *rw = reinterpret_cast<double *>(at(L.rec_w));
+  for (int r = 0; r < s->nrec; ++r)
+    for (int c = 0; c < 6; ++c)
+      for (int a = 0; a < 3; ++a) {
+        st = locate_axis(g, a, kHalf[c][a], s->rec[3 * r + a], &rs[(r * 6 + c) * 3 + a],
+                         rw + (static_cast<size_t>(r * 6 + c) * 3 + a) * m);
+        if (st != EMM_OK) return st;
+      }
+  // wavelet samples at t_{n+1/2} and DTFT factors e^{i w' t} dt, w' = (1+i) sqrt(w w0)
+  float *amp = reinterpret_cast<float *>(at(L.amp));
+  double *fE = reinterpret_cast<double *>(at(L.fE)), *fH = reinterpret_cast<double *>(at(L.fH));
+  float *fE32 = reinterpret_cast<float *>(at(L.fE32)), *fH32 = reinterpret_cast<float *>(at(L.fH32));
+  std::vector<std::complex<double>> jhat(nf, 0.0), wp(nf);
+  for (int f = 0; f < nf; ++f)
+    wp[f] = std::complex<double>(1.0, 1.0) * std::sqrt(2.0 * M_PI * s->freqs[f] * s->omega0);
+  const double t0 = 1.5 / s->fmax;
+  const std::complex<double> I(0.0, 1.0);
+  for (int n = 0; n < nt; ++n) {
+    const double th = (n + 0.5) * dt, te_ = (n + 1.0) * dt;
+    const double u = M_PI * s->fmax * (th - t0);
+    const double a = s->moment * std::exp(-u * u);
+    amp[n] = static_cast<float>(a);
+    for (int f = 0; f < nf; ++f) {
+      const std::complex<double> eE = std::exp(I * wp[f] * te_) * dt, eH = std::exp(I * wp[f] * th) * dt;
+      const size_t o = (static_cast<size_t>(n) * nf + f) * 2;
+      fE[o] = eE.real();
+      fE[o + 1] = eE.imag();
+      fH[o] = eH.real();
+      fH[o + 1] = eH.imag();
+      fE32[o] = static_cast<float>(eE.real());
+      fE32[o + 1] = static_cast<float>(eE.imag());
+      fH32[o] = static_cast<float>(eH.real());
+      fH32[o + 1] = static_cast<float>(eH.imag());
+      jhat[f] += eH * a;  // J is sampled at t_{n+1/2}, the H label
+    }
+  }
+  // normalisation (Eq. 7): G^EE = sqrt(-i w / (2 w0)) E'/J', G^HE = H'/J'
+  double *norm = reinterpret_cast<double *>(at(L.norm));
+  for (int f = 0; f < nf; ++f) {
+    const std::complex<double> sE =
+        std::sqrt(2.0 * M_PI * s->freqs[f] / (2.0 * s->omega0)) * std::exp(-I * (M_PI / 4.0));
+    const std::complex<double> nE = (jhat[f] != 0.0) ? sE / jhat[f] : 0.0;
+    const std::complex<double> nH = (jhat[f] != 0.0) ? 1.0 / jhat[f] : 0.0;
+    norm[2 * f] = nE.real();
+    norm[2 * f + 1] = nE.imag();
+    norm[2 * nf + 2 * f] = nH.real();
+    norm[2 * nf + 2 * f + 1] = nH.imag();
+  }
+
+  // ---- device parameters ----
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  for (int a = 0; a < 3; ++a) {
+    p.np[a] = g->ax[a].npad;
+    p.n[a] = g->ax[a].n;
+    p.cm[a] = reinterpret_cast<const float *>(base + L.cm[a]);
+    p.cp[a] = reinterpret_cast<const float *>(base + L.cp[a]);
+    p.pml[a] = reinterpret_cast<const float *>(base + L.pml[a]);
+  }
+  p.nbe = nbe;
+  p.nb = nb;
+  for (int c = 0; c < 3; ++c) {
+    p.E[c] = reinterpret_cast<float *>(base + L.E[c]);
+    p.H[c] = reinterpret_cast<float *>(base + L.H[c]);
+    p.ie[c] = reinterpret_cast<const float *>(base + L.ie[c]);
+    p.jw[c] = reinterpret_cast<const float *>(base + L.jw[c]);
+  }
+  for (int c = 0; c < 6; ++c) {
+    p.psiE[c] = reinterpret_cast<float *>(base + L.psiE[c]);
+    p.psiH[c] = reinterpret_cast<float *>(base + L.psiH[c]);
+  }
+  p.dt_mu = static_cast<float>(dt / kMu0);
+  p.amp = reinterpret_cast<const float *>(base + L.amp);
+  p.nrec = s->nrec;
+  p.nf = nf;
+  p.rec_start = reinterpret_cast<const int *>(base + L.rec_start);
+  p.rec_w = reinterpret_cast<const double *>(base + L.rec_w);
+  p.rec_acc = rec_out;
+  p.fE = reinterpret_cast<const double *>(base + L.fE);
+  p.fH = reinterpret_cast<const double *>(base + L.fH);
+  p.fE32 = reinterpret_cast<const float *>(base + L.fE32);
+  p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
+  p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
+  p.status = reinterpret_cast<int *>(base + L.status);
+  // launch shape: TX x TY column tiles, z split so the grid covers the GPU
+  p.tiles_x = (p.np[0] + TX - 1) / TX;
+  p.tiles_y = (p.np[1] + TY - 1) / TY;
+  int sms = 148;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int tiles = p.tiles_x * p.tiles_y;
+  int zch = (4 * sms + tiles - 1) / tiles;
+  zch = std::max(1, std::min(zch, std::max(1, p.np[2] / 8)));
+  p.kchunk = (p.np[2] + zch - 1) / zch;
+  p.zchunks = (p.np[2] + p.kchunk - 1) / p.kchunk;
+  p.stencil_blocks = tiles * p.zchunks;
+  const int rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
+  const int blocks = p.stencil_blocks + rec_blocks;
+
+  // ---- enqueue ----
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, cs);
+  if (e == cudaSuccess && s->nrec > 0)
+    e = cudaMemsetAsync(rec_out, 0, static_cast<size_t>(s->nrec) * 6 * nf * 2 * sizeof(double), cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base + tab0, blob.data(), blob.size(), cudaMemcpyHostToDevice, cs);
+  if (e != cudaSuccess) return EMM_ECUDA;
+  k_prepare<<<4 * sms, 256, 0, cs>>>(sigma, reinterpret_cast<float *>(base + L.ie[0]),
+                                     reinterpret_cast<float *>(base + L.ie[1]),
+                                     reinterpret_cast<float *>(base + L.ie[2]), p.n[0], p.n[1], p.n[2], p.np[0],
+                                     p.np[1], p.np[2], nbe, 2.0 * s->omega0 * dt, s->sigma_min, p.status);
+  switch (rd) {
+    case 1: e = launch_steps<1>(p, nt, blocks, cs, te); break;
+    case 2: e = launch_steps<2>(p, nt, blocks, cs, te); break;
+    case 3: e = launch_steps<3>(p, nt, blocks, cs, te); break;
+    default: e = launch_steps<4>(p, nt, blocks, cs, te); break;
+  }
+  if (e != cudaSuccess) return EMM_ECUDA;
+  const double *dnorm = reinterpret_cast<const double *>(base + L.norm);
+  if (s->nrec > 0) {
+    const int tot = s->nrec * 6 * nf;
+    k_finalize_rec<<<(tot + 255) / 256, 256, 0, cs>>>(rec_out, dnorm, s->nrec, nf);
+  }
+  if (s->volume) {
+    const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+    k_finalize_vol<<<8 * sms, 256, 0, cs>>>(p.vacc, vol_out, dnorm, nint, nf);
+  }
+  return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+}  // namespace
+}  // namespace emm
+
+using namespace emm;
+
+extern "C" {
+
+int emm_workspace_size(const emm_grid *g, const emm_survey *s, size_t *bytes) {
+  const int st = check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (!bytes) return EMM_EINVAL;
+  *bytes = plan(g, s).total;
+  return EMM_OK;
+}
+
+int emm_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                double *rec_out, double *vol_out, emm_stream stream) {
+  return forward_impl(g, s, sigma, ws, ws_bytes, rec_out, vol_out, stream, nullptr);
+}
+
+int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                      double *rec_out, double *vol_out, emm_stream stream, emm_timing *timing) {
+  if (!timing || timing->every < 1) return EMM_EINVAL;
+  int st = check_survey(g, s);
+  if (st != EMM_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int nsamp = s->nt > 0 ? (s->nt + timing->every - 1) / timing->every : 0;
+  std::vector<cudaEvent_t> all(3 * static_cast<size_t>(nsamp) + 2, nullptr);
+  for (auto &e : all)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto &d : all)
+        if (d) cudaEventDestroy(d);
+      return EMM_ECUDA;
+    }
+  StepEvents te;
+  te.every = timing->every;
+  te.ev.assign(all.begin(), all.begin() + 3 * static_cast<size_t>(nsamp));
+  cudaEvent_t t0 = all[all.size() - 2], t1 = all[all.size() - 1];
+  cudaEventRecord(t0, cs);
+  st = forward_impl(g, s, sigma, ws, ws_bytes, rec_out, vol_out, stream, &te);
+  cudaEventRecord(t1, cs);
+  if (cudaStreamSynchronize(cs) != cudaSuccess && st == EMM_OK) st = EMM_ECUDA;
+  double se = 0, sh = 0;
+  float ms = 0.f;
+  for (int q = 0; q < nsamp && st == EMM_OK; ++q) {
+    cudaEventElapsedTime(&ms, te.ev[3 * q], te.ev[3 * q + 1]);
+    se += ms;
+    cudaEventElapsedTime(&ms, te.ev[3 * q + 1], te.ev[3 * q + 2]);
+    sh += ms;
+  }
+  timing->samples = nsamp;
+  timing->e_ms = nsamp ? se / nsamp : 0.0;
+  timing->h_ms = nsamp ? sh / nsamp : 0.0;
+  ms = 0.f;
+  if (st == EMM_OK) cudaEventElapsedTime(&ms, t0, t1);
+  timing->total_ms = ms;
+  for (auto &e : all) cudaEventDestroy(e);
+  return st;
+}
+
+int emm_status(const void *ws, int *status, emm_stream stream) {
+  if (!ws || !status) return EMM_EINVAL;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, ws, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess) return EMM_ECUDA;
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return EMM_ECUDA;
+  *status = v;
+  return EMM_OK;
+}
+
+}  // extern "C"
