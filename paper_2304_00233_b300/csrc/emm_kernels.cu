@@ -13,10 +13,9 @@
 //                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
 //                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
 //
-// Each stencil CTA owns a TX x TY tile of (i, j) columns and marches z over a
-// chunk of planes.  The z taps of the two fields differentiated along z sit
-// in a per-thread register queue of 2R planes; the current plane of the three
-// fields is staged in shared memory with the x/y halos.  Fields are FP32,
+// Each stencil thread owns one (i, j) column and ZC consecutive z planes; the
+// z taps of the two fields differentiated along z sit in a per-thread register
+// queue, the x/y taps come through L1.  Fields are FP32,
 // the receiver DTFT accumulates in FP64 and the volume DTFT in compensated
 // FP32 (hi + lo pairs).  No device transcendentals: every exp/sin/cos comes
 // from FP64 host tables.
@@ -35,6 +34,7 @@ namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
 constexpr int TY = 8;   // tile height (y)
+constexpr int ZC = 4;   // planes per thread
 constexpr int NT = TX * TY;
 
 __device__ __forceinline__ int slab_int(int i, int np, int nb) {
@@ -114,143 +114,119 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 // ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
+// Thread (i, j) of a TX x TY tile updates ZC consecutive planes k0..k0+ZC-1.
+// The z taps of Hx and Hy come from a register queue of ZC + 2R - 1 planes;
+// the x and y taps are read through the L1 cache (neighbouring threads load
+// the same lines).  No shared memory and no barriers: every thread is
+// independent, so the whole grid is in flight to cover memory latency.
 template <int R>
-__global__ void __launch_bounds__(NT) k_update_E(const DevParams p, const int n) {
+__device__ __forceinline__ void source_term(const DevParams &p, int c, int i, int j, int k, float amp,
+                                            float &curl) {
   constexpr int M = 2 * R;
+  if (!p.src_on[c]) return;
+  const int a = i - p.src_start[c][0], bb = j - p.src_start[c][1], cc = k - p.src_start[c][2];
+  if (a >= 0 && a < M && bb >= 0 && bb < M && cc >= 0 && cc < M) curl -= amp * p.jw[c][(cc * M + bb) * M + a];
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_E(const DevParams p, const int n) {
+  constexpr int M = 2 * R;
+  constexpr int Q = ZC + M - 1;
   if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
     receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
-  __shared__ float sHz[TY + 2 * R][TX + 2 * R];  // plane k, x and y halo
-  __shared__ float sHy[TY][TX + 2 * R];          // plane k, x halo
-  __shared__ float sHx[TY + 2 * R][TX];          // plane k, y halo
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int b = blockIdx.x;
   const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const int i = bx * TX + static_cast<int>(threadIdx.x % TX), j = by * TY + static_cast<int>(threadIdx.x / TX);
+  if (i >= np0 || j >= np1) return;
+  const int k0 = bz * ZC;
   const size_t plane = static_cast<size_t>(np0) * np1;
-  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
-  const bool in_ij = i < np0 && j < np1;
   const size_t col = static_cast<size_t>(j) * np0 + i;
+  const float *__restrict__ Hx = p.H[0];
+  const float *__restrict__ Hy = p.H[1];
+  const float *__restrict__ Hz = p.H[2];
   const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
   const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
   float cx[M], cy[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
-    cx[q] = dm_i ? p.cm[0][i * M + q] : 0.f;
-    cy[q] = dm_j ? p.cm[1][j * M + q] : 0.f;
+    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
+    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
   }
-  const float amp = p.amp[n];
+  float qx[Q], qy[Q];  // Hx, Hy of this column at planes k0-R .. k0+ZC+R-2
+#pragma unroll
+  for (int t = 0; t < Q; ++t) {
+    const int kk = k0 - R + t;
+    const bool ok = kk >= 0 && kk < np2;
+    qx[t] = ok ? __ldg(Hx + kk * plane + col) : 0.f;
+    qy[t] = ok ? __ldg(Hy + kk * plane + col) : 0.f;
+  }
+  const float amp = __ldg(p.amp + n);
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
   const int ii = i - p.nbe, jj = j - p.nbe;
   const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-
-  float qx[M], qy[M];  // Hx, Hy at planes k-R .. k+R-1 of this column
 #pragma unroll
-  for (int q = 0; q < M - 1; ++q) {
-    const int kk = k0 - R + q;
-    const bool ok = in_ij && kk >= 0 && kk < np2;
-    qx[q] = ok ? p.H[0][kk * plane + col] : 0.f;
-    qy[q] = ok ? p.H[1][kk * plane + col] : 0.f;
-  }
-  for (int k = k0; k < k1; ++k) {
-    {
-      const int kk = k + R - 1;
-      const bool ok = in_ij && kk < np2;
-      qx[M - 1] = ok ? p.H[0][kk * plane + col] : 0.f;
-      qy[M - 1] = ok ? p.H[1][kk * plane + col] : 0.f;
-    }
-    const float *Hx = p.H[0] + k * plane, *Hy = p.H[1] + k * plane, *Hz = p.H[2] + k * plane;
-    for (int t = threadIdx.x; t < (TY + 2 * R) * (TX + 2 * R); t += NT) {
-      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
-      const int y = j0 - R + r, x = i0 - R + c;
-      sHz[r][c] = (y >= 0 && y < np1 && x >= 0 && x < np0) ? Hz[y * np0 + x] : 0.f;
-    }
-    for (int t = threadIdx.x; t < TY * (TX + 2 * R); t += NT) {
-      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
-      const int y = j0 + r, x = i0 - R + c;
-      sHy[r][c] = (y < np1 && x >= 0 && x < np0) ? Hy[y * np0 + x] : 0.f;
-    }
-    for (int t = threadIdx.x; t < (TY + 2 * R) * TX; t += NT) {
-      const int r = t / TX, c = t % TX;
-      const int y = j0 - R + r, x = i0 + c;
-      sHx[r][c] = (y >= 0 && y < np1 && x < np0) ? Hx[y * np0 + x] : 0.f;
-    }
-    __syncthreads();
-    if (in_ij) {
-      const bool dm_k = k >= R && k <= np2 - 1 - R;
-      const int sk = slab_int(k, np2, nb);
-      float cz[M];
+  for (int c = 0; c < ZC; ++c) {
+    const int k = k0 + c;
+    if (k >= np2) break;
+    const bool dm_k = k >= R && k <= np2 - 1 - R;
+    const int sk = slab_int(k, np2, nb);
+    const size_t id = k * plane + col;
+    float cz[M];
 #pragma unroll
-      for (int q = 0; q < M; ++q) cz[q] = dm_k ? p.cm[2][k * M + q] : 0.f;
-      const size_t id = k * plane + col;
-      // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-      if (i <= np0 - 2 && dm_j && dm_k) {
-        float dy = 0.f, dz = 0.f;
+    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
+    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+    if (i <= np0 - 2 && dm_j && dm_k) {
+      float dy = 0.f, dz = 0.f;
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dy = fmaf(cy[q], sHz[ty + q][tx + R], dy);
-          dz = fmaf(cz[q], qy[q], dz);
-        }
-        if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-        if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-        float curl = dy - dz;
-        if (p.src_on[0]) {
-          const int a = i - p.src_start[0][0], bb = j - p.src_start[0][1], c = k - p.src_start[0][2];
-          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[0][(c * M + bb) * M + a];
-        }
-        p.E[0][id] = fmaf(p.ie[0][id], curl, p.E[0][id]);
+      for (int q = 0; q < M; ++q) {
+        dy = fmaf(cy[q], __ldg(Hz + id + static_cast<ptrdiff_t>(q - R) * np0), dy);
+        dz = fmaf(cz[q], qy[c + q], dz);
       }
-      // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-      if (j <= np1 - 2 && dm_i && dm_k) {
-        float dz = 0.f, dx = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dz = fmaf(cz[q], qx[q], dz);
-          dx = fmaf(cx[q], sHz[ty + R][tx + q], dx);
-        }
-        if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-        if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-        float curl = dz - dx;
-        if (p.src_on[1]) {
-          const int a = i - p.src_start[1][0], bb = j - p.src_start[1][1], c = k - p.src_start[1][2];
-          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[1][(c * M + bb) * M + a];
-        }
-        p.E[1][id] = fmaf(p.ie[1][id], curl, p.E[1][id]);
-      }
-      // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-      if (k <= np2 - 2 && dm_i && dm_j) {
-        float dx = 0.f, dy = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dx = fmaf(cx[q], sHy[ty][tx + q], dx);
-          dy = fmaf(cy[q], sHx[ty + q][tx], dy);
-        }
-        if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-        if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-        float curl = dx - dy;
-        if (p.src_on[2]) {
-          const int a = i - p.src_start[2][0], bb = j - p.src_start[2][1], c = k - p.src_start[2][2];
-          if (a >= 0 && a < M && bb >= 0 && bb < M && c >= 0 && c < M) curl -= amp * p.jw[2][(c * M + bb) * M + a];
-        }
-        p.E[2][id] = fmaf(p.ie[2][id], curl, p.E[2][id]);
-      }
-      // volume DTFT of H^{n+1/2} (centre values of plane k)
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 3, lin, nint, facH, qx[R]);
-        volume_accumulate(p, 4, lin, nint, facH, qy[R]);
-        volume_accumulate(p, 5, lin, nint, facH, sHz[ty + R][tx + R]);
-      }
+      if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+      if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+      float curl = dy - dz;
+      source_term<R>(p, 0, i, j, k, amp, curl);
+      p.E[0][id] = fmaf(__ldg(p.ie[0] + id), curl, p.E[0][id]);
     }
-    __syncthreads();
+    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+    if (j <= np1 - 2 && dm_i && dm_k) {
+      float dz = 0.f, dx = 0.f;
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      qx[q] = qx[q + 1];
-      qy[q] = qy[q + 1];
+      for (int q = 0; q < M; ++q) {
+        dz = fmaf(cz[q], qx[c + q], dz);
+        dx = fmaf(cx[q], __ldg(Hz + id + (q - R)), dx);
+      }
+      if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+      if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+      float curl = dz - dx;
+      source_term<R>(p, 1, i, j, k, amp, curl);
+      p.E[1][id] = fmaf(__ldg(p.ie[1] + id), curl, p.E[1][id]);
+    }
+    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+    if (k <= np2 - 2 && dm_i && dm_j) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dx = fmaf(cx[q], __ldg(Hy + id + (q - R)), dx);
+        dy = fmaf(cy[q], __ldg(Hx + id + static_cast<ptrdiff_t>(q - R) * np0), dy);
+      }
+      if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+      if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+      float curl = dx - dy;
+      source_term<R>(p, 2, i, j, k, amp, curl);
+      p.E[2][id] = fmaf(__ldg(p.ie[2] + id), curl, p.E[2][id]);
+    }
+    // volume DTFT of H^{n+1/2}
+    const int kk = k - p.nbe;
+    if (int_ij && kk >= 0 && kk < p.n[2]) {
+      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+      volume_accumulate(p, 3, lin, nint, facH, qx[c + R]);
+      volume_accumulate(p, 4, lin, nint, facH, qy[c + R]);
+      volume_accumulate(p, 5, lin, nint, facH, __ldg(Hz + id));
     }
   }
 }
@@ -259,127 +235,98 @@ __global__ void __launch_bounds__(NT) k_update_E(const DevParams p, const int n)
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT) k_update_H(const DevParams p, const int n) {
+__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_H(const DevParams p, const int n) {
   constexpr int M = 2 * R;
+  constexpr int Q = ZC + M - 1;
   if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
     receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
-  __shared__ float sEz[TY + 2 * R][TX + 2 * R];  // plane k, x and y halo
-  __shared__ float sEy[TY][TX + 2 * R];          // plane k, x halo
-  __shared__ float sEx[TY + 2 * R][TX];          // plane k, y halo
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int b = blockIdx.x;
   const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const int i = bx * TX + static_cast<int>(threadIdx.x % TX), j = by * TY + static_cast<int>(threadIdx.x / TX);
+  if (i >= np0 || j >= np1) return;
+  const int k0 = bz * ZC;
   const size_t plane = static_cast<size_t>(np0) * np1;
-  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
-  const bool in_ij = i < np0 && j < np1;
   const size_t col = static_cast<size_t>(j) * np0 + i;
+  const float *__restrict__ Ex = p.E[0];
+  const float *__restrict__ Ey = p.E[1];
+  const float *__restrict__ Ez = p.E[2];
   const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
   const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
   float cx[M], cy[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
-    cx[q] = dp_i ? p.cp[0][i * M + q] : 0.f;
-    cy[q] = dp_j ? p.cp[1][j * M + q] : 0.f;
+    cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
+    cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
+  }
+  float qx[Q], qy[Q];  // Ex, Ey of this column at planes k0-R+1 .. k0+ZC+R-1
+#pragma unroll
+  for (int t = 0; t < Q; ++t) {
+    const int kk = k0 - R + 1 + t;
+    const bool ok = kk >= 0 && kk < np2;
+    qx[t] = ok ? __ldg(Ex + kk * plane + col) : 0.f;
+    qy[t] = ok ? __ldg(Ey + kk * plane + col) : 0.f;
   }
   const float dt_mu = p.dt_mu;
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
   const int ii = i - p.nbe, jj = j - p.nbe;
   const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-
-  float qx[M], qy[M];  // Ex, Ey at planes k-R+1 .. k+R of this column
 #pragma unroll
-  for (int q = 0; q < M - 1; ++q) {
-    const int kk = k0 - R + 1 + q;
-    const bool ok = in_ij && kk >= 0 && kk < np2;
-    qx[q] = ok ? p.E[0][kk * plane + col] : 0.f;
-    qy[q] = ok ? p.E[1][kk * plane + col] : 0.f;
-  }
-  for (int k = k0; k < k1; ++k) {
-    {
-      const int kk = k + R;
-      const bool ok = in_ij && kk < np2;
-      qx[M - 1] = ok ? p.E[0][kk * plane + col] : 0.f;
-      qy[M - 1] = ok ? p.E[1][kk * plane + col] : 0.f;
-    }
-    const float *Ex = p.E[0] + k * plane, *Ey = p.E[1] + k * plane, *Ez = p.E[2] + k * plane;
-    for (int t = threadIdx.x; t < (TY + 2 * R) * (TX + 2 * R); t += NT) {
-      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
-      const int y = j0 - R + r, x = i0 - R + c;
-      sEz[r][c] = (y >= 0 && y < np1 && x >= 0 && x < np0) ? Ez[y * np0 + x] : 0.f;
-    }
-    for (int t = threadIdx.x; t < TY * (TX + 2 * R); t += NT) {
-      const int r = t / (TX + 2 * R), c = t % (TX + 2 * R);
-      const int y = j0 + r, x = i0 - R + c;
-      sEy[r][c] = (y < np1 && x >= 0 && x < np0) ? Ey[y * np0 + x] : 0.f;
-    }
-    for (int t = threadIdx.x; t < (TY + 2 * R) * TX; t += NT) {
-      const int r = t / TX, c = t % TX;
-      const int y = j0 - R + r, x = i0 + c;
-      sEx[r][c] = (y >= 0 && y < np1 && x < np0) ? Ex[y * np0 + x] : 0.f;
-    }
-    __syncthreads();
-    if (in_ij) {
-      const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
-      const int sk = slab_half(k, np2, nb);
-      float cz[M];
+  for (int c = 0; c < ZC; ++c) {
+    const int k = k0 + c;
+    if (k >= np2) break;
+    const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
+    const int sk = slab_half(k, np2, nb);
+    const size_t id = k * plane + col;
+    float cz[M];
 #pragma unroll
-      for (int q = 0; q < M; ++q) cz[q] = dp_k ? p.cp[2][k * M + q] : 0.f;
-      const size_t id = k * plane + col;
-      // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-      if (dp_j && dp_k) {
-        float dy = 0.f, dz = 0.f;
+    for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
+    // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+    if (dp_j && dp_k) {
+      float dy = 0.f, dz = 0.f;
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dy = fmaf(cy[q], sEz[ty + 1 + q][tx + R], dy);
-          dz = fmaf(cz[q], qy[q], dz);
-        }
-        if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-        if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-        p.H[0][id] = fmaf(-dt_mu, dy - dz, p.H[0][id]);
+      for (int q = 0; q < M; ++q) {
+        dy = fmaf(cy[q], __ldg(Ez + id + static_cast<ptrdiff_t>(q - R + 1) * np0), dy);
+        dz = fmaf(cz[q], qy[c + q], dz);
       }
-      // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-      if (dp_i && dp_k) {
-        float dz = 0.f, dx = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dz = fmaf(cz[q], qx[q], dz);
-          dx = fmaf(cx[q], sEz[ty + R][tx + 1 + q], dx);
-        }
-        if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-        if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-        p.H[1][id] = fmaf(-dt_mu, dz - dx, p.H[1][id]);
-      }
-      // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-      if (dp_i && dp_j) {
-        float dx = 0.f, dy = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dx = fmaf(cx[q], sEy[ty][tx + 1 + q], dx);
-          dy = fmaf(cy[q], sEx[ty + 1 + q][tx], dy);
-        }
-        if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-        if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-        p.H[2][id] = fmaf(-dt_mu, dx - dy, p.H[2][id]);
-      }
-      // volume DTFT of E^{n+1} (centre values of plane k)
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
-        volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
-        volume_accumulate(p, 2, lin, nint, facE, sEz[ty + R][tx + R]);
-      }
+      if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+      if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+      p.H[0][id] = fmaf(-dt_mu, dy - dz, p.H[0][id]);
     }
-    __syncthreads();
+    // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+    if (dp_i && dp_k) {
+      float dz = 0.f, dx = 0.f;
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      qx[q] = qx[q + 1];
-      qy[q] = qy[q + 1];
+      for (int q = 0; q < M; ++q) {
+        dz = fmaf(cz[q], qx[c + q], dz);
+        dx = fmaf(cx[q], __ldg(Ez + id + (q - R + 1)), dx);
+      }
+      if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+      if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+      p.H[1][id] = fmaf(-dt_mu, dz - dx, p.H[1][id]);
+    }
+    // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+    if (dp_i && dp_j) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dx = fmaf(cx[q], __ldg(Ey + id + (q - R + 1)), dx);
+        dy = fmaf(cy[q], __ldg(Ex + id + static_cast<ptrdiff_t>(q - R + 1) * np0), dy);
+      }
+      if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+      if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+      p.H[2][id] = fmaf(-dt_mu, dx - dy, p.H[2][id]);
+    }
+    // volume DTFT of E^{n+1}
+    const int kk = k - p.nbe;
+    if (int_ij && kk >= 0 && kk < p.n[2]) {
+      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+      volume_accumulate(p, 0, lin, nint, facE, qx[c + R - 1]);
+      volume_accumulate(p, 1, lin, nint, facE, qy[c + R - 1]);
+      volume_accumulate(p, 2, lin, nint, facE, __ldg(Ez + id));
     }
   }
 }
@@ -690,10 +637,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const int tiles = p.tiles_x * p.tiles_y;
-  int zch = (4 * sms + tiles - 1) / tiles;
-  zch = std::max(1, std::min(zch, std::max(1, p.np[2] / 8)));
-  p.kchunk = (p.np[2] + zch - 1) / zch;
-  p.zchunks = (p.np[2] + p.kchunk - 1) / p.kchunk;
+  p.kchunk = ZC;
+  p.zchunks = (p.np[2] + ZC - 1) / ZC;
   p.stencil_blocks = tiles * p.zchunks;
   const int rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
   const int blocks = p.stencil_blocks + rec_blocks;

@@ -54,9 +54,15 @@ def test_whole_space_full_steps_against_golden():
     G, _, grid, survey = _run_gpu(wl, int(g["nt"]))
     dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
     assert dt == pytest.approx(float(g["dt"]), rel=1e-13)
-    eE, eH = compare_G(G, g["G"])
-    assert eE < REL_L2_TOL and eH < REL_L2_TOL, (eE, eH)
+    # inline receivers: E is compared; H vanishes on the dipole axis by
+    # symmetry, so both paths must give a negligible H (relative to the
+    # broadside magnitude 1/(4 pi r^2) of G^HE at that offset)
+    eE, _ = compare_G(G, g["G"])
+    assert eE < REL_L2_TOL, eE
     assert max_rel_masked(G[:, 0], g["G"][:, 0], 1e-3) < 1e-3
+    r = wl.rec[:, 0]
+    assert np.all(np.abs(G[:, 3:, 0]).max(axis=1) < 1e-5 / (4 * np.pi * r ** 2))
+    assert np.all(np.abs(g["G"][:, 3:, 0]).max(axis=1) < 1e-9 / (4 * np.pi * r ** 2))
 
 
 @pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "marine_1d_128x128x96.npz")),
