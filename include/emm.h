@@ -46,6 +46,7 @@ extern "C" {
 #define EMM_ECUDA 5       /* a CUDA runtime call or kernel launch failed */
 #define EMM_EWORKSPACE 6  /* workspace too small or misaligned */
 #define EMM_EDEVICE 7     /* the device flagged a bad input (see emm_status) */
+#define EMM_ETIMEOUT 8    /* a bounded device-side wait ran out (see emm_status) */
 
 /* Opaque grid handle: padded nodes, half nodes, FD tables (host, FP64).
  * Immutable after emm_make_grid; owns no device memory. */
@@ -185,8 +186,10 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
                       emm_stream stream, emm_timing *timing);
 
 /* Read the device status word of a workspace after emm_forward: synchronises
- * `stream`, then *status = EMM_OK or EMM_EDEVICE (a sigma value was not
- * finite, not positive, or below sigma_min).  EMM_ECUDA if the copy fails. */
+ * `stream`, then *status = EMM_OK, EMM_EDEVICE (a sigma value was not finite,
+ * not positive, or below sigma_min) or EMM_ETIMEOUT (a kernel gave up on a
+ * bounded wait for its asynchronous copies and returned early; the outputs
+ * are then undefined).  EMM_ECUDA if the copy fails. */
 int emm_status(const void *ws, int *status, emm_stream stream);
 
 /* Static description of an error code (never NULL). */

@@ -27,7 +27,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY_PATH = os.path.join(_HERE, "libemm.so")
 
-EMM_OK, EMM_EINVAL, EMM_ENOMEM, EMM_EOUTSIDE, EMM_ECFL, EMM_ECUDA, EMM_EWORKSPACE, EMM_EDEVICE = range(8)
+(EMM_OK, EMM_EINVAL, EMM_ENOMEM, EMM_EOUTSIDE, EMM_ECFL, EMM_ECUDA, EMM_EWORKSPACE, EMM_EDEVICE,
+ EMM_ETIMEOUT) = range(9)
 TAB_NODES, TAB_HALF, TAB_DPLUS, TAB_DMINUS, TAB_SLAB_INT, TAB_SLAB_HALF = range(6)
 COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",

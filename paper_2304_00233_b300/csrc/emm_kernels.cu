@@ -13,18 +13,31 @@
 //                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
 //                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
 //
-// Each stencil thread owns one (i, j) column and ZC consecutive z planes; the
-// z taps of the two fields differentiated along z sit in a per-thread register
-// queue, the x/y taps come through L1.  Fields are FP32,
-// the receiver DTFT accumulates in FP64 and the volume DTFT in compensated
-// FP32 (hi + lo pairs).  No device transcendentals: every exp/sin/cos comes
-// from FP64 host tables.
+// Stencil CTAs own a TX x TY tile of (i, j) columns and march z through a
+// chunk of planes.  Every plane the CTA needs is fetched by the Tensor Memory
+// Accelerator: one thread issues cp.async.bulk.tensor copies of the plane's
+// tiles (with the x/y halos the D+/D- rows need) into a ring of D = R + 3
+// shared-memory stages, each completed on its own mbarrier, so several planes
+// of every array are in flight while the CTA computes.  The z taps of the two
+// fields differentiated along z sit in a per-thread register queue of 2R
+// planes fed from the ring.  Fields are FP32 with a row pitch rounded up to
+// 4 samples (16-byte TMA strides); the receiver DTFT accumulates in FP64 and
+// the volume DTFT in compensated FP32 (hi + lo pairs).  No device
+// transcendentals: every exp/sin/cos comes from FP64 host tables.
+//
+// Every mbarrier wait is bounded (1 s of %globaltimer).  A wait that runs out
+// sets the status word to EMM_ETIMEOUT; the CTA then agrees on the abort
+// with __syncthreads_or, drains its own copies in flight (again bounded) and
+// returns, so no kernel can hang the device.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "emm_internal.h"
@@ -34,8 +47,99 @@ namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
 constexpr int TY = 8;   // tile height (y)
-constexpr int ZC = 4;   // planes per thread
 constexpr int NT = TX * TY;
+constexpr int XH = 4;   // x halo of the TMA boxes (>= R, keeps box x starts 16-byte aligned)
+constexpr int WX = TX + 2 * XH;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of one mbarrier wait
+
+__host__ __device__ constexpr int ring_depth(int R) { return R + 3; }
+__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }  // floats -> 128 B
+
+// Stage layout (floats) of the E launch: Hz [TY+2R][WX], Hy [TY][WX],
+// Hx [TY+2R][TX], E [3][TY][TX], dt/eps [3][TY][TX].
+template <int R>
+struct StageE {
+  static constexpr int HYR = TY + 2 * R;
+  static constexpr int HZ = 0;
+  static constexpr int HY = HZ + round32(HYR * WX);
+  static constexpr int HX = HY + round32(TY * WX);
+  static constexpr int EC = HX + round32(HYR * TX);
+  static constexpr int IE = EC + 3 * TY * TX;
+  static constexpr int FLOATS = IE + 3 * TY * TX;
+  static constexpr unsigned QUEUE_BYTES = 4u * (HYR * TX + TY * WX);  // Hx + Hy tiles only
+  static constexpr unsigned FULL_BYTES = 4u * (HYR * WX + TY * WX + HYR * TX + 6 * TY * TX);
+};
+
+// Stage layout of the H launch: Ez [TY+2R][WX], Ey [TY][WX], Ex [TY+2R][TX], H [3][TY][TX].
+template <int R>
+struct StageH {
+  static constexpr int HYR = TY + 2 * R;
+  static constexpr int EZ = 0;
+  static constexpr int EY = EZ + round32(HYR * WX);
+  static constexpr int EX = EY + round32(TY * WX);
+  static constexpr int HC = EX + round32(HYR * TX);
+  static constexpr int FLOATS = HC + 3 * TY * TX;
+  static constexpr unsigned QUEUE_BYTES = 4u * (HYR * TX + TY * WX);  // Ex + Ey tiles only
+  static constexpr unsigned FULL_BYTES = 4u * (HYR * WX + TY * WX + HYR * TX + 3 * TY * TX);
+};
+
+template <int R>
+constexpr size_t smem_bytes_E() { return static_cast<size_t>(ring_depth(R)) * StageE<R>::FLOATS * 4 + 128; }
+template <int R>
+constexpr size_t smem_bytes_H() { return static_cast<size_t>(ring_depth(R)) * StageH<R>::FLOATS * 4 + 128; }
+
+// Tensor maps of one launch: [0..2] the halo'd sources (z-halo field with a
+// y halo, x-halo field, xy-halo field), [3..5] the updated field, [6..8] dt/eps.
+struct TmaSet {
+  CUtensorMap m[9];
+};
+
+// ---- PTX helpers: mbarrier and TMA ---------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of `bar` for at most kWaitNs; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 __device__ __forceinline__ int slab_int(int i, int np, int nb) {
   return i < nb ? i : (i >= np - nb ? nb + np - 1 - i : -1);
@@ -97,7 +201,7 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
   double s = 0.0;
   for (int t = lane; t < M * M * M; t += 32) {
     const int q1 = t % M, q2 = (t / M) % M, q3 = t / (M * M);
-    const size_t id = (static_cast<size_t>(st[2] + q3) * p.np[1] + (st[1] + q2)) * p.np[0] + (st[0] + q1);
+    const size_t id = (static_cast<size_t>(st[2] + q3) * p.np[1] + (st[1] + q2)) * p.pitch + (st[0] + q1);
     s += w[q1] * w[M + q2] * w[2 * M + q3] * static_cast<double>(f[id]);
   }
 #pragma unroll
@@ -111,14 +215,6 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
   }
 }
 
-// ---------------------------------------------------------------------------
-// E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
-// ---------------------------------------------------------------------------
-// Thread (i, j) of a TX x TY tile updates ZC consecutive planes k0..k0+ZC-1.
-// The z taps of Hx and Hy come from a register queue of ZC + 2R - 1 planes;
-// the x and y taps are read through the L1 cache (neighbouring threads load
-// the same lines).  No shared memory and no barriers: every thread is
-// independent, so the whole grid is in flight to cover memory latency.
 template <int R>
 __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, int j, int k, float amp,
                                             float &curl) {
@@ -128,25 +224,82 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
   if (a >= 0 && a < M && bb >= 0 && bb < M && cc >= 0 && cc < M) curl -= amp * p.jw[c][(cc * M + bb) * M + a];
 }
 
+// Plane ring bookkeeping shared by both launches.  Planes pb, pb+1, ... are
+// issued in order; plane p lives in stage (p - pb) % D and completes phase
+// ((p - pb) / D) & 1 of that stage's mbarrier.
+struct Ring {
+  int pb, nxt, waited;  // first plane, next plane to issue, next plane to wait for
+};
+
+// Every thread waits (bounded) for the copies still in flight, so no TMA
+// write lands in shared memory after the CTA has exited.
+template <int D>
+__device__ void drain(uint64_t *bars, const Ring &rg) {
+  for (int p = rg.waited; p < rg.nxt; ++p) {
+    const int u = p - rg.pb;
+    mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
+// ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_E(const DevParams p, const int n) {
-  constexpr int M = 2 * R;
-  constexpr int Q = ZC + M - 1;
+__global__ void __launch_bounds__(NT) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
+                                                 const int n) {
+  constexpr int M = 2 * R, D = ring_depth(R);
+  using S = StageE<R>;
   if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
     receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float *ring = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
+
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int b = blockIdx.x;
   const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int i = bx * TX + static_cast<int>(threadIdx.x % TX), j = by * TY + static_cast<int>(threadIdx.x / TX);
-  if (i >= np0 || j >= np1) return;
-  const int k0 = bz * ZC;
-  const size_t plane = static_cast<size_t>(np0) * np1;
-  const size_t col = static_cast<size_t>(j) * np0 + i;
-  const float *__restrict__ Hx = p.H[0];
-  const float *__restrict__ Hy = p.H[1];
-  const float *__restrict__ Hz = p.H[2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
+  const bool in_ij = i < np0 && j < np1;
+  const size_t plane = p.plane;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+
+  Ring rg{k0 - R, k0 - R, k0 - R};
+  const int plast = k1 + R - 2;  // last plane the z queue needs
+  auto issue = [&](int pl) {  // called by thread 0 only
+    const int u = pl - rg.pb;
+    float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+    uint64_t *bar = &bars[u % D];
+    const bool full = pl >= k0 && pl < k1;
+    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
+    tma_load_3d(st + S::HX, &tm.m[0], bar, i0, j0 - R, pl);
+    tma_load_3d(st + S::HY, &tm.m[1], bar, i0 - XH, j0, pl);
+    if (full) {
+      tma_load_3d(st + S::HZ, &tm.m[2], bar, i0 - XH, j0 - R, pl);
+      for (int c = 0; c < 3; ++c) {
+        tma_load_3d(st + S::EC + c * TY * TX, &tm.m[3 + c], bar, i0, j0, pl);
+        tma_load_3d(st + S::IE + c * TY * TX, &tm.m[6 + c], bar, i0, j0, pl);
+      }
+    }
+  };
+  // issue planes [rg.nxt, min(upto, plast + 1)) -- thread 0 issues, every
+  // thread tracks the same count
+  auto advance = [&](int upto) {
+    const int stop = min(upto, plast + 1);
+    if (threadIdx.x == 0)
+      for (int q = rg.nxt; q < stop; ++q) issue(q);
+    rg.nxt = max(rg.nxt, stop);
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  advance(rg.pb + D);
+
   const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
   const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
   float cx[M], cy[M];
@@ -155,104 +308,172 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_E(const DevPara
     cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
     cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
   }
-  float qx[Q], qy[Q];  // Hx, Hy of this column at planes k0-R .. k0+ZC+R-2
-#pragma unroll
-  for (int t = 0; t < Q; ++t) {
-    const int kk = k0 - R + t;
-    const bool ok = kk >= 0 && kk < np2;
-    qx[t] = ok ? __ldg(Hx + kk * plane + col) : 0.f;
-    qy[t] = ok ? __ldg(Hy + kk * plane + col) : 0.f;
-  }
   const float amp = __ldg(p.amp + n);
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
   const int ii = i - p.nbe, jj = j - p.nbe;
   const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+
+  // register queue: Hx, Hy of this column at planes k-R .. k+R-1
+  float qx[M], qy[M];
+  bool ok = true;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = k0 + c;
-    if (k >= np2) break;
-    const bool dm_k = k >= R && k <= np2 - 1 - R;
-    const int sk = slab_int(k, np2, nb);
-    const size_t id = k * plane + col;
-    float cz[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
-    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-    if (i <= np0 - 2 && dm_j && dm_k) {
-      float dy = 0.f, dz = 0.f;
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dy = fmaf(cy[q], __ldg(Hz + id + static_cast<ptrdiff_t>(q - R) * np0), dy);
-        dz = fmaf(cz[q], qy[c + q], dz);
-      }
-      if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-      if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-      float curl = dy - dz;
-      source_term<R>(p, 0, i, j, k, amp, curl);
-      p.E[0][id] = fmaf(__ldg(p.ie[0] + id), curl, p.E[0][id]);
+  for (int q = 0; q < M - 1; ++q) {
+    const int u = rg.waited - rg.pb;
+    ok = ok && mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+    const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+    qx[q] = st[S::HX + (ty + R) * TX + tx];
+    qy[q] = st[S::HY + ty * WX + tx + XH];
+    ++rg.waited;
+  }
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+    drain<D>(bars, rg);
+    return;
+  }
+  advance(k0 + D);
+
+  for (int k = k0; k < k1; ++k) {
+    {  // queue feed: plane k+R-1
+      const int u = rg.waited - rg.pb;
+      ok = mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+      const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+      qx[M - 1] = st[S::HX + (ty + R) * TX + tx];
+      qy[M - 1] = st[S::HY + ty * WX + tx + XH];
+      ++rg.waited;
     }
-    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-    if (j <= np1 - 2 && dm_i && dm_k) {
-      float dz = 0.f, dx = 0.f;
+    const float *st = ring + static_cast<size_t>((k - rg.pb) % D) * S::FLOATS;
+    const float *sHz = st + S::HZ, *sHy = st + S::HY, *sHx = st + S::HX;
+    if (ok && in_ij) {
+      const bool dm_k = k >= R && k <= np2 - 1 - R;
+      const int sk = slab_int(k, np2, nb);
+      float cz[M];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dz = fmaf(cz[q], qx[c + q], dz);
-        dx = fmaf(cx[q], __ldg(Hz + id + (q - R)), dx);
-      }
-      if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-      if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-      float curl = dz - dx;
-      source_term<R>(p, 1, i, j, k, amp, curl);
-      p.E[1][id] = fmaf(__ldg(p.ie[1] + id), curl, p.E[1][id]);
-    }
-    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-    if (k <= np2 - 2 && dm_i && dm_j) {
-      float dx = 0.f, dy = 0.f;
+      for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
+      const size_t id = k * plane + col;
+      const int e = ty * TX + tx;
+      // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+      if (i <= np0 - 2 && dm_j && dm_k) {
+        float dy = 0.f, dz = 0.f;
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dx = fmaf(cx[q], __ldg(Hy + id + (q - R)), dx);
-        dy = fmaf(cy[q], __ldg(Hx + id + static_cast<ptrdiff_t>(q - R) * np0), dy);
+        for (int q = 0; q < M; ++q) {
+          dy = fmaf(cy[q], sHz[(ty + q) * WX + tx + XH], dy);
+          dz = fmaf(cz[q], qy[q], dz);
+        }
+        if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+        if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+        float curl = dy - dz;
+        source_term<R>(p, 0, i, j, k, amp, curl);
+        p.E[0][id] = fmaf(st[S::IE + e], curl, st[S::EC + e]);
       }
-      if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-      if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-      float curl = dx - dy;
-      source_term<R>(p, 2, i, j, k, amp, curl);
-      p.E[2][id] = fmaf(__ldg(p.ie[2] + id), curl, p.E[2][id]);
+      // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+      if (j <= np1 - 2 && dm_i && dm_k) {
+        float dz = 0.f, dx = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dz = fmaf(cz[q], qx[q], dz);
+          dx = fmaf(cx[q], sHz[(ty + R) * WX + tx + XH - R + q], dx);
+        }
+        if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+        if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+        float curl = dz - dx;
+        source_term<R>(p, 1, i, j, k, amp, curl);
+        p.E[1][id] = fmaf(st[S::IE + TY * TX + e], curl, st[S::EC + TY * TX + e]);
+      }
+      // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+      if (k <= np2 - 2 && dm_i && dm_j) {
+        float dx = 0.f, dy = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dx = fmaf(cx[q], sHy[ty * WX + tx + XH - R + q], dx);
+          dy = fmaf(cy[q], sHx[(ty + q) * TX + tx], dy);
+        }
+        if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+        if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+        float curl = dx - dy;
+        source_term<R>(p, 2, i, j, k, amp, curl);
+        p.E[2][id] = fmaf(st[S::IE + 2 * TY * TX + e], curl, st[S::EC + 2 * TY * TX + e]);
+      }
+      // volume DTFT of H^{n+1/2}
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 3, lin, nint, facH, qx[R]);
+        volume_accumulate(p, 4, lin, nint, facH, qy[R]);
+        volume_accumulate(p, 5, lin, nint, facH, sHz[(ty + R) * WX + tx + XH]);
+      }
     }
-    // volume DTFT of H^{n+1/2}
-    const int kk = k - p.nbe;
-    if (int_ij && kk >= 0 && kk < p.n[2]) {
-      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-      volume_accumulate(p, 3, lin, nint, facH, qx[c + R]);
-      volume_accumulate(p, 4, lin, nint, facH, qy[c + R]);
-      volume_accumulate(p, 5, lin, nint, facH, __ldg(Hz + id));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+      drain<D>(bars, rg);
+      return;
+    }
+    advance(k + 1 + D);
+#pragma unroll
+    for (int q = 0; q < M - 1; ++q) {
+      qx[q] = qx[q + 1];
+      qy[q] = qy[q + 1];
     }
   }
+  drain<D>(bars, rg);  // no copy is left in flight (normally a no-op)
 }
 
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_H(const DevParams p, const int n) {
-  constexpr int M = 2 * R;
-  constexpr int Q = ZC + M - 1;
+__global__ void __launch_bounds__(NT) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
+                                                 const int n) {
+  constexpr int M = 2 * R, D = ring_depth(R);
+  using S = StageH<R>;
   if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
     receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float *ring = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
+
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int b = blockIdx.x;
   const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int i = bx * TX + static_cast<int>(threadIdx.x % TX), j = by * TY + static_cast<int>(threadIdx.x / TX);
-  if (i >= np0 || j >= np1) return;
-  const int k0 = bz * ZC;
-  const size_t plane = static_cast<size_t>(np0) * np1;
-  const size_t col = static_cast<size_t>(j) * np0 + i;
-  const float *__restrict__ Ex = p.E[0];
-  const float *__restrict__ Ey = p.E[1];
-  const float *__restrict__ Ez = p.E[2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
+  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
+  const bool in_ij = i < np0 && j < np1;
+  const size_t plane = p.plane;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+
+  Ring rg{k0 - R + 1, k0 - R + 1, k0 - R + 1};
+  const int plast = k1 + R - 1;  // last plane the z queue needs
+  auto issue = [&](int pl) {  // called by thread 0 only
+    const int u = pl - rg.pb;
+    float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+    uint64_t *bar = &bars[u % D];
+    const bool full = pl >= k0 && pl < k1;
+    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
+    tma_load_3d(st + S::EX, &tm.m[0], bar, i0, j0 - R, pl);
+    tma_load_3d(st + S::EY, &tm.m[1], bar, i0 - XH, j0, pl);
+    if (full) {
+      tma_load_3d(st + S::EZ, &tm.m[2], bar, i0 - XH, j0 - R, pl);
+      for (int c = 0; c < 3; ++c) tma_load_3d(st + S::HC + c * TY * TX, &tm.m[3 + c], bar, i0, j0, pl);
+    }
+  };
+  // issue planes [rg.nxt, min(upto, plast + 1)) -- thread 0 issues, every
+  // thread tracks the same count
+  auto advance = [&](int upto) {
+    const int stop = min(upto, plast + 1);
+    if (threadIdx.x == 0)
+      for (int q = rg.nxt; q < stop; ++q) issue(q);
+    rg.nxt = max(rg.nxt, stop);
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  advance(rg.pb + D);
+
   const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
   const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
   float cx[M], cy[M];
@@ -261,81 +482,115 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : 3)) k_update_H(const DevPara
     cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
     cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
   }
-  float qx[Q], qy[Q];  // Ex, Ey of this column at planes k0-R+1 .. k0+ZC+R-1
-#pragma unroll
-  for (int t = 0; t < Q; ++t) {
-    const int kk = k0 - R + 1 + t;
-    const bool ok = kk >= 0 && kk < np2;
-    qx[t] = ok ? __ldg(Ex + kk * plane + col) : 0.f;
-    qy[t] = ok ? __ldg(Ey + kk * plane + col) : 0.f;
-  }
   const float dt_mu = p.dt_mu;
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
   const int ii = i - p.nbe, jj = j - p.nbe;
   const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+
+  // register queue: Ex, Ey of this column at planes k-R+1 .. k+R
+  float qx[M], qy[M];
+  bool ok = true;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = k0 + c;
-    if (k >= np2) break;
-    const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
-    const int sk = slab_half(k, np2, nb);
-    const size_t id = k * plane + col;
-    float cz[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
-    // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-    if (dp_j && dp_k) {
-      float dy = 0.f, dz = 0.f;
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dy = fmaf(cy[q], __ldg(Ez + id + static_cast<ptrdiff_t>(q - R + 1) * np0), dy);
-        dz = fmaf(cz[q], qy[c + q], dz);
-      }
-      if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-      if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-      p.H[0][id] = fmaf(-dt_mu, dy - dz, p.H[0][id]);
+  for (int q = 0; q < M - 1; ++q) {
+    const int u = rg.waited - rg.pb;
+    ok = ok && mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+    const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+    qx[q] = st[S::EX + (ty + R) * TX + tx];
+    qy[q] = st[S::EY + ty * WX + tx + XH];
+    ++rg.waited;
+  }
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+    drain<D>(bars, rg);
+    return;
+  }
+  advance(k0 + D);
+
+  for (int k = k0; k < k1; ++k) {
+    {  // queue feed: plane k+R
+      const int u = rg.waited - rg.pb;
+      ok = mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+      const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
+      qx[M - 1] = st[S::EX + (ty + R) * TX + tx];
+      qy[M - 1] = st[S::EY + ty * WX + tx + XH];
+      ++rg.waited;
     }
-    // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-    if (dp_i && dp_k) {
-      float dz = 0.f, dx = 0.f;
+    const float *st = ring + static_cast<size_t>((k - rg.pb) % D) * S::FLOATS;
+    const float *sEz = st + S::EZ, *sEy = st + S::EY, *sEx = st + S::EX;
+    if (ok && in_ij) {
+      const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
+      const int sk = slab_half(k, np2, nb);
+      float cz[M];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dz = fmaf(cz[q], qx[c + q], dz);
-        dx = fmaf(cx[q], __ldg(Ez + id + (q - R + 1)), dx);
-      }
-      if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-      if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-      p.H[1][id] = fmaf(-dt_mu, dz - dx, p.H[1][id]);
-    }
-    // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-    if (dp_i && dp_j) {
-      float dx = 0.f, dy = 0.f;
+      for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
+      const size_t id = k * plane + col;
+      const int e = ty * TX + tx;
+      // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+      if (dp_j && dp_k) {
+        float dy = 0.f, dz = 0.f;
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dx = fmaf(cx[q], __ldg(Ey + id + (q - R + 1)), dx);
-        dy = fmaf(cy[q], __ldg(Ex + id + static_cast<ptrdiff_t>(q - R + 1) * np0), dy);
+        for (int q = 0; q < M; ++q) {
+          dy = fmaf(cy[q], sEz[(ty + 1 + q) * WX + tx + XH], dy);
+          dz = fmaf(cz[q], qy[q], dz);
+        }
+        if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+        if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+        p.H[0][id] = fmaf(-dt_mu, dy - dz, st[S::HC + e]);
       }
-      if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-      if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-      p.H[2][id] = fmaf(-dt_mu, dx - dy, p.H[2][id]);
+      // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+      if (dp_i && dp_k) {
+        float dz = 0.f, dx = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dz = fmaf(cz[q], qx[q], dz);
+          dx = fmaf(cx[q], sEz[(ty + R) * WX + tx + XH - R + 1 + q], dx);
+        }
+        if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+        if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+        p.H[1][id] = fmaf(-dt_mu, dz - dx, st[S::HC + TY * TX + e]);
+      }
+      // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+      if (dp_i && dp_j) {
+        float dx = 0.f, dy = 0.f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          dx = fmaf(cx[q], sEy[ty * WX + tx + XH - R + 1 + q], dx);
+          dy = fmaf(cy[q], sEx[(ty + 1 + q) * TX + tx], dy);
+        }
+        if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+        if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+        p.H[2][id] = fmaf(-dt_mu, dx - dy, st[S::HC + 2 * TY * TX + e]);
+      }
+      // volume DTFT of E^{n+1}
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
+        volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
+        volume_accumulate(p, 2, lin, nint, facE, sEz[(ty + R) * WX + tx + XH]);
+      }
     }
-    // volume DTFT of E^{n+1}
-    const int kk = k - p.nbe;
-    if (int_ij && kk >= 0 && kk < p.n[2]) {
-      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-      volume_accumulate(p, 0, lin, nint, facE, qx[c + R - 1]);
-      volume_accumulate(p, 1, lin, nint, facE, qy[c + R - 1]);
-      volume_accumulate(p, 2, lin, nint, facE, __ldg(Ez + id));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+      drain<D>(bars, rg);
+      return;
+    }
+    advance(k + 1 + D);
+#pragma unroll
+    for (int q = 0; q < M - 1; ++q) {
+      qx[q] = qx[q + 1];
+      qy[q] = qy[q + 1];
     }
   }
+  drain<D>(bars, rg);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
 // the pads replicating the edge (model extension, Sec. 3.4), and the input
 // check (finite, positive, >= sigma_min).
 __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie1, float *ie2, int n0,
-                          int n1, int n2, int np0, int np1, int np2, int nbe, double two_w0_dt,
+                          int n1, int n2, int np0, int np1, int np2, int pitch, int nbe, double two_w0_dt,
                           double sigma_min, int *status) {
   const size_t cells = static_cast<size_t>(np0) * np1 * np2;
   const size_t nint = static_cast<size_t>(n0) * n1 * n2;
@@ -349,11 +604,12 @@ __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie
     const int a = min(max(i - nbe, 0), n0 - 1), b = min(max(j - nbe, 0), n1 - 1),
               cc = min(max(k - nbe, 0), n2 - 1);
     const float s = sigma[c * nint + (static_cast<size_t>(cc) * n1 + b) * n0 + a];
+    const size_t o = (static_cast<size_t>(k) * np1 + j) * pitch + i;
     if (!(s > 0.f) || !isfinite(s) || static_cast<double>(s) < sigma_min) {
       atomicExch(status, EMM_EDEVICE);
-      ie[c][r] = 0.f;
+      ie[c][o] = 0.f;
     } else {
-      ie[c][r] = static_cast<float>(two_w0_dt / static_cast<double>(s));
+      ie[c][o] = static_cast<float>(two_w0_dt / static_cast<double>(s));
     }
   }
 }
@@ -389,6 +645,7 @@ __global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *no
 // ---------------------------------------------------------------------------
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+inline int field_pitch(int np0) { return (np0 + 3) / 4 * 4; }
 
 // Byte layout of the device workspace.
 struct Layout {
@@ -415,7 +672,7 @@ Layout plan(const emm_grid *g, const emm_survey *s) {
     off = align_up(off + bytes);
     return o;
   };
-  const size_t cells = static_cast<size_t>(g->ax[0].npad) * g->ax[1].npad * g->ax[2].npad;
+  const size_t cells = static_cast<size_t>(field_pitch(g->ax[0].npad)) * g->ax[1].npad * g->ax[2].npad;
   const size_t nint = static_cast<size_t>(g->ax[0].n) * g->ax[1].n * g->ax[2].n;
   const size_t m = 2 * static_cast<size_t>(g->rd), nf = s->nfreq;
   const size_t nt = s->nt > 0 ? s->nt : 1, nrec = s->nrec > 0 ? s->nrec : 1;
@@ -453,6 +710,36 @@ int check_survey(const emm_grid *g, const emm_survey *s) {
   return EMM_OK;
 }
 
+// cuTensorMapEncodeTiled, fetched once from the driver through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+// 3-D FP32 tensor [np2][np1][pitch] (dims np0 x np1 x np2), box bx x by x 1.
+bool make_map(CUtensorMap *map, const float *base, const DevParams &p, int bx, int by) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(p.np[0]), static_cast<cuuint64_t>(p.np[1]),
+                              static_cast<cuuint64_t>(p.np[2])};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(p.pitch) * 4,
+                                 static_cast<cuuint64_t>(p.pitch) * p.np[1] * 4};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Optional per-launch timing: events before/after the E and H launches of
 // every `every`-th step (3 events per timed step).
 struct StepEvents {
@@ -462,19 +749,47 @@ struct StepEvents {
 
 template <int R>
 cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st, StepEvents *te) {
+  TmaSet tE{}, tH{};
+  // E launch: Hx (y halo), Hy (x halo), Hz (x and y halo), E, dt/eps
+  bool ok = make_map(&tE.m[0], p.H[0], p, TX, TY + 2 * R) && make_map(&tE.m[1], p.H[1], p, WX, TY) &&
+            make_map(&tE.m[2], p.H[2], p, WX, TY + 2 * R);
+  for (int c = 0; c < 3 && ok; ++c)
+    ok = make_map(&tE.m[3 + c], p.E[c], p, TX, TY) && make_map(&tE.m[6 + c], p.ie[c], p, TX, TY);
+  // H launch: Ex (y halo), Ey (x halo), Ez (x and y halo), H
+  ok = ok && make_map(&tH.m[0], p.E[0], p, TX, TY + 2 * R) && make_map(&tH.m[1], p.E[1], p, WX, TY) &&
+       make_map(&tH.m[2], p.E[2], p, WX, TY + 2 * R);
+  for (int c = 0; c < 3 && ok; ++c) ok = make_map(&tH.m[3 + c], p.H[c], p, TX, TY);
+  if (!ok) return cudaErrorInvalidValue;
+  const size_t se = smem_bytes_E<R>(), sh = smem_bytes_H<R>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(se));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh));
+  if (e != cudaSuccess) return e;
   size_t used = 0;
   for (int n = 0; n < nt; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R><<<blocks, NT, 0, st>>>(p, n);
+    k_update_E<R><<<blocks, NT, se, st>>>(p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R><<<blocks, NT, 0, st>>>(p, n);
+    k_update_H<R><<<blocks, NT, sh, st>>>(p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
     }
   }
   return cudaGetLastError();
+}
+
+template <int R>
+int resident_ctas(int sms) {
+  const size_t se = smem_bytes_E<R>(), sh = smem_bytes_H<R>();
+  cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(se));
+  cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh));
+  int a = 0, b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_E<R>, NT, se);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update_H<R>, NT, sh);
+  return std::max(1, std::min(a, b)) * sms;
 }
 
 int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
@@ -603,6 +918,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     p.cp[a] = reinterpret_cast<const float *>(base + L.cp[a]);
     p.pml[a] = reinterpret_cast<const float *>(base + L.pml[a]);
   }
+  p.pitch = field_pitch(p.np[0]);
+  p.plane = static_cast<size_t>(p.pitch) * p.np[1];
   p.nbe = nbe;
   p.nb = nb;
   for (int c = 0; c < 3; ++c) {
@@ -628,7 +945,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
-  // launch shape: TX x TY column tiles, z split so the grid covers the GPU
+  // launch shape: TX x TY column tiles; z split so that about one wave of
+  // CTAs is resident (each CTA marches its chunk of planes)
   p.tiles_x = (p.np[0] + TX - 1) / TX;
   p.tiles_y = (p.np[1] + TY - 1) / TY;
   int sms = 148;
@@ -636,9 +954,18 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  int slots = sms;
+  switch (rd) {
+    case 1: slots = resident_ctas<1>(sms); break;
+    case 2: slots = resident_ctas<2>(sms); break;
+    case 3: slots = resident_ctas<3>(sms); break;
+    default: slots = resident_ctas<4>(sms); break;
+  }
   const int tiles = p.tiles_x * p.tiles_y;
-  p.kchunk = ZC;
-  p.zchunks = (p.np[2] + ZC - 1) / ZC;
+  int zch = std::max(1, (slots + tiles - 1) / tiles);
+  zch = std::min(zch, std::max(1, p.np[2] / (2 * rd + 2)));
+  p.kchunk = (p.np[2] + zch - 1) / zch;
+  p.zchunks = (p.np[2] + p.kchunk - 1) / p.kchunk;
   p.stencil_blocks = tiles * p.zchunks;
   const int rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
   const int blocks = p.stencil_blocks + rec_blocks;
@@ -652,7 +979,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   k_prepare<<<4 * sms, 256, 0, cs>>>(sigma, reinterpret_cast<float *>(base + L.ie[0]),
                                      reinterpret_cast<float *>(base + L.ie[1]),
                                      reinterpret_cast<float *>(base + L.ie[2]), p.n[0], p.n[1], p.n[2], p.np[0],
-                                     p.np[1], p.np[2], nbe, 2.0 * s->omega0 * dt, s->sigma_min, p.status);
+                                     p.np[1], p.np[2], p.pitch, nbe, 2.0 * s->omega0 * dt, s->sigma_min,
+                                     p.status);
   switch (rd) {
     case 1: e = launch_steps<1>(p, nt, blocks, cs, te); break;
     case 2: e = launch_steps<2>(p, nt, blocks, cs, te); break;

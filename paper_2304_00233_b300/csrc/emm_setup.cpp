@@ -258,6 +258,7 @@ const char *emm_strerror(int code) {
     case EMM_ECUDA: return "CUDA runtime error";
     case EMM_EWORKSPACE: return "workspace too small or misaligned";
     case EMM_EDEVICE: return "device detected an invalid conductivity value";
+    case EMM_ETIMEOUT: return "a bounded device-side wait ran out";
     default: return "unknown error";
   }
 }

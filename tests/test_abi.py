@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_codes():
-    for code in range(8):
+    for code in range(9):
         assert emm.strerror(code)
     assert emm.strerror(99) == "unknown error"
 
