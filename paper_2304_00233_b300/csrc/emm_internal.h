@@ -52,7 +52,8 @@ struct DevParams {
   int pitch;        // row pitch (samples) of the field arrays: np[0] rounded up to 4
   size_t plane;     // pitch * np[1]
   int nbe, nb;
-  int tiles_x, tiles_y, kchunk, zchunks, stencil_blocks;
+  int tiles_x, tiles_y, kchunk, zchunks, stencil_blocks;  // stencil_blocks: CTAs of a launch
+  int rec_blocks;   // CTAs (the first ones) that also gather the receiver DTFT
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
@@ -63,6 +64,7 @@ struct DevParams {
   // source
   int src_on[3];
   int src_start[3][3];
+  int src_any, src_lo[3], src_hi[3];  // bounding box of the source stencils
   const float *jw[3];          // dir_c * w / V at the (2rd)^3 stencil nodes
   const float *amp;            // [nt]: moment * wavelet(t_{n+1/2})
   // receivers

@@ -85,6 +85,7 @@ struct StageH {
 
 template <int R>
 constexpr size_t smem_bytes_E() { return static_cast<size_t>(ring_depth(R)) * StageE<R>::FLOATS * 4 + 128; }
+// (the 128 bytes after the ring hold the D mbarriers and the issued-entry count)
 template <int R>
 constexpr size_t smem_bytes_H() { return static_cast<size_t>(ring_depth(R)) * StageH<R>::FLOATS * 4 + 128; }
 
@@ -224,366 +225,408 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
   if (a >= 0 && a < M && bb >= 0 && bb < M && cc >= 0 && cc < M) curl -= amp * p.jw[c][(cc * M + bb) * M + a];
 }
 
-// Plane ring bookkeeping shared by both launches.  Planes pb, pb+1, ... are
-// issued in order; plane p lives in stage (p - pb) % D and completes phase
-// ((p - pb) / D) & 1 of that stage's mbarrier.
-struct Ring {
-  int pb, nxt, waited;  // first plane, next plane to issue, next plane to wait for
+// ---------------------------------------------------------------------------
+// Persistent plane stream
+// ---------------------------------------------------------------------------
+// A launch has exactly as many CTAs as fit on the GPU at once.  CTA b walks
+// the work items w = b, b + gridDim.x, ...; item w is the TX x TY column tile
+// w % tiles over the z chunk [k0, k1) of chunk w / tiles.  Each item needs the
+// planes k0 - LEAD .. k1 + 2R - 2 - LEAD (the leading/trailing ones only to
+// fill the register z queue).  The planes of all items of a CTA form one
+// stream of entries e = 0, 1, 2, ...: entry e lives in ring stage e % D and
+// completes phase (e / D) & 1 of that stage's mbarrier.  Thread 0 issues the
+// TMA copies of entry e as soon as entry e - D has been released, so the
+// prefetch runs across item boundaries and the ring never drains between
+// items.
+
+struct Item {
+  int i0, j0, k0, k1;
 };
 
-// Every thread waits (bounded) for the copies still in flight, so no TMA
-// write lands in shared memory after the CTA has exited.
-template <int D>
-__device__ void drain(uint64_t *bars, const Ring &rg) {
-  for (int p = rg.waited; p < rg.nxt; ++p) {
-    const int u = p - rg.pb;
-    mbar_wait_bounded(&bars[u % D], (u / D) & 1);
+__device__ __forceinline__ Item item_of(const DevParams &p, int w) {
+  const int tiles = p.tiles_x * p.tiles_y;
+  const int t = w % tiles, c = w / tiles;
+  Item it;
+  it.i0 = (t % p.tiles_x) * TX;
+  it.j0 = (t / p.tiles_x) * TY;
+  it.k0 = c * p.kchunk;
+  it.k1 = min(it.k0 + p.kchunk, p.np[2]);
+  return it;
+}
+
+// E launch: copies of one plane entry; Hx (y halo) and Hy (x halo) feed the z
+// queue, the rest only matter for planes the item updates ("full").
+template <int R>
+struct HalfE {
+  using S = StageE<R>;
+  static constexpr int LEAD = R;  // queue planes below k0
+  __device__ static void issue(const TmaSet &tm, float *st, uint64_t *bar, const Item &it, int pl) {
+    const bool full = pl >= it.k0 && pl < it.k1;
+    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
+    tma_load_3d(st + S::HX, &tm.m[0], bar, it.i0, it.j0 - R, pl);
+    tma_load_3d(st + S::HY, &tm.m[1], bar, it.i0 - XH, it.j0, pl);
+    if (full) {
+      tma_load_3d(st + S::HZ, &tm.m[2], bar, it.i0 - XH, it.j0 - R, pl);
+      for (int c = 0; c < 3; ++c) {
+        tma_load_3d(st + S::EC + c * TY * TX, &tm.m[3 + c], bar, it.i0, it.j0, pl);
+        tma_load_3d(st + S::IE + c * TY * TX, &tm.m[6 + c], bar, it.i0, it.j0, pl);
+      }
+    }
   }
+  __device__ static void queue_vals(const float *st, int tx, int ty, float &a, float &b) {
+    a = st[S::HX + (ty + R) * TX + tx];
+    b = st[S::HY + ty * WX + tx + XH];
+  }
+};
+
+// H launch: Ex (y halo) and Ey (x halo) feed the z queue.
+template <int R>
+struct HalfH {
+  using S = StageH<R>;
+  static constexpr int LEAD = R - 1;
+  __device__ static void issue(const TmaSet &tm, float *st, uint64_t *bar, const Item &it, int pl) {
+    const bool full = pl >= it.k0 && pl < it.k1;
+    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
+    tma_load_3d(st + S::EX, &tm.m[0], bar, it.i0, it.j0 - R, pl);
+    tma_load_3d(st + S::EY, &tm.m[1], bar, it.i0 - XH, it.j0, pl);
+    if (full) {
+      tma_load_3d(st + S::EZ, &tm.m[2], bar, it.i0 - XH, it.j0 - R, pl);
+      for (int c = 0; c < 3; ++c) tma_load_3d(st + S::HC + c * TY * TX, &tm.m[3 + c], bar, it.i0, it.j0, pl);
+    }
+  }
+  __device__ static void queue_vals(const float *st, int tx, int ty, float &a, float &b) {
+    a = st[S::EX + (ty + R) * TX + tx];
+    b = st[S::EY + ty * WX + tx + XH];
+  }
+};
+
+// Producer side of the stream (thread 0 only): items, entry count.
+struct Producer {
+  int w, q;        // current item and entry index within it
+  long long e;     // entries issued so far
+};
+
+template <int R, class Pol>
+__device__ __forceinline__ void produce(const DevParams &p, const TmaSet &tm, float *ring, uint64_t *bars,
+                                        Producer &pr, long long limit, int nitems, long long *s_issued) {
+  constexpr int D = ring_depth(R), M = 2 * R;
+  while (pr.e < limit && pr.w < nitems) {
+    const Item it = item_of(p, pr.w);
+    const int s = static_cast<int>(pr.e % D);
+    Pol::issue(tm, ring + static_cast<size_t>(s) * Pol::S::FLOATS, &bars[s], it, it.k0 - Pol::LEAD + pr.q);
+    ++pr.e;
+    if (++pr.q == (it.k1 - it.k0) + M - 1) {
+      pr.q = 0;
+      pr.w += gridDim.x;
+    }
+  }
+  *s_issued = pr.e;
+}
+
+template <int D>
+__device__ __forceinline__ bool wait_entry(uint64_t *bars, long long e) {
+  return mbar_wait_bounded(&bars[e % D], static_cast<uint32_t>((e / D) & 1));
+}
+
+// Abort path: every thread waits (bounded) for the copies still in flight,
+// so no TMA write lands in shared memory after the CTA has exited.
+template <int D>
+__device__ void drain(uint64_t *bars, long long from, long long issued) {
+  for (long long e = from; e < issued; ++e) wait_entry<D>(bars, e);
+}
+
+// Does the item's box meet the source stencils' bounding box?
+__device__ __forceinline__ bool item_has_source(const DevParams &p, const Item &it) {
+  return p.src_any && it.i0 + TX > p.src_lo[0] && it.i0 <= p.src_hi[0] && it.j0 + TY > p.src_lo[1] &&
+         it.j0 <= p.src_hi[1] && it.k1 > p.src_lo[2] && it.k0 <= p.src_hi[2];
 }
 
 // ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
+__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
                                                  const int n) {
   constexpr int M = 2 * R, D = ring_depth(R);
+  using Pol = HalfE<R>;
   using S = StageE<R>;
-  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
-    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
-    return;
-  }
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-
-  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const int b = blockIdx.x;
-  const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
-  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
-  const bool in_ij = i < np0 && j < np1;
-  const size_t plane = p.plane;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
-
-  Ring rg{k0 - R, k0 - R, k0 - R};
-  const int plast = k1 + R - 2;  // last plane the z queue needs
-  auto issue = [&](int pl) {  // called by thread 0 only
-    const int u = pl - rg.pb;
-    float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-    uint64_t *bar = &bars[u % D];
-    const bool full = pl >= k0 && pl < k1;
-    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
-    tma_load_3d(st + S::HX, &tm.m[0], bar, i0, j0 - R, pl);
-    tma_load_3d(st + S::HY, &tm.m[1], bar, i0 - XH, j0, pl);
-    if (full) {
-      tma_load_3d(st + S::HZ, &tm.m[2], bar, i0 - XH, j0 - R, pl);
-      for (int c = 0; c < 3; ++c) {
-        tma_load_3d(st + S::EC + c * TY * TX, &tm.m[3 + c], bar, i0, j0, pl);
-        tma_load_3d(st + S::IE + c * TY * TX, &tm.m[6 + c], bar, i0, j0, pl);
-      }
-    }
-  };
-  // issue planes [rg.nxt, min(upto, plast + 1)) -- thread 0 issues, every
-  // thread tracks the same count
-  auto advance = [&](int upto) {
-    const int stop = min(upto, plast + 1);
-    if (threadIdx.x == 0)
-      for (int q = rg.nxt; q < stop; ++q) issue(q);
-    rg.nxt = max(rg.nxt, stop);
-  };
+  long long *s_issued = reinterpret_cast<long long *>(bars + D);
+  const int nitems = p.tiles_x * p.tiles_y * p.zchunks;
+  Producer pr{static_cast<int>(blockIdx.x), 0, 0};
   if (threadIdx.x == 0) {
     for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
+    produce<R, Pol>(p, tm, ring, bars, pr, D, nitems, s_issued);
   }
+  // receiver DTFT of H^{n+1/2} (this launch does not write H)
+  if (static_cast<int>(blockIdx.x) < p.rec_blocks)
+    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
   __syncthreads();
-  advance(rg.pb + D);
 
-  const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
-  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
-  float cx[M], cy[M];
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
-    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
-  }
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const float amp = __ldg(p.amp + n);
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
-  const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-
-  // register queue: Hx, Hy of this column at planes k-R .. k+R-1
-  float qx[M], qy[M];
-  bool ok = true;
+  long long ec = 0;  // entries consumed
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const Item it = item_of(p, w);
+    const int i = it.i0 + tx, j = it.j0 + ty;
+    const bool in_ij = i < np0 && j < np1;
+    const size_t col = static_cast<size_t>(j) * p.pitch + i;
+    const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
+    const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
+    const bool src = item_has_source(p, it);
+    float cx[M], cy[M];
 #pragma unroll
-  for (int q = 0; q < M - 1; ++q) {
-    const int u = rg.waited - rg.pb;
-    ok = ok && mbar_wait_bounded(&bars[u % D], (u / D) & 1);
-    const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-    qx[q] = st[S::HX + (ty + R) * TX + tx];
-    qy[q] = st[S::HY + ty * WX + tx + XH];
-    ++rg.waited;
-  }
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-    drain<D>(bars, rg);
-    return;
-  }
-  advance(k0 + D);
-
-  for (int k = k0; k < k1; ++k) {
-    {  // queue feed: plane k+R-1
-      const int u = rg.waited - rg.pb;
-      ok = mbar_wait_bounded(&bars[u % D], (u / D) & 1);
-      const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-      qx[M - 1] = st[S::HX + (ty + R) * TX + tx];
-      qy[M - 1] = st[S::HY + ty * WX + tx + XH];
-      ++rg.waited;
+    for (int q = 0; q < M; ++q) {
+      cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
+      cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
     }
-    const float *st = ring + static_cast<size_t>((k - rg.pb) % D) * S::FLOATS;
-    const float *sHz = st + S::HZ, *sHy = st + S::HY, *sHx = st + S::HX;
-    if (ok && in_ij) {
-      const bool dm_k = k >= R && k <= np2 - 1 - R;
-      const int sk = slab_int(k, np2, nb);
-      float cz[M];
+    const int ii = i - p.nbe, jj = j - p.nbe;
+    const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+    const long long e0 = ec;
+
+    // z queue: Hx, Hy of this column at planes k-R .. k+R-1
+    float qx[M], qy[M];
+    bool ok = true;
 #pragma unroll
-      for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
-      const size_t id = k * plane + col;
-      const int e = ty * TX + tx;
-      // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-      if (i <= np0 - 2 && dm_j && dm_k) {
-        float dy = 0.f, dz = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dy = fmaf(cy[q], sHz[(ty + q) * WX + tx + XH], dy);
-          dz = fmaf(cz[q], qy[q], dz);
-        }
-        if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-        if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-        float curl = dy - dz;
-        source_term<R>(p, 0, i, j, k, amp, curl);
-        p.E[0][id] = fmaf(st[S::IE + e], curl, st[S::EC + e]);
-      }
-      // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-      if (j <= np1 - 2 && dm_i && dm_k) {
-        float dz = 0.f, dx = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dz = fmaf(cz[q], qx[q], dz);
-          dx = fmaf(cx[q], sHz[(ty + R) * WX + tx + XH - R + q], dx);
-        }
-        if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-        if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-        float curl = dz - dx;
-        source_term<R>(p, 1, i, j, k, amp, curl);
-        p.E[1][id] = fmaf(st[S::IE + TY * TX + e], curl, st[S::EC + TY * TX + e]);
-      }
-      // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-      if (k <= np2 - 2 && dm_i && dm_j) {
-        float dx = 0.f, dy = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dx = fmaf(cx[q], sHy[ty * WX + tx + XH - R + q], dx);
-          dy = fmaf(cy[q], sHx[(ty + q) * TX + tx], dy);
-        }
-        if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-        if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-        float curl = dx - dy;
-        source_term<R>(p, 2, i, j, k, amp, curl);
-        p.E[2][id] = fmaf(st[S::IE + 2 * TY * TX + e], curl, st[S::EC + 2 * TY * TX + e]);
-      }
-      // volume DTFT of H^{n+1/2}
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 3, lin, nint, facH, qx[R]);
-        volume_accumulate(p, 4, lin, nint, facH, qy[R]);
-        volume_accumulate(p, 5, lin, nint, facH, sHz[(ty + R) * WX + tx + XH]);
-      }
+    for (int q = 0; q < M - 1; ++q) {
+      ok = wait_entry<D>(bars, ec) && ok;
+      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
+      ++ec;
     }
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-      drain<D>(bars, rg);
+      drain<D>(bars, ec - (M - 1), *s_issued);
       return;
     }
-    advance(k + 1 + D);
+    if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, e0 + Pol::LEAD + D, nitems, s_issued);
+
+    for (int k = it.k0; k < it.k1; ++k) {
+      ok = wait_entry<D>(bars, ec);  // queue feed: plane k+R-1
+      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
+      ++ec;
+      const long long ek = e0 + Pol::LEAD + (k - it.k0);  // entry of plane k
+      const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
+      const float *sHz = st + S::HZ, *sHy = st + S::HY, *sHx = st + S::HX;
+      if (ok && in_ij) {
+        const bool dm_k = k >= R && k <= np2 - 1 - R;
+        const int sk = slab_int(k, np2, nb);
+        float cz[M];
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      qx[q] = qx[q + 1];
-      qy[q] = qy[q + 1];
+        for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
+        const size_t id = k * p.plane + col;
+        const int e = ty * TX + tx;
+        // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+        if (i <= np0 - 2 && dm_j && dm_k) {
+          float dy = 0.f, dz = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dy = fmaf(cy[q], sHz[(ty + q) * WX + tx + XH], dy);
+            dz = fmaf(cz[q], qy[q], dz);
+          }
+          if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+          if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+          float curl = dy - dz;
+          if (src) source_term<R>(p, 0, i, j, k, amp, curl);
+          p.E[0][id] = fmaf(st[S::IE + e], curl, st[S::EC + e]);
+        }
+        // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+        if (j <= np1 - 2 && dm_i && dm_k) {
+          float dz = 0.f, dx = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dz = fmaf(cz[q], qx[q], dz);
+            dx = fmaf(cx[q], sHz[(ty + R) * WX + tx + XH - R + q], dx);
+          }
+          if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
+          if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+          float curl = dz - dx;
+          if (src) source_term<R>(p, 1, i, j, k, amp, curl);
+          p.E[1][id] = fmaf(st[S::IE + TY * TX + e], curl, st[S::EC + TY * TX + e]);
+        }
+        // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+        if (k <= np2 - 2 && dm_i && dm_j) {
+          float dx = 0.f, dy = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dx = fmaf(cx[q], sHy[ty * WX + tx + XH - R + q], dx);
+            dy = fmaf(cy[q], sHx[(ty + q) * TX + tx], dy);
+          }
+          if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
+          if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
+          float curl = dx - dy;
+          if (src) source_term<R>(p, 2, i, j, k, amp, curl);
+          p.E[2][id] = fmaf(st[S::IE + 2 * TY * TX + e], curl, st[S::EC + 2 * TY * TX + e]);
+        }
+        // volume DTFT of H^{n+1/2}
+        const int kk = k - p.nbe;
+        if (int_ij && kk >= 0 && kk < p.n[2]) {
+          const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+          volume_accumulate(p, 3, lin, nint, facH, qx[R]);
+          volume_accumulate(p, 4, lin, nint, facH, qy[R]);
+          volume_accumulate(p, 5, lin, nint, facH, sHz[(ty + R) * WX + tx + XH]);
+        }
+      }
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+        drain<D>(bars, ec - 1, *s_issued);
+        return;
+      }
+      // release plane k (and, after the last plane, the item's trailing queue planes)
+      const long long freed = (k + 1 == it.k1) ? ec : ek + 1;
+      if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, freed + D, nitems, s_issued);
+#pragma unroll
+      for (int q = 0; q < M - 1; ++q) {
+        qx[q] = qx[q + 1];
+        qy[q] = qy[q + 1];
+      }
     }
   }
-  drain<D>(bars, rg);  // no copy is left in flight (normally a no-op)
 }
 
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
+__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
                                                  const int n) {
   constexpr int M = 2 * R, D = ring_depth(R);
+  using Pol = HalfH<R>;
   using S = StageH<R>;
-  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
-    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
-    return;
-  }
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-
-  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const int b = blockIdx.x;
-  const int bx = b % p.tiles_x, by = (b / p.tiles_x) % p.tiles_y, bz = b / (p.tiles_x * p.tiles_y);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = bx * TX, j0 = by * TY, i = i0 + tx, j = j0 + ty;
-  const int k0 = bz * p.kchunk, k1 = min(k0 + p.kchunk, np2);
-  const bool in_ij = i < np0 && j < np1;
-  const size_t plane = p.plane;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
-
-  Ring rg{k0 - R + 1, k0 - R + 1, k0 - R + 1};
-  const int plast = k1 + R - 1;  // last plane the z queue needs
-  auto issue = [&](int pl) {  // called by thread 0 only
-    const int u = pl - rg.pb;
-    float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-    uint64_t *bar = &bars[u % D];
-    const bool full = pl >= k0 && pl < k1;
-    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
-    tma_load_3d(st + S::EX, &tm.m[0], bar, i0, j0 - R, pl);
-    tma_load_3d(st + S::EY, &tm.m[1], bar, i0 - XH, j0, pl);
-    if (full) {
-      tma_load_3d(st + S::EZ, &tm.m[2], bar, i0 - XH, j0 - R, pl);
-      for (int c = 0; c < 3; ++c) tma_load_3d(st + S::HC + c * TY * TX, &tm.m[3 + c], bar, i0, j0, pl);
-    }
-  };
-  // issue planes [rg.nxt, min(upto, plast + 1)) -- thread 0 issues, every
-  // thread tracks the same count
-  auto advance = [&](int upto) {
-    const int stop = min(upto, plast + 1);
-    if (threadIdx.x == 0)
-      for (int q = rg.nxt; q < stop; ++q) issue(q);
-    rg.nxt = max(rg.nxt, stop);
-  };
+  long long *s_issued = reinterpret_cast<long long *>(bars + D);
+  const int nitems = p.tiles_x * p.tiles_y * p.zchunks;
+  Producer pr{static_cast<int>(blockIdx.x), 0, 0};
   if (threadIdx.x == 0) {
     for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
+    produce<R, Pol>(p, tm, ring, bars, pr, D, nitems, s_issued);
   }
+  // receiver DTFT of E^{n+1} (this launch does not write E)
+  if (static_cast<int>(blockIdx.x) < p.rec_blocks)
+    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
   __syncthreads();
-  advance(rg.pb + D);
 
-  const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
-  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
-  float cx[M], cy[M];
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
-    cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
-  }
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const float dt_mu = p.dt_mu;
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
-  const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-
-  // register queue: Ex, Ey of this column at planes k-R+1 .. k+R
-  float qx[M], qy[M];
-  bool ok = true;
+  long long ec = 0;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const Item it = item_of(p, w);
+    const int i = it.i0 + tx, j = it.j0 + ty;
+    const bool in_ij = i < np0 && j < np1;
+    const size_t col = static_cast<size_t>(j) * p.pitch + i;
+    const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
+    const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
+    float cx[M], cy[M];
 #pragma unroll
-  for (int q = 0; q < M - 1; ++q) {
-    const int u = rg.waited - rg.pb;
-    ok = ok && mbar_wait_bounded(&bars[u % D], (u / D) & 1);
-    const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-    qx[q] = st[S::EX + (ty + R) * TX + tx];
-    qy[q] = st[S::EY + ty * WX + tx + XH];
-    ++rg.waited;
-  }
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-    drain<D>(bars, rg);
-    return;
-  }
-  advance(k0 + D);
-
-  for (int k = k0; k < k1; ++k) {
-    {  // queue feed: plane k+R
-      const int u = rg.waited - rg.pb;
-      ok = mbar_wait_bounded(&bars[u % D], (u / D) & 1);
-      const float *st = ring + static_cast<size_t>(u % D) * S::FLOATS;
-      qx[M - 1] = st[S::EX + (ty + R) * TX + tx];
-      qy[M - 1] = st[S::EY + ty * WX + tx + XH];
-      ++rg.waited;
+    for (int q = 0; q < M; ++q) {
+      cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
+      cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
     }
-    const float *st = ring + static_cast<size_t>((k - rg.pb) % D) * S::FLOATS;
-    const float *sEz = st + S::EZ, *sEy = st + S::EY, *sEx = st + S::EX;
-    if (ok && in_ij) {
-      const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
-      const int sk = slab_half(k, np2, nb);
-      float cz[M];
+    const int ii = i - p.nbe, jj = j - p.nbe;
+    const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+    const long long e0 = ec;
+
+    // z queue: Ex, Ey of this column at planes k-R+1 .. k+R
+    float qx[M], qy[M];
+    bool ok = true;
 #pragma unroll
-      for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
-      const size_t id = k * plane + col;
-      const int e = ty * TX + tx;
-      // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-      if (dp_j && dp_k) {
-        float dy = 0.f, dz = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dy = fmaf(cy[q], sEz[(ty + 1 + q) * WX + tx + XH], dy);
-          dz = fmaf(cz[q], qy[q], dz);
-        }
-        if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-        if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-        p.H[0][id] = fmaf(-dt_mu, dy - dz, st[S::HC + e]);
-      }
-      // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-      if (dp_i && dp_k) {
-        float dz = 0.f, dx = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dz = fmaf(cz[q], qx[q], dz);
-          dx = fmaf(cx[q], sEz[(ty + R) * WX + tx + XH - R + 1 + q], dx);
-        }
-        if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-        if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-        p.H[1][id] = fmaf(-dt_mu, dz - dx, st[S::HC + TY * TX + e]);
-      }
-      // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-      if (dp_i && dp_j) {
-        float dx = 0.f, dy = 0.f;
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-          dx = fmaf(cx[q], sEy[ty * WX + tx + XH - R + 1 + q], dx);
-          dy = fmaf(cy[q], sEx[(ty + 1 + q) * TX + tx], dy);
-        }
-        if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-        if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-        p.H[2][id] = fmaf(-dt_mu, dx - dy, st[S::HC + 2 * TY * TX + e]);
-      }
-      // volume DTFT of E^{n+1}
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
-        volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
-        volume_accumulate(p, 2, lin, nint, facE, sEz[(ty + R) * WX + tx + XH]);
-      }
+    for (int q = 0; q < M - 1; ++q) {
+      ok = wait_entry<D>(bars, ec) && ok;
+      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
+      ++ec;
     }
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-      drain<D>(bars, rg);
+      drain<D>(bars, ec - (M - 1), *s_issued);
       return;
     }
-    advance(k + 1 + D);
+    if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, e0 + Pol::LEAD + D, nitems, s_issued);
+
+    for (int k = it.k0; k < it.k1; ++k) {
+      ok = wait_entry<D>(bars, ec);  // queue feed: plane k+R
+      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
+      ++ec;
+      const long long ek = e0 + Pol::LEAD + (k - it.k0);
+      const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
+      const float *sEz = st + S::EZ, *sEy = st + S::EY, *sEx = st + S::EX;
+      if (ok && in_ij) {
+        const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
+        const int sk = slab_half(k, np2, nb);
+        float cz[M];
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      qx[q] = qx[q + 1];
-      qy[q] = qy[q + 1];
+        for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
+        const size_t id = k * p.plane + col;
+        const int e = ty * TX + tx;
+        // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+        if (dp_j && dp_k) {
+          float dy = 0.f, dz = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dy = fmaf(cy[q], sEz[(ty + 1 + q) * WX + tx + XH], dy);
+            dz = fmaf(cz[q], qy[q], dz);
+          }
+          if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+          if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+          p.H[0][id] = fmaf(-dt_mu, dy - dz, st[S::HC + e]);
+        }
+        // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+        if (dp_i && dp_k) {
+          float dz = 0.f, dx = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dz = fmaf(cz[q], qx[q], dz);
+            dx = fmaf(cx[q], sEz[(ty + R) * WX + tx + XH - R + 1 + q], dx);
+          }
+          if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
+          if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+          p.H[1][id] = fmaf(-dt_mu, dz - dx, st[S::HC + TY * TX + e]);
+        }
+        // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+        if (dp_i && dp_j) {
+          float dx = 0.f, dy = 0.f;
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            dx = fmaf(cx[q], sEy[ty * WX + tx + XH - R + 1 + q], dx);
+            dy = fmaf(cy[q], sEx[(ty + 1 + q) * TX + tx], dy);
+          }
+          if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
+          if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
+          p.H[2][id] = fmaf(-dt_mu, dx - dy, st[S::HC + 2 * TY * TX + e]);
+        }
+        // volume DTFT of E^{n+1}
+        const int kk = k - p.nbe;
+        if (int_ij && kk >= 0 && kk < p.n[2]) {
+          const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+          volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
+          volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
+          volume_accumulate(p, 2, lin, nint, facE, sEz[(ty + R) * WX + tx + XH]);
+        }
+      }
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+        drain<D>(bars, ec - 1, *s_issued);
+        return;
+      }
+      const long long freed = (k + 1 == it.k1) ? ec : ek + 1;
+      if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, freed + D, nitems, s_issued);
+#pragma unroll
+      for (int q = 0; q < M - 1; ++q) {
+        qx[q] = qx[q + 1];
+        qy[q] = qy[q + 1];
+      }
     }
   }
-  drain<D>(bars, rg);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -945,8 +988,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
-  // launch shape: TX x TY column tiles; z split so that about one wave of
-  // CTAs is resident (each CTA marches its chunk of planes)
+  // launch shape: one resident wave of persistent CTAs walking (tile, z-chunk)
+  // work items; the chunk length gives about four items per CTA
   p.tiles_x = (p.np[0] + TX - 1) / TX;
   p.tiles_y = (p.np[1] + TY - 1) / TY;
   int sms = 148;
@@ -961,14 +1004,30 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     case 3: slots = resident_ctas<3>(sms); break;
     default: slots = resident_ctas<4>(sms); break;
   }
-  const int tiles = p.tiles_x * p.tiles_y;
-  int zch = std::max(1, (slots + tiles - 1) / tiles);
-  zch = std::min(zch, std::max(1, p.np[2] / (2 * rd + 2)));
-  p.kchunk = (p.np[2] + zch - 1) / zch;
-  p.zchunks = (p.np[2] + p.kchunk - 1) / p.kchunk;
-  p.stencil_blocks = tiles * p.zchunks;
-  const int rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
-  const int blocks = p.stencil_blocks + rec_blocks;
+  const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
+  int kc = static_cast<int>(tiles * p.np[2] / (4LL * slots));
+  kc = std::max(kc, 8);
+  kc = std::min(kc, p.np[2]);
+  p.kchunk = kc;
+  p.zchunks = (p.np[2] + kc - 1) / kc;
+  const long long nitems = tiles * p.zchunks;
+  p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
+  const int blocks = static_cast<int>(std::max<long long>(std::min<long long>(slots, nitems), p.rec_blocks));
+  p.stencil_blocks = blocks;
+  // bounding box of the source stencils (lets CTAs far from it skip the test)
+  p.src_any = 0;
+  for (int a = 0; a < 3; ++a) {
+    p.src_lo[a] = 1 << 30;
+    p.src_hi[a] = -1;
+  }
+  for (int c = 0; c < 3; ++c)
+    if (p.src_on[c]) {
+      p.src_any = 1;
+      for (int a = 0; a < 3; ++a) {
+        p.src_lo[a] = std::min(p.src_lo[a], p.src_start[c][a]);
+        p.src_hi[a] = std::max(p.src_hi[a], p.src_start[c][a] + m - 1);
+      }
+    }
 
   // ---- enqueue ----
   cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, cs);
