@@ -47,12 +47,18 @@ namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
 constexpr int TY = 8;   // tile height (y)
-constexpr int NT = TX * TY;
+constexpr int NT = TX * TY;  // consumer threads (one per column of the tile)
+constexpr int NCW = NT / 32;   // consumer warps
+constexpr int NTB = NT + 32;   // block: consumers + one producer warp
 constexpr int XH = 4;   // x halo of the TMA boxes (>= R, keeps box x starts 16-byte aligned)
 constexpr int WX = TX + 2 * XH;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of one mbarrier wait
 
-__host__ __device__ constexpr int ring_depth(int R) { return R + 3; }
+// Ring stages (>= 2R-1 so an item's queue prologue fits) and resident CTAs
+// per SM; together they keep about four planes per CTA in flight within the
+// 227 KB of shared memory.
+__host__ __device__ constexpr int ring_depth(int R) { return R == 1 ? 5 : (R == 2 ? 6 : (R == 3 ? 6 : 8)); }
+__host__ __device__ constexpr int min_ctas(int R) { return R <= 3 ? 3 : 2; }
 __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }  // floats -> 128 B
 
 // Stage layout (floats) of the E launch: Hz [TY+2R][WX], Hy [TY][WX],
@@ -84,10 +90,10 @@ struct StageH {
 };
 
 template <int R>
-constexpr size_t smem_bytes_E() { return static_cast<size_t>(ring_depth(R)) * StageE<R>::FLOATS * 4 + 128; }
-// (the 128 bytes after the ring hold the D mbarriers and the issued-entry count)
+constexpr size_t smem_bytes_E() { return static_cast<size_t>(ring_depth(R)) * StageE<R>::FLOATS * 4 + 256; }
+// (the 256 bytes after the ring hold the full/empty mbarriers and the control words)
 template <int R>
-constexpr size_t smem_bytes_H() { return static_cast<size_t>(ring_depth(R)) * StageH<R>::FLOATS * 4 + 128; }
+constexpr size_t smem_bytes_H() { return static_cast<size_t>(ring_depth(R)) * StageH<R>::FLOATS * 4 + 256; }
 
 // Tensor maps of one launch: [0..2] the halo'd sources (z-halo field with a
 // y halo, x-halo field, xy-halo field), [3..5] the updated field, [6..8] dt/eps.
@@ -226,32 +232,45 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 }
 
 // ---------------------------------------------------------------------------
-// Persistent plane stream
+// Persistent, warp-specialised plane stream
 // ---------------------------------------------------------------------------
-// A launch has exactly as many CTAs as fit on the GPU at once.  CTA b walks
-// the work items w = b, b + gridDim.x, ...; item w is the TX x TY column tile
-// w % tiles over the z chunk [k0, k1) of chunk w / tiles.  Each item needs the
-// planes k0 - LEAD .. k1 + 2R - 2 - LEAD (the leading/trailing ones only to
-// fill the register z queue).  The planes of all items of a CTA form one
-// stream of entries e = 0, 1, 2, ...: entry e lives in ring stage e % D and
-// completes phase (e / D) & 1 of that stage's mbarrier.  Thread 0 issues the
-// TMA copies of entry e as soon as entry e - D has been released, so the
-// prefetch runs across item boundaries and the ring never drains between
-// items.
+// A launch has exactly as many CTAs as fit on the GPU at once.  The
+// (column tile, plane) units of the grid, tile-major with z fastest, are cut
+// into gridDim.x equal contiguous ranges, one per CTA, so every CTA updates
+// the same number of planes.  A range is walked as items: a run of planes
+// [k0, k1) of one tile.  An item needs the planes k0 - LEAD .. k1 + 2R - 2 -
+// LEAD, the leading and trailing ones only to fill the register z queue.
+// Every plane of every item of the CTA is one entry of a FIFO e = 0, 1, ...:
+// entry e lives in ring stage e % D.  Warp NCW (the producer) issues the TMA
+// copies of entry e once the consumers have released entry e - D (empty
+// barrier) and completes it on the full barrier; the NCW consumer warps wait
+// on full, compute, and release entries in FIFO order.  No CTA-wide barrier
+// sits in the loop.
 
 struct Item {
   int i0, j0, k0, k1;
 };
 
-__device__ __forceinline__ Item item_of(const DevParams &p, int w) {
-  const int tiles = p.tiles_x * p.tiles_y;
-  const int t = w % tiles, c = w / tiles;
-  Item it;
-  it.i0 = (t % p.tiles_x) * TX;
-  it.j0 = (t / p.tiles_x) * TY;
-  it.k0 = c * p.kchunk;
-  it.k1 = min(it.k0 + p.kchunk, p.np[2]);
-  return it;
+struct Range {
+  long long u, u1;  // next unit, end of this CTA's units
+};
+
+__device__ __forceinline__ Range cta_range(const DevParams &p) {
+  const long long units = static_cast<long long>(p.tiles_x) * p.tiles_y * p.np[2];
+  return Range{units * blockIdx.x / gridDim.x, units * (blockIdx.x + 1) / gridDim.x};
+}
+
+// Next item of the range (false when the range is exhausted).
+__device__ __forceinline__ bool next_item(const DevParams &p, Range &r, Item &it) {
+  if (r.u >= r.u1) return false;
+  const int np2 = p.np[2];
+  const long long t = r.u / np2;
+  it.k0 = static_cast<int>(r.u - t * np2);
+  it.k1 = static_cast<int>(min(static_cast<long long>(np2), r.u1 - t * np2));
+  it.i0 = static_cast<int>(t % p.tiles_x) * TX;
+  it.j0 = static_cast<int>(t / p.tiles_x) * TY;
+  r.u = t * np2 + it.k1;
+  return true;
 }
 
 // E launch: copies of one plane entry; Hx (y halo) and Hy (x halo) feed the z
@@ -300,39 +319,78 @@ struct HalfH {
   }
 };
 
-// Producer side of the stream (thread 0 only): items, entry count.
-struct Producer {
-  int w, q;        // current item and entry index within it
-  long long e;     // entries issued so far
+// Shared-memory control block after the ring.
+template <int D>
+struct Ctl {
+  uint64_t full[D];
+  uint64_t empty[D];
+  long long issued;  // entries issued by the producer
+  int abort;         // a bounded wait ran out somewhere in the CTA
 };
 
+// Bounded wait that also gives up when another warp has flagged an abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && (*abort || global_ns() - t0 > kWaitNs)) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Producer warp, lane 0: issue every entry of the CTA's range in order.
 template <int R, class Pol>
-__device__ __forceinline__ void produce(const DevParams &p, const TmaSet &tm, float *ring, uint64_t *bars,
-                                        Producer &pr, long long limit, int nitems, long long *s_issued) {
+__device__ void producer_loop(const DevParams &p, const TmaSet &tm, float *ring, Ctl<ring_depth(R)> *ctl) {
   constexpr int D = ring_depth(R), M = 2 * R;
-  while (pr.e < limit && pr.w < nitems) {
-    const Item it = item_of(p, pr.w);
-    const int s = static_cast<int>(pr.e % D);
-    Pol::issue(tm, ring + static_cast<size_t>(s) * Pol::S::FLOATS, &bars[s], it, it.k0 - Pol::LEAD + pr.q);
-    ++pr.e;
-    if (++pr.q == (it.k1 - it.k0) + M - 1) {
-      pr.q = 0;
-      pr.w += gridDim.x;
+  Range r = cta_range(p);
+  Item it;
+  long long e = 0;
+  while (next_item(p, r, it)) {
+    const int cnt = (it.k1 - it.k0) + M - 1;
+    for (int q = 0; q < cnt; ++q, ++e) {
+      const int s = static_cast<int>(e % D);
+      if (e >= D && !wait_or_abort(&ctl->empty[s], static_cast<uint32_t>((e / D - 1) & 1), &ctl->abort)) {
+        ctl->abort = 1;
+        atomicExch(p.status, EMM_ETIMEOUT);
+        return;
+      }
+      Pol::issue(tm, ring + static_cast<size_t>(s) * Pol::S::FLOATS, &ctl->full[s], it, it.k0 - Pol::LEAD + q);
+      *reinterpret_cast<volatile long long *>(&ctl->issued) = e + 1;
     }
   }
-  *s_issued = pr.e;
 }
 
+// Consumer side: wait for entry e to land (false on timeout/abort).
 template <int D>
-__device__ __forceinline__ bool wait_entry(uint64_t *bars, long long e) {
-  return mbar_wait_bounded(&bars[e % D], static_cast<uint32_t>((e / D) & 1));
+__device__ __forceinline__ bool consume_wait(Ctl<D> *ctl, long long e) {
+  if (wait_or_abort(&ctl->full[e % D], static_cast<uint32_t>((e / D) & 1), &ctl->abort)) return true;
+  ctl->abort = 1;
+  return false;
 }
 
-// Abort path: every thread waits (bounded) for the copies still in flight,
-// so no TMA write lands in shared memory after the CTA has exited.
+// Consumer side: this warp is done with entry e.
 template <int D>
-__device__ void drain(uint64_t *bars, long long from, long long issued) {
-  for (long long e = from; e < issued; ++e) wait_entry<D>(bars, e);
+__device__ __forceinline__ void release(Ctl<D> *ctl, long long e) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&ctl->empty[e % D]);
+}
+
+// End of the kernel: if anything aborted, wait (bounded) for the copies that
+// may still be in flight (only the last D issued entries can be) so no TMA
+// write lands in shared memory after the CTA has exited.
+template <int D>
+__device__ void finish(const DevParams &p, Ctl<D> *ctl) {
+  __syncthreads();
+  if (ctl->abort) {
+    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
+    const long long is = ctl->issued;
+    for (long long e = max(0LL, is - D); e < is; ++e)
+      mbar_wait_bounded(&ctl->full[e % D], static_cast<uint32_t>((e / D) & 1));
+  }
 }
 
 // Does the item's box meet the source stencils' bounding box?
@@ -341,39 +399,53 @@ __device__ __forceinline__ bool item_has_source(const DevParams &p, const Item &
          it.j0 <= p.src_hi[1] && it.k1 > p.src_lo[2] && it.k0 <= p.src_hi[2];
 }
 
+template <int R>
+__device__ __forceinline__ void ctl_init(Ctl<ring_depth(R)> *ctl) {
+  constexpr int D = ring_depth(R);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < D; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], NCW);
+    }
+    ctl->issued = 0;
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
-                                                 const int n) {
+__global__ void __launch_bounds__(NTB, min_ctas(R)) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
+                                                               const int n) {
   constexpr int M = 2 * R, D = ring_depth(R);
   using Pol = HalfE<R>;
   using S = StageE<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-  long long *s_issued = reinterpret_cast<long long *>(bars + D);
-  const int nitems = p.tiles_x * p.tiles_y * p.zchunks;
-  Producer pr{static_cast<int>(blockIdx.x), 0, 0};
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
-    fence_barrier_init();
-    produce<R, Pol>(p, tm, ring, bars, pr, D, nitems, s_issued);
+  Ctl<D> *ctl = reinterpret_cast<Ctl<D> *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
+  ctl_init<R>(ctl);
+  if (threadIdx.x >= NT) {  // producer warp
+    if (threadIdx.x == NT) producer_loop<R, Pol>(p, tm, ring, ctl);
+    finish<D>(p, ctl);
+    return;
   }
   // receiver DTFT of H^{n+1/2} (this launch does not write H)
   if (static_cast<int>(blockIdx.x) < p.rec_blocks)
     receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
-  __syncthreads();
 
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const float amp = __ldg(p.amp + n);
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+  Range rg = cta_range(p);
+  Item it;
   long long ec = 0;  // entries consumed
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const Item it = item_of(p, w);
+  bool ok = true;
+  while (ok && next_item(p, rg, it)) {
     const int i = it.i0 + tx, j = it.j0 + ty;
     const bool in_ij = i < np0 && j < np1;
     const size_t col = static_cast<size_t>(j) * p.pitch + i;
@@ -392,28 +464,26 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_
 
     // z queue: Hx, Hy of this column at planes k-R .. k+R-1
     float qx[M], qy[M];
-    bool ok = true;
 #pragma unroll
     for (int q = 0; q < M - 1; ++q) {
-      ok = wait_entry<D>(bars, ec) && ok;
+      ok = ok && consume_wait<D>(ctl, ec);
       Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
       ++ec;
     }
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-      drain<D>(bars, ec - (M - 1), *s_issued);
-      return;
-    }
-    if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, e0 + Pol::LEAD + D, nitems, s_issued);
+    if (!ok) break;
+    for (long long e = e0; e < e0 + Pol::LEAD; ++e) release<D>(ctl, e);  // planes below k0
 
     for (int k = it.k0; k < it.k1; ++k) {
-      ok = wait_entry<D>(bars, ec);  // queue feed: plane k+R-1
+      if (!consume_wait<D>(ctl, ec)) {  // queue feed: plane k+R-1
+        ok = false;
+        break;
+      }
       Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
       ++ec;
       const long long ek = e0 + Pol::LEAD + (k - it.k0);  // entry of plane k
       const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
       const float *sHz = st + S::HZ, *sHy = st + S::HY, *sHx = st + S::HX;
-      if (ok && in_ij) {
+      if (in_ij) {
         const bool dm_k = k >= R && k <= np2 - 1 - R;
         const int sk = slab_int(k, np2, nb);
         float cz[M];
@@ -472,56 +542,51 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_
           volume_accumulate(p, 5, lin, nint, facH, sHz[(ty + R) * WX + tx + XH]);
         }
       }
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-        drain<D>(bars, ec - 1, *s_issued);
-        return;
-      }
-      // release plane k (and, after the last plane, the item's trailing queue planes)
-      const long long freed = (k + 1 == it.k1) ? ec : ek + 1;
-      if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, freed + D, nitems, s_issued);
+      release<D>(ctl, ek);
 #pragma unroll
       for (int q = 0; q < M - 1; ++q) {
         qx[q] = qx[q + 1];
         qy[q] = qy[q + 1];
       }
     }
+    if (!ok) break;
+    for (long long e = e0 + Pol::LEAD + (it.k1 - it.k0); e < ec; ++e) release<D>(ctl, e);  // trailing
   }
+  finish<D>(p, ctl);
 }
 
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
-                                                 const int n) {
+__global__ void __launch_bounds__(NTB, min_ctas(R)) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
+                                                               const int n) {
   constexpr int M = 2 * R, D = ring_depth(R);
   using Pol = HalfH<R>;
   using S = StageH<R>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-  long long *s_issued = reinterpret_cast<long long *>(bars + D);
-  const int nitems = p.tiles_x * p.tiles_y * p.zchunks;
-  Producer pr{static_cast<int>(blockIdx.x), 0, 0};
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
-    fence_barrier_init();
-    produce<R, Pol>(p, tm, ring, bars, pr, D, nitems, s_issued);
+  Ctl<D> *ctl = reinterpret_cast<Ctl<D> *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
+  ctl_init<R>(ctl);
+  if (threadIdx.x >= NT) {  // producer warp
+    if (threadIdx.x == NT) producer_loop<R, Pol>(p, tm, ring, ctl);
+    finish<D>(p, ctl);
+    return;
   }
   // receiver DTFT of E^{n+1} (this launch does not write E)
   if (static_cast<int>(blockIdx.x) < p.rec_blocks)
     receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
-  __syncthreads();
 
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const float dt_mu = p.dt_mu;
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
+  Range rg = cta_range(p);
+  Item it;
   long long ec = 0;
-  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const Item it = item_of(p, w);
+  bool ok = true;
+  while (ok && next_item(p, rg, it)) {
     const int i = it.i0 + tx, j = it.j0 + ty;
     const bool in_ij = i < np0 && j < np1;
     const size_t col = static_cast<size_t>(j) * p.pitch + i;
@@ -539,28 +604,26 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_
 
     // z queue: Ex, Ey of this column at planes k-R+1 .. k+R
     float qx[M], qy[M];
-    bool ok = true;
 #pragma unroll
     for (int q = 0; q < M - 1; ++q) {
-      ok = wait_entry<D>(bars, ec) && ok;
+      ok = ok && consume_wait<D>(ctl, ec);
       Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
       ++ec;
     }
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-      drain<D>(bars, ec - (M - 1), *s_issued);
-      return;
-    }
-    if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, e0 + Pol::LEAD + D, nitems, s_issued);
+    if (!ok) break;
+    for (long long e = e0; e < e0 + Pol::LEAD; ++e) release<D>(ctl, e);
 
     for (int k = it.k0; k < it.k1; ++k) {
-      ok = wait_entry<D>(bars, ec);  // queue feed: plane k+R
+      if (!consume_wait<D>(ctl, ec)) {  // queue feed: plane k+R
+        ok = false;
+        break;
+      }
       Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
       ++ec;
       const long long ek = e0 + Pol::LEAD + (k - it.k0);
       const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
       const float *sEz = st + S::EZ, *sEy = st + S::EY, *sEx = st + S::EX;
-      if (ok && in_ij) {
+      if (in_ij) {
         const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
         const int sk = slab_half(k, np2, nb);
         float cz[M];
@@ -613,20 +676,17 @@ __global__ void __launch_bounds__(NT, (R <= 2 ? 4 : (R == 3 ? 3 : 2))) k_update_
           volume_accumulate(p, 2, lin, nint, facE, sEz[(ty + R) * WX + tx + XH]);
         }
       }
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-        drain<D>(bars, ec - 1, *s_issued);
-        return;
-      }
-      const long long freed = (k + 1 == it.k1) ? ec : ek + 1;
-      if (threadIdx.x == 0) produce<R, Pol>(p, tm, ring, bars, pr, freed + D, nitems, s_issued);
+      release<D>(ctl, ek);
 #pragma unroll
       for (int q = 0; q < M - 1; ++q) {
         qx[q] = qx[q + 1];
         qy[q] = qy[q + 1];
       }
     }
+    if (!ok) break;
+    for (long long e = e0 + Pol::LEAD + (it.k1 - it.k0); e < ec; ++e) release<D>(ctl, e);
   }
+  finish<D>(p, ctl);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -813,9 +873,9 @@ cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st
   for (int n = 0; n < nt; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R><<<blocks, NT, se, st>>>(p, tE, n);
+    k_update_E<R><<<blocks, NTB, se, st>>>(p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R><<<blocks, NT, sh, st>>>(p, tH, n);
+    k_update_H<R><<<blocks, NTB, sh, st>>>(p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -830,8 +890,8 @@ int resident_ctas(int sms) {
   cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(se));
   cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh));
   int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_E<R>, NT, se);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update_H<R>, NT, sh);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_E<R>, NTB, se);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update_H<R>, NTB, sh);
   return std::max(1, std::min(a, b)) * sms;
 }
 
@@ -1004,15 +1064,11 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     case 3: slots = resident_ctas<3>(sms); break;
     default: slots = resident_ctas<4>(sms); break;
   }
-  const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
-  int kc = static_cast<int>(tiles * p.np[2] / (4LL * slots));
-  kc = std::max(kc, 8);
-  kc = std::min(kc, p.np[2]);
-  p.kchunk = kc;
-  p.zchunks = (p.np[2] + kc - 1) / kc;
-  const long long nitems = tiles * p.zchunks;
-  p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
-  const int blocks = static_cast<int>(std::max<long long>(std::min<long long>(slots, nitems), p.rec_blocks));
+  const long long units = static_cast<long long>(p.tiles_x) * p.tiles_y * p.np[2];
+  p.kchunk = 0;
+  p.zchunks = 0;
+  p.rec_blocks = (s->nrec * 3 + NCW - 1) / NCW;
+  const int blocks = static_cast<int>(std::max<long long>(std::min<long long>(slots, units), p.rec_blocks));
   p.stencil_blocks = blocks;
   // bounding box of the source stencils (lets CTAs far from it skip the test)
   p.src_any = 0;
