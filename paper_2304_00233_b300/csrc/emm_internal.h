@@ -49,7 +49,7 @@ void cpml_axis(const emm_grid *g, int axis, double vmax, double fmax, double dt,
 struct DevParams {
   int np[3];        // padded sizes
   int n[3];         // interior sizes
-  int pitch;        // row pitch (samples) of the field arrays: np[0] rounded up to 4
+  int pitch;        // row pitch (samples) of the field arrays: np[0] rounded up to 32
   size_t plane;     // pitch * np[1]
   int nbe, nb;
   int tiles_x, tiles_y, kchunk, zchunks, stencil_blocks;  // stencil_blocks: CTAs of a launch

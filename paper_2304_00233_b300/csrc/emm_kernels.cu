@@ -21,7 +21,7 @@
 // of every array are in flight while the CTA computes.  The z taps of the two
 // fields differentiated along z sit in a per-thread register queue of 2R
 // planes fed from the ring.  Fields are FP32 with a row pitch rounded up to
-// 4 samples (16-byte TMA strides); the receiver DTFT accumulates in FP64 and
+// 32 samples (rows start on 128-byte lines, TMA strides are 16-byte multiples); the receiver DTFT accumulates in FP64 and
 // the volume DTFT in compensated FP32 (hi + lo pairs).  No device
 // transcendentals: every exp/sin/cos comes from FP64 host tables.
 //
@@ -234,42 +234,40 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised plane stream
 // ---------------------------------------------------------------------------
-// A launch has exactly as many CTAs as fit on the GPU at once.  The
-// (column tile, plane) units of the grid, tile-major with z fastest, are cut
-// into gridDim.x equal contiguous ranges, one per CTA, so every CTA updates
-// the same number of planes.  A range is walked as items: a run of planes
-// [k0, k1) of one tile.  An item needs the planes k0 - LEAD .. k1 + 2R - 2 -
-// LEAD, the leading and trailing ones only to fill the register z queue.
-// Every plane of every item of the CTA is one entry of a FIFO e = 0, 1, ...:
-// entry e lives in ring stage e % D.  Warp NCW (the producer) issues the TMA
-// copies of entry e once the consumers have released entry e - D (empty
-// barrier) and completes it on the full barrier; the NCW consumer warps wait
-// on full, compute, and release entries in FIFO order.  No CTA-wide barrier
-// sits in the loop.
+// A launch has at most as many CTAs as fit on the GPU at once.  Work item w
+// is the column tile w % tiles over the z chunk [k0, k1) of chunk w / tiles;
+// CTA b takes items b, b + G, b + 2G, ... (G = gridDim.x), so the items the
+// CTAs process at the same time are neighbouring tiles of the same chunk and
+// their halo reads meet in L2.  The host picks the chunk length so that every
+// CTA gets the same number of items.  An item needs the planes k0 - LEAD ..
+// k1 + 2R - 2 - LEAD, the leading and trailing ones only to fill the register
+// z queue.  Every plane of every item of the CTA is one entry of a FIFO
+// e = 0, 1, ...: entry e lives in ring stage e % D.  Warp NCW (the producer)
+// issues the TMA copies of entry e once the consumers have released entry
+// e - D (empty barrier) and completes it on the full barrier; the NCW
+// consumer warps wait on full, compute, and release entries in FIFO order.
+// No CTA-wide barrier sits in the loop.
 
 struct Item {
   int i0, j0, k0, k1;
 };
 
 struct Range {
-  long long u, u1;  // next unit, end of this CTA's units
+  int w;  // next work item of this CTA
 };
 
-__device__ __forceinline__ Range cta_range(const DevParams &p) {
-  const long long units = static_cast<long long>(p.tiles_x) * p.tiles_y * p.np[2];
-  return Range{units * blockIdx.x / gridDim.x, units * (blockIdx.x + 1) / gridDim.x};
-}
+__device__ __forceinline__ Range cta_range(const DevParams &) { return Range{static_cast<int>(blockIdx.x)}; }
 
-// Next item of the range (false when the range is exhausted).
+// Next item of this CTA (false when none is left).
 __device__ __forceinline__ bool next_item(const DevParams &p, Range &r, Item &it) {
-  if (r.u >= r.u1) return false;
-  const int np2 = p.np[2];
-  const long long t = r.u / np2;
-  it.k0 = static_cast<int>(r.u - t * np2);
-  it.k1 = static_cast<int>(min(static_cast<long long>(np2), r.u1 - t * np2));
-  it.i0 = static_cast<int>(t % p.tiles_x) * TX;
-  it.j0 = static_cast<int>(t / p.tiles_x) * TY;
-  r.u = t * np2 + it.k1;
+  const int tiles = p.tiles_x * p.tiles_y;
+  if (r.w >= tiles * p.zchunks) return false;
+  const int t = r.w % tiles, c = r.w / tiles;
+  it.i0 = (t % p.tiles_x) * TX;
+  it.j0 = (t / p.tiles_x) * TY;
+  it.k0 = c * p.kchunk;
+  it.k1 = min(it.k0 + p.kchunk, p.np[2]);
+  r.w += gridDim.x;
   return true;
 }
 
@@ -748,7 +746,7 @@ __global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *no
 // ---------------------------------------------------------------------------
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-inline int field_pitch(int np0) { return (np0 + 3) / 4 * 4; }
+inline int field_pitch(int np0) { return (np0 + 31) / 32 * 32; }  // rows start on 128-byte lines
 
 // Byte layout of the device workspace.
 struct Layout {
@@ -1064,11 +1062,27 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     case 3: slots = resident_ctas<3>(sms); break;
     default: slots = resident_ctas<4>(sms); break;
   }
-  const long long units = static_cast<long long>(p.tiles_x) * p.tiles_y * p.np[2];
-  p.kchunk = 0;
-  p.zchunks = 0;
+  // z chunk length: smallest per-CTA work (items per CTA x (chunk + queue
+  // fill)) with at most `slots` CTAs, every CTA taking the same item count
+  const int tiles = p.tiles_x * p.tiles_y;
+  int best_kc = p.np[2], best_cost = 1 << 30;
+  for (int zc = 1; zc <= p.np[2]; ++zc) {
+    const int kc = (p.np[2] + zc - 1) / zc;
+    if ((p.np[2] + kc - 1) / kc != zc) continue;
+    const long long nit = static_cast<long long>(tiles) * zc;
+    const long long q = (nit + slots - 1) / slots;  // items per CTA
+    const int cost = static_cast<int>(q * (kc + 2 * rd));
+    if (cost < best_cost) {
+      best_cost = cost;
+      best_kc = kc;
+    }
+  }
+  p.kchunk = best_kc;
+  p.zchunks = (p.np[2] + best_kc - 1) / best_kc;
+  const long long nitems = static_cast<long long>(tiles) * p.zchunks;
+  const long long q = (nitems + slots - 1) / slots;
   p.rec_blocks = (s->nrec * 3 + NCW - 1) / NCW;
-  const int blocks = static_cast<int>(std::max<long long>(std::min<long long>(slots, units), p.rec_blocks));
+  const int blocks = static_cast<int>(std::max<long long>((nitems + q - 1) / q, p.rec_blocks));
   p.stencil_blocks = blocks;
   // bounding box of the source stencils (lets CTAs far from it skip the test)
   p.src_any = 0;
