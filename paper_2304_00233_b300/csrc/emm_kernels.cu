@@ -13,22 +13,24 @@
 //                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
 //                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
 //
-// Stencil CTAs own a TX x TY tile of (i, j) columns and march z through a
-// chunk of planes.  Every plane the CTA needs is fetched by the Tensor Memory
-// Accelerator: one thread issues cp.async.bulk.tensor copies of the plane's
-// tiles (with the x/y halos the D+/D- rows need) into a ring of D = R + 3
-// shared-memory stages, each completed on its own mbarrier, so several planes
-// of every array are in flight while the CTA computes.  The z taps of the two
-// fields differentiated along z sit in a per-thread register queue of 2R
-// planes fed from the ring.  Fields are FP32 with a row pitch rounded up to
-// 32 samples (rows start on 128-byte lines, TMA strides are 16-byte multiples); the receiver DTFT accumulates in FP64 and
-// the volume DTFT in compensated FP32 (hi + lo pairs).  No device
-// transcendentals: every exp/sin/cos comes from FP64 host tables.
+// Launch shape: the step is bound by HBM bandwidth, and what the memory
+// system needs is many bytes in flight from many CTAs.  A CTA owns a 32 x 8
+// column tile over a short run of ZC planes (one thread per column) and the
+// grid covers the padded volume thousands of CTAs deep.  On entry one thread
+// issues three TMA copies (cp.async.bulk.tensor) that bring the three source
+// fields of the tile, with the x, y and z halos their derivatives need, into
+// shared memory; meanwhile every thread loads its own samples of the updated
+// field and of dt/eps (coalesced 128-byte rows, no reuse) into registers.
+// After the copies land, every tap is a shared-memory read at a fixed offset.
+// Fields are FP32 in arrays whose rows are padded to 32 samples (rows start on
+// 128-byte lines; TMA strides are 16-byte multiples); the receiver DTFT
+// accumulates in FP64 and the volume DTFT in compensated FP32 (hi + lo pairs).
+// No device transcendentals: every exp/sin/cos comes from FP64 host tables.
 //
-// Every mbarrier wait is bounded (1 s of %globaltimer).  A wait that runs out
-// sets the status word to EMM_ETIMEOUT; the CTA then agrees on the abort
-// with __syncthreads_or, drains its own copies in flight (again bounded) and
-// returns, so no kernel can hang the device.
+// The one mbarrier wait of a CTA is bounded (1 s of %globaltimer).  If it
+// runs out the status word is set to EMM_ETIMEOUT, the CTA agrees on the
+// abort with __syncthreads_or, waits (again bounded) for its copies and
+// returns without writing, so no kernel can hang the device.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -47,58 +49,33 @@ namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
 constexpr int TY = 8;   // tile height (y)
-constexpr int NT = TX * TY;  // consumer threads (one per column of the tile)
-constexpr int NCW = NT / 32;   // consumer warps
-constexpr int NTB = NT + 32;   // block: consumers + one producer warp
-constexpr int XH = 4;   // x halo of the TMA boxes (>= R, keeps box x starts 16-byte aligned)
+constexpr int NT = TX * TY;
+constexpr int ZC = 4;   // planes per CTA
+constexpr int XH = 4;   // x halo of the TMA boxes (>= R; keeps box x starts 16-byte aligned)
 constexpr int WX = TX + 2 * XH;
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of one mbarrier wait
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of the mbarrier wait
 
-// Ring stages (>= 2R-1 so an item's queue prologue fits) and resident CTAs
-// per SM; together they keep about four planes per CTA in flight within the
-// 227 KB of shared memory.
-__host__ __device__ constexpr int ring_depth(int R) { return R == 1 ? 5 : (R == 2 ? 6 : (R == 3 ? 6 : 8)); }
-__host__ __device__ constexpr int min_ctas(int R) { return R <= 3 ? 3 : 2; }
-__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }  // floats -> 128 B
+// Resident CTAs per SM the register budget is sized for.
+__host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 4 : 3; }
 
-// Stage layout (floats) of the E launch: Hz [TY+2R][WX], Hy [TY][WX],
-// Hx [TY+2R][TX], E [3][TY][TX], dt/eps [3][TY][TX].
+// Shared-memory tiles of one CTA, for either half-step.  "zf" is the source
+// field with z and y halos (Hx / Ex), "xf" the one with z and x halos
+// (Hy / Ey), "xy" the one with x and y halos (Hz / Ez).
 template <int R>
-struct StageE {
-  static constexpr int HYR = TY + 2 * R;
-  static constexpr int HZ = 0;
-  static constexpr int HY = HZ + round32(HYR * WX);
-  static constexpr int HX = HY + round32(TY * WX);
-  static constexpr int EC = HX + round32(HYR * TX);
-  static constexpr int IE = EC + 3 * TY * TX;
-  static constexpr int FLOATS = IE + 3 * TY * TX;
-  static constexpr unsigned QUEUE_BYTES = 4u * (HYR * TX + TY * WX);  // Hx + Hy tiles only
-  static constexpr unsigned FULL_BYTES = 4u * (HYR * WX + TY * WX + HYR * TX + 6 * TY * TX);
+struct Tiles {
+  static constexpr int ZQ = ZC + 2 * R - 1;  // planes of the z-halo boxes
+  static constexpr int YH = TY + 2 * R;      // rows of the y-halo boxes
+  static constexpr int ZF = ZQ * YH * TX;
+  static constexpr int XF = ZQ * TY * WX;
+  static constexpr int XY = ZC * YH * WX;
+  static constexpr size_t BYTES = static_cast<size_t>(ZF + XF + XY) * 4;
 };
-
-// Stage layout of the H launch: Ez [TY+2R][WX], Ey [TY][WX], Ex [TY+2R][TX], H [3][TY][TX].
 template <int R>
-struct StageH {
-  static constexpr int HYR = TY + 2 * R;
-  static constexpr int EZ = 0;
-  static constexpr int EY = EZ + round32(HYR * WX);
-  static constexpr int EX = EY + round32(TY * WX);
-  static constexpr int HC = EX + round32(HYR * TX);
-  static constexpr int FLOATS = HC + 3 * TY * TX;
-  static constexpr unsigned QUEUE_BYTES = 4u * (HYR * TX + TY * WX);  // Ex + Ey tiles only
-  static constexpr unsigned FULL_BYTES = 4u * (HYR * WX + TY * WX + HYR * TX + 3 * TY * TX);
-};
+constexpr size_t smem_bytes() { return Tiles<R>::BYTES + 144; }  // + alignment pad + mbarrier
 
-template <int R>
-constexpr size_t smem_bytes_E() { return static_cast<size_t>(ring_depth(R)) * StageE<R>::FLOATS * 4 + 256; }
-// (the 256 bytes after the ring hold the full/empty mbarriers and the control words)
-template <int R>
-constexpr size_t smem_bytes_H() { return static_cast<size_t>(ring_depth(R)) * StageH<R>::FLOATS * 4 + 256; }
-
-// Tensor maps of one launch: [0..2] the halo'd sources (z-halo field with a
-// y halo, x-halo field, xy-halo field), [3..5] the updated field, [6..8] dt/eps.
+// Tensor maps of one launch: the three source fields with their boxes.
 struct TmaSet {
-  CUtensorMap m[9];
+  CUtensorMap m[3];
 };
 
 // ---- PTX helpers: mbarrier and TMA ---------------------------------------
@@ -163,11 +140,9 @@ __device__ __forceinline__ size_t psi_at(int a, int s, int i, int j, int k, cons
   return (static_cast<size_t>(s) * np[1] + j) * np[0] + i;
 }
 
-// psi <- b psi + a d ; return d + psi   (Eq. 16-17, kappa = 1)
-__device__ __forceinline__ float cpml(float d, float *psi, size_t idx, const float *tab, int s, int nb,
-                                      bool half) {
-  const float a = tab[(half ? 4 : 0) * nb + s];
-  const float b = tab[(half ? 6 : 2) * nb + s];
+// CPML update of one derivative d (Eq. 16-17, kappa = 1):
+// psi <- b psi + a d, stored back; returns d + psi.
+__device__ __forceinline__ float cpml_step(float d, float *__restrict__ psi, size_t idx, float a, float b) {
   const float v = fmaf(b, psi[idx], a * d);
   psi[idx] = v;
   return d + v;
@@ -222,6 +197,62 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Common CTA prologue: origin of the tile, the TMA copies of the three source
+// fields, and the bounded wait for them.
+// ---------------------------------------------------------------------------
+struct Origin {
+  int i0, j0, k0;
+};
+__device__ __forceinline__ Origin origin_of(const DevParams &p, int b) {
+  return Origin{(b % p.tiles_x) * TX, ((b / p.tiles_x) % p.tiles_y) * TY, (b / (p.tiles_x * p.tiles_y)) * ZC};
+}
+
+// Shared-memory views of the three tiles (see Tiles).
+template <int R>
+struct View {
+  using T = Tiles<R>;
+  const float *s;
+  __device__ float zf(int pz, int y, int x) const { return s[(pz * T::YH + y) * TX + x]; }
+  __device__ float xf(int pz, int y, int x) const { return s[T::ZF + (pz * TY + y) * WX + x]; }
+  __device__ float xy(int pz, int y, int x) const { return s[T::ZF + T::XF + (pz * T::YH + y) * WX + x]; }
+};
+
+// Thread 0: initialise the CTA's mbarrier and issue the three copies.  The
+// z-halo boxes start `lead` planes from k0 (-R for D-, -R+1 for D+).
+template <int R>
+__device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t *bar, const Origin &o, int lead) {
+  using T = Tiles<R>;
+  mbar_init(bar, 1);
+  fence_barrier_init();
+  mbar_expect_tx(bar, static_cast<uint32_t>(T::BYTES));
+  tma_load_3d(s, &tm.m[0], bar, o.i0, o.j0 - R, o.k0 + lead);
+  tma_load_3d(s + T::ZF, &tm.m[1], bar, o.i0 - XH, o.j0, o.k0 + lead);
+  tma_load_3d(s + T::ZF + T::XF, &tm.m[2], bar, o.i0 - XH, o.j0 - R, o.k0);
+}
+
+// All threads: wait for the copies.  False (after setting the status word
+// and draining the copies, both bounded) if the wait ran out anywhere.
+__device__ __forceinline__ bool tiles_ready(const DevParams &p, uint64_t *bar) {
+  __syncthreads();  // the barrier is initialised
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(p.status, EMM_ETIMEOUT);
+      mbar_wait_bounded(bar, 0);
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float *smem_tiles(unsigned char *raw) {
+  const uint32_t pad = (128u - (smem_u32(raw) & 127u)) & 127u;
+  return reinterpret_cast<float *>(raw + pad);
+}
+
 template <int R>
 __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, int j, int k, float amp,
                                             float &curl) {
@@ -232,459 +263,239 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 }
 
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised plane stream
-// ---------------------------------------------------------------------------
-// A launch has at most as many CTAs as fit on the GPU at once.  Work item w
-// is the column tile w % tiles over the z chunk [k0, k1) of chunk w / tiles;
-// CTA b takes items b, b + G, b + 2G, ... (G = gridDim.x), so the items the
-// CTAs process at the same time are neighbouring tiles of the same chunk and
-// their halo reads meet in L2.  The host picks the chunk length so that every
-// CTA gets the same number of items.  An item needs the planes k0 - LEAD ..
-// k1 + 2R - 2 - LEAD, the leading and trailing ones only to fill the register
-// z queue.  Every plane of every item of the CTA is one entry of a FIFO
-// e = 0, 1, ...: entry e lives in ring stage e % D.  Warp NCW (the producer)
-// issues the TMA copies of entry e once the consumers have released entry
-// e - D (empty barrier) and completes it on the full barrier; the NCW
-// consumer warps wait on full, compute, and release entries in FIFO order.
-// No CTA-wide barrier sits in the loop.
-
-struct Item {
-  int i0, j0, k0, k1;
-};
-
-struct Range {
-  int w;  // next work item of this CTA
-};
-
-__device__ __forceinline__ Range cta_range(const DevParams &) { return Range{static_cast<int>(blockIdx.x)}; }
-
-// Next item of this CTA (false when none is left).
-__device__ __forceinline__ bool next_item(const DevParams &p, Range &r, Item &it) {
-  const int tiles = p.tiles_x * p.tiles_y;
-  if (r.w >= tiles * p.zchunks) return false;
-  const int t = r.w % tiles, c = r.w / tiles;
-  it.i0 = (t % p.tiles_x) * TX;
-  it.j0 = (t / p.tiles_x) * TY;
-  it.k0 = c * p.kchunk;
-  it.k1 = min(it.k0 + p.kchunk, p.np[2]);
-  r.w += gridDim.x;
-  return true;
-}
-
-// E launch: copies of one plane entry; Hx (y halo) and Hy (x halo) feed the z
-// queue, the rest only matter for planes the item updates ("full").
-template <int R>
-struct HalfE {
-  using S = StageE<R>;
-  static constexpr int LEAD = R;  // queue planes below k0
-  __device__ static void issue(const TmaSet &tm, float *st, uint64_t *bar, const Item &it, int pl) {
-    const bool full = pl >= it.k0 && pl < it.k1;
-    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
-    tma_load_3d(st + S::HX, &tm.m[0], bar, it.i0, it.j0 - R, pl);
-    tma_load_3d(st + S::HY, &tm.m[1], bar, it.i0 - XH, it.j0, pl);
-    if (full) {
-      tma_load_3d(st + S::HZ, &tm.m[2], bar, it.i0 - XH, it.j0 - R, pl);
-      for (int c = 0; c < 3; ++c) {
-        tma_load_3d(st + S::EC + c * TY * TX, &tm.m[3 + c], bar, it.i0, it.j0, pl);
-        tma_load_3d(st + S::IE + c * TY * TX, &tm.m[6 + c], bar, it.i0, it.j0, pl);
-      }
-    }
-  }
-  __device__ static void queue_vals(const float *st, int tx, int ty, float &a, float &b) {
-    a = st[S::HX + (ty + R) * TX + tx];
-    b = st[S::HY + ty * WX + tx + XH];
-  }
-};
-
-// H launch: Ex (y halo) and Ey (x halo) feed the z queue.
-template <int R>
-struct HalfH {
-  using S = StageH<R>;
-  static constexpr int LEAD = R - 1;
-  __device__ static void issue(const TmaSet &tm, float *st, uint64_t *bar, const Item &it, int pl) {
-    const bool full = pl >= it.k0 && pl < it.k1;
-    mbar_expect_tx(bar, full ? S::FULL_BYTES : S::QUEUE_BYTES);
-    tma_load_3d(st + S::EX, &tm.m[0], bar, it.i0, it.j0 - R, pl);
-    tma_load_3d(st + S::EY, &tm.m[1], bar, it.i0 - XH, it.j0, pl);
-    if (full) {
-      tma_load_3d(st + S::EZ, &tm.m[2], bar, it.i0 - XH, it.j0 - R, pl);
-      for (int c = 0; c < 3; ++c) tma_load_3d(st + S::HC + c * TY * TX, &tm.m[3 + c], bar, it.i0, it.j0, pl);
-    }
-  }
-  __device__ static void queue_vals(const float *st, int tx, int ty, float &a, float &b) {
-    a = st[S::EX + (ty + R) * TX + tx];
-    b = st[S::EY + ty * WX + tx + XH];
-  }
-};
-
-// Shared-memory control block after the ring.
-template <int D>
-struct Ctl {
-  uint64_t full[D];
-  uint64_t empty[D];
-  long long issued;  // entries issued by the producer
-  int abort;         // a bounded wait ran out somewhere in the CTA
-};
-
-// Bounded wait that also gives up when another warp has flagged an abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0 && (*abort || global_ns() - t0 > kWaitNs)) return false;
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Producer warp, lane 0: issue every entry of the CTA's range in order.
-template <int R, class Pol>
-__device__ void producer_loop(const DevParams &p, const TmaSet &tm, float *ring, Ctl<ring_depth(R)> *ctl) {
-  constexpr int D = ring_depth(R), M = 2 * R;
-  Range r = cta_range(p);
-  Item it;
-  long long e = 0;
-  while (next_item(p, r, it)) {
-    const int cnt = (it.k1 - it.k0) + M - 1;
-    for (int q = 0; q < cnt; ++q, ++e) {
-      const int s = static_cast<int>(e % D);
-      if (e >= D && !wait_or_abort(&ctl->empty[s], static_cast<uint32_t>((e / D - 1) & 1), &ctl->abort)) {
-        ctl->abort = 1;
-        atomicExch(p.status, EMM_ETIMEOUT);
-        return;
-      }
-      Pol::issue(tm, ring + static_cast<size_t>(s) * Pol::S::FLOATS, &ctl->full[s], it, it.k0 - Pol::LEAD + q);
-      *reinterpret_cast<volatile long long *>(&ctl->issued) = e + 1;
-    }
-  }
-}
-
-// Consumer side: wait for entry e to land (false on timeout/abort).
-template <int D>
-__device__ __forceinline__ bool consume_wait(Ctl<D> *ctl, long long e) {
-  if (wait_or_abort(&ctl->full[e % D], static_cast<uint32_t>((e / D) & 1), &ctl->abort)) return true;
-  ctl->abort = 1;
-  return false;
-}
-
-// Consumer side: this warp is done with entry e.
-template <int D>
-__device__ __forceinline__ void release(Ctl<D> *ctl, long long e) {
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(&ctl->empty[e % D]);
-}
-
-// End of the kernel: if anything aborted, wait (bounded) for the copies that
-// may still be in flight (only the last D issued entries can be) so no TMA
-// write lands in shared memory after the CTA has exited.
-template <int D>
-__device__ void finish(const DevParams &p, Ctl<D> *ctl) {
-  __syncthreads();
-  if (ctl->abort) {
-    if (threadIdx.x == 0) atomicExch(p.status, EMM_ETIMEOUT);
-    const long long is = ctl->issued;
-    for (long long e = max(0LL, is - D); e < is; ++e)
-      mbar_wait_bounded(&ctl->full[e % D], static_cast<uint32_t>((e / D) & 1));
-  }
-}
-
-// Does the item's box meet the source stencils' bounding box?
-__device__ __forceinline__ bool item_has_source(const DevParams &p, const Item &it) {
-  return p.src_any && it.i0 + TX > p.src_lo[0] && it.i0 <= p.src_hi[0] && it.j0 + TY > p.src_lo[1] &&
-         it.j0 <= p.src_hi[1] && it.k1 > p.src_lo[2] && it.k0 <= p.src_hi[2];
-}
-
-template <int R>
-__device__ __forceinline__ void ctl_init(Ctl<ring_depth(R)> *ctl) {
-  constexpr int D = ring_depth(R);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < D; ++s) {
-      mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], NCW);
-    }
-    ctl->issued = 0;
-    ctl->abort = 0;
-    fence_barrier_init();
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NTB, min_ctas(R)) k_update_E(const DevParams p, const __grid_constant__ TmaSet tm,
-                                                               const int n) {
-  constexpr int M = 2 * R, D = ring_depth(R);
-  using Pol = HalfE<R>;
-  using S = StageE<R>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  float *ring = reinterpret_cast<float *>(smem_raw);
-  Ctl<D> *ctl = reinterpret_cast<Ctl<D> *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-  ctl_init<R>(ctl);
-  if (threadIdx.x >= NT) {  // producer warp
-    if (threadIdx.x == NT) producer_loop<R, Pol>(p, tm, ring, ctl);
-    finish<D>(p, ctl);
+__global__ void __launch_bounds__(NT, min_ctas(R))
+    k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  constexpr int M = 2 * R;
+  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
+    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
-  // receiver DTFT of H^{n+1/2} (this launch does not write H)
-  if (static_cast<int>(blockIdx.x) < p.rec_blocks)
-    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
+  extern __shared__ unsigned char smem_raw[];
+  float *s = smem_tiles(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::BYTES / 4);
+  const Origin o = origin_of(p, blockIdx.x);
+  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
-  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = o.i0 + tx, j = o.j0 + ty;
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const bool in_ij = i < np0 && j < np1;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+  // this thread's own samples, loaded while the copies are in flight
+  float e[3][ZC], w[3][ZC];
+#pragma unroll
+  for (int c = 0; c < ZC; ++c) {
+    const bool ok = in_ij && o.k0 + c < np2;
+    const size_t id = static_cast<size_t>(o.k0 + c) * p.plane + col;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      e[a][c] = ok ? p.E[a][id] : 0.f;
+      w[a][c] = ok ? __ldg(p.ie[a] + id) : 0.f;
+    }
+  }
+  if (!tiles_ready(p, bar) || !in_ij) return;
+
+  const View<R> v{s};
+  const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
+  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
+  float cx[M], cy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
+    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
+  }
   const float amp = __ldg(p.amp + n);
+  const int ii = i - p.nbe, jj = j - p.nbe;
+  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
-  Range rg = cta_range(p);
-  Item it;
-  long long ec = 0;  // entries consumed
-  bool ok = true;
-  while (ok && next_item(p, rg, it)) {
-    const int i = it.i0 + tx, j = it.j0 + ty;
-    const bool in_ij = i < np0 && j < np1;
-    const size_t col = static_cast<size_t>(j) * p.pitch + i;
-    const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
-    const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
-    const bool src = item_has_source(p, it);
-    float cx[M], cy[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-      cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
-      cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
-    }
-    const int ii = i - p.nbe, jj = j - p.nbe;
-    const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-    const long long e0 = ec;
 
-    // z queue: Hx, Hy of this column at planes k-R .. k+R-1
-    float qx[M], qy[M];
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      ok = ok && consume_wait<D>(ctl, ec);
-      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
-      ++ec;
+  for (int c = 0; c < ZC; ++c) {
+    const int k = o.k0 + c;
+    if (k >= np2) break;
+    const size_t id = static_cast<size_t>(k) * p.plane + col;
+    const bool dm_k = k >= R && k <= np2 - 1 - R;
+    const int sk = slab_int(k, np2, nb);
+    float cz[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
+    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+    if (i <= np0 - 2 && dm_j && dm_k) {
+      float dy = 0.f, dz = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dy = fmaf(cy[q], v.xy(c, ty + q, tx + XH), dy);
+        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
+      }
+      if (sj >= 0)
+        dy = cpml_step(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][sj], p.pml[1][2 * nb + sj]);
+      if (sk >= 0)
+        dz = cpml_step(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][sk], p.pml[2][2 * nb + sk]);
+      float curl = dy - dz;
+      source_term<R>(p, 0, i, j, k, amp, curl);
+      p.E[0][id] = fmaf(w[0][c], curl, e[0][c]);
     }
-    if (!ok) break;
-    for (long long e = e0; e < e0 + Pol::LEAD; ++e) release<D>(ctl, e);  // planes below k0
-
-    for (int k = it.k0; k < it.k1; ++k) {
-      if (!consume_wait<D>(ctl, ec)) {  // queue feed: plane k+R-1
-        ok = false;
-        break;
+    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+    if (j <= np1 - 2 && dm_i && dm_k) {
+      float dz = 0.f, dx = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
+        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + q), dx);
       }
-      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
-      ++ec;
-      const long long ek = e0 + Pol::LEAD + (k - it.k0);  // entry of plane k
-      const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
-      const float *sHz = st + S::HZ, *sHy = st + S::HY, *sHx = st + S::HX;
-      if (in_ij) {
-        const bool dm_k = k >= R && k <= np2 - 1 - R;
-        const int sk = slab_int(k, np2, nb);
-        float cz[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
-        const size_t id = k * p.plane + col;
-        const int e = ty * TX + tx;
-        // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-        if (i <= np0 - 2 && dm_j && dm_k) {
-          float dy = 0.f, dz = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dy = fmaf(cy[q], sHz[(ty + q) * WX + tx + XH], dy);
-            dz = fmaf(cz[q], qy[q], dz);
-          }
-          if (sj >= 0) dy = cpml(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-          if (sk >= 0) dz = cpml(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-          float curl = dy - dz;
-          if (src) source_term<R>(p, 0, i, j, k, amp, curl);
-          p.E[0][id] = fmaf(st[S::IE + e], curl, st[S::EC + e]);
-        }
-        // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-        if (j <= np1 - 2 && dm_i && dm_k) {
-          float dz = 0.f, dx = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dz = fmaf(cz[q], qx[q], dz);
-            dx = fmaf(cx[q], sHz[(ty + R) * WX + tx + XH - R + q], dx);
-          }
-          if (sk >= 0) dz = cpml(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, false);
-          if (si >= 0) dx = cpml(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-          float curl = dz - dx;
-          if (src) source_term<R>(p, 1, i, j, k, amp, curl);
-          p.E[1][id] = fmaf(st[S::IE + TY * TX + e], curl, st[S::EC + TY * TX + e]);
-        }
-        // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-        if (k <= np2 - 2 && dm_i && dm_j) {
-          float dx = 0.f, dy = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dx = fmaf(cx[q], sHy[ty * WX + tx + XH - R + q], dx);
-            dy = fmaf(cy[q], sHx[(ty + q) * TX + tx], dy);
-          }
-          if (si >= 0) dx = cpml(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, false);
-          if (sj >= 0) dy = cpml(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, false);
-          float curl = dx - dy;
-          if (src) source_term<R>(p, 2, i, j, k, amp, curl);
-          p.E[2][id] = fmaf(st[S::IE + 2 * TY * TX + e], curl, st[S::EC + 2 * TY * TX + e]);
-        }
-        // volume DTFT of H^{n+1/2}
-        const int kk = k - p.nbe;
-        if (int_ij && kk >= 0 && kk < p.n[2]) {
-          const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-          volume_accumulate(p, 3, lin, nint, facH, qx[R]);
-          volume_accumulate(p, 4, lin, nint, facH, qy[R]);
-          volume_accumulate(p, 5, lin, nint, facH, sHz[(ty + R) * WX + tx + XH]);
-        }
-      }
-      release<D>(ctl, ek);
-#pragma unroll
-      for (int q = 0; q < M - 1; ++q) {
-        qx[q] = qx[q + 1];
-        qy[q] = qy[q + 1];
-      }
+      if (sk >= 0)
+        dz = cpml_step(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][sk], p.pml[2][2 * nb + sk]);
+      if (si >= 0)
+        dx = cpml_step(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][si], p.pml[0][2 * nb + si]);
+      float curl = dz - dx;
+      source_term<R>(p, 1, i, j, k, amp, curl);
+      p.E[1][id] = fmaf(w[1][c], curl, e[1][c]);
     }
-    if (!ok) break;
-    for (long long e = e0 + Pol::LEAD + (it.k1 - it.k0); e < ec; ++e) release<D>(ctl, e);  // trailing
+    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+    if (dm_i && dm_j && k <= np2 - 2) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dx = fmaf(cx[q], v.xf(c + R, ty, tx + XH - R + q), dx);
+        dy = fmaf(cy[q], v.zf(c + R, ty + q, tx), dy);
+      }
+      if (si >= 0)
+        dx = cpml_step(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][si], p.pml[0][2 * nb + si]);
+      if (sj >= 0)
+        dy = cpml_step(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][sj], p.pml[1][2 * nb + sj]);
+      float curl = dx - dy;
+      source_term<R>(p, 2, i, j, k, amp, curl);
+      p.E[2][id] = fmaf(w[2][c], curl, e[2][c]);
+    }
+    // volume DTFT of H^{n+1/2}
+    const int kk = k - p.nbe;
+    if (int_ij && kk >= 0 && kk < p.n[2]) {
+      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+      volume_accumulate(p, 3, lin, nint, facH, v.zf(c + R, ty + R, tx));
+      volume_accumulate(p, 4, lin, nint, facH, v.xf(c + R, ty, tx + XH));
+      volume_accumulate(p, 5, lin, nint, facH, v.xy(c, ty + R, tx + XH));
+    }
   }
-  finish<D>(p, ctl);
 }
 
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(NTB, min_ctas(R)) k_update_H(const DevParams p, const __grid_constant__ TmaSet tm,
-                                                               const int n) {
-  constexpr int M = 2 * R, D = ring_depth(R);
-  using Pol = HalfH<R>;
-  using S = StageH<R>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  float *ring = reinterpret_cast<float *>(smem_raw);
-  Ctl<D> *ctl = reinterpret_cast<Ctl<D> *>(smem_raw + static_cast<size_t>(D) * S::FLOATS * 4);
-  ctl_init<R>(ctl);
-  if (threadIdx.x >= NT) {  // producer warp
-    if (threadIdx.x == NT) producer_loop<R, Pol>(p, tm, ring, ctl);
-    finish<D>(p, ctl);
+__global__ void __launch_bounds__(NT, min_ctas(R))
+    k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  constexpr int M = 2 * R;
+  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
+    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
   }
-  // receiver DTFT of E^{n+1} (this launch does not write E)
-  if (static_cast<int>(blockIdx.x) < p.rec_blocks)
-    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x);
+  extern __shared__ unsigned char smem_raw[];
+  float *s = smem_tiles(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::BYTES / 4);
+  const Origin o = origin_of(p, blockIdx.x);
+  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
 
-  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = o.i0 + tx, j = o.j0 + ty;
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const bool in_ij = i < np0 && j < np1;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+  float h[3][ZC];
+#pragma unroll
+  for (int c = 0; c < ZC; ++c) {
+    const bool ok = in_ij && o.k0 + c < np2;
+    const size_t id = static_cast<size_t>(o.k0 + c) * p.plane + col;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h[a][c] = ok ? p.H[a][id] : 0.f;
+  }
+  if (!tiles_ready(p, bar) || !in_ij) return;
+
+  const View<R> v{s};
+  const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
+  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
+  float cx[M], cy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
+    cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
+  }
   const float dt_mu = p.dt_mu;
+  const int ii = i - p.nbe, jj = j - p.nbe;
+  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
-  Range rg = cta_range(p);
-  Item it;
-  long long ec = 0;
-  bool ok = true;
-  while (ok && next_item(p, rg, it)) {
-    const int i = it.i0 + tx, j = it.j0 + ty;
-    const bool in_ij = i < np0 && j < np1;
-    const size_t col = static_cast<size_t>(j) * p.pitch + i;
-    const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
-    const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
-    float cx[M], cy[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-      cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
-      cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
-    }
-    const int ii = i - p.nbe, jj = j - p.nbe;
-    const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-    const long long e0 = ec;
 
-    // z queue: Ex, Ey of this column at planes k-R+1 .. k+R
-    float qx[M], qy[M];
 #pragma unroll
-    for (int q = 0; q < M - 1; ++q) {
-      ok = ok && consume_wait<D>(ctl, ec);
-      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[q], qy[q]);
-      ++ec;
+  for (int c = 0; c < ZC; ++c) {
+    const int k = o.k0 + c;
+    if (k >= np2) break;
+    const size_t id = static_cast<size_t>(k) * p.plane + col;
+    const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
+    const int sk = slab_half(k, np2, nb);
+    float cz[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
+    // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+    if (dp_j && dp_k) {
+      float dy = 0.f, dz = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dy = fmaf(cy[q], v.xy(c, ty + q + 1, tx + XH), dy);
+        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
+      }
+      if (sj >= 0)
+        dy = cpml_step(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj],
+                       p.pml[1][6 * nb + sj]);
+      if (sk >= 0)
+        dz = cpml_step(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk],
+                       p.pml[2][6 * nb + sk]);
+      p.H[0][id] = fmaf(-dt_mu, dy - dz, h[0][c]);
     }
-    if (!ok) break;
-    for (long long e = e0; e < e0 + Pol::LEAD; ++e) release<D>(ctl, e);
-
-    for (int k = it.k0; k < it.k1; ++k) {
-      if (!consume_wait<D>(ctl, ec)) {  // queue feed: plane k+R
-        ok = false;
-        break;
+    // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+    if (dp_i && dp_k) {
+      float dz = 0.f, dx = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
+        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + 1 + q), dx);
       }
-      Pol::queue_vals(ring + static_cast<size_t>(ec % D) * S::FLOATS, tx, ty, qx[M - 1], qy[M - 1]);
-      ++ec;
-      const long long ek = e0 + Pol::LEAD + (k - it.k0);
-      const float *st = ring + static_cast<size_t>(ek % D) * S::FLOATS;
-      const float *sEz = st + S::EZ, *sEy = st + S::EY, *sEx = st + S::EX;
-      if (in_ij) {
-        const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
-        const int sk = slab_half(k, np2, nb);
-        float cz[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
-        const size_t id = k * p.plane + col;
-        const int e = ty * TX + tx;
-        // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-        if (dp_j && dp_k) {
-          float dy = 0.f, dz = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dy = fmaf(cy[q], sEz[(ty + 1 + q) * WX + tx + XH], dy);
-            dz = fmaf(cz[q], qy[q], dz);
-          }
-          if (sj >= 0) dy = cpml(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-          if (sk >= 0) dz = cpml(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-          p.H[0][id] = fmaf(-dt_mu, dy - dz, st[S::HC + e]);
-        }
-        // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-        if (dp_i && dp_k) {
-          float dz = 0.f, dx = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dz = fmaf(cz[q], qx[q], dz);
-            dx = fmaf(cx[q], sEz[(ty + R) * WX + tx + XH - R + 1 + q], dx);
-          }
-          if (sk >= 0) dz = cpml(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2], sk, nb, true);
-          if (si >= 0) dx = cpml(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-          p.H[1][id] = fmaf(-dt_mu, dz - dx, st[S::HC + TY * TX + e]);
-        }
-        // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-        if (dp_i && dp_j) {
-          float dx = 0.f, dy = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            dx = fmaf(cx[q], sEy[ty * WX + tx + XH - R + 1 + q], dx);
-            dy = fmaf(cy[q], sEx[(ty + 1 + q) * TX + tx], dy);
-          }
-          if (si >= 0) dx = cpml(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0], si, nb, true);
-          if (sj >= 0) dy = cpml(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1], sj, nb, true);
-          p.H[2][id] = fmaf(-dt_mu, dx - dy, st[S::HC + 2 * TY * TX + e]);
-        }
-        // volume DTFT of E^{n+1}
-        const int kk = k - p.nbe;
-        if (int_ij && kk >= 0 && kk < p.n[2]) {
-          const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-          volume_accumulate(p, 0, lin, nint, facE, qx[R - 1]);
-          volume_accumulate(p, 1, lin, nint, facE, qy[R - 1]);
-          volume_accumulate(p, 2, lin, nint, facE, sEz[(ty + R) * WX + tx + XH]);
-        }
-      }
-      release<D>(ctl, ek);
-#pragma unroll
-      for (int q = 0; q < M - 1; ++q) {
-        qx[q] = qx[q + 1];
-        qy[q] = qy[q + 1];
-      }
+      if (sk >= 0)
+        dz = cpml_step(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk],
+                       p.pml[2][6 * nb + sk]);
+      if (si >= 0)
+        dx = cpml_step(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si],
+                       p.pml[0][6 * nb + si]);
+      p.H[1][id] = fmaf(-dt_mu, dz - dx, h[1][c]);
     }
-    if (!ok) break;
-    for (long long e = e0 + Pol::LEAD + (it.k1 - it.k0); e < ec; ++e) release<D>(ctl, e);
+    // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+    if (dp_i && dp_j) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dx = fmaf(cx[q], v.xf(c + R - 1, ty, tx + XH - R + 1 + q), dx);
+        dy = fmaf(cy[q], v.zf(c + R - 1, ty + q + 1, tx), dy);
+      }
+      if (si >= 0)
+        dx = cpml_step(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si],
+                       p.pml[0][6 * nb + si]);
+      if (sj >= 0)
+        dy = cpml_step(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj],
+                       p.pml[1][6 * nb + sj]);
+      p.H[2][id] = fmaf(-dt_mu, dx - dy, h[2][c]);
+    }
+    // volume DTFT of E^{n+1}
+    const int kk = k - p.nbe;
+    if (int_ij && kk >= 0 && kk < p.n[2]) {
+      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+      volume_accumulate(p, 0, lin, nint, facE, v.zf(c + R - 1, ty + R, tx));
+      volume_accumulate(p, 1, lin, nint, facE, v.xf(c + R - 1, ty, tx + XH));
+      volume_accumulate(p, 2, lin, nint, facE, v.xy(c, ty + R, tx + XH));
+    }
   }
-  finish<D>(p, ctl);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -693,19 +504,23 @@ __global__ void __launch_bounds__(NTB, min_ctas(R)) k_update_H(const DevParams p
 __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie1, float *ie2, int n0,
                           int n1, int n2, int np0, int np1, int np2, int pitch, int nbe, double two_w0_dt,
                           double sigma_min, int *status) {
-  const size_t cells = static_cast<size_t>(np0) * np1 * np2;
+  const size_t cells = static_cast<size_t>(pitch) * np1 * np2;  // including the row padding
   const size_t nint = static_cast<size_t>(n0) * n1 * n2;
   float *ie[3] = {ie0, ie1, ie2};
   for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < 3 * cells;
        t += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int c = static_cast<int>(t / cells);
     const size_t r = t % cells;
-    const int i = static_cast<int>(r % np0), j = static_cast<int>((r / np0) % np1),
-              k = static_cast<int>(r / (static_cast<size_t>(np0) * np1));
+    const int i = static_cast<int>(r % pitch), j = static_cast<int>((r / pitch) % np1),
+              k = static_cast<int>(r / (static_cast<size_t>(pitch) * np1));
+    if (i >= np0) {  // row padding: defined zeros (read by the stage copies, never used)
+      ie[c][r] = 0.f;
+      continue;
+    }
     const int a = min(max(i - nbe, 0), n0 - 1), b = min(max(j - nbe, 0), n1 - 1),
               cc = min(max(k - nbe, 0), n2 - 1);
     const float s = sigma[c * nint + (static_cast<size_t>(cc) * n1 + b) * n0 + a];
-    const size_t o = (static_cast<size_t>(k) * np1 + j) * pitch + i;
+    const size_t o = r;
     if (!(s > 0.f) || !isfinite(s) || static_cast<double>(s) < sigma_min) {
       atomicExch(status, EMM_EDEVICE);
       ie[c][o] = 0.f;
@@ -826,19 +641,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D FP32 tensor [np2][np1][pitch] (dims np0 x np1 x np2), box bx x by x 1.
-bool make_map(CUtensorMap *map, const float *base, const DevParams &p, int bx, int by) {
+// 3-D FP32 tensor [np2][np1][pitch] (dims np0 x np1 x np2), box bx x by x bz.
+bool make_map(CUtensorMap *map, const float *base, const DevParams &p, int bx, int by, int bz) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(p.np[0]), static_cast<cuuint64_t>(p.np[1]),
                               static_cast<cuuint64_t>(p.np[2])};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(p.pitch) * 4,
-                                 static_cast<cuuint64_t>(p.pitch) * p.np[1] * 4};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by), 1};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(p.pitch) * 4, static_cast<cuuint64_t>(p.plane) * 4};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by),
+                             static_cast<cuuint32_t>(bz)};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The boxes of the three source fields (see Tiles).
+template <int R>
+bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
+  using T = Tiles<R>;
+  return make_map(&t->m[0], F[0], p, TX, T::YH, T::ZQ) && make_map(&t->m[1], F[1], p, WX, TY, T::ZQ) &&
+         make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
 // Optional per-launch timing: events before/after the E and H launches of
@@ -851,46 +674,26 @@ struct StepEvents {
 template <int R>
 cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
-  // E launch: Hx (y halo), Hy (x halo), Hz (x and y halo), E, dt/eps
-  bool ok = make_map(&tE.m[0], p.H[0], p, TX, TY + 2 * R) && make_map(&tE.m[1], p.H[1], p, WX, TY) &&
-            make_map(&tE.m[2], p.H[2], p, WX, TY + 2 * R);
-  for (int c = 0; c < 3 && ok; ++c)
-    ok = make_map(&tE.m[3 + c], p.E[c], p, TX, TY) && make_map(&tE.m[6 + c], p.ie[c], p, TX, TY);
-  // H launch: Ex (y halo), Ey (x halo), Ez (x and y halo), H
-  ok = ok && make_map(&tH.m[0], p.E[0], p, TX, TY + 2 * R) && make_map(&tH.m[1], p.E[1], p, WX, TY) &&
-       make_map(&tH.m[2], p.E[2], p, WX, TY + 2 * R);
-  for (int c = 0; c < 3 && ok; ++c) ok = make_map(&tH.m[3 + c], p.H[c], p, TX, TY);
-  if (!ok) return cudaErrorInvalidValue;
-  const size_t se = smem_bytes_E<R>(), sh = smem_bytes_H<R>();
+  if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
+  const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(se));
+      cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh));
+    e = cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   size_t used = 0;
   for (int n = 0; n < nt; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R><<<blocks, NTB, se, st>>>(p, tE, n);
+    k_update_E<R><<<blocks, NT, sb, st>>>(p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R><<<blocks, NTB, sh, st>>>(p, tH, n);
+    k_update_H<R><<<blocks, NT, sb, st>>>(p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
     }
   }
   return cudaGetLastError();
-}
-
-template <int R>
-int resident_ctas(int sms) {
-  const size_t se = smem_bytes_E<R>(), sh = smem_bytes_H<R>();
-  cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(se));
-  cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh));
-  int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_E<R>, NTB, se);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update_H<R>, NTB, sh);
-  return std::max(1, std::min(a, b)) * sms;
 }
 
 int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
@@ -1046,8 +849,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
-  // launch shape: one resident wave of persistent CTAs walking (tile, z-chunk)
-  // work items; the chunk length gives about four items per CTA
+  // launch shape: TX x TY column tiles times runs of ZC planes, then the
+  // receiver CTAs (one warp per receiver component)
   p.tiles_x = (p.np[0] + TX - 1) / TX;
   p.tiles_y = (p.np[1] + TY - 1) / TY;
   int sms = 148;
@@ -1055,35 +858,11 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  int slots = sms;
-  switch (rd) {
-    case 1: slots = resident_ctas<1>(sms); break;
-    case 2: slots = resident_ctas<2>(sms); break;
-    case 3: slots = resident_ctas<3>(sms); break;
-    default: slots = resident_ctas<4>(sms); break;
-  }
-  // z chunk length: smallest per-CTA work (items per CTA x (chunk + queue
-  // fill)) with at most `slots` CTAs, every CTA taking the same item count
-  const int tiles = p.tiles_x * p.tiles_y;
-  int best_kc = p.np[2], best_cost = 1 << 30;
-  for (int zc = 1; zc <= p.np[2]; ++zc) {
-    const int kc = (p.np[2] + zc - 1) / zc;
-    if ((p.np[2] + kc - 1) / kc != zc) continue;
-    const long long nit = static_cast<long long>(tiles) * zc;
-    const long long q = (nit + slots - 1) / slots;  // items per CTA
-    const int cost = static_cast<int>(q * (kc + 2 * rd));
-    if (cost < best_cost) {
-      best_cost = cost;
-      best_kc = kc;
-    }
-  }
-  p.kchunk = best_kc;
-  p.zchunks = (p.np[2] + best_kc - 1) / best_kc;
-  const long long nitems = static_cast<long long>(tiles) * p.zchunks;
-  const long long q = (nitems + slots - 1) / slots;
-  p.rec_blocks = (s->nrec * 3 + NCW - 1) / NCW;
-  const int blocks = static_cast<int>(std::max<long long>((nitems + q - 1) / q, p.rec_blocks));
-  p.stencil_blocks = blocks;
+  p.kchunk = ZC;
+  p.zchunks = (p.np[2] + ZC - 1) / ZC;
+  p.stencil_blocks = p.tiles_x * p.tiles_y * p.zchunks;
+  p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
+  const int blocks = p.stencil_blocks + p.rec_blocks;
   // bounding box of the source stencils (lets CTAs far from it skip the test)
   p.src_any = 0;
   for (int a = 0; a < 3; ++a) {
