@@ -56,7 +56,7 @@ constexpr int WX = TX + 2 * XH;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of the mbarrier wait
 
 // Resident CTAs per SM the register budget is sized for.
-__host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 4 : 3; }
+__host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 3 : 2; }
 
 // Shared-memory tiles of one CTA, for either half-step.  "zf" is the source
 // field with z and y halos (Hx / Ex), "xf" the one with z and x halos
@@ -68,10 +68,12 @@ struct Tiles {
   static constexpr int ZF = ZQ * YH * TX;
   static constexpr int XF = ZQ * TY * WX;
   static constexpr int XY = ZC * YH * WX;
-  static constexpr size_t BYTES = static_cast<size_t>(ZF + XF + XY) * 4;
+  static constexpr size_t BYTES = static_cast<size_t>(ZF + XF + XY) * 4;  // the three TMA boxes
+  static constexpr int PSI = 6 * ZC * NT;  // CPML memory staged per thread: [6 slots][ZC][NT]
+  static constexpr size_t ALL = BYTES + static_cast<size_t>(PSI) * 4;
 };
 template <int R>
-constexpr size_t smem_bytes() { return Tiles<R>::BYTES + 144; }  // + alignment pad + mbarrier
+constexpr size_t smem_bytes() { return Tiles<R>::ALL + 144; }  // + alignment pad + mbarrier
 
 // Tensor maps of one launch: the three source fields with their boxes.
 struct TmaSet {
@@ -120,6 +122,12 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -140,12 +148,47 @@ __device__ __forceinline__ size_t psi_at(int a, int s, int i, int j, int k, cons
   return (static_cast<size_t>(s) * np[1] + j) * np[0] + i;
 }
 
-// CPML update of one derivative d (Eq. 16-17, kappa = 1):
-// psi <- b psi + a d, stored back; returns d + psi.
-__device__ __forceinline__ float cpml_step(float d, float *__restrict__ psi, size_t idx, float a, float b) {
-  const float v = fmaf(b, psi[idx], a * d);
+// CPML update of one derivative d (Eq. 16-17, kappa = 1): psi <- b psi + a d
+// from the staged old value, stored back; returns d + psi.
+__device__ __forceinline__ float cpml_step(float d, float old, float *__restrict__ psi, size_t idx, float a,
+                                           float b) {
+  const float v = fmaf(b, old, a * d);
   psi[idx] = v;
   return d + v;
+}
+
+// Stage this thread's CPML memory of planes k0 .. k0+ZC-1 into shared memory
+// slots [slot][c][thread] with asynchronous copies.  Slots follow the psi
+// arrays: 0 (y), 1 (z), 2 (z), 3 (x), 4 (x), 5 (y) derivative.  sx, sy are
+// the x / y slab entries of the column (-1 outside), slab_k(k) the z entry.
+template <class SlabK>
+__device__ __forceinline__ void stage_psi(float *ps, float *const *psi, const DevParams &p, int i, int j, int k0,
+                                          int sx, int sy, SlabK slab_k) {
+  constexpr int S = ZC * NT;
+  const int nb2 = 2 * p.nb;
+#pragma unroll
+  for (int c = 0; c < ZC; ++c) {
+    const int k = k0 + c;
+    if (k >= p.np[2]) break;
+    const int sz = slab_k(k);
+    float *d = ps + c * NT + threadIdx.x;
+    if (sy >= 0) {
+      const size_t id = psi_at(1, sy, i, j, k, p.np, nb2);
+      cp_async4(d, psi[0] + id);
+      cp_async4(d + 5 * S, psi[5] + id);
+    }
+    if (sz >= 0) {
+      const size_t id = psi_at(2, sz, i, j, k, p.np, nb2);
+      cp_async4(d + S, psi[1] + id);
+      cp_async4(d + 2 * S, psi[2] + id);
+    }
+    if (sx >= 0) {
+      const size_t id = psi_at(0, sx, i, j, k, p.np, nb2);
+      cp_async4(d + 3 * S, psi[3] + id);
+      cp_async4(d + 4 * S, psi[4] + id);
+    }
+  }
+  cp_async_commit();
 }
 
 // Error-free accumulation (hi, lo) += v  (Knuth's TwoSum).
@@ -253,6 +296,12 @@ __device__ __forceinline__ float *smem_tiles(unsigned char *raw) {
   return reinterpret_cast<float *>(raw + pad);
 }
 
+// Does the CTA's box meet the bounding box of the source stencils?
+__device__ __forceinline__ bool cta_has_source(const DevParams &p, const Origin &o) {
+  return p.src_any && o.i0 + TX > p.src_lo[0] && o.i0 <= p.src_hi[0] && o.j0 + TY > p.src_lo[1] &&
+         o.j0 <= p.src_hi[1] && o.k0 + ZC > p.src_lo[2] && o.k0 <= p.src_hi[2];
+}
+
 template <int R>
 __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, int j, int k, float amp,
                                             float &curl) {
@@ -265,7 +314,7 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 // ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
-template <int R>
+template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   constexpr int M = 2 * R;
@@ -275,7 +324,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::BYTES / 4);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
   const Origin o = origin_of(p, blockIdx.x);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
@@ -296,11 +345,16 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
       w[a][c] = ok ? __ldg(p.ie[a] + id) : 0.f;
     }
   }
+  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
+  float *ps = s + Tiles<R>::BYTES / 4;
+  if (in_ij) stage_psi(ps, p.psiE, p, i, j, o.k0, si, sj, [&](int k) { return slab_int(k, np2, nb); });
+  else cp_async_commit();
+  const bool src = cta_has_source(p, o);
+  cp_async_wait_all();
   if (!tiles_ready(p, bar) || !in_ij) return;
 
   const View<R> v{s};
   const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
-  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
   float cx[M], cy[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
@@ -309,7 +363,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   const float amp = __ldg(p.amp + n);
   const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
 
@@ -332,11 +386,13 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
       }
       if (sj >= 0)
-        dy = cpml_step(dy, p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][sj], p.pml[1][2 * nb + sj]);
+        dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                       p.pml[1][sj], p.pml[1][2 * nb + sj]);
       if (sk >= 0)
-        dz = cpml_step(dz, p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][sk], p.pml[2][2 * nb + sk]);
+        dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                       p.pml[2][sk], p.pml[2][2 * nb + sk]);
       float curl = dy - dz;
-      source_term<R>(p, 0, i, j, k, amp, curl);
+      if (src) source_term<R>(p, 0, i, j, k, amp, curl);
       p.E[0][id] = fmaf(w[0][c], curl, e[0][c]);
     }
     // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
@@ -348,11 +404,13 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + q), dx);
       }
       if (sk >= 0)
-        dz = cpml_step(dz, p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][sk], p.pml[2][2 * nb + sk]);
+        dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                       p.pml[2][sk], p.pml[2][2 * nb + sk]);
       if (si >= 0)
-        dx = cpml_step(dx, p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][si], p.pml[0][2 * nb + si]);
+        dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                       p.pml[0][si], p.pml[0][2 * nb + si]);
       float curl = dz - dx;
-      source_term<R>(p, 1, i, j, k, amp, curl);
+      if (src) source_term<R>(p, 1, i, j, k, amp, curl);
       p.E[1][id] = fmaf(w[1][c], curl, e[1][c]);
     }
     // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
@@ -364,11 +422,13 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dy = fmaf(cy[q], v.zf(c + R, ty + q, tx), dy);
       }
       if (si >= 0)
-        dx = cpml_step(dx, p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][si], p.pml[0][2 * nb + si]);
+        dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                       p.pml[0][si], p.pml[0][2 * nb + si]);
       if (sj >= 0)
-        dy = cpml_step(dy, p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][sj], p.pml[1][2 * nb + sj]);
+        dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                       p.pml[1][sj], p.pml[1][2 * nb + sj]);
       float curl = dx - dy;
-      source_term<R>(p, 2, i, j, k, amp, curl);
+      if (src) source_term<R>(p, 2, i, j, k, amp, curl);
       p.E[2][id] = fmaf(w[2][c], curl, e[2][c]);
     }
     // volume DTFT of H^{n+1/2}
@@ -385,7 +445,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
-template <int R>
+template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   constexpr int M = 2 * R;
@@ -395,7 +455,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::BYTES / 4);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
   const Origin o = origin_of(p, blockIdx.x);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
 
@@ -412,11 +472,15 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
 #pragma unroll
     for (int a = 0; a < 3; ++a) h[a][c] = ok ? p.H[a][id] : 0.f;
   }
+  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
+  float *ps = s + Tiles<R>::BYTES / 4;
+  if (in_ij) stage_psi(ps, p.psiH, p, i, j, o.k0, si, sj, [&](int k) { return slab_half(k, np2, nb); });
+  else cp_async_commit();
+  cp_async_wait_all();
   if (!tiles_ready(p, bar) || !in_ij) return;
 
   const View<R> v{s};
   const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
-  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
   float cx[M], cy[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
@@ -425,7 +489,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   const float dt_mu = p.dt_mu;
   const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = p.vacc && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
   const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
   const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
 
@@ -448,11 +512,11 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
       }
       if (sj >= 0)
-        dy = cpml_step(dy, p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj],
-                       p.pml[1][6 * nb + sj]);
+        dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiH[0],
+                       psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
       if (sk >= 0)
-        dz = cpml_step(dz, p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk],
-                       p.pml[2][6 * nb + sk]);
+        dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiH[1],
+                       psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
       p.H[0][id] = fmaf(-dt_mu, dy - dz, h[0][c]);
     }
     // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
@@ -464,11 +528,11 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + 1 + q), dx);
       }
       if (sk >= 0)
-        dz = cpml_step(dz, p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk],
-                       p.pml[2][6 * nb + sk]);
+        dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiH[2],
+                       psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
       if (si >= 0)
-        dx = cpml_step(dx, p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si],
-                       p.pml[0][6 * nb + si]);
+        dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiH[3],
+                       psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
       p.H[1][id] = fmaf(-dt_mu, dz - dx, h[1][c]);
     }
     // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
@@ -480,11 +544,11 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
         dy = fmaf(cy[q], v.zf(c + R - 1, ty + q + 1, tx), dy);
       }
       if (si >= 0)
-        dx = cpml_step(dx, p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si],
-                       p.pml[0][6 * nb + si]);
+        dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiH[4],
+                       psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
       if (sj >= 0)
-        dy = cpml_step(dy, p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj],
-                       p.pml[1][6 * nb + sj]);
+        dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiH[5],
+                       psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
       p.H[2][id] = fmaf(-dt_mu, dx - dy, h[2][c]);
     }
     // volume DTFT of E^{n+1}
@@ -671,23 +735,24 @@ struct StepEvents {
   std::vector<cudaEvent_t> ev;
 };
 
-template <int R>
+template <int R, bool VOL>
 cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+      cudaFuncSetAttribute(k_update_E<R, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+    e = cudaFuncSetAttribute(k_update_H<R, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   size_t used = 0;
   for (int n = 0; n < nt; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R><<<blocks, NT, sb, st>>>(p, tE, n);
+    k_update_E<R, VOL><<<blocks, NT, sb, st>>>(p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R><<<blocks, NT, sb, st>>>(p, tH, n);
+    k_update_H<R, VOL><<<blocks, NT, sb, st>>>(p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -889,11 +954,16 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
                                      reinterpret_cast<float *>(base + L.ie[2]), p.n[0], p.n[1], p.n[2], p.np[0],
                                      p.np[1], p.np[2], p.pitch, nbe, 2.0 * s->omega0 * dt, s->sigma_min,
                                      p.status);
+  const bool vol = p.vacc != nullptr;
   switch (rd) {
-    case 1: e = launch_steps<1>(p, nt, blocks, cs, te); break;
-    case 2: e = launch_steps<2>(p, nt, blocks, cs, te); break;
-    case 3: e = launch_steps<3>(p, nt, blocks, cs, te); break;
-    default: e = launch_steps<4>(p, nt, blocks, cs, te); break;
+    case 1: e = vol ? launch_steps<1, true>(p, nt, blocks, cs, te) : launch_steps<1, false>(p, nt, blocks, cs, te);
+      break;
+    case 2: e = vol ? launch_steps<2, true>(p, nt, blocks, cs, te) : launch_steps<2, false>(p, nt, blocks, cs, te);
+      break;
+    case 3: e = vol ? launch_steps<3, true>(p, nt, blocks, cs, te) : launch_steps<3, false>(p, nt, blocks, cs, te);
+      break;
+    default: e = vol ? launch_steps<4, true>(p, nt, blocks, cs, te) : launch_steps<4, false>(p, nt, blocks, cs, te);
+      break;
   }
   if (e != cudaSuccess) return EMM_ECUDA;
   const double *dnorm = reinterpret_cast<const double *>(base + L.norm);
