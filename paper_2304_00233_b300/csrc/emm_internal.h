@@ -49,13 +49,14 @@ void cpml_axis(const emm_grid *g, int axis, double vmax, double fmax, double dt,
 struct DevParams {
   int np[3];        // padded sizes
   int n[3];         // interior sizes
-  int pitch;        // row pitch (samples) of the field arrays: np[0] rounded up to 32
+  int pitch;        // row pitch (samples) of the field arrays, a multiple of 32
   size_t plane;     // pitch * np[1]
   int nbe, nb;
-  int tiles_x, tiles_y, kchunk, zchunks, stencil_blocks;  // stencil_blocks: CTAs of a launch
+  int org[3];       // grid coordinates of the first tile (<= 0)
+  int tiles_x, tiles_y, tiles_z, stencil_blocks;  // stencil_blocks: stencil CTAs of a launch
   int rec_blocks;   // CTAs (the first ones) that also gather the receiver DTFT
   float dt_mu;      // dt / mu0
-  float *E[3], *H[3];
+  float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
   float *psiE[6];            // CPML memory of curl H terms (E update)
   float *psiH[6];            // CPML memory of curl E terms (H update)

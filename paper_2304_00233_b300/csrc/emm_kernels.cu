@@ -169,6 +169,7 @@ __device__ __forceinline__ void stage_psi(float *ps, float *const *psi, const De
 #pragma unroll
   for (int c = 0; c < ZC; ++c) {
     const int k = k0 + c;
+    if (k < 0) continue;
     if (k >= p.np[2]) break;
     const int sz = slab_k(k);
     float *d = ps + c * NT + threadIdx.x;
@@ -249,7 +250,8 @@ struct Origin {
   int i0, j0, k0;
 };
 __device__ __forceinline__ Origin origin_of(const DevParams &p, int b) {
-  return Origin{(b % p.tiles_x) * TX, ((b / p.tiles_x) % p.tiles_y) * TY, (b / (p.tiles_x * p.tiles_y)) * ZC};
+  return Origin{p.org[0] + (b % p.tiles_x) * TX, p.org[1] + ((b / p.tiles_x) % p.tiles_y) * TY,
+                p.org[2] + (b / (p.tiles_x * p.tiles_y)) * ZC};
 }
 
 // Shared-memory views of the three tiles (see Tiles).
@@ -314,10 +316,127 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 // ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
+// Is every cell of the CTA inside the CPML-free region where all D- rows
+// exist (no slab, no boundary test needed)?
+__device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, int R) {
+  const int m = max(p.nb, R);
+  return o.i0 >= m && o.i0 + TX - 1 <= p.np[0] - 1 - m && o.j0 >= m && o.j0 + TY - 1 <= p.np[1] - 1 - m &&
+         o.k0 >= m && o.k0 + ZC - 1 <= p.np[2] - 1 - m;
+}
+
+// The ZC planes of one column.  FAST: an interior CTA without the source,
+// where every validity test is true and every slab test false.
+template <int R, bool VOL, bool FAST>
+__device__ __forceinline__ void e_planes(const DevParams &p, const View<R> &v, const Origin &o, int tx, int ty,
+                                         const float (&e)[3][ZC], const float (&w)[3][ZC], const float *ps,
+                                         int n, bool src) {
+  constexpr int M = 2 * R;
+  const int i = o.i0 + tx, j = o.j0 + ty;
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+  const bool dm_i = FAST || (i >= R && i <= np0 - 1 - R), dm_j = FAST || (j >= R && j <= np1 - 1 - R);
+  const int si = FAST ? -1 : slab_int(i, np0, nb), sj = FAST ? -1 : slab_int(j, np1, nb);
+  float cx[M], cy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
+    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
+  }
+  const float amp = FAST ? 0.f : __ldg(p.amp + n);
+  const int ii = i - p.nbe, jj = j - p.nbe;
+  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
+  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+  const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+
+#pragma unroll
+  for (int c = 0; c < ZC; ++c) {
+    const int k = o.k0 + c;
+    if (!FAST) {
+      if (k < 0) continue;
+      if (k >= np2) break;
+    }
+    const size_t id = static_cast<size_t>(k) * p.plane + col;
+    const bool dm_k = FAST || (k >= R && k <= np2 - 1 - R);
+    const int sk = FAST ? -1 : slab_int(k, np2, nb);
+    float cz[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
+    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+    if (FAST || (i <= np0 - 2 && dm_j && dm_k)) {
+      float dy = 0.f, dz = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dy = fmaf(cy[q], v.xy(c, ty + q, tx + XH), dy);
+        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
+      }
+      if (!FAST) {
+        if (sj >= 0)
+          dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                         p.pml[1][sj], p.pml[1][2 * nb + sj]);
+        if (sk >= 0)
+          dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                         p.pml[2][sk], p.pml[2][2 * nb + sk]);
+      }
+      float curl = dy - dz;
+      if (!FAST && src) source_term<R>(p, 0, i, j, k, amp, curl);
+      p.E[0][id] = fmaf(w[0][c], curl, e[0][c]);
+    }
+    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+    if (FAST || (j <= np1 - 2 && dm_i && dm_k)) {
+      float dz = 0.f, dx = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
+        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + q), dx);
+      }
+      if (!FAST) {
+        if (sk >= 0)
+          dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                         p.pml[2][sk], p.pml[2][2 * nb + sk]);
+        if (si >= 0)
+          dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                         p.pml[0][si], p.pml[0][2 * nb + si]);
+      }
+      float curl = dz - dx;
+      if (!FAST && src) source_term<R>(p, 1, i, j, k, amp, curl);
+      p.E[1][id] = fmaf(w[1][c], curl, e[1][c]);
+    }
+    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+    if (FAST || (dm_i && dm_j && k <= np2 - 2)) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        dx = fmaf(cx[q], v.xf(c + R, ty, tx + XH - R + q), dx);
+        dy = fmaf(cy[q], v.zf(c + R, ty + q, tx), dy);
+      }
+      if (!FAST) {
+        if (si >= 0)
+          dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                         p.pml[0][si], p.pml[0][2 * nb + si]);
+        if (sj >= 0)
+          dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                         p.pml[1][sj], p.pml[1][2 * nb + sj]);
+      }
+      float curl = dx - dy;
+      if (!FAST && src) source_term<R>(p, 2, i, j, k, amp, curl);
+      p.E[2][id] = fmaf(w[2][c], curl, e[2][c]);
+    }
+    // volume DTFT of H^{n+1/2}
+    if (VOL) {
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 3, lin, nint, facH, v.zf(c + R, ty + R, tx));
+        volume_accumulate(p, 4, lin, nint, facH, v.xf(c + R, ty, tx + XH));
+        volume_accumulate(p, 5, lin, nint, facH, v.xy(c, ty + R, tx + XH));
+      }
+    }
+  }
+}
+
 template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  constexpr int M = 2 * R;
   if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
     receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
     return;
@@ -331,156 +450,59 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = o.i0 + tx, j = o.j0 + ty;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const bool in_ij = i < np0 && j < np1;
+  const bool in_ij = i >= 0 && i < np0 && j >= 0 && j < np1;
   const size_t col = static_cast<size_t>(j) * p.pitch + i;
   // this thread's own samples, loaded while the copies are in flight
   float e[3][ZC], w[3][ZC];
 #pragma unroll
   for (int c = 0; c < ZC; ++c) {
-    const bool ok = in_ij && o.k0 + c < np2;
-    const size_t id = static_cast<size_t>(o.k0 + c) * p.plane + col;
+    const int k = o.k0 + c;
+    const bool ok = in_ij && k >= 0 && k < np2;
+    const size_t id = static_cast<size_t>(k) * p.plane + col;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       e[a][c] = ok ? p.E[a][id] : 0.f;
       w[a][c] = ok ? __ldg(p.ie[a] + id) : 0.f;
     }
   }
-  const int si = slab_int(i, np0, nb), sj = slab_int(j, np1, nb);
-  float *ps = s + Tiles<R>::BYTES / 4;
-  if (in_ij) stage_psi(ps, p.psiE, p, i, j, o.k0, si, sj, [&](int k) { return slab_int(k, np2, nb); });
-  else cp_async_commit();
   const bool src = cta_has_source(p, o);
+  const bool fast = !src && interior_E(p, o, R);
+  float *ps = s + Tiles<R>::BYTES / 4;
+  if (!fast && in_ij)
+    stage_psi(ps, p.psiE, p, i, j, o.k0, slab_int(i, np0, nb), slab_int(j, np1, nb),
+              [&](int k) { return slab_int(k, np2, nb); });
+  else
+    cp_async_commit();
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !in_ij) return;
-
   const View<R> v{s};
-  const bool dm_i = i >= R && i <= np0 - 1 - R, dm_j = j >= R && j <= np1 - 1 - R;
-  float cx[M], cy[M];
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
-    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
-  }
-  const float amp = __ldg(p.amp + n);
-  const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-  const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
-
-#pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = o.k0 + c;
-    if (k >= np2) break;
-    const size_t id = static_cast<size_t>(k) * p.plane + col;
-    const bool dm_k = k >= R && k <= np2 - 1 - R;
-    const int sk = slab_int(k, np2, nb);
-    float cz[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
-    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-    if (i <= np0 - 2 && dm_j && dm_k) {
-      float dy = 0.f, dz = 0.f;
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dy = fmaf(cy[q], v.xy(c, ty + q, tx + XH), dy);
-        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
-      }
-      if (sj >= 0)
-        dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                       p.pml[1][sj], p.pml[1][2 * nb + sj]);
-      if (sk >= 0)
-        dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                       p.pml[2][sk], p.pml[2][2 * nb + sk]);
-      float curl = dy - dz;
-      if (src) source_term<R>(p, 0, i, j, k, amp, curl);
-      p.E[0][id] = fmaf(w[0][c], curl, e[0][c]);
-    }
-    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-    if (j <= np1 - 2 && dm_i && dm_k) {
-      float dz = 0.f, dx = 0.f;
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
-        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + q), dx);
-      }
-      if (sk >= 0)
-        dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                       p.pml[2][sk], p.pml[2][2 * nb + sk]);
-      if (si >= 0)
-        dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                       p.pml[0][si], p.pml[0][2 * nb + si]);
-      float curl = dz - dx;
-      if (src) source_term<R>(p, 1, i, j, k, amp, curl);
-      p.E[1][id] = fmaf(w[1][c], curl, e[1][c]);
-    }
-    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-    if (dm_i && dm_j && k <= np2 - 2) {
-      float dx = 0.f, dy = 0.f;
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dx = fmaf(cx[q], v.xf(c + R, ty, tx + XH - R + q), dx);
-        dy = fmaf(cy[q], v.zf(c + R, ty + q, tx), dy);
-      }
-      if (si >= 0)
-        dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                       p.pml[0][si], p.pml[0][2 * nb + si]);
-      if (sj >= 0)
-        dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                       p.pml[1][sj], p.pml[1][2 * nb + sj]);
-      float curl = dx - dy;
-      if (src) source_term<R>(p, 2, i, j, k, amp, curl);
-      p.E[2][id] = fmaf(w[2][c], curl, e[2][c]);
-    }
-    // volume DTFT of H^{n+1/2}
-    const int kk = k - p.nbe;
-    if (int_ij && kk >= 0 && kk < p.n[2]) {
-      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-      volume_accumulate(p, 3, lin, nint, facH, v.zf(c + R, ty + R, tx));
-      volume_accumulate(p, 4, lin, nint, facH, v.xf(c + R, ty, tx + XH));
-      volume_accumulate(p, 5, lin, nint, facH, v.xy(c, ty + R, tx + XH));
-    }
-  }
+  if (fast)
+    e_planes<R, VOL, true>(p, v, o, tx, ty, e, w, ps, n, false);
+  else
+    e_planes<R, VOL, false>(p, v, o, tx, ty, e, w, ps, n, src);
 }
 
 // ---------------------------------------------------------------------------
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
-template <int R, bool VOL>
-__global__ void __launch_bounds__(NT, min_ctas(R))
-    k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  constexpr int M = 2 * R;
-  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
-    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
-    return;
-  }
-  extern __shared__ unsigned char smem_raw[];
-  float *s = smem_tiles(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of(p, blockIdx.x);
-  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
+// Is every cell of the CTA inside the CPML-free region where all D+ rows exist?
+__device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, int R) {
+  const int lo = max(p.nb, R - 1);
+  const int hx = min(p.np[0] - 2 - p.nb, p.np[0] - 1 - R), hy = min(p.np[1] - 2 - p.nb, p.np[1] - 1 - R),
+            hz = min(p.np[2] - 2 - p.nb, p.np[2] - 1 - R);
+  return o.i0 >= lo && o.i0 + TX - 1 <= hx && o.j0 >= lo && o.j0 + TY - 1 <= hy && o.k0 >= lo &&
+         o.k0 + ZC - 1 <= hz;
+}
 
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+template <int R, bool VOL, bool FAST>
+__device__ __forceinline__ void h_planes(const DevParams &p, const View<R> &v, const Origin &o, int tx, int ty,
+                                         const float (&h)[3][ZC], const float *ps, int n) {
+  constexpr int M = 2 * R;
   const int i = o.i0 + tx, j = o.j0 + ty;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const bool in_ij = i < np0 && j < np1;
   const size_t col = static_cast<size_t>(j) * p.pitch + i;
-  float h[3][ZC];
-#pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const bool ok = in_ij && o.k0 + c < np2;
-    const size_t id = static_cast<size_t>(o.k0 + c) * p.plane + col;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) h[a][c] = ok ? p.H[a][id] : 0.f;
-  }
-  const int si = slab_half(i, np0, nb), sj = slab_half(j, np1, nb);
-  float *ps = s + Tiles<R>::BYTES / 4;
-  if (in_ij) stage_psi(ps, p.psiH, p, i, j, o.k0, si, sj, [&](int k) { return slab_half(k, np2, nb); });
-  else cp_async_commit();
-  cp_async_wait_all();
-  if (!tiles_ready(p, bar) || !in_ij) return;
-
-  const View<R> v{s};
-  const bool dp_i = i >= R - 1 && i <= np0 - 1 - R, dp_j = j >= R - 1 && j <= np1 - 1 - R;
+  const bool dp_i = FAST || (i >= R - 1 && i <= np0 - 1 - R), dp_j = FAST || (j >= R - 1 && j <= np1 - 1 - R);
+  const int si = FAST ? -1 : slab_half(i, np0, nb), sj = FAST ? -1 : slab_half(j, np1, nb);
   float cx[M], cy[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
@@ -496,78 +518,132 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
 #pragma unroll
   for (int c = 0; c < ZC; ++c) {
     const int k = o.k0 + c;
-    if (k >= np2) break;
+    if (!FAST) {
+      if (k < 0) continue;
+      if (k >= np2) break;
+    }
     const size_t id = static_cast<size_t>(k) * p.plane + col;
-    const bool dp_k = k >= R - 1 && k <= np2 - 1 - R;
-    const int sk = slab_half(k, np2, nb);
+    const bool dp_k = FAST || (k >= R - 1 && k <= np2 - 1 - R);
+    const int sk = FAST ? -1 : slab_half(k, np2, nb);
     float cz[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
     // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-    if (dp_j && dp_k) {
+    if (FAST || (dp_j && dp_k)) {
       float dy = 0.f, dz = 0.f;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         dy = fmaf(cy[q], v.xy(c, ty + q + 1, tx + XH), dy);
         dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
       }
-      if (sj >= 0)
-        dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiH[0],
-                       psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
-      if (sk >= 0)
-        dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiH[1],
-                       psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+      if (!FAST) {
+        if (sj >= 0)
+          dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                         p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+        if (sk >= 0)
+          dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                         p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+      }
       p.H[0][id] = fmaf(-dt_mu, dy - dz, h[0][c]);
     }
     // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-    if (dp_i && dp_k) {
+    if (FAST || (dp_i && dp_k)) {
       float dz = 0.f, dx = 0.f;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
         dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + 1 + q), dx);
       }
-      if (sk >= 0)
-        dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiH[2],
-                       psi_at(2, sk, i, j, k, p.np, 2 * nb), p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
-      if (si >= 0)
-        dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiH[3],
-                       psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
+      if (!FAST) {
+        if (sk >= 0)
+          dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
+                         p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+        if (si >= 0)
+          dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                         p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
+      }
       p.H[1][id] = fmaf(-dt_mu, dz - dx, h[1][c]);
     }
     // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-    if (dp_i && dp_j) {
+    if (FAST || (dp_i && dp_j)) {
       float dx = 0.f, dy = 0.f;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         dx = fmaf(cx[q], v.xf(c + R - 1, ty, tx + XH - R + 1 + q), dx);
         dy = fmaf(cy[q], v.zf(c + R - 1, ty + q + 1, tx), dy);
       }
-      if (si >= 0)
-        dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiH[4],
-                       psi_at(0, si, i, j, k, p.np, 2 * nb), p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
-      if (sj >= 0)
-        dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiH[5],
-                       psi_at(1, sj, i, j, k, p.np, 2 * nb), p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+      if (!FAST) {
+        if (si >= 0)
+          dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
+                         p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
+        if (sj >= 0)
+          dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
+                         p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+      }
       p.H[2][id] = fmaf(-dt_mu, dx - dy, h[2][c]);
     }
     // volume DTFT of E^{n+1}
-    const int kk = k - p.nbe;
-    if (int_ij && kk >= 0 && kk < p.n[2]) {
-      const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-      volume_accumulate(p, 0, lin, nint, facE, v.zf(c + R - 1, ty + R, tx));
-      volume_accumulate(p, 1, lin, nint, facE, v.xf(c + R - 1, ty, tx + XH));
-      volume_accumulate(p, 2, lin, nint, facE, v.xy(c, ty + R, tx + XH));
+    if (VOL) {
+      const int kk = k - p.nbe;
+      if (int_ij && kk >= 0 && kk < p.n[2]) {
+        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
+        volume_accumulate(p, 0, lin, nint, facE, v.zf(c + R - 1, ty + R, tx));
+        volume_accumulate(p, 1, lin, nint, facE, v.xf(c + R - 1, ty, tx + XH));
+        volume_accumulate(p, 2, lin, nint, facE, v.xy(c, ty + R, tx + XH));
+      }
     }
   }
+}
+
+template <int R, bool VOL>
+__global__ void __launch_bounds__(NT, min_ctas(R))
+    k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
+    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  float *s = smem_tiles(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
+  const Origin o = origin_of(p, blockIdx.x);
+  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = o.i0 + tx, j = o.j0 + ty;
+  const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
+  const bool in_ij = i >= 0 && i < np0 && j >= 0 && j < np1;
+  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+  float h[3][ZC];
+#pragma unroll
+  for (int c = 0; c < ZC; ++c) {
+    const int k = o.k0 + c;
+    const bool ok = in_ij && k >= 0 && k < np2;
+    const size_t id = static_cast<size_t>(k) * p.plane + col;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h[a][c] = ok ? p.H[a][id] : 0.f;
+  }
+  const bool fast = interior_H(p, o, R);
+  float *ps = s + Tiles<R>::BYTES / 4;
+  if (!fast && in_ij)
+    stage_psi(ps, p.psiH, p, i, j, o.k0, slab_half(i, np0, nb), slab_half(j, np1, nb),
+              [&](int k) { return slab_half(k, np2, nb); });
+  else
+    cp_async_commit();
+  cp_async_wait_all();
+  if (!tiles_ready(p, bar) || !in_ij) return;
+  const View<R> v{s};
+  if (fast)
+    h_planes<R, VOL, true>(p, v, o, tx, ty, h, ps, n);
+  else
+    h_planes<R, VOL, false>(p, v, o, tx, ty, h, ps, n);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
 // the pads replicating the edge (model extension, Sec. 3.4), and the input
 // check (finite, positive, >= sigma_min).
 __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie1, float *ie2, int n0,
-                          int n1, int n2, int np0, int np1, int np2, int pitch, int nbe, double two_w0_dt,
-                          double sigma_min, int *status) {
+                          int n1, int n2, int np0, int np1, int np2, int pitch, int xshift, int nbe,
+                          double two_w0_dt, double sigma_min, int *status) {
   const size_t cells = static_cast<size_t>(pitch) * np1 * np2;  // including the row padding
   const size_t nint = static_cast<size_t>(n0) * n1 * n2;
   float *ie[3] = {ie0, ie1, ie2};
@@ -575,9 +651,9 @@ __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie
        t += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int c = static_cast<int>(t / cells);
     const size_t r = t % cells;
-    const int i = static_cast<int>(r % pitch), j = static_cast<int>((r / pitch) % np1),
+    const int i = static_cast<int>(r % pitch) - xshift, j = static_cast<int>((r / pitch) % np1),
               k = static_cast<int>(r / (static_cast<size_t>(pitch) * np1));
-    if (i >= np0) {  // row padding: defined zeros (read by the stage copies, never used)
+    if (i < 0 || i >= np0) {  // row padding: defined zeros, never used
       ie[c][r] = 0.f;
       continue;
     }
@@ -625,7 +701,29 @@ __global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *no
 // ---------------------------------------------------------------------------
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-inline int field_pitch(int np0) { return (np0 + 31) / 32 * 32; }  // rows start on 128-byte lines
+// Tiling of the padded grid and the matching field-array geometry.  Tiles
+// start at org[a] <= 0, chosen so that a tile edge falls on the first
+// CPML-free sample max(nb, rd) (x: rounded down to a multiple of 4 for the
+// TMA boxes), which maximises the CTAs that take the interior path.  Field
+// rows hold xshift = -org[0] leading samples, so every tile row starts on a
+// 128-byte line; the row pitch is a multiple of 32 samples.
+struct FieldGeom {
+  int org[3], tiles[3], xshift, pitch;
+};
+FieldGeom field_geom(const emm_grid *g) {
+  FieldGeom f{};
+  const int lo = std::max(g->nb, g->rd);
+  const int lo4 = lo & ~3;
+  const int step[3] = {TX, TY, ZC};
+  const int first[3] = {lo4, lo, lo};
+  for (int a = 0; a < 3; ++a) {
+    f.org[a] = first[a] - step[a] * ((first[a] + step[a] - 1) / step[a]);
+    f.tiles[a] = (g->ax[a].npad - f.org[a] + step[a] - 1) / step[a];
+  }
+  f.xshift = -f.org[0];
+  f.pitch = (g->ax[0].npad + f.xshift + 31) / 32 * 32;
+  return f;
+}
 
 // Byte layout of the device workspace.
 struct Layout {
@@ -652,7 +750,7 @@ Layout plan(const emm_grid *g, const emm_survey *s) {
     off = align_up(off + bytes);
     return o;
   };
-  const size_t cells = static_cast<size_t>(field_pitch(g->ax[0].npad)) * g->ax[1].npad * g->ax[2].npad;
+  const size_t cells = static_cast<size_t>(field_geom(g).pitch) * g->ax[1].npad * g->ax[2].npad;
   const size_t nint = static_cast<size_t>(g->ax[0].n) * g->ax[1].n * g->ax[2].n;
   const size_t m = 2 * static_cast<size_t>(g->rd), nf = s->nfreq;
   const size_t nt = s->nt > 0 ? s->nt : 1, nrec = s->nrec > 0 ? s->nrec : 1;
@@ -887,14 +985,15 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     p.cp[a] = reinterpret_cast<const float *>(base + L.cp[a]);
     p.pml[a] = reinterpret_cast<const float *>(base + L.pml[a]);
   }
-  p.pitch = field_pitch(p.np[0]);
+  const FieldGeom fg = field_geom(g);
+  p.pitch = fg.pitch;
   p.plane = static_cast<size_t>(p.pitch) * p.np[1];
   p.nbe = nbe;
   p.nb = nb;
   for (int c = 0; c < 3; ++c) {
-    p.E[c] = reinterpret_cast<float *>(base + L.E[c]);
-    p.H[c] = reinterpret_cast<float *>(base + L.H[c]);
-    p.ie[c] = reinterpret_cast<const float *>(base + L.ie[c]);
+    p.E[c] = reinterpret_cast<float *>(base + L.E[c]) + fg.xshift;
+    p.H[c] = reinterpret_cast<float *>(base + L.H[c]) + fg.xshift;
+    p.ie[c] = reinterpret_cast<const float *>(base + L.ie[c]) + fg.xshift;
     p.jw[c] = reinterpret_cast<const float *>(base + L.jw[c]);
   }
   for (int c = 0; c < 6; ++c) {
@@ -916,16 +1015,16 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   p.status = reinterpret_cast<int *>(base + L.status);
   // launch shape: TX x TY column tiles times runs of ZC planes, then the
   // receiver CTAs (one warp per receiver component)
-  p.tiles_x = (p.np[0] + TX - 1) / TX;
-  p.tiles_y = (p.np[1] + TY - 1) / TY;
+  for (int a = 0; a < 3; ++a) p.org[a] = fg.org[a];
+  p.tiles_x = fg.tiles[0];
+  p.tiles_y = fg.tiles[1];
+  p.tiles_z = fg.tiles[2];
   int sms = 148;
   {
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  p.kchunk = ZC;
-  p.zchunks = (p.np[2] + ZC - 1) / ZC;
-  p.stencil_blocks = p.tiles_x * p.tiles_y * p.zchunks;
+  p.stencil_blocks = p.tiles_x * p.tiles_y * p.tiles_z;
   p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
   const int blocks = p.stencil_blocks + p.rec_blocks;
   // bounding box of the source stencils (lets CTAs far from it skip the test)
@@ -952,7 +1051,7 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   k_prepare<<<4 * sms, 256, 0, cs>>>(sigma, reinterpret_cast<float *>(base + L.ie[0]),
                                      reinterpret_cast<float *>(base + L.ie[1]),
                                      reinterpret_cast<float *>(base + L.ie[2]), p.n[0], p.n[1], p.n[2], p.np[0],
-                                     p.np[1], p.np[2], p.pitch, nbe, 2.0 * s->omega0 * dt, s->sigma_min,
+                                     p.np[1], p.np[2], p.pitch, fg.xshift, nbe, 2.0 * s->omega0 * dt, s->sigma_min,
                                      p.status);
   const bool vol = p.vacc != nullptr;
   switch (rd) {
