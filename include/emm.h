@@ -4,8 +4,8 @@
  * The library advances the diffusive Maxwell equations transformed to the
  * fictitious wave domain (Yang, libEMM, arXiv 2304.00233, Sec. 2.2 Eq. 3-5)
  * with a 2r-th order staggered leapfrog on a non-uniform rectilinear grid
- * (Sec. 3.1 Eq. 8, 12-13), CPML absorbing layers (Sec. 3.4 Eq. 16-18), an
- * electric dipole source, and an on-the-fly DTFT (Sec. 3.5 Eq. 19) that yields
+ * (Sec. 3.1 Eq. 8, 13-14), CPML absorbing layers (Sec. 3.4 Eq. 22-24), an
+ * electric dipole source, and an on-the-fly DTFT (Sec. 3.5 Eq. 25) that yields
  * frequency-domain Green's functions (Sec. 2.2 Eq. 7) at receivers and,
  * optionally, over the model volume.  The time loop runs in CUDA kernels on
  * one GPU (sm_103a).
@@ -71,7 +71,7 @@ typedef struct {
 } emm_grid_info;
 
 /* Build a grid: pads the nodes (Sec. 3.4), forms half nodes, and tabulates
- * the D+ / D- rows of every sample (row 1 of [V^T]^{-1}, Sec. 3.1 Eq. 9-13).
+ * the D+ / D- rows of every sample (row 1 of [V^T]^{-1}, Sec. 3.1 Eq. 9-14).
  * desc (host, read only during the call).  *out receives a handle that the
  * caller releases with emm_free_grid.  EMM_EINVAL for bad sizes, rd outside
  * 1..4, nb < rd, ne < 0, or non-ascending nodes; EMM_ENOMEM. */
@@ -86,9 +86,9 @@ int emm_grid_query(const emm_grid *grid, emm_grid_info *info);
 /* Table kinds for emm_grid_tables. */
 #define EMM_TAB_NODES 0      /* coef[npad+1]: padded integer nodes X (X[npad] only bounds the last half cell) */
 #define EMM_TAB_HALF 1       /* coef[npad]: half nodes Xh[i] = (X[i] + X[i+1]) / 2 */
-#define EMM_TAB_DPLUS 2      /* coef[npad][2rd]: D+ rows at Xh[i] over F[i-rd+1 .. i+rd] (Eq. 12);
+#define EMM_TAB_DPLUS 2      /* coef[npad][2rd]: D+ rows at Xh[i] over F[i-rd+1 .. i+rd] (Eq. 13);
                                 idx[npad]: first tap i-rd+1, or -1 where the row is off the grid */
-#define EMM_TAB_DMINUS 3     /* coef[npad][2rd]: D- rows at X[i] over half samples F[i-rd .. i+rd-1] (Eq. 13);
+#define EMM_TAB_DMINUS 3     /* coef[npad][2rd]: D- rows at X[i] over half samples F[i-rd .. i+rd-1] (Eq. 14);
                                 idx[npad]: first tap i-rd, or -1 */
 #define EMM_TAB_SLAB_INT 4   /* idx[npad]: CPML slab entry 0..2nb-1 of integer sample i, or -1 */
 #define EMM_TAB_SLAB_HALF 5  /* idx[npad]: CPML slab entry 0..2nb-1 of half sample i, or -1 */
@@ -98,7 +98,7 @@ int emm_grid_query(const emm_grid *grid, emm_grid_info *info);
  * EMM_EINVAL on a bad axis or kind. */
 int emm_grid_tables(const emm_grid *grid, int axis, int kind, double *coef, int *idx);
 
-/* Time step of the stability condition (Sec. 3.2 Eq. 14-15):
+/* Time step of the stability condition (Sec. 3.2 Eq. 15-16):
  * vmax = sqrt(2 omega0 / (mu0 sigma_min)), eta = vmax/2 sqrt(sum_a Dmax_a^2),
  * Dmax_a = largest absolute row sum of the D+ and D- tables of axis a.
  * *dt = 0.99 / eta; *eta and *vmax (both may be NULL) receive the others.
@@ -106,7 +106,7 @@ int emm_grid_tables(const emm_grid *grid, int axis, int kind, double *coef, int 
 int emm_time_step(const emm_grid *grid, double sigma_min, double omega0,
                   double *dt, double *eta, double *vmax);
 
-/* CPML coefficients of axis `axis` for a given vmax, fmax and dt (Eq. 17-18,
+/* CPML coefficients of axis `axis` for a given vmax, fmax and dt (Eq. 23-24,
  * kappa = 1, profile d = d0 (xi/L)^2 with d0 = -3 vmax ln(1e-3) / (2L),
  * alpha = pi fmax (1 - xi/L)); ab (host) receives [4][2nb]:
  * a at integer samples, b at integer samples, a at half samples, b at half

@@ -14,10 +14,10 @@
  * What it computes, in the paper's order (Algorithm 1 without the airwave
  * step, which is not modelled here):
  *   for it = 0 .. Nt-1:
- *     curl H (with CPML memory, Sec. 3.4 Eq. 16-18)  -> curlH
+ *     curl H (with CPML memory, Sec. 3.4 Eq. 22-24)  -> curlH
  *     inject electric source J at t_{n+1/2}           -> curlH - J
  *     update E:  E += dt/eps (curlH - J)              (Sec. 3.1 Eq. 8)
- *     DTFT of E^{n+1} and H^{n+1/2}                   (Sec. 3.5 Eq. 19)
+ *     DTFT of E^{n+1} and H^{n+1/2}                   (Sec. 3.5 Eq. 25)
  *     curl E (with CPML memory)                        -> curlE
  *     update H:  H -= dt/mu curlE                     (Eq. 8)
  *   Green's functions (Sec. 2.2 Eq. 7) at receivers and over the volume.
@@ -163,7 +163,7 @@ static int orc_axis_nodes(orc_axis *ax, int n, const double *x, int rd, int nb, 
   return ORC_OK;
 }
 
-/* FD tables of Eq. 12-13, reading of which Vandermonde gives which operator:
+/* FD tables of Eq. 13-14, reading of which Vandermonde gives which operator:
  *   D+ at Xh[i] uses integer nodes X[i-r+1..i+r] and multiplies F[i-r+1..i+r];
  *   D- at X[i]  uses half nodes Xh[i-r..i+r-1]   and multiplies F[i-r..i+r-1].
  * The grid holds integer samples 0..np-1 and half samples 0..np-2 (reading:
@@ -178,7 +178,7 @@ static void orc_axis_fd(orc_axis *ax)
     orc_row_weights(m, &ax->Xh[i - r], ax->X[i], 1, &ax->cm[(size_t)i * m]);
 }
 
-/* CPML coefficients (Eq. 17-18) with kappa = 1.  Profile after Komatitsch &
+/* CPML coefficients (Eq. 23-24) with kappa = 1.  Profile after Komatitsch &
  * Martin (2007): d = d0 (xi/L)^2, d0 = -3 vmax ln(R) / (2L), R = 1e-3,
  * alpha = pi fmax (1 - xi/L); xi is the distance of the sample coordinate
  * into the layer and L the layer thickness on that face. */
@@ -209,7 +209,7 @@ static void orc_axis_cpml(orc_axis *ax, double vmax, double fmax, double dt)
   }
 }
 
-/* D_max of Sec. 3.2 (Eq. 15): the largest absolute row sum of either table. */
+/* D_max of Sec. 3.2 (Eq. 16): the largest absolute row sum of either table. */
 static double orc_axis_dmax(const orc_axis *ax)
 {
   int r = ax->rd, m = 2 * r, np = ax->npad;
@@ -393,7 +393,7 @@ static double orc_dp(const orc_state *st, int a, const double *G, int i, int j, 
   return s;
 }
 
-/* CPML memory update psi <- b psi + a d, returns d + psi (Eq. 16-17). */
+/* CPML memory update psi <- b psi + a d, returns d + psi (Eq. 22-23). */
 static double orc_pml(const orc_state *st, int pml, int a, int half, int c, double *psi,
                       size_t idx, double d)
 {
@@ -555,7 +555,7 @@ int orc_forward(orc_problem *P)
   st->ncell = (size_t)st->np[0] * st->np[1] * st->np[2];
   size_t nint = (size_t)P->n[0] * P->n[1] * P->n[2];
 
-  /* vmax = 1/sqrt(mu eps), eps = sigma/(2 omega0)  (Sec. 2.2 and Eq. 14) */
+  /* vmax = 1/sqrt(mu eps), eps = sigma/(2 omega0)  (Sec. 2.2 and Eq. 15) */
   double smin = P->sigma_min;
   if (smin <= 0) {
     smin = INFINITY;
@@ -578,7 +578,7 @@ int orc_forward(orc_problem *P)
   for (int c = 0; c < 12; ++c) st->psi[c] = P->pml ? calloc(st->ncell, sizeof(double)) : NULL;
   for (int c = 0; c < 6; ++c) if (!st->F[c]) { orc_state_free(st); return ORC_ENOMEM; }
 
-  /* Model extension into the pads by edge replication (Sec. 3.4, extend_model),
+  /* Model extension into the pads by edge replication (Sec. 3.8, extend_model),
    * then dt/eps = 2 omega0 dt / sigma. */
   int nbe = nb + ne;
   for (int c = 0; c < 3; ++c) {
@@ -638,7 +638,7 @@ int orc_forward(orc_problem *P)
         if (st_code) { free(rst); for (int c2 = 0; c2 < 3; ++c2) free(jw[c2]); orc_state_free(st); return st_code; }
       }
 
-  /* DTFT (Sec. 3.5, Eq. 19) with omega' = (1+i) sqrt(omega omega0) (Eq. 4) and,
+  /* DTFT (Sec. 3.5, Eq. 25) with omega' = (1+i) sqrt(omega omega0) (Eq. 4) and,
    * reading, the dt factor of the integral in Eq. 6 and these time labels:
    * E^{n+1} at (n+1) dt, H^{n+1/2} and J at (n+1/2) dt. */
   double complex *wp = malloc(sizeof(double complex) * (nf > 0 ? nf : 1));

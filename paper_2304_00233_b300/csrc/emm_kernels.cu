@@ -4,12 +4,12 @@
 //
 // One leapfrog step (Algorithm 1 without the airwave step) is two launches:
 //
-//   k_update_E<R>  curl H with D- rows and CPML memory (Eq. 13, 16-18), the
+//   k_update_E<R>  curl H with D- rows and CPML memory (Eq. 14, 22-24), the
 //                  electric source at t_{n+1/2}, E += dt/eps (curl H - J)
 //                  (Eq. 8); extra CTAs accumulate the receiver DTFT of
-//                  H^{n+1/2} (Eq. 19), which this launch only reads; interior
+//                  H^{n+1/2} (Eq. 25), which this launch only reads; interior
 //                  threads accumulate the volume DTFT of H^{n+1/2}.
-//   k_update_H<R>  curl E with D+ rows and CPML memory (Eq. 12, 16-18),
+//   k_update_H<R>  curl E with D+ rows and CPML memory (Eq. 13, 22-24),
 //                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
 //                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
 //
@@ -148,7 +148,7 @@ __device__ __forceinline__ size_t psi_at(int a, int s, int i, int j, int k, cons
   return (static_cast<size_t>(s) * np[1] + j) * np[0] + i;
 }
 
-// CPML update of one derivative d (Eq. 16-17, kappa = 1): psi <- b psi + a d
+// CPML update of one derivative d (Eq. 22-23, kappa = 1): psi <- b psi + a d
 // from the staged old value, stored back; returns d + psi.
 __device__ __forceinline__ float cpml_step(float d, float old, float *__restrict__ psi, size_t idx, float a,
                                            float b) {
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
-// the pads replicating the edge (model extension, Sec. 3.4), and the input
+// the pads replicating the edge (model extension, Sec. 3.8), and the input
 // check (finite, positive, >= sigma_min).
 __global__ void k_prepare(const float *__restrict__ sigma, float *ie0, float *ie1, float *ie2, int n0,
                           int n1, int n2, int np0, int np1, int np2, int pitch, int xshift, int nbe,

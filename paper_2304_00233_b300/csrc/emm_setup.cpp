@@ -104,7 +104,7 @@ double dmax_axis(const Axis &ax, int rd) {
   return best;
 }
 
-// CPML damping of Eq. 17-18 with kappa = 1.  For slab entry s the sample's
+// CPML damping of Eq. 23-24 with kappa = 1.  For slab entry s the sample's
 // depth xi into its layer is measured from the layer's inner face (X[nb] on
 // the low side, X[np-1-nb] on the high side); L is that face's thickness.
 void cpml_axis(const emm_grid *g, int axis, double vmax, double fmax, double dt, double *ab) {

@@ -9,9 +9,9 @@ Everything here is deterministic: grids are closed-form, random conductivity
 perturbations use ``numpy.random.default_rng`` with a fixed seed.
 
 Paper references (Yang, libEMM, arXiv 2304.00233):
-  * Sec. 3.7, Eq. 21-23: geometric-progression non-uniform grid and the fixed
+  * Sec. 3.7, Eq. 27-29: geometric-progression non-uniform grid and the fixed
     point iteration for its ratio q  -> ``create_nugrid``.
-  * Sec. 3.6, Eq. 20: medium homogenisation (arithmetic mean for the
+  * Sec. 3.6, Eq. 26: medium homogenisation (arithmetic mean for the
     tangential conductivity, harmonic mean for the normal one)
     -> ``staggered_conductivity``.
   * Sec. 5.6: the solver consumes three resistivity/conductivity cubes of size
@@ -39,10 +39,10 @@ __all__ = [
 def create_nugrid(n: int, length: float, dx: float, tol: float = 1e-15,
                   max_iter: int = 100000) -> np.ndarray:
     """n intervals (n+1 nodes) from 0 to ``length``, first interval ``dx``,
-    growing geometrically with ratio q (Eq. 21: L = dx (q^n - 1)/(q - 1)).
+    growing geometrically with ratio q (Eq. 27: L = dx (q^n - 1)/(q - 1)).
 
     q is found with the fixed-point iteration q <- (L/dx (q-1) + 1)^(1/n)
-    of Eq. 22-23, started from q = 1.1, in FP64 with a relative tolerance.
+    of Eq. 28-29, started from q = 1.1, in FP64 with a relative tolerance.
     When n*dx == L the grid is uniform and returned directly.  L < n*dx has no
     solution with q > 1 and raises ValueError.
     """
@@ -145,7 +145,7 @@ def cell_conductivity(model: LayeredModel, x: np.ndarray, y: np.ndarray,
     Inside each cell the z-range is cut at every layer/box boundary.  On each
     z piece the conductivity is averaged arithmetically over the cell's x-y
     face (box volume fraction).  sigma_h is the arithmetic mean of the pieces
-    over z, sigma_v the harmonic mean over z (Eq. 20: tangential = resistors in
+    over z, sigma_v the harmonic mean over z (Eq. 26: tangential = resistors in
     parallel, normal = resistors in series)."""
     nx, ny, nz = len(x) - 1, len(y) - 1, len(z) - 1
     sh = np.empty((nz, ny, nx))

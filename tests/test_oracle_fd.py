@@ -6,7 +6,7 @@ P2  uniform limit equals the textbook staggered coefficients (Appendix A),
     read from a golden fixture and re-derived here in exact rational arithmetic.
 P3  derivative error on a smooth stretched grid falls as h^(2r).
 P4  [V^T]^{-1} from unit vectors (Eq. 12) agrees with a dense LU inverse.
-P6  eta of Sec. 3.2 equals the von Neumann bound of Appendix A (Eq. A5 at the
+P6  eta of Sec. 3.2 equals the von Neumann bound of Appendix A (Eq. A8 at the
     Nyquist corner) on a uniform grid.
 """
 import math
@@ -142,7 +142,7 @@ def test_p4_vandermonde_vs_lu(m):
 @pytest.mark.parametrize("rd", [1, 2, 3, 4])
 def test_p6_eta_is_von_neumann_bound(rd):
     """On a uniform grid, eta = (1/2) v sqrt(sum D_max^2) equals the largest
-    sin(omega dt/2)/dt allowed by Eq. A5, i.e. max_k of
+    sin(omega dt/2)/dt allowed by Eq. A8, i.e. max_k of
     v sqrt(sum_a (sum_i c_i sin((i-1/2) k_a d_a)/d_a)^2)."""
     gold_c, _ = _golden()[rd]
     c = np.array([float(v) for v in gold_c])

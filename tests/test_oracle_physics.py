@@ -1,10 +1,10 @@
 """Pins of the oracle's time stepping, CPML, source, receivers and DTFT.
 
 P7  A discrete plane-wave eigenmode of the staggered leapfrog advances with the
-    frequency of the Appendix A dispersion relation (Eq. A5), every component,
+    frequency of the Appendix A dispersion relation (Eq. A8), every component,
     to rounding.  Pins curl signs, staggering, D+/D- pairing, the leapfrog
     order and eps = sigma / (2 omega0) (Sec. 2.2).
-P14 Constant fields: the DTFT (Eq. 19, with the dt of Eq. 6) equals the
+P14 Constant fields: the DTFT (Eq. 25, with the dt of Eq. 6) equals the
     closed-form geometric series, which pins the time labels of E (n+1) and
     H (n+1/2).
 P8  Homogeneous whole space: Green's functions (Eq. 7) against the analytic
@@ -59,7 +59,7 @@ def test_p7_plane_wave_eigenmode(rd):
     probe = oracle.forward(*axes, np.full((3, n, n, n), sigma), rd=rd, nb=nb, ne=ne,
                            omega0=omega0, nt=0, fmax=1.0, inject=False, pml=False)
     dt = probe["dt"]
-    s = 0.5 * v * dt * np.linalg.norm(K)       # sin(omega dt / 2), Eq. A5
+    s = 0.5 * v * dt * np.linalg.norm(K)       # sin(omega dt / 2), Eq. A8
     assert 0 < s < 1
     w = 2 * math.asin(s) / dt
     B = dt / (2 * MU0 * s) * np.cross(K, A)
