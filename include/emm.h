@@ -192,6 +192,36 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
  * are then undefined).  EMM_ECUDA if the copy fails. */
 int emm_status(const void *ws, int *status, emm_stream stream);
 
+/* Size of the scratch array that emm_forward_static works in. */
+#define EMM_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* emm_forward for callers that cannot allocate device memory: for instance a
+ * plug-in inside a host application that owns every device allocation and
+ * forbids its modules to call cudaMalloc, or code that must not call it at
+ * solve time because an allocation can synchronise the device.  The paper has
+ * no counterpart of this call; it computes what emm_forward computes.
+ *   Instead of a caller workspace it uses one file-scope device array of
+ *   EMM_STATIC_SCRATCH_BYTES (64 MiB) inside the library, which every GPU that
+ *   loads the library holds until the process exits.  It allocates nothing:
+ *   no cudaMalloc, no cudaFree, no allocating library routine.  The first
+ *   call on a device looks up that device's address of the array (the device
+ *   that is current at the call); make this first call on each device before
+ *   any stream capture.
+ *   Arguments sigma, rec_out, vol_out and stream are those of emm_forward
+ *   (device buffers the caller owns).  status: NULL, or a host int that, after
+ *   the call has synchronised `stream`, receives the device status word of
+ *   the run (EMM_OK, EMM_EDEVICE or EMM_ETIMEOUT, as emm_status reports it);
+ *   with status NULL the call returns before the GPU finishes.
+ *   Errors: those of emm_forward; EMM_EWORKSPACE when the problem needs more
+ *   than EMM_STATIC_SCRATCH_BYTES (emm_workspace_size gives the need), with
+ *   nothing enqueued; EMM_ECUDA if the address lookup fails.
+ *   Every call shares the one array and finds the previous call's contents in
+ *   it; the call clears what must start at zero.  Calls whose work overlaps
+ *   on the GPU (different streams, or several host threads) race on the array
+ *   and give undefined results: serialise them on one stream. */
+int emm_forward_static(const emm_grid *grid, const emm_survey *survey, const float *sigma,
+                       double *rec_out, double *vol_out, emm_stream stream, int *status);
+
 /* Static description of an error code (never NULL). */
 const char *emm_strerror(int code);
 

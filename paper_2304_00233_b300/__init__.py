@@ -33,7 +33,8 @@ TAB_NODES, TAB_HALF, TAB_DPLUS, TAB_DMINUS, TAB_SLAB_INT, TAB_SLAB_HALF = range(
 COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",
             "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
-            "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror")
+            "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
+            "emm_forward_static")
 
 
 class EmmError(RuntimeError):
@@ -94,6 +95,7 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_forward_timed": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V,
                                C.POINTER(_Timing)], C.c_int),
         "emm_status": ([V, _I, V], C.c_int),
+        "emm_forward_static": ([V, C.POINTER(_Survey), V, V, V, V, _I], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -301,6 +303,37 @@ def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int
         C.byref(t))
     _check(code, "emm_forward_timed")
     return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, total_ms=t.total_ms)
+
+
+def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None,
+                   wait: bool = True) -> Optional[int]:
+    """``emm_forward_static``: the forward run in the library's own static
+    device scratch (no device allocation by the call), for callers that may
+    not allocate.  ``rec`` (and ``vol`` when ``survey.volume``) are the
+    caller's CUDA float64 output tensors, shaped as ``Workspace.rec`` /
+    ``Workspace.vol``.  With ``wait`` the call synchronises the stream and
+    returns the device status word; otherwise it returns None at once."""
+    import torch
+    _check_sigma(grid, sigma)
+    nf = len(survey.freqs)
+    if not (rec.is_cuda and rec.dtype == torch.float64 and rec.is_contiguous()
+            and rec.numel() >= max(survey.nrec, 1) * 6 * nf * 2):
+        raise TypeError("rec must be a contiguous CUDA float64 tensor [nrec][6][nfreq][2]")
+    if survey.volume:
+        n1, n2, n3 = grid.n
+        if vol is None or not (vol.is_cuda and vol.dtype == torch.float64 and vol.is_contiguous()
+                               and vol.numel() == 6 * nf * n1 * n2 * n3 * 2):
+            raise TypeError("vol must be a contiguous CUDA float64 tensor [6][nfreq][n3][n2][n1][2]")
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    s, keep = survey._c()
+    st = C.c_int(-1)
+    code = load_library().emm_forward_static(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(rec.data_ptr()),
+        C.c_void_p(0 if vol is None else vol.data_ptr()), C.c_void_p(stream.cuda_stream),
+        C.byref(st) if wait else None)
+    _check(code, "emm_forward_static")
+    return st.value if wait else None
 
 
 def status(work: Workspace, stream=None) -> int:

@@ -44,6 +44,11 @@
 
 #include "emm_internal.h"
 
+// Scratch of emm_forward_static: one array per device for the process
+// lifetime.  In host code this name only stands for the symbol; its device
+// address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char emm_static_scratch[EMM_STATIC_SCRATCH_BYTES];
+
 namespace emm {
 namespace {
 
@@ -1077,6 +1082,26 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
+// Device address of emm_static_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+int static_scratch(void **ptr) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static void *addr[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return EMM_ECUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < kMaxDevices && addr[dev]) {
+    *ptr = addr[dev];
+    return EMM_OK;
+  }
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, emm_static_scratch) != cudaSuccess || !p) return EMM_ECUDA;
+  if (dev < kMaxDevices) addr[dev] = p;
+  *ptr = p;
+  return EMM_OK;
+}
+
 }  // namespace
 }  // namespace emm
 
@@ -1134,6 +1159,19 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   if (st == EMM_OK) cudaEventElapsedTime(&ms, t0, t1);
   timing->total_ms = ms;
   for (auto &e : all) cudaEventDestroy(e);
+  return st;
+}
+
+int emm_forward_static(const emm_grid *g, const emm_survey *s, const float *sigma, double *rec_out,
+                       double *vol_out, emm_stream stream, int *status) {
+  int st = emm::check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (emm::plan(g, s).total > EMM_STATIC_SCRATCH_BYTES) return EMM_EWORKSPACE;
+  void *ws = nullptr;
+  st = emm::static_scratch(&ws);
+  if (st != EMM_OK) return st;
+  st = emm::forward_impl(g, s, sigma, ws, EMM_STATIC_SCRATCH_BYTES, rec_out, vol_out, stream, nullptr);
+  if (st == EMM_OK && status) st = emm_status(ws, status, stream);
   return st;
 }
 
