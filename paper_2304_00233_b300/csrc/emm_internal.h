@@ -60,6 +60,7 @@ struct DevParams {
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
   float *psiE[6];            // CPML memory of curl H terms (E update)
   float *psiH[6];            // CPML memory of curl E terms (H update)
+  int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage ([0] psiE, [1] psiH)
   const float *cm[3], *cp[3];  // FD rows [npad][2rd]
   const float *pml[3];         // [4][2nb]: a_int, b_int, a_half, b_half
   // source

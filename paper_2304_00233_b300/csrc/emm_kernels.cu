@@ -54,14 +54,14 @@ namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
 constexpr int TY = 8;   // tile height (y)
-constexpr int NT = TX * TY;
-constexpr int ZC = 4;   // planes per CTA
+constexpr int ZC = 2;   // planes per CTA
+constexpr int NT = (TX / 4) * TY * ZC;  // threads: one per quad of 4 x-adjacent cells
 constexpr int XH = 4;   // x halo of the TMA boxes (>= R; keeps box x starts 16-byte aligned)
 constexpr int WX = TX + 2 * XH;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of the mbarrier wait
 
 // Resident CTAs per SM the register budget is sized for.
-__host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 3 : 2; }
+__host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 5 : 4; }
 
 // Shared-memory tiles of one CTA, for either half-step.  "zf" is the source
 // field with z and y halos (Hx / Ex), "xf" the one with z and x halos
@@ -74,7 +74,7 @@ struct Tiles {
   static constexpr int XF = ZQ * TY * WX;
   static constexpr int XY = ZC * YH * WX;
   static constexpr size_t BYTES = static_cast<size_t>(ZF + XF + XY) * 4;  // the three TMA boxes
-  static constexpr int PSI = 6 * ZC * NT;  // CPML memory staged per thread: [6 slots][ZC][NT]
+  static constexpr int PSI = 6 * NT * 4;  // CPML memory staged per thread: [6 slots][NT] float4
   static constexpr size_t ALL = BYTES + static_cast<size_t>(PSI) * 4;
 };
 template <int R>
@@ -96,12 +96,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// One test of phase `parity`; the thread may be suspended for up to
+// kSuspendNs while the phase is incomplete (it resumes when it completes).
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -127,9 +130,9 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
-// 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// 16-byte asynchronous global -> shared copy, L2 only (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -143,58 +146,6 @@ __device__ __forceinline__ int slab_int(int i, int np, int nb) {
 }
 __device__ __forceinline__ int slab_half(int i, int np, int nb) {
   return i < nb ? i : ((i >= np - 1 - nb && i <= np - 2) ? nb + np - 2 - i : -1);
-}
-
-// CPML memory array of a derivative along axis a: the slab (2nb entries)
-// replaces that axis.  x: [np2][np1][2nb], y: [np2][2nb][np0], z: [2nb][np1][np0].
-__device__ __forceinline__ size_t psi_at(int a, int s, int i, int j, int k, const int *np, int nb2) {
-  if (a == 0) return (static_cast<size_t>(k) * np[1] + j) * nb2 + s;
-  if (a == 1) return (static_cast<size_t>(k) * nb2 + s) * np[0] + i;
-  return (static_cast<size_t>(s) * np[1] + j) * np[0] + i;
-}
-
-// CPML update of one derivative d (Eq. 22-23, kappa = 1): psi <- b psi + a d
-// from the staged old value, stored back; returns d + psi.
-__device__ __forceinline__ float cpml_step(float d, float old, float *__restrict__ psi, size_t idx, float a,
-                                           float b) {
-  const float v = fmaf(b, old, a * d);
-  psi[idx] = v;
-  return d + v;
-}
-
-// Stage this thread's CPML memory of planes k0 .. k0+ZC-1 into shared memory
-// slots [slot][c][thread] with asynchronous copies.  Slots follow the psi
-// arrays: 0 (y), 1 (z), 2 (z), 3 (x), 4 (x), 5 (y) derivative.  sx, sy are
-// the x / y slab entries of the column (-1 outside), slab_k(k) the z entry.
-template <class SlabK>
-__device__ __forceinline__ void stage_psi(float *ps, float *const *psi, const DevParams &p, int i, int j, int k0,
-                                          int sx, int sy, SlabK slab_k) {
-  constexpr int S = ZC * NT;
-  const int nb2 = 2 * p.nb;
-#pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = k0 + c;
-    if (k < 0) continue;
-    if (k >= p.np[2]) break;
-    const int sz = slab_k(k);
-    float *d = ps + c * NT + threadIdx.x;
-    if (sy >= 0) {
-      const size_t id = psi_at(1, sy, i, j, k, p.np, nb2);
-      cp_async4(d, psi[0] + id);
-      cp_async4(d + 5 * S, psi[5] + id);
-    }
-    if (sz >= 0) {
-      const size_t id = psi_at(2, sz, i, j, k, p.np, nb2);
-      cp_async4(d + S, psi[1] + id);
-      cp_async4(d + 2 * S, psi[2] + id);
-    }
-    if (sx >= 0) {
-      const size_t id = psi_at(0, sx, i, j, k, p.np, nb2);
-      cp_async4(d + 3 * S, psi[3] + id);
-      cp_async4(d + 4 * S, psi[4] + id);
-    }
-  }
-  cp_async_commit();
 }
 
 // Error-free accumulation (hi, lo) += v  (Knuth's TwoSum).
@@ -249,25 +200,20 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 
 // ---------------------------------------------------------------------------
 // Common CTA prologue: origin of the tile, the TMA copies of the three source
-// fields, and the bounded wait for them.
+// fields, and the bounded wait for them.  The grid is 3-D: (tiles_x,
+// tiles_y, tiles_z) stencil CTAs, then extra z layers of receiver CTAs.
 // ---------------------------------------------------------------------------
 struct Origin {
   int i0, j0, k0;
 };
-__device__ __forceinline__ Origin origin_of(const DevParams &p, int b) {
-  return Origin{p.org[0] + (b % p.tiles_x) * TX, p.org[1] + ((b / p.tiles_x) % p.tiles_y) * TY,
-                p.org[2] + (b / (p.tiles_x * p.tiles_y)) * ZC};
+__device__ __forceinline__ Origin origin_of(const DevParams &p) {
+  return Origin{p.org[0] + static_cast<int>(blockIdx.x) * TX, p.org[1] + static_cast<int>(blockIdx.y) * TY,
+                p.org[2] + static_cast<int>(blockIdx.z) * ZC};
 }
-
-// Shared-memory views of the three tiles (see Tiles).
-template <int R>
-struct View {
-  using T = Tiles<R>;
-  const float *s;
-  __device__ float zf(int pz, int y, int x) const { return s[(pz * T::YH + y) * TX + x]; }
-  __device__ float xf(int pz, int y, int x) const { return s[T::ZF + (pz * TY + y) * WX + x]; }
-  __device__ float xy(int pz, int y, int x) const { return s[T::ZF + T::XF + (pz * T::YH + y) * WX + x]; }
-};
+__device__ __forceinline__ int receiver_block(const DevParams &p) {
+  return ((static_cast<int>(blockIdx.z) - p.tiles_z) * p.tiles_y + static_cast<int>(blockIdx.y)) * p.tiles_x +
+         static_cast<int>(blockIdx.x);
+}
 
 // Thread 0: initialise the CTA's mbarrier and issue the three copies.  The
 // z-halo boxes start `lead` planes from k0 (-R for D-, -R+1 for D+).
@@ -282,20 +228,19 @@ __device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t
   tma_load_3d(s + T::ZF + T::XF, &tm.m[2], bar, o.i0 - XH, o.j0 - R, o.k0);
 }
 
-// All threads: wait for the copies.  False (after setting the status word
-// and draining the copies, both bounded) if the wait ran out anywhere.
+// Wait for the copies: thread 0 (which initialised the barrier and issued
+// them) waits on the mbarrier, bounded; the other threads wait at the CTA
+// barrier that follows, which orders the landed tiles before their reads.
+// False, for the whole CTA, if the wait ran out (thread 0 has then set the
+// status word and drained the copies, again bounded).
 __device__ __forceinline__ bool tiles_ready(const DevParams &p, uint64_t *bar) {
-  __syncthreads();  // the barrier is initialised
-  const bool ok = mbar_wait_bounded(bar, 0);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      atomicExch(p.status, EMM_ETIMEOUT);
-      mbar_wait_bounded(bar, 0);
-    }
-    __syncthreads();
-    return false;
+  int late = 0;
+  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0)) {
+    late = 1;
+    atomicExch(p.status, EMM_ETIMEOUT);
+    mbar_wait_bounded(bar, 0);
   }
-  return true;
+  return !__syncthreads_or(late);
 }
 
 __device__ __forceinline__ float *smem_tiles(unsigned char *raw) {
@@ -319,6 +264,157 @@ __device__ __forceinline__ void source_term(const DevParams &p, int c, int i, in
 }
 
 // ---------------------------------------------------------------------------
+// Thread layout of a stencil CTA: the tile is 32 (x) x 8 (y) x ZC (z) cells;
+// thread t owns the 4 x-adjacent cells ("quad") q = t % 8 of row r = t / 8 % 8
+// in plane c = t / 64.  A quad starts on a 16-byte boundary of every field
+// row, so its samples move as one float4 and its taps as float4 shared-memory
+// reads; derivatives along y and z use paired FP32 FMAs (f32x2).
+// ---------------------------------------------------------------------------
+
+struct Quad {
+  int q, r, c;   // quad, row, plane inside the tile
+  int i, j, k;   // grid coordinates of the first cell
+};
+__device__ __forceinline__ Quad quad_of(const Origin &o) {
+  const int t = threadIdx.x;
+  Quad u;
+  u.q = t & 7;
+  u.r = (t >> 3) & 7;
+  u.c = t >> 6;
+  u.i = o.i0 + 4 * u.q;
+  u.j = o.j0 + u.r;
+  u.k = o.k0 + u.c;
+  return u;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// acc[0..3] += coef * v[0..3], two cells per instruction.
+struct Acc4 {
+  float2 lo, hi;
+  __device__ __forceinline__ Acc4() : lo(make_float2(0.f, 0.f)), hi(make_float2(0.f, 0.f)) {}
+  __device__ __forceinline__ void fma(float coef, const float4 &v) {
+    lo = fma2(make_float2(coef, coef), make_float2(v.x, v.y), lo);
+    hi = fma2(make_float2(coef, coef), make_float2(v.z, v.w), hi);
+  }
+  __device__ __forceinline__ float operator[](int e) const {
+    return e == 0 ? lo.x : (e == 1 ? lo.y : (e == 2 ? hi.x : hi.y));
+  }
+};
+
+__device__ __forceinline__ float get(const float4 &v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void put(float4 &v, int e, float x) {
+  if (e == 0) v.x = x;
+  else if (e == 1) v.y = x;
+  else if (e == 2) v.z = x;
+  else v.w = x;
+}
+
+// Shared-memory views of the three tiles (see Tiles), as float4 at quad
+// granularity: x is a sample column of the box, a multiple of 4.
+template <int R>
+struct View {
+  using T = Tiles<R>;
+  const float *s;
+  __device__ float4 zf(int pz, int y, int x) const {
+    return *reinterpret_cast<const float4 *>(s + (pz * T::YH + y) * TX + x);
+  }
+  __device__ float4 xf(int pz, int y, int x) const {
+    return *reinterpret_cast<const float4 *>(s + T::ZF + (pz * TY + y) * WX + x);
+  }
+  __device__ float4 xy(int pz, int y, int x) const {
+    return *reinterpret_cast<const float4 *>(s + T::ZF + T::XF + (pz * T::YH + y) * WX + x);
+  }
+};
+
+// A row of 12 samples (box columns 4q .. 4q+11) for the x derivatives of a
+// quad: cell e of the quad sits at box column 4q + XH + e.
+struct Row12 {
+  float v[12];
+  __device__ __forceinline__ void load(float4 a, float4 b, float4 c) {
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// CPML memory.  Arrays of derivatives along y and z keep x innermost with the
+// field row geometry: y: [np2][2nb][pitch], z: [2nb][np1][pitch] (sample i at
+// column i of a row shifted like the fields).  Arrays of derivatives along x
+// are [np2][np1][wx] with the near slab at entries 0..nb-1 and the far slab
+// at hx + (i - first far sample), hx chosen so that a quad starts on a
+// 16-byte boundary there too and no quad of one slab touches the other's
+// entries.  The CPML coefficients use the slab entry of Sec. 3.4 (mirrored on
+// the far face); only the storage differs.
+// ---------------------------------------------------------------------------
+struct PsiX {
+  int hx, wx, far0;  // storage offset of the far slab, row width, first far sample
+};
+
+// Element of the quad's first cell in a y-, z- or x-derivative CPML array.
+__device__ __forceinline__ size_t psi_y_at(const DevParams &p, const Quad &u, int sy) {
+  return (static_cast<size_t>(u.k) * static_cast<size_t>(2 * p.nb) + static_cast<size_t>(sy)) * p.pitch +
+         static_cast<size_t>(u.i);
+}
+__device__ __forceinline__ size_t psi_z_at(const DevParams &p, const Quad &u, int sz) {
+  return (static_cast<size_t>(sz) * p.np[1] + static_cast<size_t>(u.j)) * p.pitch + static_cast<size_t>(u.i);
+}
+__device__ __forceinline__ size_t psi_x_at(const DevParams &p, const Quad &u, int xs, int wx) {
+  return (static_cast<size_t>(u.k) * p.np[1] + static_cast<size_t>(u.j)) * wx + static_cast<size_t>(xs);
+}
+
+// Stage this thread's CPML memory (float4 per array) into shared-memory
+// slots [slot][thread] with 16-byte asynchronous copies.  Slots: 0 (y) and
+// 1 (z) of the first component, 2 (z) and 3 (x) of the second, 4 (x) and
+// 5 (y) of the third, matching psi[0..5].  sy, sz: slab entries of the row and
+// plane (-1 outside); xs: storage column of the quad's first cell in the
+// x-derivative arrays, or -1 if the quad does not touch an x slab.
+__device__ __forceinline__ void stage_psi(float4 *ps, float *const *psi, const DevParams &p, const Quad &u, int sy,
+                                          int sz, int xs, int wx) {
+  float4 *d = ps + threadIdx.x;
+  if (sy >= 0) {
+    const size_t id = psi_y_at(p, u, sy);
+    cp_async16(d, psi[0] + id);
+    cp_async16(d + 5 * NT, psi[5] + id);
+  }
+  if (sz >= 0) {
+    const size_t id = psi_z_at(p, u, sz);
+    cp_async16(d + 1 * NT, psi[1] + id);
+    cp_async16(d + 2 * NT, psi[2] + id);
+  }
+  if (xs >= 0) {
+    const size_t id = psi_x_at(p, u, xs, wx);
+    cp_async16(d + 3 * NT, psi[3] + id);
+    cp_async16(d + 4 * NT, psi[4] + id);
+  }
+}
+
+// Storage column of a quad starting at sample i in an x-derivative array, or
+// -1 if none of its cells lies in an x slab (slab entries: sample < nb, or
+// far0 <= sample <= last).
+__device__ __forceinline__ int psi_x_column(int i, int nb, const PsiX &x, int last) {
+  if (i < nb) return i;
+  if (i + 3 >= x.far0 && i <= last) return x.hx + (i - x.far0);
+  return -1;
+}
+
+// One CPML update (Eq. 22-23, kappa = 1): psi <- b psi + a d; d + psi.
+__device__ __forceinline__ float cpml1(float d, float &psi, float a, float b) {
+  psi = fmaf(b, psi, a * d);
+  return d + psi;
+}
+
+// ---------------------------------------------------------------------------
 // E half-step: E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J^{n+1/2})
 // ---------------------------------------------------------------------------
 // Is every cell of the CTA inside the CPML-free region where all D- rows
@@ -329,111 +425,173 @@ __device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, 
          o.k0 >= m && o.k0 + ZC - 1 <= p.np[2] - 1 - m;
 }
 
-// The ZC planes of one column.  FAST: an interior CTA without the source,
-// where every validity test is true and every slab test false.
+// One quad of the E update.  FAST: an interior CTA without the source, where
+// every validity test is true and every slab test false.
 template <int R, bool VOL, bool FAST>
-__device__ __forceinline__ void e_planes(const DevParams &p, const View<R> &v, const Origin &o, int tx, int ty,
-                                         const float (&e)[3][ZC], const float (&w)[3][ZC], const float *ps,
-                                         int n, bool src) {
+__device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, const Quad &u, const float4 (&e)[3],
+                                       const float4 (&w)[3], const float4 *ps, int n, bool src) {
   constexpr int M = 2 * R;
-  const int i = o.i0 + tx, j = o.j0 + ty;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
-  const bool dm_i = FAST || (i >= R && i <= np0 - 1 - R), dm_j = FAST || (j >= R && j <= np1 - 1 - R);
-  const int si = FAST ? -1 : slab_int(i, np0, nb), sj = FAST ? -1 : slab_int(j, np1, nb);
-  float cx[M], cy[M];
+  const int q4 = 4 * u.q, t = threadIdx.x;
+  float cy[M], cz[M], cx[4][M];
 #pragma unroll
-  for (int q = 0; q < M; ++q) {
-    cx[q] = dm_i ? __ldg(p.cm[0] + i * M + q) : 0.f;
-    cy[q] = dm_j ? __ldg(p.cm[1] + j * M + q) : 0.f;
+  for (int m = 0; m < M; ++m) {
+    cy[m] = __ldg(p.cm[1] + u.j * M + m);
+    cz[m] = __ldg(p.cm[2] + u.k * M + m);
   }
+  {
+    const float4 *c4 = reinterpret_cast<const float4 *>(p.cm[0] + static_cast<size_t>(u.i) * M);
+#pragma unroll
+    for (int f = 0; f < M; ++f) {
+      const float4 a = __ldg(c4 + f);
+      cx[(4 * f) / M][(4 * f) % M] = a.x;
+      cx[(4 * f + 1) / M][(4 * f + 1) % M] = a.y;
+      cx[(4 * f + 2) / M][(4 * f + 2) % M] = a.z;
+      cx[(4 * f + 3) / M][(4 * f + 3) % M] = a.w;
+    }
+  }
+  const bool dm_j = FAST || (u.j >= R && u.j <= np1 - 1 - R);
+  const bool dm_k = FAST || (u.k >= R && u.k <= np2 - 1 - R);
+  bool dm_i[4];
+  int si[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    dm_i[c] = FAST || (u.i + c >= R && u.i + c <= np0 - 1 - R);
+    si[c] = FAST ? -1 : slab_int(u.i + c, np0, nb);
+  }
+  const int sj = FAST ? -1 : slab_int(u.j, np1, nb), sk = FAST ? -1 : slab_int(u.k, np2, nb);
+  const int xs = FAST ? -1 : psi_x_column(u.i, nb, PsiX{p.psx_hx[0], p.psx_wx[0], p.psx_far0[0]}, np0 - 1);
   const float amp = FAST ? 0.f : __ldg(p.amp + n);
-  const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-  const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+  float4 out[3] = {e[0], e[1], e[2]};
 
+  // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
+  {
+    Acc4 dy, dz;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = o.k0 + c;
+    for (int m = 0; m < M; ++m) {
+      dy.fma(cy[m], v.xy(u.c, u.r + m, q4 + XH));
+      dz.fma(cz[m], v.xf(u.c + m, u.r, q4 + XH));
+    }
+    float4 py = FAST ? float4{} : ps[0 * NT + t], pz = FAST ? float4{} : ps[1 * NT + t];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (u.i + c <= np0 - 2 && dm_j && dm_k))) continue;
+      float a = dy[c], b = dz[c];
+      if (!FAST) {
+        if (sj >= 0) {
+          float s = get(py, c);
+          a = cpml1(a, s, p.pml[1][sj], p.pml[1][2 * nb + sj]);
+          put(py, c, s);
+        }
+        if (sk >= 0) {
+          float s = get(pz, c);
+          b = cpml1(b, s, p.pml[2][sk], p.pml[2][2 * nb + sk]);
+          put(pz, c, s);
+        }
+      }
+      float curl = a - b;
+      if (!FAST && src) source_term<R>(p, 0, u.i + c, u.j, u.k, amp, curl);
+      put(out[0], c, fmaf(get(w[0], c), curl, get(e[0], c)));
+    }
     if (!FAST) {
-      if (k < 0) continue;
-      if (k >= np2) break;
+      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiE[0] + psi_y_at(p, u, sj)) = py;
+      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiE[1] + psi_z_at(p, u, sk)) = pz;
     }
-    const size_t id = static_cast<size_t>(k) * p.plane + col;
-    const bool dm_k = FAST || (k >= R && k <= np2 - 1 - R);
-    const int sk = FAST ? -1 : slab_int(k, np2, nb);
-    float cz[M];
+  }
+  // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
+  {
+    Acc4 dz;
 #pragma unroll
-    for (int q = 0; q < M; ++q) cz[q] = dm_k ? __ldg(p.cm[2] + k * M + q) : 0.f;
-    // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
-    if (FAST || (i <= np0 - 2 && dm_j && dm_k)) {
-      float dy = 0.f, dz = 0.f;
+    for (int m = 0; m < M; ++m) dz.fma(cz[m], v.zf(u.c + m, u.r + R, q4));
+    Row12 hz;
+    hz.load(v.xy(u.c, u.r + R, q4), v.xy(u.c, u.r + R, q4 + 4), v.xy(u.c, u.r + R, q4 + 8));
+    float4 pz = FAST ? float4{} : ps[2 * NT + t], px = FAST ? float4{} : ps[3 * NT + t];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dy = fmaf(cy[q], v.xy(c, ty + q, tx + XH), dy);
-        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
-      }
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (u.j <= np1 - 2 && dm_i[c] && dm_k))) continue;
+      float dx = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) dx = fmaf(cx[c][m], hz.v[XH + c - R + m], dx);
+      float b = dz[c];
       if (!FAST) {
-        if (sj >= 0)
-          dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiE[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                         p.pml[1][sj], p.pml[1][2 * nb + sj]);
-        if (sk >= 0)
-          dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiE[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                         p.pml[2][sk], p.pml[2][2 * nb + sk]);
+        if (sk >= 0) {
+          float s = get(pz, c);
+          b = cpml1(b, s, p.pml[2][sk], p.pml[2][2 * nb + sk]);
+          put(pz, c, s);
+        }
+        if (si[c] >= 0) {
+          float s = get(px, c);
+          dx = cpml1(dx, s, p.pml[0][si[c]], p.pml[0][2 * nb + si[c]]);
+          put(px, c, s);
+        }
       }
-      float curl = dy - dz;
-      if (!FAST && src) source_term<R>(p, 0, i, j, k, amp, curl);
-      p.E[0][id] = fmaf(w[0][c], curl, e[0][c]);
+      float curl = b - dx;
+      if (!FAST && src) source_term<R>(p, 1, u.i + c, u.j, u.k, amp, curl);
+      put(out[1], c, fmaf(get(w[1], c), curl, get(e[1], c)));
     }
-    // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
-    if (FAST || (j <= np1 - 2 && dm_i && dm_k)) {
-      float dz = 0.f, dx = 0.f;
+    if (!FAST) {
+      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiE[2] + psi_z_at(p, u, sk)) = pz;
+      if (xs >= 0)
+        *reinterpret_cast<float4 *>(p.psiE[3] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
+    }
+  }
+  // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
+  {
+    Acc4 dy;
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
-        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + q), dx);
-      }
-      if (!FAST) {
-        if (sk >= 0)
-          dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiE[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                         p.pml[2][sk], p.pml[2][2 * nb + sk]);
-        if (si >= 0)
-          dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiE[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                         p.pml[0][si], p.pml[0][2 * nb + si]);
-      }
-      float curl = dz - dx;
-      if (!FAST && src) source_term<R>(p, 1, i, j, k, amp, curl);
-      p.E[1][id] = fmaf(w[1][c], curl, e[1][c]);
-    }
-    // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
-    if (FAST || (dm_i && dm_j && k <= np2 - 2)) {
-      float dx = 0.f, dy = 0.f;
+    for (int m = 0; m < M; ++m) dy.fma(cy[m], v.zf(u.c + R, u.r + m, q4));
+    Row12 hy;
+    hy.load(v.xf(u.c + R, u.r, q4), v.xf(u.c + R, u.r, q4 + 4), v.xf(u.c + R, u.r, q4 + 8));
+    float4 px = FAST ? float4{} : ps[4 * NT + t], py = FAST ? float4{} : ps[5 * NT + t];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dx = fmaf(cx[q], v.xf(c + R, ty, tx + XH - R + q), dx);
-        dy = fmaf(cy[q], v.zf(c + R, ty + q, tx), dy);
-      }
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (dm_i[c] && dm_j && u.k <= np2 - 2))) continue;
+      float dx = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) dx = fmaf(cx[c][m], hy.v[XH + c - R + m], dx);
+      float b = dy[c];
       if (!FAST) {
-        if (si >= 0)
-          dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiE[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                         p.pml[0][si], p.pml[0][2 * nb + si]);
-        if (sj >= 0)
-          dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiE[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                         p.pml[1][sj], p.pml[1][2 * nb + sj]);
+        if (si[c] >= 0) {
+          float s = get(px, c);
+          dx = cpml1(dx, s, p.pml[0][si[c]], p.pml[0][2 * nb + si[c]]);
+          put(px, c, s);
+        }
+        if (sj >= 0) {
+          float s = get(py, c);
+          b = cpml1(b, s, p.pml[1][sj], p.pml[1][2 * nb + sj]);
+          put(py, c, s);
+        }
       }
-      float curl = dx - dy;
-      if (!FAST && src) source_term<R>(p, 2, i, j, k, amp, curl);
-      p.E[2][id] = fmaf(w[2][c], curl, e[2][c]);
+      float curl = dx - b;
+      if (!FAST && src) source_term<R>(p, 2, u.i + c, u.j, u.k, amp, curl);
+      put(out[2], c, fmaf(get(w[2], c), curl, get(e[2], c)));
     }
-    // volume DTFT of H^{n+1/2}
-    if (VOL) {
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
+    if (!FAST) {
+      if (xs >= 0)
+        *reinterpret_cast<float4 *>(p.psiE[4] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
+      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiE[5] + psi_y_at(p, u, sj)) = py;
+    }
+  }
+  const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(p.E[a] + id) = out[a];
+
+  // volume DTFT of H^{n+1/2}
+  if (VOL) {
+    const int jj = u.j - p.nbe, kk = u.k - p.nbe;
+    if (jj >= 0 && jj < p.n[1] && kk >= 0 && kk < p.n[2]) {
+      const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+      const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+      const float4 hx = v.zf(u.c + R, u.r + R, q4), hy = v.xf(u.c + R, u.r, q4 + XH),
+                   hz = v.xy(u.c, u.r + R, q4 + XH);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ii = u.i + c - p.nbe;
+        if (ii < 0 || ii >= p.n[0]) continue;
         const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 3, lin, nint, facH, v.zf(c + R, ty + R, tx));
-        volume_accumulate(p, 4, lin, nint, facH, v.xf(c + R, ty, tx + XH));
-        volume_accumulate(p, 5, lin, nint, facH, v.xy(c, ty + R, tx + XH));
+        volume_accumulate(p, 3, lin, nint, facH, get(hx, c));
+        volume_accumulate(p, 4, lin, nint, facH, get(hy, c));
+        volume_accumulate(p, 5, lin, nint, facH, get(hz, c));
       }
     }
   }
@@ -442,49 +600,41 @@ __device__ __forceinline__ void e_planes(const DevParams &p, const View<R> &v, c
 template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
-    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
+  if (static_cast<int>(blockIdx.z) >= p.tiles_z) {
+    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of(p, blockIdx.x);
+  const Origin o = origin_of(p);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = o.i0 + tx, j = o.j0 + ty;
+  const Quad u = quad_of(o);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const bool in_ij = i >= 0 && i < np0 && j >= 0 && j < np1;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
+  const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
   // this thread's own samples, loaded while the copies are in flight
-  float e[3][ZC], w[3][ZC];
+  float4 e[3], w[3];
+  const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = o.k0 + c;
-    const bool ok = in_ij && k >= 0 && k < np2;
-    const size_t id = static_cast<size_t>(k) * p.plane + col;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      e[a][c] = ok ? p.E[a][id] : 0.f;
-      w[a][c] = ok ? __ldg(p.ie[a] + id) : 0.f;
-    }
+  for (int a = 0; a < 3; ++a) {
+    e[a] = live ? *reinterpret_cast<const float4 *>(p.E[a] + id) : float4{};
+    w[a] = live ? __ldg(reinterpret_cast<const float4 *>(p.ie[a] + id)) : float4{};
   }
   const bool src = cta_has_source(p, o);
   const bool fast = !src && interior_E(p, o, R);
-  float *ps = s + Tiles<R>::BYTES / 4;
-  if (!fast && in_ij)
-    stage_psi(ps, p.psiE, p, i, j, o.k0, slab_int(i, np0, nb), slab_int(j, np1, nb),
-              [&](int k) { return slab_int(k, np2, nb); });
-  else
-    cp_async_commit();
+  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
+  if (!fast && live)
+    stage_psi(ps, p.psiE, p, u, slab_int(u.j, np1, nb), slab_int(u.k, np2, nb),
+              psi_x_column(u.i, nb, PsiX{p.psx_hx[0], p.psx_wx[0], p.psx_far0[0]}, np0 - 1), p.psx_wx[0]);
+  cp_async_commit();
   cp_async_wait_all();
-  if (!tiles_ready(p, bar) || !in_ij) return;
+  if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    e_planes<R, VOL, true>(p, v, o, tx, ty, e, w, ps, n, false);
+    e_quad<R, VOL, true>(p, v, u, e, w, ps, n, false);
   else
-    e_planes<R, VOL, false>(p, v, o, tx, ty, e, w, ps, n, src);
+    e_quad<R, VOL, false>(p, v, u, e, w, ps, n, src);
 }
 
 // ---------------------------------------------------------------------------
@@ -500,101 +650,165 @@ __device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, 
 }
 
 template <int R, bool VOL, bool FAST>
-__device__ __forceinline__ void h_planes(const DevParams &p, const View<R> &v, const Origin &o, int tx, int ty,
-                                         const float (&h)[3][ZC], const float *ps, int n) {
+__device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, const Quad &u, const float4 (&h)[3],
+                                       const float4 *ps, int n) {
   constexpr int M = 2 * R;
-  const int i = o.i0 + tx, j = o.j0 + ty;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
-  const bool dp_i = FAST || (i >= R - 1 && i <= np0 - 1 - R), dp_j = FAST || (j >= R - 1 && j <= np1 - 1 - R);
-  const int si = FAST ? -1 : slab_half(i, np0, nb), sj = FAST ? -1 : slab_half(j, np1, nb);
-  float cx[M], cy[M];
+  const int q4 = 4 * u.q, t = threadIdx.x;
+  float cy[M], cz[M], cx[4][M];
 #pragma unroll
-  for (int q = 0; q < M; ++q) {
-    cx[q] = dp_i ? __ldg(p.cp[0] + i * M + q) : 0.f;
-    cy[q] = dp_j ? __ldg(p.cp[1] + j * M + q) : 0.f;
+  for (int m = 0; m < M; ++m) {
+    cy[m] = __ldg(p.cp[1] + u.j * M + m);
+    cz[m] = __ldg(p.cp[2] + u.k * M + m);
   }
+  {
+    const float4 *c4 = reinterpret_cast<const float4 *>(p.cp[0] + static_cast<size_t>(u.i) * M);
+#pragma unroll
+    for (int f = 0; f < M; ++f) {
+      const float4 a = __ldg(c4 + f);
+      cx[(4 * f) / M][(4 * f) % M] = a.x;
+      cx[(4 * f + 1) / M][(4 * f + 1) % M] = a.y;
+      cx[(4 * f + 2) / M][(4 * f + 2) % M] = a.z;
+      cx[(4 * f + 3) / M][(4 * f + 3) % M] = a.w;
+    }
+  }
+  const bool dp_j = FAST || (u.j >= R - 1 && u.j <= np1 - 1 - R);
+  const bool dp_k = FAST || (u.k >= R - 1 && u.k <= np2 - 1 - R);
+  bool dp_i[4], in_i[4];
+  int si[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    dp_i[c] = FAST || (u.i + c >= R - 1 && u.i + c <= np0 - 1 - R);
+    in_i[c] = FAST || (u.i + c < np0);
+    si[c] = FAST ? -1 : slab_half(u.i + c, np0, nb);
+  }
+  const int sj = FAST ? -1 : slab_half(u.j, np1, nb), sk = FAST ? -1 : slab_half(u.k, np2, nb);
+  const int xs = FAST ? -1 : psi_x_column(u.i, nb, PsiX{p.psx_hx[1], p.psx_wx[1], p.psx_far0[1]}, np0 - 2);
   const float dt_mu = p.dt_mu;
-  const int ii = i - p.nbe, jj = j - p.nbe;
-  const bool int_ij = VOL && ii >= 0 && ii < p.n[0] && jj >= 0 && jj < p.n[1];
-  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-  const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
+  float4 out[3] = {h[0], h[1], h[2]};
 
+  // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
+  {
+    Acc4 dy, dz;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = o.k0 + c;
+    for (int m = 0; m < M; ++m) {
+      dy.fma(cy[m], v.xy(u.c, u.r + m + 1, q4 + XH));
+      dz.fma(cz[m], v.xf(u.c + m, u.r, q4 + XH));
+    }
+    float4 py = FAST ? float4{} : ps[0 * NT + t], pz = FAST ? float4{} : ps[1 * NT + t];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (in_i[c] && dp_j && dp_k))) continue;
+      float a = dy[c], b = dz[c];
+      if (!FAST) {
+        if (sj >= 0) {
+          float s = get(py, c);
+          a = cpml1(a, s, p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+          put(py, c, s);
+        }
+        if (sk >= 0) {
+          float s = get(pz, c);
+          b = cpml1(b, s, p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+          put(pz, c, s);
+        }
+      }
+      put(out[0], c, fmaf(-dt_mu, a - b, get(h[0], c)));
+    }
     if (!FAST) {
-      if (k < 0) continue;
-      if (k >= np2) break;
+      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiH[0] + psi_y_at(p, u, sj)) = py;
+      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiH[1] + psi_z_at(p, u, sk)) = pz;
     }
-    const size_t id = static_cast<size_t>(k) * p.plane + col;
-    const bool dp_k = FAST || (k >= R - 1 && k <= np2 - 1 - R);
-    const int sk = FAST ? -1 : slab_half(k, np2, nb);
-    float cz[M];
+  }
+  // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
+  {
+    Acc4 dz;
 #pragma unroll
-    for (int q = 0; q < M; ++q) cz[q] = dp_k ? __ldg(p.cp[2] + k * M + q) : 0.f;
-    // Hx at (i, j+1/2, k+1/2): D+_y Ez - D+_z Ey
-    if (FAST || (dp_j && dp_k)) {
-      float dy = 0.f, dz = 0.f;
+    for (int m = 0; m < M; ++m) dz.fma(cz[m], v.zf(u.c + m, u.r + R, q4));
+    Row12 ez;
+    ez.load(v.xy(u.c, u.r + R, q4), v.xy(u.c, u.r + R, q4 + 4), v.xy(u.c, u.r + R, q4 + 8));
+    float4 pz = FAST ? float4{} : ps[2 * NT + t], px = FAST ? float4{} : ps[3 * NT + t];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dy = fmaf(cy[q], v.xy(c, ty + q + 1, tx + XH), dy);
-        dz = fmaf(cz[q], v.xf(c + q, ty, tx + XH), dz);
-      }
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (dp_i[c] && dp_k))) continue;
+      float dx = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) dx = fmaf(cx[c][m], ez.v[XH + c - R + 1 + m], dx);
+      float b = dz[c];
       if (!FAST) {
-        if (sj >= 0)
-          dy = cpml_step(dy, ps[(0 * ZC + c) * NT + threadIdx.x], p.psiH[0], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                         p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
-        if (sk >= 0)
-          dz = cpml_step(dz, ps[(1 * ZC + c) * NT + threadIdx.x], p.psiH[1], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                         p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+        if (sk >= 0) {
+          float s = get(pz, c);
+          b = cpml1(b, s, p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
+          put(pz, c, s);
+        }
+        if (si[c] >= 0) {
+          float s = get(px, c);
+          dx = cpml1(dx, s, p.pml[0][4 * nb + si[c]], p.pml[0][6 * nb + si[c]]);
+          put(px, c, s);
+        }
       }
-      p.H[0][id] = fmaf(-dt_mu, dy - dz, h[0][c]);
+      put(out[1], c, fmaf(-dt_mu, b - dx, get(h[1], c)));
     }
-    // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
-    if (FAST || (dp_i && dp_k)) {
-      float dz = 0.f, dx = 0.f;
+    if (!FAST) {
+      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiH[2] + psi_z_at(p, u, sk)) = pz;
+      if (xs >= 0)
+        *reinterpret_cast<float4 *>(p.psiH[3] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
+    }
+  }
+  // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
+  {
+    Acc4 dy;
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dz = fmaf(cz[q], v.zf(c + q, ty + R, tx), dz);
-        dx = fmaf(cx[q], v.xy(c, ty + R, tx + XH - R + 1 + q), dx);
-      }
-      if (!FAST) {
-        if (sk >= 0)
-          dz = cpml_step(dz, ps[(2 * ZC + c) * NT + threadIdx.x], p.psiH[2], psi_at(2, sk, i, j, k, p.np, 2 * nb),
-                         p.pml[2][4 * nb + sk], p.pml[2][6 * nb + sk]);
-        if (si >= 0)
-          dx = cpml_step(dx, ps[(3 * ZC + c) * NT + threadIdx.x], p.psiH[3], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                         p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
-      }
-      p.H[1][id] = fmaf(-dt_mu, dz - dx, h[1][c]);
-    }
-    // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
-    if (FAST || (dp_i && dp_j)) {
-      float dx = 0.f, dy = 0.f;
+    for (int m = 0; m < M; ++m) dy.fma(cy[m], v.zf(u.c + R - 1, u.r + m + 1, q4));
+    Row12 ey;
+    ey.load(v.xf(u.c + R - 1, u.r, q4), v.xf(u.c + R - 1, u.r, q4 + 4), v.xf(u.c + R - 1, u.r, q4 + 8));
+    float4 px = FAST ? float4{} : ps[4 * NT + t], py = FAST ? float4{} : ps[5 * NT + t];
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        dx = fmaf(cx[q], v.xf(c + R - 1, ty, tx + XH - R + 1 + q), dx);
-        dy = fmaf(cy[q], v.zf(c + R - 1, ty + q + 1, tx), dy);
-      }
+    for (int c = 0; c < 4; ++c) {
+      if (!(FAST || (dp_i[c] && dp_j))) continue;
+      float dx = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) dx = fmaf(cx[c][m], ey.v[XH + c - R + 1 + m], dx);
+      float b = dy[c];
       if (!FAST) {
-        if (si >= 0)
-          dx = cpml_step(dx, ps[(4 * ZC + c) * NT + threadIdx.x], p.psiH[4], psi_at(0, si, i, j, k, p.np, 2 * nb),
-                         p.pml[0][4 * nb + si], p.pml[0][6 * nb + si]);
-        if (sj >= 0)
-          dy = cpml_step(dy, ps[(5 * ZC + c) * NT + threadIdx.x], p.psiH[5], psi_at(1, sj, i, j, k, p.np, 2 * nb),
-                         p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+        if (si[c] >= 0) {
+          float s = get(px, c);
+          dx = cpml1(dx, s, p.pml[0][4 * nb + si[c]], p.pml[0][6 * nb + si[c]]);
+          put(px, c, s);
+        }
+        if (sj >= 0) {
+          float s = get(py, c);
+          b = cpml1(b, s, p.pml[1][4 * nb + sj], p.pml[1][6 * nb + sj]);
+          put(py, c, s);
+        }
       }
-      p.H[2][id] = fmaf(-dt_mu, dx - dy, h[2][c]);
+      put(out[2], c, fmaf(-dt_mu, dx - b, get(h[2], c)));
     }
-    // volume DTFT of E^{n+1}
-    if (VOL) {
-      const int kk = k - p.nbe;
-      if (int_ij && kk >= 0 && kk < p.n[2]) {
+    if (!FAST) {
+      if (xs >= 0)
+        *reinterpret_cast<float4 *>(p.psiH[4] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
+      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiH[5] + psi_y_at(p, u, sj)) = py;
+    }
+  }
+  const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(p.H[a] + id) = out[a];
+
+  // volume DTFT of E^{n+1}
+  if (VOL) {
+    const int jj = u.j - p.nbe, kk = u.k - p.nbe;
+    if (jj >= 0 && jj < p.n[1] && kk >= 0 && kk < p.n[2]) {
+      const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+      const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
+      const float4 ex = v.zf(u.c + R - 1, u.r + R, q4), ey = v.xf(u.c + R - 1, u.r, q4 + XH),
+                   ez = v.xy(u.c, u.r + R, q4 + XH);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ii = u.i + c - p.nbe;
+        if (ii < 0 || ii >= p.n[0]) continue;
         const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 0, lin, nint, facE, v.zf(c + R - 1, ty + R, tx));
-        volume_accumulate(p, 1, lin, nint, facE, v.xf(c + R - 1, ty, tx + XH));
-        volume_accumulate(p, 2, lin, nint, facE, v.xy(c, ty + R, tx + XH));
+        volume_accumulate(p, 0, lin, nint, facE, get(ex, c));
+        volume_accumulate(p, 1, lin, nint, facE, get(ey, c));
+        volume_accumulate(p, 2, lin, nint, facE, get(ez, c));
       }
     }
   }
@@ -603,44 +817,36 @@ __device__ __forceinline__ void h_planes(const DevParams &p, const View<R> &v, c
 template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  if (static_cast<int>(blockIdx.x) >= p.stencil_blocks) {
-    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, blockIdx.x - p.stencil_blocks);
+  if (static_cast<int>(blockIdx.z) >= p.tiles_z) {
+    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of(p, blockIdx.x);
+  const Origin o = origin_of(p);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
 
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = o.i0 + tx, j = o.j0 + ty;
+  const Quad u = quad_of(o);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
-  const bool in_ij = i >= 0 && i < np0 && j >= 0 && j < np1;
-  const size_t col = static_cast<size_t>(j) * p.pitch + i;
-  float h[3][ZC];
+  const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
+  float4 h[3];
+  const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int c = 0; c < ZC; ++c) {
-    const int k = o.k0 + c;
-    const bool ok = in_ij && k >= 0 && k < np2;
-    const size_t id = static_cast<size_t>(k) * p.plane + col;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) h[a][c] = ok ? p.H[a][id] : 0.f;
-  }
+  for (int a = 0; a < 3; ++a) h[a] = live ? *reinterpret_cast<const float4 *>(p.H[a] + id) : float4{};
   const bool fast = interior_H(p, o, R);
-  float *ps = s + Tiles<R>::BYTES / 4;
-  if (!fast && in_ij)
-    stage_psi(ps, p.psiH, p, i, j, o.k0, slab_half(i, np0, nb), slab_half(j, np1, nb),
-              [&](int k) { return slab_half(k, np2, nb); });
-  else
-    cp_async_commit();
+  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
+  if (!fast && live)
+    stage_psi(ps, p.psiH, p, u, slab_half(u.j, np1, nb), slab_half(u.k, np2, nb),
+              psi_x_column(u.i, nb, PsiX{p.psx_hx[1], p.psx_wx[1], p.psx_far0[1]}, np0 - 2), p.psx_wx[1]);
+  cp_async_commit();
   cp_async_wait_all();
-  if (!tiles_ready(p, bar) || !in_ij) return;
+  if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    h_planes<R, VOL, true>(p, v, o, tx, ty, h, ps, n);
+    h_quad<R, VOL, true>(p, v, u, h, ps, n);
   else
-    h_planes<R, VOL, false>(p, v, o, tx, ty, h, ps, n);
+    h_quad<R, VOL, false>(p, v, u, h, ps, n);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -714,6 +920,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // 128-byte line; the row pitch is a multiple of 32 samples.
 struct FieldGeom {
   int org[3], tiles[3], xshift, pitch;
+  int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage: [0] integer, [1] half samples
 };
 FieldGeom field_geom(const emm_grid *g) {
   FieldGeom f{};
@@ -727,6 +934,16 @@ FieldGeom field_geom(const emm_grid *g) {
   }
   f.xshift = -f.org[0];
   f.pitch = (g->ax[0].npad + f.xshift + 31) / 32 * 32;
+  // Far slab of the x-derivative CPML arrays: stored from hx = (first far
+  // sample) mod 4 above the near slab's last quad, so quads stay 16-byte
+  // aligned and never overlap the near slab's entries.
+  const int np0 = g->ax[0].npad, nb = g->nb, nb4 = (nb + 3) / 4 * 4;
+  const int far0[2] = {np0 - nb, np0 - 1 - nb};
+  for (int h = 0; h < 2; ++h) {
+    f.psx_far0[h] = far0[h];
+    f.psx_hx[h] = nb4 + 4 + (far0[h] & 3);
+    f.psx_wx[h] = (f.psx_hx[h] + nb + 3 + 3) / 4 * 4;
+  }
   return f;
 }
 
@@ -736,12 +953,14 @@ struct Layout {
   size_t cm[3], cp[3], pml[3], jw[3], amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
 };
 
-size_t psi_elems(const emm_grid *g, int axis) {
+// Elements of one CPML memory array (layouts in the kernels' comment).
+size_t psi_elems(const emm_grid *g, int axis, int half) {
+  const FieldGeom f = field_geom(g);
   const size_t nb2 = 2 * static_cast<size_t>(g->nb);
-  const size_t p0 = g->ax[0].npad, p1 = g->ax[1].npad, p2 = g->ax[2].npad;
-  if (axis == 0) return p2 * p1 * nb2;
-  if (axis == 1) return p2 * nb2 * p0;
-  return nb2 * p1 * p0;
+  const size_t p1 = g->ax[1].npad, p2 = g->ax[2].npad;
+  if (axis == 0) return p2 * p1 * static_cast<size_t>(f.psx_wx[half]);
+  if (axis == 1) return p2 * nb2 * static_cast<size_t>(f.pitch);
+  return nb2 * p1 * static_cast<size_t>(f.pitch);
 }
 
 // Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
@@ -762,13 +981,16 @@ Layout plan(const emm_grid *g, const emm_survey *s) {
   L.status = take(sizeof(int));
   for (int c = 0; c < 3; ++c) L.E[c] = take(cells * 4);
   for (int c = 0; c < 3; ++c) L.H[c] = take(cells * 4);
-  for (int c = 0; c < 6; ++c) L.psiE[c] = take(psi_elems(g, psi_axis(c)) * 4);
-  for (int c = 0; c < 6; ++c) L.psiH[c] = take(psi_elems(g, psi_axis(c)) * 4);
+  for (int c = 0; c < 6; ++c) L.psiE[c] = take(psi_elems(g, psi_axis(c), 0) * 4);
+  for (int c = 0; c < 6; ++c) L.psiH[c] = take(psi_elems(g, psi_axis(c), 1) * 4);
   L.vacc = take(s->volume ? 6 * nf * nint * sizeof(float4) : 0);
   L.zero_end = off;
   for (int c = 0; c < 3; ++c) L.ie[c] = take(cells * 4);
-  for (int a = 0; a < 3; ++a) L.cm[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
-  for (int a = 0; a < 3; ++a) L.cp[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  // FD rows; the x tables run on to a whole field row (zero rows past npad),
+  // because the kernels read the rows of all four cells of a quad at once
+  const size_t xrows = std::max<size_t>(g->ax[0].npad, field_geom(g).pitch);
+  for (int a = 0; a < 3; ++a) L.cm[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
+  for (int a = 0; a < 3; ++a) L.cp[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) L.pml[a] = take(8 * static_cast<size_t>(g->nb) * 4);
   for (int c = 0; c < 3; ++c) L.jw[c] = take(m * m * m * 4);
   L.amp = take(nt * 4);
@@ -839,7 +1061,7 @@ struct StepEvents {
 };
 
 template <int R, bool VOL>
-cudaError_t launch_steps(const DevParams &p, int nt, int blocks, cudaStream_t st, StepEvents *te) {
+cudaError_t launch_steps(const DevParams &p, int nt, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
@@ -1002,8 +1224,15 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
     p.jw[c] = reinterpret_cast<const float *>(base + L.jw[c]);
   }
   for (int c = 0; c < 6; ++c) {
-    p.psiE[c] = reinterpret_cast<float *>(base + L.psiE[c]);
-    p.psiH[c] = reinterpret_cast<float *>(base + L.psiH[c]);
+    // y- and z-derivative arrays share the field rows' x shift
+    const int shift = psi_axis(c) == 0 ? 0 : fg.xshift;
+    p.psiE[c] = reinterpret_cast<float *>(base + L.psiE[c]) + shift;
+    p.psiH[c] = reinterpret_cast<float *>(base + L.psiH[c]) + shift;
+  }
+  for (int h = 0; h < 2; ++h) {
+    p.psx_hx[h] = fg.psx_hx[h];
+    p.psx_wx[h] = fg.psx_wx[h];
+    p.psx_far0[h] = fg.psx_far0[h];
   }
   p.dt_mu = static_cast<float>(dt / kMu0);
   p.amp = reinterpret_cast<const float *>(base + L.amp);
@@ -1031,7 +1260,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   }
   p.stencil_blocks = p.tiles_x * p.tiles_y * p.tiles_z;
   p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
-  const int blocks = p.stencil_blocks + p.rec_blocks;
+  const int layer = p.tiles_x * p.tiles_y;
+  const dim3 blocks(p.tiles_x, p.tiles_y, p.tiles_z + (p.rec_blocks + layer - 1) / layer);
   // bounding box of the source stencils (lets CTAs far from it skip the test)
   p.src_any = 0;
   for (int a = 0; a < 3; ++a) {
