@@ -54,7 +54,8 @@ struct DevParams {
   int nbe, nb;
   int org[3];       // grid coordinates of the first tile (<= 0)
   int tiles_x, tiles_y, tiles_z, stencil_blocks;  // stencil_blocks: stencil CTAs of a launch
-  int rec_blocks;   // CTAs (the first ones) that also gather the receiver DTFT
+  int rec_blocks;   // receiver CTAs (one warp per receiver component)
+  int rec_layers;   // grid z layers holding them (the first ones)
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid

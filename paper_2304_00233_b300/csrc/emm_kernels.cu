@@ -200,18 +200,20 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 
 // ---------------------------------------------------------------------------
 // Common CTA prologue: origin of the tile, the TMA copies of the three source
-// fields, and the bounded wait for them.  The grid is 3-D: (tiles_x,
-// tiles_y, tiles_z) stencil CTAs, then extra z layers of receiver CTAs.
+// fields, and the bounded wait for them.  The grid is 3-D: rec_layers z
+// layers of receiver CTAs first (so that they run beside the first stencil
+// wave instead of trailing the launch), then (tiles_x, tiles_y, tiles_z)
+// stencil CTAs.
 // ---------------------------------------------------------------------------
 struct Origin {
   int i0, j0, k0;
 };
 __device__ __forceinline__ Origin origin_of(const DevParams &p) {
   return Origin{p.org[0] + static_cast<int>(blockIdx.x) * TX, p.org[1] + static_cast<int>(blockIdx.y) * TY,
-                p.org[2] + static_cast<int>(blockIdx.z) * ZC};
+                p.org[2] + (static_cast<int>(blockIdx.z) - p.rec_layers) * ZC};
 }
 __device__ __forceinline__ int receiver_block(const DevParams &p) {
-  return ((static_cast<int>(blockIdx.z) - p.tiles_z) * p.tiles_y + static_cast<int>(blockIdx.y)) * p.tiles_x +
+  return (static_cast<int>(blockIdx.z) * p.tiles_y + static_cast<int>(blockIdx.y)) * p.tiles_x +
          static_cast<int>(blockIdx.x);
 }
 
@@ -600,7 +602,7 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, con
 template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  if (static_cast<int>(blockIdx.z) >= p.tiles_z) {
+  if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
     return;
   }
@@ -817,7 +819,7 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, con
 template <int R, bool VOL>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  if (static_cast<int>(blockIdx.z) >= p.tiles_z) {
+  if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
     return;
   }
@@ -1261,7 +1263,8 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   p.stencil_blocks = p.tiles_x * p.tiles_y * p.tiles_z;
   p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
   const int layer = p.tiles_x * p.tiles_y;
-  const dim3 blocks(p.tiles_x, p.tiles_y, p.tiles_z + (p.rec_blocks + layer - 1) / layer);
+  p.rec_layers = (p.rec_blocks + layer - 1) / layer;
+  const dim3 blocks(p.tiles_x, p.tiles_y, p.rec_layers + p.tiles_z);
   // bounding box of the source stencils (lets CTAs far from it skip the test)
   p.src_any = 0;
   for (int a = 0; a < 3; ++a) {
