@@ -11,6 +11,8 @@ Entry points:
                       contraction) into ``oracle/_build/liboracle.so``.
   * ``row_weights``   row 0 / row 1 of [V^T]^{-1}  (Sec. 3.1, Eq. 9-12).
   * ``vander_inverse``full [V^T]^{-1} by unit vectors (Eq. 12).
+  * ``vjp``           exact discrete adjoint of ``forward`` (gradient of
+                      Re(sum conj(v) G) with respect to the conductivity).
   * ``axis_tables``   padded nodes, half nodes, D+/D- rows, CPML slabs and
                       coefficients, D_max  (Sec. 3.1-3.4).
   * ``locate``        source/receiver stencil start and 1-D weights.
@@ -67,6 +69,8 @@ def _load():
         _lib.orc_locate.restype = C.c_int
         _lib.orc_forward.argtypes = [C.POINTER(_Problem)]
         _lib.orc_forward.restype = C.c_int
+        _lib.orc_vjp.argtypes = [C.POINTER(_Problem), D, D, C.c_int]
+        _lib.orc_vjp.restype = C.c_int
         _lib.orc_threads.restype = C.c_int
     return _lib
 
@@ -245,6 +249,45 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     if vsG is not None:
         out["vol_samples_G"] = cplx(vsG)[:, :nf]
     return out
+
+
+def vjp(x, y, z, sigma, v, *, rd: int, nb: int, ne: int, omega0: float, nt: int,
+        fmax: float, sigma_min: float, src=(0.0, 0.0, 0.0), az: float = 0.0,
+        dip: float = 0.0, moment: float = 1.0, rec=None, freqs=(), dt: float = 0.0,
+        inject: bool = True, pml: bool = True, ckpt_every: int = 50) -> np.ndarray:
+    """Exact discrete adjoint of ``forward``: the gradient with respect to the
+    interior staggered conductivity [3][n3][n2][n1] of Re(sum conj(v) G),
+    ``v`` a complex cotangent [nrec][6][nfreq] of the receiver Green's
+    functions.  ``sigma_min`` (> 0) and ``dt`` fix the time step and the CPML
+    as ``forward`` would with the same arguments."""
+    lib = _load()
+    xs = [_f64(x), _f64(y), _f64(z)]
+    n = [len(a) for a in xs]
+    sigma = _f64(sigma)
+    assert sigma.shape == (3, n[2], n[1], n[0]), sigma.shape
+    rec = _f64(np.zeros((0, 3)) if rec is None else rec).reshape(-1, 3)
+    freqs = _f64(freqs)
+    nrec, nf = rec.shape[0], len(freqs)
+    v = np.asarray(v, dtype=np.complex128).reshape(nrec, 6, nf)
+    vv = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1), dtype=np.float64)
+    P = _Problem()
+    P.n = (C.c_int * 3)(*n)
+    P.x = (C.POINTER(C.c_double) * 3)(*[_dp(a) for a in xs])
+    P.rd, P.nb, P.ne = rd, nb, ne
+    P.sigma = _dp(sigma)
+    P.omega0, P.sigma_min, P.dt = omega0, sigma_min, dt
+    P.nt, P.fmax = int(nt), fmax
+    P.src = (C.c_double * 3)(*[float(a) for a in src])
+    P.az, P.dip, P.moment = az, dip, moment
+    P.nrec = nrec
+    P.rec = _dp(rec) if nrec else None
+    P.nfreq = nf
+    P.freqs = _dp(freqs) if nf else None
+    P.inject, P.pml = int(inject), int(pml)
+    grad = np.zeros((3, n[2], n[1], n[0]))
+    code = lib.orc_vjp(C.byref(P), _dp(vv), _dp(grad), int(ckpt_every))
+    _check(code, "vjp")
+    return grad
 
 
 def forward_workload(w, **kw) -> Dict[str, object]:

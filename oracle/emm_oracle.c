@@ -774,3 +774,299 @@ int orc_forward(orc_problem *P)
   orc_state_free(st);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse-mode derivative of the forward map sigma -> G (test reference for  */
+/* the gradient).                                                            */
+/* ------------------------------------------------------------------------ */
+/* The paper computes no gradient (its Discussion leaves inversion for later);
+ * this is the exact discrete adjoint of the loop of orc_forward: every linear
+ * step transposed, the steps taken in reverse order.  Given a cotangent v
+ * ([nrec][6][nfreq] complex) it returns
+ *     grad = d/d sigma  Re( sum_{r,c,f} conj(v) G )      ([3][n3][n2][n1]),
+ * the derivative with respect to the interior staggered conductivity, pads
+ * included through the edge replication.  dt, nt and the CPML coefficients
+ * follow from survey constants (sigma_min must be given, > 0), so the map is
+ * differentiated with them fixed.  sigma enters only through dt/eps:
+ *     E^{n+1} = E^n + ie (curl H - J),  ie = 2 omega0 dt / sigma,
+ * hence dL/d sigma = - sum_n lambda_E^{n+1} (E^{n+1} - E^n) / sigma, with
+ * lambda_E^{n+1} the adjoint of E^{n+1}.  Forward states are recomputed from
+ * checkpoints taken every ckpt_every steps. */
+
+/* Transposes of D- and D+ at sample (i,j,k): G[tap] += w[q] g. */
+static void orc_dm_T(const orc_state *st, int a, double *G, int i, int j, int k, double g)
+{
+  int r = st->rd, m = 2 * r;
+  int c = (a == 0) ? i : (a == 1 ? j : k);
+  const double *w = &st->ax[a].cm[(size_t)c * m];
+  for (int q = 0; q < m; ++q) {
+    int ii = i, jj = j, kk = k;
+    if (a == 0) ii = i - r + q; else if (a == 1) jj = j - r + q; else kk = k - r + q;
+    G[IDX(st, kk, jj, ii)] += w[q] * g;
+  }
+}
+static void orc_dp_T(const orc_state *st, int a, double *G, int i, int j, int k, double g)
+{
+  int r = st->rd, m = 2 * r;
+  int c = (a == 0) ? i : (a == 1 ? j : k);
+  const double *w = &st->ax[a].cp[(size_t)c * m];
+  for (int q = 0; q < m; ++q) {
+    int ii = i, jj = j, kk = k;
+    if (a == 0) ii = i - r + 1 + q; else if (a == 1) jj = j - r + 1 + q; else kk = k - r + 1 + q;
+    G[IDX(st, kk, jj, ii)] += w[q] * g;
+  }
+}
+
+/* Transpose of the CPML step  psi' = b psi + a t,  d = t + psi'.  Given the
+ * adjoint gd of d, and in mu[idx] the adjoint of psi' (from later steps),
+ * return the adjoint of t and leave in mu[idx] the adjoint of the old psi. */
+static double orc_pml_T(const orc_state *st, int pml, int a, int half, int c, double *mu,
+                        size_t idx, double gd)
+{
+  if (!pml) return gd;
+  int s = half ? st->ax[a].slabh[c] : st->ax[a].slab[c];
+  if (s < 0) return gd;
+  double aa = half ? st->ax[a].pa_h[s] : st->ax[a].pa_i[s];
+  double bb = half ? st->ax[a].pb_h[s] : st->ax[a].pb_i[s];
+  double gpsi = gd + mu[idx];
+  mu[idx] = bb * gpsi;
+  return gd + aa * gpsi;
+}
+
+/* Transpose of curl H + E update: lamH += (curl H)^T (ie lamE), CPML memory
+ * adjoints muE[0..5] updated.  Serial: the transposed stencils scatter. */
+static void orc_adj_E(orc_state *st, int pml, double *const *lamE, double *const *lamH, double *const *muE)
+{
+  for (int c = 0; c < 3; ++c) {
+    int p = (c + 1) % 3, q = (c + 2) % 3, lo[3], hi[3];
+    lo[c] = 0; hi[c] = st->np[c] - 2;
+    orc_range_Dm(st, p, &lo[p], &hi[p]);
+    orc_range_Dm(st, q, &lo[q], &hi[q]);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          size_t id = IDX(st, k, j, i);
+          int cc[3] = {i, j, k};
+          double g = st->ie[c][id] * lamE[c][id];          /* adjoint of curl H - J */
+          double tp = orc_pml_T(st, pml, p, 0, cc[p], muE[2 * c], id, g);
+          double tq = orc_pml_T(st, pml, q, 0, cc[q], muE[2 * c + 1], id, -g);
+          orc_dm_T(st, p, lamH[q], i, j, k, tp);            /* D_p H_q */
+          orc_dm_T(st, q, lamH[p], i, j, k, tq);            /* D_q H_p */
+        }
+  }
+}
+
+/* Transpose of curl E + H update: lamE += (curl E)^T (-dt/mu0 lamH), CPML
+ * memory adjoints muH[0..5] updated. */
+static void orc_adj_H(orc_state *st, int pml, double dt, double *const *lamE, double *const *lamH,
+                      double *const *muH)
+{
+  double f = dt / ORC_MU0;
+  for (int c = 0; c < 3; ++c) {
+    int p = (c + 1) % 3, q = (c + 2) % 3, lo[3], hi[3];
+    lo[c] = 0; hi[c] = st->np[c] - 1;
+    orc_range_Dp(st, p, &lo[p], &hi[p]);
+    orc_range_Dp(st, q, &lo[q], &hi[q]);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          size_t id = IDX(st, k, j, i);
+          int cc[3] = {i, j, k};
+          double g = -f * lamH[c][id];                      /* adjoint of curl E */
+          double tp = orc_pml_T(st, pml, p, 1, cc[p], muH[2 * c], id, g);
+          double tq = orc_pml_T(st, pml, q, 1, cc[q], muH[2 * c + 1], id, -g);
+          orc_dp_T(st, p, lamE[q], i, j, k, tp);            /* D_p E_q */
+          orc_dp_T(st, q, lamE[p], i, j, k, tq);            /* D_q E_p */
+        }
+  }
+}
+
+/* Transpose of the receiver interpolation: F[nodes] += w g. */
+static void orc_sample_T(const orc_state *st, double *F, const orc_stencil *s, double g)
+{
+  int m = 2 * st->rd;
+  for (int c = 0; c < m; ++c)
+    for (int b = 0; b < m; ++b)
+      for (int a = 0; a < m; ++a)
+        F[IDX(st, s->start[2] + c, s->start[1] + b, s->start[0] + a)] +=
+            s->w[2][c] * s->w[1][b] * s->w[0][a] * g;
+}
+
+/* One forward leapfrog step without the DTFT (curl H, source, E, curl E, H). */
+static void orc_step(orc_state *st, int pml, double dt, double amp, double *const *jw, const orc_stencil *sst)
+{
+  int m = 2 * st->rd;
+  orc_curl_H(st, pml);
+  for (int c = 0; c < 3; ++c) {
+    if (!jw[c]) continue;
+    for (int q3 = 0; q3 < m; ++q3)
+      for (int q2 = 0; q2 < m; ++q2)
+        for (int q1 = 0; q1 < m; ++q1)
+          st->C[c][IDX(st, sst[c].start[2] + q3, sst[c].start[1] + q2, sst[c].start[0] + q1)]
+              -= amp * jw[c][(q3 * m + q2) * m + q1];
+  }
+  orc_update_E(st);
+  orc_curl_E(st, pml);
+  orc_update_H(st, dt);
+}
+
+int orc_vjp(orc_problem *P, const double *v, double *grad, int ckpt_every)
+{
+  orc_state S, *st = &S;
+  memset(st, 0, sizeof(S));
+  int rd = P->rd, nb = P->nb, ne = P->ne, code = ORC_OK;
+  if (rd < 1 || rd > 4 || nb < rd || ne < 0 || P->nt < 0 || P->omega0 <= 0 || !(P->sigma_min > 0) ||
+      ckpt_every < 1 || !v || !grad)
+    return ORC_EINVAL;
+  st->rd = rd;
+  for (int a = 0; a < 3; ++a) {
+    code = orc_axis_nodes(&st->ax[a], P->n[a], P->x[a], rd, nb, ne);
+    if (code) { orc_state_free(st); return code; }
+    orc_axis_fd(&st->ax[a]);
+    st->np[a] = st->ax[a].npad;
+  }
+  st->ncell = (size_t)st->np[0] * st->np[1] * st->np[2];
+  size_t nint = (size_t)P->n[0] * P->n[1] * P->n[2], nc = st->ncell;
+  for (size_t q = 0; q < 3 * nint; ++q)
+    if (!(P->sigma[q] > 0) || !isfinite(P->sigma[q])) { orc_state_free(st); return ORC_EINVAL; }
+  /* dt and CPML exactly as orc_forward with the given sigma_min */
+  double vmax = sqrt(2.0 * P->omega0 / (ORC_MU0 * P->sigma_min));
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) { double dm = orc_axis_dmax(&st->ax[a]); d2 += dm * dm; }
+  double dt = (P->dt > 0) ? P->dt : 0.99 / (0.5 * vmax * sqrt(d2));
+  for (int a = 0; a < 3; ++a) orc_axis_cpml(&st->ax[a], vmax, P->fmax, dt);
+  int pml = P->pml, nt = P->nt, m = 2 * rd, nbe = nb + ne;
+  for (int c = 0; c < 6; ++c) st->F[c] = calloc(nc, sizeof(double));
+  for (int c = 0; c < 3; ++c) { st->C[c] = calloc(nc, sizeof(double)); st->ie[c] = calloc(nc, sizeof(double)); }
+  for (int c = 0; c < 12; ++c) st->psi[c] = pml ? calloc(nc, sizeof(double)) : NULL;
+  for (int c = 0; c < 3; ++c) {
+    const double *sg = P->sigma + c * nint;
+    for (int k = 0; k < st->np[2]; ++k)
+      for (int j = 0; j < st->np[1]; ++j)
+        for (int i = 0; i < st->np[0]; ++i) {
+          double s = sg[((size_t)orc_clampi(k - nbe, 0, P->n[2] - 1) * P->n[1] + orc_clampi(j - nbe, 0, P->n[1] - 1)) *
+                            P->n[0] + orc_clampi(i - nbe, 0, P->n[0] - 1)];
+          st->ie[c][IDX(st, k, j, i)] = 2.0 * P->omega0 * dt / s;
+        }
+  }
+  /* source and receiver stencils, as in orc_forward */
+  double dir[3] = {cos(P->dip) * cos(P->az), cos(P->dip) * sin(P->az), sin(P->dip)};
+  orc_stencil sst[3];
+  double *jw[3] = {NULL, NULL, NULL};
+  for (int c = 0; c < 3 && P->inject; ++c) {
+    if (dir[c] == 0.0) continue;
+    for (int a = 0; a < 3 && !code; ++a)
+      code = orc_locate_axis(&st->ax[a], ORC_HALF[c][a], P->src[a], &sst[c].start[a], sst[c].w[a]);
+    if (code) break;
+    jw[c] = malloc(sizeof(double) * m * m * m);
+    for (int q3 = 0; q3 < m; ++q3)
+      for (int q2 = 0; q2 < m; ++q2)
+        for (int q1 = 0; q1 < m; ++q1) {
+          int id3[3] = {sst[c].start[0] + q1, sst[c].start[1] + q2, sst[c].start[2] + q3};
+          double V = 1.0;
+          for (int a = 0; a < 3; ++a) {
+            const orc_axis *ax = &st->ax[a];
+            V *= ORC_HALF[c][a] ? (ax->X[id3[a] + 1] - ax->X[id3[a]]) : (ax->Xh[id3[a]] - ax->Xh[id3[a] - 1]);
+          }
+          jw[c][(q3 * m + q2) * m + q1] = dir[c] * sst[c].w[0][q1] * sst[c].w[1][q2] * sst[c].w[2][q3] / V;
+        }
+  }
+  int nrec = P->nrec, nf = P->nfreq;
+  orc_stencil *rst = calloc((size_t)(nrec > 0 ? nrec : 1) * 6, sizeof(orc_stencil));
+  for (int r = 0; r < nrec && !code; ++r)
+    for (int c = 0; c < 6 && !code; ++c)
+      for (int a = 0; a < 3 && !code; ++a)
+        code = orc_locate_axis(&st->ax[a], ORC_HALF[c][a], P->rec[3 * r + a], &rst[r * 6 + c].start[a],
+                               rst[r * 6 + c].w[a]);
+  if (code) { free(rst); for (int c = 0; c < 3; ++c) free(jw[c]); orc_state_free(st); return code; }
+
+  /* source spectrum J' and the weights c_{r,c,f} = conj(v) s_c / J' of Eq. 7:
+   * dL/du_{r,c,n} = Re( sum_f c_{r,c,f} e^{i w' t_n} dt ) */
+  double complex *wp = malloc(sizeof(double complex) * (nf > 0 ? nf : 1));
+  double complex *jh = calloc(nf > 0 ? nf : 1, sizeof(double complex));
+  for (int f = 0; f < nf; ++f) wp[f] = (1.0 + I) * sqrt(2.0 * M_PI * P->freqs[f] * P->omega0);
+  for (int n = 0; n < nt; ++n)
+    for (int f = 0; f < nf; ++f)
+      jh[f] += cexp(I * wp[f] * ((n + 0.5) * dt)) * dt * P->moment * orc_wavelet((n + 0.5) * dt, P->fmax);
+  double complex *cw = calloc((size_t)(nrec > 0 ? nrec : 1) * 6 * (nf > 0 ? nf : 1), sizeof(double complex));
+  for (int f = 0; f < nf; ++f) {
+    double complex sE = sqrt(2.0 * M_PI * P->freqs[f] / (2.0 * P->omega0)) * cexp(-I * M_PI / 4.0);
+    for (int r = 0; r < nrec; ++r)
+      for (int c = 0; c < 6; ++c) {
+        size_t o = ((size_t)r * 6 + c) * nf + f;
+        double complex vv = v[2 * o] + I * v[2 * o + 1];
+        cw[o] = conj(vv) * (c < 3 ? sE : 1.0) / jh[f];
+      }
+  }
+
+  /* forward sweep: checkpoints of the whole state before steps 0, K, 2K, ... */
+  int K = ckpt_every, nck = (nt + K - 1) / K;
+  int nstate = pml ? 18 : 6;
+  double *ck = malloc(sizeof(double) * (size_t)(nck > 0 ? nck : 1) * nstate * nc);
+  double *Eh = malloc(sizeof(double) * (size_t)(K + 1) * 3 * nc);
+  double *lam[6], *mu[12], *gpad[3];
+  for (int c = 0; c < 6; ++c) lam[c] = calloc(nc, sizeof(double));
+  for (int c = 0; c < 12; ++c) mu[c] = pml ? calloc(nc, sizeof(double)) : NULL;
+  for (int c = 0; c < 3; ++c) gpad[c] = calloc(nc, sizeof(double));
+  if (!ck || !Eh) code = ORC_ENOMEM;
+  for (int it = 0; it < nt && !code; ++it) {
+    if (it % K == 0) {
+      double *dst = ck + (size_t)(it / K) * nstate * nc;
+      for (int c = 0; c < 6; ++c) memcpy(dst + c * nc, st->F[c], sizeof(double) * nc);
+      for (int c = 0; c < 12 && pml; ++c) memcpy(dst + (6 + c) * nc, st->psi[c], sizeof(double) * nc);
+    }
+    orc_step(st, pml, dt, P->moment * orc_wavelet((it + 0.5) * dt, P->fmax), jw, sst);
+  }
+
+  /* reverse sweep, one checkpoint segment at a time */
+  for (int s = nck - 1; s >= 0 && !code; --s) {
+    int it0 = s * K, it1 = (it0 + K < nt) ? it0 + K : nt;
+    const double *src = ck + (size_t)s * nstate * nc;
+    for (int c = 0; c < 6; ++c) memcpy(st->F[c], src + c * nc, sizeof(double) * nc);
+    for (int c = 0; c < 12 && pml; ++c) memcpy(st->psi[c], src + (6 + c) * nc, sizeof(double) * nc);
+    for (int it = it0; it < it1; ++it) {
+      for (int c = 0; c < 3; ++c) memcpy(Eh + ((size_t)(it - it0) * 3 + c) * nc, st->F[c], sizeof(double) * nc);
+      orc_step(st, pml, dt, P->moment * orc_wavelet((it + 0.5) * dt, P->fmax), jw, sst);
+    }
+    for (int c = 0; c < 3; ++c) memcpy(Eh + ((size_t)(it1 - it0) * 3 + c) * nc, st->F[c], sizeof(double) * nc);
+    for (int it = it1 - 1; it >= it0; --it) {
+      /* H update of step it: H^{it+3/2} = H^{it+1/2} - dt/mu0 curl E^{it+1} */
+      orc_adj_H(st, pml, dt, lam, lam + 3, mu + 6);
+      /* receiver DTFT of E^{it+1} (label (it+1) dt) and H^{it+1/2} ((it+1/2) dt) */
+      for (int r = 0; r < nrec; ++r)
+        for (int c = 0; c < 6; ++c) {
+          double t = (c < 3) ? (it + 1.0) * dt : (it + 0.5) * dt, g = 0.0;
+          for (int f = 0; f < nf; ++f) g += creal(cw[((size_t)r * 6 + c) * nf + f] * cexp(I * wp[f] * t) * dt);
+          orc_sample_T(st, lam[c], &rst[r * 6 + c], g);
+        }
+      /* gradient: dL/dsigma += - lambda_E^{it+1} (E^{it+1} - E^it) / sigma,
+       * with sigma = 2 omega0 dt / ie on the padded grid */
+      const double *E0 = Eh + (size_t)(it - it0) * 3 * nc, *E1 = Eh + (size_t)(it - it0 + 1) * 3 * nc;
+      for (int c = 0; c < 3; ++c)
+        for (size_t id = 0; id < nc; ++id) {
+          double dE = E1[c * nc + id] - E0[c * nc + id];
+          if (dE != 0.0) gpad[c][id] -= lam[c][id] * dE * st->ie[c][id] / (2.0 * P->omega0 * dt);
+        }
+      /* E update of step it */
+      orc_adj_E(st, pml, lam, lam + 3, mu);
+    }
+  }
+  /* fold the padded gradient onto the interior samples it replicates */
+  if (!code) {
+    memset(grad, 0, sizeof(double) * 3 * nint);
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < st->np[2]; ++k)
+        for (int j = 0; j < st->np[1]; ++j)
+          for (int i = 0; i < st->np[0]; ++i) {
+            size_t o = ((size_t)orc_clampi(k - nbe, 0, P->n[2] - 1) * P->n[1] + orc_clampi(j - nbe, 0, P->n[1] - 1)) *
+                           P->n[0] + orc_clampi(i - nbe, 0, P->n[0] - 1);
+            grad[c * nint + o] += gpad[c][IDX(st, k, j, i)];
+          }
+  }
+  for (int c = 0; c < 6; ++c) free(lam[c]);
+  for (int c = 0; c < 12; ++c) free(mu[c]);
+  for (int c = 0; c < 3; ++c) { free(gpad[c]); free(jw[c]); }
+  free(ck); free(Eh); free(cw); free(jh); free(wp); free(rst);
+  orc_state_free(st);
+  return code;
+}
