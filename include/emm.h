@@ -192,6 +192,35 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
  * are then undefined).  EMM_ECUDA if the copy fails. */
 int emm_status(const void *ws, int *status, emm_stream stream);
 
+/* Device workspace bytes emm_gradient needs (the forward workspace, the
+ * checkpoints of every ckpt_every-th step, the E snapshots of one checkpoint
+ * segment, the adjoint fields and the FP64 gradient accumulators).
+ * EMM_EINVAL on bad input, ckpt_every < 1 or survey->volume set. */
+int emm_gradient_workspace_size(const emm_grid *grid, const emm_survey *survey, int ckpt_every,
+                                size_t *bytes);
+
+/* Gradient of the receiver Green's functions with respect to the
+ * conductivity: for a cotangent dG it computes
+ *     grad = d/d sigma  Re( sum_{r,c,f} conj(dG[r][c][f]) G[r][c][f] ),
+ * the vector-Jacobian product of the forward map sigma -> G.  The paper
+ * stops at the forward solver (inversion is named as future work); this is
+ * the exact discrete adjoint of the time loop emm_forward runs (Sec. 3.1,
+ * Eq. 8; CPML Eq. 22-24; DTFT Eq. 25; Eq. 7), with dt, nt and the CPML
+ * coefficients fixed by the survey constants.  Forward states are recomputed
+ * from checkpoints taken every ckpt_every steps.
+ *   sigma     device float [3][n3][n2][n1], as for emm_forward.
+ *   dG        device double [nrec][6][nfreq][2] (re, im) cotangent.
+ *   ws        device workspace of emm_gradient_workspace_size bytes, 256-byte
+ *             aligned; contents on entry do not matter.
+ *   rec_out   device double [nrec][6][nfreq][2]: G of the forward sweep.
+ *   grad      device double [3][n3][n2][n1]: the gradient with respect to
+ *             the interior staggered sigma_xx, sigma_yy, sigma_zz (the pads'
+ *             replicated values folded onto the edge samples).
+ * Asynchronous on `stream`; errors as emm_forward (survey->volume must be 0). */
+int emm_gradient(const emm_grid *grid, const emm_survey *survey, const float *sigma, const double *dG,
+                 int ckpt_every, void *ws, size_t ws_bytes, double *rec_out, double *grad,
+                 emm_stream stream);
+
 /* Size of the scratch array that emm_forward_static works in. */
 #define EMM_STATIC_SCRATCH_BYTES (64u << 20)
 

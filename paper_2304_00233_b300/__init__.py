@@ -34,7 +34,7 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",
             "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
             "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
-            "emm_forward_static")
+            "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient")
 
 
 class EmmError(RuntimeError):
@@ -96,6 +96,8 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
                                C.POINTER(_Timing)], C.c_int),
         "emm_status": ([V, _I, V], C.c_int),
         "emm_forward_static": ([V, C.POINTER(_Survey), V, V, V, V, _I], C.c_int),
+        "emm_gradient_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "emm_gradient": ([V, C.POINTER(_Survey), V, V, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -334,6 +336,82 @@ def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None
         C.byref(st) if wait else None)
     _check(code, "emm_forward_static")
     return st.value if wait else None
+
+
+def gradient_workspace_size(grid: Grid, survey: Survey, ckpt_every: int) -> int:
+    s, keep = survey._c()
+    n = C.c_size_t(0)
+    _check(load_library().emm_gradient_workspace_size(grid.handle, C.byref(s), int(ckpt_every), C.byref(n)),
+           "emm_gradient_workspace_size")
+    return n.value
+
+
+def vjp(grid: Grid, survey: Survey, sigma, dG, ckpt_every: Optional[int] = None, stream=None, check: bool = True):
+    """``emm_gradient``: the gradient d/dsigma Re(sum conj(dG) G) with respect to
+    the interior staggered conductivity (float64 CUDA tensor [3][n3][n2][n1]),
+    and G of the forward sweep (complex128 [nrec][6][nfreq]).  ``dG`` is a
+    complex tensor [nrec][6][nfreq]; ``ckpt_every`` defaults to about
+    sqrt(nt) steps between checkpoints."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    nf = len(survey.freqs)
+    if ckpt_every is None:
+        ckpt_every = max(1, int(round(max(survey.nt, 1) ** 0.5)))
+    nbytes = gradient_workspace_size(grid, survey, ckpt_every)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=sigma.device)
+    ptr = ws.data_ptr() + (-ws.data_ptr()) % 256
+    dG = torch.as_tensor(dG, dtype=torch.complex128, device=sigma.device).reshape(survey.nrec, 6, nf)
+    dG2 = torch.view_as_real(dG.contiguous()).contiguous()
+    rec = torch.zeros((max(survey.nrec, 1), 6, nf, 2), dtype=torch.float64, device=sigma.device)
+    n1, n2, n3 = grid.n
+    grad = torch.empty((3, n3, n2, n1), dtype=torch.float64, device=sigma.device)
+    s, keep = survey._c()
+    code = load_library().emm_gradient(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(dG2.data_ptr()), int(ckpt_every),
+        C.c_void_p(ptr), C.c_size_t(nbytes), C.c_void_p(rec.data_ptr()), C.c_void_p(grad.data_ptr()),
+        C.c_void_p(stream.cuda_stream))
+    _check(code, "emm_gradient")
+    if check:
+        v = C.c_int(0)
+        _check(load_library().emm_status(C.c_void_p(ptr), C.byref(v), C.c_void_p(stream.cuda_stream)), "emm_status")
+        if v.value != EMM_OK:
+            raise EmmError(v.value, "emm_gradient (device status)")
+    return grad, torch.view_as_complex(rec)[: survey.nrec]
+
+
+def _emm_function():
+    import torch
+
+    class EmmForward(torch.autograd.Function):
+        """G = forward(sigma) as a differentiable torch function: the forward
+        pass runs ``emm_forward``, the backward pass ``emm_gradient`` with the
+        incoming gradient of G as cotangent (torch's convention for a complex
+        output of a real input: sigma.grad = Re(sum conj(dG) dG/dsigma))."""
+
+        @staticmethod
+        def forward(ctx, sigma, grid, survey, ckpt_every):
+            ctx.grid, ctx.survey, ctx.ckpt_every = grid, survey, ckpt_every
+            ctx.save_for_backward(sigma)
+            G, _ = forward(grid, survey, sigma.detach().to(torch.float32).contiguous())
+            return G.clone()
+
+        @staticmethod
+        def backward(ctx, dG):
+            (sigma,) = ctx.saved_tensors
+            grad, _ = vjp(ctx.grid, ctx.survey, sigma.detach().to(torch.float32).contiguous(), dG,
+                          ckpt_every=ctx.ckpt_every)
+            return grad.to(sigma.dtype), None, None, None
+
+    return EmmForward
+
+
+def green_functions(sigma, grid: Grid, survey: Survey, ckpt_every: Optional[int] = None):
+    """Receiver Green's functions G (complex128 [nrec][6][nfreq]) of the
+    conductivity tensor ``sigma`` [3][n3][n2][n1] (CUDA), differentiable with
+    respect to ``sigma`` through the exact discrete adjoint."""
+    return _emm_function().apply(sigma, grid, survey, ckpt_every)
 
 
 def status(work: Workspace, stream=None) -> int:

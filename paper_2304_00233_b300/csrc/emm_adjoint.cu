@@ -1,0 +1,482 @@
+// emm_adjoint.cu -- gradient of the receiver Green's functions with respect to
+// the staggered conductivity: emm_gradient_workspace_size and emm_gradient.
+//
+// The paper stops at the forward solver (its Discussion names inversion as
+// future work).  This is the exact discrete adjoint of the time loop the
+// forward kernels run: every linear step of a leapfrog step transposed and
+// the steps taken in reverse order.  For a cotangent v of the Green's
+// functions G (complex, [nrec][6][nfreq]) it returns
+//     grad = d/d sigma Re( sum conj(v) G ),
+// the vector-Jacobian product a torch.autograd.Function needs.  sigma enters
+// the loop only through dt/eps (E^{n+1} = E^n + ie (curl H - J), ie = 2 omega0
+// dt / sigma), so
+//     dL/d sigma = - sum_n lambda_E^{n+1} (E^{n+1} - E^n) / sigma,
+// lambda_E^{n+1} being the adjoint of E^{n+1}.  dt, nt and the CPML
+// coefficients depend on survey constants (sigma_min, fmax), not on sigma.
+//
+// Schedule: a forward sweep stores the whole state (fields and CPML memory)
+// every K steps; the reverse sweep, one checkpoint segment at a time,
+// recomputes the segment's E snapshots and then runs the adjoint steps
+// backwards.  One adjoint step, the transpose of one forward step:
+//   1. H update:  per-derivative adjoints T = -dt/mu0 lambda_H (CPML memory
+//      adjoints updated), then lambda_E += (D+)^T T  (transposed-row gather);
+//   2. receivers: lambda += interpolation^T of Re(conj(v) norm f_n);
+//   3. gradient:  g_pad += - lambda_E (E^{n+1} - E^n) / sigma   (FP64);
+//   4. E update:  T = ie lambda_E (CPML), then lambda_H += (D-)^T T.
+// Finally the padded gradient is folded onto the interior samples the pads
+// replicate.  Adjoint fields are FP32 like the forward fields; the gradient
+// accumulates in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "emm_internal.h"
+
+namespace emm {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct AdjParams {
+  int np[3], n[3], pitch, nb, rd, nbe;
+  size_t plane;
+  float kappa;               // dt / mu0
+  double inv_2w0dt;          // 1 / (2 omega0 dt): sigma = 2 omega0 dt / ie
+  const float *ie[3];
+  float *lamE[3], *lamH[3];  // adjoint fields (field layout)
+  float *T[6];               // per-derivative adjoints (field layout)
+  float *muE[6], *muH[6];    // adjoints of the CPML memory (psi layouts)
+  int psx_hx[2], psx_wx[2], psx_far0[2];
+  const float *pml[3];       // [4][2nb]: a_int, b_int, a_half, b_half
+  const float *cpT[3];       // transposed D+ rows, gather form [rows][2rd]
+  const float *cmT[3];       // transposed D- rows, gather form [rows][2rd]
+  const float *E0[3], *E1[3];  // forward E before / after the step
+  double *gpad[3];           // dL/dsigma on the padded grid (field layout)
+  int nrec, nf;
+  const int *rec_start;      // [nrec][6][3]
+  const double *rec_w;       // [nrec][6][3][2rd]
+  const double *cw;          // [nrec][6][nf][2]: conj(v) * norm
+  const double *fE, *fH;     // [nt][nf][2]
+};
+
+__device__ __forceinline__ int slab_int(int i, int np, int nb) {
+  return i < nb ? i : (i >= np - nb ? nb + np - 1 - i : -1);
+}
+__device__ __forceinline__ int slab_half(int i, int np, int nb) {
+  return i < nb ? i : ((i >= np - 1 - nb && i <= np - 2) ? nb + np - 2 - i : -1);
+}
+
+// Element of sample (i, j, k) in a CPML memory array of a derivative along
+// axis `axis` with slab entry s (layouts as the forward kernels store them;
+// h = 0 integer / 1 half samples for the x-derivative storage).
+__device__ __forceinline__ size_t psi_index(const AdjParams &a, int axis, int h, int s, int i, int j, int k) {
+  if (axis == 1) return (static_cast<size_t>(k) * (2 * a.nb) + s) * a.pitch + i;
+  if (axis == 2) return (static_cast<size_t>(s) * a.np[1] + j) * a.pitch + i;
+  const int xs = i < a.nb ? i : a.psx_hx[h] + (i - a.psx_far0[h]);
+  return (static_cast<size_t>(k) * a.np[1] + j) * a.psx_wx[h] + xs;
+}
+
+// Transpose of the CPML step psi' = b psi + a t, d = t + psi' (Eq. 22-23):
+// adjoint of t from the adjoint gd of d; mu (adjoint of psi') becomes the
+// adjoint of the old psi.
+__device__ __forceinline__ float pml_T(float gd, float *mu, size_t idx, float pa, float pb) {
+  const float gpsi = gd + mu[idx];
+  mu[idx] = pb * gpsi;
+  return gd + pa * gpsi;
+}
+
+__device__ __forceinline__ void cell_of(const AdjParams &a, size_t t, int &i, int &j, int &k) {
+  i = static_cast<int>(t % a.np[0]);
+  const size_t r = t / a.np[0];
+  j = static_cast<int>(r % a.np[1]);
+  k = static_cast<int>(r / a.np[1]);
+}
+__device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
+  return static_cast<size_t>(k) * a.plane + static_cast<size_t>(j) * a.pitch + i;
+}
+
+// 1a. Transpose of the H update's CPML and scaling: T[2c+t] at H_c positions.
+__global__ void k_adj_h_pre(const AdjParams a) {
+  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
+  const int R = a.rd, nb = a.nb;
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int idx[3];
+    cell_of(a, t, idx[0], idx[1], idx[2]);
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+    bool dp[3];
+    for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
+    for (int c = 0; c < 3; ++c) {
+      const int p = (c + 1) % 3, q = (c + 2) % 3;
+      const bool valid = dp[p] && dp[q];
+      const float g = -a.kappa * a.lamH[c][id];
+      for (int term = 0; term < 2; ++term) {
+        const int ax = term == 0 ? p : q;
+        float gd = term == 0 ? g : -g;
+        if (valid) {
+          const int s = slab_half(idx[ax], a.np[ax], nb);
+          if (s >= 0)
+            gd = pml_T(gd, a.muH[2 * c + term], psi_index(a, ax, 1, s, idx[0], idx[1], idx[2]),
+                       a.pml[ax][4 * nb + s], a.pml[ax][6 * nb + s]);
+        }
+        a.T[2 * c + term][id] = valid ? gd : 0.f;
+      }
+    }
+  }
+}
+
+// Gather of a transposed FD operator along axis ax: sum_q tab[idx][q] F[r],
+// r = idx + off + q (off = -R for (D+)^T, -R+1 for (D-)^T), rows off the grid
+// skipped (their coefficients are zero).
+__device__ __forceinline__ float gatherT(const AdjParams &a, const float *tab, const float *F, int ax,
+                                         const int *idx, size_t id, int off) {
+  const int M = 2 * a.rd;
+  const size_t stride = ax == 0 ? 1 : (ax == 1 ? static_cast<size_t>(a.pitch) : a.plane);
+  float acc = 0.f;
+  for (int q = 0; q < M; ++q) {
+    const int r = idx[ax] + off + q;
+    if (r < 0 || r >= a.np[ax]) continue;
+    acc = fmaf(tab[static_cast<size_t>(idx[ax]) * M + q], F[id + (static_cast<ptrdiff_t>(r) - idx[ax]) * static_cast<ptrdiff_t>(stride)], acc);
+  }
+  return acc;
+}
+
+// 1b. lambda_E_e += (D+_{e+2})^T T[2(e+1)+0] + (D+_{e+1})^T T[2(e+2)+1].
+__global__ void k_adj_h_apply(const AdjParams a) {
+  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int idx[3];
+    cell_of(a, t, idx[0], idx[1], idx[2]);
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+    for (int e = 0; e < 3; ++e) {
+      const int c1 = (e + 1) % 3, a1 = (e + 2) % 3, c2 = (e + 2) % 3, a2 = (e + 1) % 3;
+      const float s = gatherT(a, a.cpT[a1], a.T[2 * c1], a1, idx, id, -a.rd) +
+                      gatherT(a, a.cpT[a2], a.T[2 * c2 + 1], a2, idx, id, -a.rd);
+      a.lamE[e][id] += s;
+    }
+  }
+}
+
+// 2. Receivers at step n: lambda_c[stencil] += w * Re(sum_f cw f_n).
+__global__ void k_adj_receivers(const AdjParams a, int n) {
+  const int M = 2 * a.rd, M3 = M * M * M;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nrec * 6 * M3) return;
+  const int node = t % M3, rc = t / M3, c = rc % 6;
+  const double *fac = (c < 3 ? a.fE : a.fH) + static_cast<size_t>(n) * a.nf * 2;
+  double g = 0.0;
+  for (int f = 0; f < a.nf; ++f) {
+    const double *w = a.cw + (static_cast<size_t>(rc) * a.nf + f) * 2;
+    g += w[0] * fac[2 * f] - w[1] * fac[2 * f + 1];
+  }
+  const int q1 = node % M, q2 = (node / M) % M, q3 = node / (M * M);
+  const int *st = a.rec_start + rc * 3;
+  const double *wt = a.rec_w + static_cast<size_t>(rc) * 3 * M;
+  const double val = wt[q1] * wt[M + q2] * wt[2 * M + q3] * g;
+  float *F = c < 3 ? a.lamE[c] : a.lamH[c - 3];
+  atomicAdd(F + fid(a, st[0] + q1, st[1] + q2, st[2] + q3), static_cast<float>(val));
+}
+
+// 3. g_pad_c += - lambda_E_c (E1_c - E0_c) ie_c / (2 omega0 dt).
+__global__ void k_adj_grad(const AdjParams a) {
+  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int i, j, k;
+    cell_of(a, t, i, j, k);
+    const size_t id = fid(a, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+      const float dE = a.E1[c][id] - a.E0[c][id];
+      if (dE != 0.f)
+        a.gpad[c][id] -= static_cast<double>(a.lamE[c][id]) * static_cast<double>(dE) *
+                         static_cast<double>(a.ie[c][id]) * a.inv_2w0dt;
+    }
+  }
+}
+
+// 4a. Transpose of the E update's scaling and CPML: T[2e+t] at E_e positions.
+__global__ void k_adj_e_pre(const AdjParams a) {
+  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
+  const int R = a.rd, nb = a.nb;
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int idx[3];
+    cell_of(a, t, idx[0], idx[1], idx[2]);
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+    bool dm[3];
+    for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
+    for (int e = 0; e < 3; ++e) {
+      const int p = (e + 1) % 3, q = (e + 2) % 3;
+      const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
+      const float g = a.ie[e][id] * a.lamE[e][id];
+      for (int term = 0; term < 2; ++term) {
+        const int ax = term == 0 ? p : q;
+        float gd = term == 0 ? g : -g;
+        if (valid) {
+          const int s = slab_int(idx[ax], a.np[ax], nb);
+          if (s >= 0)
+            gd = pml_T(gd, a.muE[2 * e + term], psi_index(a, ax, 0, s, idx[0], idx[1], idx[2]), a.pml[ax][s],
+                       a.pml[ax][2 * nb + s]);
+        }
+        a.T[2 * e + term][id] = valid ? gd : 0.f;
+      }
+    }
+  }
+}
+
+// 4b. lambda_H_h += (D-_{h+2})^T T[2(h+1)+0] + (D-_{h+1})^T T[2(h+2)+1].
+__global__ void k_adj_e_apply(const AdjParams a) {
+  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int idx[3];
+    cell_of(a, t, idx[0], idx[1], idx[2]);
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+    for (int h = 0; h < 3; ++h) {
+      const int e1 = (h + 1) % 3, a1 = (h + 2) % 3, e2 = (h + 2) % 3, a2 = (h + 1) % 3;
+      const float s = gatherT(a, a.cmT[a1], a.T[2 * e1], a1, idx, id, 1 - a.rd) +
+                      gatherT(a, a.cmT[a2], a.T[2 * e2 + 1], a2, idx, id, 1 - a.rd);
+      a.lamH[h][id] += s;
+    }
+  }
+}
+
+// cw[r][c][f] = conj(v) * norm[c < 3 ? 0 : 1][f]  (Eq. 7 normalisation).
+__global__ void k_adj_weights(const double *v, const double *norm, double *cw, int nrec, int nf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrec * 6 * nf) return;
+  const int f = t % nf, c = (t / nf) % 6;
+  const double vr = v[2 * t], vi = -v[2 * t + 1];
+  const double *nm = norm + ((c < 3 ? 0 : 1) * nf + f) * 2;
+  cw[2 * t] = vr * nm[0] - vi * nm[1];
+  cw[2 * t + 1] = vr * nm[1] + vi * nm[0];
+}
+
+// Fold the padded gradient onto the interior samples: every padded sample
+// holds the value of the interior sample its clamped index names.
+__global__ void k_adj_fold(const AdjParams a, double *grad) {
+  const size_t nint = static_cast<size_t>(a.n[0]) * a.n[1] * a.n[2];
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < 3 * nint;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(t / nint);
+    const size_t r = t % nint;
+    const int ii = static_cast<int>(r % a.n[0]), jj = static_cast<int>((r / a.n[0]) % a.n[1]),
+              kk = static_cast<int>(r / (static_cast<size_t>(a.n[0]) * a.n[1]));
+    int lo[3], hi[3];
+    const int in[3] = {ii, jj, kk};
+    for (int ax = 0; ax < 3; ++ax) {
+      lo[ax] = in[ax] == 0 ? 0 : in[ax] + a.nbe;
+      hi[ax] = in[ax] == a.n[ax] - 1 ? a.np[ax] - 1 : in[ax] + a.nbe;
+    }
+    double s = 0.0;
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) s += a.gpad[c][fid(a, i, j, k)];
+    grad[t] = s;
+  }
+}
+
+// Byte layout of the gradient's extra workspace, after the forward one.
+struct AdjLayout {
+  size_t fwd, ck, state, nck, eh, ebytes, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], cpT[3], cmT[3], cw,
+      total;
+};
+
+AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
+  AdjLayout A{};
+  const Layout L = plan(g, s);
+  const FieldGeom fg = field_geom(g);
+  size_t off = L.total;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t cells = static_cast<size_t>(fg.pitch) * g->ax[1].npad * g->ax[2].npad;
+  const int nt = s->nt > 0 ? s->nt : 0;
+  A.fwd = L.total;
+  A.state = L.zero_end - L.E[0];           // E, H and the CPML memory
+  A.ebytes = L.H[0] - L.E[0];              // E only
+  A.nck = nt > 0 ? static_cast<size_t>((nt + K - 1) / K) : 0;
+  A.ck = take(A.nck * A.state);
+  A.eh = take(static_cast<size_t>(K + 1) * A.ebytes);
+  for (int c = 0; c < 3; ++c) A.lamE[c] = take(cells * 4);
+  for (int c = 0; c < 3; ++c) A.lamH[c] = take(cells * 4);
+  for (int c = 0; c < 6; ++c) A.T[c] = take(cells * 4);
+  for (int c = 0; c < 6; ++c) A.muE[c] = take((c < 5 ? L.psiE[c + 1] : L.psiH[0]) - L.psiE[c]);
+  for (int c = 0; c < 6; ++c) A.muH[c] = take((c < 5 ? L.psiH[c + 1] : L.vacc) - L.psiH[c]);
+  for (int c = 0; c < 3; ++c) A.gpad[c] = take(cells * 8);
+  const size_t m = 2 * static_cast<size_t>(g->rd);
+  for (int a = 0; a < 3; ++a) A.cpT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  for (int a = 0; a < 3; ++a) A.cmT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  A.cw = take(static_cast<size_t>(s->nrec > 0 ? s->nrec : 1) * 6 * s->nfreq * 2 * sizeof(double));
+  A.total = off;
+  return A;
+}
+
+// Transposed FD rows in gather form.  D+ row r (half sample r, valid for
+// rd-1 <= r <= npad-1-rd) reads integer samples r-rd+1 .. r+rd; its transpose
+// at integer sample i gathers rows r = i-rd+q, q = 0..2rd-1, with coefficient
+// cp[r][2rd-1-q].  D- row r (integer sample, valid rd <= r <= npad-1-rd)
+// reads half samples r-rd .. r+rd-1; its transpose at half sample i gathers
+// rows r = i-rd+1+q with coefficient cm[r][2rd-1-q].  Invalid rows give 0.
+void transposed_rows(const Axis &ax, int rd, std::vector<float> &pT, std::vector<float> &mT) {
+  const int np = ax.npad, M = 2 * rd;
+  pT.assign(static_cast<size_t>(np) * M, 0.f);
+  mT.assign(static_cast<size_t>(np) * M, 0.f);
+  for (int i = 0; i < np; ++i)
+    for (int q = 0; q < M; ++q) {
+      const int rp = i - rd + q;
+      if (rp >= rd - 1 && rp <= np - 1 - rd) pT[static_cast<size_t>(i) * M + q] = static_cast<float>(ax.cp[static_cast<size_t>(rp) * M + M - 1 - q]);
+      const int rm = i - rd + 1 + q;
+      if (rm >= rd && rm <= np - 1 - rd) mT[static_cast<size_t>(i) * M + q] = static_cast<float>(ax.cm[static_cast<size_t>(rm) * M + M - 1 - q]);
+    }
+}
+
+int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int K, void *ws,
+                  size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs) {
+  int st = check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (K < 1 || s->volume || !grad || !sigma || !ws || (s->nrec > 0 && (!dG || !rec_out))) return EMM_EINVAL;
+  const AdjLayout A = adj_plan(g, s, K);
+  if (ws_bytes < A.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
+  Prepared P;
+  st = prepare_forward(g, s, sigma, ws, A.fwd, rec_out, nullptr, cs, &P);
+  if (st != EMM_OK) return st;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  const Layout &L = P.L;
+  const int nt = s->nt, nf = s->nfreq, rd = g->rd;
+
+  // forward sweep with checkpoints; the receivers accumulate G on the way
+  cudaError_t e = cudaSuccess;
+  for (int it0 = 0; it0 < nt && e == cudaSuccess; it0 += K) {
+    e = cudaMemcpyAsync(base + A.ck + static_cast<size_t>(it0 / K) * A.state, base + L.E[0], A.state,
+                        cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess) e = run_steps(P, P.p, P.blocks, it0, std::min(it0 + K, nt), cs, nullptr);
+  }
+  if (e != cudaSuccess) return EMM_ECUDA;
+  st = finalize_forward(P, s, rec_out, nullptr, cs);
+  if (st != EMM_OK) return st;
+
+  // adjoint state and tables
+  AdjParams a{};
+  for (int ax = 0; ax < 3; ++ax) {
+    a.np[ax] = P.p.np[ax];
+    a.n[ax] = P.p.n[ax];
+    a.pml[ax] = P.p.pml[ax];
+    a.cpT[ax] = reinterpret_cast<const float *>(base + A.cpT[ax]);
+    a.cmT[ax] = reinterpret_cast<const float *>(base + A.cmT[ax]);
+  }
+  a.pitch = P.p.pitch;
+  a.plane = P.p.plane;
+  a.nb = g->nb;
+  a.rd = rd;
+  a.nbe = P.p.nbe;
+  a.kappa = P.p.dt_mu;
+  a.inv_2w0dt = 1.0 / (2.0 * s->omega0 * P.dt);
+  const int xs = P.fg.xshift;
+  for (int c = 0; c < 3; ++c) {
+    a.ie[c] = P.p.ie[c];
+    a.lamE[c] = reinterpret_cast<float *>(base + A.lamE[c]) + xs;
+    a.lamH[c] = reinterpret_cast<float *>(base + A.lamH[c]) + xs;
+    a.gpad[c] = reinterpret_cast<double *>(base + A.gpad[c]) + xs;
+  }
+  for (int c = 0; c < 6; ++c) {
+    a.T[c] = reinterpret_cast<float *>(base + A.T[c]) + xs;
+    const int shift = psi_axis(c) == 0 ? 0 : xs;
+    a.muE[c] = reinterpret_cast<float *>(base + A.muE[c]) + shift;
+    a.muH[c] = reinterpret_cast<float *>(base + A.muH[c]) + shift;
+  }
+  for (int h = 0; h < 2; ++h) {
+    a.psx_hx[h] = P.p.psx_hx[h];
+    a.psx_wx[h] = P.p.psx_wx[h];
+    a.psx_far0[h] = P.p.psx_far0[h];
+  }
+  a.nrec = s->nrec;
+  a.nf = nf;
+  a.rec_start = P.p.rec_start;
+  a.rec_w = P.p.rec_w;
+  a.cw = reinterpret_cast<const double *>(base + A.cw);
+  a.fE = P.p.fE;
+  a.fH = P.p.fH;
+
+  // everything from the first adjoint field to the gradient starts at zero
+  e = cudaMemsetAsync(base + A.lamE[0], 0, A.cpT[0] - A.lamE[0], cs);
+  std::vector<float> pT, mT;
+  for (int ax = 0; ax < 3 && e == cudaSuccess; ++ax) {
+    transposed_rows(g->ax[ax], rd, pT, mT);
+    e = cudaMemcpyAsync(base + A.cpT[ax], pT.data(), pT.size() * 4, cudaMemcpyHostToDevice, cs);
+    // pageable sources: each copy has taken the data when it returns
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + A.cmT[ax], mT.data(), mT.size() * 4, cudaMemcpyHostToDevice, cs);
+  }
+  if (e != cudaSuccess) return EMM_ECUDA;
+  if (s->nrec > 0) {
+    const int tot = s->nrec * 6 * nf;
+    k_adj_weights<<<(tot + 255) / 256, 256, 0, cs>>>(dG, reinterpret_cast<const double *>(base + L.norm),
+                                                     reinterpret_cast<double *>(base + A.cw), s->nrec, nf);
+  }
+
+  // recomputation runs without receivers (G is already accumulated)
+  DevParams pr = P.p;
+  pr.nrec = 0;
+  pr.rec_blocks = 0;
+  pr.rec_layers = 0;
+  const dim3 blocks_r(P.p.tiles_x, P.p.tiles_y, P.p.tiles_z);
+  const int grid_cells = P.sms * 8;
+  const int M = 2 * rd, rec_threads = s->nrec * 6 * M * M * M;
+  for (int seg = static_cast<int>(A.nck) - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int it0 = seg * K, it1 = std::min(it0 + K, nt);
+    e = cudaMemcpyAsync(base + L.E[0], base + A.ck + static_cast<size_t>(seg) * A.state, A.state,
+                        cudaMemcpyDeviceToDevice, cs);
+    for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
+      e = cudaMemcpyAsync(base + A.eh + static_cast<size_t>(it - it0) * A.ebytes, base + L.E[0], A.ebytes,
+                          cudaMemcpyDeviceToDevice, cs);
+      if (e == cudaSuccess) e = run_steps(P, pr, blocks_r, it, it + 1, cs, nullptr);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + A.eh + static_cast<size_t>(it1 - it0) * A.ebytes, base + L.E[0], A.ebytes,
+                          cudaMemcpyDeviceToDevice, cs);
+    for (int it = it1 - 1; it >= it0 && e == cudaSuccess; --it) {
+      for (int c = 0; c < 3; ++c) {
+        const size_t ec = L.E[c] - L.E[0];
+        a.E0[c] = reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0) * A.ebytes + ec) + xs;
+        a.E1[c] =
+            reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0 + 1) * A.ebytes + ec) + xs;
+      }
+      k_adj_h_pre<<<grid_cells, kThreads, 0, cs>>>(a);
+      k_adj_h_apply<<<grid_cells, kThreads, 0, cs>>>(a);
+      if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
+      k_adj_grad<<<grid_cells, kThreads, 0, cs>>>(a);
+      k_adj_e_pre<<<grid_cells, kThreads, 0, cs>>>(a);
+      k_adj_e_apply<<<grid_cells, kThreads, 0, cs>>>(a);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) return EMM_ECUDA;
+  k_adj_fold<<<grid_cells, kThreads, 0, cs>>>(a, grad);
+  return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+}  // namespace
+}  // namespace emm
+
+extern "C" {
+
+int emm_gradient_workspace_size(const emm_grid *g, const emm_survey *s, int ckpt_every, size_t *bytes) {
+  const int st = emm::check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (!bytes || ckpt_every < 1 || s->volume) return EMM_EINVAL;
+  *bytes = emm::adj_plan(g, s, ckpt_every).total;
+  return EMM_OK;
+}
+
+int emm_gradient(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int ckpt_every,
+                 void *ws, size_t ws_bytes, double *rec_out, double *grad, emm_stream stream) {
+  return emm::gradient_impl(g, s, sigma, dG, ckpt_every, ws, ws_bytes, rec_out, grad,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

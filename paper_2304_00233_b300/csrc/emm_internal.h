@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime_api.h>
 #include <vector_types.h>
 
 #include "../../include/emm.h"
@@ -81,5 +82,60 @@ struct DevParams {
   const float *fE32, *fH32;    // [nt][nf][2] FP32 copies of the factors for the volume
   int *status;
 };
+
+// ---- host-side pieces shared by the forward and the gradient entry points ----
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Tiling of the padded grid and the matching field-array geometry.  Tiles
+// start at org[a] <= 0, chosen so that a tile edge falls on the first
+// CPML-free sample max(nb, rd) (x: rounded down to a multiple of 4 for the
+// TMA boxes), which maximises the CTAs that take the interior path.  Field
+// rows hold xshift = -org[0] leading samples, so every tile row starts on a
+// 128-byte line; the row pitch is a multiple of 32 samples.
+struct FieldGeom {
+  int org[3], tiles[3], xshift, pitch;
+  int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage: [0] integer, [1] half samples
+};
+FieldGeom field_geom(const emm_grid *g);
+
+// Byte layout of the device workspace.
+struct Layout {
+  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], vacc, zero_end;
+  size_t cm[3], cp[3], pml[3], jw[3], amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
+};
+
+Layout plan(const emm_grid *g, const emm_survey *s);
+int check_survey(const emm_grid *g, const emm_survey *s);
+
+// Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
+inline int psi_axis(int c) { return (c % 2 == 0) ? (c / 2 + 1) % 3 : (c / 2 + 2) % 3; }
+
+// Optional per-launch timing: events before/after the E and H launches of
+// every `every`-th step (3 events per timed step).
+struct StepEvents {
+  int every = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+// A forward run set up in a workspace: the launch parameters of its steps.
+struct Prepared {
+  DevParams p;
+  Layout L;
+  FieldGeom fg;
+  dim3 blocks;
+  double dt;
+  int sms, rd;
+};
+
+// Validate, upload the tables, clear the state and compute dt/eps (enqueued
+// on cs); fills *out.  Host-detected errors enqueue nothing.
+int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out);
+// Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
+cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
+                      StepEvents *te);
+// Enqueue the Green's-function normalisation of the receivers (and volume).
+int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, double *vol_out, cudaStream_t cs);
 
 }  // namespace emm

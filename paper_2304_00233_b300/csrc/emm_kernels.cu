@@ -909,21 +909,11 @@ __global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *no
   }
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // Host side of emm_forward
 // ---------------------------------------------------------------------------
-constexpr size_t kAlign = 256;
-inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-// Tiling of the padded grid and the matching field-array geometry.  Tiles
-// start at org[a] <= 0, chosen so that a tile edge falls on the first
-// CPML-free sample max(nb, rd) (x: rounded down to a multiple of 4 for the
-// TMA boxes), which maximises the CTAs that take the interior path.  Field
-// rows hold xshift = -org[0] leading samples, so every tile row starts on a
-// 128-byte line; the row pitch is a multiple of 32 samples.
-struct FieldGeom {
-  int org[3], tiles[3], xshift, pitch;
-  int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage: [0] integer, [1] half samples
-};
 FieldGeom field_geom(const emm_grid *g) {
   FieldGeom f{};
   const int lo = std::max(g->nb, g->rd);
@@ -949,12 +939,6 @@ FieldGeom field_geom(const emm_grid *g) {
   return f;
 }
 
-// Byte layout of the device workspace.
-struct Layout {
-  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], vacc, zero_end;
-  size_t cm[3], cp[3], pml[3], jw[3], amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
-};
-
 // Elements of one CPML memory array (layouts in the kernels' comment).
 size_t psi_elems(const emm_grid *g, int axis, int half) {
   const FieldGeom f = field_geom(g);
@@ -965,8 +949,6 @@ size_t psi_elems(const emm_grid *g, int axis, int half) {
   return nb2 * p1 * static_cast<size_t>(f.pitch);
 }
 
-// Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
-inline int psi_axis(int c) { return (c % 2 == 0) ? (c / 2 + 1) % 3 : (c / 2 + 2) % 3; }
 
 Layout plan(const emm_grid *g, const emm_survey *s) {
   Layout L{};
@@ -1055,15 +1037,8 @@ bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
          make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
-// Optional per-launch timing: events before/after the E and H launches of
-// every `every`-th step (3 events per timed step).
-struct StepEvents {
-  int every = 0;
-  std::vector<cudaEvent_t> ev;
-};
-
 template <int R, bool VOL>
-cudaError_t launch_steps(const DevParams &p, int nt, dim3 blocks, cudaStream_t st, StepEvents *te) {
+cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
@@ -1074,7 +1049,7 @@ cudaError_t launch_steps(const DevParams &p, int nt, dim3 blocks, cudaStream_t s
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   size_t used = 0;
-  for (int n = 0; n < nt; ++n) {
+  for (int n = n0; n < n1; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
     k_update_E<R, VOL><<<blocks, NT, sb, st>>>(p, tE, n);
@@ -1088,14 +1063,13 @@ cudaError_t launch_steps(const DevParams &p, int nt, dim3 blocks, cudaStream_t s
   return cudaGetLastError();
 }
 
-int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
-                 double *rec_out, double *vol_out, emm_stream stream, StepEvents *te) {
+int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
   const Layout L = plan(g, s);
   if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
-  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   const int rd = g->rd, m = 2 * rd, nf = s->nfreq, nt = s->nt, nb = g->nb;
   const int nbe = g->nb + g->ne;
 
@@ -1291,33 +1265,55 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
                                      reinterpret_cast<float *>(base + L.ie[2]), p.n[0], p.n[1], p.n[2], p.np[0],
                                      p.np[1], p.np[2], p.pitch, fg.xshift, nbe, 2.0 * s->omega0 * dt, s->sigma_min,
                                      p.status);
+  out->p = p;
+  out->L = L;
+  out->fg = fg;
+  out->blocks = blocks;
+  out->dt = dt;
+  out->sms = sms;
+  out->rd = rd;
+  return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
+                      StepEvents *te) {
   const bool vol = p.vacc != nullptr;
-  switch (rd) {
-    case 1: e = vol ? launch_steps<1, true>(p, nt, blocks, cs, te) : launch_steps<1, false>(p, nt, blocks, cs, te);
-      break;
-    case 2: e = vol ? launch_steps<2, true>(p, nt, blocks, cs, te) : launch_steps<2, false>(p, nt, blocks, cs, te);
-      break;
-    case 3: e = vol ? launch_steps<3, true>(p, nt, blocks, cs, te) : launch_steps<3, false>(p, nt, blocks, cs, te);
-      break;
-    default: e = vol ? launch_steps<4, true>(p, nt, blocks, cs, te) : launch_steps<4, false>(p, nt, blocks, cs, te);
-      break;
+  switch (P.rd) {
+    case 1: return vol ? launch_steps<1, true>(p, n0, n1, blocks, cs, te) : launch_steps<1, false>(p, n0, n1, blocks, cs, te);
+    case 2: return vol ? launch_steps<2, true>(p, n0, n1, blocks, cs, te) : launch_steps<2, false>(p, n0, n1, blocks, cs, te);
+    case 3: return vol ? launch_steps<3, true>(p, n0, n1, blocks, cs, te) : launch_steps<3, false>(p, n0, n1, blocks, cs, te);
+    default: return vol ? launch_steps<4, true>(p, n0, n1, blocks, cs, te) : launch_steps<4, false>(p, n0, n1, blocks, cs, te);
   }
-  if (e != cudaSuccess) return EMM_ECUDA;
-  const double *dnorm = reinterpret_cast<const double *>(base + L.norm);
+}
+
+int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, double *vol_out, cudaStream_t cs) {
+  const int nf = s->nfreq;
+  const double *dnorm = reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(P.p.status) -
+                                                         P.L.status + P.L.norm);
   if (s->nrec > 0) {
     const int tot = s->nrec * 6 * nf;
     k_finalize_rec<<<(tot + 255) / 256, 256, 0, cs>>>(rec_out, dnorm, s->nrec, nf);
   }
   if (s->volume) {
-    const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-    k_finalize_vol<<<8 * sms, 256, 0, cs>>>(p.vacc, vol_out, dnorm, nint, nf);
+    const size_t nint = static_cast<size_t>(P.p.n[0]) * P.p.n[1] * P.p.n[2];
+    k_finalize_vol<<<8 * P.sms, 256, 0, cs>>>(P.p.vacc, vol_out, dnorm, nint, nf);
   }
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
+int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                 double *rec_out, double *vol_out, emm_stream stream, StepEvents *te) {
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  int st = prepare_forward(g, s, sigma, ws, ws_bytes, rec_out, vol_out, cs, &P);
+  if (st != EMM_OK) return st;
+  if (run_steps(P, P.p, P.blocks, 0, s->nt, cs, te) != cudaSuccess) return EMM_ECUDA;
+  return finalize_forward(P, s, rec_out, vol_out, cs);
+}
+
 // Device address of emm_static_scratch on the current device, looked up once
 // per device (with that device current) and cached.
-int static_scratch(void **ptr) {
+static int static_scratch(void **ptr) {
   constexpr int kMaxDevices = 64;
   static std::mutex mu;
   static void *addr[kMaxDevices] = {};
@@ -1335,7 +1331,6 @@ int static_scratch(void **ptr) {
   return EMM_OK;
 }
 
-}  // namespace
 }  // namespace emm
 
 using namespace emm;
