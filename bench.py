@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
     ap.add_argument("--timesteps", type=int, default=0,
                     help="override the leapfrog steps per solve (short profiling runs only)")
     args = ap.parse_args()
@@ -321,6 +323,26 @@ def main():
         "gpu_launches": kernel_launches,
         "clocks": clocks,
     }
+    if not args.no_gradient:
+        # gradient of Re(sum conj(v) G) for a seeded cotangent v: one warm-up
+        # call, one timed call (CUDA events), against one forward solve
+        rng = np.random.default_rng(230400237)
+        v = rng.standard_normal((survey.nrec, 6, len(wl.freqs))) + 1j * rng.standard_normal(
+            (survey.nrec, 6, len(wl.freqs)))
+        vt = torch.from_numpy(v).cuda()
+        ck = max(1, int(round(nt ** 0.5)))
+        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, check=False)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        grad_ms = max_over_ranks(g0.elapsed_time(g1) / 1e3) * 1e3
+        fwd_ms = 1e3 * elapsed / args.steps
+        line["gradient"] = {"ms": grad_ms, "forward_ms": fwd_ms, "ratio_to_forward": grad_ms / fwd_ms,
+                            "ckpt_every": ck, "what": "emm_gradient: forward sweep with checkpoints, "
+                            "recomputation and the adjoint sweep, one cotangent of all receiver data"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W.WORKLOADS[args.workload]())
     if rank == 0:

@@ -17,7 +17,8 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
 
 # FP32 forward and adjoint fields against FP64: relative L2 of the gradient
-GRAD_TOL = 2e-3
+# (measured on B300: 0.9e-7 .. 2.1e-7 for these cases)
+GRAD_TOL = 1e-5
 
 CASES = [dict(rd=1, n=(22, 20, 18)), dict(rd=2, n=(23, 19, 17)), dict(rd=3, n=(26, 22, 20)),
          dict(rd=4, n=(28, 26, 24))]
