@@ -177,6 +177,34 @@ def cpu_baseline(wl, budget_s=15.0):
                       f"{t:.1f} s"}
 
 
+# ---- multi-GPU (one process per GPU): sharding over transmitters ----
+TOW_SPACING = 200.0  # m between the transmitters of consecutive ranks
+
+
+def rank_source(src, rank):
+    """Transmitter of rank `rank`: the workload's, shifted along the tow line
+    (x) by rank * 200 m.  Sources are independent problems, so ranks share
+    nothing but the timing (weak scaling)."""
+    return np.asarray(src, dtype=np.float64) + np.array([TOW_SPACING * rank, 0.0, 0.0])
+
+
+def max_over_ranks(v, dist=None, device="cpu"):
+    """The slowest rank's value (the job's time): all-reduce MAX, or v itself
+    in a single process."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, cells, nt, steps, seconds):
+    """Whole-job throughput in Gcell-steps/s: every rank advances `cells`
+    padded cells `nt` steps per solve, `steps` solves, in `seconds`."""
+    return world * cells * nt * steps / seconds / 1e9
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on the host cores, each step a
     bounded sample (a fixed number of leapfrog steps) of the same workload."""
@@ -236,7 +264,7 @@ def main():
 
     wl = W.WORKLOADS[args.workload]()
     # weak scaling: rank r solves the transmitter shifted 200 m along the tow line
-    wl.src = wl.src + np.array([200.0 * rank, 0.0, 0.0])
+    wl.src = rank_source(wl.src, rank)
     grid = emm.grid_for(wl)
     nt = args.timesteps if args.timesteps > 0 else emm.steps_for(wl, grid)
     survey = emm.survey_for(wl, nt=nt)
@@ -256,12 +284,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def job_max(v):
+        return max_over_ranks(v, dist, "cuda")
 
     # ---- timed region: K device-resident solves ----
     e_ms, h_ms = [], []
@@ -275,9 +299,9 @@ def main():
             h_ms.append(t["h_ms"])
         ev1.record(stream)
         barrier()
-    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    elapsed = job_max(ev0.elapsed_time(ev1) / 1e3)
     clocks = clk.summary()
-    value = world * cells * nt * args.steps / elapsed / 1e9
+    value = aggregate_rate(world, cells, nt, args.steps, elapsed)
 
     # ---- e2e: pinned host sigma in, receiver Green's functions out ----
     rec_host = torch.empty(work.rec.shape, dtype=work.rec.dtype).pin_memory()
@@ -288,9 +312,9 @@ def main():
         emm.forward_async(grid, survey, sig_dev, work)
         rec_host.copy_(work.rec, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = job_max(time.perf_counter() - t0)
     barrier()
-    e2e_value = world * cells * nt * args.steps / e2e_s / 1e9
+    e2e_value = aggregate_rate(world, cells, nt, args.steps, e2e_s)
 
     peak, peak_kind = measured_peaks()
     e_mean, h_mean = float(np.mean(e_ms)), float(np.mean(h_ms))
@@ -338,7 +362,7 @@ def main():
         emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, check=False)
         g1.record(stream)
         torch.cuda.synchronize()
-        grad_ms = max_over_ranks(g0.elapsed_time(g1) / 1e3) * 1e3
+        grad_ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
         fwd_ms = 1e3 * elapsed / args.steps
         line["gradient"] = {"ms": grad_ms, "forward_ms": fwd_ms, "ratio_to_forward": grad_ms / fwd_ms,
                             "ckpt_every": ck, "what": "emm_gradient: forward sweep with checkpoints, "
