@@ -21,7 +21,8 @@
 //   1. H update:  per-derivative adjoints T = -dt/mu0 lambda_H (CPML memory
 //      adjoints updated), then lambda_E += (D+)^T T  (transposed-row gather);
 //   2. receivers: lambda += interpolation^T of Re(conj(v) norm f_n);
-//   3. gradient:  g_pad += - lambda_E (E^{n+1} - E^n) / sigma   (FP64);
+//   3. gradient:  g += - lambda_E (E^{n+1} - E^n) / sigma (FP32 within a
+//      checkpoint segment, added into FP64 at its end);
 //   4. E update:  T = ie lambda_E (CPML), then lambda_H += (D-)^T T.
 // Finally the padded gradient is folded onto the interior samples the pads
 // replicate.  Adjoint fields are FP32 like the forward fields; the gradient
@@ -54,6 +55,7 @@ struct AdjParams {
   const float *cmT[3];       // transposed D- rows, gather form [rows][2rd]
   const float *E0[3], *E1[3];  // forward E before / after the step
   double *gpad[3];           // dL/dsigma on the padded grid (field layout)
+  float *gseg[3];            // the current segment's share, FP32, flushed into gpad
   int nrec, nf;
   const int *rec_start;      // [nrec][6][3]
   const double *rec_w;       // [nrec][6][3][2rd]
@@ -87,11 +89,13 @@ __device__ __forceinline__ float pml_T(float gd, float *mu, size_t idx, float pa
   return gd + pa * gpsi;
 }
 
-__device__ __forceinline__ void cell_of(const AdjParams &a, size_t t, int &i, int &j, int &k) {
-  i = static_cast<int>(t % a.np[0]);
-  const size_t r = t / a.np[0];
-  j = static_cast<int>(r % a.np[1]);
-  k = static_cast<int>(r / a.np[1]);
+// Cell of this thread in a 3-D launch of 32 x 8 threads per (x, y) tile and
+// one grid z layer per plane; false outside the padded grid.
+__device__ __forceinline__ bool cell3(const AdjParams &a, int *idx) {
+  idx[0] = blockIdx.x * 32 + threadIdx.x;
+  idx[1] = blockIdx.y * 8 + threadIdx.y;
+  idx[2] = blockIdx.z;
+  return idx[0] < a.np[0] && idx[1] < a.np[1];
 }
 __device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
   return static_cast<size_t>(k) * a.plane + static_cast<size_t>(j) * a.pitch + i;
@@ -99,12 +103,10 @@ __device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
 
 // 1a. Transpose of the H update's CPML and scaling: T[2c+t] at H_c positions.
 __global__ void k_adj_h_pre(const AdjParams a) {
-  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
   const int R = a.rd, nb = a.nb;
-  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
-       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int idx[3];
-    cell_of(a, t, idx[0], idx[1], idx[2]);
+  int idx[3];
+  if (!cell3(a, idx)) return;
+  {
     const size_t id = fid(a, idx[0], idx[1], idx[2]);
     bool dp[3];
     for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
@@ -145,11 +147,9 @@ __device__ __forceinline__ float gatherT(const AdjParams &a, const float *tab, c
 
 // 1b. lambda_E_e += (D+_{e+2})^T T[2(e+1)+0] + (D+_{e+1})^T T[2(e+2)+1].
 __global__ void k_adj_h_apply(const AdjParams a) {
-  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
-  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
-       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int idx[3];
-    cell_of(a, t, idx[0], idx[1], idx[2]);
+  int idx[3];
+  if (!cell3(a, idx)) return;
+  {
     const size_t id = fid(a, idx[0], idx[1], idx[2]);
     for (int e = 0; e < 3; ++e) {
       const int c1 = (e + 1) % 3, a1 = (e + 2) % 3, c2 = (e + 2) % 3, a2 = (e + 1) % 3;
@@ -180,38 +180,24 @@ __global__ void k_adj_receivers(const AdjParams a, int n) {
   atomicAdd(F + fid(a, st[0] + q1, st[1] + q2, st[2] + q3), static_cast<float>(val));
 }
 
-// 3. g_pad_c += - lambda_E_c (E1_c - E0_c) ie_c / (2 omega0 dt).
-__global__ void k_adj_grad(const AdjParams a) {
-  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
-  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
-       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int i, j, k;
-    cell_of(a, t, i, j, k);
-    const size_t id = fid(a, i, j, k);
-    for (int c = 0; c < 3; ++c) {
-      const float dE = a.E1[c][id] - a.E0[c][id];
-      if (dE != 0.f)
-        a.gpad[c][id] -= static_cast<double>(a.lamE[c][id]) * static_cast<double>(dE) *
-                         static_cast<double>(a.ie[c][id]) * a.inv_2w0dt;
-    }
-  }
-}
-
-// 4a. Transpose of the E update's scaling and CPML: T[2e+t] at E_e positions.
+// 3 + 4a. Gradient term g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e / (2 omega0
+// dt) (lambda_E is final for this step here), then the transpose of the E
+// update's scaling and CPML: T[2e+t] at E_e positions.
 __global__ void k_adj_e_pre(const AdjParams a) {
-  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
   const int R = a.rd, nb = a.nb;
-  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
-       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int idx[3];
-    cell_of(a, t, idx[0], idx[1], idx[2]);
+  int idx[3];
+  if (!cell3(a, idx)) return;
+  {
     const size_t id = fid(a, idx[0], idx[1], idx[2]);
     bool dm[3];
     for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
     for (int e = 0; e < 3; ++e) {
       const int p = (e + 1) % 3, q = (e + 2) % 3;
       const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
-      const float g = a.ie[e][id] * a.lamE[e][id];
+      const float lam = a.lamE[e][id], ie = a.ie[e][id];
+      const float dE = a.E1[e][id] - a.E0[e][id];
+      if (dE != 0.f) a.gseg[e][id] -= static_cast<float>(static_cast<double>(lam) * dE * ie * a.inv_2w0dt);
+      const float g = ie * lam;
       for (int term = 0; term < 2; ++term) {
         const int ax = term == 0 ? p : q;
         float gd = term == 0 ? g : -g;
@@ -229,17 +215,29 @@ __global__ void k_adj_e_pre(const AdjParams a) {
 
 // 4b. lambda_H_h += (D-_{h+2})^T T[2(h+1)+0] + (D-_{h+1})^T T[2(h+2)+1].
 __global__ void k_adj_e_apply(const AdjParams a) {
-  const size_t cells = static_cast<size_t>(a.np[0]) * a.np[1] * a.np[2];
-  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < cells;
-       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int idx[3];
-    cell_of(a, t, idx[0], idx[1], idx[2]);
+  int idx[3];
+  if (!cell3(a, idx)) return;
+  {
     const size_t id = fid(a, idx[0], idx[1], idx[2]);
     for (int h = 0; h < 3; ++h) {
       const int e1 = (h + 1) % 3, a1 = (h + 2) % 3, e2 = (h + 2) % 3, a2 = (h + 1) % 3;
       const float s = gatherT(a, a.cmT[a1], a.T[2 * e1], a1, idx, id, 1 - a.rd) +
                       gatherT(a, a.cmT[a2], a.T[2 * e2 + 1], a2, idx, id, 1 - a.rd);
       a.lamH[h][id] += s;
+    }
+  }
+}
+
+// End of a checkpoint segment: g_pad += g_seg (FP64), g_seg = 0.
+__global__ void k_adj_flush(const AdjParams a) {
+  int idx[3];
+  if (!cell3(a, idx)) return;
+  const size_t id = fid(a, idx[0], idx[1], idx[2]);
+  for (int c = 0; c < 3; ++c) {
+    const float g = a.gseg[c][id];
+    if (g != 0.f) {
+      a.gpad[c][id] += static_cast<double>(g);
+      a.gseg[c][id] = 0.f;
     }
   }
 }
@@ -281,7 +279,7 @@ __global__ void k_adj_fold(const AdjParams a, double *grad) {
 
 // Byte layout of the gradient's extra workspace, after the forward one.
 struct AdjLayout {
-  size_t fwd, ck, state, nck, eh, ebytes, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], cpT[3], cmT[3], cw,
+  size_t fwd, ck, state, nck, eh, ebytes, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
       total;
 };
 
@@ -309,6 +307,7 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
   for (int c = 0; c < 6; ++c) A.muE[c] = take((c < 5 ? L.psiE[c + 1] : L.psiH[0]) - L.psiE[c]);
   for (int c = 0; c < 6; ++c) A.muH[c] = take((c < 5 ? L.psiH[c + 1] : L.vacc) - L.psiH[c]);
   for (int c = 0; c < 3; ++c) A.gpad[c] = take(cells * 8);
+  for (int c = 0; c < 3; ++c) A.gseg[c] = take(cells * 4);
   const size_t m = 2 * static_cast<size_t>(g->rd);
   for (int a = 0; a < 3; ++a) A.cpT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) A.cmT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
@@ -383,6 +382,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
     a.lamE[c] = reinterpret_cast<float *>(base + A.lamE[c]) + xs;
     a.lamH[c] = reinterpret_cast<float *>(base + A.lamH[c]) + xs;
     a.gpad[c] = reinterpret_cast<double *>(base + A.gpad[c]) + xs;
+    a.gseg[c] = reinterpret_cast<float *>(base + A.gseg[c]) + xs;
   }
   for (int c = 0; c < 6; ++c) {
     a.T[c] = reinterpret_cast<float *>(base + A.T[c]) + xs;
@@ -426,6 +426,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   pr.rec_layers = 0;
   const dim3 blocks_r(P.p.tiles_x, P.p.tiles_y, P.p.tiles_z);
   const int grid_cells = P.sms * 8;
+  const dim3 tb(32, 8, 1), grid3((P.p.np[0] + 31) / 32, (P.p.np[1] + 7) / 8, P.p.np[2]);
   const int M = 2 * rd, rec_threads = s->nrec * 6 * M * M * M;
   for (int seg = static_cast<int>(A.nck) - 1; seg >= 0 && e == cudaSuccess; --seg) {
     const int it0 = seg * K, it1 = std::min(it0 + K, nt);
@@ -446,12 +447,15 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
         a.E1[c] =
             reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0 + 1) * A.ebytes + ec) + xs;
       }
-      k_adj_h_pre<<<grid_cells, kThreads, 0, cs>>>(a);
-      k_adj_h_apply<<<grid_cells, kThreads, 0, cs>>>(a);
+      k_adj_h_pre<<<grid3, tb, 0, cs>>>(a);
+      k_adj_h_apply<<<grid3, tb, 0, cs>>>(a);
       if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
-      k_adj_grad<<<grid_cells, kThreads, 0, cs>>>(a);
-      k_adj_e_pre<<<grid_cells, kThreads, 0, cs>>>(a);
-      k_adj_e_apply<<<grid_cells, kThreads, 0, cs>>>(a);
+      k_adj_e_pre<<<grid3, tb, 0, cs>>>(a);
+      k_adj_e_apply<<<grid3, tb, 0, cs>>>(a);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_adj_flush<<<grid3, tb, 0, cs>>>(a);
       e = cudaGetLastError();
     }
   }
