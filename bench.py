@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
+    ap.add_argument("--batch", type=int, default=8,
+                    help="transmitters of the batched-survey line (emm_forward_batch; 0 = skip)")
     ap.add_argument("--timesteps", type=int, default=0,
                     help="override the leapfrog steps per solve (short profiling runs only)")
     args = ap.parse_args()
@@ -347,6 +349,26 @@ def main():
         "gpu_launches": kernel_launches,
         "clocks": clocks,
     }
+    if args.batch > 0:
+        # batched survey: transmitters every 200 m along the tow line
+        # (x = -3100 + 200 k, 50 m above the seabed), advanced together;
+        # one warm-up solve, one timed solve (CUDA events)
+        pos = np.array([[-3100.0 + TOW_SPACING * (k + args.batch * rank), 0.0, float(wl.src[2])]
+                        for k in range(args.batch)])
+        _, bwork = emm.forward_batch(grid, survey, sigma, pos)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        emm.forward_batch(grid, survey, sigma, pos, work=bwork, check=False)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bsec = job_max(b0.elapsed_time(b1) / 1e3)
+        bval = aggregate_rate(world, cells * args.batch, nt, 1, bsec)
+        del bwork
+        line["batch"] = {"nsrc": args.batch, "value": bval, "unit": "Gcell-steps/s", "ms_per_solve": 1e3 * bsec,
+                         "vs_one_at_a_time": bval / value,
+                         "what": "emm_forward_batch: transmitters sharing grid, sigma and receivers in the same "
+                                 "launches, against the device-resident single-transmitter value"}
     if not args.no_gradient:
         # gradient of Re(sum conj(v) G) for a seeded cotangent v: one warm-up
         # call, one timed call (CUDA events), against one forward solve

@@ -192,6 +192,24 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
  * are then undefined).  EMM_ECUDA if the copy fails. */
 int emm_status(const void *ws, int *status, emm_stream stream);
 
+/* Device workspace bytes emm_forward_batch needs for nsrc transmitters (one
+ * shared dt/eps and table set, nsrc field and CPML state blocks).
+ * EMM_EINVAL on bad input, nsrc < 1 or survey->volume set. */
+int emm_batch_workspace_size(const emm_grid *grid, const emm_survey *survey, int nsrc, size_t *bytes);
+
+/* emm_forward for nsrc transmitters on one grid and one conductivity, all
+ * advanced in the same launches (the independent transmitters of a survey,
+ * one MPI rank each in the paper's Sec. 5.3 set-up).  Each transmitter has
+ * its own fields and CPML memory; dt/eps, the tables, the receivers, the
+ * wavelet and the source orientation and moment (from `survey`) are shared.
+ *   src_pos   host double [nsrc][3]: transmitter positions (survey->src is
+ *             ignored); each must pass the checks of emm_locate.
+ *   rec_out   device double [nsrc][nrec][6][nfreq][2].
+ *   ws        device workspace of emm_batch_workspace_size bytes.
+ * Other arguments, asynchrony and errors as emm_forward; no volume DTFT. */
+int emm_forward_batch(const emm_grid *grid, const emm_survey *survey, int nsrc, const double *src_pos,
+                      const float *sigma, void *ws, size_t ws_bytes, double *rec_out, emm_stream stream);
+
 /* Device workspace bytes emm_gradient needs (the forward workspace, the
  * checkpoints of every ckpt_every-th step, the E snapshots of one checkpoint
  * segment, the adjoint fields and the FP64 gradient accumulators).

@@ -34,7 +34,8 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",
             "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
             "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
-            "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient")
+            "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient",
+            "emm_batch_workspace_size", "emm_forward_batch")
 
 
 class EmmError(RuntimeError):
@@ -96,6 +97,8 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
                                C.POINTER(_Timing)], C.c_int),
         "emm_status": ([V, _I, V], C.c_int),
         "emm_forward_static": ([V, C.POINTER(_Survey), V, V, V, V, _I], C.c_int),
+        "emm_batch_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "emm_forward_batch": ([V, C.POINTER(_Survey), C.c_int, _D, V, V, C.c_size_t, V, V], C.c_int),
         "emm_gradient_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "emm_gradient": ([V, C.POINTER(_Survey), V, V, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
@@ -336,6 +339,37 @@ def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None
         C.byref(st) if wait else None)
     _check(code, "emm_forward_static")
     return st.value if wait else None
+
+
+def forward_batch(grid: Grid, survey: Survey, sigma, src_pos, work=None, stream=None, check: bool = True):
+    """``emm_forward_batch``: the receiver Green's functions of several
+    transmitters (positions ``src_pos`` [nsrc][3], host) on one conductivity,
+    advanced together.  Returns complex128 [nsrc][nrec][6][nfreq] (CUDA) and
+    the workspace tensor (pass it back as ``work`` to reuse it)."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    pos = _f64(src_pos).reshape(-1, 3)
+    nsrc, nf = pos.shape[0], len(survey.freqs)
+    s, keep = survey._c()
+    n = C.c_size_t(0)
+    _check(load_library().emm_batch_workspace_size(grid.handle, C.byref(s), nsrc, C.byref(n)),
+           "emm_batch_workspace_size")
+    if work is None or work.numel() < n.value + 256:
+        work = torch.empty(n.value + 256, dtype=torch.uint8, device=sigma.device)
+    ptr = work.data_ptr() + (-work.data_ptr()) % 256
+    rec = torch.zeros((nsrc, max(survey.nrec, 1), 6, nf, 2), dtype=torch.float64, device=sigma.device)
+    code = load_library().emm_forward_batch(
+        grid.handle, C.byref(s), nsrc, _dp(pos), C.c_void_p(sigma.data_ptr()), C.c_void_p(ptr),
+        C.c_size_t(n.value), C.c_void_p(rec.data_ptr()), C.c_void_p(stream.cuda_stream))
+    _check(code, "emm_forward_batch")
+    if check:
+        v = C.c_int(0)
+        _check(load_library().emm_status(C.c_void_p(ptr), C.byref(v), C.c_void_p(stream.cuda_stream)), "emm_status")
+        if v.value != EMM_OK:
+            raise EmmError(v.value, "emm_forward_batch (device status)")
+    return torch.view_as_complex(rec)[:, : survey.nrec], work
 
 
 def gradient_workspace_size(grid: Grid, survey: Survey, ckpt_every: int) -> int:

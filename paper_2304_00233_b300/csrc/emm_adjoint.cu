@@ -296,7 +296,7 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
   const size_t cells = static_cast<size_t>(fg.pitch) * g->ax[1].npad * g->ax[2].npad;
   const int nt = s->nt > 0 ? s->nt : 0;
   A.fwd = L.total;
-  A.state = L.zero_end - L.E[0];           // E, H and the CPML memory
+  A.state = L.sstride;                     // E, H and the CPML memory
   A.ebytes = L.H[0] - L.E[0];              // E only
   A.nck = nt > 0 ? static_cast<size_t>((nt + K - 1) / K) : 0;
   A.ck = take(A.nck * A.state);
@@ -305,7 +305,7 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
   for (int c = 0; c < 3; ++c) A.lamH[c] = take(cells * 4);
   for (int c = 0; c < 6; ++c) A.T[c] = take(cells * 4);
   for (int c = 0; c < 6; ++c) A.muE[c] = take((c < 5 ? L.psiE[c + 1] : L.psiH[0]) - L.psiE[c]);
-  for (int c = 0; c < 6; ++c) A.muH[c] = take((c < 5 ? L.psiH[c + 1] : L.vacc) - L.psiH[c]);
+  for (int c = 0; c < 6; ++c) A.muH[c] = take((c < 5 ? L.psiH[c + 1] : L.E[0] + L.sstride) - L.psiH[c]);
   for (int c = 0; c < 3; ++c) A.gpad[c] = take(cells * 8);
   for (int c = 0; c < 3; ++c) A.gseg[c] = take(cells * 4);
   const size_t m = 2 * static_cast<size_t>(g->rd);

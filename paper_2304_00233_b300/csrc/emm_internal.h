@@ -46,6 +46,14 @@ int locate_axis(const emm_grid *g, int axis, int half, double p, int *start, dou
 double dmax_axis(const Axis &ax, int rd);
 void cpml_axis(const emm_grid *g, int axis, double vmax, double fmax, double dt, double *ab);
 
+// Source of one transmitter of a batch: which E components it drives, the
+// first node of each (2rd)^3 stencil, and their bounding box.
+struct SrcDev {
+  int on[3];
+  int start[3][3];
+  int any, lo[3], hi[3];
+};
+
 // Everything the kernels read, packed by value into the launch parameters.
 struct DevParams {
   int np[3];        // padded sizes
@@ -65,17 +73,18 @@ struct DevParams {
   int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage ([0] psiE, [1] psiH)
   const float *cm[3], *cp[3];  // FD rows [npad][2rd]
   const float *pml[3];         // [4][2nb]: a_int, b_int, a_half, b_half
-  // source
-  int src_on[3];
-  int src_start[3][3];
-  int src_any, src_lo[3], src_hi[3];  // bounding box of the source stencils
-  const float *jw[3];          // dir_c * w / V at the (2rd)^3 stencil nodes
+  // transmitters: nsrc state blocks (fields and CPML memory) sstride floats
+  // apart, sharing dt/eps, the tables and the receivers
+  int nsrc;
+  size_t sstride;
+  const SrcDev *srcs;          // [nsrc]
+  const float *jw;             // [nsrc][3][(2rd)^3]: dir_c * w / V at the stencil nodes
   const float *amp;            // [nt]: moment * wavelet(t_{n+1/2})
   // receivers
   int nrec, nf;
   const int *rec_start;        // [nrec][6][3]
   const double *rec_w;         // [nrec][6][3][2rd]
-  double *rec_acc;             // [nrec][6][nf][2] (the caller's output, accumulated in place)
+  double *rec_acc;             // [nsrc][nrec][6][nf][2] (the caller's output, accumulated in place)
   const double *fE, *fH;       // [nt][nf][2] DTFT factors e^{i w' t} dt (E: t=(n+1)dt, H: (n+1/2)dt)
   // volume
   float4 *vacc;                // [6][nf][n3][n2][n1] compensated FP32 (re_hi, re_lo, im_hi, im_lo)
@@ -100,12 +109,14 @@ struct FieldGeom {
 FieldGeom field_geom(const emm_grid *g);
 
 // Byte layout of the device workspace.
+// The state of transmitter 0 (E[3], H[3], psiE[6], psiH[6]) is one block
+// at E[0]; transmitter k's block starts sstride bytes further per k.
 struct Layout {
-  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], vacc, zero_end;
-  size_t cm[3], cp[3], pml[3], jw[3], amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
+  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, zero_end;
+  size_t cm[3], cp[3], pml[3], srcs, jw, amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
 };
 
-Layout plan(const emm_grid *g, const emm_survey *s);
+Layout plan(const emm_grid *g, const emm_survey *s, int nsrc = 1);
 int check_survey(const emm_grid *g, const emm_survey *s);
 
 // Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
@@ -130,8 +141,10 @@ struct Prepared {
 
 // Validate, upload the tables, clear the state and compute dt/eps (enqueued
 // on cs); fills *out.  Host-detected errors enqueue nothing.
+// nsrc transmitters at src_pos ([nsrc][3], host; NULL: the survey's source).
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
-                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out);
+                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc = 1,
+                    const double *src_pos = nullptr);
 // Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te);

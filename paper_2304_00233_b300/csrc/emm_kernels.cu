@@ -122,12 +122,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
   }
 }
-__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
-                                            int z) {
+// 4-D box (x, y, z, transmitter) of a tensor into shared memory.
+__device__ __forceinline__ void tma_load_4d(float *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z, int w) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
 // 16-byte asynchronous global -> shared copy, L2 only (completes at cp_async_wait_all).
@@ -171,7 +172,8 @@ __device__ __forceinline__ void volume_accumulate(const DevParams &p, int comp, 
 // One warp per (receiver, component): (2R)^3 weighted gather in FP64, warp
 // shuffle reduction, then acc += factor * value for every frequency.
 template <int R>
-__device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, const double *fac, int block) {
+__device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, const double *fac, int block,
+                             double *rec_acc) {
   constexpr int M = 2 * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = block * (NT / 32) + warp;
@@ -179,7 +181,9 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
   const int rec = item / 3, c = comp0 + item % 3;
   const int *st = p.rec_start + (rec * 6 + c) * 3;
   const double *w = p.rec_w + static_cast<size_t>(rec * 6 + c) * 3 * M;
-  const float *f = F[c - comp0];
+  // pick the component without indexing the pointer array (keeps it in registers)
+  const int cc = c - comp0;
+  const float *f = cc == 0 ? F[0] : (cc == 1 ? F[1] : F[2]);
   double s = 0.0;
   for (int t = lane; t < M * M * M; t += 32) {
     const int q1 = t % M, q2 = (t / M) % M, q3 = t / (M * M);
@@ -189,7 +193,7 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) {
-    double *acc = p.rec_acc + static_cast<size_t>(rec * 6 + c) * p.nf * 2;
+    double *acc = rec_acc + static_cast<size_t>(rec * 6 + c) * p.nf * 2;
     for (int q = 0; q < p.nf; ++q) {
       acc[2 * q] += fac[2 * q] * s;
       acc[2 * q + 1] += fac[2 * q + 1] * s;
@@ -205,16 +209,49 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 // wave instead of trailing the launch), then (tiles_x, tiles_y, tiles_z)
 // stencil CTAs.
 // ---------------------------------------------------------------------------
+// Grid x = transmitter + nsrc * tile: the transmitters of a tile run side by
+// side and share its dt/eps reads in L2.
 struct Origin {
-  int i0, j0, k0;
+  int i0, j0, k0, src;
 };
+// MULTI: a batch of transmitters (otherwise transmitter 0 alone, and no
+// index arithmetic for it).
+template <bool MULTI>
 __device__ __forceinline__ Origin origin_of(const DevParams &p) {
-  return Origin{p.org[0] + static_cast<int>(blockIdx.x) * TX, p.org[1] + static_cast<int>(blockIdx.y) * TY,
-                p.org[2] + (static_cast<int>(blockIdx.z) - p.rec_layers) * ZC};
+  const int bx = MULTI ? static_cast<int>(blockIdx.x) / p.nsrc : static_cast<int>(blockIdx.x);
+  return Origin{p.org[0] + bx * TX, p.org[1] + static_cast<int>(blockIdx.y) * TY,
+                p.org[2] + (static_cast<int>(blockIdx.z) - p.rec_layers) * ZC,
+                MULTI ? static_cast<int>(blockIdx.x) % p.nsrc : 0};
 }
+template <bool MULTI>
 __device__ __forceinline__ int receiver_block(const DevParams &p) {
   return (static_cast<int>(blockIdx.z) * p.tiles_y + static_cast<int>(blockIdx.y)) * p.tiles_x +
-         static_cast<int>(blockIdx.x);
+         (MULTI ? static_cast<int>(blockIdx.x) / p.nsrc : static_cast<int>(blockIdx.x));
+}
+template <bool MULTI>
+__device__ __forceinline__ int receiver_source(const DevParams &p) {
+  return MULTI ? static_cast<int>(blockIdx.x) % p.nsrc : 0;
+}
+
+// The state arrays of transmitter src.
+struct Fields {
+  float *E[3], *H[3], *psiE[6], *psiH[6];
+};
+template <bool MULTI>
+__device__ __forceinline__ Fields fields_of(const DevParams &p, int src) {
+  Fields f;
+  const size_t o = MULTI ? static_cast<size_t>(src) * p.sstride : 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f.E[a] = p.E[a] + o;
+    f.H[a] = p.H[a] + o;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    f.psiE[c] = p.psiE[c] + o;
+    f.psiH[c] = p.psiH[c] + o;
+  }
+  return f;
 }
 
 // Thread 0: initialise the CTA's mbarrier and issue the three copies.  The
@@ -225,9 +262,9 @@ __device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t
   mbar_init(bar, 1);
   fence_barrier_init();
   mbar_expect_tx(bar, static_cast<uint32_t>(T::BYTES));
-  tma_load_3d(s, &tm.m[0], bar, o.i0, o.j0 - R, o.k0 + lead);
-  tma_load_3d(s + T::ZF, &tm.m[1], bar, o.i0 - XH, o.j0, o.k0 + lead);
-  tma_load_3d(s + T::ZF + T::XF, &tm.m[2], bar, o.i0 - XH, o.j0 - R, o.k0);
+  tma_load_4d(s, &tm.m[0], bar, o.i0, o.j0 - R, o.k0 + lead, o.src);
+  tma_load_4d(s + T::ZF, &tm.m[1], bar, o.i0 - XH, o.j0, o.k0 + lead, o.src);
+  tma_load_4d(s + T::ZF + T::XF, &tm.m[2], bar, o.i0 - XH, o.j0 - R, o.k0, o.src);
 }
 
 // Wait for the copies: thread 0 (which initialised the barrier and issued
@@ -251,18 +288,20 @@ __device__ __forceinline__ float *smem_tiles(unsigned char *raw) {
 }
 
 // Does the CTA's box meet the bounding box of the source stencils?
-__device__ __forceinline__ bool cta_has_source(const DevParams &p, const Origin &o) {
-  return p.src_any && o.i0 + TX > p.src_lo[0] && o.i0 <= p.src_hi[0] && o.j0 + TY > p.src_lo[1] &&
-         o.j0 <= p.src_hi[1] && o.k0 + ZC > p.src_lo[2] && o.k0 <= p.src_hi[2];
+__device__ __forceinline__ bool cta_has_source(const SrcDev &sd, const Origin &o) {
+  return sd.any && o.i0 + TX > sd.lo[0] && o.i0 <= sd.hi[0] && o.j0 + TY > sd.lo[1] && o.j0 <= sd.hi[1] &&
+         o.k0 + ZC > sd.lo[2] && o.k0 <= sd.hi[2];
 }
 
+// jw: this transmitter's [3][(2R)^3] stencil weights.
 template <int R>
-__device__ __forceinline__ void source_term(const DevParams &p, int c, int i, int j, int k, float amp,
-                                            float &curl) {
+__device__ __forceinline__ void source_term(const SrcDev &sd, const float *jw, int c, int i, int j, int k,
+                                            float amp, float &curl) {
   constexpr int M = 2 * R;
-  if (!p.src_on[c]) return;
-  const int a = i - p.src_start[c][0], bb = j - p.src_start[c][1], cc = k - p.src_start[c][2];
-  if (a >= 0 && a < M && bb >= 0 && bb < M && cc >= 0 && cc < M) curl -= amp * p.jw[c][(cc * M + bb) * M + a];
+  if (!sd.on[c]) return;
+  const int a = i - sd.start[c][0], bb = j - sd.start[c][1], cc = k - sd.start[c][2];
+  if (a >= 0 && a < M && bb >= 0 && bb < M && cc >= 0 && cc < M)
+    curl -= amp * jw[(c * M + cc) * M * M + bb * M + a];
 }
 
 // ---------------------------------------------------------------------------
@@ -381,23 +420,24 @@ __device__ __forceinline__ size_t psi_x_at(const DevParams &p, const Quad &u, in
 // 5 (y) of the third, matching psi[0..5].  sy, sz: slab entries of the row and
 // plane (-1 outside); xs: storage column of the quad's first cell in the
 // x-derivative arrays, or -1 if the quad does not touch an x slab.
-__device__ __forceinline__ void stage_psi(float4 *ps, float *const *psi, const DevParams &p, const Quad &u, int sy,
-                                          int sz, int xs, int wx) {
+__device__ __forceinline__ void stage_psi(float4 *ps, float *psi0, float *psi1, float *psi2, float *psi3,
+                                          float *psi4, float *psi5, const DevParams &p, const Quad &u, int sy, int sz,
+                                          int xs, int wx) {
   float4 *d = ps + threadIdx.x;
   if (sy >= 0) {
     const size_t id = psi_y_at(p, u, sy);
-    cp_async16(d, psi[0] + id);
-    cp_async16(d + 5 * NT, psi[5] + id);
+    cp_async16(d, psi0 + id);
+    cp_async16(d + 5 * NT, psi5 + id);
   }
   if (sz >= 0) {
     const size_t id = psi_z_at(p, u, sz);
-    cp_async16(d + 1 * NT, psi[1] + id);
-    cp_async16(d + 2 * NT, psi[2] + id);
+    cp_async16(d + 1 * NT, psi1 + id);
+    cp_async16(d + 2 * NT, psi2 + id);
   }
   if (xs >= 0) {
     const size_t id = psi_x_at(p, u, xs, wx);
-    cp_async16(d + 3 * NT, psi[3] + id);
-    cp_async16(d + 4 * NT, psi[4] + id);
+    cp_async16(d + 3 * NT, psi3 + id);
+    cp_async16(d + 4 * NT, psi4 + id);
   }
 }
 
@@ -430,8 +470,9 @@ __device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, 
 // One quad of the E update.  FAST: an interior CTA without the source, where
 // every validity test is true and every slab test false.
 template <int R, bool VOL, bool FAST>
-__device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, const Quad &u, const float4 (&e)[3],
-                                       const float4 (&w)[3], const float4 *ps, int n, bool src) {
+__device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
+                                       const float4 (&e)[3], const float4 (&w)[3], const float4 *ps, int n,
+                                       bool src, const SrcDev *sd, const float *jw) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int q4 = 4 * u.q, t = threadIdx.x;
@@ -492,12 +533,12 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, con
         }
       }
       float curl = a - b;
-      if (!FAST && src) source_term<R>(p, 0, u.i + c, u.j, u.k, amp, curl);
+      if (!FAST && src) source_term<R>(*sd, jw, 0, u.i + c, u.j, u.k, amp, curl);
       put(out[0], c, fmaf(get(w[0], c), curl, get(e[0], c)));
     }
     if (!FAST) {
-      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiE[0] + psi_y_at(p, u, sj)) = py;
-      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiE[1] + psi_z_at(p, u, sk)) = pz;
+      if (sj >= 0) *reinterpret_cast<float4 *>(f.psiE[0] + psi_y_at(p, u, sj)) = py;
+      if (sk >= 0) *reinterpret_cast<float4 *>(f.psiE[1] + psi_z_at(p, u, sk)) = pz;
     }
   }
   // Ey at (i, j+1/2, k): D-_z Hx - D-_x Hz
@@ -528,13 +569,13 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, con
         }
       }
       float curl = b - dx;
-      if (!FAST && src) source_term<R>(p, 1, u.i + c, u.j, u.k, amp, curl);
+      if (!FAST && src) source_term<R>(*sd, jw, 1, u.i + c, u.j, u.k, amp, curl);
       put(out[1], c, fmaf(get(w[1], c), curl, get(e[1], c)));
     }
     if (!FAST) {
-      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiE[2] + psi_z_at(p, u, sk)) = pz;
+      if (sk >= 0) *reinterpret_cast<float4 *>(f.psiE[2] + psi_z_at(p, u, sk)) = pz;
       if (xs >= 0)
-        *reinterpret_cast<float4 *>(p.psiE[3] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
+        *reinterpret_cast<float4 *>(f.psiE[3] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
     }
   }
   // Ez at (i, j, k+1/2): D-_x Hy - D-_y Hx
@@ -565,18 +606,18 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, con
         }
       }
       float curl = dx - b;
-      if (!FAST && src) source_term<R>(p, 2, u.i + c, u.j, u.k, amp, curl);
+      if (!FAST && src) source_term<R>(*sd, jw, 2, u.i + c, u.j, u.k, amp, curl);
       put(out[2], c, fmaf(get(w[2], c), curl, get(e[2], c)));
     }
     if (!FAST) {
       if (xs >= 0)
-        *reinterpret_cast<float4 *>(p.psiE[4] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
-      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiE[5] + psi_y_at(p, u, sj)) = py;
+        *reinterpret_cast<float4 *>(f.psiE[4] + psi_x_at(p, u, xs, p.psx_wx[0])) = px;
+      if (sj >= 0) *reinterpret_cast<float4 *>(f.psiE[5] + psi_y_at(p, u, sj)) = py;
     }
   }
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(p.E[a] + id) = out[a];
+  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.E[a] + id) = out[a];
 
   // volume DTFT of H^{n+1/2}
   if (VOL) {
@@ -599,20 +640,24 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const View<R> &v, con
   }
 }
 
-template <int R, bool VOL>
+template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
-    receiver_dft<R>(p, 3, p.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
+    const int rs = receiver_source<MULTI>(p);
+    const Fields f = fields_of<MULTI>(p, rs);
+    receiver_dft<R>(p, 3, f.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+                    p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of(p);
+  const Origin o = origin_of<MULTI>(p);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
   const Quad u = quad_of(o);
+  const Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
   // this thread's own samples, loaded while the copies are in flight
@@ -620,23 +665,26 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    e[a] = live ? *reinterpret_cast<const float4 *>(p.E[a] + id) : float4{};
+    e[a] = live ? *reinterpret_cast<const float4 *>(f.E[a] + id) : float4{};
     w[a] = live ? __ldg(reinterpret_cast<const float4 *>(p.ie[a] + id)) : float4{};
   }
-  const bool src = cta_has_source(p, o);
+  const SrcDev *sd = p.srcs + o.src;
+  const float *jw = p.jw + static_cast<size_t>(o.src) * 3 * (2 * R) * (2 * R) * (2 * R);
+  const bool src = cta_has_source(*sd, o);
   const bool fast = !src && interior_E(p, o, R);
   float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
   if (!fast && live)
-    stage_psi(ps, p.psiE, p, u, slab_int(u.j, np1, nb), slab_int(u.k, np2, nb),
+    stage_psi(ps, f.psiE[0], f.psiE[1], f.psiE[2], f.psiE[3], f.psiE[4], f.psiE[5], p, u, slab_int(u.j, np1, nb),
+              slab_int(u.k, np2, nb),
               psi_x_column(u.i, nb, PsiX{p.psx_hx[0], p.psx_wx[0], p.psx_far0[0]}, np0 - 1), p.psx_wx[0]);
   cp_async_commit();
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    e_quad<R, VOL, true>(p, v, u, e, w, ps, n, false);
+    e_quad<R, VOL, true>(p, f, v, u, e, w, ps, n, false, sd, jw);
   else
-    e_quad<R, VOL, false>(p, v, u, e, w, ps, n, src);
+    e_quad<R, VOL, false>(p, f, v, u, e, w, ps, n, src, sd, jw);
 }
 
 // ---------------------------------------------------------------------------
@@ -652,8 +700,8 @@ __device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, 
 }
 
 template <int R, bool VOL, bool FAST>
-__device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, const Quad &u, const float4 (&h)[3],
-                                       const float4 *ps, int n) {
+__device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
+                                       const float4 (&h)[3], const float4 *ps, int n) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int q4 = 4 * u.q, t = threadIdx.x;
@@ -717,8 +765,8 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, con
       put(out[0], c, fmaf(-dt_mu, a - b, get(h[0], c)));
     }
     if (!FAST) {
-      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiH[0] + psi_y_at(p, u, sj)) = py;
-      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiH[1] + psi_z_at(p, u, sk)) = pz;
+      if (sj >= 0) *reinterpret_cast<float4 *>(f.psiH[0] + psi_y_at(p, u, sj)) = py;
+      if (sk >= 0) *reinterpret_cast<float4 *>(f.psiH[1] + psi_z_at(p, u, sk)) = pz;
     }
   }
   // Hy at (i+1/2, j, k+1/2): D+_z Ex - D+_x Ez
@@ -751,9 +799,9 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, con
       put(out[1], c, fmaf(-dt_mu, b - dx, get(h[1], c)));
     }
     if (!FAST) {
-      if (sk >= 0) *reinterpret_cast<float4 *>(p.psiH[2] + psi_z_at(p, u, sk)) = pz;
+      if (sk >= 0) *reinterpret_cast<float4 *>(f.psiH[2] + psi_z_at(p, u, sk)) = pz;
       if (xs >= 0)
-        *reinterpret_cast<float4 *>(p.psiH[3] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
+        *reinterpret_cast<float4 *>(f.psiH[3] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
     }
   }
   // Hz at (i+1/2, j+1/2, k): D+_x Ey - D+_y Ex
@@ -787,13 +835,13 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, con
     }
     if (!FAST) {
       if (xs >= 0)
-        *reinterpret_cast<float4 *>(p.psiH[4] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
-      if (sj >= 0) *reinterpret_cast<float4 *>(p.psiH[5] + psi_y_at(p, u, sj)) = py;
+        *reinterpret_cast<float4 *>(f.psiH[4] + psi_x_at(p, u, xs, p.psx_wx[1])) = px;
+      if (sj >= 0) *reinterpret_cast<float4 *>(f.psiH[5] + psi_y_at(p, u, sj)) = py;
     }
   }
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(p.H[a] + id) = out[a];
+  for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.H[a] + id) = out[a];
 
   // volume DTFT of E^{n+1}
   if (VOL) {
@@ -816,39 +864,44 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const View<R> &v, con
   }
 }
 
-template <int R, bool VOL>
+template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
-    receiver_dft<R>(p, 0, p.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block(p));
+    const int rs = receiver_source<MULTI>(p);
+    const Fields f = fields_of<MULTI>(p, rs);
+    receiver_dft<R>(p, 0, f.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+                    p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of(p);
+  const Origin o = origin_of<MULTI>(p);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
 
   const Quad u = quad_of(o);
+  const Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
   float4 h[3];
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) h[a] = live ? *reinterpret_cast<const float4 *>(p.H[a] + id) : float4{};
+  for (int a = 0; a < 3; ++a) h[a] = live ? *reinterpret_cast<const float4 *>(f.H[a] + id) : float4{};
   const bool fast = interior_H(p, o, R);
   float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
   if (!fast && live)
-    stage_psi(ps, p.psiH, p, u, slab_half(u.j, np1, nb), slab_half(u.k, np2, nb),
+    stage_psi(ps, f.psiH[0], f.psiH[1], f.psiH[2], f.psiH[3], f.psiH[4], f.psiH[5], p, u, slab_half(u.j, np1, nb),
+              slab_half(u.k, np2, nb),
               psi_x_column(u.i, nb, PsiX{p.psx_hx[1], p.psx_wx[1], p.psx_far0[1]}, np0 - 2), p.psx_wx[1]);
   cp_async_commit();
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    h_quad<R, VOL, true>(p, v, u, h, ps, n);
+    h_quad<R, VOL, true>(p, f, v, u, h, ps, n);
   else
-    h_quad<R, VOL, false>(p, v, u, h, ps, n);
+    h_quad<R, VOL, false>(p, f, v, u, h, ps, n);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -950,7 +1003,7 @@ size_t psi_elems(const emm_grid *g, int axis, int half) {
 }
 
 
-Layout plan(const emm_grid *g, const emm_survey *s) {
+Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -963,10 +1016,14 @@ Layout plan(const emm_grid *g, const emm_survey *s) {
   const size_t m = 2 * static_cast<size_t>(g->rd), nf = s->nfreq;
   const size_t nt = s->nt > 0 ? s->nt : 1, nrec = s->nrec > 0 ? s->nrec : 1;
   L.status = take(sizeof(int));
+  // transmitter 0's state block; transmitters 1 .. nsrc-1 follow it
+  const size_t b0 = off;
   for (int c = 0; c < 3; ++c) L.E[c] = take(cells * 4);
   for (int c = 0; c < 3; ++c) L.H[c] = take(cells * 4);
   for (int c = 0; c < 6; ++c) L.psiE[c] = take(psi_elems(g, psi_axis(c), 0) * 4);
   for (int c = 0; c < 6; ++c) L.psiH[c] = take(psi_elems(g, psi_axis(c), 1) * 4);
+  L.sstride = off - b0;
+  off += static_cast<size_t>(nsrc > 1 ? nsrc - 1 : 0) * L.sstride;
   L.vacc = take(s->volume ? 6 * nf * nint * sizeof(float4) : 0);
   L.zero_end = off;
   for (int c = 0; c < 3; ++c) L.ie[c] = take(cells * 4);
@@ -976,7 +1033,8 @@ Layout plan(const emm_grid *g, const emm_survey *s) {
   for (int a = 0; a < 3; ++a) L.cm[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) L.cp[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) L.pml[a] = take(8 * static_cast<size_t>(g->nb) * 4);
-  for (int c = 0; c < 3; ++c) L.jw[c] = take(m * m * m * 4);
+  L.srcs = take(static_cast<size_t>(nsrc) * sizeof(SrcDev));
+  L.jw = take(static_cast<size_t>(nsrc) * 3 * m * m * m * 4);
   L.amp = take(nt * 4);
   L.rec_start = take(nrec * 18 * sizeof(int));
   L.rec_w = take(nrec * 18 * m * sizeof(double));
@@ -1014,17 +1072,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D FP32 tensor [np2][np1][pitch] (dims np0 x np1 x np2), box bx x by x bz.
+// 4-D FP32 tensor [nsrc][np2][np1][pitch] (dims np0 x np1 x np2 x nsrc, the
+// transmitters' state blocks sstride floats apart), box bx x by x bz x 1.
 bool make_map(CUtensorMap *map, const float *base, const DevParams &p, int bx, int by, int bz) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(p.np[0]), static_cast<cuuint64_t>(p.np[1]),
-                              static_cast<cuuint64_t>(p.np[2])};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(p.pitch) * 4, static_cast<cuuint64_t>(p.plane) * 4};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by),
-                             static_cast<cuuint32_t>(bz)};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+  const cuuint64_t dims[4] = {static_cast<cuuint64_t>(p.np[0]), static_cast<cuuint64_t>(p.np[1]),
+                              static_cast<cuuint64_t>(p.np[2]), static_cast<cuuint64_t>(p.nsrc)};
+  const cuuint64_t strides[3] = {static_cast<cuuint64_t>(p.pitch) * 4, static_cast<cuuint64_t>(p.plane) * 4,
+                                 static_cast<cuuint64_t>(p.sstride) * 4};
+  const cuuint32_t box[4] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by),
+                             static_cast<cuuint32_t>(bz), 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1037,24 +1097,25 @@ bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
          make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
-template <int R, bool VOL>
+template <int R, bool VOL, bool MULTI>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+      cudaFuncSetAttribute(k_update_E<R, VOL, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_update_H<R, VOL, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   size_t used = 0;
   for (int n = n0; n < n1; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R, VOL><<<blocks, NT, sb, st>>>(p, tE, n);
+    k_update_E<R, VOL, MULTI><<<blocks, NT, sb, st>>>(p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R, VOL><<<blocks, NT, sb, st>>>(p, tH, n);
+    k_update_H<R, VOL, MULTI><<<blocks, NT, sb, st>>>(p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -1064,11 +1125,13 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
 }
 
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
-                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out) {
+                    double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc,
+                    const double *src_pos) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
-  const Layout L = plan(g, s);
+  if (nsrc < 1 || (nsrc > 1 && s->volume)) return EMM_EINVAL;
+  const Layout L = plan(g, s, nsrc);
   if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
   const int rd = g->rd, m = 2 * rd, nf = s->nfreq, nt = s->nt, nb = g->nb;
   const int nbe = g->nb + g->ne;
@@ -1100,33 +1163,51 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     float *pm = reinterpret_cast<float *>(at(L.pml[a]));
     for (size_t q = 0; q < ab.size(); ++q) pm[q] = static_cast<float>(ab[q]);
   }
-  // source: J_node = moment s(t) dir_c w_node / V_node, V = dual-cell volume
+  // sources: J_node = moment s(t) dir_c w_node / V_node, V = dual-cell volume,
+  // one stencil set per transmitter
   const double dir[3] = {std::cos(s->src_dip) * std::cos(s->src_az), std::cos(s->src_dip) * std::sin(s->src_az),
                          std::sin(s->src_dip)};
   DevParams p{};
-  for (int c = 0; c < 3; ++c) {
-    p.src_on[c] = 0;
-    if (dir[c] == 0.0) continue;
-    int start[3];
-    double w[3][2 * kMaxRd];
+  SrcDev *srcs = reinterpret_cast<SrcDev *>(at(L.srcs));
+  const size_t m3 = static_cast<size_t>(m) * m * m;
+  for (int k = 0; k < nsrc; ++k) {
+    const double *pos = src_pos ? src_pos + 3 * k : s->src;
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(pos[a])) return EMM_EINVAL;
+    SrcDev &sd = srcs[k];
+    sd = SrcDev{};
     for (int a = 0; a < 3; ++a) {
-      st = locate_axis(g, a, kHalf[c][a], s->src[a], &start[a], w[a]);
-      if (st != EMM_OK) return st;
+      sd.lo[a] = 1 << 30;
+      sd.hi[a] = -1;
     }
-    float *jw = reinterpret_cast<float *>(at(L.jw[c]));
-    for (int q3 = 0; q3 < m; ++q3)
-      for (int q2 = 0; q2 < m; ++q2)
-        for (int q1 = 0; q1 < m; ++q1) {
-          const int idx[3] = {start[0] + q1, start[1] + q2, start[2] + q3};
-          double vol = 1.0;
-          for (int a = 0; a < 3; ++a) {
-            const Axis &ax = g->ax[a];
-            vol *= kHalf[c][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+    for (int c = 0; c < 3; ++c) {
+      if (dir[c] == 0.0) continue;
+      int start[3];
+      double w[3][2 * kMaxRd];
+      for (int a = 0; a < 3; ++a) {
+        st = locate_axis(g, a, kHalf[c][a], pos[a], &start[a], w[a]);
+        if (st != EMM_OK) return st;
+      }
+      float *jw = reinterpret_cast<float *>(at(L.jw)) + (static_cast<size_t>(k) * 3 + c) * m3;
+      for (int q3 = 0; q3 < m; ++q3)
+        for (int q2 = 0; q2 < m; ++q2)
+          for (int q1 = 0; q1 < m; ++q1) {
+            const int idx[3] = {start[0] + q1, start[1] + q2, start[2] + q3};
+            double vol = 1.0;
+            for (int a = 0; a < 3; ++a) {
+              const Axis &ax = g->ax[a];
+              vol *= kHalf[c][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+            }
+            jw[(q3 * m + q2) * m + q1] = static_cast<float>(dir[c] * w[0][q1] * w[1][q2] * w[2][q3] / vol);
           }
-          jw[(q3 * m + q2) * m + q1] = static_cast<float>(dir[c] * w[0][q1] * w[1][q2] * w[2][q3] / vol);
-        }
-    p.src_on[c] = 1;
-    for (int a = 0; a < 3; ++a) p.src_start[c][a] = start[a];
+      sd.on[c] = 1;
+      sd.any = 1;
+      for (int a = 0; a < 3; ++a) {
+        sd.start[c][a] = start[a];
+        sd.lo[a] = std::min(sd.lo[a], start[a]);
+        sd.hi[a] = std::max(sd.hi[a], start[a] + m - 1);
+      }
+    }
   }
   // receivers: stencils of all six components
   int *rs = reinterpret_cast<int *>(at(L.rec_start));
@@ -1197,7 +1278,6 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     p.E[c] = reinterpret_cast<float *>(base + L.E[c]) + fg.xshift;
     p.H[c] = reinterpret_cast<float *>(base + L.H[c]) + fg.xshift;
     p.ie[c] = reinterpret_cast<const float *>(base + L.ie[c]) + fg.xshift;
-    p.jw[c] = reinterpret_cast<const float *>(base + L.jw[c]);
   }
   for (int c = 0; c < 6; ++c) {
     // y- and z-derivative arrays share the field rows' x shift
@@ -1210,6 +1290,10 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     p.psx_wx[h] = fg.psx_wx[h];
     p.psx_far0[h] = fg.psx_far0[h];
   }
+  p.nsrc = nsrc;
+  p.sstride = L.sstride / 4;
+  p.srcs = reinterpret_cast<const SrcDev *>(base + L.srcs);
+  p.jw = reinterpret_cast<const float *>(base + L.jw);
   p.dt_mu = static_cast<float>(dt / kMu0);
   p.amp = reinterpret_cast<const float *>(base + L.amp);
   p.nrec = s->nrec;
@@ -1238,26 +1322,12 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
   const int layer = p.tiles_x * p.tiles_y;
   p.rec_layers = (p.rec_blocks + layer - 1) / layer;
-  const dim3 blocks(p.tiles_x, p.tiles_y, p.rec_layers + p.tiles_z);
-  // bounding box of the source stencils (lets CTAs far from it skip the test)
-  p.src_any = 0;
-  for (int a = 0; a < 3; ++a) {
-    p.src_lo[a] = 1 << 30;
-    p.src_hi[a] = -1;
-  }
-  for (int c = 0; c < 3; ++c)
-    if (p.src_on[c]) {
-      p.src_any = 1;
-      for (int a = 0; a < 3; ++a) {
-        p.src_lo[a] = std::min(p.src_lo[a], p.src_start[c][a]);
-        p.src_hi[a] = std::max(p.src_hi[a], p.src_start[c][a] + m - 1);
-      }
-    }
+  const dim3 blocks(p.tiles_x * nsrc, p.tiles_y, p.rec_layers + p.tiles_z);
 
   // ---- enqueue ----
   cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, cs);
   if (e == cudaSuccess && s->nrec > 0)
-    e = cudaMemsetAsync(rec_out, 0, static_cast<size_t>(s->nrec) * 6 * nf * 2 * sizeof(double), cs);
+    e = cudaMemsetAsync(rec_out, 0, static_cast<size_t>(nsrc) * s->nrec * 6 * nf * 2 * sizeof(double), cs);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + tab0, blob.data(), blob.size(), cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return EMM_ECUDA;
   k_prepare<<<4 * sms, 256, 0, cs>>>(sigma, reinterpret_cast<float *>(base + L.ie[0]),
@@ -1277,12 +1347,25 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
 
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te) {
-  const bool vol = p.vacc != nullptr;
+  // three variants per order: one transmitter, one with the volume DTFT, a batch
+  const bool vol = p.vacc != nullptr, multi = p.nsrc > 1;
   switch (P.rd) {
-    case 1: return vol ? launch_steps<1, true>(p, n0, n1, blocks, cs, te) : launch_steps<1, false>(p, n0, n1, blocks, cs, te);
-    case 2: return vol ? launch_steps<2, true>(p, n0, n1, blocks, cs, te) : launch_steps<2, false>(p, n0, n1, blocks, cs, te);
-    case 3: return vol ? launch_steps<3, true>(p, n0, n1, blocks, cs, te) : launch_steps<3, false>(p, n0, n1, blocks, cs, te);
-    default: return vol ? launch_steps<4, true>(p, n0, n1, blocks, cs, te) : launch_steps<4, false>(p, n0, n1, blocks, cs, te);
+    case 1:
+      return multi ? launch_steps<1, false, true>(p, n0, n1, blocks, cs, te)
+                   : (vol ? launch_steps<1, true, false>(p, n0, n1, blocks, cs, te)
+                          : launch_steps<1, false, false>(p, n0, n1, blocks, cs, te));
+    case 2:
+      return multi ? launch_steps<2, false, true>(p, n0, n1, blocks, cs, te)
+                   : (vol ? launch_steps<2, true, false>(p, n0, n1, blocks, cs, te)
+                          : launch_steps<2, false, false>(p, n0, n1, blocks, cs, te));
+    case 3:
+      return multi ? launch_steps<3, false, true>(p, n0, n1, blocks, cs, te)
+                   : (vol ? launch_steps<3, true, false>(p, n0, n1, blocks, cs, te)
+                          : launch_steps<3, false, false>(p, n0, n1, blocks, cs, te));
+    default:
+      return multi ? launch_steps<4, false, true>(p, n0, n1, blocks, cs, te)
+                   : (vol ? launch_steps<4, true, false>(p, n0, n1, blocks, cs, te)
+                          : launch_steps<4, false, false>(p, n0, n1, blocks, cs, te));
   }
 }
 
@@ -1291,8 +1374,8 @@ int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, do
   const double *dnorm = reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(P.p.status) -
                                                          P.L.status + P.L.norm);
   if (s->nrec > 0) {
-    const int tot = s->nrec * 6 * nf;
-    k_finalize_rec<<<(tot + 255) / 256, 256, 0, cs>>>(rec_out, dnorm, s->nrec, nf);
+    const int nr = P.p.nsrc * s->nrec, tot = nr * 6 * nf;
+    k_finalize_rec<<<(tot + 255) / 256, 256, 0, cs>>>(rec_out, dnorm, nr, nf);
   }
   if (s->volume) {
     const size_t nint = static_cast<size_t>(P.p.n[0]) * P.p.n[1] * P.p.n[2];
@@ -1388,6 +1471,25 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   timing->total_ms = ms;
   for (auto &e : all) cudaEventDestroy(e);
   return st;
+}
+
+int emm_batch_workspace_size(const emm_grid *g, const emm_survey *s, int nsrc, size_t *bytes) {
+  const int st = emm::check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (!bytes || nsrc < 1 || s->volume) return EMM_EINVAL;
+  *bytes = emm::plan(g, s, nsrc).total;
+  return EMM_OK;
+}
+
+int emm_forward_batch(const emm_grid *g, const emm_survey *s, int nsrc, const double *src_pos, const float *sigma,
+                      void *ws, size_t ws_bytes, double *rec_out, emm_stream stream) {
+  if (nsrc < 1 || !src_pos) return EMM_EINVAL;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  emm::Prepared P;
+  int st = emm::prepare_forward(g, s, sigma, ws, ws_bytes, rec_out, nullptr, cs, &P, nsrc, src_pos);
+  if (st != EMM_OK) return st;
+  if (emm::run_steps(P, P.p, P.blocks, 0, s->nt, cs, nullptr) != cudaSuccess) return EMM_ECUDA;
+  return emm::finalize_forward(P, s, rec_out, nullptr, cs);
 }
 
 int emm_forward_static(const emm_grid *g, const emm_survey *s, const float *sigma, double *rec_out,
