@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libemm.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("emm_kernels.cu", "emm_adjoint.cu", "emm_setup.cpp")]
-HEADERS = [os.path.join(HERE, "csrc", "emm_internal.h"),
+HEADERS = [os.path.join(HERE, "csrc", "emm_internal.h"), os.path.join(HERE, "csrc", "emm_tma.cuh"),
            os.path.join(os.path.dirname(HERE), "include", "emm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -19,11 +19,13 @@
 // recomputes the segment's E snapshots and then runs the adjoint steps
 // backwards.  One adjoint step, the transpose of one forward step:
 //   1. H update:  per-derivative adjoints T = -dt/mu0 lambda_H (CPML memory
-//      adjoints updated), then lambda_E += (D+)^T T  (transposed-row gather);
+//      adjoints updated in the shell), then lambda_E += (D+)^T T
+//      (transposed-row gather);
 //   2. receivers: lambda += interpolation^T of Re(conj(v) norm f_n);
 //   3. gradient:  g += - lambda_E (E^{n+1} - E^n) / sigma (FP32 within a
 //      checkpoint segment, added into FP64 at its end);
-//   4. E update:  T = ie lambda_E (CPML), then lambda_H += (D-)^T T.
+//   4. E update:  T = ie lambda_E (CPML in the shell), then
+//      lambda_H += (D-)^T T.
 // Finally the padded gradient is folded onto the interior samples the pads
 // replicate.  Adjoint fields are FP32 like the forward fields; the gradient
 // accumulates in FP64.
@@ -34,6 +36,7 @@
 #include <vector>
 
 #include "emm_internal.h"
+#include "emm_tma.cuh"
 
 namespace emm {
 namespace {
@@ -41,13 +44,14 @@ namespace {
 constexpr int kThreads = 256;
 
 struct AdjParams {
-  int np[3], n[3], pitch, nb, rd, nbe;
+  int np[3], n[3], pitch, nb, rd, nbe, org[3];
   size_t plane;
   float kappa;               // dt / mu0
   double inv_2w0dt;          // 1 / (2 omega0 dt): sigma = 2 omega0 dt / ie
   const float *ie[3];
   float *lamE[3], *lamH[3];  // adjoint fields (field layout)
-  float *T[6];               // per-derivative adjoints (field layout)
+  float *T[6];               // per-derivative adjoints of the current half step (field layout)
+  int *status;
   float *muE[6], *muH[6];    // adjoints of the CPML memory (psi layouts)
   int psx_hx[2], psx_wx[2], psx_far0[2];
   const float *pml[3];       // [4][2nb]: a_int, b_int, a_half, b_half
@@ -80,15 +84,6 @@ __device__ __forceinline__ size_t psi_index(const AdjParams &a, int axis, int h,
   return (static_cast<size_t>(k) * a.np[1] + j) * a.psx_wx[h] + xs;
 }
 
-// Transpose of the CPML step psi' = b psi + a t, d = t + psi' (Eq. 22-23):
-// adjoint of t from the adjoint gd of d; mu (adjoint of psi') becomes the
-// adjoint of the old psi.
-__device__ __forceinline__ float pml_T(float gd, float *mu, size_t idx, float pa, float pb) {
-  const float gpsi = gd + mu[idx];
-  mu[idx] = pb * gpsi;
-  return gd + pa * gpsi;
-}
-
 // Cell of this thread in a 3-D launch of 32 x 8 threads per (x, y) tile and
 // one grid z layer per plane; false outside the padded grid.
 __device__ __forceinline__ bool cell3(const AdjParams &a, int *idx) {
@@ -101,61 +96,42 @@ __device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
   return static_cast<size_t>(k) * a.plane + static_cast<size_t>(j) * a.pitch + i;
 }
 
-// 1a. Transpose of the H update's CPML and scaling: T[2c+t] at H_c positions.
+// The per-derivative adjoint of a forward term, T = g (+ the transposed CPML
+// step in a slab, Eq. 22-23: T = g + a (g + mu), mu <- b (g + mu), mu the
+// adjoint of the CPML memory), or 0 where the forward loop does not update
+// the sample; g is the scaled adjoint with the term's sign (-dt/mu0
+// lambda_H for the H update, dt/eps lambda_E for the E update).  T[2c+t]
+// belongs to component c and its term t (0: derivative along c+1, 1: along
+// c+2).  A pointwise pass writes T; a gather then applies the transposed FD
+// rows to it.
+
+// 1a. T[2c+t] at the H_c samples from lambda_H.
 __global__ void k_adj_h_pre(const AdjParams a) {
   const int R = a.rd, nb = a.nb;
   int idx[3];
   if (!cell3(a, idx)) return;
-  {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-    bool dp[3];
-    for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
-    for (int c = 0; c < 3; ++c) {
-      const int p = (c + 1) % 3, q = (c + 2) % 3;
-      const bool valid = dp[p] && dp[q];
-      const float g = -a.kappa * a.lamH[c][id];
-      for (int term = 0; term < 2; ++term) {
-        const int ax = term == 0 ? p : q;
-        float gd = term == 0 ? g : -g;
-        if (valid) {
-          const int s = slab_half(idx[ax], a.np[ax], nb);
-          if (s >= 0)
-            gd = pml_T(gd, a.muH[2 * c + term], psi_index(a, ax, 1, s, idx[0], idx[1], idx[2]),
-                       a.pml[ax][4 * nb + s], a.pml[ax][6 * nb + s]);
+  const size_t id = fid(a, idx[0], idx[1], idx[2]);
+  bool dp[3];
+  for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
+  for (int c = 0; c < 3; ++c) {
+    const int p = (c + 1) % 3, q = (c + 2) % 3;
+    const bool valid = dp[p] && dp[q];
+    const float g = -a.kappa * a.lamH[c][id];
+    for (int term = 0; term < 2; ++term) {
+      const int ax = term == 0 ? p : q;
+      float t = 0.f;
+      if (valid) {
+        t = term == 0 ? g : -g;
+        const int s = slab_half(idx[ax], a.np[ax], nb);
+        if (s >= 0) {
+          float *mu = a.muH[2 * c + term];
+          const size_t k = psi_index(a, ax, 1, s, idx[0], idx[1], idx[2]);
+          const float gpsi = t + mu[k];
+          mu[k] = a.pml[ax][6 * nb + s] * gpsi;
+          t += a.pml[ax][4 * nb + s] * gpsi;
         }
-        a.T[2 * c + term][id] = valid ? gd : 0.f;
       }
-    }
-  }
-}
-
-// Gather of a transposed FD operator along axis ax: sum_q tab[idx][q] F[r],
-// r = idx + off + q (off = -R for (D+)^T, -R+1 for (D-)^T), rows off the grid
-// skipped (their coefficients are zero).
-__device__ __forceinline__ float gatherT(const AdjParams &a, const float *tab, const float *F, int ax,
-                                         const int *idx, size_t id, int off) {
-  const int M = 2 * a.rd;
-  const size_t stride = ax == 0 ? 1 : (ax == 1 ? static_cast<size_t>(a.pitch) : a.plane);
-  float acc = 0.f;
-  for (int q = 0; q < M; ++q) {
-    const int r = idx[ax] + off + q;
-    if (r < 0 || r >= a.np[ax]) continue;
-    acc = fmaf(tab[static_cast<size_t>(idx[ax]) * M + q], F[id + (static_cast<ptrdiff_t>(r) - idx[ax]) * static_cast<ptrdiff_t>(stride)], acc);
-  }
-  return acc;
-}
-
-// 1b. lambda_E_e += (D+_{e+2})^T T[2(e+1)+0] + (D+_{e+1})^T T[2(e+2)+1].
-__global__ void k_adj_h_apply(const AdjParams a) {
-  int idx[3];
-  if (!cell3(a, idx)) return;
-  {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-    for (int e = 0; e < 3; ++e) {
-      const int c1 = (e + 1) % 3, a1 = (e + 2) % 3, c2 = (e + 2) % 3, a2 = (e + 1) % 3;
-      const float s = gatherT(a, a.cpT[a1], a.T[2 * c1], a1, idx, id, -a.rd) +
-                      gatherT(a, a.cpT[a2], a.T[2 * c2 + 1], a2, idx, id, -a.rd);
-      a.lamE[e][id] += s;
+      a.T[2 * c + term][id] = t;
     }
   }
 }
@@ -180,51 +156,161 @@ __global__ void k_adj_receivers(const AdjParams a, int n) {
   atomicAdd(F + fid(a, st[0] + q1, st[1] + q2, st[2] + q3), static_cast<float>(val));
 }
 
-// 3 + 4a. Gradient term g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e / (2 omega0
-// dt) (lambda_E is final for this step here), then the transpose of the E
-// update's scaling and CPML: T[2e+t] at E_e positions.
+// 3. The gradient term of this step, g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e
+// / (2 omega0 dt) (lambda_E is final for the step here), and T[2e+t] at the
+// E_e samples from lambda_E.
 __global__ void k_adj_e_pre(const AdjParams a) {
   const int R = a.rd, nb = a.nb;
   int idx[3];
   if (!cell3(a, idx)) return;
-  {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-    bool dm[3];
-    for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
-    for (int e = 0; e < 3; ++e) {
-      const int p = (e + 1) % 3, q = (e + 2) % 3;
-      const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
-      const float lam = a.lamE[e][id], ie = a.ie[e][id];
-      const float dE = a.E1[e][id] - a.E0[e][id];
-      if (dE != 0.f) a.gseg[e][id] -= static_cast<float>(static_cast<double>(lam) * dE * ie * a.inv_2w0dt);
-      const float g = ie * lam;
-      for (int term = 0; term < 2; ++term) {
-        const int ax = term == 0 ? p : q;
-        float gd = term == 0 ? g : -g;
-        if (valid) {
-          const int s = slab_int(idx[ax], a.np[ax], nb);
-          if (s >= 0)
-            gd = pml_T(gd, a.muE[2 * e + term], psi_index(a, ax, 0, s, idx[0], idx[1], idx[2]), a.pml[ax][s],
-                       a.pml[ax][2 * nb + s]);
+  const size_t id = fid(a, idx[0], idx[1], idx[2]);
+  bool dm[3];
+  for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
+  for (int e = 0; e < 3; ++e) {
+    const int p = (e + 1) % 3, q = (e + 2) % 3;
+    const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
+    const float lam = a.lamE[e][id], ie = a.ie[e][id];
+    const float dE = a.E1[e][id] - a.E0[e][id];
+    if (dE != 0.f) a.gseg[e][id] -= static_cast<float>(static_cast<double>(lam) * dE * ie * a.inv_2w0dt);
+    const float g = ie * lam;
+    for (int term = 0; term < 2; ++term) {
+      const int ax = term == 0 ? p : q;
+      float t = 0.f;
+      if (valid) {
+        t = term == 0 ? g : -g;
+        const int s = slab_int(idx[ax], a.np[ax], nb);
+        if (s >= 0) {
+          float *mu = a.muE[2 * e + term];
+          const size_t k = psi_index(a, ax, 0, s, idx[0], idx[1], idx[2]);
+          const float gpsi = t + mu[k];
+          mu[k] = a.pml[ax][2 * nb + s] * gpsi;
+          t += a.pml[ax][s] * gpsi;
         }
-        a.T[2 * e + term][id] = valid ? gd : 0.f;
       }
+      a.T[2 * e + term][id] = t;
     }
   }
 }
 
-// 4b. lambda_H_h += (D-_{h+2})^T T[2(h+1)+0] + (D-_{h+1})^T T[2(h+2)+1].
-__global__ void k_adj_e_apply(const AdjParams a) {
-  int idx[3];
-  if (!cell3(a, idx)) return;
-  {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-    for (int h = 0; h < 3; ++h) {
-      const int e1 = (h + 1) % 3, a1 = (h + 2) % 3, e2 = (h + 2) % 3, a2 = (h + 1) % 3;
-      const float s = gatherT(a, a.cmT[a1], a.T[2 * e1], a1, idx, id, 1 - a.rd) +
-                      gatherT(a, a.cmT[a2], a.T[2 * e2 + 1], a2, idx, id, 1 - a.rd);
-      a.lamH[h][id] += s;
+// ---- 1b / 4. The transposed FD gathers, TMA-fed --------------------------
+// out_o += (D_{o+2})^T T[2(o+1)+0] + (D_{o+1})^T T[2(o+2)+1], with the
+// transposed D+ rows into lambda_E (KIND 0, taps -R .. R-1) or the transposed
+// D- rows into lambda_H (KIND 1, taps -R+1 .. R).  A CTA owns 32 x 8 columns x
+// GZ planes, one thread per quad of 4 x-adjacent cells; each T array arrives
+// by one bulk tensor copy with a halo along the one axis its term
+// differentiates.  Every T value already holds the CPML and the update
+// masks, so every CTA takes the same path.
+constexpr int GX = 32, GY = 8, GZ = 2, GH = 4, GT = (GX / 4) * GY * GZ;
+template <int R>
+struct GTiles {
+  static constexpr int YB = GX * (GY + 2 * R) * GZ;   // y-halo box: T[0], T[5]
+  static constexpr int ZB = GX * GY * (GZ + 2 * R);   // z-halo box: T[1], T[2]
+  static constexpr int XB = (GX + 2 * GH) * GY * GZ;  // x-halo box: T[3], T[4]
+  __host__ __device__ static constexpr int off(int t) {
+    return t == 0 ? 0 : t == 5 ? YB : t == 1 ? 2 * YB : t == 2 ? 2 * YB + ZB : t == 3 ? 2 * YB + 2 * ZB
+                                                                                       : 2 * YB + 2 * ZB + XB;
+  }
+  static constexpr int FLOATS = 2 * (YB + ZB + XB);
+};
+struct GMaps {
+  CUtensorMap m[6];
+};
+
+template <int R, int KIND>
+__global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __grid_constant__ GMaps tm) {
+  using G = GTiles<R>;
+  constexpr int M = 2 * R, OFF = KIND == 0 ? -R : 1 - R;
+  extern __shared__ unsigned char smem_raw[];
+  float *s = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + G::FLOATS);
+  const int i0 = a.org[0] + static_cast<int>(blockIdx.x) * GX, j0 = a.org[1] + static_cast<int>(blockIdx.y) * GY,
+            k0 = static_cast<int>(blockIdx.z) * GZ;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+    mbar_expect_tx(bar, static_cast<uint32_t>(G::FLOATS * 4));
+    tma_load_3d(s + G::off(0), &tm.m[0], bar, i0, j0 - R, k0);
+    tma_load_3d(s + G::off(5), &tm.m[5], bar, i0, j0 - R, k0);
+    tma_load_3d(s + G::off(1), &tm.m[1], bar, i0, j0, k0 - R);
+    tma_load_3d(s + G::off(2), &tm.m[2], bar, i0, j0, k0 - R);
+    tma_load_3d(s + G::off(3), &tm.m[3], bar, i0 - GH, j0, k0);
+    tma_load_3d(s + G::off(4), &tm.m[4], bar, i0 - GH, j0, k0);
+  }
+  const int t = threadIdx.x, q4 = 4 * (t & 7), r = (t >> 3) & 7, c = t >> 6;
+  const int i = i0 + q4, j = j0 + r, k = k0 + c;
+  const bool live = i >= 0 && i < a.np[0] && j < a.np[1] && k < a.np[2];
+  float *const *out = KIND == 0 ? a.lamE : a.lamH;
+  const float *const *tab = KIND == 0 ? a.cpT : a.cmT;
+  const size_t id = fid(a, live ? i : 0, live ? j : 0, live ? k : 0);
+  float4 o4[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) o4[o] = live ? *reinterpret_cast<const float4 *>(out[o] + id) : float4{};
+  float cx[4][M], cy[M], cz[M];
+#pragma unroll
+  for (int f = 0; f < M; ++f) {
+    const float4 v = live ? __ldg(reinterpret_cast<const float4 *>(tab[0] + static_cast<size_t>(i) * M) + f) : float4{};
+    cx[(4 * f) / M][(4 * f) % M] = v.x;
+    cx[(4 * f + 1) / M][(4 * f + 1) % M] = v.y;
+    cx[(4 * f + 2) / M][(4 * f + 2) % M] = v.z;
+    cx[(4 * f + 3) / M][(4 * f + 3) % M] = v.w;
+    cy[f] = live ? __ldg(tab[1] + static_cast<size_t>(j) * M + f) : 0.f;
+    cz[f] = live ? __ldg(tab[2] + static_cast<size_t>(k) * M + f) : 0.f;
+  }
+  __syncthreads();
+  int late = 0;
+  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0)) {
+    late = 1;
+    atomicExch(a.status, EMM_ETIMEOUT);
+    mbar_wait_bounded(bar, 0);
+  }
+  if (__syncthreads_or(late) || !live) return;
+
+  // taps of term array tt along axis ax for the quad, accumulated into acc
+  auto ybox = [&](int tt, int row) {
+    return *reinterpret_cast<const float4 *>(s + G::off(tt) + (c * (GY + 2 * R) + row) * GX + q4);
+  };
+  auto zbox = [&](int tt, int plane) {
+    return *reinterpret_cast<const float4 *>(s + G::off(tt) + (plane * GY + r) * GX + q4);
+  };
+  auto xrow = [&](int tt, float *row) {
+    const float *b = s + G::off(tt) + (c * GY + r) * (GX + 2 * GH) + q4;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const float4 v = *reinterpret_cast<const float4 *>(b + 4 * u);
+      row[4 * u] = v.x; row[4 * u + 1] = v.y; row[4 * u + 2] = v.z; row[4 * u + 3] = v.w;
     }
+  };
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const int ta = 2 * ((o + 1) % 3), aa = (o + 2) % 3, tb = 2 * ((o + 2) % 3) + 1, ab = (o + 1) % 3;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int term = 0; term < 2; ++term) {
+      const int tt = term == 0 ? ta : tb, ax = term == 0 ? aa : ab;
+      if (ax == 0) {
+        float row[12];
+        xrow(tt, row);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc[e] = fmaf(cx[e][m], row[GH + e + OFF + m], acc[e]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float4 v = ax == 1 ? ybox(tt, r + R + OFF + m) : zbox(tt, c + R + OFF + m);
+          const float cf = ax == 1 ? cy[m] : cz[m];
+          acc[0] = fmaf(cf, v.x, acc[0]);
+          acc[1] = fmaf(cf, v.y, acc[1]);
+          acc[2] = fmaf(cf, v.z, acc[2]);
+          acc[3] = fmaf(cf, v.w, acc[3]);
+        }
+      }
+    }
+    if (i + 0 < a.np[0]) o4[o].x += acc[0];
+    if (i + 1 < a.np[0]) o4[o].y += acc[1];
+    if (i + 2 < a.np[0]) o4[o].z += acc[2];
+    if (i + 3 < a.np[0]) o4[o].w += acc[3];
+    *reinterpret_cast<float4 *>(out[o] + id) = o4[o];
   }
 }
 
@@ -277,6 +363,48 @@ __global__ void k_adj_fold(const AdjParams a, double *grad) {
   }
 }
 
+// 3-D FP32 tensor [np2][np1][pitch] (dims np0 x np1 x np2), box bx x by x bz.
+bool make_map3(CUtensorMap *map, const float *base, const AdjParams &a, int bx, int by, int bz) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(a.np[0]), static_cast<cuuint64_t>(a.np[1]),
+                              static_cast<cuuint64_t>(a.np[2])};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(a.pitch) * 4, static_cast<cuuint64_t>(a.plane) * 4};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bx), static_cast<cuuint32_t>(by), static_cast<cuuint32_t>(bz)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The two gathers of one adjoint step, for order R.
+struct Gathers {
+  GMaps maps;
+  dim3 grid;
+  size_t smem;
+  void (*g0)(AdjParams, GMaps);
+  void (*g1)(AdjParams, GMaps);
+};
+template <int R>
+bool make_gathers(const AdjParams &a, Gathers *G) {
+  bool ok = true;
+  for (int t = 0; t < 6 && ok; ++t) {
+    const int bx = (t == 3 || t == 4) ? GX + 2 * GH : GX;
+    const int by = (t == 0 || t == 5) ? GY + 2 * R : GY;
+    const int bz = (t == 1 || t == 2) ? GZ + 2 * R : GZ;
+    ok = make_map3(&G->maps.m[t], a.T[t], a, bx, by, bz);
+  }
+  G->grid = dim3((a.np[0] - a.org[0] + GX - 1) / GX, (a.np[1] - a.org[1] + GY - 1) / GY, (a.np[2] + GZ - 1) / GZ);
+  G->smem = GTiles<R>::FLOATS * 4 + 128 + 16;
+  G->g0 = k_adj_gather<R, 0>;
+  G->g1 = k_adj_gather<R, 1>;
+  ok = ok && cudaFuncSetAttribute(k_adj_gather<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(G->smem)) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_adj_gather<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(G->smem)) == cudaSuccess;
+  return ok;
+}
+
 // Byte layout of the gradient's extra workspace, after the forward one.
 struct AdjLayout {
   size_t fwd, ck, state, nck, eh, ebytes, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
@@ -309,8 +437,11 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
   for (int c = 0; c < 3; ++c) A.gpad[c] = take(cells * 8);
   for (int c = 0; c < 3; ++c) A.gseg[c] = take(cells * 4);
   const size_t m = 2 * static_cast<size_t>(g->rd);
-  for (int a = 0; a < 3; ++a) A.cpT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
-  for (int a = 0; a < 3; ++a) A.cmT[a] = take(static_cast<size_t>(g->ax[a].npad) * m * 4);
+  // the x tables run on to a whole field row (zero rows past npad): the
+  // gathers read the rows of all four cells of a quad at once
+  const size_t xrows = std::max<size_t>(g->ax[0].npad, fg.pitch);
+  for (int a = 0; a < 3; ++a) A.cpT[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
+  for (int a = 0; a < 3; ++a) A.cmT[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   A.cw = take(static_cast<size_t>(s->nrec > 0 ? s->nrec : 1) * 6 * s->nfreq * 2 * sizeof(double));
   A.total = off;
   return A;
@@ -374,6 +505,8 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   a.nb = g->nb;
   a.rd = rd;
   a.nbe = P.p.nbe;
+  for (int ax = 0; ax < 3; ++ax) a.org[ax] = P.p.org[ax];
+  a.status = P.p.status;
   a.kappa = P.p.dt_mu;
   a.inv_2w0dt = 1.0 / (2.0 * s->omega0 * P.dt);
   const int xs = P.fg.xshift;
@@ -408,6 +541,11 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   std::vector<float> pT, mT;
   for (int ax = 0; ax < 3 && e == cudaSuccess; ++ax) {
     transposed_rows(g->ax[ax], rd, pT, mT);
+    if (ax == 0) {
+      const size_t rows = std::max<size_t>(g->ax[0].npad, P.fg.pitch) * 2 * rd;
+      pT.resize(rows, 0.f);
+      mT.resize(rows, 0.f);
+    }
     e = cudaMemcpyAsync(base + A.cpT[ax], pT.data(), pT.size() * 4, cudaMemcpyHostToDevice, cs);
     // pageable sources: each copy has taken the data when it returns
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + A.cmT[ax], mT.data(), mT.size() * 4, cudaMemcpyHostToDevice, cs);
@@ -427,6 +565,12 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const dim3 blocks_r(P.p.tiles_x, P.p.tiles_y, P.p.tiles_z);
   const int grid_cells = P.sms * 8;
   const dim3 tb(32, 8, 1), grid3((P.p.np[0] + 31) / 32, (P.p.np[1] + 7) / 8, P.p.np[2]);
+  Gathers GA{};
+  const bool gok = rd == 1 ? make_gathers<1>(a, &GA)
+                   : rd == 2 ? make_gathers<2>(a, &GA)
+                             : rd == 3 ? make_gathers<3>(a, &GA) : make_gathers<4>(a, &GA);
+  if (!gok) return EMM_ECUDA;
+
   const int M = 2 * rd, rec_threads = s->nrec * 6 * M * M * M;
   for (int seg = static_cast<int>(A.nck) - 1; seg >= 0 && e == cudaSuccess; --seg) {
     const int it0 = seg * K, it1 = std::min(it0 + K, nt);
@@ -448,10 +592,10 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
             reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0 + 1) * A.ebytes + ec) + xs;
       }
       k_adj_h_pre<<<grid3, tb, 0, cs>>>(a);
-      k_adj_h_apply<<<grid3, tb, 0, cs>>>(a);
+      GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
       if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
       k_adj_e_pre<<<grid3, tb, 0, cs>>>(a);
-      k_adj_e_apply<<<grid3, tb, 0, cs>>>(a);
+      GA.g1<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

@@ -65,3 +65,22 @@ def test_checkpoint_spacing_and_autograd():
     loss.backward()
     rel = (torch.linalg.norm(s.grad - g1) / torch.linalg.norm(g1)).item()
     assert rel < 1e-5, rel
+
+
+def test_gradient_interior_blocks_against_oracle():
+    # wide enough in x for 32 x 8 blocks whose cells and taps all lie outside
+    # the CPML shell (the vectorised interior path of the adjoint)
+    wl, v = _problem(2, (54, 26, 22), nt=90, seed=31)
+    grid, survey = emm.grid_for(wl), emm.survey_for(wl, nt=wl.nt)
+    np0 = len(wl.x) + 2 * (wl.nb + wl.ne)
+    lo = wl.nb + wl.rd
+    assert any(i0 >= lo and i0 + 31 <= np0 - 2 - lo for i0 in range(0, np0, 32))
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    grad, _ = emm.vjp(grid, survey, sigma, torch.from_numpy(v).cuda(), ckpt_every=23)
+    dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
+    ref = oracle.vjp(wl.x, wl.y, wl.z, wl.sigma, v, rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0,
+                     nt=wl.nt, fmax=wl.fmax, sigma_min=survey.sigma_min, dt=dt, src=wl.src, az=wl.src_az,
+                     dip=wl.src_dip, moment=wl.moment, rec=wl.rec, freqs=wl.freqs, ckpt_every=30)
+    g = grad.cpu().numpy()
+    err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert err < GRAD_TOL, err
