@@ -47,7 +47,7 @@ struct AdjParams {
   int np[3], n[3], pitch, nb, rd, nbe, org[3];
   size_t plane;
   float kappa;               // dt / mu0
-  double inv_2w0dt;          // 1 / (2 omega0 dt): sigma = 2 omega0 dt / ie
+  float inv_2w0dt;           // 1 / (2 omega0 dt): sigma = 2 omega0 dt / ie
   const float *ie[3];
   float *lamE[3], *lamH[3];  // adjoint fields (field layout)
   float *T[6];               // per-derivative adjoints of the current half step (field layout)
@@ -105,11 +105,27 @@ __device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
 // c+2).  A pointwise pass writes T; a gather then applies the transposed FD
 // rows to it.
 
+// Pre-pass geometry: a thread owns 4 x-adjacent samples (a quad starting on
+// a 16-byte boundary of the field rows); quads with no CPML sample and every
+// sample updated take a float4 path, the others a per-sample one.
+__device__ __forceinline__ bool quad_of_pre(const AdjParams &a, int *idx) {
+  idx[0] = a.org[0] + static_cast<int>(blockIdx.x * 128 + threadIdx.x * 4);
+  idx[1] = static_cast<int>(blockIdx.y * 4 + threadIdx.y);
+  idx[2] = static_cast<int>(blockIdx.z);
+  return idx[0] + 3 >= 0 && idx[0] < a.np[0] && idx[1] < a.np[1];
+}
+__device__ __forceinline__ float4 ldf4(const float *p, size_t id) { return *reinterpret_cast<const float4 *>(p + id); }
+__device__ __forceinline__ void stf4(float *p, size_t id, const float4 &v) { *reinterpret_cast<float4 *>(p + id) = v; }
+__device__ __forceinline__ float4 scl4(float c, const float4 &v) { return make_float4(c * v.x, c * v.y, c * v.z, c * v.w); }
+// is every sample of the quad outside the CPML slabs and updated (lo .. hi
+// per axis)?
+__device__ __forceinline__ bool quad_plain(const AdjParams &a, const int *idx, int lo, const int *hi) {
+  return idx[0] >= lo && idx[0] + 3 <= hi[0] && idx[1] >= lo && idx[1] <= hi[1] && idx[2] >= lo && idx[2] <= hi[2];
+}
+
 // 1a. T[2c+t] at the H_c samples from lambda_H.
-__global__ void k_adj_h_pre(const AdjParams a) {
+__device__ __forceinline__ void h_pre_cell(const AdjParams &a, const int *idx) {
   const int R = a.rd, nb = a.nb;
-  int idx[3];
-  if (!cell3(a, idx)) return;
   const size_t id = fid(a, idx[0], idx[1], idx[2]);
   bool dp[3];
   for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
@@ -133,6 +149,26 @@ __global__ void k_adj_h_pre(const AdjParams a) {
       }
       a.T[2 * c + term][id] = t;
     }
+  }
+}
+__global__ void k_adj_h_pre(const AdjParams a) {
+  int idx[3];
+  if (!quad_of_pre(a, idx)) return;
+  // H samples with no half-sample slab and every D+ row: nb .. np-2-nb
+  const int hi[3] = {a.np[0] - 2 - a.nb, a.np[1] - 2 - a.nb, a.np[2] - 2 - a.nb};
+  if (quad_plain(a, idx, a.nb, hi)) {
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 g = scl4(-a.kappa, ldf4(a.lamH[c], id));
+      stf4(a.T[2 * c], id, g);
+      stf4(a.T[2 * c + 1], id, scl4(-1.f, g));
+    }
+    return;
+  }
+  for (int e = 0; e < 4; ++e) {
+    const int cell[3] = {idx[0] + e, idx[1], idx[2]};
+    if (cell[0] >= 0 && cell[0] < a.np[0]) h_pre_cell(a, cell);
   }
 }
 
@@ -159,10 +195,8 @@ __global__ void k_adj_receivers(const AdjParams a, int n) {
 // 3. The gradient term of this step, g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e
 // / (2 omega0 dt) (lambda_E is final for the step here), and T[2e+t] at the
 // E_e samples from lambda_E.
-__global__ void k_adj_e_pre(const AdjParams a) {
+__device__ __forceinline__ void e_pre_cell(const AdjParams &a, const int *idx) {
   const int R = a.rd, nb = a.nb;
-  int idx[3];
-  if (!cell3(a, idx)) return;
   const size_t id = fid(a, idx[0], idx[1], idx[2]);
   bool dm[3];
   for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
@@ -171,7 +205,7 @@ __global__ void k_adj_e_pre(const AdjParams a) {
     const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
     const float lam = a.lamE[e][id], ie = a.ie[e][id];
     const float dE = a.E1[e][id] - a.E0[e][id];
-    if (dE != 0.f) a.gseg[e][id] -= static_cast<float>(static_cast<double>(lam) * dE * ie * a.inv_2w0dt);
+    a.gseg[e][id] -= lam * dE * ie * a.inv_2w0dt;
     const float g = ie * lam;
     for (int term = 0; term < 2; ++term) {
       const int ax = term == 0 ? p : q;
@@ -189,6 +223,35 @@ __global__ void k_adj_e_pre(const AdjParams a) {
       }
       a.T[2 * e + term][id] = t;
     }
+  }
+}
+__global__ void k_adj_e_pre(const AdjParams a) {
+  int idx[3];
+  if (!quad_of_pre(a, idx)) return;
+  // E samples with no integer-sample slab and every D- row: nb .. np-1-nb
+  const int hi[3] = {a.np[0] - 1 - a.nb, a.np[1] - 1 - a.nb, a.np[2] - 1 - a.nb};
+  if (quad_plain(a, idx, a.nb, hi)) {
+    const size_t id = fid(a, idx[0], idx[1], idx[2]);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const float4 lam = ldf4(a.lamE[e], id), ie = ldf4(a.ie[e], id), e0 = ldf4(a.E0[e], id),
+                   e1 = ldf4(a.E1[e], id);
+      float4 gs = ldf4(a.gseg[e], id);
+      const float c = a.inv_2w0dt;
+      gs.x -= lam.x * (e1.x - e0.x) * ie.x * c;
+      gs.y -= lam.y * (e1.y - e0.y) * ie.y * c;
+      gs.z -= lam.z * (e1.z - e0.z) * ie.z * c;
+      gs.w -= lam.w * (e1.w - e0.w) * ie.w * c;
+      stf4(a.gseg[e], id, gs);
+      const float4 g = make_float4(ie.x * lam.x, ie.y * lam.y, ie.z * lam.z, ie.w * lam.w);
+      stf4(a.T[2 * e], id, g);
+      stf4(a.T[2 * e + 1], id, scl4(-1.f, g));
+    }
+    return;
+  }
+  for (int e = 0; e < 4; ++e) {
+    const int cell[3] = {idx[0] + e, idx[1], idx[2]};
+    if (cell[0] >= 0 && cell[0] < a.np[0]) e_pre_cell(a, cell);
   }
 }
 
@@ -508,7 +571,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   for (int ax = 0; ax < 3; ++ax) a.org[ax] = P.p.org[ax];
   a.status = P.p.status;
   a.kappa = P.p.dt_mu;
-  a.inv_2w0dt = 1.0 / (2.0 * s->omega0 * P.dt);
+  a.inv_2w0dt = static_cast<float>(1.0 / (2.0 * s->omega0 * P.dt));
   const int xs = P.fg.xshift;
   for (int c = 0; c < 3; ++c) {
     a.ie[c] = P.p.ie[c];
@@ -565,6 +628,8 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const dim3 blocks_r(P.p.tiles_x, P.p.tiles_y, P.p.tiles_z);
   const int grid_cells = P.sms * 8;
   const dim3 tb(32, 8, 1), grid3((P.p.np[0] + 31) / 32, (P.p.np[1] + 7) / 8, P.p.np[2]);
+  // pre passes: 32 x 4 threads, 4 x-adjacent samples each, over x from org[0]
+  const dim3 tpre(32, 4, 1), gpre((P.p.np[0] - P.p.org[0] + 127) / 128, (P.p.np[1] + 3) / 4, P.p.np[2]);
   Gathers GA{};
   const bool gok = rd == 1 ? make_gathers<1>(a, &GA)
                    : rd == 2 ? make_gathers<2>(a, &GA)
@@ -591,10 +656,10 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
         a.E1[c] =
             reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0 + 1) * A.ebytes + ec) + xs;
       }
-      k_adj_h_pre<<<grid3, tb, 0, cs>>>(a);
+      k_adj_h_pre<<<gpre, tpre, 0, cs>>>(a);
       GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
       if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
-      k_adj_e_pre<<<grid3, tb, 0, cs>>>(a);
+      k_adj_e_pre<<<gpre, tpre, 0, cs>>>(a);
       GA.g1<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
       e = cudaGetLastError();
     }
