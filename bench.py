@@ -290,7 +290,7 @@ def main():
         return max_over_ranks(v, dist, "cuda")
 
     # ---- timed region: K device-resident solves ----
-    e_ms, h_ms = [], []
+    e_ms, h_ms, loop_ms = [], [], []
     with ClockSampler(local) as clk:
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -299,6 +299,7 @@ def main():
             t = emm.forward_timed(grid, survey, sigma, work, every=64)
             e_ms.append(t["e_ms"])
             h_ms.append(t["h_ms"])
+            loop_ms.append(t["loop_ms"])
         ev1.record(stream)
         barrier()
     elapsed = job_max(ev0.elapsed_time(ev1) / 1e3)
@@ -322,7 +323,9 @@ def main():
     e_mean, h_mean = float(np.mean(e_ms)), float(np.mean(h_ms))
     alg = algorithmic_bytes(wl)
     be, bh = per_kernel_bytes(wl)
-    step_s = (e_mean + h_mean) / 1e3
+    # one leapfrog step as the time loop runs it: E and H back to back, each
+    # launch a programmatic dependent of the one before
+    step_s = float(np.mean(loop_ms)) / nt / 1e3
     achieved = alg / step_s / 1e9
     kernel_launches = args.steps * (1 + 2 * nt + (1 if survey.nrec else 0) + (1 if survey.volume else 0))
     line = {
@@ -340,6 +343,8 @@ def main():
                      "peak_kind": ("of measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                    if peak_kind == "measured" else "of fallback 6.4 TB/s"),
                      "algorithmic_bytes_per_step": alg, "step_ms": 1e3 * step_s,
+                     "step_ms_from": "CUDA events around the whole time loop / leapfrog steps",
+                     "isolated_step_ms": e_mean + h_mean,
                      "traffic": recorded_traffic(wl.name),
                      "kernels": {"k_update_E": {"ms": e_mean, "min_bytes": be, "gbs": be / e_mean / 1e6},
                                  "k_update_H": {"ms": h_mean, "min_bytes": bh, "gbs": bh / h_mean / 1e6}}},

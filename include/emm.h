@@ -174,10 +174,13 @@ typedef struct {
   double e_ms;     /* out: mean duration (ms) of one E half-step launch */
   double h_ms;     /* out: mean duration (ms) of one H half-step launch */
   double total_ms; /* out: duration (ms) of the whole enqueued forward run */
+  double loop_ms;  /* out: duration (ms) of the time loop alone: every E and H
+                      launch back to back, from the first to the last */
 } emm_timing;
 
 /* emm_forward, with CUDA events recorded on `stream` around the E and H
- * launches of every timing->every-th step and around the whole run.  Same
+ * launches of every timing->every-th step, around the time loop and around
+ * the whole run.  Same
  * arguments, outputs and errors as emm_forward; in addition it synchronises
  * `stream` before returning and fills *timing (host).  EMM_EINVAL if timing
  * is NULL or timing->every < 1. */

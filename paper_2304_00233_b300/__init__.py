@@ -59,7 +59,7 @@ class _GridInfo(C.Structure):
 
 class _Timing(C.Structure):
     _fields_ = [("every", C.c_int), ("samples", C.c_int), ("e_ms", C.c_double),
-                ("h_ms", C.c_double), ("total_ms", C.c_double)]
+                ("h_ms", C.c_double), ("total_ms", C.c_double), ("loop_ms", C.c_double)]
 
 
 class _Survey(C.Structure):
@@ -293,7 +293,7 @@ def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int
                   stream=None) -> dict:
     """``emm_forward_timed``: like ``forward_async`` but synchronises and
     returns the mean device duration of the E and H launches (sampled every
-    ``every`` steps) and of the whole run, in ms."""
+    ``every`` steps), of the time loop and of the whole run, in ms."""
     import torch
     _check_sigma(grid, sigma)
     if stream is None:
@@ -307,7 +307,7 @@ def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int
         C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream),
         C.byref(t))
     _check(code, "emm_forward_timed")
-    return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, total_ms=t.total_ms)
+    return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, total_ms=t.total_ms, loop_ms=t.loop_ms)
 
 
 def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None,

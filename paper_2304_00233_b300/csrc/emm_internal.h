@@ -127,6 +127,7 @@ inline int psi_axis(int c) { return (c % 2 == 0) ? (c / 2 + 1) % 3 : (c / 2 + 2)
 struct StepEvents {
   int every = 0;
   std::vector<cudaEvent_t> ev;
+  cudaEvent_t loop[2] = {nullptr, nullptr};  // around the whole time loop
 };
 
 // A forward run set up in a workspace: the launch parameters of its steps.

@@ -586,6 +586,8 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
 template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  wait_prior_grid();
+  allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
     const Fields f = fields_of<MULTI>(p, rs);
@@ -810,6 +812,8 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, cons
 template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  wait_prior_grid();
+  allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
     const Fields f = fields_of<MULTI>(p, rs);
@@ -1037,19 +1041,22 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
     e = cudaFuncSetAttribute(k_update_H<R, VOL, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
+  // each half-step is launched as a programmatic dependent of the one before
   size_t used = 0;
-  for (int n = n0; n < n1; ++n) {
+  if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
+  for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    k_update_E<R, VOL, MULTI><<<blocks, NT, sb, st>>>(p, tE, n);
+    e = launch_dependent(k_update_E<R, VOL, MULTI>, blocks, dim3(NT), sb, st, p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    k_update_H<R, VOL, MULTI><<<blocks, NT, sb, st>>>(p, tH, n);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI>, blocks, dim3(NT), sb, st, p, tH, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
     }
   }
-  return cudaGetLastError();
+  if (te && te->loop[1]) cudaEventRecord(te->loop[1], st);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
@@ -1368,7 +1375,7 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   if (st != EMM_OK) return st;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   const int nsamp = s->nt > 0 ? (s->nt + timing->every - 1) / timing->every : 0;
-  std::vector<cudaEvent_t> all(3 * static_cast<size_t>(nsamp) + 2, nullptr);
+  std::vector<cudaEvent_t> all(3 * static_cast<size_t>(nsamp) + 4, nullptr);
   for (auto &e : all)
     if (cudaEventCreate(&e) != cudaSuccess) {
       for (auto &d : all)
@@ -1379,6 +1386,8 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   te.every = timing->every;
   te.ev.assign(all.begin(), all.begin() + 3 * static_cast<size_t>(nsamp));
   cudaEvent_t t0 = all[all.size() - 2], t1 = all[all.size() - 1];
+  te.loop[0] = all[all.size() - 4];
+  te.loop[1] = all[all.size() - 3];
   cudaEventRecord(t0, cs);
   st = forward_impl(g, s, sigma, ws, ws_bytes, rec_out, vol_out, stream, &te);
   cudaEventRecord(t1, cs);
@@ -1397,6 +1406,9 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   ms = 0.f;
   if (st == EMM_OK) cudaEventElapsedTime(&ms, t0, t1);
   timing->total_ms = ms;
+  ms = 0.f;
+  if (st == EMM_OK && s->nt > 0) cudaEventElapsedTime(&ms, te.loop[0], te.loop[1]);
+  timing->loop_ms = ms;
   for (auto &e : all) cudaEventDestroy(e);
   return st;
 }

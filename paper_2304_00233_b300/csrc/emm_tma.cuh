@@ -10,6 +10,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <utility>
 
 namespace emm {
 
@@ -79,6 +80,31 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Programmatic dependent launch.  A kernel launched with launch_dependent()
+// may be dispatched while the kernel before it on the stream drains; its CTAs
+// call wait_prior_grid() before touching memory that kernel wrote (the wait
+// ends when that grid has completed and its writes are visible), and
+// allow_next_launch() lets the next dependent kernel be dispatched once every
+// CTA of this one has started.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args &&...args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // cuTensorMapEncodeTiled, fetched once from the driver through the runtime.
