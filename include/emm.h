@@ -188,6 +188,25 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
                       void *ws, size_t ws_bytes, double *rec_out, double *vol_out,
                       emm_stream stream, emm_timing *timing);
 
+/* emm_forward with the paper's stopping rule (Sec. 4.1): after step 0, and
+ * after every step it = 100, 200, ..., a one-warp kernel compares the DTFT of
+ * the six components at the 8 corners of the model interior (the samples
+ * nb+ne and nb+ne+n-1 of each axis) for the lowest frequency with its value
+ * at the previous check.  The run has converged after step it when, at every
+ * corner, the change is at most 1e-5 of the current value and that value is
+ * nonzero; it then keeps nt_run = it + 1 steps, and every leapfrog launch
+ * already enqueued returns at once.  At most survey->nt steps run.
+ * The verdicts reach the host through mapped pinned host memory (allocated
+ * and freed by the call: 8 bytes), polled with one chunk of launches enqueued
+ * ahead, each poll bounded (EMM_ETIMEOUT after 600 s without progress).
+ * Synchronous: returns with `stream` drained.  *nt_run (host) receives the
+ * steps taken.  Arguments, workspace (emm_workspace_size) and outputs as
+ * emm_forward, the outputs being those of emm_forward with nt = *nt_run.
+ * EMM_EINVAL if nt_run is NULL; other errors as emm_forward. */
+int emm_forward_converge(const emm_grid *grid, const emm_survey *survey, const float *sigma,
+                         void *ws, size_t ws_bytes, double *rec_out, double *vol_out,
+                         emm_stream stream, int *nt_run);
+
 /* Read the device status word of a workspace after emm_forward: synchronises
  * `stream`, then *status = EMM_OK, EMM_EDEVICE (a sigma value was not finite,
  * not positive, or below sigma_min) or EMM_ETIMEOUT (a kernel gave up on a

@@ -35,7 +35,7 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
             "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
             "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient",
-            "emm_batch_workspace_size", "emm_forward_batch")
+            "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge")
 
 
 class EmmError(RuntimeError):
@@ -99,6 +99,7 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_forward_static": ([V, C.POINTER(_Survey), V, V, V, V, _I], C.c_int),
         "emm_batch_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "emm_forward_batch": ([V, C.POINTER(_Survey), C.c_int, _D, V, V, C.c_size_t, V, V], C.c_int),
+        "emm_forward_converge": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V, _I], C.c_int),
         "emm_gradient_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "emm_gradient": ([V, C.POINTER(_Survey), V, V, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
@@ -287,6 +288,26 @@ def forward_async(grid: Grid, survey: Survey, sigma, work: Workspace, stream=Non
         C.c_size_t(work.bytes), C.c_void_p(work.rec.data_ptr()),
         C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream))
     _check(code, "emm_forward")
+
+
+def forward_converge(grid: Grid, survey: Survey, sigma, work: Workspace, stream=None) -> int:
+    """``emm_forward_converge``: ``forward_async`` with the paper's corner
+    convergence test every 100 steps (at most ``survey.nt`` steps).
+    Synchronous; returns the number of leapfrog steps taken.  ``work.rec``
+    (and ``work.vol``) hold the Green's functions of that many steps."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    s, keep = survey._c()
+    nt_run = C.c_int(0)
+    code = load_library().emm_forward_converge(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(work.ptr),
+        C.c_size_t(work.bytes), C.c_void_p(work.rec.data_ptr()),
+        C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream),
+        C.byref(nt_run))
+    _check(code, "emm_forward_converge")
+    return int(nt_run.value)
 
 
 def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int = 64,

@@ -65,6 +65,13 @@ struct DevParams {
   int tiles_x, tiles_y, tiles_z, stencil_blocks;  // stencil_blocks: stencil CTAs of a launch
   int rec_blocks;   // receiver CTAs (one warp per receiver component)
   int rec_layers;   // grid z layers holding them (the first ones)
+  // Convergence runs (else null): DTFT of the six components at the 8
+  // corners of the model interior for the lowest frequency, [8][6][2] FP64,
+  // followed by its value at the last check; and the stop word, nonzero once
+  // the corner test has passed (every later launch then returns at once).
+  double *corner;
+  const int *halt;
+  int conv_f;       // index of the lowest frequency
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
@@ -112,7 +119,7 @@ FieldGeom field_geom(const emm_grid *g);
 // The state of transmitter 0 (E[3], H[3], psiE[6], psiH[6]) is one block
 // at E[0]; transmitter k's block starts sstride bytes further per k.
 struct Layout {
-  size_t status, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, zero_end;
+  size_t status, conv, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, zero_end;
   size_t cm[3], cp[3], pml[3], srcs, jw, amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
 };
 
@@ -145,7 +152,7 @@ struct Prepared {
 // nsrc transmitters at src_pos ([nsrc][3], host; NULL: the survey's source).
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc = 1,
-                    const double *src_pos = nullptr);
+                    const double *src_pos = nullptr, bool converge = false);
 // Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te);

@@ -36,10 +36,12 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "emm_internal.h"
@@ -120,7 +122,20 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
   constexpr int M = 2 * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = block * (NT / 32) + warp;
-  if (item >= p.nrec * 3) return;
+  if (item >= p.nrec * 3) {
+    if (p.corner && item == p.nrec * 3 && lane < 24) {
+      // convergence runs: the corner DTFT, one lane per (corner, component)
+      const int q = lane / 3, cc = lane % 3;
+      const int i = p.nbe + ((q & 1) ? p.n[0] - 1 : 0), j = p.nbe + ((q & 2) ? p.n[1] - 1 : 0),
+                k = p.nbe + ((q & 4) ? p.n[2] - 1 : 0);
+      const float *f = cc == 0 ? F[0] : (cc == 1 ? F[1] : F[2]);
+      const double v = f[static_cast<size_t>(k) * p.plane + static_cast<size_t>(j) * p.pitch + i];
+      double *acc = p.corner + (q * 6 + comp0 + cc) * 2;
+      acc[0] += fac[2 * p.conv_f] * v;
+      acc[1] += fac[2 * p.conv_f + 1] * v;
+    }
+    return;
+  }
   const int rec = item / 3, c = comp0 + item % 3;
   const int *st = p.rec_start + (rec * 6 + c) * 3;
   const double *w = p.rec_w + static_cast<size_t>(rec * 6 + c) * 3 * M;
@@ -587,6 +602,7 @@ template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
+  if (p.halt && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
@@ -813,6 +829,7 @@ template <int R, bool VOL, bool MULTI>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
+  if (p.halt && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
@@ -909,6 +926,39 @@ __global__ void k_finalize_vol(const float4 *vacc, double *vol, const double *no
   }
 }
 
+// Corner test of a convergence run (Sec. 4.1), after step `it`: with
+// init, remember the corner DTFT; otherwise the run has converged when, at
+// each of the 8 corners, the change of the corner DTFT (six components,
+// lowest frequency) since the last check is at most 1e-5 of its current
+// value and that value is nonzero.  Then *halt = it + 1, the steps to keep.
+// host (mapped host memory): [0] the last step checked, [1] *halt.
+__global__ void k_corner_check(double *corner, int *halt, volatile int *host, int it, int init) {
+  if (*halt) return;  // stopped at an earlier check: the look-ahead chunk changed nothing
+  const int lane = threadIdx.x;
+  double *prev = corner + 8 * 6 * 2;
+  bool ok = true;
+  if (!init && lane < 8) {
+    double dn = 0.0, un = 0.0;
+    for (int c = 0; c < 6; ++c) {
+      const double *a = corner + (lane * 6 + c) * 2, *b = prev + (lane * 6 + c) * 2;
+      const double dr = a[0] - b[0], di = a[1] - b[1];
+      dn += dr * dr + di * di;
+      un += a[0] * a[0] + a[1] * a[1];
+    }
+    ok = un > 0.0 && !(sqrt(dn) > 1e-5 * sqrt(un));
+  }
+  const bool all = __all_sync(0xffffffffu, ok);
+  for (int t = lane; t < 8 * 6 * 2; t += 32) prev[t] = corner[t];
+  if (lane == 0) {
+    if (!init && all) {
+      *halt = it + 1;
+      host[1] = it + 1;
+    }
+    host[0] = it;
+    __threadfence_system();
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -963,6 +1013,7 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   const size_t m = 2 * static_cast<size_t>(g->rd), nf = s->nfreq;
   const size_t nt = s->nt > 0 ? s->nt : 1, nrec = s->nrec > 0 ? s->nrec : 1;
   L.status = take(sizeof(int));
+  L.conv = take((2 * 8 * 6 * 2) * sizeof(double) + 2 * sizeof(int));  // corners, last check, stop word
   // transmitter 0's state block; transmitters 1 .. nsrc-1 follow it
   const size_t b0 = off;
   for (int c = 0; c < 3; ++c) L.E[c] = take(cells * 4);
@@ -1059,9 +1110,37 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+// Normalisation of the DTFT (Eq. 7) for a run of nsteps leapfrog steps:
+// norm[0][f] = sqrt(-i w / (2 w0)) / J'(f) for G^EE and norm[1][f] = 1 / J'(f)
+// for G^HE, J' the DTFT of the source wavelet sampled at t_{n+1/2} (the H
+// label), as complex pairs [2][nfreq][2].
+void normalisation(const emm_survey *s, double dt, int nsteps, double *norm) {
+  const int nf = s->nfreq;
+  const std::complex<double> I(0.0, 1.0);
+  const double t0 = 1.5 / s->fmax;
+  for (int f = 0; f < nf; ++f) {
+    const std::complex<double> wp = std::complex<double>(1.0, 1.0) * std::sqrt(2.0 * M_PI * s->freqs[f] * s->omega0);
+    std::complex<double> jhat = 0.0;
+    for (int n = 0; n < nsteps; ++n) {
+      const double th = (n + 0.5) * dt;
+      const double u = M_PI * s->fmax * (th - t0);
+      const double a = s->moment * std::exp(-u * u);
+      jhat += std::exp(I * wp * th) * dt * a;
+    }
+    const std::complex<double> sE =
+        std::sqrt(2.0 * M_PI * s->freqs[f] / (2.0 * s->omega0)) * std::exp(-I * (M_PI / 4.0));
+    const std::complex<double> nE = (jhat != 0.0) ? sE / jhat : 0.0;
+    const std::complex<double> nH = (jhat != 0.0) ? 1.0 / jhat : 0.0;
+    norm[2 * f] = nE.real();
+    norm[2 * f + 1] = nE.imag();
+    norm[2 * nf + 2 * f] = nH.real();
+    norm[2 * nf + 2 * f + 1] = nH.imag();
+  }
+}
+
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc,
-                    const double *src_pos) {
+                    const double *src_pos, bool converge) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
@@ -1158,7 +1237,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   float *amp = reinterpret_cast<float *>(at(L.amp));
   double *fE = reinterpret_cast<double *>(at(L.fE)), *fH = reinterpret_cast<double *>(at(L.fH));
   float *fE32 = reinterpret_cast<float *>(at(L.fE32)), *fH32 = reinterpret_cast<float *>(at(L.fH32));
-  std::vector<std::complex<double>> jhat(nf, 0.0), wp(nf);
+  std::vector<std::complex<double>> wp(nf);
   for (int f = 0; f < nf; ++f)
     wp[f] = std::complex<double>(1.0, 1.0) * std::sqrt(2.0 * M_PI * s->freqs[f] * s->omega0);
   const double t0 = 1.5 / s->fmax;
@@ -1179,21 +1258,9 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
       fE32[o + 1] = static_cast<float>(eE.imag());
       fH32[o] = static_cast<float>(eH.real());
       fH32[o + 1] = static_cast<float>(eH.imag());
-      jhat[f] += eH * a;  // J is sampled at t_{n+1/2}, the H label
     }
   }
-  // normalisation (Eq. 7): G^EE = sqrt(-i w / (2 w0)) E'/J', G^HE = H'/J'
-  double *norm = reinterpret_cast<double *>(at(L.norm));
-  for (int f = 0; f < nf; ++f) {
-    const std::complex<double> sE =
-        std::sqrt(2.0 * M_PI * s->freqs[f] / (2.0 * s->omega0)) * std::exp(-I * (M_PI / 4.0));
-    const std::complex<double> nE = (jhat[f] != 0.0) ? sE / jhat[f] : 0.0;
-    const std::complex<double> nH = (jhat[f] != 0.0) ? 1.0 / jhat[f] : 0.0;
-    norm[2 * f] = nE.real();
-    norm[2 * f + 1] = nE.imag();
-    norm[2 * nf + 2 * f] = nH.real();
-    norm[2 * nf + 2 * f + 1] = nH.imag();
-  }
+  normalisation(s, dt, nt, reinterpret_cast<double *>(at(L.norm)));
 
   // ---- device parameters ----
   unsigned char *base = static_cast<unsigned char *>(ws);
@@ -1242,6 +1309,13 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
+  if (converge) {
+    p.corner = reinterpret_cast<double *>(base + L.conv);
+    p.halt = reinterpret_cast<const int *>(base + L.conv + 2 * 8 * 6 * 2 * sizeof(double));
+    p.conv_f = 0;
+    for (int f = 1; f < nf; ++f)
+      if (s->freqs[f] < s->freqs[p.conv_f]) p.conv_f = f;
+  }
   // launch shape: TX x TY column tiles times runs of ZC planes, then the
   // receiver CTAs (one warp per receiver component)
   for (int a = 0; a < 3; ++a) p.org[a] = fg.org[a];
@@ -1254,7 +1328,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   p.stencil_blocks = p.tiles_x * p.tiles_y * p.tiles_z;
-  p.rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
+  p.rec_blocks = (s->nrec * 3 + (converge ? 1 : 0) + NT / 32 - 1) / (NT / 32);
   const int layer = p.tiles_x * p.tiles_y;
   p.rec_layers = (p.rec_blocks + layer - 1) / layer;
   const dim3 blocks(p.tiles_x * nsrc, p.tiles_y, p.rec_layers + p.tiles_z);
@@ -1410,6 +1484,80 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   if (st == EMM_OK && s->nt > 0) cudaEventElapsedTime(&ms, te.loop[0], te.loop[1]);
   timing->loop_ms = ms;
   for (auto &e : all) cudaEventDestroy(e);
+  return st;
+}
+
+int emm_forward_converge(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
+                         double *rec_out, double *vol_out, emm_stream stream, int *nt_run) {
+  using namespace emm;
+  if (!nt_run) return EMM_EINVAL;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  int st = prepare_forward(g, s, sigma, ws, ws_bytes, rec_out, vol_out, cs, &P, 1, nullptr, true);
+  if (st != EMM_OK) return st;
+  // The verdicts come back through mapped host memory (Sec. 4.1): [0] the
+  // last step checked, [1] the steps to keep once converged.
+  int *hw = nullptr, *dw = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void **>(&hw), 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+    return EMM_ECUDA;
+  volatile int *vhw = hw;
+  vhw[0] = -1;
+  vhw[1] = 0;
+  if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&dw), hw, 0) != cudaSuccess) {
+    cudaFreeHost(hw);
+    return EMM_ECUDA;
+  }
+  int *halt = const_cast<int *>(P.p.halt);
+  // Chunks: step 0, then the reference corner values; then up to and
+  // including each step it = 100, 200, ... and its check; then the rest.
+  const int nt = s->nt;
+  struct Chunk {
+    int lo, hi, check;  // steps lo .. hi-1, then the check after step `check` (-1: none)
+  };
+  std::vector<Chunk> chunks;
+  if (nt > 0) chunks.push_back({0, 1, 0});
+  for (int it = 100; it < nt; it += 100) chunks.push_back({chunks.back().hi, it + 1, it});
+  if (!chunks.empty() && chunks.back().hi < nt) chunks.push_back({chunks.back().hi, nt, -1});
+  auto enqueue = [&](const Chunk &c) {
+    cudaError_t e = run_steps(P, P.p, P.blocks, c.lo, c.hi, cs, nullptr);
+    if (e == cudaSuccess && c.check >= 0) {
+      k_corner_check<<<1, 32, 0, cs>>>(P.p.corner, halt, dw, c.check, c.check == 0 ? 1 : 0);
+      e = cudaGetLastError();
+    }
+    return e;
+  };
+  // One chunk of look-ahead: chunk q+1 is enqueued before the host waits
+  // (bounded) for the verdict of chunk q; launches after a stop return at once.
+  constexpr double kPollSeconds = 600.0;
+  size_t next = 0;
+  bool stopped = false;
+  for (size_t q = 0; q < chunks.size() && st == EMM_OK && !stopped; ++q) {
+    while (next < chunks.size() && next <= q + 1 && st == EMM_OK)
+      if (enqueue(chunks[next++]) != cudaSuccess) st = EMM_ECUDA;
+    if (st != EMM_OK || chunks[q].check < 0) continue;
+    const auto t0 = std::chrono::steady_clock::now();
+    while (vhw[0] < chunks[q].check) {
+      if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kPollSeconds) {
+        st = EMM_ETIMEOUT;
+        break;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    if (vhw[1] > 0) stopped = true;
+  }
+  if (cudaStreamSynchronize(cs) != cudaSuccess && st == EMM_OK) st = EMM_ECUDA;
+  const int kept = vhw[1] > 0 ? vhw[1] : nt;
+  cudaFreeHost(hw);
+  if (st != EMM_OK) return st;
+  // normalisation over the steps taken
+  std::vector<double> norm(4 * static_cast<size_t>(s->nfreq));
+  normalisation(s, P.dt, kept, norm.data());
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  if (cudaMemcpy(base + P.L.norm, norm.data(), norm.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return EMM_ECUDA;
+  st = finalize_forward(P, s, rec_out, vol_out, cs);
+  if (st == EMM_OK && cudaStreamSynchronize(cs) != cudaSuccess) st = EMM_ECUDA;
+  *nt_run = kept;
   return st;
 }
 
