@@ -139,6 +139,14 @@ typedef struct {
   int volume;           /* 1: also accumulate the DTFT of all six components on
                            every interior sample (the n1 x n2 x n3 samples of each
                            component's own staggered positions) */
+  int src_kind;         /* 0: electric dipole J, injected in the E update at
+                           t_{n+1/2}; outputs G^EE = sqrt(-i w/(2 w0)) E'/J' and
+                           G^HE = H'/J' (Eq. 7).  1: magnetic dipole M (Eq. 1),
+                           on the H samples, injected in the H update at t_{n+1}
+                           (mu dH/dt = -(curl E + M)); outputs, from the
+                           correspondence of Eq. 5 (E' = E, H' = sqrt(-i w/(2 w0)) H,
+                           M' = M), G^EH = E'/M' and G^HH = H'/(sqrt(-i w/(2 w0)) M').
+                           Same orientation (src_az, src_dip) and wavelet. */
 } emm_survey;
 
 /* Device workspace bytes emm_forward needs for this grid and survey
@@ -256,7 +264,8 @@ int emm_gradient_workspace_size(const emm_grid *grid, const emm_survey *survey, 
  *   grad      device double [3][n3][n2][n1]: the gradient with respect to
  *             the interior staggered sigma_xx, sigma_yy, sigma_zz (the pads'
  *             replicated values folded onto the edge samples).
- * Asynchronous on `stream`; errors as emm_forward (survey->volume must be 0). */
+ * Asynchronous on `stream`; errors as emm_forward (survey->volume must be 0
+ * and survey->src_kind 0: EMM_EINVAL otherwise). */
 int emm_gradient(const emm_grid *grid, const emm_survey *survey, const float *sigma, const double *dG,
                  int ckpt_every, void *ws, size_t ws_bytes, double *rec_out, double *grad,
                  emm_stream stream);

@@ -175,6 +175,7 @@ class _Problem(C.Structure):
         ("info", C.POINTER(C.c_double)),
         ("nvs", C.c_int), ("vs_idx", C.POINTER(C.c_longlong)),
         ("vs_G", C.POINTER(C.c_double)),
+        ("magnetic", C.c_int),
     ]
 
 
@@ -185,13 +186,16 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
             convergence: bool = False, inject: bool = True, pml: bool = True,
             init_fields: Optional[np.ndarray] = None,
             want_fields: bool = False,
-            vol_samples: Optional[np.ndarray] = None) -> Dict[str, object]:
+            vol_samples: Optional[np.ndarray] = None,
+            magnetic: bool = False) -> Dict[str, object]:
     """Run the FP64 oracle.  ``sigma`` is [3][n3][n2][n1] (staggered sigma_xx,
     sigma_yy, sigma_zz).  Returns a dict with ``G`` [nrec][6][nfreq] complex,
     ``acc`` (raw DTFT), ``jhat`` [nfreq], optional ``vol`` [6][nfreq][n3][n2][n1]
     and ``fields`` [6][n3p][n2p][n1p], plus ``dt``, ``vmax``, ``nt``, ``eta``.
     ``vol_samples`` (flat indices into [6][n3][n2][n1]) gives ``vol_samples_G``
-    [nvs][nfreq]: the volume Green's functions at those samples only."""
+    [nvs][nfreq]: the volume Green's functions at those samples only.
+    ``magnetic``: the dipole is a magnetic source M (G^EH, G^HH) instead of an
+    electric current J (G^EE, G^HE)."""
     lib = _load()
     xs = [_f64(x), _f64(y), _f64(z)]
     n = [len(a) for a in xs]
@@ -217,6 +221,7 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     P.want_volume = int(volume)
     P.convergence = int(convergence)
     P.inject, P.pml = int(inject), int(pml)
+    P.magnetic = int(magnetic)
     ncell = npad[0] * npad[1] * npad[2]
     if init_fields is not None:
         init_fields = _f64(init_fields)

@@ -338,6 +338,8 @@ typedef struct {
   int nvs;
   const long long *vs_idx;
   double *vs_G;              /* [nvs][nfreq][2] Green's functions at those samples */
+  int magnetic;              /* 1: the source is a magnetic dipole M, injected in
+                                the H update (Eq. 5); 0: an electric dipole J */
 } orc_problem;
 
 typedef struct {
@@ -525,6 +527,16 @@ static double orc_sample(const orc_state *st, const double *F, const orc_stencil
 }
 
 /* Source wavelet, reading: Gaussian exp(-(pi fmax (t - t0))^2), t0 = 1.5/fmax. */
+/* Factor of component c (0..5) in the Green's functions.  Eq. 7 for an
+ * electric source: G^EE = sE E'/J', G^HE = H'/J', sE = sqrt(-i w/(2 w0)).
+ * Reading, for a magnetic source, from the correspondence of Eq. 5 (E' = E,
+ * H' = sE H, M' = M): G^EH = E'/M', G^HH = H'/(sE M'). */
+static double complex orc_norm(int c, double complex sE, int magnetic)
+{
+  if (!magnetic) return c < 3 ? sE : 1.0;
+  return c < 3 ? 1.0 : 1.0 / sE;
+}
+
 static double orc_wavelet(double t, double fmax)
 {
   double u = M_PI * fmax * (t - 1.5 / fmax);
@@ -596,16 +608,18 @@ int orc_forward(orc_problem *P)
   if (P->init_fields)
     for (int c = 0; c < 6; ++c) memcpy(st->F[c], P->init_fields + c * st->ncell, sizeof(double) * st->ncell);
 
-  /* Source stencils (only E components with a nonzero direction cosine). */
+  /* Source stencils (only components with a nonzero direction cosine): on
+   * the E samples of an electric dipole, on the H samples of a magnetic one
+   * (sc = 3). */
   double dir[3] = {cos(P->dip) * cos(P->az), cos(P->dip) * sin(P->az), sin(P->dip)};
   orc_stencil sst[3];
   double *jw[3] = {NULL, NULL, NULL};   /* dir_c * w / V per stencil node */
-  int m = 2 * rd;
+  int m = 2 * rd, sc = P->magnetic ? 3 : 0;
   if (P->inject) {
     for (int c = 0; c < 3; ++c) {
       if (dir[c] == 0.0) continue;
       for (int a = 0; a < 3; ++a) {
-        st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c][a], P->src[a], &sst[c].start[a], sst[c].w[a]);
+        st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c + sc][a], P->src[a], &sst[c].start[a], sst[c].w[a]);
         if (st_code) { orc_state_free(st); return st_code; }
       }
       jw[c] = malloc(sizeof(double) * m * m * m);
@@ -619,8 +633,8 @@ int orc_forward(orc_problem *P)
             double V = 1.0;
             for (int a = 0; a < 3; ++a) {
               const orc_axis *ax = &st->ax[a];
-              V *= ORC_HALF[c][a] ? (ax->X[id3[a] + 1] - ax->X[id3[a]])
-                                  : (ax->Xh[id3[a]] - ax->Xh[id3[a] - 1]);
+              V *= ORC_HALF[c + sc][a] ? (ax->X[id3[a] + 1] - ax->X[id3[a]])
+                                       : (ax->Xh[id3[a]] - ax->Xh[id3[a] - 1]);
             }
             jw[c][(q3 * m + q2) * m + q1] = dir[c] * sst[c].w[0][q1] * sst[c].w[1][q2] * sst[c].w[2][q3] / V;
           }
@@ -663,8 +677,10 @@ int orc_forward(orc_problem *P)
   for (int it = 0; it < P->nt; ++it) {
     double tJ = (it + 0.5) * dt, tE = (it + 1.0) * dt, tH = (it + 0.5) * dt;
     orc_curl_H(st, P->pml);
-    double amp = P->moment * orc_wavelet(tJ, P->fmax);
-    if (P->inject) {
+    /* reading: J is sampled at t_{n+1/2} (the E update's centre), M at
+     * t_{n+1} (the H update's centre) */
+    double amp = P->moment * orc_wavelet(P->magnetic ? tE : tJ, P->fmax);
+    if (P->inject && !P->magnetic) {
       for (int c = 0; c < 3; ++c) {
         if (!jw[c]) continue;
         for (int q3 = 0; q3 < m; ++q3)
@@ -681,7 +697,7 @@ int orc_forward(orc_problem *P)
     for (int f = 0; f < nf; ++f) {
       double complex fE = cexp(I * wp[f] * tE) * dt;
       double complex fH = cexp(I * wp[f] * tH) * dt;
-      jh[f] += cexp(I * wp[f] * tJ) * dt * amp;
+      jh[f] += cexp(I * wp[f] * (P->magnetic ? tE : tJ)) * dt * amp;
       for (int r = 0; r < nrec; ++r)
         for (int c = 0; c < 6; ++c)
           acc[((size_t)r * 6 + c) * nf + f] += (c < 3 ? fE : fH) * rval[r * 6 + c];
@@ -716,6 +732,17 @@ int orc_forward(orc_problem *P)
       }
     }
     orc_curl_E(st, P->pml);
+    /* magnetic source: mu dH/dt = -(curl E + M) (Eq. 5, time domain) */
+    if (P->inject && P->magnetic) {
+      for (int c = 0; c < 3; ++c) {
+        if (!jw[c]) continue;
+        for (int q3 = 0; q3 < m; ++q3)
+          for (int q2 = 0; q2 < m; ++q2)
+            for (int q1 = 0; q1 < m; ++q1)
+              st->C[c][IDX(st, sst[c].start[2] + q3, sst[c].start[1] + q2, sst[c].start[0] + q1)]
+                  += amp * jw[c][(q3 * m + q2) * m + q1];
+      }
+    }
     orc_update_H(st, dt);
     if (P->convergence && it > 0 && it % 100 == 0) {
       /* converged when, at every corner, the change since the last check is at
@@ -743,20 +770,20 @@ int orc_forward(orc_problem *P)
     for (int r = 0; r < nrec; ++r)
       for (int c = 0; c < 6; ++c) {
         size_t o = ((size_t)r * 6 + c) * nf + f;
-        double complex g = (c < 3 ? sE : 1.0) * acc[o] / jh[f];
+        double complex g = orc_norm(c, sE, P->magnetic) * acc[o] / jh[f];
         if (P->rec_G) { P->rec_G[2 * o] = creal(g); P->rec_G[2 * o + 1] = cimag(g); }
         if (P->rec_acc) { P->rec_acc[2 * o] = creal(acc[o]); P->rec_acc[2 * o + 1] = cimag(acc[o]); }
       }
     if (vsa && P->vs_G)
       for (int q = 0; q < P->nvs; ++q) {
         int c = (int)(P->vs_idx[q] / (long long)nint);
-        double complex g = (c < 3 ? sE : 1.0) * vsa[(size_t)q * nf + f] / jh[f];
+        double complex g = orc_norm(c, sE, P->magnetic) * vsa[(size_t)q * nf + f] / jh[f];
         P->vs_G[2 * ((size_t)q * nf + f)] = creal(g);
         P->vs_G[2 * ((size_t)q * nf + f) + 1] = cimag(g);
       }
     if (vol && P->vol_G)
       for (int c = 0; c < 6; ++c) {
-        double complex fac = (c < 3 ? sE : 1.0) / jh[f];
+        double complex fac = orc_norm(c, sE, P->magnetic) / jh[f];
         double complex *vc = vol + ((size_t)c * nf + f) * nint;
         double *out = P->vol_G + 2 * ((size_t)c * nf + f) * nint;
         for (size_t q = 0; q < nint; ++q) {
@@ -916,7 +943,7 @@ int orc_vjp(orc_problem *P, const double *v, double *grad, int ckpt_every)
   memset(st, 0, sizeof(S));
   int rd = P->rd, nb = P->nb, ne = P->ne, code = ORC_OK;
   if (rd < 1 || rd > 4 || nb < rd || ne < 0 || P->nt < 0 || P->omega0 <= 0 || !(P->sigma_min > 0) ||
-      ckpt_every < 1 || !v || !grad)
+      ckpt_every < 1 || !v || !grad || P->magnetic)
     return ORC_EINVAL;
   st->rd = rd;
   for (int a = 0; a < 3; ++a) {

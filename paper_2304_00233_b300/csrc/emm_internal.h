@@ -72,6 +72,7 @@ struct DevParams {
   double *corner;
   const int *halt;
   int conv_f;       // index of the lowest frequency
+  int src_magnetic; // 1: the source is a magnetic dipole, injected in the H update
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid

@@ -116,14 +116,15 @@ __device__ __forceinline__ void volume_accumulate(const DevParams &p, int comp, 
 
 // One warp per (receiver, component): (2R)^3 weighted gather in FP64, warp
 // shuffle reduction, then acc += factor * value for every frequency.
-template <int R>
+// CONV: a convergence run, whose extra warp accumulates the corner DTFT.
+template <int R, bool CONV>
 __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, const double *fac, int block,
                              double *rec_acc) {
   constexpr int M = 2 * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = block * (NT / 32) + warp;
   if (item >= p.nrec * 3) {
-    if (p.corner && item == p.nrec * 3 && lane < 24) {
+    if (CONV && item == p.nrec * 3 && lane < 24) {
       // convergence runs: the corner DTFT, one lane per (corner, component)
       const int q = lane / 3, cc = lane % 3;
       const int i = p.nbe + ((q & 1) ? p.n[0] - 1 : 0), j = p.nbe + ((q & 2) ? p.n[1] - 1 : 0),
@@ -598,16 +599,18 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
   }
 }
 
-template <int R, bool VOL, bool MULTI>
+// CONV: a convergence run (corner DTFT, and every launch returns at once
+// after the stop).
+template <int R, bool VOL, bool MULTI, bool CONV>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
-  if (p.halt && *p.halt) return;  // a convergence run that has stopped
+  if (CONV && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
     const Fields f = fields_of<MULTI>(p, rs);
-    receiver_dft<R>(p, 3, f.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+    receiver_dft<R, CONV>(p, 3, f.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
                     p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   const SrcDev *sd = p.srcs + o.src;
   const float *jw = p.jw + static_cast<size_t>(o.src) * 3 * (2 * R) * (2 * R) * (2 * R);
-  const bool src = cta_has_source(*sd, o);
+  const bool src = !p.src_magnetic && cta_has_source(*sd, o);
   const bool fast = !src && interior_E(p, o, R);
   float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
   if (!fast && live)
@@ -825,16 +828,16 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, cons
   }
 }
 
-template <int R, bool VOL, bool MULTI>
+template <int R, bool VOL, bool MULTI, bool CONV>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
-  if (p.halt && *p.halt) return;  // a convergence run that has stopped
+  if (CONV && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
   if (static_cast<int>(blockIdx.z) < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p);
     const Fields f = fields_of<MULTI>(p, rs);
-    receiver_dft<R>(p, 0, f.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+    receiver_dft<R, CONV>(p, 0, f.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
                     p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
@@ -866,6 +869,30 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
     h_quad<R, VOL, true>(p, f, v, u, h, ps, n);
   else
     h_quad<R, VOL, false>(p, f, v, u, h, ps, n);
+}
+
+// Magnetic source, after the H launch of step n: mu dH/dt = -(curl E + M)
+// (Eq. 1 in the time domain), M = amp(t_{n+1}) dir_c w / V on the (2R)^3 H
+// samples of each component's stencil, so H -= dt/mu0 M there.  One thread
+// per (transmitter, component, stencil node).
+template <int R, bool MULTI>
+__global__ void k_inject_M(const DevParams p, const int n) {
+  wait_prior_grid();
+  if (p.halt && *p.halt) return;  // a convergence run that has stopped
+  allow_next_launch();
+  constexpr int M = 2 * R, M3 = M * M * M;
+  const int t = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  if (t >= p.nsrc * 3 * M3) return;
+  const int node = t % M3, c = (t / M3) % 3, src = t / (3 * M3);
+  const SrcDev &sd = p.srcs[src];
+  if (!sd.on[c]) return;
+  const int q1 = node % M, q2 = (node / M) % M, q3 = node / (M * M);
+  const Fields f = fields_of<MULTI>(p, src);
+  float *H = c == 0 ? f.H[0] : (c == 1 ? f.H[1] : f.H[2]);
+  const size_t id = static_cast<size_t>(sd.start[c][2] + q3) * p.plane +
+                    static_cast<size_t>(sd.start[c][1] + q2) * p.pitch + (sd.start[c][0] + q1);
+  const float w = p.jw[(static_cast<size_t>(src) * 3 + c) * M3 + node];
+  H[id] = fmaf(-p.dt_mu, __ldg(p.amp + n) * w, H[id]);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -1052,6 +1079,7 @@ int check_survey(const emm_grid *g, const emm_survey *s) {
   for (int f = 0; f < s->nfreq; ++f)
     if (!(s->freqs[f] > 0) || !std::isfinite(s->freqs[f])) return EMM_EINVAL;
   if (!std::isfinite(s->moment) || !std::isfinite(s->src_az) || !std::isfinite(s->src_dip)) return EMM_EINVAL;
+  if (s->src_kind != 0 && s->src_kind != 1) return EMM_EINVAL;
   return EMM_OK;
 }
 
@@ -1080,16 +1108,16 @@ bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
          make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
-template <int R, bool VOL, bool MULTI>
+template <int R, bool VOL, bool MULTI, bool CONV>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R, VOL, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_update_E<R, VOL, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R, VOL, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_update_H<R, VOL, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   // each half-step is launched as a programmatic dependent of the one before
@@ -1098,9 +1126,11 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    e = launch_dependent(k_update_E<R, VOL, MULTI>, blocks, dim3(NT), sb, st, p, tE, n);
+    e = launch_dependent(k_update_E<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI>, blocks, dim3(NT), sb, st, p, tH, n);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
+    if (e == cudaSuccess && p.src_magnetic)
+      e = launch_dependent(k_inject_M<R, MULTI>, dim3((p.nsrc * 3 * 8 * R * R * R + 127) / 128), dim3(128), 0, st, p, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -1110,10 +1140,11 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-// Normalisation of the DTFT (Eq. 7) for a run of nsteps leapfrog steps:
-// norm[0][f] = sqrt(-i w / (2 w0)) / J'(f) for G^EE and norm[1][f] = 1 / J'(f)
-// for G^HE, J' the DTFT of the source wavelet sampled at t_{n+1/2} (the H
-// label), as complex pairs [2][nfreq][2].
+// Normalisation of the DTFT (Eq. 7) for a run of nsteps leapfrog steps, as
+// complex pairs [2][nfreq][2] for the E and the H components.  Electric
+// source: sqrt(-i w / (2 w0)) / J'(f) and 1 / J'(f), J' the DTFT of the
+// wavelet sampled at t_{n+1/2}; magnetic source: 1 / M'(f) and
+// 1 / (sqrt(-i w / (2 w0)) M'(f)), M' sampled at t_{n+1}.
 void normalisation(const emm_survey *s, double dt, int nsteps, double *norm) {
   const int nf = s->nfreq;
   const std::complex<double> I(0.0, 1.0);
@@ -1122,15 +1153,18 @@ void normalisation(const emm_survey *s, double dt, int nsteps, double *norm) {
     const std::complex<double> wp = std::complex<double>(1.0, 1.0) * std::sqrt(2.0 * M_PI * s->freqs[f] * s->omega0);
     std::complex<double> jhat = 0.0;
     for (int n = 0; n < nsteps; ++n) {
-      const double th = (n + 0.5) * dt;
-      const double u = M_PI * s->fmax * (th - t0);
+      const double ts = (n + (s->src_kind == 1 ? 1.0 : 0.5)) * dt;
+      const double u = M_PI * s->fmax * (ts - t0);
       const double a = s->moment * std::exp(-u * u);
-      jhat += std::exp(I * wp * th) * dt * a;
+      jhat += std::exp(I * wp * ts) * dt * a;
     }
     const std::complex<double> sE =
         std::sqrt(2.0 * M_PI * s->freqs[f] / (2.0 * s->omega0)) * std::exp(-I * (M_PI / 4.0));
-    const std::complex<double> nE = (jhat != 0.0) ? sE / jhat : 0.0;
-    const std::complex<double> nH = (jhat != 0.0) ? 1.0 / jhat : 0.0;
+    // electric source: G^EE = sE E'/J', G^HE = H'/J'; magnetic: G^EH = E'/M',
+    // G^HH = H'/(sE M')
+    const bool mag = s->src_kind == 1;
+    const std::complex<double> nE = (jhat != 0.0) ? (mag ? 1.0 / jhat : sE / jhat) : 0.0;
+    const std::complex<double> nH = (jhat != 0.0) ? (mag ? 1.0 / (sE * jhat) : 1.0 / jhat) : 0.0;
     norm[2 * f] = nE.real();
     norm[2 * f + 1] = nE.imag();
     norm[2 * nf + 2 * f] = nH.real();
@@ -1194,12 +1228,15 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
       sd.lo[a] = 1 << 30;
       sd.hi[a] = -1;
     }
+    // the stencils sit on the E samples of an electric dipole, on the H
+    // samples of a magnetic one
+    const int sc = s->src_kind == 1 ? 3 : 0;
     for (int c = 0; c < 3; ++c) {
       if (dir[c] == 0.0) continue;
       int start[3];
       double w[3][2 * kMaxRd];
       for (int a = 0; a < 3; ++a) {
-        st = locate_axis(g, a, kHalf[c][a], pos[a], &start[a], w[a]);
+        st = locate_axis(g, a, kHalf[c + sc][a], pos[a], &start[a], w[a]);
         if (st != EMM_OK) return st;
       }
       float *jw = reinterpret_cast<float *>(at(L.jw)) + (static_cast<size_t>(k) * 3 + c) * m3;
@@ -1210,7 +1247,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
             double vol = 1.0;
             for (int a = 0; a < 3; ++a) {
               const Axis &ax = g->ax[a];
-              vol *= kHalf[c][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+              vol *= kHalf[c + sc][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
             }
             jw[(q3 * m + q2) * m + q1] = static_cast<float>(dir[c] * w[0][q1] * w[1][q2] * w[2][q3] / vol);
           }
@@ -1244,7 +1281,8 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   const std::complex<double> I(0.0, 1.0);
   for (int n = 0; n < nt; ++n) {
     const double th = (n + 0.5) * dt, te_ = (n + 1.0) * dt;
-    const double u = M_PI * s->fmax * (th - t0);
+    // J is sampled at t_{n+1/2} (the E update's centre), M at t_{n+1} (the H update's)
+    const double u = M_PI * s->fmax * ((s->src_kind == 1 ? te_ : th) - t0);
     const double a = s->moment * std::exp(-u * u);
     amp[n] = static_cast<float>(a);
     for (int f = 0; f < nf; ++f) {
@@ -1309,6 +1347,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   p.fH32 = reinterpret_cast<const float *>(base + L.fH32);
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
+  p.src_magnetic = s->src_kind == 1 ? 1 : 0;
   if (converge) {
     p.corner = reinterpret_cast<double *>(base + L.conv);
     p.halt = reinterpret_cast<const int *>(base + L.conv + 2 * 8 * 6 * 2 * sizeof(double));
@@ -1354,27 +1393,26 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
+// The launch variants of one order: one transmitter, with or without the
+// volume DTFT; a batch; a convergence run, with or without the volume DTFT.
+template <int R>
+cudaError_t run_order(const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs, StepEvents *te) {
+  const bool vol = p.vacc != nullptr;
+  if (p.nsrc > 1) return launch_steps<R, false, true, false>(p, n0, n1, blocks, cs, te);
+  if (p.corner)
+    return vol ? launch_steps<R, true, false, true>(p, n0, n1, blocks, cs, te)
+               : launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te);
+  return vol ? launch_steps<R, true, false, false>(p, n0, n1, blocks, cs, te)
+             : launch_steps<R, false, false, false>(p, n0, n1, blocks, cs, te);
+}
+
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te) {
-  // three variants per order: one transmitter, one with the volume DTFT, a batch
-  const bool vol = p.vacc != nullptr, multi = p.nsrc > 1;
   switch (P.rd) {
-    case 1:
-      return multi ? launch_steps<1, false, true>(p, n0, n1, blocks, cs, te)
-                   : (vol ? launch_steps<1, true, false>(p, n0, n1, blocks, cs, te)
-                          : launch_steps<1, false, false>(p, n0, n1, blocks, cs, te));
-    case 2:
-      return multi ? launch_steps<2, false, true>(p, n0, n1, blocks, cs, te)
-                   : (vol ? launch_steps<2, true, false>(p, n0, n1, blocks, cs, te)
-                          : launch_steps<2, false, false>(p, n0, n1, blocks, cs, te));
-    case 3:
-      return multi ? launch_steps<3, false, true>(p, n0, n1, blocks, cs, te)
-                   : (vol ? launch_steps<3, true, false>(p, n0, n1, blocks, cs, te)
-                          : launch_steps<3, false, false>(p, n0, n1, blocks, cs, te));
-    default:
-      return multi ? launch_steps<4, false, true>(p, n0, n1, blocks, cs, te)
-                   : (vol ? launch_steps<4, true, false>(p, n0, n1, blocks, cs, te)
-                          : launch_steps<4, false, false>(p, n0, n1, blocks, cs, te));
+    case 1: return run_order<1>(p, blocks, n0, n1, cs, te);
+    case 2: return run_order<2>(p, blocks, n0, n1, cs, te);
+    case 3: return run_order<3>(p, blocks, n0, n1, cs, te);
+    default: return run_order<4>(p, blocks, n0, n1, cs, te);
   }
 }
 

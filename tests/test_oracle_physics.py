@@ -9,6 +9,11 @@ P14 Constant fields: the DTFT (Eq. 25, with the dt of Eq. 6) equals the
     H (n+1/2).
 P8  Homogeneous whole space: Green's functions (Eq. 7) against the analytic
     field of an electric dipole in a conductor, inline E_x and broadside H_z.
+P8M The same for a magnetic dipole M injected in the H update (Eq. 1 and the
+    correspondence of Eq. 5): E = m x grad g, g = e^{ikr}/(4 pi r), so a
+    z-directed m gives E_y = -m (1 - ikr) e^{ikr} / (4 pi r^2) inline and
+    E_x = +m (1 - ikr) e^{ikr} / (4 pi r^2) broadside, and
+    H_z = m (1 - ikr - k^2 r^2) e^{ikr} / (4 pi i w mu r^3) on both lines.
 P12 Mirror symmetries of an x-directed dipole at the centre of a symmetric
     non-uniform grid, all six components of the volume DTFT.
 P10 Invariance of G under omega0 -> 4 omega0 with fmax -> 2 fmax.
@@ -145,6 +150,36 @@ def test_p8_whole_space_dipole():
         assert np.abs(ph).max() < 0.25, ph
     # fields that vanish by symmetry on these lines
     assert np.abs(G[:k, 1:]).max() < 1e-6 * np.abs(G[:k, 0]).max()
+
+
+def _magnetic_dipole_whole_space(r, f, sigma):
+    """Fields of a unit z-directed magnetic dipole at distance r in the plane
+    z = 0: the E factor of m x r_hat, and H_z (Eq. 1, e^{-i w t})."""
+    om = 2 * math.pi * f
+    k = np.sqrt(1j * om * MU0 * sigma)
+    e_fac = -(1 - 1j * k * r) * np.exp(1j * k * r) / (4 * math.pi * r ** 2)
+    hz = (1 - 1j * k * r - (k * r) ** 2) * np.exp(1j * k * r) / (4 * math.pi * 1j * om * MU0 * r ** 3)
+    return e_fac, hz
+
+
+def test_p8m_whole_space_magnetic_dipole():
+    wl = W.whole_space()
+    off = np.arange(400.0, 1601.0, 200.0)
+    broad = np.stack([np.zeros_like(off), off, np.zeros_like(off)], 1)
+    inline = np.stack([off, np.zeros_like(off), np.zeros_like(off)], 1)
+    wl.rec = np.concatenate([inline, broad])
+    res = oracle.forward_workload(wl, magnetic=True, az=0.0, dip=math.pi / 2)
+    G = res["G"][:, :, 0]
+    e_fac, hz = _magnetic_dipole_whole_space(off, 0.5, 1.0)
+    k = len(off)
+    # m x r_hat: z x x = +y inline, z x y = -x broadside
+    for got, ref in ((G[:k, 1], e_fac), (G[k:, 0], -e_fac), (G[:k, 5], hz), (G[k:, 5], hz)):
+        amp = np.abs(got) / np.abs(ref) - 1
+        ph = np.degrees(np.angle(got / ref))
+        assert np.abs(amp).max() < 5e-3, amp
+        assert np.abs(ph).max() < 0.25, ph
+    # E along m and the radial E vanish on these lines
+    assert np.abs(G[:k, [0, 2]]).max() < 1e-6 * np.abs(G[:k, 1]).max()
 
 
 def _ranges(comp, axis, npa, r):
