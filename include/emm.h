@@ -147,6 +147,12 @@ typedef struct {
                            correspondence of Eq. 5 (E' = E, H' = sqrt(-i w/(2 w0)) H,
                            M' = M), G^EH = E'/M' and G^HH = H'/(sqrt(-i w/(2 w0)) M').
                            Same orientation (src_az, src_dip) and wavelet. */
+  double src_length;    /* m, >= 0.  0: a point dipole at src.  > 0: an antenna of
+                           this length along the dipole direction, centred at src,
+                           carrying the moment spread evenly over src_points
+                           sub-dipoles at the midpoints of equal segments (the
+                           paper's uniformly distributed current, Sec. 7) */
+  int src_points;       /* 1 .. 256 sub-dipoles when src_length > 0 */
 } emm_survey;
 
 /* Device workspace bytes emm_forward needs for this grid and survey
@@ -265,7 +271,7 @@ int emm_gradient_workspace_size(const emm_grid *grid, const emm_survey *survey, 
  *             the interior staggered sigma_xx, sigma_yy, sigma_zz (the pads'
  *             replicated values folded onto the edge samples).
  * Asynchronous on `stream`; errors as emm_forward (survey->volume must be 0
- * and survey->src_kind 0: EMM_EINVAL otherwise). */
+ * survey->src_kind 0 and survey->src_length 0: EMM_EINVAL otherwise). */
 int emm_gradient(const emm_grid *grid, const emm_survey *survey, const float *sigma, const double *dG,
                  int ckpt_every, void *ws, size_t ws_bytes, double *rec_out, double *grad,
                  emm_stream stream);

@@ -176,6 +176,7 @@ class _Problem(C.Structure):
         ("nvs", C.c_int), ("vs_idx", C.POINTER(C.c_longlong)),
         ("vs_G", C.POINTER(C.c_double)),
         ("magnetic", C.c_int),
+        ("src_length", C.c_double), ("src_points", C.c_int),
     ]
 
 
@@ -187,7 +188,8 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
             init_fields: Optional[np.ndarray] = None,
             want_fields: bool = False,
             vol_samples: Optional[np.ndarray] = None,
-            magnetic: bool = False) -> Dict[str, object]:
+            magnetic: bool = False, src_length: float = 0.0,
+            src_points: int = 1) -> Dict[str, object]:
     """Run the FP64 oracle.  ``sigma`` is [3][n3][n2][n1] (staggered sigma_xx,
     sigma_yy, sigma_zz).  Returns a dict with ``G`` [nrec][6][nfreq] complex,
     ``acc`` (raw DTFT), ``jhat`` [nfreq], optional ``vol`` [6][nfreq][n3][n2][n1]
@@ -195,7 +197,9 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     ``vol_samples`` (flat indices into [6][n3][n2][n1]) gives ``vol_samples_G``
     [nvs][nfreq]: the volume Green's functions at those samples only.
     ``magnetic``: the dipole is a magnetic source M (G^EH, G^HH) instead of an
-    electric current J (G^EE, G^HE)."""
+    electric current J (G^EE, G^HE).  ``src_length`` > 0: an antenna of that
+    length along the dipole direction, centred at ``src``, as ``src_points``
+    equal sub-dipoles at the midpoints of equal segments."""
     lib = _load()
     xs = [_f64(x), _f64(y), _f64(z)]
     n = [len(a) for a in xs]
@@ -222,6 +226,7 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     P.convergence = int(convergence)
     P.inject, P.pml = int(inject), int(pml)
     P.magnetic = int(magnetic)
+    P.src_length, P.src_points = float(src_length), int(src_points)
     ncell = npad[0] * npad[1] * npad[2]
     if init_fields is not None:
         init_fields = _f64(init_fields)

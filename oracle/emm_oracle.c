@@ -41,6 +41,7 @@
 
 #define ORC_MU0 (4.0e-7 * M_PI) /* reading: mu = mu0 everywhere */
 #define ORC_MAXK 8              /* 2r knots, r <= 4 */
+#define ORC_MAXPT 256           /* sub-dipoles of an antenna */
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EOUTSIDE = 3 };
 
@@ -340,6 +341,9 @@ typedef struct {
   double *vs_G;              /* [nvs][nfreq][2] Green's functions at those samples */
   int magnetic;              /* 1: the source is a magnetic dipole M, injected in
                                 the H update (Eq. 5); 0: an electric dipole J */
+  double src_length;         /* > 0: an antenna of this length (m) along the
+                                dipole direction, centred at src */
+  int src_points;            /* its sub-dipoles (used when src_length > 0) */
 } orc_problem;
 
 typedef struct {
@@ -610,34 +614,51 @@ int orc_forward(orc_problem *P)
 
   /* Source stencils (only components with a nonzero direction cosine): on
    * the E samples of an electric dipole, on the H samples of a magnetic one
-   * (sc = 3). */
+   * (sc = 3).  Reading of the antenna of finite length (Sec. 7: the current
+   * spread uniformly over its length): src_points sub-dipoles at the
+   * midpoints of equal segments along the dipole direction, each carrying
+   * 1/src_points of the moment. */
   double dir[3] = {cos(P->dip) * cos(P->az), cos(P->dip) * sin(P->az), sin(P->dip)};
-  orc_stencil sst[3];
-  double *jw[3] = {NULL, NULL, NULL};   /* dir_c * w / V per stencil node */
+  int npt = P->src_length > 0 ? P->src_points : 1;
+  if (npt < 1 || npt > ORC_MAXPT) { orc_state_free(st); return ORC_EINVAL; }
+  orc_stencil *sst = calloc((size_t)npt * 3, sizeof(orc_stencil));
+  double *jw[ORC_MAXPT * 3];            /* [point][c]: dir_c * w / (V npt) per stencil node */
+  for (int q = 0; q < npt * 3; ++q) jw[q] = NULL;
   int m = 2 * rd, sc = P->magnetic ? 3 : 0;
   if (P->inject) {
-    for (int c = 0; c < 3; ++c) {
-      if (dir[c] == 0.0) continue;
-      for (int a = 0; a < 3; ++a) {
-        st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c + sc][a], P->src[a], &sst[c].start[a], sst[c].w[a]);
-        if (st_code) { orc_state_free(st); return st_code; }
-      }
-      jw[c] = malloc(sizeof(double) * m * m * m);
-      /* reading: J_node = p s(t) w_node / V_node with V the dual-cell volume of
-       * the staggered sample: along a half-node axis X[i+1]-X[i], along an
-       * integer-node axis Xh[i]-Xh[i-1]. */
-      for (int q3 = 0; q3 < m; ++q3)
-        for (int q2 = 0; q2 < m; ++q2)
-          for (int q1 = 0; q1 < m; ++q1) {
-            int id3[3] = {sst[c].start[0] + q1, sst[c].start[1] + q2, sst[c].start[2] + q3};
-            double V = 1.0;
-            for (int a = 0; a < 3; ++a) {
-              const orc_axis *ax = &st->ax[a];
-              V *= ORC_HALF[c + sc][a] ? (ax->X[id3[a] + 1] - ax->X[id3[a]])
-                                       : (ax->Xh[id3[a]] - ax->Xh[id3[a] - 1]);
-            }
-            jw[c][(q3 * m + q2) * m + q1] = dir[c] * sst[c].w[0][q1] * sst[c].w[1][q2] * sst[c].w[2][q3] / V;
+    for (int k = 0; k < npt; ++k) {
+      double pos[3];
+      const double off = P->src_length > 0 ? (-0.5 + (k + 0.5) / npt) * P->src_length : 0.0;
+      for (int a = 0; a < 3; ++a) pos[a] = P->src[a] + off * dir[a];
+      for (int c = 0; c < 3; ++c) {
+        if (dir[c] == 0.0) continue;
+        orc_stencil *ss = &sst[k * 3 + c];
+        for (int a = 0; a < 3; ++a) {
+          st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c + sc][a], pos[a], &ss->start[a], ss->w[a]);
+          if (st_code) {
+            for (int q = 0; q < npt * 3; ++q) free(jw[q]);
+            free(sst);
+            orc_state_free(st);
+            return st_code;
           }
+        }
+        double *wk = jw[k * 3 + c] = malloc(sizeof(double) * m * m * m);
+        /* reading: J_node = p s(t) w_node / V_node with V the dual-cell volume
+         * of the staggered sample: along a half-node axis X[i+1]-X[i], along
+         * an integer-node axis Xh[i]-Xh[i-1]. */
+        for (int q3 = 0; q3 < m; ++q3)
+          for (int q2 = 0; q2 < m; ++q2)
+            for (int q1 = 0; q1 < m; ++q1) {
+              int id3[3] = {ss->start[0] + q1, ss->start[1] + q2, ss->start[2] + q3};
+              double V = 1.0;
+              for (int a = 0; a < 3; ++a) {
+                const orc_axis *ax = &st->ax[a];
+                V *= ORC_HALF[c + sc][a] ? (ax->X[id3[a] + 1] - ax->X[id3[a]])
+                                         : (ax->Xh[id3[a]] - ax->Xh[id3[a] - 1]);
+              }
+              wk[(q3 * m + q2) * m + q1] = dir[c] * ss->w[0][q1] * ss->w[1][q2] * ss->w[2][q3] / V / npt;
+            }
+      }
     }
   }
 
@@ -649,7 +670,13 @@ int orc_forward(orc_problem *P)
       for (int a = 0; a < 3; ++a) {
         st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c][a], P->rec[3 * r + a],
                                   &rst[r * 6 + c].start[a], rst[r * 6 + c].w[a]);
-        if (st_code) { free(rst); for (int c2 = 0; c2 < 3; ++c2) free(jw[c2]); orc_state_free(st); return st_code; }
+        if (st_code) {
+          free(rst);
+          for (int q = 0; q < npt * 3; ++q) free(jw[q]);
+          free(sst);
+          orc_state_free(st);
+          return st_code;
+        }
       }
 
   /* DTFT (Sec. 3.5, Eq. 25) with omega' = (1+i) sqrt(omega omega0) (Eq. 4) and,
@@ -665,7 +692,13 @@ int orc_forward(orc_problem *P)
   if (P->nvs > 0) vsa = calloc((size_t)P->nvs * nf, sizeof(double complex));
   if (P->want_volume) {
     vol = calloc(6 * (size_t)nf * nint, sizeof(double complex));
-    if (!vol) { free(rst); free(wp); free(acc); free(jh); free(rval); orc_state_free(st); return ORC_ENOMEM; }
+    if (!vol) {
+      free(rst); free(wp); free(acc); free(jh); free(rval);
+      for (int q = 0; q < npt * 3; ++q) free(jw[q]);
+      free(sst);
+      orc_state_free(st);
+      return ORC_ENOMEM;
+    }
   }
   /* 8 corners of the interior cube, lowest frequency, all 6 components (A18). */
   int flo = 0;
@@ -681,13 +714,14 @@ int orc_forward(orc_problem *P)
      * t_{n+1} (the H update's centre) */
     double amp = P->moment * orc_wavelet(P->magnetic ? tE : tJ, P->fmax);
     if (P->inject && !P->magnetic) {
-      for (int c = 0; c < 3; ++c) {
-        if (!jw[c]) continue;
+      for (int q = 0; q < npt * 3; ++q) {
+        if (!jw[q]) continue;
+        const int c = q % 3;
         for (int q3 = 0; q3 < m; ++q3)
           for (int q2 = 0; q2 < m; ++q2)
             for (int q1 = 0; q1 < m; ++q1)
-              st->C[c][IDX(st, sst[c].start[2] + q3, sst[c].start[1] + q2, sst[c].start[0] + q1)]
-                  -= amp * jw[c][(q3 * m + q2) * m + q1];
+              st->C[c][IDX(st, sst[q].start[2] + q3, sst[q].start[1] + q2, sst[q].start[0] + q1)]
+                  -= amp * jw[q][(q3 * m + q2) * m + q1];
       }
     }
     orc_update_E(st);
@@ -734,13 +768,14 @@ int orc_forward(orc_problem *P)
     orc_curl_E(st, P->pml);
     /* magnetic source: mu dH/dt = -(curl E + M) (Eq. 5, time domain) */
     if (P->inject && P->magnetic) {
-      for (int c = 0; c < 3; ++c) {
-        if (!jw[c]) continue;
+      for (int q = 0; q < npt * 3; ++q) {
+        if (!jw[q]) continue;
+        const int c = q % 3;
         for (int q3 = 0; q3 < m; ++q3)
           for (int q2 = 0; q2 < m; ++q2)
             for (int q1 = 0; q1 < m; ++q1)
-              st->C[c][IDX(st, sst[c].start[2] + q3, sst[c].start[1] + q2, sst[c].start[0] + q1)]
-                  += amp * jw[c][(q3 * m + q2) * m + q1];
+              st->C[c][IDX(st, sst[q].start[2] + q3, sst[q].start[1] + q2, sst[q].start[0] + q1)]
+                  += amp * jw[q][(q3 * m + q2) * m + q1];
       }
     }
     orc_update_H(st, dt);
@@ -797,7 +832,8 @@ int orc_forward(orc_problem *P)
   if (P->info) { P->info[0] = dt; P->info[1] = vmax; P->info[2] = nt_run; P->info[3] = eta; }
 
   free(vsa); free(vol); free(acc); free(jh); free(wp); free(rst); free(rval);
-  for (int c = 0; c < 3; ++c) free(jw[c]);
+  for (int q = 0; q < npt * 3; ++q) free(jw[q]);
+  free(sst);
   orc_state_free(st);
   return ORC_OK;
 }
@@ -943,7 +979,7 @@ int orc_vjp(orc_problem *P, const double *v, double *grad, int ckpt_every)
   memset(st, 0, sizeof(S));
   int rd = P->rd, nb = P->nb, ne = P->ne, code = ORC_OK;
   if (rd < 1 || rd > 4 || nb < rd || ne < 0 || P->nt < 0 || P->omega0 <= 0 || !(P->sigma_min > 0) ||
-      ckpt_every < 1 || !v || !grad || P->magnetic)
+      ckpt_every < 1 || !v || !grad || P->magnetic || P->src_length > 0)
     return ORC_EINVAL;
   st->rd = rd;
   for (int a = 0; a < 3; ++a) {

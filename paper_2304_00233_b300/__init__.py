@@ -67,7 +67,8 @@ class _Survey(C.Structure):
                 ("dt", C.c_double), ("nt", C.c_int), ("src", C.c_double * 3),
                 ("src_az", C.c_double), ("src_dip", C.c_double), ("moment", C.c_double),
                 ("nrec", C.c_int), ("rec", _D), ("nfreq", C.c_int), ("freqs", _D),
-                ("volume", C.c_int), ("src_kind", C.c_int)]
+                ("volume", C.c_int), ("src_kind", C.c_int),
+                ("src_length", C.c_double), ("src_points", C.c_int)]
 
 
 _lib = None
@@ -219,6 +220,8 @@ class Survey:
     moment: float = 1.0
     volume: bool = False
     src_kind: int = 0          # 0: electric dipole J; 1: magnetic dipole M
+    src_length: float = 0.0    # > 0: an antenna of this length (m), as src_points sub-dipoles
+    src_points: int = 1
 
     def _c(self) -> Tuple[_Survey, list]:
         rec = _f64(np.zeros((0, 3)) if self.rec is None else self.rec).reshape(-1, 3)
@@ -234,6 +237,7 @@ class Survey:
         s.freqs = _dp(freqs) if len(freqs) else None
         s.volume = int(bool(self.volume))
         s.src_kind = int(self.src_kind)
+        s.src_length, s.src_points = float(self.src_length), int(self.src_points)
         return s, [rec, freqs]   # the arrays must outlive every use of the struct
 
     @property

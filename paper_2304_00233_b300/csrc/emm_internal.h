@@ -48,10 +48,16 @@ void cpml_axis(const emm_grid *g, int axis, double vmax, double fmax, double dt,
 
 // Source of one transmitter of a batch: which E components it drives, the
 // first node of each (2rd)^3 stencil, and their bounding box.
+// Source stencil of one transmitter: per component c, weights on the box of
+// samples start[c] .. start[c] + box[c] - 1 (x fastest), at float offset
+// woff[c] of the transmitter's block of jw.  A point dipole has (2rd)^3
+// boxes; an antenna the union of its sub-dipoles' boxes.  lo/hi: the
+// bounding box of all components.
 struct SrcDev {
   int on[3];
   int start[3][3];
   int any, lo[3], hi[3];
+  int box[3][3], woff[3];
 };
 
 // Everything the kernels read, packed by value into the launch parameters.
@@ -73,6 +79,9 @@ struct DevParams {
   const int *halt;
   int conv_f;       // index of the lowest frequency
   int src_magnetic; // 1: the source is a magnetic dipole, injected in the H update
+  int src_fused;    // 1: the E kernel injects J itself (an electric point dipole);
+                    // otherwise k_inject does, after the E or the H launch
+  size_t jstride;   // floats of jw per transmitter
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
@@ -125,6 +134,9 @@ struct Layout {
 };
 
 Layout plan(const emm_grid *g, const emm_survey *s, int nsrc = 1);
+// Floats of source weights per transmitter (three component boxes, each at
+// most the bound of an antenna of survey->src_length on this grid).
+size_t source_stride(const emm_grid *g, const emm_survey *s);
 int check_survey(const emm_grid *g, const emm_survey *s);
 
 // Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.

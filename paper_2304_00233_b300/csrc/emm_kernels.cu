@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   }
   const SrcDev *sd = p.srcs + o.src;
   const float *jw = p.jw + static_cast<size_t>(o.src) * 3 * (2 * R) * (2 * R) * (2 * R);
-  const bool src = !p.src_magnetic && cta_has_source(*sd, o);
+  const bool src = p.src_fused && cta_has_source(*sd, o);
   const bool fast = !src && interior_E(p, o, R);
   float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
   if (!fast && live)
@@ -871,28 +871,38 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
     h_quad<R, VOL, false>(p, f, v, u, h, ps, n);
 }
 
-// Magnetic source, after the H launch of step n: mu dH/dt = -(curl E + M)
-// (Eq. 1 in the time domain), M = amp(t_{n+1}) dir_c w / V on the (2R)^3 H
-// samples of each component's stencil, so H -= dt/mu0 M there.  One thread
-// per (transmitter, component, stencil node).
-template <int R, bool MULTI>
-__global__ void k_inject_M(const DevParams p, const int n) {
+// Sources the stencil kernels do not inject themselves, one thread per
+// (transmitter, component, box sample):
+//   FIELD 0, after the E launch of step n: an electric antenna,
+//     E -= dt/eps J with J = amp(t_{n+1/2}) dir_c w / V;
+//   FIELD 1, after the H launch: a magnetic dipole or antenna,
+//     mu dH/dt = -(curl E + M) (Eq. 1 in the time domain), so
+//     H -= dt/mu0 M with M = amp(t_{n+1}) dir_c w / V.
+template <bool MULTI, int FIELD>
+__global__ void k_inject(const DevParams p, const int n) {
   wait_prior_grid();
   if (p.halt && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
-  constexpr int M = 2 * R, M3 = M * M * M;
-  const int t = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
-  if (t >= p.nsrc * 3 * M3) return;
-  const int node = t % M3, c = (t / M3) % 3, src = t / (3 * M3);
+  const size_t per = p.jstride, cv = per / 3;
+  const size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= static_cast<size_t>(p.nsrc) * per) return;
+  const int src = static_cast<int>(t / per), c = static_cast<int>((t % per) / cv);
+  const int node = static_cast<int>(t % cv);
   const SrcDev &sd = p.srcs[src];
-  if (!sd.on[c]) return;
-  const int q1 = node % M, q2 = (node / M) % M, q3 = node / (M * M);
+  const int bx = sd.box[c][0], by = sd.box[c][1], bz = sd.box[c][2];
+  if (!sd.on[c] || node >= bx * by * bz) return;
+  const int q1 = node % bx, q2 = (node / bx) % by, q3 = node / (bx * by);
   const Fields f = fields_of<MULTI>(p, src);
-  float *H = c == 0 ? f.H[0] : (c == 1 ? f.H[1] : f.H[2]);
   const size_t id = static_cast<size_t>(sd.start[c][2] + q3) * p.plane +
                     static_cast<size_t>(sd.start[c][1] + q2) * p.pitch + (sd.start[c][0] + q1);
-  const float w = p.jw[(static_cast<size_t>(src) * 3 + c) * M3 + node];
-  H[id] = fmaf(-p.dt_mu, __ldg(p.amp + n) * w, H[id]);
+  const float a = __ldg(p.amp + n) * p.jw[static_cast<size_t>(src) * per + sd.woff[c] + node];
+  if (FIELD == 0) {
+    float *E = c == 0 ? f.E[0] : (c == 1 ? f.E[1] : f.E[2]);
+    E[id] = fmaf(-p.ie[c][id], a, E[id]);
+  } else {
+    float *H = c == 0 ? f.H[0] : (c == 1 ? f.H[1] : f.H[2]);
+    H[id] = fmaf(-p.dt_mu, a, H[id]);
+  }
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -1027,6 +1037,31 @@ size_t psi_elems(const emm_grid *g, int axis, int half) {
 }
 
 
+// Per axis, an antenna of length L along dir spans at most
+// ceil(L |dir_a| / h_min) + 1 sample intervals between its sub-dipoles'
+// stencil starts, h_min the smallest spacing of the axis (nodes or half
+// nodes); each stencil adds 2rd samples.
+static void source_box_bound(const emm_grid *g, const emm_survey *s, int ext[3]) {
+  const double dir[3] = {std::cos(s->src_dip) * std::cos(s->src_az), std::cos(s->src_dip) * std::sin(s->src_az),
+                         std::sin(s->src_dip)};
+  const int m = 2 * g->rd;
+  for (int a = 0; a < 3; ++a) {
+    ext[a] = m;
+    if (!(s->src_length > 0)) continue;
+    const Axis &ax = g->ax[a];
+    double h = 1e300;
+    for (size_t i = 0; i + 1 < ax.X.size(); ++i) h = std::min(h, ax.X[i + 1] - ax.X[i]);
+    for (size_t i = 0; i + 1 < ax.Xh.size(); ++i) h = std::min(h, ax.Xh[i + 1] - ax.Xh[i]);
+    ext[a] = m + static_cast<int>(std::ceil(s->src_length * std::fabs(dir[a]) / h)) + 2;
+  }
+}
+
+size_t source_stride(const emm_grid *g, const emm_survey *s) {
+  int ext[3];
+  source_box_bound(g, s, ext);
+  return 3 * static_cast<size_t>(ext[0]) * ext[1] * ext[2];
+}
+
 Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   Layout L{};
   size_t off = 0;
@@ -1059,7 +1094,7 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   for (int a = 0; a < 3; ++a) L.cp[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) L.pml[a] = take(8 * static_cast<size_t>(g->nb) * 4);
   L.srcs = take(static_cast<size_t>(nsrc) * sizeof(SrcDev));
-  L.jw = take(static_cast<size_t>(nsrc) * 3 * m * m * m * 4);
+  L.jw = take(static_cast<size_t>(nsrc) * source_stride(g, s) * 4);
   L.amp = take(nt * 4);
   L.rec_start = take(nrec * 18 * sizeof(int));
   L.rec_w = take(nrec * 18 * m * sizeof(double));
@@ -1080,6 +1115,9 @@ int check_survey(const emm_grid *g, const emm_survey *s) {
     if (!(s->freqs[f] > 0) || !std::isfinite(s->freqs[f])) return EMM_EINVAL;
   if (!std::isfinite(s->moment) || !std::isfinite(s->src_az) || !std::isfinite(s->src_dip)) return EMM_EINVAL;
   if (s->src_kind != 0 && s->src_kind != 1) return EMM_EINVAL;
+  if (!(s->src_length >= 0) || !std::isfinite(s->src_length) ||
+      (s->src_length > 0 && (s->src_points < 1 || s->src_points > 256)))
+    return EMM_EINVAL;
   return EMM_OK;
 }
 
@@ -1121,16 +1159,18 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   // each half-step is launched as a programmatic dependent of the one before
+  const dim3 inj(static_cast<unsigned>((p.nsrc * p.jstride + 127) / 128));  // k_inject threads
   size_t used = 0;
   if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
     e = launch_dependent(k_update_E<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
+    if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
+      e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, p, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
     if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
-    if (e == cudaSuccess && p.src_magnetic)
-      e = launch_dependent(k_inject_M<R, MULTI>, dim3((p.nsrc * 3 * 8 * R * R * R + 127) / 128), dim3(128), 0, st, p, n);
+    if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, p, n);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -1217,7 +1257,6 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
                          std::sin(s->src_dip)};
   DevParams p{};
   SrcDev *srcs = reinterpret_cast<SrcDev *>(at(L.srcs));
-  const size_t m3 = static_cast<size_t>(m) * m * m;
   for (int k = 0; k < nsrc; ++k) {
     const double *pos = src_pos ? src_pos + 3 * k : s->src;
     for (int a = 0; a < 3; ++a)
@@ -1229,34 +1268,59 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
       sd.hi[a] = -1;
     }
     // the stencils sit on the E samples of an electric dipole, on the H
-    // samples of a magnetic one
+    // samples of a magnetic one; an antenna is npt sub-dipoles at the
+    // midpoints of equal segments along dir, each with 1/npt of the moment,
+    // whose weights are summed on the union of their boxes
     const int sc = s->src_kind == 1 ? 3 : 0;
+    const int npt = s->src_length > 0 ? s->src_points : 1;
+    int ext[3];
+    source_box_bound(g, s, ext);
+    const size_t jstride = source_stride(g, s), cv = jstride / 3;
     for (int c = 0; c < 3; ++c) {
       if (dir[c] == 0.0) continue;
-      int start[3];
-      double w[3][2 * kMaxRd];
-      for (int a = 0; a < 3; ++a) {
-        st = locate_axis(g, a, kHalf[c + sc][a], pos[a], &start[a], w[a]);
-        if (st != EMM_OK) return st;
+      std::vector<int> starts(static_cast<size_t>(npt) * 3);
+      std::vector<double> ws(static_cast<size_t>(npt) * 3 * m);
+      int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+      for (int q = 0; q < npt; ++q) {
+        const double off = s->src_length > 0 ? (-0.5 + (q + 0.5) / npt) * s->src_length : 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double pa = pos[a] + off * dir[a];
+          st = locate_axis(g, a, kHalf[c + sc][a], pa, &starts[q * 3 + a], &ws[(static_cast<size_t>(q) * 3 + a) * m]);
+          if (st != EMM_OK) return st;
+          lo[a] = std::min(lo[a], starts[q * 3 + a]);
+          hi[a] = std::max(hi[a], starts[q * 3 + a] + m - 1);
+        }
       }
-      float *jw = reinterpret_cast<float *>(at(L.jw)) + (static_cast<size_t>(k) * 3 + c) * m3;
-      for (int q3 = 0; q3 < m; ++q3)
-        for (int q2 = 0; q2 < m; ++q2)
-          for (int q1 = 0; q1 < m; ++q1) {
-            const int idx[3] = {start[0] + q1, start[1] + q2, start[2] + q3};
-            double vol = 1.0;
-            for (int a = 0; a < 3; ++a) {
-              const Axis &ax = g->ax[a];
-              vol *= kHalf[c + sc][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+      int box[3];
+      for (int a = 0; a < 3; ++a) {
+        box[a] = hi[a] - lo[a] + 1;
+        if (box[a] > ext[a]) return EMM_EINVAL;
+      }
+      std::vector<double> acc(static_cast<size_t>(box[0]) * box[1] * box[2], 0.0);
+      for (int q = 0; q < npt; ++q)
+        for (int q3 = 0; q3 < m; ++q3)
+          for (int q2 = 0; q2 < m; ++q2)
+            for (int q1 = 0; q1 < m; ++q1) {
+              const int idx[3] = {starts[q * 3] + q1, starts[q * 3 + 1] + q2, starts[q * 3 + 2] + q3};
+              double vol = 1.0;
+              for (int a = 0; a < 3; ++a) {
+                const Axis &ax = g->ax[a];
+                vol *= kHalf[c + sc][a] ? (ax.X[idx[a] + 1] - ax.X[idx[a]]) : (ax.Xh[idx[a]] - ax.Xh[idx[a] - 1]);
+              }
+              const double *w = &ws[static_cast<size_t>(q) * 3 * m];
+              acc[(static_cast<size_t>(idx[2] - lo[2]) * box[1] + (idx[1] - lo[1])) * box[0] + (idx[0] - lo[0])] +=
+                  dir[c] * w[q1] * w[m + q2] * w[2 * m + q3] / vol / npt;
             }
-            jw[(q3 * m + q2) * m + q1] = static_cast<float>(dir[c] * w[0][q1] * w[1][q2] * w[2][q3] / vol);
-          }
+      float *jw = reinterpret_cast<float *>(at(L.jw)) + static_cast<size_t>(k) * jstride + c * cv;
+      for (size_t q = 0; q < acc.size(); ++q) jw[q] = static_cast<float>(acc[q]);
       sd.on[c] = 1;
       sd.any = 1;
+      sd.woff[c] = static_cast<int>(c * cv);
       for (int a = 0; a < 3; ++a) {
-        sd.start[c][a] = start[a];
-        sd.lo[a] = std::min(sd.lo[a], start[a]);
-        sd.hi[a] = std::max(sd.hi[a], start[a] + m - 1);
+        sd.start[c][a] = lo[a];
+        sd.box[c][a] = box[a];
+        sd.lo[a] = std::min(sd.lo[a], lo[a]);
+        sd.hi[a] = std::max(sd.hi[a], hi[a]);
       }
     }
   }
@@ -1348,6 +1412,8 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   p.vacc = s->volume ? reinterpret_cast<float4 *>(base + L.vacc) : nullptr;
   p.status = reinterpret_cast<int *>(base + L.status);
   p.src_magnetic = s->src_kind == 1 ? 1 : 0;
+  p.src_fused = (s->src_kind == 0 && !(s->src_length > 0)) ? 1 : 0;
+  p.jstride = source_stride(g, s);
   if (converge) {
     p.corner = reinterpret_cast<double *>(base + L.conv);
     p.halt = reinterpret_cast<const int *>(base + L.conv + 2 * 8 * 6 * 2 * sizeof(double));

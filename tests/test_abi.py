@@ -62,8 +62,21 @@ def test_survey_errors_before_any_device_call():
     good = emm.Survey(omega0=1.0, fmax=1.0, sigma_min=1.0, nt=10, src=(55, 55, 55),
                       rec=np.array([[40.0, 50.0, 60.0]]), freqs=[1.0])
     assert emm.workspace_size(g, good) > 0
-    for bad in (dict(omega0=0.0), dict(fmax=-1.0), dict(sigma_min=0.0), dict(nt=-1), dict(freqs=[])):
+    for bad in (dict(omega0=0.0), dict(fmax=-1.0), dict(sigma_min=0.0), dict(nt=-1), dict(freqs=[]),
+                dict(src_kind=2), dict(src_length=-1.0), dict(src_length=100.0, src_points=0),
+                dict(src_length=100.0, src_points=257)):
         s = emm.Survey(**{**good.__dict__, **bad})
         with pytest.raises(emm.EmmError) as e:
             emm.workspace_size(g, s)
         assert e.value.code == emm.EMM_EINVAL
+
+
+def test_antenna_workspace_holds_the_union_boxes():
+    # an antenna's weights need more room than a point dipole's (2rd)^3 boxes
+    x = np.arange(40.0) * 10
+    g = emm.make_grid(x, x, x, rd=2, nb=4, ne=3)
+    point = emm.Survey(omega0=1.0, fmax=1.0, sigma_min=1.0, nt=10, src=(195, 195, 195),
+                       rec=np.array([[150.0, 150.0, 150.0]]), freqs=[1.0])
+    ant = emm.Survey(**{**point.__dict__, "src_length": 60.0, "src_points": 6})
+    assert emm.workspace_size(g, ant) > emm.workspace_size(g, point)
+

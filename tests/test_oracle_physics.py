@@ -290,3 +290,22 @@ def test_a10_edge_samples_stay_zero():
             assert np.all(a[:lo] == 0) and np.all(a[hi + 1:] == 0), (comp, axis)
             assert np.abs(a[lo:hi + 1]).max() > 0
     assert np.abs(F).max() > 0
+
+
+def test_extended_antenna_is_the_mean_of_its_sub_dipoles():
+    """An antenna of length L as N sub-dipoles (the current spread uniformly
+    over its length): by linearity its G equals the mean of the N point-dipole
+    G at the segment midpoints, each run alone (same wavelet and moment, so
+    the same normalisation)."""
+    wl = W.small_case(rd=2, nt=120, volume=False, nfreq=2)
+    L, N = 150.0, 3
+    d = np.array([math.cos(wl.src_dip) * math.cos(wl.src_az), math.cos(wl.src_dip) * math.sin(wl.src_az),
+                  math.sin(wl.src_dip)])
+    for magnetic in (False, True):
+        ext = oracle.forward_workload(wl, src_length=L, src_points=N, magnetic=magnetic)["G"]
+        pts = [wl.src + (-0.5 + (k + 0.5) / N) * L * d for k in range(N)]
+        mean = sum(oracle.forward_workload(wl, src=tuple(p), magnetic=magnetic)["G"] for p in pts) / N
+        np.testing.assert_allclose(ext, mean, rtol=0, atol=1e-12 * np.abs(mean).max())
+        # and the antenna is not the point dipole at its centre
+        point = oracle.forward_workload(wl, magnetic=magnetic)["G"]
+        assert np.abs(ext - point).max() > 1e-6 * np.abs(point).max()
