@@ -177,6 +177,7 @@ class _Problem(C.Structure):
         ("vs_G", C.POINTER(C.c_double)),
         ("magnetic", C.c_int),
         ("src_length", C.c_double), ("src_points", C.c_int),
+        ("airwave", C.c_int),
     ]
 
 
@@ -189,7 +190,7 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
             want_fields: bool = False,
             vol_samples: Optional[np.ndarray] = None,
             magnetic: bool = False, src_length: float = 0.0,
-            src_points: int = 1) -> Dict[str, object]:
+            src_points: int = 1, airwave: bool = False) -> Dict[str, object]:
     """Run the FP64 oracle.  ``sigma`` is [3][n3][n2][n1] (staggered sigma_xx,
     sigma_yy, sigma_zz).  Returns a dict with ``G`` [nrec][6][nfreq] complex,
     ``acc`` (raw DTFT), ``jhat`` [nfreq], optional ``vol`` [6][nfreq][n3][n2][n1]
@@ -199,7 +200,8 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     ``magnetic``: the dipole is a magnetic source M (G^EH, G^HH) instead of an
     electric current J (G^EE, G^HE).  ``src_length`` > 0: an antenna of that
     length along the dipole direction, centred at ``src``, as ``src_points``
-    equal sub-dipoles at the midpoints of equal segments."""
+    equal sub-dipoles at the midpoints of equal segments.  ``airwave``: air
+    above the top interior node (needs uniform x and y)."""
     lib = _load()
     xs = [_f64(x), _f64(y), _f64(z)]
     n = [len(a) for a in xs]
@@ -227,6 +229,7 @@ def forward(x, y, z, sigma, *, rd: int, nb: int, ne: int, omega0: float,
     P.inject, P.pml = int(inject), int(pml)
     P.magnetic = int(magnetic)
     P.src_length, P.src_points = float(src_length), int(src_points)
+    P.airwave = int(airwave)
     ncell = npad[0] * npad[1] * npad[2]
     if init_fields is not None:
         init_fields = _f64(init_fields)
@@ -315,3 +318,23 @@ def forward_workload(w, **kw) -> Dict[str, object]:
         probe = forward(w.x, w.y, w.z, w.sigma, nt=0, **{**args, "volume": False, "rec": None})
         nt = int(np.ceil(w.t_max / probe["dt"]))
     return forward(w.x, w.y, w.z, w.sigma, nt=nt, **args)
+
+
+def air_extrapolate(plane, dx: float, dy: float, heights, kind: int) -> np.ndarray:
+    """The oracle's air extrapolation of one interface plane [ny][nx] (the top
+    boundary of Sec. 3.3): kind 0 gives the same component at each height
+    above the interface, [nh][ny][nx]; kind 1 takes H_z and gives H_x, H_y
+    at their own x-y positions, [nh][2][ny][nx]."""
+    lib = _load()
+    plane = _f64(plane)
+    ny, nx = plane.shape
+    h = _f64(heights)
+    nh = len(h)
+    out = np.zeros((nh, 2, ny, nx) if kind == 1 else (nh, ny, nx))
+    fn = lib.orc_air_extrapolate
+    fn.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), C.c_int,
+                   C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double)]
+    fn.restype = C.c_int
+    _check(fn(nx, ny, dx, dy, _dp(plane), nh, _dp(h), int(kind), _dp(out)), "air_extrapolate")
+    return out
+

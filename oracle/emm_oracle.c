@@ -344,6 +344,8 @@ typedef struct {
   double src_length;         /* > 0: an antenna of this length (m) along the
                                 dipole direction, centred at src */
   int src_points;            /* its sub-dipoles (used when src_length > 0) */
+  int airwave;               /* 1: the top interior node is an interface with
+                                air (Sec. 3.3), no CPML on the top face */
 } orc_problem;
 
 typedef struct {
@@ -555,6 +557,127 @@ static void orc_state_free(orc_state *st)
   for (int c = 0; c < 12; ++c) free(st->psi[c]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Top boundary with air (Sec. 3.3)                                          */
+/* ------------------------------------------------------------------------ */
+/* Reading.  The top interior z node k_s = nb + ne is the interface; above it
+ * the air has sigma = 0 and no source, so curl H = 0 and div H = 0 (H =
+ * -grad phi, phi harmonic) and every component of E is harmonic (Delta E =
+ * 0).  A harmonic field that vanishes far above the interface is, for each
+ * horizontal wavenumber k = (kx, ky), f(k, z) = f(k, z_s) e^{-|k| h} at the
+ * height h = z_s - z above it (z down).  With phi = -H_z / |k| at z_s:
+ *   H_x(k) = i kx / |k| H_z(k),   H_y(k) = i ky / |k| H_z(k)
+ * (the relations of Sec. 3.3), times e^{-i kx dx / 2} (e^{-i ky dy / 2}) to
+ * move from H_z's half x (y) position to H_x's (H_y's) integer one; the
+ * k = 0 term of H_x, H_y is 0.  The transform is the 2-D DFT of the whole
+ * padded x-y plane (uniform spacing dx, dy, as the FFT of the paper needs),
+ * kx = 2 pi p / (nx dx) with p taken in (-nx/2, nx/2]; the extrapolated
+ * values are the real part of the inverse. */
+static double orc_wavenumber(int p, int n, double d)
+{
+  return 2.0 * M_PI * (p <= n / 2 ? p : p - n) / (n * d);
+}
+
+/* out[q][p] = sum_{j,i} in[j][i] e^{sgn 2 pi i (p i / nx + q j / ny)}, with
+ * the twiddles e^{sgn 2 pi i m / n} tabulated for m = 0 .. n-1 */
+static void orc_dft2(int nx, int ny, const double complex *in, double complex *out, int sgn)
+{
+  double complex *t = malloc(sizeof(double complex) * (size_t)nx * ny);
+  double complex *wx = malloc(sizeof(double complex) * nx), *wy = malloc(sizeof(double complex) * ny);
+  for (int m = 0; m < nx; ++m) wx[m] = cexp(sgn * 2.0 * M_PI * I * m / nx);
+  for (int m = 0; m < ny; ++m) wy[m] = cexp(sgn * 2.0 * M_PI * I * m / ny);
+  for (int j = 0; j < ny; ++j)
+    for (int p = 0; p < nx; ++p) {
+      double complex s = 0;
+      for (int i = 0; i < nx; ++i) s += in[(size_t)j * nx + i] * wx[(long)p * i % nx];
+      t[(size_t)j * nx + p] = s;
+    }
+  for (int q = 0; q < ny; ++q)
+    for (int p = 0; p < nx; ++p) {
+      double complex s = 0;
+      for (int j = 0; j < ny; ++j) s += t[(size_t)j * nx + p] * wy[(long)q * j % ny];
+      out[(size_t)q * nx + p] = s;
+    }
+  free(t); free(wx); free(wy);
+}
+
+/* The air extrapolation of one interface plane in [ny][nx].  kind 0: out[r]
+ * = the same E component at the height h[r]; kind 1 (in = H_z): out[2r] =
+ * H_x and out[2r+1] = H_y at the height h[r], at their own x-y positions.
+ * out holds nh (kind 0) or 2 nh (kind 1) planes [ny][nx]. */
+int orc_air_extrapolate(int nx, int ny, double dx, double dy, const double *in, int nh, const double *h,
+                        int kind, double *out)
+{
+  if (nx < 1 || ny < 1 || !(dx > 0) || !(dy > 0) || nh < 0 || (kind != 0 && kind != 1)) return ORC_EINVAL;
+  size_t n = (size_t)nx * ny;
+  double complex *a = malloc(sizeof(double complex) * n), *F = malloc(sizeof(double complex) * n);
+  double complex *G = malloc(sizeof(double complex) * n), *g = malloc(sizeof(double complex) * n);
+  for (size_t q = 0; q < n; ++q) a[q] = in[q];
+  orc_dft2(nx, ny, a, F, -1);
+  for (int r = 0; r < nh; ++r)
+    for (int o = 0; o < (kind ? 2 : 1); ++o) {
+      for (int q = 0; q < ny; ++q)
+        for (int p = 0; p < nx; ++p) {
+          double kx = orc_wavenumber(p, nx, dx), ky = orc_wavenumber(q, ny, dy), kk = sqrt(kx * kx + ky * ky);
+          double complex f = exp(-kk * h[r]);
+          if (kind == 1)
+            f *= kk > 0 ? (o == 0 ? I * kx / kk * cexp(-I * kx * dx / 2) : I * ky / kk * cexp(-I * ky * dy / 2)) : 0.0;
+          G[(size_t)q * nx + p] = F[(size_t)q * nx + p] * f;
+        }
+      orc_dft2(nx, ny, G, g, +1);
+      double *dst = out + (size_t)(kind ? 2 * r + o : r) * n;
+      for (size_t q = 0; q < n; ++q) dst[q] = creal(g[q]) / (double)n;
+    }
+  free(a); free(F); free(G); free(g);
+  return ORC_OK;
+}
+
+/* After the E update: E_x, E_y on the rd - 1 integer rows above the interface. */
+static void orc_airwave_E(orc_state *st)
+{
+  const orc_axis *az = &st->ax[2];
+  int nx = st->np[0], ny = st->np[1], ks = az->nbe, nh = st->rd - 1;
+  if (nh < 1) return;
+  double h[ORC_MAXK], dx = st->ax[0].X[1] - st->ax[0].X[0], dy = st->ax[1].X[1] - st->ax[1].X[0];
+  for (int r = 0; r < nh; ++r) h[r] = az->X[ks] - az->X[ks - 1 - r];
+  size_t n = (size_t)nx * ny;
+  double *in = malloc(sizeof(double) * n), *out = malloc(sizeof(double) * n * nh);
+  for (int c = 0; c < 2; ++c) {
+    memcpy(in, st->F[c] + IDX(st, ks, 0, 0), sizeof(double) * n);
+    orc_air_extrapolate(nx, ny, dx, dy, in, nh, h, 0, out);
+    for (int r = 0; r < nh; ++r) memcpy(st->F[c] + IDX(st, ks - 1 - r, 0, 0), out + (size_t)r * n, sizeof(double) * n);
+  }
+  free(in); free(out);
+}
+
+/* After the H update: H_x, H_y on the rd half rows above the interface (half
+ * row k sits at Xh[k] = z_{k+1/2}), from H_z on the interface row. */
+static void orc_airwave_H(orc_state *st)
+{
+  const orc_axis *az = &st->ax[2];
+  int nx = st->np[0], ny = st->np[1], ks = az->nbe, nh = st->rd;
+  double h[ORC_MAXK], dx = st->ax[0].X[1] - st->ax[0].X[0], dy = st->ax[1].X[1] - st->ax[1].X[0];
+  for (int r = 0; r < nh; ++r) h[r] = az->X[ks] - az->Xh[ks - 1 - r];
+  size_t n = (size_t)nx * ny;
+  double *in = malloc(sizeof(double) * n), *out = malloc(sizeof(double) * n * 2 * nh);
+  memcpy(in, st->F[5] + IDX(st, ks, 0, 0), sizeof(double) * n);
+  orc_air_extrapolate(nx, ny, dx, dy, in, nh, h, 1, out);
+  for (int r = 0; r < nh; ++r) {
+    memcpy(st->F[3] + IDX(st, ks - 1 - r, 0, 0), out + (size_t)(2 * r) * n, sizeof(double) * n);
+    memcpy(st->F[4] + IDX(st, ks - 1 - r, 0, 0), out + (size_t)(2 * r + 1) * n, sizeof(double) * n);
+  }
+  free(in); free(out);
+}
+
+/* Is the padded axis uniformly spaced (relative tolerance 1e-9)? */
+static int orc_axis_uniform(const orc_axis *ax)
+{
+  double d = ax->X[1] - ax->X[0];
+  for (int i = 1; i <= ax->npad; ++i)
+    if (fabs((ax->X[i] - ax->X[i - 1]) - d) > 1e-9 * d) return 0;
+  return 1;
+}
+
 int orc_forward(orc_problem *P)
 {
   orc_state S, *st = &S;
@@ -585,6 +708,14 @@ int orc_forward(orc_problem *P)
   double eta = 0.5 * vmax * sqrt(d2);
   double dt = (P->dt > 0) ? P->dt : 0.99 / eta;   /* Sec. 3.2: dt = 0.99 / eta */
   for (int a = 0; a < 3; ++a) orc_axis_cpml(&st->ax[a], vmax, P->fmax, dt);
+  if (P->airwave) {
+    /* the FFT of Sec. 3.3 needs uniform x and y; no CPML on the top face */
+    if (!orc_axis_uniform(&st->ax[0]) || !orc_axis_uniform(&st->ax[1])) { orc_state_free(st); return ORC_EINVAL; }
+    for (int s = 0; s < nb; ++s) {
+      st->ax[2].pa_i[s] = st->ax[2].pb_i[s] = 0.0;
+      st->ax[2].pa_h[s] = st->ax[2].pb_h[s] = 0.0;
+    }
+  }
 
   for (int c = 0; c < 6; ++c) st->F[c] = calloc(st->ncell, sizeof(double));
   for (int c = 0; c < 3; ++c) {
@@ -635,6 +766,8 @@ int orc_forward(orc_problem *P)
         orc_stencil *ss = &sst[k * 3 + c];
         for (int a = 0; a < 3; ++a) {
           st_code = orc_locate_axis(&st->ax[a], ORC_HALF[c + sc][a], pos[a], &ss->start[a], ss->w[a]);
+          /* with air above the model, the source stencil stays below the interface */
+          if (!st_code && P->airwave && a == 2 && ss->start[2] < st->ax[2].nbe) st_code = ORC_EOUTSIDE;
           if (st_code) {
             for (int q = 0; q < npt * 3; ++q) free(jw[q]);
             free(sst);
@@ -725,6 +858,7 @@ int orc_forward(orc_problem *P)
       }
     }
     orc_update_E(st);
+    if (P->airwave) orc_airwave_E(st);
     /* receiver values: E^{n+1} (just updated) and H^{n+1/2} (not yet updated) */
     for (int r = 0; r < nrec; ++r)
       for (int c = 0; c < 6; ++c) rval[r * 6 + c] = orc_sample(st, st->F[c], &rst[r * 6 + c]);
@@ -779,6 +913,7 @@ int orc_forward(orc_problem *P)
       }
     }
     orc_update_H(st, dt);
+    if (P->airwave) orc_airwave_H(st);
     if (P->convergence && it > 0 && it % 100 == 0) {
       /* converged when, at every corner, the change since the last check is at
        * most 1e-5 of the current value (and that value is nonzero). */
