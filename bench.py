@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
+    ap.add_argument("--no-airwave", action="store_true",
+                    help="skip the air-boundary line (uniform-xy marine model with and without air on top)")
     ap.add_argument("--batch", type=int, default=8,
                     help="transmitters of the batched-survey line (emm_forward_batch; 0 = skip)")
     ap.add_argument("--timesteps", type=int, default=0,
@@ -374,6 +376,33 @@ def main():
                          "vs_one_at_a_time": bval / value,
                          "what": "emm_forward_batch: transmitters sharing grid, sigma and receivers in the same "
                                  "launches, against the device-resident single-transmitter value"}
+    if not args.no_airwave and wl.name.startswith("marine"):
+        # top boundary with air (Sec. 3.3): the marine model on a grid uniform
+        # in x and y, one warm-up and one timed solve with and without air
+        awl = W.marine_1d_air()
+        agrid = emm.grid_for(awl)
+        ant = emm.steps_for(awl, agrid)
+        asig = torch.from_numpy(awl.sigma.astype(np.float32)).cuda()
+        acells = agrid.cells
+        rates = {}
+        for air in (False, True):
+            asurvey = emm.survey_for(awl, nt=ant, airwave=air)
+            awork = emm.Workspace(agrid, asurvey)
+            emm.forward_async(agrid, asurvey, asig, awork)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            emm.forward_async(agrid, asurvey, asig, awork)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            assert emm.status(awork) == emm.EMM_OK
+            rates[air] = aggregate_rate(world, acells, ant, 1, job_max(a0.elapsed_time(a1) / 1e3))
+            del awork
+        line["airwave"] = {"workload": awl.name, "value": rates[True], "unit": "Gcell-steps/s",
+                           "without_air": rates[False], "overhead": rates[False] / rates[True],
+                           "timesteps_per_solve": ant,
+                           "what": "forward solve with air above the sea surface (plane DFTs after every "
+                                   "half step) against the same model with CPML on the top face"}
     if not args.no_gradient:
         # gradient of Re(sum conj(v) G) for a seeded cotangent v: one warm-up
         # call, one timed call (CUDA events), against one forward solve

@@ -153,6 +153,16 @@ typedef struct {
                            sub-dipoles at the midpoints of equal segments (the
                            paper's uniformly distributed current, Sec. 7) */
   int src_points;       /* 1 .. 256 sub-dipoles when src_length > 0 */
+  int airwave;          /* 1: air above the top interior node (Sec. 3.3): no CPML
+                           on the top face; after every E update E_x, E_y on the
+                           rd-1 integer rows above the interface, and after every
+                           H update H_x, H_y on the rd half rows above it, are the
+                           harmonic continuation of the interface plane (per
+                           horizontal wavenumber k: e^{-|k| h} at height h, and
+                           H_x,y = i k_x,y / |k| H_z, shifted to their own x-y
+                           positions), through the 2-D DFT of the padded plane.
+                           Needs uniform x and y spacing (EMM_EINVAL) and source
+                           stencils below the interface (EMM_EOUTSIDE). */
 } emm_survey;
 
 /* Device workspace bytes emm_forward needs for this grid and survey
@@ -271,7 +281,8 @@ int emm_gradient_workspace_size(const emm_grid *grid, const emm_survey *survey, 
  *             the interior staggered sigma_xx, sigma_yy, sigma_zz (the pads'
  *             replicated values folded onto the edge samples).
  * Asynchronous on `stream`; errors as emm_forward (survey->volume must be 0
- * survey->src_kind 0 and survey->src_length 0: EMM_EINVAL otherwise). */
+ * survey->src_kind 0, survey->src_length 0 and survey->airwave 0: EMM_EINVAL
+ * otherwise). */
 int emm_gradient(const emm_grid *grid, const emm_survey *survey, const float *sigma, const double *dG,
                  int ckpt_every, void *ws, size_t ws_bytes, double *rec_out, double *grad,
                  emm_stream stream);

@@ -68,7 +68,7 @@ class _Survey(C.Structure):
                 ("src_az", C.c_double), ("src_dip", C.c_double), ("moment", C.c_double),
                 ("nrec", C.c_int), ("rec", _D), ("nfreq", C.c_int), ("freqs", _D),
                 ("volume", C.c_int), ("src_kind", C.c_int),
-                ("src_length", C.c_double), ("src_points", C.c_int)]
+                ("src_length", C.c_double), ("src_points", C.c_int), ("airwave", C.c_int)]
 
 
 _lib = None
@@ -222,6 +222,7 @@ class Survey:
     src_kind: int = 0          # 0: electric dipole J; 1: magnetic dipole M
     src_length: float = 0.0    # > 0: an antenna of this length (m), as src_points sub-dipoles
     src_points: int = 1
+    airwave: bool = False      # air above the top interior node (needs uniform x, y)
 
     def _c(self) -> Tuple[_Survey, list]:
         rec = _f64(np.zeros((0, 3)) if self.rec is None else self.rec).reshape(-1, 3)
@@ -238,6 +239,7 @@ class Survey:
         s.volume = int(bool(self.volume))
         s.src_kind = int(self.src_kind)
         s.src_length, s.src_points = float(self.src_length), int(self.src_points)
+        s.airwave = int(bool(self.airwave))
         return s, [rec, freqs]   # the arrays must outlive every use of the struct
 
     @property

@@ -533,7 +533,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
                   size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
-  if (K < 1 || s->volume || s->src_kind != 0 || s->src_length > 0 || !grad || !sigma || !ws || (s->nrec > 0 && (!dG || !rec_out)))
+  if (K < 1 || s->volume || s->src_kind != 0 || s->src_length > 0 || s->airwave || !grad || !sigma || !ws || (s->nrec > 0 && (!dG || !rec_out)))
     return EMM_EINVAL;
   const AdjLayout A = adj_plan(g, s, K);
   if (ws_bytes < A.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;

@@ -82,6 +82,14 @@ struct DevParams {
   int src_fused;    // 1: the E kernel injects J itself (an electric point dipole);
                     // otherwise k_inject does, after the E or the H launch
   size_t jstride;   // floats of jw per transmitter
+  // Air above the model (airwave runs; else air_on = 0): interface row ks,
+  // DFT matrices e^{-2 pi i (a b mod np) / np} per axis ([np][np]), continuation factors of the E
+  // rows [rd-1][np1][np0] and of the H rows [2][rd][np1][np0] (H_x, H_y),
+  // and the work planes T, F [nsrc][3][np1][np0] and U [nsrc][2 rd][np1][np0].
+  int air_on, air_ks, air_rd;
+  const float2 *air_twx, *air_twy, *air_facH;
+  const float *air_decE;
+  float2 *air_T, *air_F, *air_U;
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
@@ -130,7 +138,8 @@ FieldGeom field_geom(const emm_grid *g);
 // at E[0]; transmitter k's block starts sstride bytes further per k.
 struct Layout {
   size_t status, conv, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, zero_end;
-  size_t cm[3], cp[3], pml[3], srcs, jw, amp, rec_start, rec_w, fE, fH, fE32, fH32, norm, total;
+  size_t cm[3], cp[3], pml[3], srcs, jw, amp, rec_start, rec_w, fE, fH, fE32, fH32, norm;
+  size_t air_twx, air_twy, air_decE, air_facH, air_work, total;
 };
 
 Layout plan(const emm_grid *g, const emm_survey *s, int nsrc = 1);

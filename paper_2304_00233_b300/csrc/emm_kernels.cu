@@ -905,6 +905,117 @@ __global__ void k_inject(const DevParams p, const int n) {
   }
 }
 
+// ---- Air above the model (Sec. 3.3) ---------------------------------------
+// KIND 0, after the E launch: the E_x, E_y interface rows continued to the
+// rd - 1 integer rows above; KIND 1, after the H launch: the H_z interface
+// row to H_x, H_y on the rd half rows above.  The 2-D DFT of the padded x-y
+// plane and its inverse are four products with DFT matrices:
+//   MODE 0 (rows):     T[c][j][q] = sum_i f_c(i, j) w0^{q i}
+//   MODE 1 (columns):  F[c][k][q] = sum_j w1^{k j} T[c][j][q]
+//   MODE 2 (inverse columns, times the continuation factor of output o):
+//                      U[o][j][q] = sum_k conj(w1^{j k}) F[c(o)][k][q] fac_o[k][q]
+//   MODE 3 (inverse rows, real part, into the field row of output o):
+//                      out_o(i, j) = Re sum_q U[o][j][q] conj(w0^{q i}) / (N0 N1)
+// with w0 = e^{-2 pi i / N0}, w1 = e^{-2 pi i / N1}: tiled complex matrix
+// products, 16 x 16 outputs per CTA (one per thread), the contraction in
+// tiles of 32 staged in shared memory, the DFT matrices tabulated in FP64 on
+// the host.  Grid z = transmitter.
+constexpr int AT = 16;
+
+template <int MODE, bool MULTI, int KIND>
+__global__ void __launch_bounds__(AT * AT) k_air_dft(const DevParams p) {
+  wait_prior_grid();
+  if (p.halt && *p.halt) return;
+  allow_next_launch();
+  constexpr int KT = 2 * AT;  // contraction tile
+  __shared__ float2 As[AT][KT + 1], Bs[KT][AT + 1];
+  const int N0 = p.np[0], N1 = p.np[1], rd = p.air_rd, src = static_cast<int>(blockIdx.z);
+  const int nin = KIND == 0 ? 2 : 1, nout = KIND == 0 ? 2 * (rd - 1) : 2 * rd;
+  // product dimensions: Out[a][b] = sum_c A[a][c] B[c][b]
+  const int NA = MODE == 0 ? nin * N1 : MODE == 3 ? nout * N1 : N1;
+  const int NB = MODE == 1 ? nin * N0 : MODE == 2 ? nout * N0 : N0;
+  const int NC = (MODE == 0 || MODE == 3) ? N0 : N1;
+  const size_t plane = static_cast<size_t>(N0) * N1;
+  const Fields f = fields_of<MULTI>(p, src);
+  const float2 *T = p.air_T + static_cast<size_t>(src) * 3 * plane;
+  const float2 *F = p.air_F + static_cast<size_t>(src) * 3 * plane;
+  const float2 *U = p.air_U + static_cast<size_t>(src) * 2 * rd * plane;
+  const int a0 = static_cast<int>(blockIdx.y) * AT, b0 = static_cast<int>(blockIdx.x) * AT;
+  const int tx = threadIdx.x % AT, ty = threadIdx.x / AT;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int c0 = 0; c0 < NC; c0 += KT) {
+    for (int h = 0; h < 2; ++h) {
+      {  // A tile element (a0 + ty, c0 + h AT + tx)
+        const int col = h * AT + tx, a = a0 + ty, c = c0 + col;
+        float2 v = make_float2(0.f, 0.f);
+        if (a < NA && c < NC) {
+          if (MODE == 0) {
+            const int comp = a / N1, j = a % N1;
+            const float *fc = KIND == 0 ? (comp == 0 ? f.E[0] : f.E[1]) : f.H[2];
+            v.x = fc[static_cast<size_t>(p.air_ks) * p.plane + static_cast<size_t>(j) * p.pitch + c];
+          } else if (MODE == 3) {
+            v = U[static_cast<size_t>(a) * N0 + c];  // a = o N1 + j
+          } else {
+            const float2 w = p.air_twy[static_cast<size_t>(a) * N1 + c];
+            v = MODE == 1 ? w : make_float2(w.x, -w.y);
+          }
+        }
+        As[ty][col] = v;
+      }
+      {  // B tile element (c0 + h AT + ty, b0 + tx)
+        const int row = h * AT + ty, c = c0 + row, b = b0 + tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (c < NC && b < NB) {
+          if (MODE == 0 || MODE == 3) {
+            const float2 w = p.air_twx[static_cast<size_t>(c) * N0 + b];
+            v = MODE == 0 ? w : make_float2(w.x, -w.y);
+          } else if (MODE == 1) {
+            const int comp = b / N0, q = b % N0;
+            v = T[(static_cast<size_t>(comp) * N1 + c) * N0 + q];
+          } else {
+            const int o = b / N0, q = b % N0, r2 = o / 2;
+            const int comp = KIND == 0 ? o % 2 : 0;
+            const float2 x = F[(static_cast<size_t>(comp) * N1 + c) * N0 + q];
+            const size_t fi = static_cast<size_t>(c) * N0 + q;
+            if (KIND == 0) {
+              const float g = p.air_decE[r2 * plane + fi];
+              v = make_float2(x.x * g, x.y * g);
+            } else {
+              const float2 g = p.air_facH[(static_cast<size_t>(o % 2) * rd + r2) * plane + fi];
+              v = make_float2(x.x * g.x - x.y * g.y, x.x * g.y + x.y * g.x);
+            }
+          }
+        }
+        Bs[row][tx] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const float2 bv = Bs[k][tx], av = As[ty][k];
+      acc.x = fmaf(av.x, bv.x, fmaf(-av.y, bv.y, acc.x));
+      acc.y = fmaf(av.x, bv.y, fmaf(av.y, bv.x, acc.y));
+    }
+    __syncthreads();
+  }
+  const int b = b0 + tx, a = a0 + ty;
+  if (b >= NB || a >= NA) return;
+  if (MODE == 0) {
+    p.air_T[static_cast<size_t>(src) * 3 * plane + static_cast<size_t>(a) * N0 + b] = acc;  // a = comp N1 + j
+  } else if (MODE == 1) {
+    const int comp = b / N0, q = b % N0;
+    p.air_F[static_cast<size_t>(src) * 3 * plane + (static_cast<size_t>(comp) * N1 + a) * N0 + q] = acc;
+  } else if (MODE == 2) {
+    const int o = b / N0, q = b % N0;
+    p.air_U[static_cast<size_t>(src) * 2 * rd * plane + (static_cast<size_t>(o) * N1 + a) * N0 + q] = acc;
+  } else {
+    const int o = a / N1, j = a % N1, r2 = o / 2, d = o % 2;
+    float *out = KIND == 0 ? (d == 0 ? f.E[0] : f.E[1]) : (d == 0 ? f.H[0] : f.H[1]);
+    out[static_cast<size_t>(p.air_ks - 1 - r2) * p.plane + static_cast<size_t>(j) * p.pitch + b] =
+        acc.x / (static_cast<float>(N0) * static_cast<float>(N1));
+  }
+}
+
 // dt/eps on the padded grid from the interior staggered conductivity, with
 // the pads replicating the edge (model extension, Sec. 3.8), and the input
 // check (finite, positive, >= sigma_min).
@@ -1087,6 +1198,9 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   L.vacc = take(s->volume ? 6 * nf * nint * sizeof(float4) : 0);
   L.zero_end = off;
   for (int c = 0; c < 3; ++c) L.ie[c] = take(cells * 4);
+  // air: work planes T, F (3 components) and U (2 rd outputs) per transmitter
+  const size_t plane2 = static_cast<size_t>(g->ax[0].npad) * g->ax[1].npad;
+  L.air_work = take(s->airwave ? static_cast<size_t>(nsrc) * (6 + 2 * g->rd) * plane2 * 8 : 0);
   // FD rows; the x tables run on to a whole field row (zero rows past npad),
   // because the kernels read the rows of all four cells of a quad at once
   const size_t xrows = std::max<size_t>(g->ax[0].npad, field_geom(g).pitch);
@@ -1103,6 +1217,11 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   L.fE32 = take(nt * nf * 2 * sizeof(float));
   L.fH32 = take(nt * nf * 2 * sizeof(float));
   L.norm = take(2 * nf * 2 * sizeof(double));
+  // air: twiddles and continuation factors
+  L.air_twx = take(s->airwave ? static_cast<size_t>(g->ax[0].npad) * g->ax[0].npad * 8 : 0);
+  L.air_twy = take(s->airwave ? static_cast<size_t>(g->ax[1].npad) * g->ax[1].npad * 8 : 0);
+  L.air_decE = take(s->airwave ? static_cast<size_t>(g->rd - 1) * plane2 * 4 : 0);
+  L.air_facH = take(s->airwave ? 2 * static_cast<size_t>(g->rd) * plane2 * 8 : 0);
   L.total = off;
   return L;
 }
@@ -1118,6 +1237,7 @@ int check_survey(const emm_grid *g, const emm_survey *s) {
   if (!(s->src_length >= 0) || !std::isfinite(s->src_length) ||
       (s->src_length > 0 && (s->src_points < 1 || s->src_points > 256)))
     return EMM_EINVAL;
+  if (s->airwave != 0 && s->airwave != 1) return EMM_EINVAL;
   return EMM_OK;
 }
 
@@ -1146,6 +1266,26 @@ bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
          make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
+// The four air products after a half step (see k_air_dft).
+template <bool MULTI, int KIND>
+cudaError_t air_step(const DevParams &p, cudaStream_t st) {
+  const int rd = p.air_rd, N0 = p.np[0], N1 = p.np[1];
+  const int nin = KIND == 0 ? 2 : 1, nout = KIND == 0 ? 2 * (rd - 1) : 2 * rd;
+  auto tiles = [](int n) { return static_cast<unsigned>((n + AT - 1) / AT); };
+  const unsigned z = static_cast<unsigned>(p.nsrc);
+  const dim3 tb(AT * AT);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess)
+    e = launch_dependent(k_air_dft<0, MULTI, KIND>, dim3(tiles(N0), tiles(nin * N1), z), tb, 0, st, p);
+  if (e == cudaSuccess)
+    e = launch_dependent(k_air_dft<1, MULTI, KIND>, dim3(tiles(nin * N0), tiles(N1), z), tb, 0, st, p);
+  if (e == cudaSuccess)
+    e = launch_dependent(k_air_dft<2, MULTI, KIND>, dim3(tiles(nout * N0), tiles(N1), z), tb, 0, st, p);
+  if (e == cudaSuccess)
+    e = launch_dependent(k_air_dft<3, MULTI, KIND>, dim3(tiles(N0), tiles(nout * N1), z), tb, 0, st, p);
+  return e;
+}
+
 template <int R, bool VOL, bool MULTI, bool CONV>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
@@ -1168,9 +1308,11 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
     e = launch_dependent(k_update_E<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
     if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
       e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, p, n);
+    if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(p, st);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
     if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
     if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, p, n);
+    if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(p, st);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -1248,6 +1390,10 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     for (size_t q = 0; q < ax.cp.size(); ++q) cp[q] = static_cast<float>(ax.cp[q]);
     std::vector<double> ab(8 * static_cast<size_t>(nb));
     cpml_axis(g, a, vmax, s->fmax, dt, ab.data());
+    // air above the model: no CPML on the top face (a = b = 0 on the near z slab)
+    if (s->airwave && a == 2)
+      for (int grp = 0; grp < 4; ++grp)
+        for (int e = 0; e < nb; ++e) ab[static_cast<size_t>(grp) * 2 * nb + e] = 0.0;
     float *pm = reinterpret_cast<float *>(at(L.pml[a]));
     for (size_t q = 0; q < ab.size(); ++q) pm[q] = static_cast<float>(ab[q]);
   }
@@ -1287,6 +1433,8 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
           const double pa = pos[a] + off * dir[a];
           st = locate_axis(g, a, kHalf[c + sc][a], pa, &starts[q * 3 + a], &ws[(static_cast<size_t>(q) * 3 + a) * m]);
           if (st != EMM_OK) return st;
+          // with air above the model the source stencil stays below the interface
+          if (s->airwave && a == 2 && starts[q * 3 + 2] < nbe) return EMM_EOUTSIDE;
           lo[a] = std::min(lo[a], starts[q * 3 + a]);
           hi[a] = std::max(hi[a], starts[q * 3 + a] + m - 1);
         }
@@ -1364,6 +1512,58 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   }
   normalisation(s, dt, nt, reinterpret_cast<double *>(at(L.norm)));
 
+  // air above the model (Sec. 3.3): DFT twiddles e^{-2 pi i m / N} and the
+  // continuation factors, per horizontal wavenumber k (kx = 2 pi p / (N dx),
+  // p in (-N/2, N/2]): e^{-|k| h} for the E rows at the heights h above the
+  // interface, and i k_{x,y} / |k| e^{-i k_{x,y} d_{x,y} / 2} e^{-|k| h} for the
+  // H_x, H_y half rows (0 at k = 0)
+  if (s->airwave) {
+    const int N0 = g->ax[0].npad, N1 = g->ax[1].npad, ks = nbe;
+    double d[2];
+    for (int a = 0; a < 2; ++a) {
+      const Axis &ax = g->ax[a];
+      d[a] = ax.X[1] - ax.X[0];
+      for (size_t i = 1; i < ax.X.size(); ++i)
+        if (std::fabs((ax.X[i] - ax.X[i - 1]) - d[a]) > 1e-9 * d[a]) return EMM_EINVAL;
+    }
+    float2 *twx = reinterpret_cast<float2 *>(at(L.air_twx)), *twy = reinterpret_cast<float2 *>(at(L.air_twy));
+    // the DFT matrices W[a][b] = e^{-2 pi i (a b mod N) / N}
+    for (int a = 0; a < N0; ++a)
+      for (int b = 0; b < N0; ++b) {
+        const int m = static_cast<int>((static_cast<long long>(a) * b) % N0);
+        twx[static_cast<size_t>(a) * N0 + b] =
+            make_float2(static_cast<float>(std::cos(2 * M_PI * m / N0)), static_cast<float>(-std::sin(2 * M_PI * m / N0)));
+      }
+    for (int a = 0; a < N1; ++a)
+      for (int b = 0; b < N1; ++b) {
+        const int m = static_cast<int>((static_cast<long long>(a) * b) % N1);
+        twy[static_cast<size_t>(a) * N1 + b] =
+            make_float2(static_cast<float>(std::cos(2 * M_PI * m / N1)), static_cast<float>(-std::sin(2 * M_PI * m / N1)));
+      }
+    const Axis &az = g->ax[2];
+    float *decE = reinterpret_cast<float *>(at(L.air_decE));
+    float2 *facH = reinterpret_cast<float2 *>(at(L.air_facH));
+    const size_t plane2 = static_cast<size_t>(N0) * N1;
+    for (int k = 0; k < N1; ++k)
+      for (int q = 0; q < N0; ++q) {
+        const double kx = 2 * M_PI * (q <= N0 / 2 ? q : q - N0) / (N0 * d[0]);
+        const double ky = 2 * M_PI * (k <= N1 / 2 ? k : k - N1) / (N1 * d[1]);
+        const double kk = std::sqrt(kx * kx + ky * ky);
+        const size_t o = static_cast<size_t>(k) * N0 + q;
+        for (int r = 0; r + 1 < rd; ++r) decE[r * plane2 + o] = static_cast<float>(std::exp(-kk * (az.X[ks] - az.X[ks - 1 - r])));
+        for (int r = 0; r < rd; ++r) {
+          const double decay = std::exp(-kk * (az.X[ks] - az.Xh[ks - 1 - r]));
+          for (int dd = 0; dd < 2; ++dd) {
+            const double kd = dd == 0 ? kx : ky;
+            const std::complex<double> f =
+                kk > 0 ? I * (kd / kk) * std::exp(-I * (kd * d[dd] / 2)) * decay : std::complex<double>(0.0);
+            facH[(static_cast<size_t>(dd) * rd + r) * plane2 + o] =
+                make_float2(static_cast<float>(f.real()), static_cast<float>(f.imag()));
+          }
+        }
+      }
+  }
+
   // ---- device parameters ----
   unsigned char *base = static_cast<unsigned char *>(ws);
   for (int a = 0; a < 3; ++a) {
@@ -1413,6 +1613,19 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   p.status = reinterpret_cast<int *>(base + L.status);
   p.src_magnetic = s->src_kind == 1 ? 1 : 0;
   p.src_fused = (s->src_kind == 0 && !(s->src_length > 0)) ? 1 : 0;
+  if (s->airwave) {
+    p.air_on = 1;
+    p.air_ks = nbe;
+    p.air_rd = rd;
+    p.air_twx = reinterpret_cast<const float2 *>(base + L.air_twx);
+    p.air_twy = reinterpret_cast<const float2 *>(base + L.air_twy);
+    p.air_decE = reinterpret_cast<const float *>(base + L.air_decE);
+    p.air_facH = reinterpret_cast<const float2 *>(base + L.air_facH);
+    const size_t plane2 = static_cast<size_t>(p.np[0]) * p.np[1];
+    p.air_T = reinterpret_cast<float2 *>(base + L.air_work);
+    p.air_F = p.air_T + static_cast<size_t>(nsrc) * 3 * plane2;
+    p.air_U = p.air_F + static_cast<size_t>(nsrc) * 3 * plane2;
+  }
   p.jstride = source_stride(g, s);
   if (converge) {
     p.corner = reinterpret_cast<double *>(base + L.conv);

@@ -328,6 +328,25 @@ def marine_1d(nxy: int = 128, nz: int = 96, rd: int = 2) -> Workload:
                     np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4)
 
 
+def marine_1d_air(nxy: int = 128, nz: int = 96, rd: int = 2) -> Workload:
+    """The layered marine model of ``marine_1d`` with the sea surface (z = 0)
+    as an interface with air, on a grid uniform in x and y (100 m, as the
+    DFT of the air boundary needs) and the same stretched z axis; same
+    source, receivers and frequencies."""
+    x = (np.arange(nxy) - 0.5 * (nxy - 1)) * 100.0
+    n_up = 16
+    z = seabed_axis(1000.0, n_up, 1000.0, nz - n_up - 1, 8000.0, 40.0)
+    model = _marine_model(True)
+    sh, sv = cell_conductivity(model, x, x, z)
+    sig = staggered_conductivity(sh, sv, x, x, z)
+    rec = np.zeros((64, 3))
+    rec[:, 0] = -6300.0 + 200.0 * np.arange(64)
+    rec[:, 2] = 1000.0
+    return Workload("marine_1d_air_128x128x96", x, x.copy(), z, _f32(sig), rd, 10,
+                    rd + 5, np.array([0.0, 0.0, 950.0]), 0.0, 0.0, 1.0, rec,
+                    np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4)
+
+
 def anomaly_3d(seed: int = 230400233) -> Workload:
     """Marine background of ``marine_1d`` on a 256 x 256 x 160 NU grid, plus a
     4 x 3 km x 100 m resistive block (0.01 S/m) at 2000-2100 m depth and a
