@@ -195,8 +195,10 @@ int emm_forward(const emm_grid *grid, const emm_survey *survey, const float *sig
 typedef struct {
   int every;       /* in: time the launches of every `every`-th step (>= 1) */
   int samples;     /* out: number of steps timed */
-  double e_ms;     /* out: mean duration (ms) of one E half-step launch */
-  double h_ms;     /* out: mean duration (ms) of one H half-step launch */
+  double e_ms;     /* out: mean duration (ms) of one E half step: the E launch
+                      and the source, air and volume-DTFT launches after it */
+  double h_ms;     /* out: mean duration (ms) of one H half step: the H launch
+                      and the source and air launches after it */
   double total_ms; /* out: duration (ms) of the whole enqueued forward run */
   double loop_ms;  /* out: duration (ms) of the time loop alone: every E and H
                       launch back to back, from the first to the last */

@@ -7,11 +7,13 @@
 //   k_update_E<R>  curl H with D- rows and CPML memory (Eq. 14, 22-24), the
 //                  electric source at t_{n+1/2}, E += dt/eps (curl H - J)
 //                  (Eq. 8); extra CTAs accumulate the receiver DTFT of
-//                  H^{n+1/2} (Eq. 25), which this launch only reads; interior
-//                  threads accumulate the volume DTFT of H^{n+1/2}.
+//                  H^{n+1/2} (Eq. 25), which this launch only reads.
 //   k_update_H<R>  curl E with D+ rows and CPML memory (Eq. 13, 22-24),
 //                  H -= dt/mu0 curl E; extra CTAs accumulate the receiver
-//                  DTFT of E^{n+1}; interior threads the volume DTFT of E^{n+1}.
+//                  DTFT of E^{n+1}.
+// Runs that need them add dependent launches after the E launch (antenna
+// source, air rows above the model, the volume DTFT of E^{n+1} and H^{n+1/2})
+// and after the H launch (magnetic source, air rows).
 //
 // Launch shape: the step is bound by HBM bandwidth, and what the memory
 // system needs is many bytes in flight from many CTAs.  A CTA owns a 32 x 8
@@ -101,17 +103,6 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
   const float err = (hi - (t - bp)) + (v - bp);
   hi = t;
   lo += err;
-}
-
-__device__ __forceinline__ void volume_accumulate(const DevParams &p, int comp, int lin, size_t nint,
-                                                  const float *fac, float v) {
-  for (int f = 0; f < p.nf; ++f) {
-    float4 *a = p.vacc + (static_cast<size_t>(comp) * p.nf + f) * nint + lin;
-    float4 acc = *a;
-    two_sum_add(acc.x, acc.y, fac[2 * f] * v);
-    two_sum_add(acc.z, acc.w, fac[2 * f + 1] * v);
-    *a = acc;
-  }
 }
 
 // One warp per (receiver, component): (2R)^3 weighted gather in FP64, warp
@@ -428,7 +419,7 @@ __device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, 
 
 // One quad of the E update.  FAST: an interior CTA without the source, where
 // every validity test is true and every slab test false.
-template <int R, bool VOL, bool FAST>
+template <int R, bool FAST>
 __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
                                        const float4 (&e)[3], const float4 (&w)[3], const float4 *ps, int n,
                                        bool src, const SrcDev *sd, const float *jw) {
@@ -577,31 +568,11 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
   for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.E[a] + id) = out[a];
-
-  // volume DTFT of H^{n+1/2}
-  if (VOL) {
-    const int jj = u.j - p.nbe, kk = u.k - p.nbe;
-    if (jj >= 0 && jj < p.n[1] && kk >= 0 && kk < p.n[2]) {
-      const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-      const float *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
-      const float4 hx = v.zf(u.c + R, u.r + R, q4), hy = v.xf(u.c + R, u.r, q4 + XH),
-                   hz = v.xy(u.c, u.r + R, q4 + XH);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int ii = u.i + c - p.nbe;
-        if (ii < 0 || ii >= p.n[0]) continue;
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 3, lin, nint, facH, get(hx, c));
-        volume_accumulate(p, 4, lin, nint, facH, get(hy, c));
-        volume_accumulate(p, 5, lin, nint, facH, get(hz, c));
-      }
-    }
-  }
 }
 
 // CONV: a convergence run (corner DTFT, and every launch returns at once
 // after the stop).
-template <int R, bool VOL, bool MULTI, bool CONV>
+template <int R, bool MULTI, bool CONV>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
@@ -646,9 +617,9 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    e_quad<R, VOL, true>(p, f, v, u, e, w, ps, n, false, sd, jw);
+    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw);
   else
-    e_quad<R, VOL, false>(p, f, v, u, e, w, ps, n, src, sd, jw);
+    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw);
 }
 
 // ---------------------------------------------------------------------------
@@ -663,7 +634,7 @@ __device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, 
          o.k0 + ZC - 1 <= hz;
 }
 
-template <int R, bool VOL, bool FAST>
+template <int R, bool FAST>
 __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
                                        const float4 (&h)[3], const float4 *ps, int n) {
   constexpr int M = 2 * R;
@@ -806,29 +777,9 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, cons
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
   for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.H[a] + id) = out[a];
-
-  // volume DTFT of E^{n+1}
-  if (VOL) {
-    const int jj = u.j - p.nbe, kk = u.k - p.nbe;
-    if (jj >= 0 && jj < p.n[1] && kk >= 0 && kk < p.n[2]) {
-      const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-      const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2;
-      const float4 ex = v.zf(u.c + R - 1, u.r + R, q4), ey = v.xf(u.c + R - 1, u.r, q4 + XH),
-                   ez = v.xy(u.c, u.r + R, q4 + XH);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int ii = u.i + c - p.nbe;
-        if (ii < 0 || ii >= p.n[0]) continue;
-        const int lin = (kk * p.n[1] + jj) * p.n[0] + ii;
-        volume_accumulate(p, 0, lin, nint, facE, get(ex, c));
-        volume_accumulate(p, 1, lin, nint, facE, get(ey, c));
-        volume_accumulate(p, 2, lin, nint, facE, get(ez, c));
-      }
-    }
-  }
 }
 
-template <int R, bool VOL, bool MULTI, bool CONV>
+template <int R, bool MULTI, bool CONV>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
@@ -866,9 +817,9 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    h_quad<R, VOL, true>(p, f, v, u, h, ps, n);
+    h_quad<R, true>(p, f, v, u, h, ps, n);
   else
-    h_quad<R, VOL, false>(p, f, v, u, h, ps, n);
+    h_quad<R, false>(p, f, v, u, h, ps, n);
 }
 
 // Sources the stencil kernels do not inject themselves, one thread per
@@ -1013,6 +964,42 @@ __global__ void __launch_bounds__(AT * AT) k_air_dft(const DevParams p) {
     float *out = KIND == 0 ? (d == 0 ? f.E[0] : f.E[1]) : (d == 0 ? f.H[0] : f.H[1]);
     out[static_cast<size_t>(p.air_ks - 1 - r2) * p.plane + static_cast<size_t>(j) * p.pitch + b] =
         acc.x / (static_cast<float>(N0) * static_cast<float>(N1));
+  }
+}
+
+// Volume DTFT of step n (Eq. 25 on every interior sample), after the E
+// launch (and the source and air launches that follow it), when E holds
+// E^{n+1} and H still holds H^{n+1/2}: for the six components and every
+// frequency, acc += factor * value in compensated FP32 (hi + lo pairs of the
+// real and imaginary parts).  One thread per interior sample, i fastest.
+__global__ void k_volume_dft(const DevParams p, const int n) {
+  wait_prior_grid();
+  if (p.halt && *p.halt) return;  // a convergence run that has stopped
+  allow_next_launch();
+  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+  const size_t lin = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (lin >= nint) return;
+  const int ii = static_cast<int>(lin % p.n[0]), jj = static_cast<int>((lin / p.n[0]) % p.n[1]),
+            kk = static_cast<int>(lin / (static_cast<size_t>(p.n[0]) * p.n[1]));
+  const size_t id = static_cast<size_t>(kk + p.nbe) * p.plane + static_cast<size_t>(jj + p.nbe) * p.pitch + (ii + p.nbe);
+  float v[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = p.E[c][id];
+    v[3 + c] = p.H[c][id];
+  }
+  const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2, *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
+  for (int f = 0; f < p.nf; ++f) {
+    float4 acc[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] = p.vacc[(static_cast<size_t>(c) * p.nf + f) * nint + lin];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float *fac = c < 3 ? facE : facH;
+      two_sum_add(acc[c].x, acc[c].y, fac[2 * f] * v[c]);
+      two_sum_add(acc[c].z, acc[c].w, fac[2 * f + 1] * v[c]);
+      p.vacc[(static_cast<size_t>(c) * p.nf + f) * nint + lin] = acc[c];
+    }
   }
 }
 
@@ -1286,31 +1273,34 @@ cudaError_t air_step(const DevParams &p, cudaStream_t st) {
   return e;
 }
 
-template <int R, bool VOL, bool MULTI, bool CONV>
+template <int R, bool MULTI, bool CONV>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   TmaSet tE{}, tH{};
   if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R, VOL, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_update_E<R, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R, VOL, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_update_H<R, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   // each half-step is launched as a programmatic dependent of the one before
   const dim3 inj(static_cast<unsigned>((p.nsrc * p.jstride + 127) / 128));  // k_inject threads
+  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
+  const dim3 vol_blocks(static_cast<unsigned>((nint + 255) / 256));             // k_volume_dft threads
   size_t used = 0;
   if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    e = launch_dependent(k_update_E<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
+    e = launch_dependent(k_update_E<R, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
     if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
       e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, p, n);
     if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(p, st);
+    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, p, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, VOL, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
     if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, p, n);
     if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(p, st);
     if (timed) {
@@ -1672,17 +1662,12 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
-// The launch variants of one order: one transmitter, with or without the
-// volume DTFT; a batch; a convergence run, with or without the volume DTFT.
+// The launch variants of one order: one transmitter; a batch; a convergence run.
 template <int R>
 cudaError_t run_order(const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs, StepEvents *te) {
-  const bool vol = p.vacc != nullptr;
-  if (p.nsrc > 1) return launch_steps<R, false, true, false>(p, n0, n1, blocks, cs, te);
-  if (p.corner)
-    return vol ? launch_steps<R, true, false, true>(p, n0, n1, blocks, cs, te)
-               : launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te);
-  return vol ? launch_steps<R, true, false, false>(p, n0, n1, blocks, cs, te)
-             : launch_steps<R, false, false, false>(p, n0, n1, blocks, cs, te);
+  if (p.nsrc > 1) return launch_steps<R, true, false>(p, n0, n1, blocks, cs, te);
+  if (p.corner) return launch_steps<R, false, true>(p, n0, n1, blocks, cs, te);
+  return launch_steps<R, false, false>(p, n0, n1, blocks, cs, te);
 }
 
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
