@@ -74,16 +74,6 @@ __device__ __forceinline__ int slab_half(int i, int np, int nb) {
   return i < nb ? i : ((i >= np - 1 - nb && i <= np - 2) ? nb + np - 2 - i : -1);
 }
 
-// Element of sample (i, j, k) in a CPML memory array of a derivative along
-// axis `axis` with slab entry s (layouts as the forward kernels store them;
-// h = 0 integer / 1 half samples for the x-derivative storage).
-__device__ __forceinline__ size_t psi_index(const AdjParams &a, int axis, int h, int s, int i, int j, int k) {
-  if (axis == 1) return (static_cast<size_t>(k) * (2 * a.nb) + s) * a.pitch + i;
-  if (axis == 2) return (static_cast<size_t>(s) * a.np[1] + j) * a.pitch + i;
-  const int xs = i < a.nb ? i : a.psx_hx[h] + (i - a.psx_far0[h]);
-  return (static_cast<size_t>(k) * a.np[1] + j) * a.psx_wx[h] + xs;
-}
-
 // Cell of this thread in a 3-D launch of 32 x 8 threads per (x, y) tile and
 // one grid z layer per plane; false outside the padded grid.
 __device__ __forceinline__ bool cell3(const AdjParams &a, int *idx) {
@@ -123,34 +113,104 @@ __device__ __forceinline__ bool quad_plain(const AdjParams &a, const int *idx, i
   return idx[0] >= lo && idx[0] + 3 <= hi[0] && idx[1] >= lo && idx[1] <= hi[1] && idx[2] >= lo && idx[2] <= hi[2];
 }
 
-// 1a. T[2c+t] at the H_c samples from lambda_H.
-__device__ __forceinline__ void h_pre_cell(const AdjParams &a, const int *idx) {
-  const int R = a.rd, nb = a.nb;
-  const size_t id = fid(a, idx[0], idx[1], idx[2]);
-  bool dp[3];
-  for (int ax = 0; ax < 3; ++ax) dp[ax] = idx[ax] >= R - 1 && idx[ax] <= a.np[ax] - 1 - R;
+__device__ __forceinline__ float lane(const float4 &v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set_lane(float4 &v, int e, float x) {
+  if (e == 0) v.x = x;
+  else if (e == 1) v.y = x;
+  else if (e == 2) v.z = x;
+  else v.w = x;
+}
+
+// The per-derivative adjoints of a quad that touches a CPML slab or a sample
+// the forward loop leaves alone (KIND 0: the H_c samples, T from lambda_H;
+// KIND 1: the E_c samples, T from dt/eps lambda_E, and the gradient term).
+// Every array moves as float4: the CPML memory adjoints use the forward
+// kernels' layouts, where a quad's four slab entries along y or z share a
+// row, and along x sit at the quad's storage column (no two quads share a
+// float4); lanes outside the slab or the update region keep their memory
+// adjoint and get T = 0 where the forward loop does not update them.
+template <int KIND>
+__device__ void pre_quad(const AdjParams &a, const int *idx) {
+  const int R = a.rd, nb = a.nb, i0 = idx[0], j = idx[1], k = idx[2];
+  const size_t id = fid(a, i0, j, k);
+  const int lo = KIND == 0 ? R - 1 : R;  // first sample with every FD row
+  bool inx[4], rx[4];
+  int sxl[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int ii = i0 + e;
+    inx[e] = ii >= 0 && ii < a.np[0];
+    rx[e] = ii >= lo && ii <= a.np[0] - 1 - R;
+    sxl[e] = KIND == 0 ? slab_half(ii, a.np[0], nb) : slab_int(ii, a.np[0], nb);
+  }
+  const bool ry = j >= lo && j <= a.np[1] - 1 - R, rz = k >= lo && k <= a.np[2] - 1 - R;
+  const int sy = KIND == 0 ? slab_half(j, a.np[1], nb) : slab_int(j, a.np[1], nb);
+  const int sz = KIND == 0 ? slab_half(k, a.np[2], nb) : slab_int(k, a.np[2], nb);
+  // storage column of the quad in the x-derivative memory arrays
+  const int last = KIND == 0 ? a.np[0] - 2 : a.np[0] - 1, h = KIND == 0 ? 1 : 0;
+  const int xs = i0 < nb ? i0 : ((i0 + 3 >= a.psx_far0[h] && i0 <= last) ? a.psx_hx[h] + (i0 - a.psx_far0[h]) : -1);
+  const float *pml_a[3], *pml_b[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    pml_a[ax] = a.pml[ax] + (KIND == 0 ? 4 * nb : 0);
+    pml_b[ax] = pml_a[ax] + 2 * nb;
+  }
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int p = (c + 1) % 3, q = (c + 2) % 3;
-    const bool valid = dp[p] && dp[q];
-    const float g = -a.kappa * a.lamH[c][id];
+    float4 g;
+    if (KIND == 0) {
+      g = scl4(-a.kappa, ldf4(a.lamH[c], id));
+    } else {
+      const float4 lam = ldf4(a.lamE[c], id), ie = ldf4(a.ie[c], id), e0 = ldf4(a.E0[c], id),
+                   e1 = ldf4(a.E1[c], id);
+      float4 gs = ldf4(a.gseg[c], id);
+      const float cg = a.inv_2w0dt;
+      gs.x -= lam.x * (e1.x - e0.x) * ie.x * cg;
+      gs.y -= lam.y * (e1.y - e0.y) * ie.y * cg;
+      gs.z -= lam.z * (e1.z - e0.z) * ie.z * cg;
+      gs.w -= lam.w * (e1.w - e0.w) * ie.w * cg;
+      stf4(a.gseg[c], id, gs);
+      g = make_float4(ie.x * lam.x, ie.y * lam.y, ie.z * lam.z, ie.w * lam.w);
+    }
+#pragma unroll
     for (int term = 0; term < 2; ++term) {
       const int ax = term == 0 ? p : q;
-      float t = 0.f;
-      if (valid) {
-        t = term == 0 ? g : -g;
-        const int s = slab_half(idx[ax], a.np[ax], nb);
-        if (s >= 0) {
-          float *mu = a.muH[2 * c + term];
-          const size_t k = psi_index(a, ax, 1, s, idx[0], idx[1], idx[2]);
-          const float gpsi = t + mu[k];
-          mu[k] = a.pml[ax][6 * nb + s] * gpsi;
-          t += a.pml[ax][4 * nb + s] * gpsi;
-        }
+      float4 t = term == 0 ? g : scl4(-1.f, g);
+      bool on[4], any = false;
+      int sl[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        bool valid = inx[e] && (p == 0 ? rx[e] : (p == 1 ? ry : rz)) && (q == 0 ? rx[e] : (q == 1 ? ry : rz));
+        if (KIND == 1) valid = valid && (c == 0 ? i0 + e <= a.np[0] - 2 : (c == 1 ? j <= a.np[1] - 2 : k <= a.np[2] - 2));
+        if (!valid) set_lane(t, e, 0.f);
+        sl[e] = ax == 0 ? sxl[e] : (ax == 1 ? sy : sz);
+        on[e] = valid && sl[e] >= 0;
+        any = any || on[e];
       }
-      a.T[2 * c + term][id] = t;
+      if (any) {
+        float *mu = KIND == 0 ? a.muH[2 * c + term] : a.muE[2 * c + term];
+        const size_t mi = ax == 1 ? (static_cast<size_t>(k) * (2 * nb) + sy) * a.pitch + i0
+                          : ax == 2 ? (static_cast<size_t>(sz) * a.np[1] + j) * a.pitch + i0
+                                    : (static_cast<size_t>(k) * a.np[1] + j) * a.psx_wx[h] + xs;
+        float4 m4 = ldf4(mu, mi);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (!on[e]) continue;
+          const float te = lane(t, e), gp = te + lane(m4, e);
+          set_lane(m4, e, pml_b[ax][sl[e]] * gp);
+          set_lane(t, e, fmaf(pml_a[ax][sl[e]], gp, te));
+        }
+        stf4(mu, mi, m4);
+      }
+      stf4(a.T[2 * c + term], id, t);
     }
   }
 }
+
+// 1a. T[2c+t] at the H_c samples from lambda_H.
 __global__ void k_adj_h_pre(const AdjParams a) {
   int idx[3];
   if (!quad_of_pre(a, idx)) return;
@@ -166,10 +226,7 @@ __global__ void k_adj_h_pre(const AdjParams a) {
     }
     return;
   }
-  for (int e = 0; e < 4; ++e) {
-    const int cell[3] = {idx[0] + e, idx[1], idx[2]};
-    if (cell[0] >= 0 && cell[0] < a.np[0]) h_pre_cell(a, cell);
-  }
+  pre_quad<0>(a, idx);
 }
 
 // 2. Receivers at step n: lambda_c[stencil] += w * Re(sum_f cw f_n).
@@ -195,36 +252,6 @@ __global__ void k_adj_receivers(const AdjParams a, int n) {
 // 3. The gradient term of this step, g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e
 // / (2 omega0 dt) (lambda_E is final for the step here), and T[2e+t] at the
 // E_e samples from lambda_E.
-__device__ __forceinline__ void e_pre_cell(const AdjParams &a, const int *idx) {
-  const int R = a.rd, nb = a.nb;
-  const size_t id = fid(a, idx[0], idx[1], idx[2]);
-  bool dm[3];
-  for (int ax = 0; ax < 3; ++ax) dm[ax] = idx[ax] >= R && idx[ax] <= a.np[ax] - 1 - R;
-  for (int e = 0; e < 3; ++e) {
-    const int p = (e + 1) % 3, q = (e + 2) % 3;
-    const bool valid = idx[e] <= a.np[e] - 2 && dm[p] && dm[q];
-    const float lam = a.lamE[e][id], ie = a.ie[e][id];
-    const float dE = a.E1[e][id] - a.E0[e][id];
-    a.gseg[e][id] -= lam * dE * ie * a.inv_2w0dt;
-    const float g = ie * lam;
-    for (int term = 0; term < 2; ++term) {
-      const int ax = term == 0 ? p : q;
-      float t = 0.f;
-      if (valid) {
-        t = term == 0 ? g : -g;
-        const int s = slab_int(idx[ax], a.np[ax], nb);
-        if (s >= 0) {
-          float *mu = a.muE[2 * e + term];
-          const size_t k = psi_index(a, ax, 0, s, idx[0], idx[1], idx[2]);
-          const float gpsi = t + mu[k];
-          mu[k] = a.pml[ax][2 * nb + s] * gpsi;
-          t += a.pml[ax][s] * gpsi;
-        }
-      }
-      a.T[2 * e + term][id] = t;
-    }
-  }
-}
 __global__ void k_adj_e_pre(const AdjParams a) {
   int idx[3];
   if (!quad_of_pre(a, idx)) return;
@@ -249,10 +276,7 @@ __global__ void k_adj_e_pre(const AdjParams a) {
     }
     return;
   }
-  for (int e = 0; e < 4; ++e) {
-    const int cell[3] = {idx[0] + e, idx[1], idx[2]};
-    if (cell[0] >= 0 && cell[0] < a.np[0]) e_pre_cell(a, cell);
-  }
+  pre_quad<1>(a, idx);
 }
 
 // ---- 1b / 4. The transposed FD gathers, TMA-fed --------------------------
