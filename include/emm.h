@@ -289,6 +289,22 @@ int emm_gradient(const emm_grid *grid, const emm_survey *survey, const float *si
                  int ckpt_every, void *ws, size_t ws_bytes, double *rec_out, double *grad,
                  emm_stream stream);
 
+/* emm_gradient with a memory budget for the reverse sweep: the forward
+ * sweep keeps the E snapshot of every step of the last
+ * floor(stored_steps / ckpt_every) checkpoint segments (at most all of them)
+ * in the workspace, and the reverse sweep recomputes only the earlier
+ * segments.  Workspace: emm_gradient_stored_workspace_size with the same
+ * ckpt_every and stored_steps (each stored step adds one E state: the three
+ * E arrays).  stored_steps = 0 is emm_gradient.  The gradient and G equal
+ * emm_gradient's bit for bit (recomputation restarts from full checkpointed
+ * states through the same deterministic kernels).  EMM_EINVAL if
+ * stored_steps < 0; otherwise as emm_gradient. */
+int emm_gradient_stored_workspace_size(const emm_grid *grid, const emm_survey *survey, int ckpt_every,
+                                       int stored_steps, size_t *bytes);
+int emm_gradient_stored(const emm_grid *grid, const emm_survey *survey, const float *sigma, const double *dG,
+                        int ckpt_every, int stored_steps, void *ws, size_t ws_bytes, double *rec_out,
+                        double *grad, emm_stream stream);
+
 /* Size of the scratch array that emm_forward_static works in. */
 #define EMM_STATIC_SCRATCH_BYTES (64u << 20)
 

@@ -35,7 +35,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_time_step", "emm_cpml_tables", "emm_locate", "emm_workspace_size",
             "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
             "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient",
-            "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge")
+            "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge",
+            "emm_gradient_stored_workspace_size", "emm_gradient_stored")
 
 
 class EmmError(RuntimeError):
@@ -103,6 +104,9 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_forward_converge": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V, _I], C.c_int),
         "emm_gradient_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "emm_gradient": ([V, C.POINTER(_Survey), V, V, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
+        "emm_gradient_stored_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.c_int, C.POINTER(C.c_size_t)],
+                                               C.c_int),
+        "emm_gradient_stored": ([V, C.POINTER(_Survey), V, V, C.c_int, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -401,20 +405,31 @@ def forward_batch(grid: Grid, survey: Survey, sigma, src_pos, work=None, stream=
     return torch.view_as_complex(rec)[:, : survey.nrec], work
 
 
-def gradient_workspace_size(grid: Grid, survey: Survey, ckpt_every: int) -> int:
+def gradient_workspace_size(grid: Grid, survey: Survey, ckpt_every: int, stored_steps: int = 0) -> int:
     s, keep = survey._c()
     n = C.c_size_t(0)
-    _check(load_library().emm_gradient_workspace_size(grid.handle, C.byref(s), int(ckpt_every), C.byref(n)),
-           "emm_gradient_workspace_size")
+    _check(load_library().emm_gradient_stored_workspace_size(grid.handle, C.byref(s), int(ckpt_every),
+                                                             int(stored_steps), C.byref(n)),
+           "emm_gradient_stored_workspace_size")
     return n.value
 
 
-def vjp(grid: Grid, survey: Survey, sigma, dG, ckpt_every: Optional[int] = None, stream=None, check: bool = True):
-    """``emm_gradient``: the gradient d/dsigma Re(sum conj(dG) G) with respect to
-    the interior staggered conductivity (float64 CUDA tensor [3][n3][n2][n1]),
-    and G of the forward sweep (complex128 [nrec][6][nfreq]).  ``dG`` is a
-    complex tensor [nrec][6][nfreq]; ``ckpt_every`` defaults to about
-    sqrt(nt) steps between checkpoints."""
+def snapshot_bytes(grid: Grid, survey: Survey, ckpt_every: int) -> int:
+    """Device bytes one stored E snapshot adds to the gradient workspace."""
+    return (gradient_workspace_size(grid, survey, ckpt_every, 2 * ckpt_every)
+            - gradient_workspace_size(grid, survey, ckpt_every, ckpt_every)) // ckpt_every
+
+
+def vjp(grid: Grid, survey: Survey, sigma, dG, ckpt_every: Optional[int] = None, stream=None, check: bool = True,
+        stored_steps: int = 0):
+    """``emm_gradient_stored``: the gradient d/dsigma Re(sum conj(dG) G) with
+    respect to the interior staggered conductivity (float64 CUDA tensor
+    [3][n3][n2][n1]), and G of the forward sweep (complex128
+    [nrec][6][nfreq]).  ``dG`` is a complex tensor [nrec][6][nfreq];
+    ``ckpt_every`` defaults to about sqrt(nt) steps between checkpoints;
+    ``stored_steps`` is the budget of final steps whose E snapshots the
+    forward sweep keeps in device memory (whole checkpoint segments), which
+    the reverse sweep then does not recompute."""
     import torch
     _check_sigma(grid, sigma)
     if stream is None:
@@ -422,7 +437,7 @@ def vjp(grid: Grid, survey: Survey, sigma, dG, ckpt_every: Optional[int] = None,
     nf = len(survey.freqs)
     if ckpt_every is None:
         ckpt_every = max(1, int(round(max(survey.nt, 1) ** 0.5)))
-    nbytes = gradient_workspace_size(grid, survey, ckpt_every)
+    nbytes = gradient_workspace_size(grid, survey, ckpt_every, stored_steps)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=sigma.device)
     ptr = ws.data_ptr() + (-ws.data_ptr()) % 256
     dG = torch.as_tensor(dG, dtype=torch.complex128, device=sigma.device).reshape(survey.nrec, 6, nf)
@@ -431,11 +446,11 @@ def vjp(grid: Grid, survey: Survey, sigma, dG, ckpt_every: Optional[int] = None,
     n1, n2, n3 = grid.n
     grad = torch.empty((3, n3, n2, n1), dtype=torch.float64, device=sigma.device)
     s, keep = survey._c()
-    code = load_library().emm_gradient(
+    code = load_library().emm_gradient_stored(
         grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(dG2.data_ptr()), int(ckpt_every),
-        C.c_void_p(ptr), C.c_size_t(nbytes), C.c_void_p(rec.data_ptr()), C.c_void_p(grad.data_ptr()),
-        C.c_void_p(stream.cuda_stream))
-    _check(code, "emm_gradient")
+        int(stored_steps), C.c_void_p(ptr), C.c_size_t(nbytes), C.c_void_p(rec.data_ptr()),
+        C.c_void_p(grad.data_ptr()), C.c_void_p(stream.cuda_stream))
+    _check(code, "emm_gradient_stored")
     if check:
         v = C.c_int(0)
         _check(load_library().emm_status(C.c_void_p(ptr), C.byref(v), C.c_void_p(stream.cuda_stream)), "emm_status")

@@ -494,11 +494,14 @@ bool make_gathers(const AdjParams &a, Gathers *G) {
 
 // Byte layout of the gradient's extra workspace, after the forward one.
 struct AdjLayout {
-  size_t fwd, ck, state, nck, eh, ebytes, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
+  size_t fwd, ck, state, nck, eh, ebytes, first_stored, snap, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
       total;
 };
 
-AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
+// K: steps between checkpoints; S: a budget of steps whose E snapshots the
+// forward sweep keeps (whole checkpoint segments from the end of the run),
+// so that the reverse sweep need not recompute them.
+AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K, int S) {
   AdjLayout A{};
   const Layout L = plan(g, s);
   const FieldGeom fg = field_geom(g);
@@ -514,8 +517,12 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K) {
   A.state = L.sstride;                     // E, H and the CPML memory
   A.ebytes = L.H[0] - L.E[0];              // E only
   A.nck = nt > 0 ? static_cast<size_t>((nt + K - 1) / K) : 0;
-  A.ck = take(A.nck * A.state);
-  A.eh = take(static_cast<size_t>(K + 1) * A.ebytes);
+  // segments first_stored .. nck-1 keep E^{first_stored K} .. E^{nt} from the forward sweep
+  const size_t ns = std::min<size_t>(A.nck, static_cast<size_t>(S > 0 ? S : 0) / static_cast<size_t>(K));
+  A.first_stored = A.nck - ns;
+  A.ck = take(A.first_stored * A.state);
+  A.eh = take(A.first_stored > 0 ? static_cast<size_t>(K + 1) * A.ebytes : 0);
+  A.snap = take(ns > 0 ? (static_cast<size_t>(nt) - A.first_stored * K + 1) * A.ebytes : 0);
   for (int c = 0; c < 3; ++c) A.lamE[c] = take(cells * 4);
   for (int c = 0; c < 3; ++c) A.lamH[c] = take(cells * 4);
   for (int c = 0; c < 6; ++c) A.T[c] = take(cells * 4);
@@ -553,13 +560,14 @@ void transposed_rows(const Axis &ax, int rd, std::vector<float> &pT, std::vector
     }
 }
 
-int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int K, void *ws,
-                  size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs) {
+int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int K, int S,
+                  void *ws, size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (K < 1 || s->volume || s->src_kind != 0 || s->src_length > 0 || s->airwave || !grad || !sigma || !ws || (s->nrec > 0 && (!dG || !rec_out)))
     return EMM_EINVAL;
-  const AdjLayout A = adj_plan(g, s, K);
+  if (S < 0) return EMM_EINVAL;
+  const AdjLayout A = adj_plan(g, s, K, S);
   if (ws_bytes < A.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
   Prepared P;
   st = prepare_forward(g, s, sigma, ws, A.fwd, rec_out, nullptr, cs, &P);
@@ -568,12 +576,24 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const Layout &L = P.L;
   const int nt = s->nt, nf = s->nfreq, rd = g->rd;
 
-  // forward sweep with checkpoints; the receivers accumulate G on the way
+  // forward sweep with checkpoints, then, over the stored segments, every
+  // E snapshot; the receivers accumulate G on the way
   cudaError_t e = cudaSuccess;
+  const int base_step = static_cast<int>(A.first_stored) * K;
+  auto snap = [&](int n) { return base + A.snap + static_cast<size_t>(n - base_step) * A.ebytes; };
   for (int it0 = 0; it0 < nt && e == cudaSuccess; it0 += K) {
-    e = cudaMemcpyAsync(base + A.ck + static_cast<size_t>(it0 / K) * A.state, base + L.E[0], A.state,
-                        cudaMemcpyDeviceToDevice, cs);
-    if (e == cudaSuccess) e = run_steps(P, P.p, P.blocks, it0, std::min(it0 + K, nt), cs, nullptr);
+    const int it1 = std::min(it0 + K, nt);
+    if (it0 < base_step) {
+      e = cudaMemcpyAsync(base + A.ck + static_cast<size_t>(it0 / K) * A.state, base + L.E[0], A.state,
+                          cudaMemcpyDeviceToDevice, cs);
+      if (e == cudaSuccess) e = run_steps(P, P.p, P.blocks, it0, it1, cs, nullptr);
+      continue;
+    }
+    if (it0 == base_step) e = cudaMemcpyAsync(snap(it0), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+    for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
+      e = run_steps(P, P.p, P.blocks, it, it + 1, cs, nullptr);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(snap(it + 1), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+    }
   }
   if (e != cudaSuccess) return EMM_ECUDA;
   st = finalize_forward(P, s, rec_out, nullptr, cs);
@@ -664,22 +684,23 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const int M = 2 * rd, rec_threads = s->nrec * 6 * M * M * M;
   for (int seg = static_cast<int>(A.nck) - 1; seg >= 0 && e == cudaSuccess; --seg) {
     const int it0 = seg * K, it1 = std::min(it0 + K, nt);
-    e = cudaMemcpyAsync(base + L.E[0], base + A.ck + static_cast<size_t>(seg) * A.state, A.state,
-                        cudaMemcpyDeviceToDevice, cs);
-    for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
-      e = cudaMemcpyAsync(base + A.eh + static_cast<size_t>(it - it0) * A.ebytes, base + L.E[0], A.ebytes,
+    const bool stored = static_cast<size_t>(seg) >= A.first_stored;
+    // E snapshot of step n: kept by the forward sweep, or recomputed here
+    auto esnap = [&](int n) { return stored ? snap(n) : base + A.eh + static_cast<size_t>(n - it0) * A.ebytes; };
+    if (!stored) {
+      e = cudaMemcpyAsync(base + L.E[0], base + A.ck + static_cast<size_t>(seg) * A.state, A.state,
                           cudaMemcpyDeviceToDevice, cs);
-      if (e == cudaSuccess) e = run_steps(P, pr, blocks_r, it, it + 1, cs, nullptr);
+      for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
+        e = cudaMemcpyAsync(esnap(it), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+        if (e == cudaSuccess) e = run_steps(P, pr, blocks_r, it, it + 1, cs, nullptr);
+      }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(esnap(it1), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
     }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(base + A.eh + static_cast<size_t>(it1 - it0) * A.ebytes, base + L.E[0], A.ebytes,
-                          cudaMemcpyDeviceToDevice, cs);
     for (int it = it1 - 1; it >= it0 && e == cudaSuccess; --it) {
       for (int c = 0; c < 3; ++c) {
         const size_t ec = L.E[c] - L.E[0];
-        a.E0[c] = reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0) * A.ebytes + ec) + xs;
-        a.E1[c] =
-            reinterpret_cast<const float *>(base + A.eh + static_cast<size_t>(it - it0 + 1) * A.ebytes + ec) + xs;
+        a.E0[c] = reinterpret_cast<const float *>(esnap(it) + ec) + xs;
+        a.E1[c] = reinterpret_cast<const float *>(esnap(it + 1) + ec) + xs;
       }
       k_adj_h_pre<<<gpre, tpre, 0, cs>>>(a);
       GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
@@ -703,18 +724,29 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
 
 extern "C" {
 
-int emm_gradient_workspace_size(const emm_grid *g, const emm_survey *s, int ckpt_every, size_t *bytes) {
+int emm_gradient_stored_workspace_size(const emm_grid *g, const emm_survey *s, int ckpt_every, int stored_steps,
+                                       size_t *bytes) {
   const int st = emm::check_survey(g, s);
   if (st != EMM_OK) return st;
-  if (!bytes || ckpt_every < 1 || s->volume) return EMM_EINVAL;
-  *bytes = emm::adj_plan(g, s, ckpt_every).total;
+  if (!bytes || ckpt_every < 1 || stored_steps < 0 || s->volume) return EMM_EINVAL;
+  *bytes = emm::adj_plan(g, s, ckpt_every, stored_steps).total;
   return EMM_OK;
+}
+
+int emm_gradient_workspace_size(const emm_grid *g, const emm_survey *s, int ckpt_every, size_t *bytes) {
+  return emm_gradient_stored_workspace_size(g, s, ckpt_every, 0, bytes);
+}
+
+int emm_gradient_stored(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG,
+                        int ckpt_every, int stored_steps, void *ws, size_t ws_bytes, double *rec_out, double *grad,
+                        emm_stream stream) {
+  return emm::gradient_impl(g, s, sigma, dG, ckpt_every, stored_steps, ws, ws_bytes, rec_out, grad,
+                            reinterpret_cast<cudaStream_t>(stream));
 }
 
 int emm_gradient(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int ckpt_every,
                  void *ws, size_t ws_bytes, double *rec_out, double *grad, emm_stream stream) {
-  return emm::gradient_impl(g, s, sigma, dG, ckpt_every, ws, ws_bytes, rec_out, grad,
-                            reinterpret_cast<cudaStream_t>(stream));
+  return emm_gradient_stored(g, s, sigma, dG, ckpt_every, 0, ws, ws_bytes, rec_out, grad, stream);
 }
 
 }  // extern "C"
