@@ -17,15 +17,17 @@
 // Schedule: a forward sweep stores the whole state (fields and CPML memory)
 // every K steps; the reverse sweep, one checkpoint segment at a time,
 // recomputes the segment's E snapshots and then runs the adjoint steps
-// backwards.  One adjoint step, the transpose of one forward step:
-//   1. H update:  per-derivative adjoints T = -dt/mu0 lambda_H (CPML memory
-//      adjoints updated in the shell), then lambda_E += (D+)^T T
-//      (transposed-row gather);
-//   2. receivers: lambda += interpolation^T of Re(conj(v) norm f_n);
-//   3. gradient:  g += - lambda_E (E^{n+1} - E^n) / sigma (FP32 within a
-//      checkpoint segment, added into FP64 at its end);
-//   4. E update:  T = ie lambda_E (CPML in the shell), then
-//      lambda_H += (D-)^T T.
+// backwards.  One adjoint step, the transpose of one forward step, is three
+// launches:
+//   1. receivers: lambda += interpolation^T of Re(conj(v) norm f_n);
+//   2. H update transposed: lambda_E += (D+)^T T_H (a TMA-fed gather), T_H
+//      the per-derivative adjoints -dt/mu0 lambda_H formed with the CPML
+//      memory adjoints by the previous launch 3; its epilogue forms, from the
+//      final lambda_E, the gradient term g -= lambda_E (E^{n+1} - E^n) /
+//      sigma (FP32 within a checkpoint segment, added into FP64 at its end)
+//      and T_E = dt/eps lambda_E with the CPML;
+//   3. E update transposed: lambda_H += (D-)^T T_E; its epilogue forms T_H
+//      of the step before from the final lambda_H.
 // Finally the padded gradient is folded onto the interior samples the pads
 // replicate.  Adjoint fields are FP32 like the forward fields; the gradient
 // accumulates in FP64.
@@ -50,7 +52,7 @@ struct AdjParams {
   float inv_2w0dt;           // 1 / (2 omega0 dt): sigma = 2 omega0 dt / ie
   const float *ie[3];
   float *lamE[3], *lamH[3];  // adjoint fields (field layout)
-  float *T[6];               // per-derivative adjoints of the current half step (field layout)
+  float *TH[6], *TE[6];      // per-derivative adjoints of the H and the E half step (field layout)
   int *status;
   float *muE[6], *muH[6];    // adjoints of the CPML memory (psi layouts)
   int psx_hx[2], psx_wx[2], psx_far0[2];
@@ -92,18 +94,11 @@ __device__ __forceinline__ size_t fid(const AdjParams &a, int i, int j, int k) {
 // the sample; g is the scaled adjoint with the term's sign (-dt/mu0
 // lambda_H for the H update, dt/eps lambda_E for the E update).  T[2c+t]
 // belongs to component c and its term t (0: derivative along c+1, 1: along
-// c+2).  A pointwise pass writes T; a gather then applies the transposed FD
-// rows to it.
+// c+2).  The epilogue of a gather forms T for the other half step (it is
+// pointwise); the next gather applies the transposed FD rows to it.
 
-// Pre-pass geometry: a thread owns 4 x-adjacent samples (a quad starting on
-// a 16-byte boundary of the field rows); quads with no CPML sample and every
-// sample updated take a float4 path, the others a per-sample one.
-__device__ __forceinline__ bool quad_of_pre(const AdjParams &a, int *idx) {
-  idx[0] = a.org[0] + static_cast<int>(blockIdx.x * 128 + threadIdx.x * 4);
-  idx[1] = static_cast<int>(blockIdx.y * 4 + threadIdx.y);
-  idx[2] = static_cast<int>(blockIdx.z);
-  return idx[0] + 3 >= 0 && idx[0] < a.np[0] && idx[1] < a.np[1];
-}
+// A quad is 4 x-adjacent samples starting on a 16-byte boundary of the
+// field rows.
 __device__ __forceinline__ float4 ldf4(const float *p, size_t id) { return *reinterpret_cast<const float4 *>(p + id); }
 __device__ __forceinline__ void stf4(float *p, size_t id, const float4 &v) { *reinterpret_cast<float4 *>(p + id) = v; }
 __device__ __forceinline__ float4 scl4(float c, const float4 &v) { return make_float4(c * v.x, c * v.y, c * v.z, c * v.w); }
@@ -132,7 +127,7 @@ __device__ __forceinline__ void set_lane(float4 &v, int e, float x) {
 // float4); lanes outside the slab or the update region keep their memory
 // adjoint and get T = 0 where the forward loop does not update them.
 template <int KIND>
-__device__ void pre_quad(const AdjParams &a, const int *idx) {
+__device__ void pre_quad(const AdjParams &a, const int *idx, const float4 (&lam4)[3]) {
   const int R = a.rd, nb = a.nb, i0 = idx[0], j = idx[1], k = idx[2];
   const size_t id = fid(a, i0, j, k);
   const int lo = KIND == 0 ? R - 1 : R;  // first sample with every FD row
@@ -162,10 +157,9 @@ __device__ void pre_quad(const AdjParams &a, const int *idx) {
     const int p = (c + 1) % 3, q = (c + 2) % 3;
     float4 g;
     if (KIND == 0) {
-      g = scl4(-a.kappa, ldf4(a.lamH[c], id));
+      g = scl4(-a.kappa, lam4[c]);
     } else {
-      const float4 lam = ldf4(a.lamE[c], id), ie = ldf4(a.ie[c], id), e0 = ldf4(a.E0[c], id),
-                   e1 = ldf4(a.E1[c], id);
+      const float4 lam = lam4[c], ie = ldf4(a.ie[c], id), e0 = ldf4(a.E0[c], id), e1 = ldf4(a.E1[c], id);
       float4 gs = ldf4(a.gseg[c], id);
       const float cg = a.inv_2w0dt;
       gs.x -= lam.x * (e1.x - e0.x) * ie.x * cg;
@@ -205,28 +199,47 @@ __device__ void pre_quad(const AdjParams &a, const int *idx) {
         }
         stf4(mu, mi, m4);
       }
-      stf4(a.T[2 * c + term], id, t);
+      stf4(KIND == 0 ? a.TH[2 * c + term] : a.TE[2 * c + term], id, t);
     }
   }
 }
 
-// 1a. T[2c+t] at the H_c samples from lambda_H.
-__global__ void k_adj_h_pre(const AdjParams a) {
-  int idx[3];
-  if (!quad_of_pre(a, idx)) return;
-  // H samples with no half-sample slab and every D+ row: nb .. np-2-nb
-  const int hi[3] = {a.np[0] - 2 - a.nb, a.np[1] - 2 - a.nb, a.np[2] - 2 - a.nb};
-  if (quad_plain(a, idx, a.nb, hi)) {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float4 g = scl4(-a.kappa, ldf4(a.lamH[c], id));
-      stf4(a.T[2 * c], id, g);
-      stf4(a.T[2 * c + 1], id, scl4(-1.f, g));
-    }
+// The per-derivative adjoints of one quad from its final lambda values:
+// KIND 0, T_H at the H_c samples from lambda_H (for the H update of the
+// step before); KIND 1, the gradient term of this step, g_seg_e -=
+// lambda_E_e (E1_e - E0_e) ie_e / (2 omega0 dt), and T_E at the E_e samples
+// from lambda_E.  Quads inside the CPML-free region where every sample is
+// updated take a float4 path without masks; the others pre_quad.
+template <int KIND>
+__device__ __forceinline__ void quad_terms(const AdjParams &a, const int *idx, const float4 (&lam)[3]) {
+  // CPML-free samples with every FD row: nb .. np-2-nb (H) or nb .. np-1-nb (E)
+  const int d = KIND == 0 ? 2 : 1;
+  const int hi[3] = {a.np[0] - d - a.nb, a.np[1] - d - a.nb, a.np[2] - d - a.nb};
+  if (!quad_plain(a, idx, a.nb, hi)) {
+    pre_quad<KIND>(a, idx, lam);
     return;
   }
-  pre_quad<0>(a, idx);
+  const size_t id = fid(a, idx[0], idx[1], idx[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float4 g;
+    if (KIND == 0) {
+      g = scl4(-a.kappa, lam[c]);
+    } else {
+      const float4 ie = ldf4(a.ie[c], id), e0 = ldf4(a.E0[c], id), e1 = ldf4(a.E1[c], id);
+      float4 gs = ldf4(a.gseg[c], id);
+      const float cg = a.inv_2w0dt;
+      gs.x -= lam[c].x * (e1.x - e0.x) * ie.x * cg;
+      gs.y -= lam[c].y * (e1.y - e0.y) * ie.y * cg;
+      gs.z -= lam[c].z * (e1.z - e0.z) * ie.z * cg;
+      gs.w -= lam[c].w * (e1.w - e0.w) * ie.w * cg;
+      stf4(a.gseg[c], id, gs);
+      g = make_float4(ie.x * lam[c].x, ie.y * lam[c].y, ie.z * lam[c].z, ie.w * lam[c].w);
+    }
+    float *const *T = KIND == 0 ? a.TH : a.TE;
+    stf4(T[2 * c], id, g);
+    stf4(T[2 * c + 1], id, scl4(-1.f, g));
+  }
 }
 
 // 2. Receivers at step n: lambda_c[stencil] += w * Re(sum_f cw f_n).
@@ -247,36 +260,6 @@ __global__ void k_adj_receivers(const AdjParams a, int n) {
   const double val = wt[q1] * wt[M + q2] * wt[2 * M + q3] * g;
   float *F = c < 3 ? a.lamE[c] : a.lamH[c - 3];
   atomicAdd(F + fid(a, st[0] + q1, st[1] + q2, st[2] + q3), static_cast<float>(val));
-}
-
-// 3. The gradient term of this step, g_seg_e -= lambda_E_e (E1_e - E0_e) ie_e
-// / (2 omega0 dt) (lambda_E is final for the step here), and T[2e+t] at the
-// E_e samples from lambda_E.
-__global__ void k_adj_e_pre(const AdjParams a) {
-  int idx[3];
-  if (!quad_of_pre(a, idx)) return;
-  // E samples with no integer-sample slab and every D- row: nb .. np-1-nb
-  const int hi[3] = {a.np[0] - 1 - a.nb, a.np[1] - 1 - a.nb, a.np[2] - 1 - a.nb};
-  if (quad_plain(a, idx, a.nb, hi)) {
-    const size_t id = fid(a, idx[0], idx[1], idx[2]);
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const float4 lam = ldf4(a.lamE[e], id), ie = ldf4(a.ie[e], id), e0 = ldf4(a.E0[e], id),
-                   e1 = ldf4(a.E1[e], id);
-      float4 gs = ldf4(a.gseg[e], id);
-      const float c = a.inv_2w0dt;
-      gs.x -= lam.x * (e1.x - e0.x) * ie.x * c;
-      gs.y -= lam.y * (e1.y - e0.y) * ie.y * c;
-      gs.z -= lam.z * (e1.z - e0.z) * ie.z * c;
-      gs.w -= lam.w * (e1.w - e0.w) * ie.w * c;
-      stf4(a.gseg[e], id, gs);
-      const float4 g = make_float4(ie.x * lam.x, ie.y * lam.y, ie.z * lam.z, ie.w * lam.w);
-      stf4(a.T[2 * e], id, g);
-      stf4(a.T[2 * e + 1], id, scl4(-1.f, g));
-    }
-    return;
-  }
-  pre_quad<1>(a, idx);
 }
 
 // ---- 1b / 4. The transposed FD gathers, TMA-fed --------------------------
@@ -399,6 +382,11 @@ __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __gr
     if (i + 3 < a.np[0]) o4[o].w += acc[3];
     *reinterpret_cast<float4 *>(out[o] + id) = o4[o];
   }
+  // epilogue: the pointwise terms that read the lambda just completed
+  // (lambda_E of this step after the receivers, or lambda_H for the step
+  // before), owned by this quad
+  const int idx[3] = {i, j, k};
+  quad_terms<KIND == 0 ? 1 : 0>(a, idx, o4);
 }
 
 // End of a checkpoint segment: g_pad += g_seg (FP64), g_seg = 0.
@@ -466,7 +454,7 @@ bool make_map3(CUtensorMap *map, const float *base, const AdjParams &a, int bx, 
 
 // The two gathers of one adjoint step, for order R.
 struct Gathers {
-  GMaps maps;
+  GMaps maps0, maps1;  // T_H for the lambda_E gather, T_E for the lambda_H gather
   dim3 grid;
   size_t smem;
   void (*g0)(AdjParams, GMaps);
@@ -479,7 +467,7 @@ bool make_gathers(const AdjParams &a, Gathers *G) {
     const int bx = (t == 3 || t == 4) ? GX + 2 * GH : GX;
     const int by = (t == 0 || t == 5) ? GY + 2 * R : GY;
     const int bz = (t == 1 || t == 2) ? GZ + 2 * R : GZ;
-    ok = make_map3(&G->maps.m[t], a.T[t], a, bx, by, bz);
+    ok = make_map3(&G->maps0.m[t], a.TH[t], a, bx, by, bz) && make_map3(&G->maps1.m[t], a.TE[t], a, bx, by, bz);
   }
   G->grid = dim3((a.np[0] - a.org[0] + GX - 1) / GX, (a.np[1] - a.org[1] + GY - 1) / GY, (a.np[2] + GZ - 1) / GZ);
   G->smem = GTiles<R>::FLOATS * 4 + 128 + 16;
@@ -494,7 +482,7 @@ bool make_gathers(const AdjParams &a, Gathers *G) {
 
 // Byte layout of the gradient's extra workspace, after the forward one.
 struct AdjLayout {
-  size_t fwd, ck, state, nck, eh, ebytes, first_stored, snap, lamE[3], lamH[3], T[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
+  size_t fwd, ck, state, nck, eh, ebytes, first_stored, snap, lamE[3], lamH[3], TH[6], TE[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
       total;
 };
 
@@ -525,7 +513,8 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K, int S) {
   A.snap = take(ns > 0 ? (static_cast<size_t>(nt) - A.first_stored * K + 1) * A.ebytes : 0);
   for (int c = 0; c < 3; ++c) A.lamE[c] = take(cells * 4);
   for (int c = 0; c < 3; ++c) A.lamH[c] = take(cells * 4);
-  for (int c = 0; c < 6; ++c) A.T[c] = take(cells * 4);
+  for (int c = 0; c < 6; ++c) A.TH[c] = take(cells * 4);
+  for (int c = 0; c < 6; ++c) A.TE[c] = take(cells * 4);
   for (int c = 0; c < 6; ++c) A.muE[c] = take((c < 5 ? L.psiE[c + 1] : L.psiH[0]) - L.psiE[c]);
   for (int c = 0; c < 6; ++c) A.muH[c] = take((c < 5 ? L.psiH[c + 1] : L.E[0] + L.sstride) - L.psiH[c]);
   for (int c = 0; c < 3; ++c) A.gpad[c] = take(cells * 8);
@@ -626,7 +615,8 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
     a.gseg[c] = reinterpret_cast<float *>(base + A.gseg[c]) + xs;
   }
   for (int c = 0; c < 6; ++c) {
-    a.T[c] = reinterpret_cast<float *>(base + A.T[c]) + xs;
+    a.TH[c] = reinterpret_cast<float *>(base + A.TH[c]) + xs;
+    a.TE[c] = reinterpret_cast<float *>(base + A.TE[c]) + xs;
     const int shift = psi_axis(c) == 0 ? 0 : xs;
     a.muE[c] = reinterpret_cast<float *>(base + A.muE[c]) + shift;
     a.muH[c] = reinterpret_cast<float *>(base + A.muH[c]) + shift;
@@ -674,7 +664,6 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const int grid_cells = P.sms * 8;
   const dim3 tb(32, 8, 1), grid3((P.p.np[0] + 31) / 32, (P.p.np[1] + 7) / 8, P.p.np[2]);
   // pre passes: 32 x 4 threads, 4 x-adjacent samples each, over x from org[0]
-  const dim3 tpre(32, 4, 1), gpre((P.p.np[0] - P.p.org[0] + 127) / 128, (P.p.np[1] + 3) / 4, P.p.np[2]);
   Gathers GA{};
   const bool gok = rd == 1 ? make_gathers<1>(a, &GA)
                    : rd == 2 ? make_gathers<2>(a, &GA)
@@ -702,11 +691,13 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
         a.E0[c] = reinterpret_cast<const float *>(esnap(it) + ec) + xs;
         a.E1[c] = reinterpret_cast<const float *>(esnap(it + 1) + ec) + xs;
       }
-      k_adj_h_pre<<<gpre, tpre, 0, cs>>>(a);
-      GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
+      // T_H of this step came from the lambda_H gather of the step after it
+      // (zero for the last step); the receivers add to lambda before the
+      // lambda_E gather, whose epilogue forms T_E and the gradient term; the
+      // lambda_H gather's epilogue forms T_H of the step before
       if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
-      k_adj_e_pre<<<gpre, tpre, 0, cs>>>(a);
-      GA.g1<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps);
+      GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps0);
+      GA.g1<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps1);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
