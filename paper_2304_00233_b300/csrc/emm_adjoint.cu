@@ -244,6 +244,8 @@ __device__ __forceinline__ void quad_terms(const AdjParams &a, const int *idx, c
 
 // 2. Receivers at step n: lambda_c[stencil] += w * Re(sum_f cw f_n).
 __global__ void k_adj_receivers(const AdjParams a, int n) {
+  wait_prior_grid();
+  allow_next_launch();
   const int M = 2 * a.rd, M3 = M * M * M;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.nrec * 6 * M3) return;
@@ -288,6 +290,8 @@ struct GMaps {
 
 template <int R, int KIND>
 __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __grid_constant__ GMaps tm) {
+  wait_prior_grid();
+  allow_next_launch();
   using G = GTiles<R>;
   constexpr int M = 2 * R, OFF = KIND == 0 ? -R : 1 - R;
   extern __shared__ unsigned char smem_raw[];
@@ -387,6 +391,16 @@ __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __gr
   // before), owned by this quad
   const int idx[3] = {i, j, k};
   quad_terms<KIND == 0 ? 1 : 0>(a, idx, o4);
+}
+
+// E snapshots: a streaming copy of the three E arrays (float4), launched as a
+// programmatic dependent like the steps around it.
+__global__ void k_copy16(const float4 *src, float4 *dst, size_t n) {
+  wait_prior_grid();
+  allow_next_launch();
+  for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x)
+    dst[t] = src[t];
 }
 
 // End of a checkpoint segment: g_pad += g_seg (FP64), g_seg = 0.
@@ -570,6 +584,12 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   cudaError_t e = cudaSuccess;
   const int base_step = static_cast<int>(A.first_stored) * K;
   auto snap = [&](int n) { return base + A.snap + static_cast<size_t>(n - base_step) * A.ebytes; };
+  // the E arrays (A.ebytes, a multiple of 256) from the state into a snapshot
+  const dim3 cgrid(static_cast<unsigned>(4 * P.sms));
+  auto copy_e = [&](unsigned char *dst) {
+    return launch_dependent(k_copy16, cgrid, dim3(256), 0, cs, reinterpret_cast<const float4 *>(base + L.E[0]),
+                            reinterpret_cast<float4 *>(dst), A.ebytes / 16);
+  };
   for (int it0 = 0; it0 < nt && e == cudaSuccess; it0 += K) {
     const int it1 = std::min(it0 + K, nt);
     if (it0 < base_step) {
@@ -578,10 +598,10 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
       if (e == cudaSuccess) e = run_steps(P, P.p, P.blocks, it0, it1, cs, nullptr);
       continue;
     }
-    if (it0 == base_step) e = cudaMemcpyAsync(snap(it0), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+    if (it0 == base_step) e = copy_e(snap(it0));
     for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
       e = run_steps(P, P.p, P.blocks, it, it + 1, cs, nullptr);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(snap(it + 1), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+      if (e == cudaSuccess) e = copy_e(snap(it + 1));
     }
   }
   if (e != cudaSuccess) return EMM_ECUDA;
@@ -680,10 +700,10 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
       e = cudaMemcpyAsync(base + L.E[0], base + A.ck + static_cast<size_t>(seg) * A.state, A.state,
                           cudaMemcpyDeviceToDevice, cs);
       for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
-        e = cudaMemcpyAsync(esnap(it), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+        e = copy_e(esnap(it));
         if (e == cudaSuccess) e = run_steps(P, pr, blocks_r, it, it + 1, cs, nullptr);
       }
-      if (e == cudaSuccess) e = cudaMemcpyAsync(esnap(it1), base + L.E[0], A.ebytes, cudaMemcpyDeviceToDevice, cs);
+      if (e == cudaSuccess) e = copy_e(esnap(it1));
     }
     for (int it = it1 - 1; it >= it0 && e == cudaSuccess; --it) {
       for (int c = 0; c < 3; ++c) {
@@ -695,10 +715,12 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
       // (zero for the last step); the receivers add to lambda before the
       // lambda_E gather, whose epilogue forms T_E and the gradient term; the
       // lambda_H gather's epilogue forms T_H of the step before
-      if (rec_threads > 0) k_adj_receivers<<<(rec_threads + kThreads - 1) / kThreads, kThreads, 0, cs>>>(a, it);
-      GA.g0<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps0);
-      GA.g1<<<GA.grid, GT, GA.smem, cs>>>(a, GA.maps1);
-      e = cudaGetLastError();
+      if (rec_threads > 0)
+        e = launch_dependent(k_adj_receivers, dim3((rec_threads + kThreads - 1) / kThreads), dim3(kThreads), 0, cs,
+                             a, it);
+      if (e == cudaSuccess) e = launch_dependent(GA.g0, GA.grid, dim3(GT), GA.smem, cs, a, GA.maps0);
+      if (e == cudaSuccess) e = launch_dependent(GA.g1, GA.grid, dim3(GT), GA.smem, cs, a, GA.maps1);
+      if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
       k_adj_flush<<<grid3, tb, 0, cs>>>(a);
