@@ -421,13 +421,15 @@ def main():
         grad_ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
         fwd_ms = 1e3 * elapsed / args.steps
         # the same with the E snapshots of as many final steps as the free
-        # device memory holds (less 16 GB), which the reverse sweep then does
-        # not recompute
+        # device memory holds (less 6 GB for the outputs and the allocator),
+        # which the reverse sweep then does not recompute
+        torch.cuda.empty_cache()
         free, _ = torch.cuda.mem_get_info()
         snap = emm.snapshot_bytes(grid, survey, ck)
-        base_ws = emm.gradient_workspace_size(grid, survey, ck)
-        stored = int(max(0, free - base_ws - (16 << 30)) // snap)
-        stored = min(stored, nt) // ck * ck
+        room = free - (6 << 30)
+        stored = min(nt, int(max(0, room) // snap)) // ck * ck
+        while stored > 0 and emm.gradient_workspace_size(grid, survey, ck, stored) > room:
+            stored -= ck
         emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, stored_steps=stored, check=False)
         torch.cuda.synchronize()
         g0.record(stream)

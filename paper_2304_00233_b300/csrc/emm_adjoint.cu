@@ -523,7 +523,7 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K, int S) {
   const size_t ns = std::min<size_t>(A.nck, static_cast<size_t>(S > 0 ? S : 0) / static_cast<size_t>(K));
   A.first_stored = A.nck - ns;
   A.ck = take(A.first_stored * A.state);
-  A.eh = take(A.first_stored > 0 ? static_cast<size_t>(K + 1) * A.ebytes : 0);
+  A.eh = take(A.first_stored > 0 ? static_cast<size_t>(K) * A.ebytes : 0);  // E^{it0+1} .. E^{it0+K}
   A.snap = take(ns > 0 ? (static_cast<size_t>(nt) - A.first_stored * K + 1) * A.ebytes : 0);
   for (int c = 0; c < 3; ++c) A.lamE[c] = take(cells * 4);
   for (int c = 0; c < 3; ++c) A.lamH[c] = take(cells * 4);
@@ -590,6 +590,18 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
     return launch_dependent(k_copy16, cgrid, dim3(256), 0, cs, reinterpret_cast<const float4 *>(base + L.E[0]),
                             reinterpret_cast<float4 *>(dst), A.ebytes / 16);
   };
+  // one step from the E arrays at src to those at dst (snapshot-shaped
+  // blocks, src == nullptr for the state's own arrays): the E half-step
+  // writes E^{n+1} there and the rest of the step reads it there
+  auto step_into = [&](const DevParams &p0, dim3 blocks, int it, unsigned char *src, unsigned char *dst) {
+    DevParams q = p0;
+    for (int c = 0; c < 3; ++c) {
+      const size_t ec = L.E[c] - L.E[0];
+      if (src) q.E[c] = reinterpret_cast<float *>(src + ec) + P.fg.xshift;
+      q.Eout[c] = reinterpret_cast<float *>(dst + ec) + P.fg.xshift;
+    }
+    return run_steps(P, q, blocks, it, it + 1, cs, nullptr);
+  };
   for (int it0 = 0; it0 < nt && e == cudaSuccess; it0 += K) {
     const int it1 = std::min(it0 + K, nt);
     if (it0 < base_step) {
@@ -599,10 +611,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
       continue;
     }
     if (it0 == base_step) e = copy_e(snap(it0));
-    for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
-      e = run_steps(P, P.p, P.blocks, it, it + 1, cs, nullptr);
-      if (e == cudaSuccess) e = copy_e(snap(it + 1));
-    }
+    for (int it = it0; it < it1 && e == cudaSuccess; ++it) e = step_into(P.p, P.blocks, it, snap(it), snap(it + 1));
   }
   if (e != cudaSuccess) return EMM_ECUDA;
   st = finalize_forward(P, s, rec_out, nullptr, cs);
@@ -695,15 +704,14 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
     const int it0 = seg * K, it1 = std::min(it0 + K, nt);
     const bool stored = static_cast<size_t>(seg) >= A.first_stored;
     // E snapshot of step n: kept by the forward sweep, or recomputed here
-    auto esnap = [&](int n) { return stored ? snap(n) : base + A.eh + static_cast<size_t>(n - it0) * A.ebytes; };
+    // from the checkpoint (whose leading bytes are the E arrays of step it0)
+    unsigned char *ck = base + A.ck + static_cast<size_t>(seg) * A.state;
+    auto esnap = [&](int n) {
+      return stored ? snap(n) : n == it0 ? ck : base + A.eh + static_cast<size_t>(n - it0 - 1) * A.ebytes;
+    };
     if (!stored) {
-      e = cudaMemcpyAsync(base + L.E[0], base + A.ck + static_cast<size_t>(seg) * A.state, A.state,
-                          cudaMemcpyDeviceToDevice, cs);
-      for (int it = it0; it < it1 && e == cudaSuccess; ++it) {
-        e = copy_e(esnap(it));
-        if (e == cudaSuccess) e = run_steps(P, pr, blocks_r, it, it + 1, cs, nullptr);
-      }
-      if (e == cudaSuccess) e = copy_e(esnap(it1));
+      e = cudaMemcpyAsync(base + L.E[0], ck, A.state, cudaMemcpyDeviceToDevice, cs);
+      for (int it = it0; it < it1 && e == cudaSuccess; ++it) e = step_into(pr, blocks_r, it, esnap(it), esnap(it + 1));
     }
     for (int it = it1 - 1; it >= it0 && e == cudaSuccess; --it) {
       for (int c = 0; c < 3; ++c) {

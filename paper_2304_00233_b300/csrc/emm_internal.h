@@ -92,6 +92,8 @@ struct DevParams {
   float2 *air_T, *air_F, *air_U;
   float dt_mu;      // dt / mu0
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
+  float *Eout[3];            // set for a one-step run: the E half-step writes E^{n+1}
+                             // here (same layout) and leaves E[] as it was
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
   float *psiE[6];            // CPML memory of curl H terms (E update)
   float *psiH[6];            // CPML memory of curl E terms (H update)

@@ -571,8 +571,8 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
 }
 
 // CONV: a convergence run (corner DTFT, and every launch returns at once
-// after the stop).
-template <int R, bool MULTI, bool CONV>
+// after the stop).  OUT: E^{n+1} goes to p.Eout (E^n stays where it is).
+template <int R, bool MULTI, bool CONV, bool OUT>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
   const Quad u = quad_of(o);
-  const Fields f = fields_of<MULTI>(p, o.src);
+  Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
   // this thread's own samples, loaded while the copies are in flight
@@ -602,6 +602,7 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
   for (int a = 0; a < 3; ++a) {
     e[a] = live ? *reinterpret_cast<const float4 *>(f.E[a] + id) : float4{};
     w[a] = live ? __ldg(reinterpret_cast<const float4 *>(p.ie[a] + id)) : float4{};
+    if (OUT) f.E[a] = p.Eout[a];  // the whole quad is stored, so Eout gets every sample
   }
   const SrcDev *sd = p.srcs + o.src;
   const float *jw = p.jw + static_cast<size_t>(o.src) * 3 * (2 * R) * (2 * R) * (2 * R);
@@ -1273,13 +1274,19 @@ cudaError_t air_step(const DevParams &p, cudaStream_t st) {
   return e;
 }
 
-template <int R, bool MULTI, bool CONV>
+// OUT: one step whose E^{n+1} goes to p.Eout; the launches after the E
+// half-step see it there.
+template <int R, bool MULTI, bool CONV, bool OUT = false>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
+  if (OUT && (MULTI || CONV || n1 - n0 != 1)) return cudaErrorInvalidValue;
+  DevParams q = p;
+  if (OUT)
+    for (int a = 0; a < 3; ++a) q.E[a] = p.Eout[a];
   TmaSet tE{}, tH{};
-  if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, p.E, p)) return cudaErrorInvalidValue;
+  if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, q.E, p)) return cudaErrorInvalidValue;
   const size_t sb = smem_bytes<R>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_update_E<R, MULTI, CONV, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sb));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_update_H<R, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1294,15 +1301,15 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    e = launch_dependent(k_update_E<R, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tE, n);
+    e = launch_dependent(k_update_E<R, MULTI, CONV, OUT>, blocks, dim3(NT), sb, st, p, tE, n);
     if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
-      e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, p, n);
-    if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(p, st);
-    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, p, n);
+      e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, q, n);
+    if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(q, st);
+    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, q, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV>, blocks, dim3(NT), sb, st, p, tH, n);
-    if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, p, n);
-    if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(p, st);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV>, blocks, dim3(NT), sb, st, q, tH, n);
+    if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, q, n);
+    if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(q, st);
     if (timed) {
       cudaEventRecord(te->ev[used + 2], st);
       used += 3;
@@ -1662,9 +1669,11 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
-// The launch variants of one order: one transmitter; a batch; a convergence run.
+// The launch variants of one order: one transmitter; a batch; a convergence
+// run; one step into another E buffer.
 template <int R>
 cudaError_t run_order(const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs, StepEvents *te) {
+  if (p.Eout[0]) return launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te);
   if (p.nsrc > 1) return launch_steps<R, true, false>(p, n0, n1, blocks, cs, te);
   if (p.corner) return launch_steps<R, false, true>(p, n0, n1, blocks, cs, te);
   return launch_steps<R, false, false>(p, n0, n1, blocks, cs, te);
