@@ -235,6 +235,69 @@ def run_reference(args, rank, world):
     return 0
 
 
+def gradient_survey_line(emm, torch, stream, job_max):
+    """Least-squares misfit gradient of the 8-transmitter gradient survey
+    (192 x 192 x 128 NU grid): observed data from the model with the
+    resistor plus 2 % noise (not timed), then the misfit and its gradient
+    with respect to the cell sigma_h, sigma_v at the model without it, with
+    the E snapshots of as many final steps as the free device memory holds;
+    against one forward solve per transmitter on the same grid."""
+    import dataclasses
+    wl = W.gradient_survey(with_resistor=False)
+    obs = W.gradient_survey(with_resistor=True)
+    grid = emm.grid_for(wl)
+    smin = float(obs.sigma.min())
+    dt, _, _ = grid.time_step(smin, wl.omega0)
+    nt = int(np.ceil(wl.t_max / dt))
+    survey = emm.survey_for(wl, nt=nt, sigma_min=smin)
+    pos = W.GRADIENT_SOURCES
+    sig_obs = torch.from_numpy(obs.sigma.astype(np.float32)).cuda()
+    G_obs, bwork = emm.forward_batch(grid, survey, sig_obs, pos)
+    d = G_obs.cpu().numpy() * W.observed_noise(G_obs.shape)
+    del bwork, sig_obs, G_obs
+    sh = torch.from_numpy(wl.sigma_h).cuda()
+    sv = torch.from_numpy(wl.sigma_v).cuda()
+    sigma = emm.stagger_sigma(grid, sh, sv)
+    work = emm.Workspace(grid, survey)
+    emm.forward_async(grid, survey, sigma, work)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    emm.forward_async(grid, survey, sigma, work)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    assert emm.status(work) == emm.EMM_OK
+    fwd_ms = job_max(f0.elapsed_time(f1) / 1e3) * 1e3
+    del work
+    ck = max(1, int(round(nt ** 0.5)))
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    room = free - (6 << 30)
+    snap = emm.snapshot_bytes(grid, survey, ck)
+    stored = min(nt, int(max(0, room) // snap)) // ck * ck
+    while stored > 0 and emm.gradient_workspace_size(grid, survey, ck, stored) > room:
+        stored -= ck
+    # warm-up on a short run of the same problem
+    emm.survey_misfit_gradient(grid, dataclasses.replace(survey, nt=2 * ck), sh, sv, pos[:1], d[:1],
+                               ckpt_every=ck)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    misfit, gh, gv, _ = emm.survey_misfit_gradient(grid, survey, sh, sv, pos, d, ckpt_every=ck,
+                                                   stored_steps=stored)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
+    ok = bool(torch.isfinite(gh).all().item() and torch.isfinite(gv).all().item())
+    return {"workload": "gradient_survey_192x192x128", "nsrc": len(pos), "timesteps_per_solve": nt,
+            "cells": grid.cells, "ms": ms, "forward_ms": fwd_ms, "ratio_to_forward": ms / (len(pos) * fwd_ms),
+            "ckpt_every": ck, "stored_steps": stored, "snapshot_gb": stored * snap / 1e9,
+            "misfit": misfit.item(), "finite": ok,
+            "what": "emm_stagger_sigma, then per transmitter emm_misfit_gradient (forward sweep, residual "
+                    "of the noisy resistor-model data, adjoint sweep) and emm_stagger_sigma_adjoint into "
+                    "the sigma_h, sigma_v gradients; ratio against one forward solve per transmitter"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,6 +308,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
+    ap.add_argument("--no-gradient-survey", action="store_true",
+                    help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid (about a minute)")
     ap.add_argument("--no-airwave", action="store_true",
                     help="skip the air-boundary line (uniform-xy marine model with and without air on top)")
     ap.add_argument("--batch", type=int, default=8,
@@ -445,6 +510,8 @@ def main():
                                     "of the last stored_steps steps in device memory, recomputation of the "
                                     "earlier segments and the adjoint sweep, one cotangent of all receiver "
                                     "data; recompute_only: every segment recomputed (emm_gradient)"}
+    if not args.no_gradient_survey:
+        line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W.WORKLOADS[args.workload]())
     if rank == 0:

@@ -305,6 +305,58 @@ int emm_gradient_stored(const emm_grid *grid, const emm_survey *survey, const fl
                         int ckpt_every, int stored_steps, void *ws, size_t ws_bytes, double *rec_out,
                         double *grad, emm_stream stream);
 
+/* Least-squares data misfit of one transmitter and its gradient, in one
+ * call (no separate forward solve for the residual):
+ *     misfit += 1/2 sum_{r,c,f} w[r][c][f] |G[r][c][f] - d_obs[r][c][f]|^2
+ *     grad    = d/d sigma of that misfit
+ * The forward sweep gives G; a device kernel forms the weighted residual
+ * w (G - d_obs) and adds the misfit (a fixed-order reduction, so repeated
+ * calls are reproducible); the residual is the cotangent of the adjoint
+ * sweep, i.e. the result is emm_gradient_stored with dG = w (G - d_obs).
+ * The paper names inversion as future work; this is the data-fit term an
+ * inversion of its Green's functions minimises.
+ *   d_obs     device double [nrec][6][nfreq][2] observed data (re, im).
+ *   weight    device double [nrec][6][nfreq], non-negative, or NULL for
+ *             all ones (a zero weight drops a datum, e.g. a channel not
+ *             recorded).
+ *   misfit    device double; the misfit is ADDED to it, so calls for the
+ *             transmitters of a survey accumulate their sum.
+ * Workspace: emm_gradient_stored_workspace_size with the same ckpt_every
+ * and stored_steps.  Other arguments, asynchrony and errors as
+ * emm_gradient_stored; EMM_EINVAL if d_obs or misfit is NULL. */
+int emm_misfit_gradient(const emm_grid *grid, const emm_survey *survey, const float *sigma,
+                        const double *d_obs, const double *weight, int ckpt_every, int stored_steps,
+                        void *ws, size_t ws_bytes, double *rec_out, double *misfit, double *grad,
+                        emm_stream stream);
+
+/* Staggered conductivity from cell values (Sec. 3.6).  Cells lie between
+ * adjacent interior nodes: [n3-1][n2-1][n1-1] arrays, x fastest, of the
+ * horizontal (sigma_h) and vertical (sigma_v) conductivity.  sigma_xx at the
+ * E_x sample (x_{i+1/2}, y_j, z_k) is the mean of sigma_h over the cells
+ * around that edge in y and z (cells j-1, j and k-1, k, clamped to the
+ * model), weighted by their y-z face areas dy dz; along x the sample takes
+ * cell min(i, n1-2).  sigma_yy likewise (x and z neighbours), sigma_zz the
+ * same mean of sigma_v over the x and y neighbours.  The map is linear.
+ *   ws        device scratch of emm_stagger_workspace_size bytes, 8-byte
+ *             aligned (the interior cell widths are copied there).
+ *   sigma_h, sigma_v  device double [n3-1][n2-1][n1-1].
+ *   sigma     device float [3][n3][n2][n1] output, as emm_forward takes it
+ *             (each mean computed in FP64, rounded once).
+ * Asynchronous on `stream`.  EMM_EINVAL on NULL arguments, EMM_EWORKSPACE
+ * on a short or misaligned ws, EMM_ECUDA on a launch error. */
+int emm_stagger_workspace_size(const emm_grid *grid, size_t *bytes);
+int emm_stagger_sigma(const emm_grid *grid, const double *sigma_h, const double *sigma_v, void *ws,
+                      size_t ws_bytes, float *sigma, emm_stream stream);
+
+/* Transpose of emm_stagger_sigma: carries a gradient with respect to the
+ * staggered conductivity, device double [3][n3][n2][n1] (emm_gradient's
+ * output), to the cells, and ADDS it to grad_h and grad_v (device double
+ * [n3-1][n2-1][n1-1]), so the transmitters of a survey accumulate.  Each
+ * cell gathers its own terms in a fixed order (deterministic).  Arguments
+ * and errors as emm_stagger_sigma. */
+int emm_stagger_sigma_adjoint(const emm_grid *grid, const double *grad, void *ws, size_t ws_bytes,
+                              double *grad_h, double *grad_v, emm_stream stream);
+
 /* Size of the scratch array that emm_forward_static works in. */
 #define EMM_STATIC_SCRATCH_BYTES (64u << 20)
 

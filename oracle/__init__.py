@@ -18,6 +18,11 @@ Entry points:
   * ``locate``        source/receiver stencil start and 1-D weights.
   * ``forward``       the whole time loop of Algorithm 1 (no airwave) and the
                       Green's functions of Eq. 7.
+  * ``stagger`` / ``stagger_T``  staggered conductivity from cell sigma_h,
+                      sigma_v (Sec. 3.6) and its transpose.
+  * ``misfit_gradient`` least-squares misfit of receiver data and its
+                      gradient with respect to the cell conductivities
+                      (``forward``, the residual, ``vjp``, ``stagger_T``).
 """
 from __future__ import annotations
 
@@ -72,6 +77,10 @@ def _load():
         _lib.orc_vjp.argtypes = [C.POINTER(_Problem), D, D, C.c_int]
         _lib.orc_vjp.restype = C.c_int
         _lib.orc_threads.restype = C.c_int
+        _lib.orc_stagger.argtypes = [I, C.POINTER(D), D, D, D]
+        _lib.orc_stagger.restype = C.c_int
+        _lib.orc_stagger_T.argtypes = [I, C.POINTER(D), D, D, D]
+        _lib.orc_stagger_T.restype = C.c_int
     return _lib
 
 
@@ -338,3 +347,54 @@ def air_extrapolate(plane, dx: float, dy: float, heights, kind: int) -> np.ndarr
     _check(fn(nx, ny, dx, dy, _dp(plane), nh, _dp(h), int(kind), _dp(out)), "air_extrapolate")
     return out
 
+
+
+def _axes(x, y, z):
+    xs = [_f64(x), _f64(y), _f64(z)]
+    n = (C.c_int * 3)(*[len(a) for a in xs])
+    return xs, n, (C.POINTER(C.c_double) * 3)(*[_dp(a) for a in xs])
+
+
+def stagger(x, y, z, sigma_h, sigma_v) -> np.ndarray:
+    """Staggered conductivity [3][n3][n2][n1] from cell values sigma_h,
+    sigma_v [n3-1][n2-1][n1-1]: at each E_c sample the mean over the cells
+    around its edge weighted by their face areas across it (Sec. 3.6)."""
+    xs, n, px = _axes(x, y, z)
+    shape = (len(xs[2]) - 1, len(xs[1]) - 1, len(xs[0]) - 1)
+    sh, sv = _f64(sigma_h), _f64(sigma_v)
+    assert sh.shape == shape and sv.shape == shape, (sh.shape, shape)
+    out = np.zeros((3, len(xs[2]), len(xs[1]), len(xs[0])))
+    _check(_load().orc_stagger(n, px, _dp(sh), _dp(sv), _dp(out)), "stagger")
+    return out
+
+
+def stagger_T(x, y, z, g):
+    """Transpose of :func:`stagger`: (grad_h, grad_v) of a gradient ``g``
+    [3][n3][n2][n1] with respect to the staggered conductivity."""
+    xs, n, px = _axes(x, y, z)
+    g = _f64(g)
+    assert g.shape == (3, len(xs[2]), len(xs[1]), len(xs[0])), g.shape
+    shape = (len(xs[2]) - 1, len(xs[1]) - 1, len(xs[0]) - 1)
+    gh, gv = np.zeros(shape), np.zeros(shape)
+    _check(_load().orc_stagger_T(n, px, _dp(g), _dp(gh), _dp(gv)), "stagger_T")
+    return gh, gv
+
+
+def misfit_gradient(x, y, z, sigma_h, sigma_v, d_obs, weight=None, **kw):
+    """Least-squares misfit L = 1/2 sum w |G - d_obs|^2 of one transmitter's
+    receiver data and its gradient with respect to the cell conductivities:
+    G from ``forward`` on ``stagger(sigma_h, sigma_v)``, the cotangent
+    w (G - d_obs) through ``vjp`` and then ``stagger_T``.  ``kw`` are the
+    arguments ``forward`` and ``vjp`` share (nt, rd, nb, ne, omega0, fmax,
+    sigma_min, src, rec, freqs, ...).  Returns dict(misfit, G, grad, grad_h,
+    grad_v), grad the staggered-conductivity gradient."""
+    sigma = stagger(x, y, z, sigma_h, sigma_v)
+    fkw = {k: v for k, v in kw.items() if k != "ckpt_every"}
+    G = forward(x, y, z, sigma, **fkw)["G"]
+    d = np.asarray(d_obs, dtype=np.complex128).reshape(G.shape)
+    w = np.ones(G.shape) if weight is None else np.asarray(weight, dtype=np.float64).reshape(G.shape)
+    r = G - d
+    misfit = 0.5 * float(np.sum(w * (r.real ** 2 + r.imag ** 2)))
+    grad = vjp(x, y, z, sigma, w * r, **kw)
+    gh, gv = stagger_T(x, y, z, grad)
+    return dict(misfit=misfit, G=G, grad=grad, grad_h=gh, grad_v=gv)

@@ -1268,3 +1268,98 @@ int orc_vjp(orc_problem *P, const double *v, double *grad, int ckpt_every)
   orc_state_free(st);
   return code;
 }
+
+/* ------------------------------------------------------------------------
+ * Conductivity model on the staggered grid (Sec. 3.6).
+ *
+ * Cells lie between adjacent interior nodes ([n3-1][n2-1][n1-1], x fastest)
+ * and carry sigma_h and sigma_v.  The staggered sigma_cc of E_c at a sample
+ * is the mean over the cells around its edge, each weighted by its face area
+ * across the edge: along the two axes a, b across the edge, node j touches
+ * cells j-1 and j (clamped to the model, so an edge on a face of the model
+ * names its one cell twice); along the edge's own axis the sample lies in
+ * cell min(i, n-2).  sigma_h feeds sigma_xx and sigma_yy, sigma_v sigma_zz.
+ * orc_stagger applies this sparse map, orc_stagger_T its transpose, both
+ * through the (cell, weight) list of orc_stagger_terms.
+ * ------------------------------------------------------------------------ */
+static void orc_cell_pair(int j, int n, int c[2])
+{
+  c[0] = orc_clampi(j - 1, 0, n - 2);
+  c[1] = orc_clampi(j, 0, n - 2);
+}
+
+/* The four (cell, weight) terms of staggered sample (comp, idx); weights sum to 1. */
+static void orc_stagger_terms(const int n[3], double *const w[3], int comp, const int idx[3], size_t cell[4],
+                              double wt[4])
+{
+  int a = comp == 0 ? 1 : 0, b = comp == 2 ? 1 : 2, ca[2], cb[2], cc[3];
+  orc_cell_pair(idx[a], n[a], ca);
+  orc_cell_pair(idx[b], n[b], cb);
+  cc[comp] = orc_clampi(idx[comp], 0, n[comp] - 2);
+  double tot = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    cc[a] = ca[q & 1];
+    cc[b] = cb[q >> 1];
+    wt[q] = w[a][cc[a]] * w[b][cc[b]];
+    tot += wt[q];
+    cell[q] = ((size_t)cc[2] * (n[1] - 1) + cc[1]) * (n[0] - 1) + cc[0];
+  }
+  for (int q = 0; q < 4; ++q) wt[q] /= tot;
+}
+
+static int orc_widths(const int n[3], const double *const x[3], double *w[3])
+{
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] < 2) return ORC_EINVAL;
+    w[a] = malloc(sizeof(double) * (n[a] - 1));
+    for (int c = 0; c + 1 < n[a]; ++c) w[a][c] = x[a][c + 1] - x[a][c];
+  }
+  return ORC_OK;
+}
+
+/* out[3][n3][n2][n1] = staggered sigma from sh, sv [n3-1][n2-1][n1-1]. */
+int orc_stagger(const int n[3], const double *const x[3], const double *sh, const double *sv, double *out)
+{
+  double *w[3] = {0, 0, 0};
+  int code = orc_widths(n, x, w);
+  if (!code) {
+    size_t per = (size_t)n[0] * n[1] * n[2];
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            int idx[3] = {i, j, k};
+            size_t cell[4];
+            double wt[4], s = 0.0;
+            orc_stagger_terms(n, w, c, idx, cell, wt);
+            for (int q = 0; q < 4; ++q) s += wt[q] * (c == 2 ? sv : sh)[cell[q]];
+            out[c * per + ((size_t)k * n[1] + j) * n[0] + i] = s;
+          }
+  }
+  for (int a = 0; a < 3; ++a) free(w[a]);
+  return code;
+}
+
+/* Transpose: gh, gv [n3-1][n2-1][n1-1] = S^T g, g [3][n3][n2][n1] (overwritten). */
+int orc_stagger_T(const int n[3], const double *const x[3], const double *g, double *gh, double *gv)
+{
+  double *w[3] = {0, 0, 0};
+  int code = orc_widths(n, x, w);
+  if (!code) {
+    size_t per = (size_t)n[0] * n[1] * n[2], ncell = (size_t)(n[0] - 1) * (n[1] - 1) * (n[2] - 1);
+    memset(gh, 0, sizeof(double) * ncell);
+    memset(gv, 0, sizeof(double) * ncell);
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            int idx[3] = {i, j, k};
+            size_t cell[4];
+            double wt[4], gs = g[c * per + ((size_t)k * n[1] + j) * n[0] + i];
+            orc_stagger_terms(n, w, c, idx, cell, wt);
+            for (int q = 0; q < 4; ++q) (c == 2 ? gv : gh)[cell[q]] += wt[q] * gs;
+          }
+  }
+  for (int a = 0; a < 3; ++a) free(w[a]);
+  return code;
+}

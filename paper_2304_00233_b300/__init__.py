@@ -36,7 +36,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_forward", "emm_forward_timed", "emm_status", "emm_strerror",
             "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient",
             "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge",
-            "emm_gradient_stored_workspace_size", "emm_gradient_stored")
+            "emm_gradient_stored_workspace_size", "emm_gradient_stored", "emm_misfit_gradient",
+            "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint")
 
 
 class EmmError(RuntimeError):
@@ -107,6 +108,11 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_gradient_stored_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.c_int, C.POINTER(C.c_size_t)],
                                                C.c_int),
         "emm_gradient_stored": ([V, C.POINTER(_Survey), V, V, C.c_int, C.c_int, V, C.c_size_t, V, V, V], C.c_int),
+        "emm_misfit_gradient": ([V, C.POINTER(_Survey), V, V, V, C.c_int, C.c_int, V, C.c_size_t, V, V, V, V],
+                                C.c_int),
+        "emm_stagger_workspace_size": ([V, C.POINTER(C.c_size_t)], C.c_int),
+        "emm_stagger_sigma": ([V, V, V, V, C.c_size_t, V, V], C.c_int),
+        "emm_stagger_sigma_adjoint": ([V, V, V, C.c_size_t, V, V, V], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -490,6 +496,184 @@ def green_functions(sigma, grid: Grid, survey: Survey, ckpt_every: Optional[int]
     conductivity tensor ``sigma`` [3][n3][n2][n1] (CUDA), differentiable with
     respect to ``sigma`` through the exact discrete adjoint."""
     return _emm_function().apply(sigma, grid, survey, ckpt_every)
+
+
+def _stagger_ws(grid: Grid, device):
+    import torch
+    n = C.c_size_t(0)
+    _check(load_library().emm_stagger_workspace_size(grid.handle, C.byref(n)), "emm_stagger_workspace_size")
+    return torch.empty(max(1, (n.value + 7) // 8), dtype=torch.float64, device=device)
+
+
+def _cells_shape(grid: Grid):
+    n1, n2, n3 = grid.n
+    return (n3 - 1, n2 - 1, n1 - 1)
+
+
+def stagger_sigma(grid: Grid, sigma_h, sigma_v, stream=None):
+    """``emm_stagger_sigma``: the staggered conductivity (float32 CUDA tensor
+    [3][n3][n2][n1], what ``forward`` takes) from cell-centred sigma_h and
+    sigma_v (float64 CUDA tensors [n3-1][n2-1][n1-1]): face-area weighted
+    means over the cells around each edge (Sec. 3.6)."""
+    import torch
+    sh = torch.as_tensor(sigma_h, dtype=torch.float64, device="cuda").contiguous()
+    sv = torch.as_tensor(sigma_v, dtype=torch.float64, device=sh.device).contiguous()
+    if tuple(sh.shape) != _cells_shape(grid) or tuple(sv.shape) != _cells_shape(grid):
+        raise ValueError(f"cell arrays must have shape {_cells_shape(grid)}")
+    if stream is None:
+        stream = torch.cuda.current_stream(sh.device)
+    n1, n2, n3 = grid.n
+    out = torch.empty((3, n3, n2, n1), dtype=torch.float32, device=sh.device)
+    ws = _stagger_ws(grid, sh.device)
+    _check(load_library().emm_stagger_sigma(grid.handle, C.c_void_p(sh.data_ptr()), C.c_void_p(sv.data_ptr()),
+                                            C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel() * 8),
+                                            C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream)),
+           "emm_stagger_sigma")
+    return out
+
+
+def stagger_sigma_adjoint(grid: Grid, grad, grad_h=None, grad_v=None, stream=None):
+    """``emm_stagger_sigma_adjoint``: adds the transpose of ``stagger_sigma``
+    applied to ``grad`` (float64 CUDA [3][n3][n2][n1]) to ``grad_h`` and
+    ``grad_v`` (float64 CUDA [n3-1][n2-1][n1-1]; zeros if not given) and
+    returns them."""
+    import torch
+    grad = grad.contiguous()
+    if stream is None:
+        stream = torch.cuda.current_stream(grad.device)
+    if grad_h is None:
+        grad_h = torch.zeros(_cells_shape(grid), dtype=torch.float64, device=grad.device)
+    if grad_v is None:
+        grad_v = torch.zeros(_cells_shape(grid), dtype=torch.float64, device=grad.device)
+    ws = _stagger_ws(grid, grad.device)
+    _check(load_library().emm_stagger_sigma_adjoint(grid.handle, C.c_void_p(grad.data_ptr()),
+                                                    C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel() * 8),
+                                                    C.c_void_p(grad_h.data_ptr()), C.c_void_p(grad_v.data_ptr()),
+                                                    C.c_void_p(stream.cuda_stream)),
+           "emm_stagger_sigma_adjoint")
+    return grad_h, grad_v
+
+
+class GradientWork:
+    """Device buffers of ``misfit_gradient`` (workspace, G and the gradient),
+    kept between the transmitters of a survey."""
+
+    def __init__(self, grid: Grid, survey: Survey, ckpt_every: int, stored_steps: int = 0, device="cuda"):
+        import torch
+        self.ckpt_every, self.stored_steps = int(ckpt_every), int(stored_steps)
+        self.nbytes = gradient_workspace_size(grid, survey, self.ckpt_every, self.stored_steps)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        self.ptr = self.buf.data_ptr() + (-self.buf.data_ptr()) % 256
+        n1, n2, n3 = grid.n
+        self.rec = torch.zeros((max(survey.nrec, 1), 6, len(survey.freqs), 2), dtype=torch.float64, device=device)
+        self.grad = torch.empty((3, n3, n2, n1), dtype=torch.float64, device=device)
+
+
+def misfit_gradient(grid: Grid, survey: Survey, sigma, d_obs, weight=None, ckpt_every: Optional[int] = None,
+                    stored_steps: int = 0, misfit=None, work: Optional[GradientWork] = None, stream=None,
+                    check: bool = True):
+    """``emm_misfit_gradient`` for one transmitter: adds 1/2 sum w |G - d_obs|^2
+    to ``misfit`` (float64 CUDA tensor [1], zeros if not given) and returns
+    (misfit, grad, G), grad the float64 [3][n3][n2][n1] gradient with respect
+    to the staggered conductivity, G complex128 [nrec][6][nfreq].  ``d_obs``
+    is complex [nrec][6][nfreq], ``weight`` real [nrec][6][nfreq] or None."""
+    import torch
+    _check_sigma(grid, sigma)
+    dev = sigma.device
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    nf = len(survey.freqs)
+    if ckpt_every is None:
+        ckpt_every = max(1, int(round(max(survey.nt, 1) ** 0.5)))
+    if work is None or work.ckpt_every != ckpt_every or work.stored_steps != stored_steps:
+        work = GradientWork(grid, survey, ckpt_every, stored_steps, dev)
+    d = torch.as_tensor(d_obs, dtype=torch.complex128, device=dev).reshape(survey.nrec, 6, nf)
+    d2 = torch.view_as_real(d.contiguous()).contiguous()
+    w = None
+    if weight is not None:
+        w = torch.as_tensor(weight, dtype=torch.float64, device=dev).reshape(survey.nrec, 6, nf).contiguous()
+    if misfit is None:
+        misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+    s, keep = survey._c()
+    code = load_library().emm_misfit_gradient(
+        grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), C.c_void_p(d2.data_ptr()),
+        C.c_void_p(w.data_ptr() if w is not None else None), int(ckpt_every), int(stored_steps),
+        C.c_void_p(work.ptr), C.c_size_t(work.nbytes), C.c_void_p(work.rec.data_ptr()), C.c_void_p(misfit.data_ptr()),
+        C.c_void_p(work.grad.data_ptr()), C.c_void_p(stream.cuda_stream))
+    _check(code, "emm_misfit_gradient")
+    if check:
+        v = C.c_int(0)
+        _check(load_library().emm_status(C.c_void_p(work.ptr), C.byref(v), C.c_void_p(stream.cuda_stream)),
+               "emm_status")
+        if v.value != EMM_OK:
+            raise EmmError(v.value, "emm_misfit_gradient (device status)")
+    return misfit, work.grad, torch.view_as_complex(work.rec)[: survey.nrec]
+
+
+def survey_misfit_gradient(grid: Grid, survey: Survey, sigma_h, sigma_v, src_pos, d_obs, weight=None,
+                           ckpt_every: Optional[int] = None, stored_steps: int = 0, stream=None,
+                           check: bool = True):
+    """Least-squares misfit of a survey and its gradient with respect to the
+    cell conductivities: for every transmitter position in ``src_pos``
+    ([nsrc][3], the rest of ``survey`` shared) one ``emm_misfit_gradient``,
+    whose gradient ``emm_stagger_sigma_adjoint`` adds to the cells.  Returns
+    (misfit float64 CUDA [1], grad_h, grad_v float64 CUDA [n3-1][n2-1][n1-1],
+    G complex128 [nsrc][nrec][6][nfreq]).  ``d_obs`` is [nsrc][nrec][6][nfreq],
+    ``weight`` None, [nrec][6][nfreq] (shared) or [nsrc][nrec][6][nfreq]."""
+    import torch
+    sigma = stagger_sigma(grid, sigma_h, sigma_v, stream)
+    dev = sigma.device
+    pos = np.asarray(src_pos, dtype=np.float64).reshape(-1, 3)
+    if ckpt_every is None:
+        ckpt_every = max(1, int(round(max(survey.nt, 1) ** 0.5)))
+    work = GradientWork(grid, survey, ckpt_every, stored_steps, dev)
+    misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad_h = torch.zeros(_cells_shape(grid), dtype=torch.float64, device=dev)
+    grad_v = torch.zeros(_cells_shape(grid), dtype=torch.float64, device=dev)
+    Gs = []
+    w_all = None if weight is None else torch.as_tensor(weight, dtype=torch.float64)
+    for k, p in enumerate(pos):
+        sk = dataclasses.replace(survey, src=tuple(float(v) for v in p))
+        wk = None if w_all is None else (w_all[k] if w_all.dim() == 4 else w_all)
+        _, grad, G = misfit_gradient(grid, sk, sigma, d_obs[k], wk, ckpt_every, stored_steps, misfit, work,
+                                     stream, check)
+        stagger_sigma_adjoint(grid, grad, grad_h, grad_v, stream)
+        Gs.append(G.clone())
+    return misfit, grad_h, grad_v, torch.stack(Gs)
+
+
+def _cell_misfit_function():
+    import torch
+
+    class CellMisfit(torch.autograd.Function):
+        """The survey misfit as a differentiable function of the cell
+        conductivities sigma_h, sigma_v: the forward pass runs
+        ``survey_misfit_gradient`` (forward sweeps, residuals, adjoint sweeps)
+        and keeps the gradient, which the backward pass scales by the
+        incoming gradient of the scalar misfit."""
+
+        @staticmethod
+        def forward(ctx, sigma_h, sigma_v, grid, survey, src_pos, d_obs, weight, ckpt_every, stored_steps):
+            misfit, gh, gv, _ = survey_misfit_gradient(grid, survey, sigma_h.detach(), sigma_v.detach(), src_pos,
+                                                       d_obs, weight, ckpt_every, stored_steps)
+            ctx.save_for_backward(gh, gv)
+            return misfit[0].clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            gh, gv = ctx.saved_tensors
+            return (g * gh).to(gh.dtype), (g * gv).to(gv.dtype), None, None, None, None, None, None, None
+
+    return CellMisfit
+
+
+def cell_misfit(sigma_h, sigma_v, grid: Grid, survey: Survey, src_pos, d_obs, weight=None,
+                ckpt_every: Optional[int] = None, stored_steps: int = 0):
+    """Survey misfit 1/2 sum w |G - d_obs|^2 (float64 CUDA scalar) of the cell
+    conductivities, differentiable with respect to ``sigma_h`` and
+    ``sigma_v`` (float64 CUDA [n3-1][n2-1][n1-1])."""
+    return _cell_misfit_function().apply(sigma_h, sigma_v, grid, survey, src_pos, d_obs, weight, ckpt_every,
+                                         stored_steps)
 
 
 def status(work: Workspace, stream=None) -> int:

@@ -418,6 +418,29 @@ __global__ void k_adj_flush(const AdjParams a) {
 }
 
 // cw[r][c][f] = conj(v) * norm[c < 3 ? 0 : 1][f]  (Eq. 7 normalisation).
+// Least-squares residual of the forward sweep's Green's functions: r =
+// w (G - d) (the cotangent of the misfit 1/2 sum w |G - d|^2, which is added
+// to *misfit).  One block; the tree reduction fixes the summation order.
+constexpr int kResThreads = 256;
+__global__ void __launch_bounds__(kResThreads)
+    k_residual(const double *G, const double *d, const double *wt, double *r, double *misfit, int n) {
+  __shared__ double part[kResThreads];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < n; t += kResThreads) {
+    const double re = G[2 * t] - d[2 * t], im = G[2 * t + 1] - d[2 * t + 1], w = wt ? wt[t] : 1.0;
+    r[2 * t] = w * re;
+    r[2 * t + 1] = w * im;
+    acc += 0.5 * w * (re * re + im * im);
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kResThreads / 2; h > 0; h /= 2) {
+    if (static_cast<int>(threadIdx.x) < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *misfit += part[0];
+}
+
 __global__ void k_adj_weights(const double *v, const double *norm, double *cw, int nrec, int nf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nrec * 6 * nf) return;
@@ -497,7 +520,7 @@ bool make_gathers(const AdjParams &a, Gathers *G) {
 // Byte layout of the gradient's extra workspace, after the forward one.
 struct AdjLayout {
   size_t fwd, ck, state, nck, eh, ebytes, first_stored, snap, lamE[3], lamH[3], TH[6], TE[6], muE[6], muH[6], gpad[3], gseg[3], cpT[3], cmT[3], cw,
-      total;
+      res, total;
 };
 
 // K: steps between checkpoints; S: a budget of steps whose E snapshots the
@@ -540,6 +563,7 @@ AdjLayout adj_plan(const emm_grid *g, const emm_survey *s, int K, int S) {
   for (int a = 0; a < 3; ++a) A.cpT[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   for (int a = 0; a < 3; ++a) A.cmT[a] = take((a == 0 ? xrows : g->ax[a].npad) * m * 4);
   A.cw = take(static_cast<size_t>(s->nrec > 0 ? s->nrec : 1) * 6 * s->nfreq * 2 * sizeof(double));
+  A.res = take(static_cast<size_t>(s->nrec > 0 ? s->nrec : 1) * 6 * s->nfreq * 2 * sizeof(double));
   A.total = off;
   return A;
 }
@@ -563,11 +587,15 @@ void transposed_rows(const Axis &ax, int rd, std::vector<float> &pT, std::vector
     }
 }
 
+// With d_obs set, the cotangent is the misfit residual w (G - d_obs) of the
+// forward sweep's own G (dG unused), and the misfit is added to *misfit.
 int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int K, int S,
-                  void *ws, size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs) {
+                  void *ws, size_t ws_bytes, double *rec_out, double *grad, cudaStream_t cs,
+                  const double *d_obs = nullptr, const double *wts = nullptr, double *misfit = nullptr) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
-  if (K < 1 || s->volume || s->src_kind != 0 || s->src_length > 0 || s->airwave || !grad || !sigma || !ws || (s->nrec > 0 && (!dG || !rec_out)))
+  if (K < 1 || s->volume || s->src_kind != 0 || s->src_length > 0 || s->airwave || !grad || !sigma || !ws ||
+      (s->nrec > 0 && ((!dG && !d_obs) || !rec_out)) || (d_obs && !misfit))
     return EMM_EINVAL;
   if (S < 0) return EMM_EINVAL;
   const AdjLayout A = adj_plan(g, s, K, S);
@@ -680,6 +708,11 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   if (e != cudaSuccess) return EMM_ECUDA;
   if (s->nrec > 0) {
     const int tot = s->nrec * 6 * nf;
+    if (d_obs) {
+      double *res = reinterpret_cast<double *>(base + A.res);
+      k_residual<<<1, kResThreads, 0, cs>>>(rec_out, d_obs, wts, res, misfit, tot);
+      dG = res;
+    }
     k_adj_weights<<<(tot + 255) / 256, 256, 0, cs>>>(dG, reinterpret_cast<const double *>(base + L.norm),
                                                      reinterpret_cast<double *>(base + A.cw), s->nrec, nf);
   }
@@ -763,6 +796,14 @@ int emm_gradient_stored(const emm_grid *g, const emm_survey *s, const float *sig
                         emm_stream stream) {
   return emm::gradient_impl(g, s, sigma, dG, ckpt_every, stored_steps, ws, ws_bytes, rec_out, grad,
                             reinterpret_cast<cudaStream_t>(stream));
+}
+
+int emm_misfit_gradient(const emm_grid *g, const emm_survey *s, const float *sigma, const double *d_obs,
+                        const double *weight, int ckpt_every, int stored_steps, void *ws, size_t ws_bytes,
+                        double *rec_out, double *misfit, double *grad, emm_stream stream) {
+  if (!d_obs || !misfit) return EMM_EINVAL;
+  return emm::gradient_impl(g, s, sigma, nullptr, ckpt_every, stored_steps, ws, ws_bytes, rec_out, grad,
+                            reinterpret_cast<cudaStream_t>(stream), d_obs, weight, misfit);
 }
 
 int emm_gradient(const emm_grid *g, const emm_survey *s, const float *sigma, const double *dG, int ckpt_every,

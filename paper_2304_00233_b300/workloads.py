@@ -29,7 +29,8 @@ __all__ = [
     "create_nugrid", "symmetric_axis", "seabed_axis", "uniform_axis",
     "LayeredModel", "Box", "cell_conductivity", "staggered_conductivity",
     "Workload", "whole_space", "marine_1d", "anomaly_3d", "small_case",
-    "WORKLOADS",
+    "gradient_survey", "gradient_survey_48", "GRADIENT_SOURCES", "GRADIENT_SOURCES_48",
+    "observed_noise", "WORKLOADS",
 ]
 
 
@@ -264,6 +265,8 @@ class Workload:
     t_max: float               # fictitious time simulated
     volume: bool = False
     nt: Optional[int] = None   # fixed step count (else ceil(t_max/dt))
+    sigma_h: Optional[np.ndarray] = None   # cell values [n3-1][n2-1][n1-1] behind sigma, when kept
+    sigma_v: Optional[np.ndarray] = None
 
     @property
     def shape(self):
@@ -370,6 +373,60 @@ def anomaly_3d(seed: int = 230400233) -> Workload:
                     np.array([0.0, 0.0, 950.0]), 0.0, 0.0, 1.0, rec,
                     np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.46,
                     volume=True)
+
+
+# transmitters of the gradient survey: a tow line 50 m above the seabed
+GRADIENT_SOURCES = np.array([[-2800.0 + 800.0 * k, 0.0, 950.0] for k in range(8)])
+
+
+def gradient_survey(with_resistor: bool = False, nt: Optional[int] = None) -> Workload:
+    """Least-squares gradient survey: the marine layering of ``marine_1d`` on a
+    192 x 192 x 128 NU grid (x, y 96 cells per side over 9550 m from 40 m; z
+    16 cells over 1000 m above the seabed and 111 over 11150 m below it, from
+    40 m), the receivers of ``marine_1d``, the transmitter at the first of
+    ``GRADIENT_SOURCES``.  The observed data come from the model with the
+    resistor; the gradient is taken at the model without it.  The cell
+    values sigma_h, sigma_v are kept (the gradient is with respect to them)."""
+    x = symmetric_axis(192, 9550.0, 40.0)
+    z = seabed_axis(1000.0, 16, 1000.0, 111, 11150.0, 40.0)
+    sh, sv = cell_conductivity(_marine_model(with_resistor), x, x, z)
+    sig = staggered_conductivity(sh, sv, x, x, z)
+    rec = np.zeros((64, 3))
+    rec[:, 0] = -6300.0 + 200.0 * np.arange(64)
+    rec[:, 2] = 1000.0
+    name = "gradient_survey_192x192x128" + ("_resistor" if with_resistor else "")
+    return Workload(name, x, x.copy(), z, _f32(sig), 2, 10, 7, GRADIENT_SOURCES[0].copy(), 0.0, 0.0, 1.0,
+                    rec, np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4, nt=nt, sigma_h=sh, sigma_v=sv)
+
+
+# transmitters of the small copy of the gradient survey
+GRADIENT_SOURCES_48 = np.array([[-400.0, 0.0, 950.0], [400.0, 0.0, 950.0]])
+
+
+def gradient_survey_48(with_resistor: bool = False, nt: int = 200) -> Workload:
+    """The gradient survey on a 48 x 48 x 48 copy small enough for the FP64
+    oracle: x, y 24 cells per side over 2400 m from 40 m; z 16 cells over
+    1000 m above the seabed and 31 over 3200 m below it; receivers every
+    200 m from -2100 to 2100 m on the seabed; transmitters at
+    ``GRADIENT_SOURCES_48``; a fixed, short step count."""
+    x = symmetric_axis(48, 2400.0, 40.0)
+    z = seabed_axis(1000.0, 16, 1000.0, 31, 3200.0, 40.0)
+    sh, sv = cell_conductivity(_marine_model(with_resistor), x, x, z)
+    sig = staggered_conductivity(sh, sv, x, x, z)
+    rec = np.zeros((22, 3))
+    rec[:, 0] = -2100.0 + 200.0 * np.arange(22)
+    rec[:, 2] = 1000.0
+    name = "gradient_survey_48" + ("_resistor" if with_resistor else "")
+    return Workload(name, x, x.copy(), z, _f32(sig), 2, 10, 7, GRADIENT_SOURCES_48[0].copy(), 0.0, 0.0, 1.0,
+                    rec, np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4, nt=nt, sigma_h=sh, sigma_v=sv)
+
+
+def observed_noise(shape, seed: int = 230400234, level: float = 0.02) -> np.ndarray:
+    """Multiplicative complex noise 1 + level (g1 + i g2) / sqrt(2), g ~ N(0, 1)
+    i.i.d., for synthetic observed data d = G (1 + noise)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(tuple(shape) + (2,))
+    return 1.0 + level * (g[..., 0] + 1j * g[..., 1]) / math.sqrt(2.0)
 
 
 def small_case(n=(40, 36, 30), rd: int = 2, seed: int = 7, nt: int = 120,
