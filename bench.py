@@ -298,6 +298,62 @@ def gradient_survey_line(emm, torch, stream, job_max):
                     "the sigma_h, sigma_v gradients; ratio against one forward solve per transmitter"}
 
 
+def jobs_line(emm, torch, stream, job_max):
+    """The uneven-grid work list (3 x 96^3, 3 x 160 x 160 x 120, 2 x 200 x
+    200 x 140 nodes, each with its own transmitter): the eight forward solves
+    one after the other (emm_forward each), against emm_forward_jobs with the
+    work-list launches and with the strategy emm_jobs_tune picks."""
+    import dataclasses
+    wls = W.uneven_jobs()
+    probs, sig, works, cells, steps = [], [], [], 0, 0
+    for wl in wls:
+        g = emm.grid_for(wl)
+        nt = emm.steps_for(wl, g)
+        probs.append((g, emm.survey_for(wl, nt=nt)))
+        sig.append(torch.from_numpy(wl.sigma.astype(np.float32)).cuda())
+        works.append(emm.Workspace(g, probs[-1][1]))
+        cells += g.cells * nt
+        steps = max(steps, nt)
+    short = [(g, dataclasses.replace(s, nt=30)) for g, s in probs]
+    for (g, s), sg, w in zip(short, sig, works):
+        emm.forward_async(g, s, sg, w)
+    emm.forward_jobs(short, sig, strategy=emm.JOBS_LIST)
+    jw = emm.JobsWork(probs)
+    best, tune_ms = emm.jobs_tune(probs, sig, jw, steps=40)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return job_max(a.elapsed_time(b) / 1e3)
+
+    def one_at_a_time():
+        for (g, s), sg, w in zip(probs, sig, works):
+            emm.forward_async(g, s, sg, w)
+
+    seq = timed(one_at_a_time)
+    for (g, s), w in zip(probs, works):
+        assert emm.status(w) == emm.EMM_OK
+    rates = {}
+    for k in sorted({emm.JOBS_LIST, best}):
+        t = timed(lambda: emm.forward_jobs(probs, sig, work=jw, check=False, strategy=k))
+        assert all(st == emm.EMM_OK for st in jw.status())
+        same = all(torch.equal(torch.view_as_complex(r)[: s.nrec], torch.view_as_complex(w.rec)[: s.nrec])
+                   for r, w, (_, s) in zip(jw.rec, works, probs))
+        rates[emm.JOBS_STRATEGIES[k]] = {"value": cells / t / 1e9, "ms": 1e3 * t, "bitwise_equal": same}
+    return {"problems": [w.name for w in wls], "cell_steps": cells, "max_timesteps": steps,
+            "value": rates[emm.JOBS_STRATEGIES[best]]["value"], "unit": "Gcell-steps/s",
+            "strategy": emm.JOBS_STRATEGIES[best], "one_at_a_time": cells / seq / 1e9,
+            "speedup": seq / (rates[emm.JOBS_STRATEGIES[best]]["ms"] / 1e3), "ms_one_at_a_time": 1e3 * seq,
+            "strategies": rates, "tune_ms_40_steps": tune_ms,
+            "what": "emm_forward_jobs by the strategy emm_jobs_tune picks (and by work-list launches: one E "
+                    "and one H launch per step over the tiles of all eight grids) against emm_forward of each "
+                    "problem in turn, device-resident inputs"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,6 +364,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
+    ap.add_argument("--no-jobs", action="store_true",
+                    help="skip the uneven-grid work-list line (eight grids, one launch per half-step)")
     ap.add_argument("--no-gradient-survey", action="store_true",
                     help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid (about a minute)")
     ap.add_argument("--no-airwave", action="store_true",
@@ -510,6 +568,8 @@ def main():
                                     "of the last stored_steps steps in device memory, recomputation of the "
                                     "earlier segments and the adjoint sweep, one cotangent of all receiver "
                                     "data; recompute_only: every segment recomputed (emm_gradient)"}
+    if not args.no_jobs:
+        line["jobs"] = jobs_line(emm, torch, stream, job_max)
     if not args.no_gradient_survey:
         line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max)
     if rank == 0 and not args.no_cpu_baseline:

@@ -258,6 +258,57 @@ int emm_batch_workspace_size(const emm_grid *grid, const emm_survey *survey, int
 int emm_forward_batch(const emm_grid *grid, const emm_survey *survey, int nsrc, const double *src_pos,
                       const float *sigma, void *ws, size_t ws_bytes, double *rec_out, emm_stream stream);
 
+/* One problem of a work-list solve: a grid, a survey (one transmitter),
+ * its conductivity and its receiver output, as emm_forward takes them. */
+typedef struct emm_job {
+  const emm_grid *grid;
+  const emm_survey *survey;
+  const float *sigma;  /* device float [3][n3][n2][n1] */
+  double *rec_out;     /* device double [nrec][6][nfreq][2] */
+} emm_job;
+
+/* Workspace of emm_forward_jobs: each problem's emm_workspace_size, 256-byte
+ * aligned, one after the other.  offsets: NULL, or a host array of njobs
+ * that receives each problem's byte offset in the workspace (emm_status on
+ * ws + offsets[j] reads problem j's device status).  EMM_EINVAL if njobs is
+ * outside 1..16, the problems' FD orders differ, or a survey asks for the
+ * volume DTFT, the air boundary, a magnetic source or an antenna. */
+int emm_jobs_workspace_size(int njobs, const emm_job *jobs, size_t *bytes, size_t *offsets);
+
+/* How emm_forward_jobs advances its problems. */
+enum {
+  EMM_JOBS_LIST = 0,        /* every leapfrog step is one E and one H launch over a work list of
+                               all the problems' tiles (and receiver CTAs): their launch tails
+                               overlap instead of each draining alone */
+  EMM_JOBS_SEQUENTIAL = 1,  /* each problem's whole time loop in turn on `stream` */
+  EMM_JOBS_STREAMS = 2      /* each problem on a stream of its own, forked from `stream` and
+                               joined back to it (the library creates and releases the streams) */
+};
+
+/* Forward solves of up to 16 problems of any grid sizes (one FD order, an
+ * electric point dipole each) by one of the strategies above (emm_jobs_tune
+ * picks the fastest for a given set of problems).  Each problem runs its own
+ * survey->nt steps (under EMM_JOBS_LIST a problem that is done returns at
+ * once from the later launches); each rec_out receives exactly what
+ * emm_forward would write for that problem, whatever the strategy (the
+ * same arithmetic on the same data).  The paper runs one transmitter per
+ * MPI rank; this is the single-GPU form of running many, including grids of
+ * uneven sizes.
+ *   ws   device workspace of emm_jobs_workspace_size bytes, 256-byte aligned.
+ * Asynchronous on `stream`; errors as emm_forward and emm_jobs_workspace_size,
+ * and EMM_EINVAL for an unknown strategy. */
+int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, size_t ws_bytes,
+                     emm_stream stream);
+
+/* Autotuner of emm_forward_jobs: runs `steps` leapfrog steps of the problems
+ * by each strategy (after a short warm-up of each), timed with CUDA events on
+ * `stream`, and returns the times in ms[3] (host, indexed by EMM_JOBS_*) and
+ * the fastest strategy in *best.  Synchronises `stream`.  The workspace is
+ * left in no particular state (every solve prepares it again).  EMM_EINVAL
+ * if steps < 1 or ms or best is NULL; otherwise as emm_forward_jobs. */
+int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
+                  double *ms, int *best);
+
 /* Device workspace bytes emm_gradient needs (the forward workspace, the
  * checkpoints of every ckpt_every-th step, the E snapshots of one checkpoint
  * segment, the adjoint fields and the FP64 gradient accumulators).

@@ -29,6 +29,8 @@ LIBRARY_PATH = os.path.join(_HERE, "libemm.so")
 
 (EMM_OK, EMM_EINVAL, EMM_ENOMEM, EMM_EOUTSIDE, EMM_ECFL, EMM_ECUDA, EMM_EWORKSPACE, EMM_EDEVICE,
  EMM_ETIMEOUT) = range(9)
+JOBS_LIST, JOBS_SEQUENTIAL, JOBS_STREAMS = range(3)
+JOBS_STRATEGIES = ("list", "sequential", "streams")
 TAB_NODES, TAB_HALF, TAB_DPLUS, TAB_DMINUS, TAB_SLAB_INT, TAB_SLAB_HALF = range(6)
 COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables",
@@ -37,7 +39,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_forward_static", "emm_gradient_workspace_size", "emm_gradient",
             "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge",
             "emm_gradient_stored_workspace_size", "emm_gradient_stored", "emm_misfit_gradient",
-            "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint")
+            "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint",
+            "emm_jobs_workspace_size", "emm_forward_jobs", "emm_jobs_tune")
 
 
 class EmmError(RuntimeError):
@@ -71,6 +74,11 @@ class _Survey(C.Structure):
                 ("nrec", C.c_int), ("rec", _D), ("nfreq", C.c_int), ("freqs", _D),
                 ("volume", C.c_int), ("src_kind", C.c_int),
                 ("src_length", C.c_double), ("src_points", C.c_int), ("airwave", C.c_int)]
+
+
+class _Job(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("survey", C.POINTER(_Survey)), ("sigma", C.c_void_p),
+                ("rec_out", C.c_void_p)]
 
 
 _lib = None
@@ -113,6 +121,10 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_stagger_workspace_size": ([V, C.POINTER(C.c_size_t)], C.c_int),
         "emm_stagger_sigma": ([V, V, V, V, C.c_size_t, V, V], C.c_int),
         "emm_stagger_sigma_adjoint": ([V, V, V, C.c_size_t, V, V, V], C.c_int),
+        "emm_jobs_workspace_size": ([C.c_int, C.POINTER(_Job), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+                                    C.c_int),
+        "emm_forward_jobs": ([C.c_int, C.POINTER(_Job), C.c_int, V, C.c_size_t, V], C.c_int),
+        "emm_jobs_tune": ([C.c_int, C.POINTER(_Job), V, C.c_size_t, C.c_int, V, _D, _I], C.c_int),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -496,6 +508,100 @@ def green_functions(sigma, grid: Grid, survey: Survey, ckpt_every: Optional[int]
     conductivity tensor ``sigma`` [3][n3][n2][n1] (CUDA), differentiable with
     respect to ``sigma`` through the exact discrete adjoint."""
     return _emm_function().apply(sigma, grid, survey, ckpt_every)
+
+
+class JobsWork:
+    """Workspace of ``forward_jobs`` for a fixed list of (grid, survey)
+    problems: the device buffer, each problem's offset in it and its
+    receiver output."""
+
+    def __init__(self, problems, device="cuda"):
+        import torch
+        self.problems = list(problems)
+        jobs, self._keep = _jobs_c(self.problems, [None] * len(self.problems), [None] * len(self.problems))
+        n = C.c_size_t(0)
+        offs = (C.c_size_t * len(jobs))()
+        _check(load_library().emm_jobs_workspace_size(len(jobs), jobs, C.byref(n), offs), "emm_jobs_workspace_size")
+        self.nbytes = n.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        self.ptr = self.buf.data_ptr() + (-self.buf.data_ptr()) % 256
+        self.offsets = [int(o) for o in offs]
+        self.strategy, self.tune_ms = None, None
+        self.rec = [torch.zeros((max(s.nrec, 1), 6, len(s.freqs), 2), dtype=torch.float64, device=device)
+                    for _, s in self.problems]
+
+    def status(self, stream=None):
+        """Device status word of each problem of the last run (synchronises)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.buf.device)
+        out = []
+        for off in self.offsets:
+            v = C.c_int(0)
+            _check(load_library().emm_status(C.c_void_p(self.ptr + off), C.byref(v), C.c_void_p(stream.cuda_stream)),
+                   "emm_status")
+            out.append(int(v.value))
+        return out
+
+
+def _jobs_c(problems, sigmas, recs):
+    jobs = (_Job * len(problems))()
+    keep = []
+    for j, (grid, survey) in enumerate(problems):
+        sc, k = survey._c()
+        keep += [sc, k]
+        jobs[j].grid = grid.handle
+        jobs[j].survey = C.pointer(sc)
+        jobs[j].sigma = sigmas[j].data_ptr() if sigmas[j] is not None else None
+        jobs[j].rec_out = recs[j].data_ptr() if recs[j] is not None else None
+    return jobs, keep
+
+
+def jobs_tune(problems, sigmas, work: "JobsWork", steps: int = 40, stream=None):
+    """``emm_jobs_tune``: times ``steps`` leapfrog steps of ``problems`` by
+    each strategy and returns (best strategy, {name: ms})."""
+    import torch
+    dev = sigmas[0].device
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    jobs, keep = _jobs_c(list(problems), list(sigmas), work.rec)
+    ms = np.zeros(3)
+    best = C.c_int(0)
+    _check(load_library().emm_jobs_tune(len(jobs), jobs, C.c_void_p(work.ptr), C.c_size_t(work.nbytes), int(steps),
+                                        C.c_void_p(stream.cuda_stream), _dp(ms), C.byref(best)), "emm_jobs_tune")
+    return int(best.value), dict(zip(JOBS_STRATEGIES, ms.tolist()))
+
+
+def forward_jobs(problems, sigmas, work: Optional[JobsWork] = None, stream=None, check: bool = True,
+                 strategy: Optional[int] = None):
+    """``emm_forward_jobs``: the forward solves of ``problems`` (a list of
+    (Grid, Survey), up to 16, one FD order) advanced together by
+    ``strategy`` (JOBS_LIST, JOBS_SEQUENTIAL or JOBS_STREAMS; None: the one
+    ``jobs_tune`` finds fastest, tuned once per ``work``).  ``sigmas`` are
+    float32 CUDA tensors [3][n3][n2][n1].  Returns ([G complex128
+    [nrec][6][nfreq] per problem], work)."""
+    import torch
+    problems = list(problems)
+    for (grid, _), sg in zip(problems, sigmas):
+        _check_sigma(grid, sg)
+    dev = sigmas[0].device
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    if work is None:
+        work = JobsWork(problems, dev)
+    if strategy is None:
+        if work.strategy is None:
+            work.strategy, work.tune_ms = jobs_tune(problems, sigmas, work, stream=stream)
+        strategy = work.strategy
+    jobs, keep = _jobs_c(problems, list(sigmas), work.rec)
+    _check(load_library().emm_forward_jobs(len(jobs), jobs, int(strategy), C.c_void_p(work.ptr),
+                                           C.c_size_t(work.nbytes), C.c_void_p(stream.cuda_stream)),
+           "emm_forward_jobs")
+    if check:
+        for j, v in enumerate(work.status(stream)):
+            if v != EMM_OK:
+                raise EmmError(v, f"emm_forward_jobs (device status of problem {j})")
+    return [torch.view_as_complex(r)[: s.nrec] for r, (_, s) in zip(work.rec, problems)], work
 
 
 def _stagger_ws(grid: Grid, device):

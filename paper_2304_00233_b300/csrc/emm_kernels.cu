@@ -42,6 +42,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -164,23 +165,30 @@ __device__ void receiver_dft(const DevParams &p, int comp0, float *const *F, con
 struct Origin {
   int i0, j0, k0, src;
 };
+// A CTA's place in its problem's launch grid: blockIdx for a launch of one
+// problem; for a launch over a work list of problems, the CTA's index
+// within its problem's share (see k_update_E_jobs).
+struct Blk {
+  int x, y, z;
+};
+__device__ __forceinline__ Blk launch_blk() {
+  return Blk{static_cast<int>(blockIdx.x), static_cast<int>(blockIdx.y), static_cast<int>(blockIdx.z)};
+}
 // MULTI: a batch of transmitters (otherwise transmitter 0 alone, and no
 // index arithmetic for it).
 template <bool MULTI>
-__device__ __forceinline__ Origin origin_of(const DevParams &p) {
-  const int bx = MULTI ? static_cast<int>(blockIdx.x) / p.nsrc : static_cast<int>(blockIdx.x);
-  return Origin{p.org[0] + bx * TX, p.org[1] + static_cast<int>(blockIdx.y) * TY,
-                p.org[2] + (static_cast<int>(blockIdx.z) - p.rec_layers) * ZC,
-                MULTI ? static_cast<int>(blockIdx.x) % p.nsrc : 0};
+__device__ __forceinline__ Origin origin_of(const DevParams &p, const Blk &b) {
+  const int bx = MULTI ? b.x / p.nsrc : b.x;
+  return Origin{p.org[0] + bx * TX, p.org[1] + b.y * TY, p.org[2] + (b.z - p.rec_layers) * ZC,
+                MULTI ? b.x % p.nsrc : 0};
 }
 template <bool MULTI>
-__device__ __forceinline__ int receiver_block(const DevParams &p) {
-  return (static_cast<int>(blockIdx.z) * p.tiles_y + static_cast<int>(blockIdx.y)) * p.tiles_x +
-         (MULTI ? static_cast<int>(blockIdx.x) / p.nsrc : static_cast<int>(blockIdx.x));
+__device__ __forceinline__ int receiver_block(const DevParams &p, const Blk &b) {
+  return (b.z * p.tiles_y + b.y) * p.tiles_x + (MULTI ? b.x / p.nsrc : b.x);
 }
 template <bool MULTI>
-__device__ __forceinline__ int receiver_source(const DevParams &p) {
-  return MULTI ? static_cast<int>(blockIdx.x) % p.nsrc : 0;
+__device__ __forceinline__ int receiver_source(const DevParams &p, const Blk &b) {
+  return MULTI ? b.x % p.nsrc : 0;
 }
 
 // The state arrays of transmitter src.
@@ -570,25 +578,21 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
   for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.E[a] + id) = out[a];
 }
 
-// CONV: a convergence run (corner DTFT, and every launch returns at once
-// after the stop).  OUT: E^{n+1} goes to p.Eout (E^n stays where it is).
+// One CTA of the E half-step.  CONV: a convergence run (corner DTFT).
+// OUT: E^{n+1} goes to p.Eout (E^n stays where it is).
 template <int R, bool MULTI, bool CONV, bool OUT>
-__global__ void __launch_bounds__(NT, min_ctas(R))
-    k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  wait_prior_grid();
-  if (CONV && *p.halt) return;  // a convergence run that has stopped
-  allow_next_launch();
-  if (static_cast<int>(blockIdx.z) < p.rec_layers) {
-    const int rs = receiver_source<MULTI>(p);
+__device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b) {
+  if (b.z < p.rec_layers) {
+    const int rs = receiver_source<MULTI>(p, b);
     const Fields f = fields_of<MULTI>(p, rs);
-    receiver_dft<R, CONV>(p, 3, f.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+    receiver_dft<R, CONV>(p, 3, f.H, p.fH + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p, b),
                     p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of<MULTI>(p);
+  const Origin o = origin_of<MULTI>(p, b);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
 
   const Quad u = quad_of(o);
@@ -621,6 +625,17 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
     e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw);
   else
     e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw);
+}
+
+// The E half-step of one problem; every launch of a convergence run returns
+// at once after the stop.
+template <int R, bool MULTI, bool CONV, bool OUT>
+__global__ void __launch_bounds__(NT, min_ctas(R))
+    k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  wait_prior_grid();
+  if (CONV && *p.halt) return;  // a convergence run that has stopped
+  allow_next_launch();
+  e_block<R, MULTI, CONV, OUT>(p, tm, n, launch_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -780,23 +795,20 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, cons
   for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.H[a] + id) = out[a];
 }
 
+// One CTA of the H half-step.
 template <int R, bool MULTI, bool CONV>
-__global__ void __launch_bounds__(NT, min_ctas(R))
-    k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
-  wait_prior_grid();
-  if (CONV && *p.halt) return;  // a convergence run that has stopped
-  allow_next_launch();
-  if (static_cast<int>(blockIdx.z) < p.rec_layers) {
-    const int rs = receiver_source<MULTI>(p);
+__device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b) {
+  if (b.z < p.rec_layers) {
+    const int rs = receiver_source<MULTI>(p, b);
     const Fields f = fields_of<MULTI>(p, rs);
-    receiver_dft<R, CONV>(p, 0, f.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p),
+    receiver_dft<R, CONV>(p, 0, f.E, p.fE + static_cast<size_t>(n) * p.nf * 2, receiver_block<MULTI>(p, b),
                     p.rec_acc + static_cast<size_t>(rs) * p.nrec * 6 * p.nf * 2);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of<MULTI>(p);
+  const Origin o = origin_of<MULTI>(p, b);
   if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
 
   const Quad u = quad_of(o);
@@ -821,6 +833,63 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
     h_quad<R, true>(p, f, v, u, h, ps, n);
   else
     h_quad<R, false>(p, f, v, u, h, ps, n);
+}
+
+template <int R, bool MULTI, bool CONV>
+__global__ void __launch_bounds__(NT, min_ctas(R))
+    k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
+  wait_prior_grid();
+  if (CONV && *p.halt) return;  // a convergence run that has stopped
+  allow_next_launch();
+  h_block<R, MULTI, CONV>(p, tm, n, launch_blk());
+}
+
+// ---------------------------------------------------------------------------
+// Work-list launches: the half-steps of several problems (grids of any size,
+// one transmitter each, one order R) in one launch.  The launch parameters
+// carry every problem's DevParams and its tensor maps for this half-step;
+// CTA b of the 1-D grid belongs to the problem j with cta0[j] <= b <
+// cta0[j+1] and takes the place of CTA b - cta0[j] of that problem's own
+// launch grid (x fastest), so the problems' tails overlap inside one launch
+// instead of each draining alone.
+// ---------------------------------------------------------------------------
+constexpr int kMaxJobs = 16;
+struct JobSet {
+  TmaSet tm[kMaxJobs];
+  DevParams p[kMaxJobs];
+  int cta0[kMaxJobs + 1];
+  int nt[kMaxJobs];  // a problem whose steps are done returns at once
+  int njobs;
+};
+
+__device__ __forceinline__ int job_of(const JobSet &J, int b) {
+  int j = 0;
+  while (j + 1 < J.njobs && b >= J.cta0[j + 1]) ++j;
+  return j;
+}
+__device__ __forceinline__ Blk job_blk(const DevParams &p, int l) {
+  const int tx = p.tiles_x, ty = p.tiles_y;
+  return Blk{l % tx, (l / tx) % ty, l / (tx * ty)};
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, min_ctas(R)) k_update_E_jobs(const __grid_constant__ JobSet J, const int n) {
+  wait_prior_grid();
+  allow_next_launch();
+  const int b = static_cast<int>(blockIdx.x), j = job_of(J, b);
+  if (n >= J.nt[j]) return;
+  const DevParams &p = J.p[j];
+  e_block<R, false, false, false>(p, J.tm[j], n, job_blk(p, b - J.cta0[j]));
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, min_ctas(R)) k_update_H_jobs(const __grid_constant__ JobSet J, const int n) {
+  wait_prior_grid();
+  allow_next_launch();
+  const int b = static_cast<int>(blockIdx.x), j = job_of(J, b);
+  if (n >= J.nt[j]) return;
+  const DevParams &p = J.p[j];
+  h_block<R, false, false>(p, J.tm[j], n, job_blk(p, b - J.cta0[j]));
 }
 
 // Sources the stencil kernels do not inject themselves, one thread per
@@ -1689,6 +1758,175 @@ cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0
   }
 }
 
+// Work-list solve of prepared problems P (one order R): every leapfrog step
+// is one E and one H launch over all of them.
+template <int R>
+cudaError_t launch_jobs(const std::vector<Prepared> &P, const std::vector<int> &nts, cudaStream_t st) {
+  const int nj = static_cast<int>(P.size());
+  std::unique_ptr<JobSet> JE(new JobSet{}), JH(new JobSet{});
+  int total = 0, nmax = 0;
+  for (int j = 0; j < nj; ++j) {
+    const DevParams &p = P[j].p;
+    if (!make_tiles<R>(&JE->tm[j], p.H, p) || !make_tiles<R>(&JH->tm[j], p.E, p)) return cudaErrorInvalidValue;
+    JE->p[j] = JH->p[j] = p;
+    JE->cta0[j] = JH->cta0[j] = total;
+    JE->nt[j] = JH->nt[j] = nts[j];
+    total += static_cast<int>(P[j].blocks.x * P[j].blocks.y * P[j].blocks.z);
+    nmax = std::max(nmax, nts[j]);
+  }
+  JE->cta0[nj] = JH->cta0[nj] = total;
+  JE->njobs = JH->njobs = nj;
+  const size_t sb = smem_bytes<R>();
+  cudaError_t e = cudaFuncSetAttribute(k_update_E_jobs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sb));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_H_jobs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  for (int n = 0; n < nmax && e == cudaSuccess; ++n) {
+    e = launch_dependent(k_update_E_jobs<R>, dim3(static_cast<unsigned>(total)), dim3(NT), sb, st, *JE, n);
+    if (e == cudaSuccess)
+      e = launch_dependent(k_update_H_jobs<R>, dim3(static_cast<unsigned>(total)), dim3(NT), sb, st, *JH, n);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// Workspace slices of a work list: each problem's forward workspace, 256-byte
+// aligned, one after the other.
+int jobs_layout(int nj, const emm_job *jobs, std::vector<size_t> *off, size_t *total) {
+  if (nj < 1 || nj > kMaxJobs || !jobs) return EMM_EINVAL;
+  size_t o = 0;
+  off->clear();
+  for (int j = 0; j < nj; ++j) {
+    const emm_survey *s = jobs[j].survey;
+    const int st = check_survey(jobs[j].grid, s);
+    if (st != EMM_OK) return st;
+    if (s->volume || s->airwave || s->src_kind != 0 || s->src_length > 0 || jobs[j].grid->rd != jobs[0].grid->rd)
+      return EMM_EINVAL;
+    off->push_back(o);
+    o = align_up(o + plan(jobs[j].grid, s).total);
+  }
+  *total = o;
+  return EMM_OK;
+}
+
+// Steps n0 .. n1-1 of prepared problems by one strategy (EMM_JOBS_*): the
+// work-list launches; each problem's steps in turn on cs; or each problem on
+// a stream of its own, forked from cs and joined back to it.
+cudaError_t run_jobs(const std::vector<Prepared> &P, const std::vector<int> &nts, int strategy, int n0, int n1,
+                     cudaStream_t cs) {
+  const int nj = static_cast<int>(P.size());
+  std::vector<int> ends(nj);
+  for (int j = 0; j < nj; ++j) ends[j] = std::min(nts[j], n1);
+  if (strategy == EMM_JOBS_LIST) {
+    if (n0 != 0) return cudaErrorInvalidValue;
+    switch (P[0].rd) {
+      case 1: return launch_jobs<1>(P, ends, cs);
+      case 2: return launch_jobs<2>(P, ends, cs);
+      case 3: return launch_jobs<3>(P, ends, cs);
+      default: return launch_jobs<4>(P, ends, cs);
+    }
+  }
+  if (strategy == EMM_JOBS_SEQUENTIAL) {
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < nj && e == cudaSuccess; ++j)
+      if (n0 < ends[j]) e = run_steps(P[j], P[j].p, P[j].blocks, n0, ends[j], cs, nullptr);
+    return e;
+  }
+  // EMM_JOBS_STREAMS: the streams and events are released once their work is done
+  cudaEvent_t fork;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(fork, cs);
+  for (int j = 0; j < nj && e == cudaSuccess; ++j) {
+    cudaStream_t sj;
+    cudaEvent_t done;
+    e = cudaStreamCreateWithFlags(&sj, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sj, fork, 0);
+    if (e == cudaSuccess && n0 < ends[j]) e = run_steps(P[j], P[j].p, P[j].blocks, n0, ends[j], sj, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(done, sj);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, done, 0);
+    cudaEventDestroy(done);
+    cudaStreamDestroy(sj);
+  }
+  cudaEventDestroy(fork);
+  return e;
+}
+
+int prepare_jobs(int nj, const emm_job *jobs, void *ws, size_t ws_bytes, cudaStream_t cs, std::vector<Prepared> *P,
+                 std::vector<int> *nts) {
+  std::vector<size_t> off;
+  size_t total = 0;
+  int st = jobs_layout(nj, jobs, &off, &total);
+  if (st != EMM_OK) return st;
+  if (!ws || ws_bytes < total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
+  for (int j = 0; j < nj; ++j)
+    if (!jobs[j].sigma || (jobs[j].survey->nrec > 0 && !jobs[j].rec_out)) return EMM_EINVAL;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  P->assign(nj, Prepared{});
+  nts->assign(nj, 0);
+  for (int j = 0; j < nj; ++j) {
+    const size_t end = j + 1 < nj ? off[j + 1] : total;
+    st = prepare_forward(jobs[j].grid, jobs[j].survey, jobs[j].sigma, base + off[j], end - off[j], jobs[j].rec_out,
+                         nullptr, cs, &(*P)[j]);
+    if (st != EMM_OK) return st;
+    (*nts)[j] = jobs[j].survey->nt;
+  }
+  return EMM_OK;
+}
+
+int forward_jobs_impl(int nj, const emm_job *jobs, int strategy, void *ws, size_t ws_bytes, cudaStream_t cs) {
+  if (strategy < EMM_JOBS_LIST || strategy > EMM_JOBS_STREAMS) return EMM_EINVAL;
+  std::vector<Prepared> P;
+  std::vector<int> nts;
+  int st = prepare_jobs(nj, jobs, ws, ws_bytes, cs, &P, &nts);
+  if (st != EMM_OK) return st;
+  const int nmax = *std::max_element(nts.begin(), nts.end());
+  if (run_jobs(P, nts, strategy, 0, nmax, cs) != cudaSuccess) return EMM_ECUDA;
+  for (int j = 0; j < nj; ++j) {
+    st = finalize_forward(P[j], jobs[j].survey, jobs[j].rec_out, nullptr, cs);
+    if (st != EMM_OK) return st;
+  }
+  return EMM_OK;
+}
+
+// Times the first `steps` leapfrog steps (at most each problem's own) of
+// every strategy on the problems (after a warm-up of a few steps each) and
+// returns the fastest.  Synchronises cs;
+// leaves the workspace to be prepared again by the next solve.
+int jobs_tune(int nj, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, cudaStream_t cs, double *ms,
+              int *best) {
+  if (steps < 1 || !ms || !best) return EMM_EINVAL;
+  std::vector<Prepared> P;
+  std::vector<int> nts;
+  int st = prepare_jobs(nj, jobs, ws, ws_bytes, cs, &P, &nts);
+  if (st != EMM_OK) return st;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return EMM_ECUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return EMM_ECUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = EMM_JOBS_LIST; k <= EMM_JOBS_STREAMS && e == cudaSuccess; ++k) {
+    e = run_jobs(P, nts, k, 0, std::min(steps, 4), cs);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, cs);
+    if (e == cudaSuccess) e = run_jobs(P, nts, k, 0, steps, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(b, cs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    ms[k] = t;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return EMM_ECUDA;
+  *best = EMM_JOBS_LIST;
+  for (int k = EMM_JOBS_LIST; k <= EMM_JOBS_STREAMS; ++k)
+    if (ms[k] < ms[*best]) *best = k;
+  return EMM_OK;
+}
+
 int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, double *vol_out, cudaStream_t cs) {
   const int nf = s->nfreq;
   const double *dnorm = reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(P.p.status) -
@@ -1870,6 +2108,25 @@ int emm_forward_converge(const emm_grid *g, const emm_survey *s, const float *si
   if (st == EMM_OK && cudaStreamSynchronize(cs) != cudaSuccess) st = EMM_ECUDA;
   *nt_run = kept;
   return st;
+}
+
+int emm_jobs_workspace_size(int njobs, const emm_job *jobs, size_t *bytes, size_t *offsets) {
+  if (!bytes) return EMM_EINVAL;
+  std::vector<size_t> off;
+  const int st = emm::jobs_layout(njobs, jobs, &off, bytes);
+  if (st != EMM_OK) return st;
+  if (offsets)
+    for (int j = 0; j < njobs; ++j) offsets[j] = off[j];
+  return EMM_OK;
+}
+
+int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, size_t ws_bytes, emm_stream stream) {
+  return emm::forward_jobs_impl(njobs, jobs, strategy, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
+                  double *ms, int *best) {
+  return emm::jobs_tune(njobs, jobs, ws, ws_bytes, steps, reinterpret_cast<cudaStream_t>(stream), ms, best);
 }
 
 int emm_batch_workspace_size(const emm_grid *g, const emm_survey *s, int nsrc, size_t *bytes) {

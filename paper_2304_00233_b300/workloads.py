@@ -30,7 +30,7 @@ __all__ = [
     "LayeredModel", "Box", "cell_conductivity", "staggered_conductivity",
     "Workload", "whole_space", "marine_1d", "anomaly_3d", "small_case",
     "gradient_survey", "gradient_survey_48", "GRADIENT_SOURCES", "GRADIENT_SOURCES_48",
-    "observed_noise", "WORKLOADS",
+    "observed_noise", "uneven_grid", "uneven_jobs", "UNEVEN_GRIDS", "WORKLOADS",
 ]
 
 
@@ -419,6 +419,44 @@ def gradient_survey_48(with_resistor: bool = False, nt: int = 200) -> Workload:
     name = "gradient_survey_48" + ("_resistor" if with_resistor else "")
     return Workload(name, x, x.copy(), z, _f32(sig), 2, 10, 7, GRADIENT_SOURCES_48[0].copy(), 0.0, 0.0, 1.0,
                     rec, np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4, nt=nt, sigma_h=sh, sigma_v=sv)
+
+
+def _stretched_length(n: int, d0: float = 40.0, d1: float = 200.0) -> float:
+    # length of n geometric cells growing from d0 to d1 (ratio (d1/d0)^(1/(n-1)))
+    q = (d1 / d0) ** (1.0 / (n - 1))
+    return d0 * (q ** n - 1.0) / (q - 1.0)
+
+
+def uneven_grid(n1: int, n3: int) -> Workload:
+    """One problem of the uneven-grid work list: the layered marine model
+    (with the resistor) on n1 x n1 x n3 nodes, x and y n1/2 cells per side
+    and z 16 cells above the seabed over 1000 m and n3 - 17 below it, every
+    axis growing from 40 m to about 200 m; the transmitter 50 m above the
+    seabed at the grid centre, seabed receivers every 200 m from -3100 m to
+    3100 m (those within 80 % of the half-width on smaller grids)."""
+    half = n1 // 2
+    L = _stretched_length(half)
+    x = symmetric_axis(n1, L, 40.0)
+    n_down = n3 - 17
+    z = seabed_axis(1000.0, 16, 1000.0, n_down, _stretched_length(n_down), 40.0)
+    sh, sv = cell_conductivity(_marine_model(True), x, x, z)
+    sig = staggered_conductivity(sh, sv, x, x, z)
+    xr = -3100.0 + 200.0 * np.arange(32)
+    xr = xr[np.abs(xr) <= 0.8 * L]
+    rec = np.zeros((len(xr), 3))
+    rec[:, 0] = xr
+    rec[:, 2] = 1000.0
+    return Workload(f"uneven_{n1}x{n1}x{n3}", x, x.copy(), z, _f32(sig), 2, 10, 7, np.array([0.0, 0.0, 950.0]),
+                    0.0, 0.0, 1.0, rec, np.array([0.25, 0.75, 1.25]), 2 * math.pi, 1.0, 6.4)
+
+
+# the uneven-grid work list: 3 x 96^3, 3 x 160 x 160 x 120, 2 x 200 x 200 x 140 nodes
+UNEVEN_GRIDS = [(96, 96)] * 3 + [(160, 120)] * 3 + [(200, 140)] * 2
+
+
+def uneven_jobs() -> List[Workload]:
+    """The eight problems of the uneven-grid work list (``UNEVEN_GRIDS``)."""
+    return [uneven_grid(a, b) for a, b in UNEVEN_GRIDS]
 
 
 def observed_noise(shape, seed: int = 230400234, level: float = 0.02) -> np.ndarray:

@@ -80,3 +80,30 @@ def test_antenna_workspace_holds_the_union_boxes():
     ant = emm.Survey(**{**point.__dict__, "src_length": 60.0, "src_points": 6})
     assert emm.workspace_size(g, ant) > emm.workspace_size(g, point)
 
+
+
+def test_work_list_layout_and_errors():
+    from paper_2304_00233_b300 import workloads as W
+    wls = [W.small_case(n=(20, 18, 16), rd=2, nt=10, volume=False), W.small_case(n=(26, 22, 19), rd=2, nt=12,
+                                                                                  volume=False)]
+    probs = [(emm.grid_for(w), emm.survey_for(w)) for w in wls]
+    sizes = [emm.workspace_size(g, s) for g, s in probs]
+    jobs, keep = emm._jobs_c(probs, [None, None], [None, None])
+    n = emm.C.c_size_t(0)
+    offs = (emm.C.c_size_t * 2)()
+    assert emm.load_library().emm_jobs_workspace_size(2, jobs, emm.C.byref(n), offs) == emm.EMM_OK
+    assert offs[0] == 0 and offs[1] >= sizes[0] and offs[1] % 256 == 0
+    assert n.value >= offs[1] + sizes[1]
+    lib = emm.load_library()
+    assert lib.emm_jobs_workspace_size(0, jobs, emm.C.byref(n), None) == emm.EMM_EINVAL
+    assert lib.emm_jobs_workspace_size(17, jobs, emm.C.byref(n), None) == emm.EMM_EINVAL
+    # differing FD orders, or a volume DTFT, are refused
+    w4 = W.small_case(n=(24, 22, 20), rd=4, nt=10, volume=False)
+    bad, keep2 = emm._jobs_c([probs[0], (emm.grid_for(w4), emm.survey_for(w4))], [None, None], [None, None])
+    assert lib.emm_jobs_workspace_size(2, bad, emm.C.byref(n), None) == emm.EMM_EINVAL
+    wv = W.small_case(n=(20, 18, 16), rd=2, nt=10, volume=True)
+    bad, keep3 = emm._jobs_c([probs[0], (emm.grid_for(wv), emm.survey_for(wv))], [None, None], [None, None])
+    assert lib.emm_jobs_workspace_size(2, bad, emm.C.byref(n), None) == emm.EMM_EINVAL
+    # a workspace that is too small is refused before anything is enqueued
+    assert lib.emm_forward_jobs(2, jobs, emm.JOBS_LIST, None, 0, None) == emm.EMM_EWORKSPACE
+    assert lib.emm_forward_jobs(2, jobs, 3, None, 0, None) == emm.EMM_EINVAL
