@@ -83,7 +83,7 @@ struct DevParams {
                     // otherwise k_inject does, after the E or the H launch
   size_t jstride;   // floats of jw per transmitter
   // Air above the model (airwave runs; else air_on = 0): interface row ks,
-  // DFT matrices e^{-2 pi i (a b mod np) / np} per axis ([np][np]), continuation factors of the E
+  // roots of unity e^{-2 pi i m / np} per axis ([np]), continuation factors of the E
   // rows [rd-1][np1][np0] and of the H rows [2][rd][np1][np0] (H_x, H_y),
   // and the work planes T, F [nsrc][3][np1][np0] and U [nsrc][2 rd][np1][np0].
   int air_on, air_ks, air_rd;

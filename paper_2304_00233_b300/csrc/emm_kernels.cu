@@ -930,110 +930,128 @@ __global__ void k_inject(const DevParams p, const int n) {
 // KIND 0, after the E launch: the E_x, E_y interface rows continued to the
 // rd - 1 integer rows above; KIND 1, after the H launch: the H_z interface
 // row to H_x, H_y on the rd half rows above.  The 2-D DFT of the padded x-y
-// plane and its inverse are four products with DFT matrices:
+// plane and its inverse are four passes of 1-D transforms:
 //   MODE 0 (rows):     T[c][j][q] = sum_i f_c(i, j) w0^{q i}
 //   MODE 1 (columns):  F[c][k][q] = sum_j w1^{k j} T[c][j][q]
 //   MODE 2 (inverse columns, times the continuation factor of output o):
 //                      U[o][j][q] = sum_k conj(w1^{j k}) F[c(o)][k][q] fac_o[k][q]
 //   MODE 3 (inverse rows, real part, into the field row of output o):
 //                      out_o(i, j) = Re sum_q U[o][j][q] conj(w0^{q i}) / (N0 N1)
-// with w0 = e^{-2 pi i / N0}, w1 = e^{-2 pi i / N1}: tiled complex matrix
-// products, 16 x 16 outputs per CTA (one per thread), the contraction in
-// tiles of 32 staged in shared memory, the DFT matrices tabulated in FP64 on
-// the host.  Grid z = transmitter.
-constexpr int AT = 16;
+// with w0 = e^{-2 pi i / N0}, w1 = e^{-2 pi i / N1}.  One CTA per line
+// (grid x = line, z = transmitter): the line is gathered into shared memory
+// and transformed by a mixed-radix Stockham FFT (radix 4 while 4 divides
+// the rest of N, then its smallest prime factors; any N), one thread per
+// output sample of each stage, with the roots of unity (tabulated in FP64
+// on the host) in shared memory.
+constexpr int AFT = 256;  // threads of an air transform CTA
 
+// One Stockham stage of a length-N transform: radix r after sub-transforms
+// of length Ns.  Output o = (t / Ns) Ns r + p Ns + k (k < Ns, p < r) is
+//   sum_q in[t + q N / r] W^{q (k + p Ns) N / (Ns r)},  t = (o / (Ns r)) Ns + k,
+// W = e^{-2 pi i / N} (conjugated for the inverse).
+template <bool INV>
+__device__ __forceinline__ void fft_stage(const float2 *in, float2 *out, const float2 *W, int N, int Ns, int r) {
+  const int span = Ns * r, step = N / span, m = N / r;
+  for (int o = threadIdx.x; o < N; o += AFT) {
+    const int blk = o / span, w = o % span, pp = w / Ns, k = w % Ns, t = blk * Ns + k;
+    const int e = (k + pp * Ns) * step;  // W exponent of q = 1
+    float2 acc = in[t];
+    int x = 0;
+    for (int q = 1; q < r; ++q) {
+      x += e;
+      if (x >= N) x -= N;
+      const float2 a = in[t + q * m], wq = W[x];
+      const float wy = INV ? -wq.y : wq.y;
+      acc.x = fmaf(a.x, wq.x, fmaf(-a.y, wy, acc.x));
+      acc.y = fmaf(a.x, wy, fmaf(a.y, wq.x, acc.y));
+    }
+    out[o] = acc;
+  }
+  __syncthreads();
+}
+
+// Transforms the line in b0 over the buffers b0, b1; returns the buffer
+// that holds the result.
+template <bool INV>
+__device__ __forceinline__ float2 *fft_line(float2 *b0, float2 *b1, const float2 *W, int N) {
+  int rest = N, Ns = 1;
+  while (rest > 1) {
+    int r = rest % 4 == 0 ? 4 : 0;
+    if (!r) {
+      r = 2;
+      while (rest % r) r = r == 2 ? 3 : r + 2;
+    }
+    fft_stage<INV>(b0, b1, W, N, Ns, r);
+    float2 *t = b0;
+    b0 = b1;
+    b1 = t;
+    Ns *= r;
+    rest /= r;
+  }
+  return b0;
+}
+
+// Shared memory: the N roots of unity and two line buffers.
 template <int MODE, bool MULTI, int KIND>
-__global__ void __launch_bounds__(AT * AT) k_air_dft(const DevParams p) {
+__global__ void __launch_bounds__(AFT) k_air_fft(const DevParams p) {
   wait_prior_grid();
   if (p.halt && *p.halt) return;
   allow_next_launch();
-  constexpr int KT = 2 * AT;  // contraction tile
-  __shared__ float2 As[AT][KT + 1], Bs[KT][AT + 1];
+  extern __shared__ float2 air_sm[];
   const int N0 = p.np[0], N1 = p.np[1], rd = p.air_rd, src = static_cast<int>(blockIdx.z);
-  const int nin = KIND == 0 ? 2 : 1, nout = KIND == 0 ? 2 * (rd - 1) : 2 * rd;
-  // product dimensions: Out[a][b] = sum_c A[a][c] B[c][b]
-  const int NA = MODE == 0 ? nin * N1 : MODE == 3 ? nout * N1 : N1;
-  const int NB = MODE == 1 ? nin * N0 : MODE == 2 ? nout * N0 : N0;
-  const int NC = (MODE == 0 || MODE == 3) ? N0 : N1;
+  const int N = (MODE == 0 || MODE == 3) ? N0 : N1;
+  const int ln = static_cast<int>(blockIdx.x);  // line: MODE 0 c N1 + j; 1 c N0 + q; 2 o N0 + q; 3 o N1 + j
   const size_t plane = static_cast<size_t>(N0) * N1;
   const Fields f = fields_of<MULTI>(p, src);
-  const float2 *T = p.air_T + static_cast<size_t>(src) * 3 * plane;
-  const float2 *F = p.air_F + static_cast<size_t>(src) * 3 * plane;
-  const float2 *U = p.air_U + static_cast<size_t>(src) * 2 * rd * plane;
-  const int a0 = static_cast<int>(blockIdx.y) * AT, b0 = static_cast<int>(blockIdx.x) * AT;
-  const int tx = threadIdx.x % AT, ty = threadIdx.x / AT;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int c0 = 0; c0 < NC; c0 += KT) {
-    for (int h = 0; h < 2; ++h) {
-      {  // A tile element (a0 + ty, c0 + h AT + tx)
-        const int col = h * AT + tx, a = a0 + ty, c = c0 + col;
-        float2 v = make_float2(0.f, 0.f);
-        if (a < NA && c < NC) {
-          if (MODE == 0) {
-            const int comp = a / N1, j = a % N1;
-            const float *fc = KIND == 0 ? (comp == 0 ? f.E[0] : f.E[1]) : f.H[2];
-            v.x = fc[static_cast<size_t>(p.air_ks) * p.plane + static_cast<size_t>(j) * p.pitch + c];
-          } else if (MODE == 3) {
-            v = U[static_cast<size_t>(a) * N0 + c];  // a = o N1 + j
-          } else {
-            const float2 w = p.air_twy[static_cast<size_t>(a) * N1 + c];
-            v = MODE == 1 ? w : make_float2(w.x, -w.y);
-          }
-        }
-        As[ty][col] = v;
+  float2 *T = p.air_T + static_cast<size_t>(src) * 3 * plane;
+  float2 *F = p.air_F + static_cast<size_t>(src) * 3 * plane;
+  float2 *U = p.air_U + static_cast<size_t>(src) * 2 * rd * plane;
+  float2 *Ws = air_sm, *b0 = air_sm + N, *b1 = b0 + N;
+  const float2 *W = (MODE == 0 || MODE == 3) ? p.air_twx : p.air_twy;
+  for (int i = threadIdx.x; i < N; i += AFT) {
+    Ws[i] = W[i];
+    float2 v;
+    if (MODE == 0) {
+      const int c = ln / N1, j = ln % N1;
+      const float *fc = KIND == 0 ? (c == 0 ? f.E[0] : f.E[1]) : f.H[2];
+      v = make_float2(fc[static_cast<size_t>(p.air_ks) * p.plane + static_cast<size_t>(j) * p.pitch + i], 0.f);
+    } else if (MODE == 1) {
+      const int c = ln / N0, q = ln % N0;
+      v = T[(static_cast<size_t>(c) * N1 + i) * N0 + q];
+    } else if (MODE == 2) {
+      const int o = ln / N0, q = ln % N0, r2 = o / 2, comp = KIND == 0 ? o % 2 : 0;
+      const float2 x = F[(static_cast<size_t>(comp) * N1 + i) * N0 + q];
+      const size_t fi = static_cast<size_t>(i) * N0 + q;
+      if (KIND == 0) {
+        const float g = p.air_decE[r2 * plane + fi];
+        v = make_float2(x.x * g, x.y * g);
+      } else {
+        const float2 g = p.air_facH[(static_cast<size_t>(o % 2) * rd + r2) * plane + fi];
+        v = make_float2(x.x * g.x - x.y * g.y, x.x * g.y + x.y * g.x);
       }
-      {  // B tile element (c0 + h AT + ty, b0 + tx)
-        const int row = h * AT + ty, c = c0 + row, b = b0 + tx;
-        float2 v = make_float2(0.f, 0.f);
-        if (c < NC && b < NB) {
-          if (MODE == 0 || MODE == 3) {
-            const float2 w = p.air_twx[static_cast<size_t>(c) * N0 + b];
-            v = MODE == 0 ? w : make_float2(w.x, -w.y);
-          } else if (MODE == 1) {
-            const int comp = b / N0, q = b % N0;
-            v = T[(static_cast<size_t>(comp) * N1 + c) * N0 + q];
-          } else {
-            const int o = b / N0, q = b % N0, r2 = o / 2;
-            const int comp = KIND == 0 ? o % 2 : 0;
-            const float2 x = F[(static_cast<size_t>(comp) * N1 + c) * N0 + q];
-            const size_t fi = static_cast<size_t>(c) * N0 + q;
-            if (KIND == 0) {
-              const float g = p.air_decE[r2 * plane + fi];
-              v = make_float2(x.x * g, x.y * g);
-            } else {
-              const float2 g = p.air_facH[(static_cast<size_t>(o % 2) * rd + r2) * plane + fi];
-              v = make_float2(x.x * g.x - x.y * g.y, x.x * g.y + x.y * g.x);
-            }
-          }
-        }
-        Bs[row][tx] = v;
-      }
+    } else {
+      v = U[static_cast<size_t>(ln) * N0 + i];  // ln = o N1 + j
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-      const float2 bv = Bs[k][tx], av = As[ty][k];
-      acc.x = fmaf(av.x, bv.x, fmaf(-av.y, bv.y, acc.x));
-      acc.y = fmaf(av.x, bv.y, fmaf(av.y, bv.x, acc.y));
-    }
-    __syncthreads();
+    b0[i] = v;
   }
-  const int b = b0 + tx, a = a0 + ty;
-  if (b >= NB || a >= NA) return;
-  if (MODE == 0) {
-    p.air_T[static_cast<size_t>(src) * 3 * plane + static_cast<size_t>(a) * N0 + b] = acc;  // a = comp N1 + j
-  } else if (MODE == 1) {
-    const int comp = b / N0, q = b % N0;
-    p.air_F[static_cast<size_t>(src) * 3 * plane + (static_cast<size_t>(comp) * N1 + a) * N0 + q] = acc;
-  } else if (MODE == 2) {
-    const int o = b / N0, q = b % N0;
-    p.air_U[static_cast<size_t>(src) * 2 * rd * plane + (static_cast<size_t>(o) * N1 + a) * N0 + q] = acc;
-  } else {
-    const int o = a / N1, j = a % N1, r2 = o / 2, d = o % 2;
-    float *out = KIND == 0 ? (d == 0 ? f.E[0] : f.E[1]) : (d == 0 ? f.H[0] : f.H[1]);
-    out[static_cast<size_t>(p.air_ks - 1 - r2) * p.plane + static_cast<size_t>(j) * p.pitch + b] =
-        acc.x / (static_cast<float>(N0) * static_cast<float>(N1));
+  __syncthreads();
+  const float2 *res = fft_line<(MODE >= 2)>(b0, b1, Ws, N);
+  const float scale = 1.f / (static_cast<float>(N0) * static_cast<float>(N1));
+  for (int i = threadIdx.x; i < N; i += AFT) {
+    const float2 v = res[i];
+    if (MODE == 0) {
+      T[static_cast<size_t>(ln) * N0 + i] = v;  // ln = c N1 + j
+    } else if (MODE == 1) {
+      const int c = ln / N0, q = ln % N0;
+      F[(static_cast<size_t>(c) * N1 + i) * N0 + q] = v;
+    } else if (MODE == 2) {
+      const int o = ln / N0, q = ln % N0;
+      U[(static_cast<size_t>(o) * N1 + i) * N0 + q] = v;
+    } else {
+      const int o = ln / N1, j = ln % N1, r2 = o / 2, d = o % 2;
+      float *out = KIND == 0 ? (d == 0 ? f.E[0] : f.E[1]) : (d == 0 ? f.H[0] : f.H[1]);
+      out[static_cast<size_t>(p.air_ks - 1 - r2) * p.plane + static_cast<size_t>(j) * p.pitch + i] = v.x * scale;
+    }
   }
 }
 
@@ -1275,8 +1293,8 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   L.fH32 = take(nt * nf * 2 * sizeof(float));
   L.norm = take(2 * nf * 2 * sizeof(double));
   // air: twiddles and continuation factors
-  L.air_twx = take(s->airwave ? static_cast<size_t>(g->ax[0].npad) * g->ax[0].npad * 8 : 0);
-  L.air_twy = take(s->airwave ? static_cast<size_t>(g->ax[1].npad) * g->ax[1].npad * 8 : 0);
+  L.air_twx = take(s->airwave ? static_cast<size_t>(g->ax[0].npad) * 8 : 0);
+  L.air_twy = take(s->airwave ? static_cast<size_t>(g->ax[1].npad) * 8 : 0);
   L.air_decE = take(s->airwave ? static_cast<size_t>(g->rd - 1) * plane2 * 4 : 0);
   L.air_facH = take(s->airwave ? 2 * static_cast<size_t>(g->rd) * plane2 * 8 : 0);
   L.total = off;
@@ -1323,23 +1341,27 @@ bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
          make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
 }
 
-// The four air products after a half step (see k_air_dft).
+// The four air transform passes after a half step (see k_air_fft).
 template <bool MULTI, int KIND>
 cudaError_t air_step(const DevParams &p, cudaStream_t st) {
   const int rd = p.air_rd, N0 = p.np[0], N1 = p.np[1];
   const int nin = KIND == 0 ? 2 : 1, nout = KIND == 0 ? 2 * (rd - 1) : 2 * rd;
-  auto tiles = [](int n) { return static_cast<unsigned>((n + AT - 1) / AT); };
   const unsigned z = static_cast<unsigned>(p.nsrc);
-  const dim3 tb(AT * AT);
+  const dim3 tb(AFT);
+  const size_t s0 = 3 * sizeof(float2) * N0, s1 = 3 * sizeof(float2) * N1;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess)
-    e = launch_dependent(k_air_dft<0, MULTI, KIND>, dim3(tiles(N0), tiles(nin * N1), z), tb, 0, st, p);
-  if (e == cudaSuccess)
-    e = launch_dependent(k_air_dft<1, MULTI, KIND>, dim3(tiles(nin * N0), tiles(N1), z), tb, 0, st, p);
-  if (e == cudaSuccess)
-    e = launch_dependent(k_air_dft<2, MULTI, KIND>, dim3(tiles(nout * N0), tiles(N1), z), tb, 0, st, p);
-  if (e == cudaSuccess)
-    e = launch_dependent(k_air_dft<3, MULTI, KIND>, dim3(tiles(N0), tiles(nout * N1), z), tb, 0, st, p);
+  if (std::max(s0, s1) > 48 * 1024) {  // lines of more than 2048 samples
+    const int mx = static_cast<int>(std::max(s0, s1));
+    e = cudaFuncSetAttribute(k_air_fft<0, MULTI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_air_fft<1, MULTI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_air_fft<2, MULTI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_air_fft<3, MULTI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_dependent(k_air_fft<0, MULTI, KIND>, dim3(nin * N1, 1, z), tb, s0, st, p);
+  if (e == cudaSuccess) e = launch_dependent(k_air_fft<1, MULTI, KIND>, dim3(nin * N0, 1, z), tb, s1, st, p);
+  if (e == cudaSuccess) e = launch_dependent(k_air_fft<2, MULTI, KIND>, dim3(nout * N0, 1, z), tb, s1, st, p);
+  if (e == cudaSuccess) e = launch_dependent(k_air_fft<3, MULTI, KIND>, dim3(nout * N1, 1, z), tb, s0, st, p);
   return e;
 }
 
@@ -1593,19 +1615,11 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
         if (std::fabs((ax.X[i] - ax.X[i - 1]) - d[a]) > 1e-9 * d[a]) return EMM_EINVAL;
     }
     float2 *twx = reinterpret_cast<float2 *>(at(L.air_twx)), *twy = reinterpret_cast<float2 *>(at(L.air_twy));
-    // the DFT matrices W[a][b] = e^{-2 pi i (a b mod N) / N}
-    for (int a = 0; a < N0; ++a)
-      for (int b = 0; b < N0; ++b) {
-        const int m = static_cast<int>((static_cast<long long>(a) * b) % N0);
-        twx[static_cast<size_t>(a) * N0 + b] =
-            make_float2(static_cast<float>(std::cos(2 * M_PI * m / N0)), static_cast<float>(-std::sin(2 * M_PI * m / N0)));
-      }
-    for (int a = 0; a < N1; ++a)
-      for (int b = 0; b < N1; ++b) {
-        const int m = static_cast<int>((static_cast<long long>(a) * b) % N1);
-        twy[static_cast<size_t>(a) * N1 + b] =
-            make_float2(static_cast<float>(std::cos(2 * M_PI * m / N1)), static_cast<float>(-std::sin(2 * M_PI * m / N1)));
-      }
+    // the roots of unity W[m] = e^{-2 pi i m / N}
+    for (int m = 0; m < N0; ++m)
+      twx[m] = make_float2(static_cast<float>(std::cos(2 * M_PI * m / N0)), static_cast<float>(-std::sin(2 * M_PI * m / N0)));
+    for (int m = 0; m < N1; ++m)
+      twy[m] = make_float2(static_cast<float>(std::cos(2 * M_PI * m / N1)), static_cast<float>(-std::sin(2 * M_PI * m / N1)));
     const Axis &az = g->ax[2];
     float *decE = reinterpret_cast<float *>(at(L.air_decE));
     float2 *facH = reinterpret_cast<float2 *>(at(L.air_facH));
