@@ -18,6 +18,7 @@ host cores, each step a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -270,6 +271,7 @@ def gradient_survey_line(emm, torch, stream, job_max):
     fwd_ms = job_max(f0.elapsed_time(f1) / 1e3) * 1e3
     del work
     ck = max(1, int(round(nt ** 0.5)))
+    gc.collect()
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
     room = free - (6 << 30)
@@ -292,7 +294,7 @@ def gradient_survey_line(emm, torch, stream, job_max):
     return {"workload": "gradient_survey_192x192x128", "nsrc": len(pos), "timesteps_per_solve": nt,
             "cells": grid.cells, "ms": ms, "forward_ms": fwd_ms, "ratio_to_forward": ms / (len(pos) * fwd_ms),
             "ckpt_every": ck, "stored_steps": stored, "snapshot_gb": stored * snap / 1e9,
-            "misfit": misfit.item(), "finite": ok,
+            "free_gb_before": free / 1e9, "misfit": misfit.item(), "finite": ok,
             "what": "emm_stagger_sigma, then per transmitter emm_misfit_gradient (forward sweep, residual "
                     "of the noisy resistor-model data, adjoint sweep) and emm_stagger_sigma_adjoint into "
                     "the sigma_h, sigma_v gradients; ratio against one forward solve per transmitter"}
@@ -370,7 +372,7 @@ def main():
                     help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid (about a minute)")
     ap.add_argument("--no-airwave", action="store_true",
                     help="skip the air-boundary line (uniform-xy marine model with and without air on top)")
-    ap.add_argument("--batch", type=int, default=8,
+    ap.add_argument("--batch", type=int, default=32,
                     help="transmitters of the batched-survey line (emm_forward_batch; 0 = skip)")
     ap.add_argument("--timesteps", type=int, default=0,
                     help="override the leapfrog steps per solve (short profiling runs only)")
@@ -482,21 +484,37 @@ def main():
     if args.batch > 0:
         # batched survey: transmitters every 200 m along the tow line
         # (x = -3100 + 200 k, 50 m above the seabed), advanced together;
-        # one warm-up solve, one timed solve (CUDA events)
+        # a short warm-up run, one timed solve (CUDA events)
+        import dataclasses
         pos = np.array([[-3100.0 + TOW_SPACING * (k + args.batch * rank), 0.0, float(wl.src[2])]
                         for k in range(args.batch)])
-        _, bwork = emm.forward_batch(grid, survey, sigma, pos)
+        emm.forward_batch(grid, dataclasses.replace(survey, nt=30), sigma, pos)
+        bwork = torch.empty(emm.batch_workspace_size(grid, survey, len(pos)) + 256, dtype=torch.uint8,
+                            device=sigma.device)
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
-        emm.forward_batch(grid, survey, sigma, pos, work=bwork, check=False)
+        emm.forward_batch(grid, survey, sigma, pos, work=bwork)  # (checks the device status)
         b1.record(stream)
         torch.cuda.synchronize()
         bsec = job_max(b0.elapsed_time(b1) / 1e3)
         bval = aggregate_rate(world, cells * args.batch, nt, 1, bsec)
         del bwork
+        # the same with the first 8 transmitters only
+        few = pos[: min(8, len(pos))]
+        _, fwork = emm.forward_batch(grid, dataclasses.replace(survey, nt=30), sigma, few)
+        fwork = torch.empty(emm.batch_workspace_size(grid, survey, len(few)) + 256, dtype=torch.uint8,
+                            device=sigma.device)
+        torch.cuda.synchronize()
+        b0.record(stream)
+        emm.forward_batch(grid, survey, sigma, few, work=fwork)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        fval = aggregate_rate(world, cells * len(few), nt, 1, job_max(b0.elapsed_time(b1) / 1e3))
+        del fwork
         line["batch"] = {"nsrc": args.batch, "value": bval, "unit": "Gcell-steps/s", "ms_per_solve": 1e3 * bsec,
                          "vs_one_at_a_time": bval / value,
+                         "nsrc_8": {"value": fval, "vs_one_at_a_time": fval / value},
                          "what": "emm_forward_batch: transmitters sharing grid, sigma and receivers in the same "
                                  "launches, against the device-resident single-transmitter value"}
     if not args.no_airwave and wl.name.startswith("marine"):
@@ -546,6 +564,7 @@ def main():
         # the same with the E snapshots of as many final steps as the free
         # device memory holds (less 6 GB for the outputs and the allocator),
         # which the reverse sweep then does not recompute
+        gc.collect()
         torch.cuda.empty_cache()
         free, _ = torch.cuda.mem_get_info()
         snap = emm.snapshot_bytes(grid, survey, ck)

@@ -392,6 +392,15 @@ def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None
     return st.value if wait else None
 
 
+def batch_workspace_size(grid: Grid, survey: Survey, nsrc: int) -> int:
+    """``emm_batch_workspace_size``: device bytes of a batch of nsrc transmitters."""
+    s, keep = survey._c()
+    n = C.c_size_t(0)
+    _check(load_library().emm_batch_workspace_size(grid.handle, C.byref(s), int(nsrc), C.byref(n)),
+           "emm_batch_workspace_size")
+    return n.value
+
+
 def forward_batch(grid: Grid, survey: Survey, sigma, src_pos, work=None, stream=None, check: bool = True):
     """``emm_forward_batch``: the receiver Green's functions of several
     transmitters (positions ``src_pos`` [nsrc][3], host) on one conductivity,
@@ -404,16 +413,14 @@ def forward_batch(grid: Grid, survey: Survey, sigma, src_pos, work=None, stream=
     pos = _f64(src_pos).reshape(-1, 3)
     nsrc, nf = pos.shape[0], len(survey.freqs)
     s, keep = survey._c()
-    n = C.c_size_t(0)
-    _check(load_library().emm_batch_workspace_size(grid.handle, C.byref(s), nsrc, C.byref(n)),
-           "emm_batch_workspace_size")
-    if work is None or work.numel() < n.value + 256:
-        work = torch.empty(n.value + 256, dtype=torch.uint8, device=sigma.device)
+    nbytes = batch_workspace_size(grid, survey, nsrc)
+    if work is None or work.numel() < nbytes + 256:
+        work = torch.empty(nbytes + 256, dtype=torch.uint8, device=sigma.device)
     ptr = work.data_ptr() + (-work.data_ptr()) % 256
     rec = torch.zeros((nsrc, max(survey.nrec, 1), 6, nf, 2), dtype=torch.float64, device=sigma.device)
     code = load_library().emm_forward_batch(
         grid.handle, C.byref(s), nsrc, _dp(pos), C.c_void_p(sigma.data_ptr()), C.c_void_p(ptr),
-        C.c_size_t(n.value), C.c_void_p(rec.data_ptr()), C.c_void_p(stream.cuda_stream))
+        C.c_size_t(nbytes), C.c_void_p(rec.data_ptr()), C.c_void_p(stream.cuda_stream))
     _check(code, "emm_forward_batch")
     if check:
         v = C.c_int(0)
