@@ -244,6 +244,10 @@ def gradient_survey_line(emm, torch, stream, job_max):
     the E snapshots of as many final steps as the free device memory holds;
     against one forward solve per transmitter on the same grid."""
     import dataclasses
+    # release the allocator's cached blocks first: a tensor allocated inside
+    # a large cached block (the earlier gradient's workspace) would pin it
+    gc.collect()
+    torch.cuda.empty_cache()
     wl = W.gradient_survey(with_resistor=False)
     obs = W.gradient_survey(with_resistor=True)
     grid = emm.grid_for(wl)
@@ -274,6 +278,8 @@ def gradient_survey_line(emm, torch, stream, job_max):
     gc.collect()
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
+    print(f"gradient survey: {free / 1e9:.1f} GB free, {torch.cuda.memory_allocated() / 1e9:.1f} GB allocated, "
+          f"{torch.cuda.memory_reserved() / 1e9:.1f} GB reserved by torch", file=sys.stderr)
     room = free - (6 << 30)
     snap = emm.snapshot_bytes(grid, survey, ck)
     stored = min(nt, int(max(0, room) // snap)) // ck * ck
