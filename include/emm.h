@@ -127,7 +127,8 @@ typedef struct {
   double fmax;          /* Hz, > 0: Gaussian wavelet exp(-(pi fmax (t - 1.5/fmax))^2) and CPML alpha */
   double sigma_min;     /* S/m, > 0: smallest conductivity in the model (sets vmax) */
   double dt;            /* s: time step; <= 0 selects 0.99/eta; > 1/eta is EMM_ECFL */
-  int nt;               /* number of leapfrog steps, >= 0 */
+  int nt;               /* number of leapfrog steps, >= 0 (with 0 no step runs, J' of Eq. 7 is 0
+                           and every Green's function is returned as 0) */
   double src[3];        /* source position (m) */
   double src_az;        /* rad: azimuth of the electric dipole */
   double src_dip;       /* rad: dip; direction (cos dip cos az, cos dip sin az, sin dip) */

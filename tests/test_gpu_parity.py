@@ -99,6 +99,21 @@ def test_repeatable_bitwise():
     np.testing.assert_array_equal(a[1], b[1])
 
 
+def test_zero_one_and_two_steps():
+    wl = W.small_case(rd=2, nt=2, volume=False)
+    # no step: J' = 0, and the library returns G = 0 (the oracle's 0/0 is NaN)
+    G0 = _run_gpu(wl, 0)[0]
+    assert np.all(G0 == 0)
+    for nt in (1, 2):
+        G = _run_gpu(wl, nt)[0]
+        ref = oracle.forward_workload(wl, nt=nt)["G"]
+        if np.abs(ref).max() == 0:     # the receivers lie outside the source's first stencil
+            assert np.all(G == 0)
+        else:
+            eE, eH = compare_G(G, ref)
+            assert eE < REL_L2_TOL and eH < REL_L2_TOL, (nt, eE, eH)
+
+
 def test_no_receivers():
     wl = W.small_case(rd=2, nt=5, volume=False)
     wl.rec = np.zeros((0, 3))
