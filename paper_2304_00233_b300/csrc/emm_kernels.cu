@@ -992,24 +992,36 @@ __device__ __forceinline__ float2 *fft_line(float2 *b0, float2 *b1, const float2
 }
 
 // Shared memory: the N roots of unity and two line buffers.
+// The roots of unity and the continuation factors are set-up tables, so a
+// CTA stages them before griddepcontrol.wait (overlapping the previous
+// launch's drain); the lines themselves, written by the launch before, are
+// gathered after it.
 template <int MODE, bool MULTI, int KIND>
 __global__ void __launch_bounds__(AFT) k_air_fft(const DevParams p) {
-  wait_prior_grid();
-  if (p.halt && *p.halt) return;
-  allow_next_launch();
   extern __shared__ float2 air_sm[];
   const int N0 = p.np[0], N1 = p.np[1], rd = p.air_rd, src = static_cast<int>(blockIdx.z);
   const int N = (MODE == 0 || MODE == 3) ? N0 : N1;
   const int ln = static_cast<int>(blockIdx.x);  // line: MODE 0 c N1 + j; 1 c N0 + q; 2 o N0 + q; 3 o N1 + j
   const size_t plane = static_cast<size_t>(N0) * N1;
-  const Fields f = fields_of<MULTI>(p, src);
-  float2 *T = p.air_T + static_cast<size_t>(src) * 3 * plane;
-  float2 *F = p.air_F + static_cast<size_t>(src) * 3 * plane;
-  float2 *U = p.air_U + static_cast<size_t>(src) * 2 * rd * plane;
   float2 *Ws = air_sm, *b0 = air_sm + N, *b1 = b0 + N;
   const float2 *W = (MODE == 0 || MODE == 3) ? p.air_twx : p.air_twy;
   for (int i = threadIdx.x; i < N; i += AFT) {
     Ws[i] = W[i];
+    if (MODE == 2) {  // the continuation factor of this line's output, sample k = i
+      const int o = ln / N0, q = ln % N0, r2 = o / 2;
+      const size_t fi = static_cast<size_t>(i) * N0 + q;
+      b1[i] = KIND == 0 ? make_float2(p.air_decE[r2 * plane + fi], 0.f)
+                        : p.air_facH[(static_cast<size_t>(o % 2) * rd + r2) * plane + fi];
+    }
+  }
+  wait_prior_grid();
+  if (p.halt && *p.halt) return;
+  allow_next_launch();
+  const Fields f = fields_of<MULTI>(p, src);
+  float2 *T = p.air_T + static_cast<size_t>(src) * 3 * plane;
+  float2 *F = p.air_F + static_cast<size_t>(src) * 3 * plane;
+  float2 *U = p.air_U + static_cast<size_t>(src) * 2 * rd * plane;
+  for (int i = threadIdx.x; i < N; i += AFT) {
     float2 v;
     if (MODE == 0) {
       const int c = ln / N1, j = ln % N1;
@@ -1019,16 +1031,9 @@ __global__ void __launch_bounds__(AFT) k_air_fft(const DevParams p) {
       const int c = ln / N0, q = ln % N0;
       v = T[(static_cast<size_t>(c) * N1 + i) * N0 + q];
     } else if (MODE == 2) {
-      const int o = ln / N0, q = ln % N0, r2 = o / 2, comp = KIND == 0 ? o % 2 : 0;
-      const float2 x = F[(static_cast<size_t>(comp) * N1 + i) * N0 + q];
-      const size_t fi = static_cast<size_t>(i) * N0 + q;
-      if (KIND == 0) {
-        const float g = p.air_decE[r2 * plane + fi];
-        v = make_float2(x.x * g, x.y * g);
-      } else {
-        const float2 g = p.air_facH[(static_cast<size_t>(o % 2) * rd + r2) * plane + fi];
-        v = make_float2(x.x * g.x - x.y * g.y, x.x * g.y + x.y * g.x);
-      }
+      const int o = ln / N0, q = ln % N0, comp = KIND == 0 ? o % 2 : 0;
+      const float2 x = F[(static_cast<size_t>(comp) * N1 + i) * N0 + q], g = b1[i];  // b1: this thread's own factor
+      v = KIND == 0 ? make_float2(x.x * g.x, x.y * g.x) : make_float2(x.x * g.x - x.y * g.y, x.x * g.y + x.y * g.x);
     } else {
       v = U[static_cast<size_t>(ln) * N0 + i];  // ln = o N1 + j
     }
