@@ -427,30 +427,42 @@ __device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, 
 
 // One quad of the E update.  FAST: an interior CTA without the source, where
 // every validity test is true and every slab test false.
+// A quad's FD rows: y and z (one row each) and x (the rows of its 4 cells),
+// from the D- (E update) or D+ (H update) tables.  Loaded while the CTA's
+// tiles are in flight, so their latency is off the compute phase.
+template <int R>
+struct Coef {
+  float cy[2 * R], cz[2 * R], cx[4][2 * R];
+};
+template <int R>
+__device__ __forceinline__ void load_coef(const float *const *tab, const Quad &u, bool live, Coef<R> &c) {
+  constexpr int M = 2 * R;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    c.cy[m] = live ? __ldg(tab[1] + u.j * M + m) : 0.f;
+    c.cz[m] = live ? __ldg(tab[2] + u.k * M + m) : 0.f;
+  }
+  const float4 *c4 = reinterpret_cast<const float4 *>(tab[0] + static_cast<size_t>(live ? u.i : 0) * M);
+#pragma unroll
+  for (int f = 0; f < M; ++f) {
+    const float4 a = live ? __ldg(c4 + f) : float4{};
+    c.cx[(4 * f) / M][(4 * f) % M] = a.x;
+    c.cx[(4 * f + 1) / M][(4 * f + 1) % M] = a.y;
+    c.cx[(4 * f + 2) / M][(4 * f + 2) % M] = a.z;
+    c.cx[(4 * f + 3) / M][(4 * f + 3) % M] = a.w;
+  }
+}
+
 template <int R, bool FAST>
 __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
                                        const float4 (&e)[3], const float4 (&w)[3], const float4 *ps, int n,
-                                       bool src, const SrcDev *sd, const float *jw) {
+                                       bool src, const SrcDev *sd, const float *jw, const Coef<R> &cf) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int q4 = 4 * u.q, t = threadIdx.x;
-  float cy[M], cz[M], cx[4][M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    cy[m] = __ldg(p.cm[1] + u.j * M + m);
-    cz[m] = __ldg(p.cm[2] + u.k * M + m);
-  }
-  {
-    const float4 *c4 = reinterpret_cast<const float4 *>(p.cm[0] + static_cast<size_t>(u.i) * M);
-#pragma unroll
-    for (int f = 0; f < M; ++f) {
-      const float4 a = __ldg(c4 + f);
-      cx[(4 * f) / M][(4 * f) % M] = a.x;
-      cx[(4 * f + 1) / M][(4 * f + 1) % M] = a.y;
-      cx[(4 * f + 2) / M][(4 * f + 2) % M] = a.z;
-      cx[(4 * f + 3) / M][(4 * f + 3) % M] = a.w;
-    }
-  }
+  const float(&cy)[M] = cf.cy;
+  const float(&cz)[M] = cf.cz;
+  const float(&cx)[4][M] = cf.cx;
   const bool dm_j = FAST || (u.j >= R && u.j <= np1 - 1 - R);
   const bool dm_k = FAST || (u.k >= R && u.k <= np2 - 1 - R);
   bool dm_i[4];
@@ -618,13 +630,15 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
               slab_int(u.k, np2, nb),
               psi_x_column(u.i, nb, PsiX{p.psx_hx[0], p.psx_wx[0], p.psx_far0[0]}, np0 - 1), p.psx_wx[0]);
   cp_async_commit();
+  Coef<R> cf;
+  load_coef<R>(p.cm, u, live, cf);
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw);
+    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw, cf);
   else
-    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw);
+    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw, cf);
 }
 
 // The E half-step of one problem; every launch of a convergence run returns
@@ -652,27 +666,13 @@ __device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, 
 
 template <int R, bool FAST>
 __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
-                                       const float4 (&h)[3], const float4 *ps, int n) {
+                                       const float4 (&h)[3], const float4 *ps, int n, const Coef<R> &cf) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int q4 = 4 * u.q, t = threadIdx.x;
-  float cy[M], cz[M], cx[4][M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    cy[m] = __ldg(p.cp[1] + u.j * M + m);
-    cz[m] = __ldg(p.cp[2] + u.k * M + m);
-  }
-  {
-    const float4 *c4 = reinterpret_cast<const float4 *>(p.cp[0] + static_cast<size_t>(u.i) * M);
-#pragma unroll
-    for (int f = 0; f < M; ++f) {
-      const float4 a = __ldg(c4 + f);
-      cx[(4 * f) / M][(4 * f) % M] = a.x;
-      cx[(4 * f + 1) / M][(4 * f + 1) % M] = a.y;
-      cx[(4 * f + 2) / M][(4 * f + 2) % M] = a.z;
-      cx[(4 * f + 3) / M][(4 * f + 3) % M] = a.w;
-    }
-  }
+  const float(&cy)[M] = cf.cy;
+  const float(&cz)[M] = cf.cz;
+  const float(&cx)[4][M] = cf.cx;
   const bool dp_j = FAST || (u.j >= R - 1 && u.j <= np1 - 1 - R);
   const bool dp_k = FAST || (u.k >= R - 1 && u.k <= np2 - 1 - R);
   bool dp_i[4], in_i[4];
@@ -826,13 +826,15 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
               slab_half(u.k, np2, nb),
               psi_x_column(u.i, nb, PsiX{p.psx_hx[1], p.psx_wx[1], p.psx_far0[1]}, np0 - 2), p.psx_wx[1]);
   cp_async_commit();
+  Coef<R> cf;
+  load_coef<R>(p.cp, u, live, cf);
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    h_quad<R, true>(p, f, v, u, h, ps, n);
+    h_quad<R, true>(p, f, v, u, h, ps, n, cf);
   else
-    h_quad<R, false>(p, f, v, u, h, ps, n);
+    h_quad<R, false>(p, f, v, u, h, ps, n, cf);
 }
 
 template <int R, bool MULTI, bool CONV>
