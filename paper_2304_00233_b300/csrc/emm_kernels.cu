@@ -456,7 +456,8 @@ __device__ __forceinline__ void load_coef(const float *const *tab, const Quad &u
 template <int R, bool FAST>
 __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
                                        const float4 (&e)[3], const float4 (&w)[3], const float4 *ps, int n,
-                                       bool src, const SrcDev *sd, const float *jw, const Coef<R> &cf) {
+                                       bool src, const SrcDev *sd, const float *jw, const Coef<R> &cf,
+                                       float amp) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const int q4 = 4 * u.q, t = threadIdx.x;
@@ -474,7 +475,6 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
   }
   const int sj = FAST ? -1 : slab_int(u.j, np1, nb), sk = FAST ? -1 : slab_int(u.k, np2, nb);
   const int xs = FAST ? -1 : psi_x_column(u.i, nb, PsiX{p.psx_hx[0], p.psx_wx[0], p.psx_far0[0]}, np0 - 1);
-  const float amp = FAST ? 0.f : __ldg(p.amp + n);
   float4 out[3] = {e[0], e[1], e[2]};
 
   // Ex at (i+1/2, j, k): D-_y Hz - D-_z Hy
@@ -632,13 +632,14 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   cp_async_commit();
   Coef<R> cf;
   load_coef<R>(p.cm, u, live, cf);
+  const float amp = src ? __ldg(p.amp + n) : 0.f;  // the wavelet at t_{n+1/2}, source CTAs only
   cp_async_wait_all();
   if (!tiles_ready(p, bar) || !live) return;
   const View<R> v{s};
   if (fast)
-    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw, cf);
+    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw, cf, 0.f);
   else
-    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw, cf);
+    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw, cf, amp);
 }
 
 // The E half-step of one problem; every launch of a convergence run returns
