@@ -288,6 +288,10 @@ struct GMaps {
   CUtensorMap m[6];
 };
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int R, int KIND>
 __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __grid_constant__ GMaps tm) {
   wait_prior_grid();
@@ -319,6 +323,17 @@ __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __gr
   float4 o4[3];
 #pragma unroll
   for (int o = 0; o < 3; ++o) o4[o] = live ? *reinterpret_cast<const float4 *>(out[o] + id) : float4{};
+  if (KIND == 0 && live) {
+    // the epilogue's inputs (dt/eps, the E snapshots, the gradient term),
+    // brought into L2 while the tiles are in flight
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      prefetch_l2(a.ie[c] + id);
+      prefetch_l2(a.E0[c] + id);
+      prefetch_l2(a.E1[c] + id);
+      prefetch_l2(a.gseg[c] + id);
+    }
+  }
   float cx[4][M], cy[M], cz[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) {
