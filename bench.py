@@ -26,6 +26,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -109,7 +110,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to BENCH_LOG_DIR (default: the system's temporary
+        # directory); the JSON line carries their summary
+        log_dir = os.environ.get("BENCH_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"emm_bench_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
