@@ -491,6 +491,25 @@ def main():
         "gpu_launches": kernel_launches,
         "clocks": clocks,
     }
+    # the same solve replayed from a CUDA graph of its time loop (emm_plan)
+    plan_t0 = time.perf_counter()
+    plan = emm.Plan(grid, survey, sigma, work)
+    torch.cuda.synchronize()
+    capture_ms = 1e3 * (time.perf_counter() - plan_t0)
+    plan.run_async(sigma)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        plan.run_async(sigma)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    assert emm.status(work) == emm.EMM_OK
+    gval = aggregate_rate(world, cells, nt, args.steps, job_max(p0.elapsed_time(p1) / 1e3))
+    line["graph"] = {"value": gval, "unit": "Gcell-steps/s", "vs_stream_launches": gval / value,
+                     "capture_and_instantiate_ms": capture_ms,
+                     "what": "emm_plan_run: the solve's time loop captured once as a CUDA graph and replayed"}
+    del plan
     if args.batch > 0:
         # batched survey: transmitters every 200 m along the tow line
         # (x = -3100 + 200 k, 50 m above the seabed), advanced together;

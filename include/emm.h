@@ -259,6 +259,29 @@ int emm_batch_workspace_size(const emm_grid *grid, const emm_survey *survey, int
 int emm_forward_batch(const emm_grid *grid, const emm_survey *survey, int nsrc, const double *src_pos,
                       const float *sigma, void *ws, size_t ws_bytes, double *rec_out, emm_stream stream);
 
+/* Forward-solve plan: the time loop of emm_forward for one grid, survey,
+ * workspace and outputs, captured once as a CUDA graph (every stencil,
+ * source, air and volume launch with its dependent-launch edges) and
+ * replayed by emm_plan_run for each conductivity.  The paper has no
+ * counterpart; it removes the per-launch host work of a solve (2 nt + more
+ * launches) for callers that solve the same survey many times.
+ *   emm_plan_create: validates like emm_forward, enqueues one set-up on
+ *     `stream` (with `sigma`; the launch parameters the graph keeps come
+ *     from it), captures the loop and instantiates the graph; the loop is
+ *     not run.  The plan keeps copies of the survey's arrays; `grid`, `ws`,
+ *     `rec_out` and `vol_out` must stay valid (and are reused) for the
+ *     plan's life.  EMM_ECUDA if capture or instantiation fails.
+ *   emm_plan_run: the solve for `sigma` (device float [3][n3][n2][n1]) on
+ *     `stream`: set-up, graph launch, normalisation; rec_out and vol_out
+ *     receive exactly what emm_forward writes.  Asynchronous; emm_status on
+ *     ws reads its device status.
+ *   emm_plan_destroy: releases the plan (a run in flight completes). */
+typedef struct emm_plan emm_plan;
+int emm_plan_create(const emm_grid *grid, const emm_survey *survey, const float *sigma, void *ws,
+                    size_t ws_bytes, double *rec_out, double *vol_out, emm_stream stream, emm_plan **plan);
+int emm_plan_run(emm_plan *plan, const float *sigma, emm_stream stream);
+void emm_plan_destroy(emm_plan *plan);
+
 /* One problem of a work-list solve: a grid, a survey (one transmitter),
  * its conductivity and its receiver output, as emm_forward takes them. */
 typedef struct emm_job {

@@ -40,7 +40,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_batch_workspace_size", "emm_forward_batch", "emm_forward_converge",
             "emm_gradient_stored_workspace_size", "emm_gradient_stored", "emm_misfit_gradient",
             "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint",
-            "emm_jobs_workspace_size", "emm_forward_jobs", "emm_jobs_tune")
+            "emm_jobs_workspace_size", "emm_forward_jobs", "emm_jobs_tune", "emm_plan_create", "emm_plan_run",
+            "emm_plan_destroy")
 
 
 class EmmError(RuntimeError):
@@ -125,6 +126,9 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
                                     C.c_int),
         "emm_forward_jobs": ([C.c_int, C.POINTER(_Job), C.c_int, V, C.c_size_t, V], C.c_int),
         "emm_jobs_tune": ([C.c_int, C.POINTER(_Job), V, C.c_size_t, C.c_int, V, _D, _I], C.c_int),
+        "emm_plan_create": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V, C.POINTER(V)], C.c_int),
+        "emm_plan_run": ([V, V, V], C.c_int),
+        "emm_plan_destroy": ([V], None),
         "emm_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -515,6 +519,52 @@ def green_functions(sigma, grid: Grid, survey: Survey, ckpt_every: Optional[int]
     conductivity tensor ``sigma`` [3][n3][n2][n1] (CUDA), differentiable with
     respect to ``sigma`` through the exact discrete adjoint."""
     return _emm_function().apply(sigma, grid, survey, ckpt_every)
+
+
+class Plan:
+    """``emm_plan_create`` / ``emm_plan_run``: the time loop of a forward
+    solve captured once as a CUDA graph on ``work`` and replayed for each
+    conductivity.  ``run(sigma)`` returns (G, vol) like ``forward``."""
+
+    def __init__(self, grid: Grid, survey: Survey, sigma, work: Optional["Workspace"] = None, stream=None):
+        import torch
+        _check_sigma(grid, sigma)
+        self.grid, self.survey = grid, survey
+        self.work = work if work is not None else Workspace(grid, survey, sigma.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(sigma.device)
+        s, keep = survey._c()
+        h = C.c_void_p()
+        vol = self.work.vol.data_ptr() if self.work.vol is not None else None
+        _check(load_library().emm_plan_create(grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()),
+                                              C.c_void_p(self.work.ptr), C.c_size_t(self.work.bytes),
+                                              C.c_void_p(self.work.rec.data_ptr()), C.c_void_p(vol),
+                                              C.c_void_p(stream.cuda_stream), C.byref(h)), "emm_plan_create")
+        self._h = h
+
+    def run_async(self, sigma, stream=None):
+        import torch
+        _check_sigma(self.grid, sigma)
+        if stream is None:
+            stream = torch.cuda.current_stream(sigma.device)
+        _check(load_library().emm_plan_run(self._h, C.c_void_p(sigma.data_ptr()), C.c_void_p(stream.cuda_stream)),
+               "emm_plan_run")
+
+    def run(self, sigma, stream=None):
+        import torch
+        self.run_async(sigma, stream)
+        st = status(self.work, stream)
+        if st != EMM_OK:
+            raise EmmError(st, "emm_plan_run (device status)")
+        G = torch.view_as_complex(self.work.rec)[: self.survey.nrec]
+        vol = None if self.work.vol is None else torch.view_as_complex(self.work.vol)
+        return G, vol
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.emm_plan_destroy(h)
+            self._h = None
 
 
 class JobsWork:

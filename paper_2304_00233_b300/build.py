@@ -2,8 +2,8 @@
 
     python -m paper_2304_00233_b300.build [--force] [-v]
 
-Compiles ``csrc/emm_kernels.cu``, ``csrc/emm_adjoint.cu``, ``csrc/emm_model.cu``
-and ``csrc/emm_setup.cpp`` with nvcc into
+Compiles ``csrc/emm_kernels.cu``, ``csrc/emm_adjoint.cu``, ``csrc/emm_model.cu``,
+``csrc/emm_graph.cu`` and ``csrc/emm_setup.cpp`` with nvcc into
 ``paper_2304_00233_b300/libemm.so`` (the shared library the Python binding and
 any C caller load).  Host code is compiled without FMA contraction so that
 the FP64 setup tables are reproducible."""
@@ -16,7 +16,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libemm.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("emm_kernels.cu", "emm_adjoint.cu", "emm_model.cu", "emm_setup.cpp")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("emm_kernels.cu", "emm_adjoint.cu", "emm_model.cu", "emm_graph.cu", "emm_setup.cpp")]
 HEADERS = [os.path.join(HERE, "csrc", "emm_internal.h"), os.path.join(HERE, "csrc", "emm_tma.cuh"),
            os.path.join(os.path.dirname(HERE), "include", "emm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
