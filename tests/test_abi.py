@@ -107,3 +107,34 @@ def test_work_list_layout_and_errors():
     # a workspace that is too small is refused before anything is enqueued
     assert lib.emm_forward_jobs(2, jobs, emm.JOBS_LIST, None, 0, None) == emm.EMM_EWORKSPACE
     assert lib.emm_forward_jobs(2, jobs, 3, None, 0, None) == emm.EMM_EINVAL
+
+
+def test_new_entry_points_refuse_bad_arguments_on_the_host():
+    C = emm.C
+    lib = emm.load_library()
+    x = np.arange(12.0) * 10
+    g = emm.make_grid(x, x, x, rd=2, nb=4, ne=3)
+    good = emm.Survey(omega0=1.0, fmax=1.0, sigma_min=1.0, nt=10, src=(55, 55, 55),
+                      rec=np.array([[40.0, 50.0, 60.0]]), freqs=[1.0])
+    bad = emm.Survey(**{**good.__dict__, "nt": -1})
+    sb, keep = bad._c()
+    sg, keep2 = good._c()
+    h = C.c_void_p()
+    # plans: invalid survey, missing output handle; run and destroy of no plan
+    assert lib.emm_plan_create(g.handle, C.byref(sb), None, None, 0, None, None, None, C.byref(h)) == emm.EMM_EINVAL
+    assert lib.emm_plan_create(g.handle, C.byref(sg), None, None, 0, None, None, None, None) == emm.EMM_EINVAL
+    assert lib.emm_plan_run(None, None, None) == emm.EMM_EINVAL
+    lib.emm_plan_destroy(None)
+    # misfit gradient: no observed data or no misfit scalar
+    dummy = C.c_void_p(16)
+    assert lib.emm_misfit_gradient(g.handle, C.byref(sg), dummy, None, None, 4, 0, dummy, 1 << 30, dummy, dummy,
+                                   dummy, None) == emm.EMM_EINVAL
+    assert lib.emm_misfit_gradient(g.handle, C.byref(sg), dummy, dummy, None, 4, 0, dummy, 1 << 30, dummy, None,
+                                   dummy, None) == emm.EMM_EINVAL
+    # staggering: missing arrays, a workspace too small for the cell widths
+    n = C.c_size_t(0)
+    assert lib.emm_stagger_workspace_size(g.handle, C.byref(n)) == emm.EMM_OK and n.value == 3 * 11 * 8
+    assert lib.emm_stagger_sigma(g.handle, None, dummy, dummy, n.value, dummy, None) == emm.EMM_EINVAL
+    assert lib.emm_stagger_sigma(g.handle, dummy, dummy, dummy, n.value - 8, dummy, None) == emm.EMM_EWORKSPACE
+    assert lib.emm_stagger_sigma_adjoint(g.handle, dummy, dummy, n.value - 8, dummy, dummy, None) == \
+        emm.EMM_EWORKSPACE
