@@ -70,3 +70,32 @@ def test_workloads_deterministic():
     a, b = W.small_case(seed=3), W.small_case(seed=3)
     np.testing.assert_array_equal(a.sigma, b.sigma)
     assert np.all(a.sigma == a.sigma.astype(np.float32).astype(np.float64))
+
+
+def test_gradient_survey_and_uneven_grids():
+    g = W.gradient_survey()
+    assert g.shape == (192, 192, 128) and g.sigma_h.shape == (127, 191, 191)
+    assert np.diff(g.x).min() == pytest.approx(40.0, rel=1e-9)
+    assert np.diff(g.x).max() < 210.0 and np.diff(g.z).max() < 210.0
+    # the resistor lies 1000-1100 m below the seabed in the observed-data model only
+    r = W.gradient_survey(with_resistor=True)
+    assert r.sigma_h.min() == pytest.approx(0.02) and g.sigma_h.min() == pytest.approx(1.0)
+    assert g.sigma_v.min() == pytest.approx(0.5)
+    assert np.all(np.abs(W.GRADIENT_SOURCES[:, 0]) < g.x[-1])
+    c = W.gradient_survey_48()
+    assert c.shape == (48, 48, 48) and np.all(np.abs(c.rec[:, 0]) < c.x[-1])
+    for (n1, n3), wl in zip(W.UNEVEN_GRIDS, W.uneven_jobs()):
+        assert wl.shape == (n1, n1, n3)
+        assert np.all(np.abs(wl.rec[:, 0]) <= 0.8 * wl.x[-1])
+        assert np.diff(wl.x).max() == pytest.approx(200.0, rel=0.05)
+
+
+def test_observed_noise_is_seeded_and_two_percent():
+    a = W.observed_noise((200, 6, 3))
+    b = W.observed_noise((200, 6, 3))
+    assert np.array_equal(a, b)
+    d = a - 1.0
+    assert abs(d.mean()) < 2e-3
+    # each of the real and imaginary parts has standard deviation 0.02 / sqrt(2)
+    assert d.real.std() == pytest.approx(0.02 / math.sqrt(2.0), rel=0.05)
+    assert d.imag.std() == pytest.approx(0.02 / math.sqrt(2.0), rel=0.05)
