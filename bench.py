@@ -1,16 +1,19 @@
 """Benchmark of the fictitious-wave FDTD forward solve on B300.
 
 One benchmark step = one complete forward solve (every leapfrog step of the
-time loop, CPML, source injection, receiver DTFT, Green's functions) of the
-marine 1-D VTI workload on its 128 x 128 x 96-node non-uniform grid
-(162 x 162 x 130 padded samples, 4th order, 3 frequencies, 64 receivers).
+time loop, CPML, source injection, receiver and volume DTFT, Green's
+functions) of the 3-D anomaly workload: 256 x 256 x 160 non-uniform nodes
+(294 x 294 x 198 padded samples), 8th order, 3 frequencies, 201 receivers
+and the volume DTFT of all six components over the 10.5 M interior samples.
 The metric is padded cell-steps per second (Gcell-steps/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own
 transmitter position (sources are independent problems, weak scaling); the
-only collective is the max over ranks of the timed duration.
+collectives are the max over ranks of the timed duration, one gather of the
+receiver Green's functions to rank 0 after the timed region, and, in the
+gradient-survey line, the sum of the per-transmitter gradients.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) on the
 host cores, each step a bounded sample of the same workload.
@@ -22,6 +25,7 @@ import gc
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -36,7 +40,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2304_00233_b300 import workloads as W  # noqa: E402
 
-WORKLOAD = "marine_1d_128x128x96"
+WORKLOAD = "anomaly_3d_256x256x160"
+MARINE = "marine_1d_128x128x96"
+E2E_SOLVES = 3          # end-to-end solves timed (each reads back the volume)
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 
 
 def _slab_cells(wl):
@@ -58,12 +65,26 @@ def algorithmic_bytes(wl):
 
 
 def per_kernel_bytes(wl):
-    """Minimal bytes of each half-step launch of the two-launch step:
-    E launch reads H, E, dt/eps and writes E (48 B/cell); H launch reads E, H
-    and writes H (36 B/cell); each has 2 CPML arrays per slab axis."""
+    """Minimal bytes of each launch of a leapfrog step: the E launch reads H,
+    E, dt/eps and writes E (48 B/cell), the H launch reads E, H and writes H
+    (36 B/cell), each with 2 CPML arrays read + written per slab axis; the
+    volume DTFT reads the six fields once (24 B per interior sample) and
+    reads + writes its 6 x nfreq compensated accumulators (32 B each)."""
     cells = int(np.prod(wl.npad))
-    vol = 32 * 3 * len(wl.freqs) * int(np.prod(wl.shape)) if wl.volume else 0
-    return 48 * cells + 16 * _slab_cells(wl) + vol, 36 * cells + 16 * _slab_cells(wl) + vol
+    nint = int(np.prod(wl.shape))
+    vol = (24 + 32 * 6 * len(wl.freqs)) * nint if wl.volume else 0
+    return {"k_update_E": 48 * cells + 16 * _slab_cells(wl), "k_update_H": 36 * cells + 16 * _slab_cells(wl),
+            "k_volume_dft": vol}
+
+
+def bench_config(wl, nt, world):
+    """The `config` object of both arms (same keys and values)."""
+    return {"workload": wl.name, "grid_nodes": list(wl.shape), "padded": list(wl.npad),
+            "padded_cells": int(np.prod(wl.npad)), "rd": wl.rd, "timesteps_per_solve": int(nt),
+            "nfreq": len(wl.freqs), "nrec": len(wl.rec), "volume_dtft": bool(wl.volume),
+            "parallelism": f"{world} independent transmitters" if world > 1 else "single GPU",
+            "l2": "no flush: per-solve working set (fields, dt/eps, CPML, volume accumulators) "
+                  "exceeds the 126 MB L2"}
 
 
 def kernel_fingerprint():
@@ -80,9 +101,9 @@ def kernel_fingerprint():
 
 
 def recorded_traffic(workload):
-    """DRAM bytes (read + write) of one leapfrog step (E + H launch) from the
-    ncu summary of this workload, or None if there is none for the current
-    kernels."""
+    """DRAM bytes (read + write) of one leapfrog step (every launch of the
+    step) from the ncu summary of this workload, or None if there is none for
+    the current kernels."""
     p = os.path.join(ROOT, "profiles", f"k_update_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -99,6 +120,62 @@ def measured_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
+
+
+# ---- error against the FP64 oracle's stored results ----
+def _rel_l2_masked(got, ref, floor=1e-6):
+    got, ref = np.asarray(got).ravel(), np.asarray(ref).ravel()
+    keep = np.abs(ref) > floor * np.abs(ref).max()
+    if not keep.any():
+        return 0.0
+    return float(np.linalg.norm(got[keep] - ref[keep]) / np.linalg.norm(ref[keep]))
+
+
+def _max_rel_masked(got, ref, floor=1e-6):
+    got, ref = np.asarray(got).ravel(), np.asarray(ref).ravel()
+    keep = np.abs(ref) > floor * np.abs(ref).max()
+    return float(np.max(np.abs(got[keep] - ref[keep]) / np.abs(ref[keep]))) if keep.any() else 0.0
+
+
+def golden_error(wl, nt, G, vol=None):
+    """Error of the solve's Green's functions against the FP64 oracle's
+    stored result of the same workload and step count (tests/golden/, written
+    by the oracle alone): relative L2 over the entries above 1e-6 of the
+    largest, per field kind, and the largest pointwise relative error there;
+    volume at the golden's seeded samples.  None when there is no golden of
+    this step count."""
+    p = os.path.join(GOLDEN_DIR, f"{wl.name}.npz")
+    if not os.path.exists(p):
+        return {"available": False, "why": "no stored oracle result"}
+    g = np.load(p)
+    if int(g["nt"]) != int(nt):
+        return {"available": False, "why": f"stored oracle result has nt={int(g['nt'])}, solve nt={nt}"}
+    G = np.asarray(G)
+    out = {"available": True, "oracle_nt": int(g["nt"]),
+           "rec_rel_l2_E": _rel_l2_masked(G[:, :3], g["G"][:, :3]),
+           "rec_rel_l2_H": _rel_l2_masked(G[:, 3:], g["G"][:, 3:]),
+           "rec_max_rel_E": _max_rel_masked(G[:, :3], g["G"][:, :3]),
+           "rec_max_rel_H": _max_rel_masked(G[:, 3:], g["G"][:, 3:])}
+    if vol is not None and "vol_idx" in g.files:
+        flat = np.asarray(vol).transpose(0, 2, 3, 4, 1).reshape(-1, vol.shape[1])
+        got, ref = flat[g["vol_idx"]], g["vol_G"]
+        isE = g["vol_idx"] < 3 * int(np.prod(wl.shape))
+        out.update({"vol_samples": int(len(g["vol_idx"])),
+                    "vol_rel_l2_E": _rel_l2_masked(got[isE], ref[isE]),
+                    "vol_rel_l2_H": _rel_l2_masked(got[~isE], ref[~isE])})
+    out["bound"] = "2e-4 relative L2 (FP32 fields against the FP64 oracle)"
+    return out
 
 
 class ClockSampler:
@@ -158,28 +235,63 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(wl, nt):
-    """Wall time of `nt` oracle steps (setup subtracted)."""
+# ---- the FP64 oracle on the host cores ----
+def oracle_setup(wl):
+    """Wall time of an oracle run of zero steps (tables, allocations)."""
     import oracle
     t0 = time.perf_counter()
     oracle.forward_workload(wl, nt=0)
-    t_setup = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def oracle_sample(wl, nt, t_setup=None):
+    """Wall time of `nt` oracle steps (the set-up of a zero-step run
+    subtracted; measured here unless given)."""
+    import oracle
+    if t_setup is None:
+        t_setup = oracle_setup(wl)
     t0 = time.perf_counter()
     oracle.forward_workload(wl, nt=nt)
     return max(time.perf_counter() - t0 - t_setup, 1e-9)
 
 
+def _one_thread_rate(name, nt, timeout=240):
+    """Oracle cell-steps/s on one thread (a child process with
+    OMP_NUM_THREADS=1), or None if it does not finish in time."""
+    code = ("import sys, json; sys.path.insert(0, %r)\n"
+            "import bench, numpy as np\n"
+            "from paper_2304_00233_b300 import workloads as W\n"
+            "wl = W.WORKLOADS[%r](); t = bench.oracle_sample(wl, %d)\n"
+            "print(json.dumps({'t': t, 'cells': int(np.prod(wl.npad))}))" % (ROOT, name, nt))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=timeout)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d["cells"] * nt / d["t"] / 1e9, d["t"]
+    except (subprocess.TimeoutExpired, ValueError, IndexError, KeyError):
+        return None, None
+
+
 def cpu_baseline(wl, budget_s=15.0):
+    """The oracle as it stands, on all host cores, on a bounded sample of the
+    workload's leapfrog steps; beside it the same on one thread."""
     import oracle
     threads = oracle.threads()
-    probe_nt = 4
-    t = oracle_sample(wl, probe_nt)
-    nt = int(min(400, max(8, budget_s / (t / probe_nt))))
-    t = oracle_sample(wl, nt)
+    probe_nt = 2
+    t_setup = oracle_setup(wl)
+    t = oracle_sample(wl, probe_nt, t_setup)
+    nt = int(min(400, max(2, budget_s / (t / probe_nt))))
+    t = oracle_sample(wl, nt, t_setup)
     cells = int(np.prod(wl.npad))
+    one_nt = 1 if cells > 5_000_000 else 4
+    one, one_t = _one_thread_rate(wl.name, one_nt)
     return {"value": cells * nt / t / 1e9, "unit": "Gcell-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{nt} leapfrog steps of {wl.name} (FP64 oracle, {threads} OpenMP threads), "
-                      f"{t:.1f} s"}
+            "sample": f"{nt} leapfrog steps of {wl.name} (FP64 oracle, {threads} OpenMP threads), {t:.1f} s",
+            "one_thread": {"value": one, "unit": "Gcell-steps/s",
+                           "sample": f"{one_nt} leapfrog steps on 1 thread"
+                                     + (f", {one_t:.1f} s" if one_t else ": did not finish")},
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 # ---- multi-GPU (one process per GPU): sharding over transmitters ----
@@ -189,8 +301,14 @@ TOW_SPACING = 200.0  # m between the transmitters of consecutive ranks
 def rank_source(src, rank):
     """Transmitter of rank `rank`: the workload's, shifted along the tow line
     (x) by rank * 200 m.  Sources are independent problems, so ranks share
-    nothing but the timing (weak scaling)."""
+    nothing during the solve (weak scaling)."""
     return np.asarray(src, dtype=np.float64) + np.array([TOW_SPACING * rank, 0.0, 0.0])
+
+
+def shard(items, rank, world):
+    """The items (transmitters) rank `rank` of `world` handles: every
+    world-th one from its rank on."""
+    return items[rank::world]
 
 
 def max_over_ranks(v, dist=None, device="cpu"):
@@ -202,6 +320,25 @@ def max_over_ranks(v, dist=None, device="cpu"):
     t = torch.tensor([float(v)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(t, dist=None):
+    """In-place sum of a tensor over the ranks (the per-transmitter gradient
+    volumes of a sharded survey); t itself in a single process."""
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
+def gather_to_rank0(t, dist=None, world=1):
+    """Every rank's tensor (same shape) stacked on rank 0 ([world, ...]);
+    None on the other ranks.  A single process gets t[None]."""
+    if dist is None:
+        return t[None]
+    import torch
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t)
+    return torch.stack(parts) if dist.get_rank() == 0 else None
 
 
 def aggregate_rate(world, cells, nt, steps, seconds):
@@ -219,37 +356,93 @@ def run_reference(args, rank, world):
     wl = W.WORKLOADS[args.workload]()
     threads = oracle.threads()
     cells = int(np.prod(wl.npad))
-    probe = oracle_sample(wl, 2) / 2
-    # each step: enough leapfrog steps for ~90 s over the whole run
-    nt = int(min(400, max(2, 90.0 / max(1, args.steps + args.warmup) / probe)))
+    probe_dt = oracle.forward_workload(wl, nt=0)["dt"]
+    nt_full = wl.nt if wl.nt is not None else int(np.ceil(wl.t_max / probe_dt))
+    t_setup = oracle_setup(wl)
+    probe = oracle_sample(wl, 1, t_setup)
+    # each step: enough leapfrog steps for ~90 s of stepping over the whole run
+    nt = int(min(400, max(1, 90.0 / max(1, args.steps + args.warmup) / probe)))
     for _ in range(args.warmup):
-        oracle_sample(wl, nt)
-    times = [oracle_sample(wl, nt) for _ in range(args.steps)]
+        oracle_sample(wl, nt, t_setup)
+    times = [oracle_sample(wl, nt, t_setup) for _ in range(args.steps)]
     tot = sum(times)
     value = cells * nt * args.steps / tot / 1e9
     line = {"metric": "FDTD forward Gcell-steps/s", "value": value, "unit": "Gcell-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl.name, "padded_cells": cells, "timesteps_per_step": nt,
-                       "note": "each step is a bounded sample of the solve's leapfrog steps"},
+            "config": bench_config(wl, nt_full, world),
             "cpu_baseline": {"value": value, "unit": "Gcell-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{nt} leapfrog steps of {wl.name} per step"},
+                             "sample": f"each step {nt} leapfrog steps of {wl.name} (of {nt_full} per solve), "
+                                       f"setup excluded", "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def gradient_survey_line(emm, torch, stream, job_max):
+def timed_events(stream, fn):
+    """Device seconds of fn() between two CUDA events on `stream`."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def marine_line(emm, torch, stream, job_max, world, rank, solves=3):
+    """The marine 1-D VTI workload (128 x 128 x 96 nodes, 4th order, no
+    volume DTFT): `solves` device-resident solves after a warm-up, the
+    leapfrog-step roofline, and the error against the oracle's stored result."""
+    wl = W.WORKLOADS[MARINE]()
+    wl.src = rank_source(wl.src, rank)
+    grid = emm.grid_for(wl)
+    nt = emm.steps_for(wl, grid)
+    survey = emm.survey_for(wl, nt=nt)
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    work = emm.Workspace(grid, survey)
+    emm.forward_async(grid, survey, sigma, work)
+    torch.cuda.synchronize()
+    loops, es, hs = [], [], []
+
+    def run():
+        for _ in range(solves):
+            t = emm.forward_timed(grid, survey, sigma, work, every=64)
+            loops.append(t["loop_ms"])
+            es.append(t["e_ms"])
+            hs.append(t["h_ms"])
+
+    sec = job_max(timed_events(stream, run))
+    assert emm.status(work) == emm.EMM_OK
+    peak, _ = measured_peaks()
+    step_s = float(np.mean(loops)) / nt / 1e3
+    alg = algorithmic_bytes(wl)
+    G = torch.view_as_complex(work.rec)[: survey.nrec].cpu().numpy()
+    return {"ctx": (wl, grid, survey, sigma, work, nt),
+            "line": {"workload": wl.name, "value": aggregate_rate(world, grid.cells, nt, solves, sec),
+                     "unit": "Gcell-steps/s", "timesteps_per_solve": nt, "padded_cells": grid.cells,
+                     "solves": solves, "ms_per_solve": 1e3 * sec / solves,
+                     "roofline": {"achieved": alg / step_s / 1e9, "peak": peak, "frac": alg / step_s / 1e9 / peak,
+                                  "unit": "GB/s", "algorithmic_bytes_per_step": alg, "step_ms": 1e3 * step_s,
+                                  "traffic": recorded_traffic(wl.name),
+                                  "k_update_E_ms": float(np.mean(es)), "k_update_H_ms": float(np.mean(hs))},
+                     "error_vs_oracle": golden_error(wl, nt, G) if rank == 0 else None}}
+
+
+def gradient_survey_line(emm, torch, stream, job_max, dist, rank, world):
     """Least-squares misfit gradient of the 8-transmitter gradient survey
     (192 x 192 x 128 NU grid): observed data from the model with the
     resistor plus 2 % noise (not timed), then the misfit and its gradient
     with respect to the cell sigma_h, sigma_v at the model without it, with
-    the E snapshots of as many final steps as the free device memory holds;
-    against one forward solve per transmitter on the same grid."""
+    the forward fields recomputed from checkpoints every 200 steps: once
+    recomputing every segment, once with the E snapshots of as many final
+    steps as the free device memory holds (less 6 GB); against one forward
+    solve per transmitter on the same grid.  Under torchrun the transmitters
+    are shared out over the ranks and the gradients summed."""
     import dataclasses
     # release the allocator's cached blocks first: a tensor allocated inside
-    # a large cached block (the earlier gradient's workspace) would pin it
+    # a large cached block (an earlier gradient's workspace) would pin it
     gc.collect()
     torch.cuda.empty_cache()
     wl = W.gradient_survey(with_resistor=False)
@@ -259,75 +452,86 @@ def gradient_survey_line(emm, torch, stream, job_max):
     dt, _, _ = grid.time_step(smin, wl.omega0)
     nt = int(np.ceil(wl.t_max / dt))
     survey = emm.survey_for(wl, nt=nt, sigma_min=smin)
-    pos = W.GRADIENT_SOURCES
+    pos_all = W.GRADIENT_SOURCES
     sig_obs = torch.from_numpy(obs.sigma.astype(np.float32)).cuda()
-    G_obs, bwork = emm.forward_batch(grid, survey, sig_obs, pos)
-    d = G_obs.cpu().numpy() * W.observed_noise(G_obs.shape)
+    G_obs, bwork = emm.forward_batch(grid, survey, sig_obs, pos_all)
+    d_all = G_obs.cpu().numpy() * W.observed_noise(G_obs.shape)
     del bwork, sig_obs, G_obs
+    pos, d = shard(pos_all, rank, world), shard(d_all, rank, world)
     sh = torch.from_numpy(wl.sigma_h).cuda()
     sv = torch.from_numpy(wl.sigma_v).cuda()
     sigma = emm.stagger_sigma(grid, sh, sv)
     work = emm.Workspace(grid, survey)
     emm.forward_async(grid, survey, sigma, work)
     torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    emm.forward_async(grid, survey, sigma, work)
-    f1.record(stream)
-    torch.cuda.synchronize()
+    fwd_ms = job_max(timed_events(stream, lambda: emm.forward_async(grid, survey, sigma, work))) * 1e3
     assert emm.status(work) == emm.EMM_OK
-    fwd_ms = job_max(f0.elapsed_time(f1) / 1e3) * 1e3
     del work
-    ck = max(1, int(round(nt ** 0.5)))
+    ck = 200
+    # warm-up on a short run of the same problem
+    emm.survey_misfit_gradient(grid, dataclasses.replace(survey, nt=2 * ck), sh, sv, pos[:1], d[:1],
+                               ckpt_every=ck)
+    torch.cuda.synchronize()
+    out = {"workload": "gradient_survey_192x192x128", "nsrc": len(pos_all), "timesteps_per_solve": nt,
+           "cells": grid.cells, "forward_ms": fwd_ms, "ckpt_every": ck}
+
+    def run(stored):
+        res = {}
+
+        def go():
+            res["r"] = emm.survey_misfit_gradient(grid, survey, sh, sv, pos, d, ckpt_every=ck, stored_steps=stored)
+
+        ms = job_max(timed_events(stream, go)) * 1e3
+        misfit, gh, gv, _ = res["r"]
+        sum_over_ranks(misfit, dist)
+        sum_over_ranks(gh, dist)
+        sum_over_ranks(gv, dist)
+        ok = bool(torch.isfinite(gh).all().item() and torch.isfinite(gv).all().item())
+        return ms, misfit.item(), ok
+
+    ms0, misfit0, ok0 = run(0)
+    out["recompute_only"] = {"ms": ms0, "ratio_to_forward": ms0 / (len(pos_all) * fwd_ms / world),
+                             "snapshot_gb": 0.0, "misfit": misfit0, "finite": ok0}
     gc.collect()
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
     print(f"gradient survey: {free / 1e9:.1f} GB free, {torch.cuda.memory_allocated() / 1e9:.1f} GB allocated, "
-          f"{torch.cuda.memory_reserved() / 1e9:.1f} GB reserved by torch", file=sys.stderr)
+          f"{torch.cuda.memory_reserved() / 1e9:.1f} GB reserved by torch", file=sys.stderr, flush=True)
     room = free - (6 << 30)
     snap = emm.snapshot_bytes(grid, survey, ck)
     stored = min(nt, int(max(0, room) // snap)) // ck * ck
     while stored > 0 and emm.gradient_workspace_size(grid, survey, ck, stored) > room:
         stored -= ck
-    # warm-up on a short run of the same problem
-    emm.survey_misfit_gradient(grid, dataclasses.replace(survey, nt=2 * ck), sh, sv, pos[:1], d[:1],
-                               ckpt_every=ck)
-    torch.cuda.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    misfit, gh, gv, _ = emm.survey_misfit_gradient(grid, survey, sh, sv, pos, d, ckpt_every=ck,
-                                                   stored_steps=stored)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
-    ok = bool(torch.isfinite(gh).all().item() and torch.isfinite(gv).all().item())
-    return {"workload": "gradient_survey_192x192x128", "nsrc": len(pos), "timesteps_per_solve": nt,
-            "cells": grid.cells, "ms": ms, "forward_ms": fwd_ms, "ratio_to_forward": ms / (len(pos) * fwd_ms),
-            "ckpt_every": ck, "stored_steps": stored, "snapshot_gb": stored * snap / 1e9,
-            "free_gb_before": free / 1e9, "misfit": misfit.item(), "finite": ok,
-            "what": "emm_stagger_sigma, then per transmitter emm_misfit_gradient (forward sweep, residual "
-                    "of the noisy resistor-model data, adjoint sweep) and emm_stagger_sigma_adjoint into "
-                    "the sigma_h, sigma_v gradients; ratio against one forward solve per transmitter"}
+    ms1, misfit1, ok1 = run(stored)
+    out["stored"] = {"ms": ms1, "ratio_to_forward": ms1 / (len(pos_all) * fwd_ms / world),
+                     "stored_steps": stored, "snapshot_gb": stored * snap / 1e9, "free_gb_before": free / 1e9,
+                     "misfit": misfit1, "finite": ok1}
+    out["ratio_to_forward"] = min(out["recompute_only"]["ratio_to_forward"], out["stored"]["ratio_to_forward"])
+    out["what"] = ("emm_stagger_sigma, then per transmitter emm_misfit_gradient (forward sweep with "
+                   "checkpoints every 200 steps, residual of the noisy resistor-model data, reverse sweep "
+                   "recomputing the segments whose E snapshots are not kept, adjoint) and "
+                   "emm_stagger_sigma_adjoint into the sigma_h, sigma_v gradients; ratio against one forward "
+                   "solve per transmitter")
+    return out
 
 
 def graph_line(emm, torch, stream, job_max, grid, survey, sigma, work, steps, rate, value):
-    """The benchmark solve replayed `steps` times from a CUDA graph of its
-    time loop (emm_plan_create once, emm_plan_run per solve)."""
+    """The solve replayed `steps` times from a CUDA graph of its time loop
+    (emm_plan_create once, emm_plan_run per solve)."""
     t0 = time.perf_counter()
-    plan = emm.Plan(grid, survey, sigma, work)
+    plan = emm.Plan(grid, survey, sigma, work, stream=stream)
     torch.cuda.synchronize()
     capture_ms = 1e3 * (time.perf_counter() - t0)
-    plan.run_async(sigma)
+    plan.run_async(sigma, stream=stream)
     torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(steps):
-        plan.run_async(sigma)
-    p1.record(stream)
-    torch.cuda.synchronize()
+
+    def run():
+        for _ in range(steps):
+            plan.run_async(sigma, stream=stream)
+
+    gval = rate(job_max(timed_events(stream, run)))
     assert emm.status(work) == emm.EMM_OK
-    gval = rate(job_max(p0.elapsed_time(p1) / 1e3))
-    del plan
+    plan.close()
     return {"value": gval, "unit": "Gcell-steps/s", "vs_stream_launches": gval / value,
             "capture_and_instantiate_ms": capture_ms,
             "what": "emm_plan_run: the solve's time loop captured once as a CUDA graph and replayed"}
@@ -357,24 +561,16 @@ def jobs_line(emm, torch, stream, job_max):
     best, tune_ms = emm.jobs_tune(probs, sig, jw, steps=40)
     torch.cuda.synchronize()
 
-    def timed(fn):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return job_max(a.elapsed_time(b) / 1e3)
-
     def one_at_a_time():
         for (g, s), sg, w in zip(probs, sig, works):
             emm.forward_async(g, s, sg, w)
 
-    seq = timed(one_at_a_time)
+    seq = job_max(timed_events(stream, one_at_a_time))
     for (g, s), w in zip(probs, works):
         assert emm.status(w) == emm.EMM_OK
     rates = {}
     for k in sorted({emm.JOBS_LIST, best}):
-        t = timed(lambda: emm.forward_jobs(probs, sig, work=jw, check=False, strategy=k))
+        t = job_max(timed_events(stream, lambda: emm.forward_jobs(probs, sig, work=jw, check=False, strategy=k)))
         assert all(st == emm.EMM_OK for st in jw.status())
         same = all(torch.equal(torch.view_as_complex(r)[: s.nrec], torch.view_as_complex(w.rec)[: s.nrec])
                    for r, w, (_, s) in zip(jw.rec, works, probs))
@@ -389,6 +585,89 @@ def jobs_line(emm, torch, stream, job_max):
                     "problem in turn, device-resident inputs"}
 
 
+def batch_line(emm, torch, stream, job_max, world, rank, grid, survey, sigma, single_value, nsrc):
+    """Batched survey on the marine model: transmitters every 200 m along
+    the tow line (x = -3100 + 200 k, 50 m above the seabed) advanced
+    together; a short warm-up run, one timed solve; then the first 8."""
+    import dataclasses
+    cells, nt = grid.cells, survey.nt
+    pos = np.array([[-3100.0 + TOW_SPACING * (k + nsrc * rank), 0.0, float(survey.src[2])]
+                    for k in range(nsrc)])
+    out = {}
+    for name, p in (("all", pos), ("nsrc_8", pos[: min(8, len(pos))])):
+        emm.forward_batch(grid, dataclasses.replace(survey, nt=30), sigma, p)
+        bwork = torch.empty(emm.batch_workspace_size(grid, survey, len(p)) + 256, dtype=torch.uint8,
+                            device=sigma.device)
+        torch.cuda.synchronize()
+        bsec = job_max(timed_events(stream, lambda: emm.forward_batch(grid, survey, sigma, p, work=bwork)))
+        out[name] = (aggregate_rate(world, cells * len(p), nt, 1, bsec), bsec)
+        del bwork
+    return {"nsrc": nsrc, "value": out["all"][0], "unit": "Gcell-steps/s", "ms_per_solve": 1e3 * out["all"][1],
+            "vs_one_at_a_time": out["all"][0] / single_value,
+            "nsrc_8": {"value": out["nsrc_8"][0], "vs_one_at_a_time": out["nsrc_8"][0] / single_value},
+            "what": "emm_forward_batch on the marine model: transmitters sharing grid, sigma and receivers in "
+                    "the same launches, against the device-resident single-transmitter marine value"}
+
+
+def airwave_line(emm, torch, stream, job_max, world):
+    """Top boundary with air (Sec. 3.3): the marine model on a grid uniform
+    in x and y, one warm-up and one timed solve with and without air."""
+    awl = W.marine_1d_air()
+    agrid = emm.grid_for(awl)
+    ant = emm.steps_for(awl, agrid)
+    asig = torch.from_numpy(awl.sigma.astype(np.float32)).cuda()
+    rates = {}
+    for air in (False, True):
+        asurvey = emm.survey_for(awl, nt=ant, airwave=air)
+        awork = emm.Workspace(agrid, asurvey)
+        emm.forward_async(agrid, asurvey, asig, awork)
+        torch.cuda.synchronize()
+        sec = job_max(timed_events(stream, lambda: emm.forward_async(agrid, asurvey, asig, awork)))
+        assert emm.status(awork) == emm.EMM_OK
+        rates[air] = aggregate_rate(world, agrid.cells, ant, 1, sec)
+        del awork
+    return {"workload": awl.name, "value": rates[True], "unit": "Gcell-steps/s", "without_air": rates[False],
+            "overhead": rates[False] / rates[True], "timesteps_per_solve": ant,
+            "what": "forward solve with air above the sea surface (plane FFTs after every half step) against "
+                    "the same model with CPML on the top face"}
+
+
+def gradient_line(emm, torch, stream, job_max, grid, survey, sigma, fwd_ms):
+    """Gradient of Re(sum conj(v) G) on the marine model for a seeded
+    cotangent v: one warm-up call and one timed call recomputing every
+    segment, then the same with the E snapshots of as many final steps as
+    the free device memory holds (less 6 GB), against one forward solve."""
+    nt = survey.nt
+    rng = np.random.default_rng(230400237)
+    v = rng.standard_normal((survey.nrec, 6, len(survey.freqs))) + 1j * rng.standard_normal(
+        (survey.nrec, 6, len(survey.freqs)))
+    vt = torch.from_numpy(v).cuda()
+    ck = max(1, int(round(nt ** 0.5)))
+    emm.vjp(grid, survey, sigma, vt, ckpt_every=ck)
+    torch.cuda.synchronize()
+    grad_ms = job_max(timed_events(stream, lambda: emm.vjp(grid, survey, sigma, vt, ckpt_every=ck,
+                                                           check=False))) * 1e3
+    gc.collect()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    snap = emm.snapshot_bytes(grid, survey, ck)
+    room = free - (6 << 30)
+    stored = min(nt, int(max(0, room) // snap)) // ck * ck
+    while stored > 0 and emm.gradient_workspace_size(grid, survey, ck, stored) > room:
+        stored -= ck
+    emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, stored_steps=stored, check=False)
+    torch.cuda.synchronize()
+    st_ms = job_max(timed_events(stream, lambda: emm.vjp(grid, survey, sigma, vt, ckpt_every=ck,
+                                                         stored_steps=stored, check=False))) * 1e3
+    return {"workload": MARINE, "ms": st_ms, "forward_ms": fwd_ms, "ratio_to_forward": st_ms / fwd_ms,
+            "ckpt_every": ck, "stored_steps": stored, "snapshot_gb": stored * snap / 1e9,
+            "recompute_only_ms": grad_ms, "ratio_recompute_only": grad_ms / fwd_ms,
+            "what": "emm_gradient_stored: forward sweep keeping checkpoints and the E snapshots of the last "
+                    "stored_steps steps in device memory, recomputation of the earlier segments and the adjoint "
+                    "sweep, one cotangent of all receiver data; recompute_only: every segment recomputed "
+                    "(emm_gradient)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,14 +676,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline line (no marine, batch, airwave, gradient, jobs or survey lines)")
+    ap.add_argument("--no-marine", action="store_true", help="skip the marine-model line")
     ap.add_argument("--no-gradient", action="store_true",
-                    help="skip the gradient / forward time ratio (one emm_gradient call after the timed region)")
+                    help="skip the gradient / forward time ratio on the marine model")
     ap.add_argument("--graph", action="store_true",
-                    help="add the CUDA-graph line (the solve replayed from a captured time loop)")
+                    help="add the CUDA-graph line (the marine solve replayed from a captured time loop)")
     ap.add_argument("--no-jobs", action="store_true",
                     help="skip the uneven-grid work-list line (eight grids, one launch per half-step)")
     ap.add_argument("--no-gradient-survey", action="store_true",
-                    help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid (about a minute)")
+                    help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid")
     ap.add_argument("--no-airwave", action="store_true",
                     help="skip the air-boundary line (uniform-xy marine model with and without air on top)")
     ap.add_argument("--batch", type=int, default=32,
@@ -452,186 +734,112 @@ def main():
         return max_over_ranks(v, dist, "cuda")
 
     # ---- timed region: K device-resident solves ----
-    e_ms, h_ms, loop_ms = [], [], []
+    tims = []
     with ClockSampler(local) as clk:
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            t = emm.forward_timed(grid, survey, sigma, work, every=64)
-            e_ms.append(t["e_ms"])
-            h_ms.append(t["h_ms"])
-            loop_ms.append(t["loop_ms"])
+            tims.append(emm.forward_timed(grid, survey, sigma, work, every=64))
         ev1.record(stream)
         barrier()
     elapsed = job_max(ev0.elapsed_time(ev1) / 1e3)
     clocks = clk.summary()
     value = aggregate_rate(world, cells, nt, args.steps, elapsed)
+    assert emm.status(work) == emm.EMM_OK
+    G_dev = torch.view_as_complex(work.rec)[: survey.nrec].clone()
+    err = None
+    if rank == 0:
+        err = golden_error(wl, nt, G_dev.cpu().numpy(),
+                           None if work.vol is None else torch.view_as_complex(work.vol).cpu().numpy())
+    # the one gather of the survey's results: every rank's receiver G on rank 0
+    gathered = gather_to_rank0(G_dev, dist, world)
 
-    # ---- e2e: pinned host sigma in, receiver Green's functions out ----
+    # ---- e2e: pinned host sigma in, receiver and volume Green's functions out ----
+    e2e_solves = max(1, min(args.steps, E2E_SOLVES))
     rec_host = torch.empty(work.rec.shape, dtype=work.rec.dtype).pin_memory()
+    vol_host = None if work.vol is None else torch.empty(work.vol.shape, dtype=work.vol.dtype).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_solves):
         sig_dev = sigma_host.to("cuda", non_blocking=True)
         emm.forward_async(grid, survey, sig_dev, work)
         rec_host.copy_(work.rec, non_blocking=True)
+        if vol_host is not None:
+            vol_host.copy_(work.vol, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = job_max(time.perf_counter() - t0)
     barrier()
-    e2e_value = aggregate_rate(world, cells, nt, args.steps, e2e_s)
+    e2e_value = aggregate_rate(world, cells, nt, e2e_solves, e2e_s)
+    d2h = int(rec_host.numel() * 8) + (0 if vol_host is None else int(vol_host.numel() * 8))
+    del vol_host
 
     peak, peak_kind = measured_peaks()
-    e_mean, h_mean = float(np.mean(e_ms)), float(np.mean(h_ms))
+    e_mean = float(np.mean([t["e_ms"] for t in tims]))
+    h_mean = float(np.mean([t["h_ms"] for t in tims]))
+    v_mean = float(np.mean([t["v_ms"] for t in tims]))
     alg = algorithmic_bytes(wl)
-    be, bh = per_kernel_bytes(wl)
-    # one leapfrog step as the time loop runs it: E and H back to back, each
-    # launch a programmatic dependent of the one before
-    step_s = float(np.mean(loop_ms)) / nt / 1e3
+    kb = per_kernel_bytes(wl)
+    # one leapfrog step as the time loop runs it: E, volume DTFT and H back to
+    # back, each launch a programmatic dependent of the one before
+    step_s = float(np.mean([t["loop_ms"] for t in tims])) / nt / 1e3
     achieved = alg / step_s / 1e9
-    kernel_launches = args.steps * (1 + 2 * nt + (1 if survey.nrec else 0) + (1 if survey.volume else 0))
+    per_solve = 1 + 2 * nt + (nt if survey.volume else 0) + (1 if survey.nrec else 0) + (1 if survey.volume else 0)
+    kernels = {"k_update_E": e_mean, "k_update_H": h_mean}
+    if survey.volume:
+        kernels["k_volume_dft"] = v_mean
     line = {
         "metric": "FDTD forward Gcell-steps/s", "value": value, "unit": "Gcell-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "grid_nodes": list(wl.shape), "padded": list(grid.npad),
-                   "padded_cells": cells, "rd": wl.rd, "timesteps_per_solve": nt,
-                   "nfreq": len(wl.freqs), "nrec": survey.nrec, "volume_dtft": bool(wl.volume),
-                   "parallelism": f"{world} independent transmitters" if world > 1 else "single GPU",
-                   "l2": "no flush: per-solve working set (fields, 1/eps, CPML) exceeds the 126 MB L2"},
-        "roofline": {"bound": "hbm", "kernel": "leapfrog step = k_update_E + k_update_H",
+        "config": bench_config(wl, nt, world),
+        "roofline": {"bound": "hbm", "kernel": "leapfrog step = k_update_E + k_volume_dft + k_update_H"
+                                               if survey.volume else "leapfrog step = k_update_E + k_update_H",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": ("of measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                    if peak_kind == "measured" else "of fallback 6.4 TB/s"),
                      "algorithmic_bytes_per_step": alg, "step_ms": 1e3 * step_s,
                      "step_ms_from": "CUDA events around the whole time loop / leapfrog steps",
-                     "isolated_step_ms": e_mean + h_mean,
+                     "isolated_step_ms": e_mean + h_mean + (v_mean if survey.volume else 0.0),
                      "traffic": recorded_traffic(wl.name),
-                     "kernels": {"k_update_E": {"ms": e_mean, "min_bytes": be, "gbs": be / e_mean / 1e6},
-                                 "k_update_H": {"ms": h_mean, "min_bytes": bh, "gbs": bh / h_mean / 1e6}}},
-        "e2e": {"value": e2e_value, "unit": "Gcell-steps/s",
-                "h2d_bytes_per_step": int(sigma_host.numel() * 4),
-                "d2h_bytes_per_step": int(rec_host.numel() * 8)},
-        "gpu_launches": kernel_launches,
+                     "kernels": {k: {"ms": ms, "min_bytes": kb[k], "gbs": kb[k] / ms / 1e6,
+                                     "frac": kb[k] / ms / 1e6 / peak} for k, ms in kernels.items()}},
+        "error_vs_oracle": err,
+        "e2e": {"value": e2e_value, "unit": "Gcell-steps/s", "solves": e2e_solves,
+                "h2d_bytes_per_step": int(sigma_host.numel() * 4), "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * per_solve,
         "clocks": clocks,
+        "gathered_transmitters": None if gathered is None else int(gathered.shape[0]),
     }
-    # the same solve replayed from a CUDA graph of its time loop (emm_plan);
-    # opt-in (--graph): a default run that included it did not finish
-    if args.graph:
-        line["graph"] = graph_line(emm, torch, stream, job_max, grid, survey, sigma, work, args.steps,
-                                   lambda sec: aggregate_rate(world, cells, nt, args.steps, sec), value)
-    if args.batch > 0:
-        # batched survey: transmitters every 200 m along the tow line
-        # (x = -3100 + 200 k, 50 m above the seabed), advanced together;
-        # a short warm-up run, one timed solve (CUDA events)
-        import dataclasses
-        pos = np.array([[-3100.0 + TOW_SPACING * (k + args.batch * rank), 0.0, float(wl.src[2])]
-                        for k in range(args.batch)])
-        emm.forward_batch(grid, dataclasses.replace(survey, nt=30), sigma, pos)
-        bwork = torch.empty(emm.batch_workspace_size(grid, survey, len(pos)) + 256, dtype=torch.uint8,
-                            device=sigma.device)
-        torch.cuda.synchronize()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        emm.forward_batch(grid, survey, sigma, pos, work=bwork)  # (checks the device status)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bsec = job_max(b0.elapsed_time(b1) / 1e3)
-        bval = aggregate_rate(world, cells * args.batch, nt, 1, bsec)
-        del bwork
-        # the same with the first 8 transmitters only
-        few = pos[: min(8, len(pos))]
-        _, fwork = emm.forward_batch(grid, dataclasses.replace(survey, nt=30), sigma, few)
-        fwork = torch.empty(emm.batch_workspace_size(grid, survey, len(few)) + 256, dtype=torch.uint8,
-                            device=sigma.device)
-        torch.cuda.synchronize()
-        b0.record(stream)
-        emm.forward_batch(grid, survey, sigma, few, work=fwork)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        fval = aggregate_rate(world, cells * len(few), nt, 1, job_max(b0.elapsed_time(b1) / 1e3))
-        del fwork
-        line["batch"] = {"nsrc": args.batch, "value": bval, "unit": "Gcell-steps/s", "ms_per_solve": 1e3 * bsec,
-                         "vs_one_at_a_time": bval / value,
-                         "nsrc_8": {"value": fval, "vs_one_at_a_time": fval / value},
-                         "what": "emm_forward_batch: transmitters sharing grid, sigma and receivers in the same "
-                                 "launches, against the device-resident single-transmitter value"}
-    if not args.no_airwave and wl.name.startswith("marine"):
-        # top boundary with air (Sec. 3.3): the marine model on a grid uniform
-        # in x and y, one warm-up and one timed solve with and without air
-        awl = W.marine_1d_air()
-        agrid = emm.grid_for(awl)
-        ant = emm.steps_for(awl, agrid)
-        asig = torch.from_numpy(awl.sigma.astype(np.float32)).cuda()
-        acells = agrid.cells
-        rates = {}
-        for air in (False, True):
-            asurvey = emm.survey_for(awl, nt=ant, airwave=air)
-            awork = emm.Workspace(agrid, asurvey)
-            emm.forward_async(agrid, asurvey, asig, awork)
-            torch.cuda.synchronize()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            emm.forward_async(agrid, asurvey, asig, awork)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            assert emm.status(awork) == emm.EMM_OK
-            rates[air] = aggregate_rate(world, acells, ant, 1, job_max(a0.elapsed_time(a1) / 1e3))
-            del awork
-        line["airwave"] = {"workload": awl.name, "value": rates[True], "unit": "Gcell-steps/s",
-                           "without_air": rates[False], "overhead": rates[False] / rates[True],
-                           "timesteps_per_solve": ant,
-                           "what": "forward solve with air above the sea surface (plane DFTs after every "
-                                   "half step) against the same model with CPML on the top face"}
-    if not args.no_gradient:
-        # gradient of Re(sum conj(v) G) for a seeded cotangent v: one warm-up
-        # call, one timed call (CUDA events), against one forward solve
-        rng = np.random.default_rng(230400237)
-        v = rng.standard_normal((survey.nrec, 6, len(wl.freqs))) + 1j * rng.standard_normal(
-            (survey.nrec, 6, len(wl.freqs)))
-        vt = torch.from_numpy(v).cuda()
-        ck = max(1, int(round(nt ** 0.5)))
-        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck)
-        torch.cuda.synchronize()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, check=False)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        grad_ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
-        fwd_ms = 1e3 * elapsed / args.steps
-        # the same with the E snapshots of as many final steps as the free
-        # device memory holds (less 6 GB for the outputs and the allocator),
-        # which the reverse sweep then does not recompute
-        gc.collect()
-        torch.cuda.empty_cache()
-        free, _ = torch.cuda.mem_get_info()
-        snap = emm.snapshot_bytes(grid, survey, ck)
-        room = free - (6 << 30)
-        stored = min(nt, int(max(0, room) // snap)) // ck * ck
-        while stored > 0 and emm.gradient_workspace_size(grid, survey, ck, stored) > room:
-            stored -= ck
-        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, stored_steps=stored, check=False)
-        torch.cuda.synchronize()
-        g0.record(stream)
-        emm.vjp(grid, survey, sigma, vt, ckpt_every=ck, stored_steps=stored, check=False)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        st_ms = job_max(g0.elapsed_time(g1) / 1e3) * 1e3
-        line["gradient"] = {"ms": st_ms, "forward_ms": fwd_ms, "ratio_to_forward": st_ms / fwd_ms,
-                            "ckpt_every": ck, "stored_steps": stored,
-                            "snapshot_gb": stored * snap / 1e9,
-                            "recompute_only_ms": grad_ms, "ratio_recompute_only": grad_ms / fwd_ms,
-                            "what": "emm_gradient_stored: forward sweep keeping checkpoints and the E snapshots "
-                                    "of the last stored_steps steps in device memory, recomputation of the "
-                                    "earlier segments and the adjoint sweep, one cotangent of all receiver "
-                                    "data; recompute_only: every segment recomputed (emm_gradient)"}
-    if not args.no_jobs:
+    del work
+    gc.collect()
+    torch.cuda.empty_cache()
+    extras = not args.no_extras
+    if extras and not args.no_marine:
+        m = marine_line(emm, torch, stream, job_max, world, rank)
+        line["marine"] = m["line"]
+        mwl, mgrid, msurvey, msigma, mwork, mnt = m["ctx"]
+        mvalue = m["line"]["value"]
+        # the same solve replayed from a CUDA graph of its time loop (emm_plan);
+        # opt-in (--graph)
+        if args.graph:
+            line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
+                                       lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)
+        if args.batch > 0:
+            line["batch"] = batch_line(emm, torch, stream, job_max, world, rank, mgrid, msurvey, msigma,
+                                       mvalue, args.batch)
+        if not args.no_airwave:
+            line["airwave"] = airwave_line(emm, torch, stream, job_max, world)
+        if not args.no_gradient:
+            line["gradient"] = gradient_line(emm, torch, stream, job_max, mgrid, msurvey, msigma,
+                                             m["line"]["ms_per_solve"])
+        del mwork, m
+    if extras and not args.no_jobs:
         line["jobs"] = jobs_line(emm, torch, stream, job_max)
-    if not args.no_gradient_survey:
-        line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max)
-    if rank == 0 and not args.no_cpu_baseline:
+    if extras and not args.no_gradient_survey:
+        line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max, dist, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W.WORKLOADS[args.workload]())
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -197,12 +197,14 @@ typedef struct {
   int every;       /* in: time the launches of every `every`-th step (>= 1) */
   int samples;     /* out: number of steps timed */
   double e_ms;     /* out: mean duration (ms) of one E half step: the E launch
-                      and the source, air and volume-DTFT launches after it */
+                      and the source and air launches after it */
   double h_ms;     /* out: mean duration (ms) of one H half step: the H launch
                       and the source and air launches after it */
   double total_ms; /* out: duration (ms) of the whole enqueued forward run */
   double loop_ms;  /* out: duration (ms) of the time loop alone: every E and H
                       launch back to back, from the first to the last */
+  double v_ms;     /* out: mean duration (ms) of one volume-DTFT launch (0 when
+                      survey->volume is 0) */
 } emm_timing;
 
 /* emm_forward, with CUDA events recorded on `stream` around the E and H
@@ -225,7 +227,10 @@ int emm_forward_timed(const emm_grid *grid, const emm_survey *survey, const floa
  * already enqueued returns at once.  At most survey->nt steps run.
  * The verdicts reach the host through mapped pinned host memory (allocated
  * and freed by the call: 8 bytes), polled with one chunk of launches enqueued
- * ahead, each poll bounded (EMM_ETIMEOUT after 600 s without progress).
+ * ahead, each poll bounded (EMM_ETIMEOUT after 600 s without progress; the
+ * environment variable EMM_POLL_TIMEOUT_S, in seconds, lowers the bound, for
+ * tests of that path).  On a poll timeout the call still drains `stream`
+ * (the enqueued launches finish) before it returns EMM_ETIMEOUT.
  * Synchronous: returns with `stream` drained.  *nt_run (host) receives the
  * steps taken.  Arguments, workspace (emm_workspace_size) and outputs as
  * emm_forward, the outputs being those of emm_forward with nt = *nt_run.
@@ -332,6 +337,84 @@ int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, siz
  * if steps < 1 or ms or best is NULL; otherwise as emm_forward_jobs. */
 int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
                   double *ms, int *best);
+
+/* ---- Persistent work list: many problems in one cooperative launch ----
+ * The paper runs one MPI rank per transmitter (Sec. 5); on one GPU the
+ * transmitters of a survey and problems on grids of uneven sizes advance
+ * together in ONE persistent launch: the resident CTAs walk the E half-step
+ * tiles (and receiver CTAs) of every problem, meet at a grid barrier, walk
+ * the H half-step tiles, meet again, for every leapfrog step.  Each item runs
+ * the per-CTA code of the problem's own launch, so every problem's G equals
+ * its emm_forward (or emm_forward_batch) result bit for bit.
+ *
+ * One task: a grid and survey with its conductivity (device float
+ * [3][n3][n2][n1]); nsrc >= 1 transmitters sharing them (as
+ * emm_forward_batch) at src_pos (host double [nsrc][3]; may be NULL when
+ * nsrc == 1: survey->src); rec_out device double [nsrc][nrec][6][nfreq][2]. */
+typedef struct emm_task {
+  const emm_grid *grid;
+  const emm_survey *survey;
+  const float *sigma;
+  int nsrc;
+  const double *src_pos;
+  double *rec_out;
+} emm_task;
+
+/* Launch options of the persistent work list. */
+typedef struct {
+  int ctas_per_sm;   /* resident CTAs per SM: 0 = as many as fit, else at most this many */
+  int max_ctas;      /* 0 = no further limit, else at most this many CTAs in all */
+  double wait_s;     /* bound of one grid-barrier wait, seconds (<= 0: 1 s) */
+  int skip_arrival;  /* testing only: the index of one CTA that leaves without arriving at the
+                        first grid barrier, so that every other CTA's bounded wait runs out and the
+                        run ends with EMM_ETIMEOUT; -1 (or any index >= the CTA count) normally */
+} emm_persist_opts;
+
+/* Workspace of emm_forward_persistent: a 256-byte header (the work list's
+ * status word first, so emm_status(ws) reads it), then each task's forward
+ * workspace (emm_batch_workspace_size of its nsrc), 256-byte aligned.
+ * offsets: NULL or a host array of ntasks receiving each task's byte offset
+ * (emm_status(ws + offsets[j]) reads task j's own status word).  EMM_EINVAL
+ * if ntasks is outside 1..16, the tasks' FD orders differ, nsrc < 1, src_pos
+ * is NULL with nsrc > 1, or a survey asks for the volume DTFT, the air
+ * boundary, a magnetic source or an antenna. */
+int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes, size_t *offsets);
+
+/* Forward solves of the tasks in one persistent cooperative launch (after
+ * each task's set-up, enqueued on `stream`, and before its normalisation).
+ * opts NULL: the defaults {0, 0, 1.0, -1}.  Every grid-barrier wait is
+ * bounded by opts->wait_s of device time; a wait that runs out writes
+ * EMM_ETIMEOUT to the header's status word and every CTA returns at its next
+ * barrier (the outputs are then undefined).  Asynchronous on `stream`;
+ * host-detected errors as emm_forward and emm_persist_workspace_size, with
+ * nothing enqueued; EMM_ECUDA if the launch fails (for instance when the
+ * CTAs cannot all be resident). */
+int emm_forward_persistent(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
+                           size_t ws_bytes, emm_stream stream);
+
+/* Autotuner of the persistent launch: times `steps` leapfrog steps (each
+ * task's own count at most) with 1, 2, ... resident CTAs per SM (at most
+ * *ncand candidates, at most the occupancy limit), each after a warm-up run,
+ * with CUDA events on `stream`; returns the times in ms[0 .. *ncand - 1]
+ * (host; *ncand receives the number tried) and the fastest options in *best.
+ * Synchronises `stream`; the workspace is left to be prepared again. */
+int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_bytes, int steps, emm_stream stream,
+                     emm_persist_opts *best, double *ms, int *ncand);
+
+/* The whole persistent solve of fixed tasks captured once as a CUDA graph:
+ * the tasks' set-up (state cleared, dt/eps from the conductivity at each
+ * task's sigma pointer; the tables are uploaded once, at creation), the
+ * cooperative launch and the normalisation.  emm_persist_plan_run replays
+ * it on `stream` for the current contents of the bound sigma buffers into
+ * the bound outputs; the plan keeps its own copies of the host arrays the
+ * tasks point to.  Errors as emm_forward_persistent; EMM_ECUDA if the
+ * capture or instantiation fails.  Destroy frees the graph (a launch in
+ * flight completes first). */
+typedef struct emm_persist_plan emm_persist_plan;
+int emm_persist_plan_create(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
+                            size_t ws_bytes, emm_stream stream, emm_persist_plan **out);
+int emm_persist_plan_run(emm_persist_plan *plan, emm_stream stream);
+void emm_persist_plan_destroy(emm_persist_plan *plan);
 
 /* Device workspace bytes emm_gradient needs (the forward workspace, the
  * checkpoints of every ckpt_every-th step, the E snapshots of one checkpoint
@@ -442,11 +525,18 @@ int emm_stagger_sigma_adjoint(const emm_grid *grid, const double *grad, void *ws
  * no counterpart of this call; it computes what emm_forward computes.
  *   Instead of a caller workspace it uses one file-scope device array of
  *   EMM_STATIC_SCRATCH_BYTES (64 MiB) inside the library, which every GPU that
- *   loads the library holds until the process exits.  It allocates nothing:
- *   no cudaMalloc, no cudaFree, no allocating library routine.  The first
- *   call on a device looks up that device's address of the array (the device
- *   that is current at the call); make this first call on each device before
- *   any stream capture.
+ *   loads the library holds until the process exits.  The call itself
+ *   allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *   routine.  The array is created when the library's device code is loaded
+ *   into a context, which the CUDA runtime does at the first library call that
+ *   touches that device (with lazy module loading, possibly at this call's
+ *   first use); that load can allocate and synchronise like any module load,
+ *   so make one library call on each device before the code that must not
+ *   allocate.  The first call in a context looks up the array's address there
+ *   (the context of the device current at the call) and caches it per
+ *   context; make this first call on each device before any stream capture.
+ *   After a device reset the module is loaded again in a new context, and the
+ *   next call looks the address up again.
  *   Arguments sigma, rec_out, vol_out and stream are those of emm_forward
  *   (device buffers the caller owns).  status: NULL, or a host int that, after
  *   the call has synchronised `stream`, receives the device status word of

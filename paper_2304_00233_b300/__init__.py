@@ -41,7 +41,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_gradient_stored_workspace_size", "emm_gradient_stored", "emm_misfit_gradient",
             "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint",
             "emm_jobs_workspace_size", "emm_forward_jobs", "emm_jobs_tune", "emm_plan_create", "emm_plan_run",
-            "emm_plan_destroy")
+            "emm_plan_destroy", "emm_persist_workspace_size", "emm_forward_persistent", "emm_persist_tune",
+            "emm_persist_plan_create", "emm_persist_plan_run", "emm_persist_plan_destroy")
 
 
 class EmmError(RuntimeError):
@@ -65,7 +66,8 @@ class _GridInfo(C.Structure):
 
 class _Timing(C.Structure):
     _fields_ = [("every", C.c_int), ("samples", C.c_int), ("e_ms", C.c_double),
-                ("h_ms", C.c_double), ("total_ms", C.c_double), ("loop_ms", C.c_double)]
+                ("h_ms", C.c_double), ("total_ms", C.c_double), ("loop_ms", C.c_double),
+                ("v_ms", C.c_double)]
 
 
 class _Survey(C.Structure):
@@ -80,6 +82,27 @@ class _Survey(C.Structure):
 class _Job(C.Structure):
     _fields_ = [("grid", C.c_void_p), ("survey", C.POINTER(_Survey)), ("sigma", C.c_void_p),
                 ("rec_out", C.c_void_p)]
+
+
+class _Task(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("survey", C.POINTER(_Survey)), ("sigma", C.c_void_p),
+                ("nsrc", C.c_int), ("src_pos", _D), ("rec_out", C.c_void_p)]
+
+
+class PersistOpts(C.Structure):
+    """``emm_persist_opts``: resident CTAs per SM (0: as many as fit), a cap
+    on all CTAs (0: none), the bound of one grid-barrier wait in seconds
+    (<= 0: 1 s) and, for tests only, a CTA that withholds its first arrival
+    (-1: none)."""
+    _fields_ = [("ctas_per_sm", C.c_int), ("max_ctas", C.c_int), ("wait_s", C.c_double),
+                ("skip_arrival", C.c_int)]
+
+    def __init__(self, ctas_per_sm=0, max_ctas=0, wait_s=0.0, skip_arrival=-1):
+        super().__init__(int(ctas_per_sm), int(max_ctas), float(wait_s), int(skip_arrival))
+
+    def __repr__(self):
+        return (f"PersistOpts(ctas_per_sm={self.ctas_per_sm}, max_ctas={self.max_ctas}, wait_s={self.wait_s}, "
+                f"skip_arrival={self.skip_arrival})")
 
 
 _lib = None
@@ -126,6 +149,15 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
                                     C.c_int),
         "emm_forward_jobs": ([C.c_int, C.POINTER(_Job), C.c_int, V, C.c_size_t, V], C.c_int),
         "emm_jobs_tune": ([C.c_int, C.POINTER(_Job), V, C.c_size_t, C.c_int, V, _D, _I], C.c_int),
+        "emm_persist_workspace_size": ([C.c_int, C.POINTER(_Task), C.POINTER(C.c_size_t),
+                                        C.POINTER(C.c_size_t)], C.c_int),
+        "emm_forward_persistent": ([C.c_int, C.POINTER(_Task), C.POINTER(PersistOpts), V, C.c_size_t, V], C.c_int),
+        "emm_persist_tune": ([C.c_int, C.POINTER(_Task), V, C.c_size_t, C.c_int, V, C.POINTER(PersistOpts), _D,
+                              _I], C.c_int),
+        "emm_persist_plan_create": ([C.c_int, C.POINTER(_Task), C.POINTER(PersistOpts), V, C.c_size_t, V,
+                                     C.POINTER(V)], C.c_int),
+        "emm_persist_plan_run": ([V, V], C.c_int),
+        "emm_persist_plan_destroy": ([V], None),
         "emm_plan_create": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V, C.POINTER(V)], C.c_int),
         "emm_plan_run": ([V, V, V], C.c_int),
         "emm_plan_destroy": ([V], None),
@@ -347,8 +379,9 @@ def forward_converge(grid: Grid, survey: Survey, sigma, work: Workspace, stream=
 def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int = 64,
                   stream=None) -> dict:
     """``emm_forward_timed``: like ``forward_async`` but synchronises and
-    returns the mean device duration of the E and H launches (sampled every
-    ``every`` steps), of the time loop and of the whole run, in ms."""
+    returns the mean device duration of the E, volume-DTFT and H launches
+    (sampled every ``every`` steps), of the time loop and of the whole run,
+    in ms."""
     import torch
     _check_sigma(grid, sigma)
     if stream is None:
@@ -362,7 +395,8 @@ def forward_timed(grid: Grid, survey: Survey, sigma, work: Workspace, every: int
         C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream),
         C.byref(t))
     _check(code, "emm_forward_timed")
-    return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, total_ms=t.total_ms, loop_ms=t.loop_ms)
+    return dict(samples=t.samples, e_ms=t.e_ms, h_ms=t.h_ms, v_ms=t.v_ms, total_ms=t.total_ms,
+                loop_ms=t.loop_ms)
 
 
 def forward_static(grid: Grid, survey: Survey, sigma, rec, vol=None, stream=None,
@@ -560,11 +594,15 @@ class Plan:
         vol = None if self.work.vol is None else torch.view_as_complex(self.work.vol)
         return G, vol
 
-    def __del__(self):
+    def close(self):
+        """``emm_plan_destroy`` now (otherwise when the object is collected)."""
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib is not None:
             _lib.emm_plan_destroy(h)
-            self._h = None
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class JobsWork:
@@ -659,6 +697,154 @@ def forward_jobs(problems, sigmas, work: Optional[JobsWork] = None, stream=None,
             if v != EMM_OK:
                 raise EmmError(v, f"emm_forward_jobs (device status of problem {j})")
     return [torch.view_as_complex(r)[: s.nrec] for r, (_, s) in zip(work.rec, problems)], work
+
+
+class PersistWork:
+    """Workspace and outputs of the persistent work list for fixed tasks.
+    A task is (Grid, Survey, src_pos): ``src_pos`` None (the survey's
+    transmitter) or [nsrc][3] transmitters sharing grid and conductivity.
+    ``rec[j]`` is task j's float64 output [nsrc][nrec][6][nfreq][2]."""
+
+    def __init__(self, tasks, device="cuda"):
+        import torch
+        self.tasks = [(g, s, None if p is None else np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3))
+                      for g, s, p in tasks]
+        self.rec = [torch.zeros((1 if p is None else len(p), max(s.nrec, 1), 6, len(s.freqs), 2),
+                                dtype=torch.float64, device=device) for _, s, p in self.tasks]
+        arr, self._keep = self._c([None] * len(self.tasks))
+        n = C.c_size_t(0)
+        offs = (C.c_size_t * len(self.tasks))()
+        _check(load_library().emm_persist_workspace_size(len(self.tasks), arr, C.byref(n), offs),
+               "emm_persist_workspace_size")
+        self.nbytes = n.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        self.ptr = self.buf.data_ptr() + (-self.buf.data_ptr()) % 256
+        self.offsets = [int(o) for o in offs]
+        self.best, self.tune_ms = None, None
+
+    def _c(self, sigmas):
+        arr = (_Task * len(self.tasks))()
+        keep = []
+        for j, (grid, survey, pos) in enumerate(self.tasks):
+            sc, k = survey._c()
+            keep += [sc, k]
+            arr[j].grid = grid.handle
+            arr[j].survey = C.pointer(sc)
+            arr[j].sigma = sigmas[j].data_ptr() if sigmas[j] is not None else None
+            arr[j].nsrc = 1 if pos is None else len(pos)
+            arr[j].src_pos = _dp(pos) if pos is not None else None
+            arr[j].rec_out = self.rec[j].data_ptr()
+        return arr, keep
+
+    def _status_at(self, off, stream):
+        v = C.c_int(0)
+        _check(load_library().emm_status(C.c_void_p(self.ptr + off), C.byref(v), C.c_void_p(stream.cuda_stream)),
+               "emm_status")
+        return int(v.value)
+
+    def status(self, stream=None):
+        """(work-list status, [each task's status]) of the last run
+        (synchronises)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.buf.device)
+        return self._status_at(0, stream), [self._status_at(o, stream) for o in self.offsets]
+
+    def G(self):
+        """Each task's Green's functions, complex128 [nsrc][nrec][6][nfreq]."""
+        import torch
+        return [torch.view_as_complex(r)[:, : s.nrec] for r, (_, s, _) in zip(self.rec, self.tasks)]
+
+
+def _persist_check(work: PersistWork, sigmas):
+    sigmas = list(sigmas)
+    if len(sigmas) != len(work.tasks):
+        raise ValueError("one sigma per task")
+    for (grid, _, _), sg in zip(work.tasks, sigmas):
+        _check_sigma(grid, sg)
+    return sigmas
+
+
+def persist_tune(work: PersistWork, sigmas, steps: int = 40, candidates: int = 8, stream=None):
+    """``emm_persist_tune``: times ``steps`` leapfrog steps with 1, 2, ...
+    resident CTAs per SM and returns (best PersistOpts, {ctas_per_sm: ms})."""
+    import torch
+    sigmas = _persist_check(work, sigmas)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigmas[0].device)
+    arr, keep = work._c(sigmas)
+    ms = np.zeros(int(candidates))
+    nc = C.c_int(int(candidates))
+    best = PersistOpts()
+    _check(load_library().emm_persist_tune(len(work.tasks), arr, C.c_void_p(work.ptr), C.c_size_t(work.nbytes),
+                                           int(steps), C.c_void_p(stream.cuda_stream), C.byref(best), _dp(ms),
+                                           C.byref(nc)), "emm_persist_tune")
+    return best, {k + 1: float(ms[k]) for k in range(nc.value)}
+
+
+def forward_persistent(work: PersistWork, sigmas, opts: Optional[PersistOpts] = None, stream=None,
+                       check: bool = True):
+    """``emm_forward_persistent``: every task's forward solve in one
+    persistent cooperative launch.  ``opts`` None: the options
+    ``persist_tune`` finds fastest (tuned once per ``work``).  Returns each
+    task's G (complex128 [nsrc][nrec][6][nfreq]); with ``check`` the status
+    words are read (synchronises) and a failure raises."""
+    import torch
+    sigmas = _persist_check(work, sigmas)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigmas[0].device)
+    if opts is None:
+        if work.best is None:
+            work.best, work.tune_ms = persist_tune(work, sigmas, stream=stream)
+        opts = work.best
+    arr, keep = work._c(sigmas)
+    _check(load_library().emm_forward_persistent(len(work.tasks), arr, C.byref(opts), C.c_void_p(work.ptr),
+                                                 C.c_size_t(work.nbytes), C.c_void_p(stream.cuda_stream)),
+           "emm_forward_persistent")
+    if check:
+        top, each = work.status(stream)
+        if top != EMM_OK:
+            raise EmmError(top, "emm_forward_persistent (work-list status)")
+        for j, v in enumerate(each):
+            if v != EMM_OK:
+                raise EmmError(v, f"emm_forward_persistent (device status of task {j})")
+    return work.G()
+
+
+class PersistPlan:
+    """``emm_persist_plan_create`` / ``_run``: the persistent solve of
+    ``work``'s tasks on the buffers ``sigmas`` captured once as a CUDA graph;
+    ``run()`` replays it for their current contents."""
+
+    def __init__(self, work: PersistWork, sigmas, opts: Optional[PersistOpts] = None, stream=None):
+        import torch
+        self.work = work
+        self.sigmas = _persist_check(work, sigmas)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.sigmas[0].device)
+        arr, keep = work._c(self.sigmas)
+        h = C.c_void_p()
+        _check(load_library().emm_persist_plan_create(len(work.tasks), arr,
+                                                      C.byref(opts) if opts is not None else None,
+                                                      C.c_void_p(work.ptr), C.c_size_t(work.nbytes),
+                                                      C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "emm_persist_plan_create")
+        self._h = h
+
+    def run_async(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.sigmas[0].device)
+        _check(load_library().emm_persist_plan_run(self._h, C.c_void_p(stream.cuda_stream)), "emm_persist_plan_run")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.emm_persist_plan_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def _stagger_ws(grid: Grid, device):

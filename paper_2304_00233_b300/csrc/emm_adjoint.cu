@@ -301,8 +301,13 @@ __global__ void __launch_bounds__(GT) k_adj_gather(const AdjParams a, const __gr
   extern __shared__ unsigned char smem_raw[];
   float *s = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + G::FLOATS);
-  const int i0 = a.org[0] + static_cast<int>(blockIdx.x) * GX, j0 = a.org[1] + static_cast<int>(blockIdx.y) * GY,
-            k0 = static_cast<int>(blockIdx.z) * GZ;
+  // the lambda_H gather walks the tiles in the reverse of the lambda_E
+  // gather's order (CTAs are dispatched in index order), so each gather
+  // starts on the tiles whose inputs the one before touched last (in L2)
+  const int bx = KIND == 0 ? static_cast<int>(blockIdx.x) : static_cast<int>(gridDim.x - 1 - blockIdx.x);
+  const int by = KIND == 0 ? static_cast<int>(blockIdx.y) : static_cast<int>(gridDim.y - 1 - blockIdx.y);
+  const int bz = KIND == 0 ? static_cast<int>(blockIdx.z) : static_cast<int>(gridDim.z - 1 - blockIdx.z);
+  const int i0 = a.org[0] + bx * GX, j0 = a.org[1] + by * GY, k0 = bz * GZ;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();

@@ -174,9 +174,12 @@ struct Prepared {
 // Validate, upload the tables, clear the state and compute dt/eps (enqueued
 // on cs); fills *out.  Host-detected errors enqueue nothing.
 // nsrc transmitters at src_pos ([nsrc][3], host; NULL: the survey's source).
+// upload_tables false: the tables are already in the workspace (a repeat of
+// an earlier prepare of the same problem); nothing reads host memory after
+// the call, so the enqueued work can be captured in a CUDA graph.
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc = 1,
-                    const double *src_pos = nullptr, bool converge = false);
+                    const double *src_pos = nullptr, bool converge = false, bool upload_tables = true);
 // Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te);

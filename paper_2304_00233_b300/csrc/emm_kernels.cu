@@ -41,6 +41,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -796,9 +797,20 @@ __device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, cons
   for (int a = 0; a < 3; ++a) *reinterpret_cast<float4 *>(f.H[a] + id) = out[a];
 }
 
+// The H half-step walks the stencil tiles in the reverse of the E
+// half-step's order (CTAs are dispatched in launch-index order): its first
+// tiles are those whose E the E launch wrote last and whose H it read last,
+// still in L2; and the next E launch starts where this one ends.
+template <bool MULTI>
+__device__ __forceinline__ Blk reversed_tile(const DevParams &p, const Blk &b) {
+  const int bx = p.tiles_x * (MULTI ? p.nsrc : 1);
+  return Blk{bx - 1 - b.x, p.tiles_y - 1 - b.y, 2 * p.rec_layers + p.tiles_z - 1 - b.z};
+}
+
 // One CTA of the H half-step.
 template <int R, bool MULTI, bool CONV>
-__device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b) {
+__device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk) {
+  const Blk b = blk.z < p.rec_layers ? blk : reversed_tile<MULTI>(p, blk);
   if (b.z < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p, b);
     const Fields f = fields_of<MULTI>(p, rs);
@@ -893,6 +905,116 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_update_H_jobs(const __grid_
   if (n >= J.nt[j]) return;
   const DevParams &p = J.p[j];
   h_block<R, false, false>(p, J.tm[j], n, job_blk(p, b - J.cta0[j]));
+}
+
+// ---------------------------------------------------------------------------
+// Persistent work list: every leapfrog step of several problems -- each a
+// grid with one transmitter or a batch of them sharing grid and
+// conductivity -- in ONE cooperative launch.  The resident CTAs walk the E
+// half-step's items (every problem's tiles and receiver CTAs; CTA b takes
+// items b, b + G, b + 2G, ...), meet at a grid barrier, walk the H
+// half-step's items, meet again, and so on for every step.  An item runs
+// the same per-CTA code as the problem's own launch would (e_block /
+// h_block), so each problem's results equal its own solve's bit for bit.
+// The barrier is an arrival counter in the workspace that only grows: a CTA
+// arrives with a release add, then waits with acquire loads for gen * G
+// arrivals, at most wait_ns of %globaltimer.  A wait that runs out sets
+// EMM_ETIMEOUT and the abort word; every CTA returns at its next barrier.
+// Proxy fences on both sides order the generic-proxy field stores of one
+// phase before the TMA (async-proxy) reads of the next.
+// ---------------------------------------------------------------------------
+constexpr int kMaxTasks = 16;
+struct PJob {
+  TmaSet tmE, tmH;  // source-field maps of the E half-step (H fields) and of the H half-step (E fields)
+  DevParams p;
+  int bx, by, nt, multi;
+};
+struct PSet {
+  PJob job[kMaxTasks];
+  int cta0[kMaxTasks + 1];  // first item of each problem, then the total
+  int njobs, nt_max;
+  unsigned *bar;            // arrivals so far (zeroed before the launch)
+  int *abort;               // nonzero once a wait ran out
+  int *status;              // the work list's status word
+  unsigned long long wait_ns;
+  int skip;                 // testing: the CTA that withholds its first arrival (-1: none)
+};
+static_assert(sizeof(PSet) <= 32764, "the work list must fit the kernel parameter space");
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *a, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// Barrier number `gen` (1, 2, ...) of the grid; false (for the whole CTA) if
+// the CTA is to stop: its wait ran out, another CTA's did, or it is the
+// test CTA that withholds its arrival.
+__device__ __forceinline__ bool grid_barrier(const PSet &S, unsigned gen) {
+  __syncthreads();
+  int go = 1;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (S.skip == static_cast<int>(blockIdx.x) && gen == 1) {
+      go = 0;  // leaves without arriving: every other CTA's wait runs out
+    } else {
+      red_release_add(S.bar, 1u);
+      const unsigned target = gen * gridDim.x;
+      const unsigned long long t0 = global_ns();
+      for (unsigned it = 0;; ++it) {
+        if (ld_acquire_u32(S.bar) >= target) break;
+        if (*reinterpret_cast<volatile const int *>(S.abort)) {
+          go = 0;
+          break;
+        }
+        if ((it & 15u) == 0 && global_ns() - t0 > S.wait_ns) {
+          atomicExch(S.status, EMM_ETIMEOUT);
+          atomicExch(S.abort, 1);
+          go = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  return __syncthreads_and(go) != 0;
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_constant__ PSet S) {
+  const int total = S.cta0[S.njobs];
+  unsigned gen = 0;
+  for (int n = 0; n < S.nt_max; ++n) {
+    for (int half = 0; half < 2; ++half) {
+      int j = 0;
+      for (int b = static_cast<int>(blockIdx.x); b < total; b += static_cast<int>(gridDim.x)) {
+        while (j + 1 < S.njobs && b >= S.cta0[j + 1]) ++j;
+        const PJob &J = S.job[j];
+        if (n < J.nt) {
+          const int l = b - S.cta0[j];
+          const Blk blk{l % J.bx, (l / J.bx) % J.by, l / (J.bx * J.by)};
+          if (half == 0) {
+            if (J.multi)
+              e_block<R, true, false, false>(J.p, J.tmE, n, blk);
+            else
+              e_block<R, false, false, false>(J.p, J.tmE, n, blk);
+          } else {
+            if (J.multi)
+              h_block<R, true, false>(J.p, J.tmH, n, blk);
+            else
+              h_block<R, false, false>(J.p, J.tmH, n, blk);
+          }
+        }
+        __syncthreads();  // the next item reuses the CTA's shared memory and mbarrier
+      }
+      if (!grid_barrier(S, ++gen)) return;
+    }
+  }
 }
 
 // Sources the stencil kernels do not inject themselves, one thread per
@@ -1398,20 +1520,21 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   size_t used = 0;
   if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
-    const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 3 <= te->ev.size();
+    const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 4 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
     e = launch_dependent(k_update_E<R, MULTI, CONV, OUT>, blocks, dim3(NT), sb, st, p, tE, n);
     if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
       e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(q, st);
-    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, q, n);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
+    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, q, n);
+    if (timed) cudaEventRecord(te->ev[used + 2], st);
     if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV>, blocks, dim3(NT), sb, st, q, tH, n);
     if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(q, st);
     if (timed) {
-      cudaEventRecord(te->ev[used + 2], st);
-      used += 3;
+      cudaEventRecord(te->ev[used + 3], st);
+      used += 4;
     }
   }
   if (te && te->loop[1]) cudaEventRecord(te->loop[1], st);
@@ -1452,7 +1575,7 @@ void normalisation(const emm_survey *s, double dt, int nsteps, double *norm) {
 
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc,
-                    const double *src_pos, bool converge) {
+                    const double *src_pos, bool converge, bool upload_tables) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
@@ -1743,7 +1866,8 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, cs);
   if (e == cudaSuccess && s->nrec > 0)
     e = cudaMemsetAsync(rec_out, 0, static_cast<size_t>(nsrc) * s->nrec * 6 * nf * 2 * sizeof(double), cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(base + tab0, blob.data(), blob.size(), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && upload_tables)
+    e = cudaMemcpyAsync(base + tab0, blob.data(), blob.size(), cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return EMM_ECUDA;
   k_prepare<<<4 * sms, 256, 0, cs>>>(sigma, reinterpret_cast<float *>(base + L.ie[0]),
                                      reinterpret_cast<float *>(base + L.ie[1]),
@@ -1949,6 +2073,143 @@ int jobs_tune(int nj, const emm_job *jobs, void *ws, size_t ws_bytes, int steps,
   return EMM_OK;
 }
 
+// ---- persistent work list (k_persist) ----
+// Workspace: a 256-byte header (status word at 0, so emm_status(ws) reads
+// the work list's status; abort word; arrival counter), then each task's
+// forward workspace, 256-byte aligned.
+constexpr size_t kPHdrStatus = 0, kPHdrAbort = 4, kPHdrBar = 8;
+
+int persist_layout(int nt, const emm_task *t, std::vector<size_t> *off, size_t *total) {
+  if (nt < 1 || nt > kMaxTasks || !t) return EMM_EINVAL;
+  size_t o = kAlign;
+  off->clear();
+  for (int j = 0; j < nt; ++j) {
+    const emm_survey *s = t[j].survey;
+    const int st = check_survey(t[j].grid, s);
+    if (st != EMM_OK) return st;
+    if (s->volume || s->airwave || s->src_kind != 0 || s->src_length > 0 || t[j].grid->rd != t[0].grid->rd ||
+        t[j].nsrc < 1 || (t[j].nsrc > 1 && !t[j].src_pos))
+      return EMM_EINVAL;
+    off->push_back(o);
+    o = align_up(o + plan(t[j].grid, s, t[j].nsrc).total);
+  }
+  *total = o;
+  return EMM_OK;
+}
+
+struct PersistRun {
+  std::vector<Prepared> P;
+  std::unique_ptr<PSet> S;
+  unsigned ctas = 0;
+  size_t smem = 0;
+  int rd = 0;
+};
+
+template <int R>
+cudaError_t persist_shape(PersistRun *run, const emm_persist_opts &o) {
+  const size_t sb = smem_bytes<R>();
+  cudaError_t e = cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, NT, sb);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
+  long long g = static_cast<long long>(per_sm) * run->P[0].sms;
+  if (o.max_ctas > 0) g = std::min<long long>(g, o.max_ctas);
+  g = std::max<long long>(1, std::min<long long>(g, run->S->cta0[run->S->njobs]));
+  run->ctas = static_cast<unsigned>(g);
+  run->smem = sb;
+  for (int j = 0; j < run->S->njobs; ++j) {
+    PJob &J = run->S->job[j];
+    if (!make_tiles<R>(&J.tmE, J.p.H, J.p) || !make_tiles<R>(&J.tmH, J.p.E, J.p)) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+// Validate, prepare every task (enqueued on cs) and fill the launch
+// parameters; steps_cap < 0: each task's own step count.
+int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, void *ws, size_t ws_bytes,
+                    cudaStream_t cs, bool upload, int steps_cap, PersistRun *run) {
+  std::vector<size_t> off;
+  size_t total = 0;
+  int st = persist_layout(nt, t, &off, &total);
+  if (st != EMM_OK) return st;
+  emm_persist_opts o{0, 0, 0.0, -1};
+  if (opts) o = *opts;
+  if (o.ctas_per_sm < 0 || o.max_ctas < 0) return EMM_EINVAL;
+  if (!ws || ws_bytes < total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
+  for (int j = 0; j < nt; ++j)
+    if (!t[j].sigma || (t[j].survey->nrec > 0 && !t[j].rec_out)) return EMM_EINVAL;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  if (cudaMemsetAsync(ws, 0, kAlign, cs) != cudaSuccess) return EMM_ECUDA;
+  run->P.assign(nt, Prepared{});
+  run->S.reset(new (std::nothrow) PSet{});
+  if (!run->S) return EMM_ENOMEM;
+  PSet &S = *run->S;
+  int cta = 0, nmax = 0;
+  for (int j = 0; j < nt; ++j) {
+    const size_t end = j + 1 < nt ? off[j + 1] : total;
+    st = prepare_forward(t[j].grid, t[j].survey, t[j].sigma, base + off[j], end - off[j], t[j].rec_out, nullptr, cs,
+                         &run->P[j], t[j].nsrc, t[j].src_pos, false, upload);
+    if (st != EMM_OK) return st;
+    const Prepared &P = run->P[j];
+    PJob &J = S.job[j];
+    J.p = P.p;
+    J.bx = static_cast<int>(P.blocks.x);
+    J.by = static_cast<int>(P.blocks.y);
+    J.nt = steps_cap >= 0 ? std::min(steps_cap, t[j].survey->nt) : t[j].survey->nt;
+    J.multi = P.p.nsrc > 1 ? 1 : 0;
+    S.cta0[j] = cta;
+    cta += static_cast<int>(P.blocks.x * P.blocks.y * P.blocks.z);
+    nmax = std::max(nmax, J.nt);
+  }
+  S.cta0[nt] = cta;
+  S.njobs = nt;
+  S.nt_max = nmax;
+  S.status = reinterpret_cast<int *>(base + kPHdrStatus);
+  S.abort = reinterpret_cast<int *>(base + kPHdrAbort);
+  S.bar = reinterpret_cast<unsigned *>(base + kPHdrBar);
+  S.wait_ns = static_cast<unsigned long long>((o.wait_s > 0 ? o.wait_s : 1.0) * 1e9);
+  S.skip = o.skip_arrival;
+  run->rd = run->P[0].rd;
+  cudaError_t e;
+  switch (run->rd) {
+    case 1: e = persist_shape<1>(run, o); break;
+    case 2: e = persist_shape<2>(run, o); break;
+    case 3: e = persist_shape<3>(run, o); break;
+    default: e = persist_shape<4>(run, o); break;
+  }
+  return e == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+// One cooperative launch of the prepared work list: every CTA resident.
+cudaError_t persist_launch(const PersistRun &run, cudaStream_t cs) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(run.ctas);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = run.smem;
+  cfg.stream = cs;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (run.rd) {
+    case 1: return cudaLaunchKernelEx(&cfg, k_persist<1>, *run.S);
+    case 2: return cudaLaunchKernelEx(&cfg, k_persist<2>, *run.S);
+    case 3: return cudaLaunchKernelEx(&cfg, k_persist<3>, *run.S);
+    default: return cudaLaunchKernelEx(&cfg, k_persist<4>, *run.S);
+  }
+}
+
+int persist_finalize(const PersistRun &run, int nt, const emm_task *t, cudaStream_t cs) {
+  for (int j = 0; j < nt; ++j) {
+    const int st = finalize_forward(run.P[j], t[j].survey, t[j].rec_out, nullptr, cs);
+    if (st != EMM_OK) return st;
+  }
+  return EMM_OK;
+}
+
 int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, double *vol_out, cudaStream_t cs) {
   const int nf = s->nfreq;
   const double *dnorm = reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(P.p.status) -
@@ -1974,22 +2235,47 @@ int forward_impl(const emm_grid *g, const emm_survey *s, const float *sigma, voi
   return finalize_forward(P, s, rec_out, vol_out, cs);
 }
 
-// Device address of emm_static_scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// cuCtxGetCurrent, fetched once from the driver through the runtime.
+static PFN_cuCtxGetCurrent_v4000 context_query() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+  });
+  return fn;
+}
+
+// Device address of emm_static_scratch in the current context, looked up
+// with that context current and cached per context.  A device reset (or any
+// context teardown) loads the module again into a new context, where the
+// array may sit at another address: that context gets a lookup of its own.
 static int static_scratch(void **ptr) {
-  constexpr int kMaxDevices = 64;
+  constexpr int kSlots = 64;
   static std::mutex mu;
-  static void *addr[kMaxDevices] = {};
+  static CUcontext ctx[kSlots] = {};
+  static void *addr[kSlots] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return EMM_ECUDA;
+  PFN_cuCtxGetCurrent_v4000 get = context_query();
+  CUcontext cur = nullptr;
+  if (!get || get(&cur) != CUDA_SUCCESS) return EMM_ECUDA;
   std::lock_guard<std::mutex> lock(mu);
-  if (dev < kMaxDevices && addr[dev]) {
-    *ptr = addr[dev];
+  const int slot = dev % kSlots;
+  if (cur && ctx[slot] == cur && addr[slot]) {
+    *ptr = addr[slot];
     return EMM_OK;
   }
   void *p = nullptr;
   if (cudaGetSymbolAddress(&p, emm_static_scratch) != cudaSuccess || !p) return EMM_ECUDA;
-  if (dev < kMaxDevices) addr[dev] = p;
+  // a thread with no current context gets the device's primary context from
+  // the lookup above
+  if (!cur && (get(&cur) != CUDA_SUCCESS || !cur)) return EMM_ECUDA;
+  ctx[slot] = cur;
+  addr[slot] = p;
   *ptr = p;
   return EMM_OK;
 }
@@ -2020,7 +2306,7 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   if (st != EMM_OK) return st;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   const int nsamp = s->nt > 0 ? (s->nt + timing->every - 1) / timing->every : 0;
-  std::vector<cudaEvent_t> all(3 * static_cast<size_t>(nsamp) + 4, nullptr);
+  std::vector<cudaEvent_t> all(4 * static_cast<size_t>(nsamp) + 4, nullptr);
   for (auto &e : all)
     if (cudaEventCreate(&e) != cudaSuccess) {
       for (auto &d : all)
@@ -2029,7 +2315,7 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
     }
   StepEvents te;
   te.every = timing->every;
-  te.ev.assign(all.begin(), all.begin() + 3 * static_cast<size_t>(nsamp));
+  te.ev.assign(all.begin(), all.begin() + 4 * static_cast<size_t>(nsamp));
   cudaEvent_t t0 = all[all.size() - 2], t1 = all[all.size() - 1];
   te.loop[0] = all[all.size() - 4];
   te.loop[1] = all[all.size() - 3];
@@ -2037,16 +2323,19 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   st = forward_impl(g, s, sigma, ws, ws_bytes, rec_out, vol_out, stream, &te);
   cudaEventRecord(t1, cs);
   if (cudaStreamSynchronize(cs) != cudaSuccess && st == EMM_OK) st = EMM_ECUDA;
-  double se = 0, sh = 0;
+  double se = 0, sv = 0, sh = 0;
   float ms = 0.f;
   for (int q = 0; q < nsamp && st == EMM_OK; ++q) {
-    cudaEventElapsedTime(&ms, te.ev[3 * q], te.ev[3 * q + 1]);
+    cudaEventElapsedTime(&ms, te.ev[4 * q], te.ev[4 * q + 1]);
     se += ms;
-    cudaEventElapsedTime(&ms, te.ev[3 * q + 1], te.ev[3 * q + 2]);
+    cudaEventElapsedTime(&ms, te.ev[4 * q + 1], te.ev[4 * q + 2]);
+    sv += ms;
+    cudaEventElapsedTime(&ms, te.ev[4 * q + 2], te.ev[4 * q + 3]);
     sh += ms;
   }
   timing->samples = nsamp;
   timing->e_ms = nsamp ? se / nsamp : 0.0;
+  timing->v_ms = (nsamp && s->volume) ? sv / nsamp : 0.0;
   timing->h_ms = nsamp ? sh / nsamp : 0.0;
   ms = 0.f;
   if (st == EMM_OK) cudaEventElapsedTime(&ms, t0, t1);
@@ -2099,7 +2388,13 @@ int emm_forward_converge(const emm_grid *g, const emm_survey *s, const float *si
   };
   // One chunk of look-ahead: chunk q+1 is enqueued before the host waits
   // (bounded) for the verdict of chunk q; launches after a stop return at once.
-  constexpr double kPollSeconds = 600.0;
+  // bound of one wait for a verdict; EMM_POLL_TIMEOUT_S (seconds) lowers it
+  // for tests of the timeout path
+  double poll_s = 600.0;
+  if (const char *env = std::getenv("EMM_POLL_TIMEOUT_S")) {
+    const double v = std::atof(env);
+    if (v > 0) poll_s = v;
+  }
   size_t next = 0;
   bool stopped = false;
   for (size_t q = 0; q < chunks.size() && st == EMM_OK && !stopped; ++q) {
@@ -2108,7 +2403,7 @@ int emm_forward_converge(const emm_grid *g, const emm_survey *s, const float *si
     if (st != EMM_OK || chunks[q].check < 0) continue;
     const auto t0 = std::chrono::steady_clock::now();
     while (vhw[0] < chunks[q].check) {
-      if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kPollSeconds) {
+      if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > poll_s) {
         st = EMM_ETIMEOUT;
         break;
       }
@@ -2149,6 +2444,140 @@ int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, siz
 int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
                   double *ms, int *best) {
   return emm::jobs_tune(njobs, jobs, ws, ws_bytes, steps, reinterpret_cast<cudaStream_t>(stream), ms, best);
+}
+
+int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes, size_t *offsets) {
+  if (!bytes) return EMM_EINVAL;
+  std::vector<size_t> off;
+  const int st = emm::persist_layout(ntasks, tasks, &off, bytes);
+  if (st != EMM_OK) return st;
+  if (offsets)
+    for (int j = 0; j < ntasks; ++j) offsets[j] = off[j];
+  return EMM_OK;
+}
+
+int emm_forward_persistent(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
+                           size_t ws_bytes, emm_stream stream) {
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  emm::PersistRun run;
+  int st = emm::persist_prepare(ntasks, tasks, opts, ws, ws_bytes, cs, true, -1, &run);
+  if (st != EMM_OK) return st;
+  if (emm::persist_launch(run, cs) != cudaSuccess) return EMM_ECUDA;
+  return emm::persist_finalize(run, ntasks, tasks, cs);
+}
+
+int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_bytes, int steps, emm_stream stream,
+                     emm_persist_opts *best, double *ms, int *ncand) {
+  if (steps < 1 || !best || !ms || !ncand) return EMM_EINVAL;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  emm::PersistRun run;
+  // the candidates: 1 .. the occupancy limit of resident CTAs per SM
+  int st = emm::persist_prepare(ntasks, tasks, nullptr, ws, ws_bytes, cs, true, steps, &run);
+  if (st != EMM_OK) return st;
+  const int top = static_cast<int>((run.ctas + run.P[0].sms - 1) / run.P[0].sms);
+  const int nc = std::min(top, *ncand);
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return EMM_ECUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return EMM_ECUDA;
+  }
+  int bi = -1;
+  for (int k = 0; k < nc && st == EMM_OK; ++k) {
+    const emm_persist_opts o{k + 1, 0, 0.0, -1};
+    for (int rep = 0; rep < 2 && st == EMM_OK; ++rep) {  // a warm-up run, then the timed one
+      st = emm::persist_prepare(ntasks, tasks, &o, ws, ws_bytes, cs, false, steps, &run);
+      if (st == EMM_OK && rep == 1 && cudaEventRecord(a, cs) != cudaSuccess) st = EMM_ECUDA;
+      if (st == EMM_OK && emm::persist_launch(run, cs) != cudaSuccess) st = EMM_ECUDA;
+      if (st == EMM_OK && rep == 1 && cudaEventRecord(b, cs) != cudaSuccess) st = EMM_ECUDA;
+    }
+    float t = 0.f;
+    if (st == EMM_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess))
+      st = EMM_ECUDA;
+    ms[k] = t;
+    if (st == EMM_OK && (bi < 0 || t < ms[bi])) bi = k;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != EMM_OK) return st;
+  *ncand = nc;
+  *best = emm_persist_opts{bi + 1, 0, 0.0, -1};
+  return EMM_OK;
+}
+
+}  // extern "C"
+
+struct emm_persist_plan {
+  std::vector<emm_task> tasks;
+  std::vector<emm_survey> surveys;
+  std::vector<std::vector<double>> recs, freqs, pos;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int emm_persist_plan_create(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
+                            size_t ws_bytes, emm_stream stream, emm_persist_plan **out) {
+  if (!out) return EMM_EINVAL;
+  *out = nullptr;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  // a first set-up on the caller's stream uploads the tables the graph's
+  // runs then find in the workspace
+  emm::PersistRun run;
+  int st = emm::persist_prepare(ntasks, tasks, opts, ws, ws_bytes, cs, true, -1, &run);
+  if (st != EMM_OK) return st;
+  std::unique_ptr<emm_persist_plan> pl(new (std::nothrow) emm_persist_plan);
+  if (!pl) return EMM_ENOMEM;
+  // the plan's own copies of what the tasks point to on the host
+  pl->tasks.assign(tasks, tasks + ntasks);
+  pl->surveys.resize(ntasks);
+  pl->recs.resize(ntasks);
+  pl->freqs.resize(ntasks);
+  pl->pos.resize(ntasks);
+  for (int j = 0; j < ntasks; ++j) {
+    const emm_survey *s = tasks[j].survey;
+    pl->surveys[j] = *s;
+    pl->recs[j].assign(s->rec, s->rec + (s->nrec > 0 ? 3 * static_cast<size_t>(s->nrec) : 0));
+    pl->freqs[j].assign(s->freqs, s->freqs + s->nfreq);
+    pl->surveys[j].rec = pl->recs[j].empty() ? nullptr : pl->recs[j].data();
+    pl->surveys[j].freqs = pl->freqs[j].data();
+    pl->tasks[j].survey = &pl->surveys[j];
+    if (tasks[j].src_pos) {
+      pl->pos[j].assign(tasks[j].src_pos, tasks[j].src_pos + 3 * static_cast<size_t>(tasks[j].nsrc));
+      pl->tasks[j].src_pos = pl->pos[j].data();
+    }
+  }
+  // capture on a stream of the plan's own: the set-up without the table
+  // upload, the cooperative launch and the normalisation
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    emm::PersistRun r2;
+    st = emm::persist_prepare(ntasks, pl->tasks.data(), opts, ws, ws_bytes, cap, false, -1, &r2);
+    if (st == EMM_OK && emm::persist_launch(r2, cap) != cudaSuccess) st = EMM_ECUDA;
+    if (st == EMM_OK) st = emm::persist_finalize(r2, ntasks, pl->tasks.data(), cap);
+    e = cudaStreamEndCapture(cap, &graph);
+  }
+  if (e == cudaSuccess && st == EMM_OK) e = cudaGraphInstantiate(&pl->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  if (st != EMM_OK) return st;
+  if (e != cudaSuccess) return EMM_ECUDA;
+  *out = pl.release();
+  return EMM_OK;
+}
+
+int emm_persist_plan_run(emm_persist_plan *pl, emm_stream stream) {
+  if (!pl || !pl->exec) return EMM_EINVAL;
+  return cudaGraphLaunch(pl->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+void emm_persist_plan_destroy(emm_persist_plan *pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  delete pl;
 }
 
 int emm_batch_workspace_size(const emm_grid *g, const emm_survey *s, int nsrc, size_t *bytes) {

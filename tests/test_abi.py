@@ -109,6 +109,54 @@ def test_work_list_layout_and_errors():
     assert lib.emm_forward_jobs(2, jobs, 3, None, 0, None) == emm.EMM_EINVAL
 
 
+def test_persistent_work_list_layout_and_errors():
+    from paper_2304_00233_b300 import workloads as W
+    C = emm.C
+    wls = [W.small_case(n=(20, 18, 16), rd=2, nt=10, volume=False),
+           W.small_case(n=(26, 22, 19), rd=2, nt=12, volume=False)]
+    probs = [(emm.grid_for(w), emm.survey_for(w)) for w in wls]
+    pos = np.array([probs[1][1].src, np.array(probs[1][1].src) + [30.0, 0.0, 0.0]])
+    keep = []
+
+    def tasks(items):
+        arr = (emm._Task * len(items))()
+        for j, (g, s, p) in enumerate(items):
+            sc, k = s._c()
+            keep.extend([sc, k, p])
+            arr[j].grid, arr[j].survey = g.handle, C.pointer(sc)
+            arr[j].nsrc = 1 if p is None else len(p)
+            arr[j].src_pos = emm._dp(p) if p is not None else None
+        return arr
+
+    lib = emm.load_library()
+    good = tasks([(probs[0][0], probs[0][1], None), (probs[1][0], probs[1][1], pos)])
+    n = C.c_size_t(0)
+    offs = (C.c_size_t * 2)()
+    assert lib.emm_persist_workspace_size(2, good, C.byref(n), offs) == emm.EMM_OK
+    # a 256-byte header, then each task's forward workspace (the second a batch of two)
+    assert offs[0] == 256 and offs[1] >= 256 + emm.workspace_size(*probs[0]) and offs[1] % 256 == 0
+    assert n.value >= offs[1] + emm.batch_workspace_size(probs[1][0], probs[1][1], 2)
+    assert lib.emm_persist_workspace_size(0, good, C.byref(n), None) == emm.EMM_EINVAL
+    assert lib.emm_persist_workspace_size(17, good, C.byref(n), None) == emm.EMM_EINVAL
+    # a batch without positions, a volume DTFT, or differing FD orders are refused
+    assert lib.emm_persist_workspace_size(
+        1, tasks([(probs[1][0], probs[1][1], None)]), C.byref(n), None) == emm.EMM_OK
+    nopos = tasks([(probs[1][0], probs[1][1], None)])
+    nopos[0].nsrc = 2
+    assert lib.emm_persist_workspace_size(1, nopos, C.byref(n), None) == emm.EMM_EINVAL
+    wv = W.small_case(n=(20, 18, 16), rd=2, nt=10, volume=True)
+    assert lib.emm_persist_workspace_size(
+        1, tasks([(emm.grid_for(wv), emm.survey_for(wv), None)]), C.byref(n), None) == emm.EMM_EINVAL
+    w4 = W.small_case(n=(24, 22, 20), rd=4, nt=10, volume=False)
+    mixed = tasks([(probs[0][0], probs[0][1], None), (emm.grid_for(w4), emm.survey_for(w4), None)])
+    assert lib.emm_persist_workspace_size(2, mixed, C.byref(n), None) == emm.EMM_EINVAL
+    # no workspace, or negative options: refused before anything is enqueued
+    assert lib.emm_forward_persistent(2, good, None, None, 0, None) == emm.EMM_EWORKSPACE
+    bad = emm.PersistOpts(ctas_per_sm=-1)
+    assert lib.emm_forward_persistent(2, good, C.byref(bad), None, 0, None) == emm.EMM_EINVAL
+    assert lib.emm_persist_plan_run(None, None) == emm.EMM_EINVAL
+
+
 def test_new_entry_points_refuse_bad_arguments_on_the_host():
     C = emm.C
     lib = emm.load_library()

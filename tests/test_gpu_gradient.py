@@ -24,6 +24,15 @@ CASES = [dict(rd=1, n=(22, 20, 18)), dict(rd=2, n=(23, 19, 17)), dict(rd=3, n=(2
          dict(rd=4, n=(28, 26, 24))]
 
 
+def _same_time_step(wl, grid, survey):
+    """The oracle takes its own dt (Sec. 3.2, from the same sigma_min); the
+    library's dt must agree with it, checked apart from the gradient."""
+    ref = oracle.forward(wl.x, wl.y, wl.z, wl.sigma, rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0,
+                         nt=0, fmax=wl.fmax, sigma_min=survey.sigma_min)["dt"]
+    dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
+    assert dt == pytest.approx(ref, rel=1e-13)
+
+
 def _problem(rd, n, nt=140, seed=21):
     wl = W.small_case(n=n, rd=rd, seed=seed, nt=nt, volume=False, nb=5, nfreq=2)
     rng = np.random.default_rng(seed + 1)
@@ -38,9 +47,9 @@ def test_gradient_against_oracle(case):
     sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
     grad, G = emm.vjp(grid, survey, sigma, torch.from_numpy(v).cuda(), ckpt_every=17)
     torch.cuda.synchronize()
-    dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
+    _same_time_step(wl, grid, survey)
     ref = oracle.vjp(wl.x, wl.y, wl.z, wl.sigma, v, rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0,
-                     nt=wl.nt, fmax=wl.fmax, sigma_min=survey.sigma_min, dt=dt, src=wl.src, az=wl.src_az,
+                     nt=wl.nt, fmax=wl.fmax, sigma_min=survey.sigma_min, src=wl.src, az=wl.src_az,
                      dip=wl.src_dip, moment=wl.moment, rec=wl.rec, freqs=wl.freqs, ckpt_every=20)
     g = grad.cpu().numpy()
     err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
@@ -77,9 +86,9 @@ def test_gradient_interior_blocks_against_oracle():
     assert any(i0 >= lo and i0 + 31 <= np0 - 2 - lo for i0 in range(0, np0, 32))
     sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
     grad, _ = emm.vjp(grid, survey, sigma, torch.from_numpy(v).cuda(), ckpt_every=23)
-    dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
+    _same_time_step(wl, grid, survey)
     ref = oracle.vjp(wl.x, wl.y, wl.z, wl.sigma, v, rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0,
-                     nt=wl.nt, fmax=wl.fmax, sigma_min=survey.sigma_min, dt=dt, src=wl.src, az=wl.src_az,
+                     nt=wl.nt, fmax=wl.fmax, sigma_min=survey.sigma_min, src=wl.src, az=wl.src_az,
                      dip=wl.src_dip, moment=wl.moment, rec=wl.rec, freqs=wl.freqs, ckpt_every=30)
     g = grad.cpu().numpy()
     err = np.linalg.norm(g - ref) / np.linalg.norm(ref)

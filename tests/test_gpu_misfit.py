@@ -69,10 +69,16 @@ def test_stagger_adjoint_against_oracle_and_accumulates():
 
 
 def _oracle_kw(wl, survey, grid):
+    """Oracle arguments of a survey.  The oracle takes its own dt from
+    sigma_min (Sec. 3.2); the library's dt is checked against it here, apart
+    from the comparisons of the results."""
+    kw = dict(rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0, nt=survey.nt, fmax=wl.fmax,
+              sigma_min=survey.sigma_min, src=tuple(survey.src), az=wl.src_az, dip=wl.src_dip,
+              moment=wl.moment, rec=wl.rec, freqs=wl.freqs)
+    odt = oracle.forward(wl.x, wl.y, wl.z, wl.sigma, **{**kw, "nt": 0, "rec": None})["dt"]
     dt, _, _ = grid.time_step(survey.sigma_min, survey.omega0)
-    return dict(rd=wl.rd, nb=wl.nb, ne=wl.ne, omega0=wl.omega0, nt=survey.nt, fmax=wl.fmax,
-                sigma_min=survey.sigma_min, dt=dt, src=tuple(survey.src), az=wl.src_az, dip=wl.src_dip,
-                moment=wl.moment, rec=wl.rec, freqs=wl.freqs)
+    assert dt == pytest.approx(odt, rel=1e-13)
+    return kw
 
 
 def _rel(a, b):

@@ -65,7 +65,8 @@ def test_time_step_and_cpml_match_oracle(wl):
     assert eta == pytest.approx(probe["eta"], rel=1e-13)
     assert vmax == pytest.approx(probe["vmax"], rel=1e-14)
     for a, x in enumerate((wl.x, wl.y, wl.z)):
-        o = oracle.axis_tables(x, wl.rd, wl.nb, wl.ne, vmax=vmax, fmax=wl.fmax, dt=dt)
+        # each side with its own vmax and dt (equal to 1e-13 above)
+        o = oracle.axis_tables(x, wl.rd, wl.nb, wl.ne, vmax=probe["vmax"], fmax=wl.fmax, dt=probe["dt"])
         ab = g.cpml_tables(a, vmax, wl.fmax, dt)
         np.testing.assert_allclose(ab, o["pml"], rtol=1e-12, atol=1e-15)
 

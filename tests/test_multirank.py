@@ -1,6 +1,8 @@
 """The N > 1 path of the benchmark on CPU: two gloo ranks, each solving its
-own transmitter (weak scaling, no collective in the data path), joined only
-by the max-over-ranks timing.  Runs without a GPU."""
+own transmitter (weak scaling, no collective during the solve), joined by
+the max-over-ranks timing, the gather of the receiver arrays on rank 0 and
+the sum of the per-transmitter gradients of a sharded survey.  Runs without
+a GPU."""
 import os
 import socket
 
@@ -33,7 +35,17 @@ def _rank_main(rank, world, port, out):
         start, w = grid.locate(0, src)
         t = 1.0 + 0.5 * rank                      # this rank's "duration"
         slow = bench.max_over_ranks(t, dist, "cpu")
-        out[rank] = (float(src[0]), slow, [int(v) for v in start])
+        # the end of a survey: receiver arrays gathered on rank 0, the
+        # per-transmitter gradient volumes of each rank's share summed
+        G = torch.full((3, 6, 2), complex(rank + 1, -rank), dtype=torch.complex128)
+        got = bench.gather_to_rank0(G, dist, world)
+        mine = bench.shard(list(range(8)), rank, world)
+        g = torch.zeros(4, 5, dtype=torch.float64)
+        for k in mine:                           # one "gradient" per transmitter
+            g += float(k + 1)
+        bench.sum_over_ranks(g, dist)
+        out[rank] = (float(src[0]), slow, [int(v) for v in start],
+                     None if got is None else got.numpy(), mine, g.numpy())
     finally:
         dist.destroy_process_group()
 
@@ -55,12 +67,23 @@ def test_two_gloo_ranks_shard_sources_and_take_the_max_time():
     assert x1 - x0 == pytest.approx(bench.TOW_SPACING)          # distinct transmitters
     assert res[0][1] == res[1][1] == pytest.approx(1.5)          # both see the slowest rank
     assert res[0][2] != res[1][2]                                # different stencils
+    # rank 0 holds every rank's receiver arrays, in rank order
+    assert res[1][3] is None
+    assert res[0][3].shape == (2, 3, 6, 2)
+    assert np.all(res[0][3][0] == 1.0) and np.all(res[0][3][1] == 2.0 - 1.0j)
+    # the transmitters are shared out without overlap; the summed gradient is
+    # that of all eight on both ranks
+    assert sorted(res[0][4] + res[1][4]) == list(range(8)) and not set(res[0][4]) & set(res[1][4])
+    assert np.all(res[0][5] == sum(range(1, 9))) and np.all(res[1][5] == res[0][5])
 
 
 def test_aggregate_rate_counts_every_rank():
     one = bench.aggregate_rate(1, 3_411_720, 6934, 5, 3.0)
     assert bench.aggregate_rate(8, 3_411_720, 6934, 5, 3.0) == pytest.approx(8 * one)
     assert bench.max_over_ranks(2.5) == 2.5
+    t = torch.ones(3)
+    assert bench.sum_over_ranks(t) is t and bench.gather_to_rank0(t).shape == (1, 3)
+    assert bench.shard(list(range(8)), 0, 1) == list(range(8))
 
 
 def test_eight_rank_sources_stay_on_the_grid():

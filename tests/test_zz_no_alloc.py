@@ -4,7 +4,8 @@ against emm_forward, through the C-ABI.
 Two calls in a row on different problems (the second finds the first one's
 contents in the shared static scratch) must each match emm_forward on the same
 inputs within the parity bound; a problem beyond the scratch size is refused
-with EMM_EWORKSPACE before anything is enqueued.  This file is collected last
+with EMM_EWORKSPACE before anything is enqueued; a second call leaves the
+device's free memory unchanged.  This file is collected last
 so that it runs both alone in a fresh process and after every other test."""
 import numpy as np
 import pytest
@@ -60,6 +61,20 @@ def test_static_scratch_matches_workspace_entry_point_twice():
         if survey.volume:
             vE, vH = compare_G(_as_complex(vol), vol_ref.cpu().numpy())
             assert vE < REL_L2_TOL and vH < REL_L2_TOL, (case, vE, vH)
+
+
+def test_second_static_call_changes_no_device_memory():
+    # the first call may load the library's device code (and with it the
+    # static array); the second must leave the device's free memory as it was
+    grid, survey, sigma = _problem(rd=2, n=(31, 27, 25), volume=True, seed=13)
+    rec, vol = _outputs(grid, survey)
+    assert emm.forward_static(grid, survey, sigma, rec, vol) == EMM_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert emm.forward_static(grid, survey, sigma, rec, vol) == EMM_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_static_scratch_refuses_oversized_problem():
