@@ -585,6 +585,70 @@ def jobs_line(emm, torch, stream, job_max):
                     "problem in turn, device-resident inputs"}
 
 
+def survey_line(emm, torch, stream, job_max, world, rank, nsrc=32):
+    """The batched survey: `nsrc` transmitters along the tow line over the
+    marine model (x = -3100 + 200 k, 50 m above the seabed) plus the eight
+    uneven grids (each with its own transmitter), all advanced in ONE
+    persistent cooperative launch (emm_forward_persistent), its resident-CTA
+    count picked by emm_persist_tune, the whole solve replayed from a CUDA
+    graph (emm_persist_plan_run); against the same problems one at a time
+    (emm_forward of each transmitter and grid in turn)."""
+    wl = W.marine_1d()
+    grid = emm.grid_for(wl)
+    nt = emm.steps_for(wl, grid)
+    survey = emm.survey_for(wl, nt=nt)
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    pos = np.array([[-3100.0 + TOW_SPACING * (k + nsrc * rank), 0.0, 950.0] for k in range(nsrc)])
+    tasks, sigmas, cells = [(grid, survey, pos)], [sigma], grid.cells * nt * nsrc
+    for u in W.uneven_jobs():
+        gu = emm.grid_for(u)
+        ntu = emm.steps_for(u, gu)
+        tasks.append((gu, emm.survey_for(u, nt=ntu), None))
+        sigmas.append(torch.from_numpy(u.sigma.astype(np.float32)).cuda())
+        cells += gu.cells * ntu
+    work = emm.PersistWork(tasks)
+    best, tune_ms = emm.persist_tune(work, sigmas, steps=40)
+    plan = emm.PersistPlan(work, sigmas, opts=best, stream=stream)
+    plan.run_async(stream)
+    torch.cuda.synchronize()
+    sec = job_max(timed_events(stream, lambda: plan.run_async(stream)))
+    top, each = work.status(stream)
+    assert top == emm.EMM_OK and all(v == emm.EMM_OK for v in each)
+    G_plan = [g.clone() for g in work.G()]
+    plan.close()
+    # one at a time: each transmitter of the tow line, then each grid
+    works = [emm.Workspace(g, s) for g, s, _ in tasks]
+    tow = [dataclasses_replace(survey, src=tuple(float(v) for v in p)) for p in pos]
+
+    def one_at_a_time():
+        for s_k in tow:
+            emm.forward_async(grid, s_k, sigma, works[0])
+        for (g, s, _), sg, w in zip(tasks[1:], sigmas[1:], works[1:]):
+            emm.forward_async(g, s, sg, w)
+
+    one_at_a_time()
+    torch.cuda.synchronize()
+    sec1 = job_max(timed_events(stream, one_at_a_time))
+    # the last transmitter and every grid: bitwise equal to their own solves
+    same = torch.equal(torch.view_as_complex(works[0].rec)[: survey.nrec], G_plan[0][-1]) and all(
+        torch.equal(torch.view_as_complex(w.rec)[: s.nrec], G[0]) for (_, s, _), w, G in zip(tasks[1:], works[1:],
+                                                                                             G_plan[1:]))
+    value = world * cells / sec / 1e9
+    return {"problems": f"{nsrc} tow-line transmitters on {wl.name} + {len(tasks) - 1} uneven grids",
+            "cell_steps": cells, "value": value, "unit": "Gcell-steps/s", "ms": 1e3 * sec,
+            "one_at_a_time": world * cells / sec1 / 1e9, "ms_one_at_a_time": 1e3 * sec1,
+            "speedup": sec1 / sec, "ctas_per_sm": best.ctas_per_sm,
+            "tune_ms_40_steps": {str(k): v for k, v in tune_ms.items()}, "bitwise_equal": bool(same),
+            "what": "emm_persist_plan_run: the whole survey (set-up, one persistent cooperative launch with "
+                    "bounded grid barriers between half-steps, normalisation) replayed from a CUDA graph, "
+                    "against emm_forward of every transmitter and grid in turn; device-resident inputs"}
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+    return dataclasses.replace(obj, **kw)
+
+
 def batch_line(emm, torch, stream, job_max, world, rank, grid, survey, sigma, single_value, nsrc):
     """Batched survey on the marine model: transmitters every 200 m along
     the tow line (x = -3100 + 200 k, 50 m above the seabed) advanced
@@ -685,6 +749,8 @@ def main():
                     help="add the CUDA-graph line (the marine solve replayed from a captured time loop)")
     ap.add_argument("--no-jobs", action="store_true",
                     help="skip the uneven-grid work-list line (eight grids, one launch per half-step)")
+    ap.add_argument("--no-survey", action="store_true",
+                    help="skip the batched-survey line (32 transmitters + 8 uneven grids in one persistent launch)")
     ap.add_argument("--no-gradient-survey", action="store_true",
                     help="skip the 8-transmitter misfit-gradient line on the 192 x 192 x 128 grid")
     ap.add_argument("--no-airwave", action="store_true",
@@ -837,6 +903,8 @@ def main():
         del mwork, m
     if extras and not args.no_jobs:
         line["jobs"] = jobs_line(emm, torch, stream, job_max)
+    if extras and not args.no_survey:
+        line["survey"] = survey_line(emm, torch, stream, job_max, world, rank)
     if extras and not args.no_gradient_survey:
         line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max, dist, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -117,6 +117,7 @@ struct DevParams {
   float4 *vacc;                // [6][nf][n3][n2][n1] compensated FP32 (re_hi, re_lo, im_hi, im_lo)
   const float *fE32, *fH32;    // [nt][nf][2] FP32 copies of the factors for the volume
   int *status;
+  int *abort;                  // persistent runs: set when a bounded wait ran out (else null)
 };
 
 // ---- host-side pieces shared by the forward and the gradient entry points ----

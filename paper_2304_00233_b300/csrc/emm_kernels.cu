@@ -213,13 +213,18 @@ __device__ __forceinline__ Fields fields_of(const DevParams &p, int src) {
   return f;
 }
 
-// Thread 0: initialise the CTA's mbarrier and issue the three copies.  The
-// z-halo boxes start `lead` planes from k0 (-R for D-, -R+1 for D+).
+// Thread 0: initialise the CTA's mbarrier (unless a CTA that runs several
+// tiles initialised it once already: `phase` > 0 counts the tiles before
+// this one) and issue the three copies.  The z-halo boxes start `lead`
+// planes from k0 (-R for D-, -R+1 for D+).
 template <int R>
-__device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t *bar, const Origin &o, int lead) {
+__device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t *bar, const Origin &o, int lead,
+                                            unsigned phase) {
   using T = Tiles<R>;
-  mbar_init(bar, 1);
-  fence_barrier_init();
+  if (phase == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
   mbar_expect_tx(bar, static_cast<uint32_t>(T::BYTES));
   tma_load_4d(s, &tm.m[0], bar, o.i0, o.j0 - R, o.k0 + lead, o.src);
   tma_load_4d(s + T::ZF, &tm.m[1], bar, o.i0 - XH, o.j0, o.k0 + lead, o.src);
@@ -227,16 +232,18 @@ __device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t
 }
 
 // Wait for the copies: thread 0 (which initialised the barrier and issued
-// them) waits on the mbarrier, bounded; the other threads wait at the CTA
-// barrier that follows, which orders the landed tiles before their reads.
-// False, for the whole CTA, if the wait ran out (thread 0 has then set the
-// status word and drained the copies, again bounded).
-__device__ __forceinline__ bool tiles_ready(const DevParams &p, uint64_t *bar) {
+// them) waits on the mbarrier's phase of this tile (parity `phase` & 1),
+// bounded; the other threads wait at the CTA barrier that follows, which
+// orders the landed tiles before their reads.  False, for the whole CTA, if
+// the wait ran out (thread 0 has then set the status word, and the abort
+// word of a persistent run, and drained the copies, again bounded).
+__device__ __forceinline__ bool tiles_ready(const DevParams &p, uint64_t *bar, unsigned phase) {
   int late = 0;
-  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0)) {
+  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, phase & 1u)) {
     late = 1;
     atomicExch(p.status, EMM_ETIMEOUT);
-    mbar_wait_bounded(bar, 0);
+    if (p.abort) atomicExch(p.abort, 1);
+    mbar_wait_bounded(bar, phase & 1u);
   }
   return !__syncthreads_or(late);
 }
@@ -593,8 +600,10 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
 
 // One CTA of the E half-step.  CONV: a convergence run (corner DTFT).
 // OUT: E^{n+1} goes to p.Eout (E^n stays where it is).
+// phase: tiles this CTA ran before this one (0 for a CTA of a launch of its own).
 template <int R, bool MULTI, bool CONV, bool OUT>
-__device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b) {
+__device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b,
+                                        unsigned phase = 0) {
   if (b.z < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p, b);
     const Fields f = fields_of<MULTI>(p, rs);
@@ -606,7 +615,7 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
   const Origin o = origin_of<MULTI>(p, b);
-  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R);
+  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R, phase);
 
   const Quad u = quad_of(o);
   Fields f = fields_of<MULTI>(p, o.src);
@@ -635,7 +644,7 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   load_coef<R>(p.cm, u, live, cf);
   const float amp = src ? __ldg(p.amp + n) : 0.f;  // the wavelet at t_{n+1/2}, source CTAs only
   cp_async_wait_all();
-  if (!tiles_ready(p, bar) || !live) return;
+  if (!tiles_ready(p, bar, phase) || !live) return;
   const View<R> v{s};
   if (fast)
     e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw, cf, 0.f);
@@ -809,7 +818,8 @@ __device__ __forceinline__ Blk reversed_tile(const DevParams &p, const Blk &b) {
 
 // One CTA of the H half-step.
 template <int R, bool MULTI, bool CONV>
-__device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk) {
+__device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk,
+                                        unsigned phase = 0) {
   const Blk b = blk.z < p.rec_layers ? blk : reversed_tile<MULTI>(p, blk);
   if (b.z < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p, b);
@@ -822,7 +832,7 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   float *s = smem_tiles(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
   const Origin o = origin_of<MULTI>(p, b);
-  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R);
+  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R, phase);
 
   const Quad u = quad_of(o);
   const Fields f = fields_of<MULTI>(p, o.src);
@@ -842,7 +852,7 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   Coef<R> cf;
   load_coef<R>(p.cp, u, live, cf);
   cp_async_wait_all();
-  if (!tiles_ready(p, bar) || !live) return;
+  if (!tiles_ready(p, bar, phase) || !live) return;
   const View<R> v{s};
   if (fast)
     h_quad<R, true>(p, f, v, u, h, ps, n, cf);
@@ -988,7 +998,7 @@ __device__ __forceinline__ bool grid_barrier(const PSet &S, unsigned gen) {
 template <int R>
 __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_constant__ PSet S) {
   const int total = S.cta0[S.njobs];
-  unsigned gen = 0;
+  unsigned gen = 0, tiles = 0;  // tiles: stencil tiles this CTA ran (the mbarrier's phase)
   for (int n = 0; n < S.nt_max; ++n) {
     for (int half = 0; half < 2; ++half) {
       int j = 0;
@@ -1000,17 +1010,18 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_consta
           const Blk blk{l % J.bx, (l / J.bx) % J.by, l / (J.bx * J.by)};
           if (half == 0) {
             if (J.multi)
-              e_block<R, true, false, false>(J.p, J.tmE, n, blk);
+              e_block<R, true, false, false>(J.p, J.tmE, n, blk, tiles);
             else
-              e_block<R, false, false, false>(J.p, J.tmE, n, blk);
+              e_block<R, false, false, false>(J.p, J.tmE, n, blk, tiles);
           } else {
             if (J.multi)
-              h_block<R, true, false>(J.p, J.tmH, n, blk);
+              h_block<R, true, false>(J.p, J.tmH, n, blk, tiles);
             else
-              h_block<R, false, false>(J.p, J.tmH, n, blk);
+              h_block<R, false, false>(J.p, J.tmH, n, blk, tiles);
           }
+          if (blk.z >= J.p.rec_layers) ++tiles;  // receiver items use no tiles
         }
-        __syncthreads();  // the next item reuses the CTA's shared memory and mbarrier
+        __syncthreads();  // the next item reuses the CTA's shared memory
       }
       if (!grid_barrier(S, ++gen)) return;
     }
@@ -2169,6 +2180,7 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
   S.status = reinterpret_cast<int *>(base + kPHdrStatus);
   S.abort = reinterpret_cast<int *>(base + kPHdrAbort);
   S.bar = reinterpret_cast<unsigned *>(base + kPHdrBar);
+  for (int j = 0; j < nt; ++j) S.job[j].p.abort = S.abort;  // a tile wait that runs out stops the run
   S.wait_ns = static_cast<unsigned long long>((o.wait_s > 0 ? o.wait_s : 1.0) * 1e9);
   S.skip = o.skip_arrival;
   run->rd = run->P[0].rd;
