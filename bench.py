@@ -589,8 +589,8 @@ def survey_line(emm, torch, stream, job_max, world, rank, nsrc=32):
     """The batched survey: `nsrc` transmitters along the tow line over the
     marine model (x = -3100 + 200 k, 50 m above the seabed) plus the eight
     uneven grids (each with its own transmitter), all advanced in ONE
-    persistent cooperative launch (emm_forward_persistent), its resident-CTA
-    count picked by emm_persist_tune, the whole solve replayed from a CUDA
+    persistent cooperative launch (emm_forward_persistent), its tile shape and
+    resident-CTA count picked by emm_persist_tune, the whole solve replayed from a CUDA
     graph (emm_persist_plan_run); against the same problems one at a time
     (emm_forward of each transmitter and grid in turn)."""
     wl = W.marine_1d()
@@ -637,8 +637,10 @@ def survey_line(emm, torch, stream, job_max, world, rank, nsrc=32):
     return {"problems": f"{nsrc} tow-line transmitters on {wl.name} + {len(tasks) - 1} uneven grids",
             "cell_steps": cells, "value": value, "unit": "Gcell-steps/s", "ms": 1e3 * sec,
             "one_at_a_time": world * cells / sec1 / 1e9, "ms_one_at_a_time": 1e3 * sec1,
-            "speedup": sec1 / sec, "ctas_per_sm": best.ctas_per_sm,
-            "tune_ms_40_steps": {str(k): v for k, v in tune_ms.items()}, "bitwise_equal": bool(same),
+            "speedup": sec1 / sec, "tile_shape": ["32x8x2", "32x4x4"][best.tile_shape],
+            "ctas_per_sm": best.ctas_per_sm,
+            "tune_ms_40_steps": {f"{['32x8x2', '32x4x4'][k[0]]}/{k[1]}": v for k, v in tune_ms.items()},
+            "bitwise_equal": bool(same),
             "what": "emm_persist_plan_run: the whole survey (set-up, one persistent cooperative launch with "
                     "bounded grid barriers between half-steps, normalisation) replayed from a CUDA graph, "
                     "against emm_forward of every transmitter and grid in turn; device-resident inputs"}

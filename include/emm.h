@@ -368,6 +368,8 @@ typedef struct {
   int skip_arrival;  /* testing only: the index of one CTA that leaves without arriving at the
                         first grid barrier, so that every other CTA's bounded wait runs out and the
                         run ends with EMM_ETIMEOUT; -1 (or any index >= the CTA count) normally */
+  int tile_shape;    /* stencil tile of one work item, 128 threads each: 0 = 32 x 8 x 2 cells
+                        (x, y, z; the shape of the plain launches), 1 = 32 x 4 x 4 cells */
 } emm_persist_opts;
 
 /* Workspace of emm_forward_persistent: a 256-byte header (the work list's
@@ -382,7 +384,7 @@ int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes,
 
 /* Forward solves of the tasks in one persistent cooperative launch (after
  * each task's set-up, enqueued on `stream`, and before its normalisation).
- * opts NULL: the defaults {0, 0, 1.0, -1}.  Every grid-barrier wait is
+ * opts NULL: the defaults {0, 0, 1.0, -1, 0}.  Every grid-barrier wait is
  * bounded by opts->wait_s of device time; a wait that runs out writes
  * EMM_ETIMEOUT to the header's status word and every CTA returns at its next
  * barrier (the outputs are then undefined).  Asynchronous on `stream`;
@@ -392,14 +394,17 @@ int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes,
 int emm_forward_persistent(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
                            size_t ws_bytes, emm_stream stream);
 
-/* Autotuner of the persistent launch: times `steps` leapfrog steps (each
- * task's own count at most) with 1, 2, ... resident CTAs per SM (at most
- * *ncand candidates, at most the occupancy limit), each after a warm-up run,
- * with CUDA events on `stream`; returns the times in ms[0 .. *ncand - 1]
- * (host; *ncand receives the number tried) and the fastest options in *best.
- * Synchronises `stream`; the workspace is left to be prepared again. */
+/* Autotuner of the persistent launch: the candidates are every tile shape
+ * (tile_shape 0, 1) with 1, 2, ... resident CTAs per SM up to that shape's
+ * occupancy limit, in that order; it times `steps` leapfrog steps (each
+ * task's own count at most) of the first *ncand candidates, each after a
+ * warm-up run, with CUDA events on `stream`.  Returns in cands[k] and ms[k]
+ * (host arrays of *ncand) each timed candidate's options and time, in
+ * *ncand the number timed and in *best the fastest.  Synchronises `stream`;
+ * the workspace is left to be prepared again.  EMM_EINVAL if steps < 1,
+ * *ncand < 1 or a pointer is NULL; otherwise as emm_forward_persistent. */
 int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_bytes, int steps, emm_stream stream,
-                     emm_persist_opts *best, double *ms, int *ncand);
+                     int *ncand, emm_persist_opts *cands, double *ms, emm_persist_opts *best);
 
 /* The whole persistent solve of fixed tasks captured once as a CUDA graph:
  * the tasks' set-up (state cleared, dt/eps from the conductivity at each

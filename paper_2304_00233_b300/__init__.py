@@ -92,17 +92,21 @@ class _Task(C.Structure):
 class PersistOpts(C.Structure):
     """``emm_persist_opts``: resident CTAs per SM (0: as many as fit), a cap
     on all CTAs (0: none), the bound of one grid-barrier wait in seconds
-    (<= 0: 1 s) and, for tests only, a CTA that withholds its first arrival
-    (-1: none)."""
+    (<= 0: 1 s), for tests only a CTA that withholds its first arrival
+    (-1: none), and the tile shape (0: 32 x 8 x 2 cells, 1: 32 x 4 x 4)."""
     _fields_ = [("ctas_per_sm", C.c_int), ("max_ctas", C.c_int), ("wait_s", C.c_double),
-                ("skip_arrival", C.c_int)]
+                ("skip_arrival", C.c_int), ("tile_shape", C.c_int)]
 
-    def __init__(self, ctas_per_sm=0, max_ctas=0, wait_s=0.0, skip_arrival=-1):
-        super().__init__(int(ctas_per_sm), int(max_ctas), float(wait_s), int(skip_arrival))
+    def __init__(self, ctas_per_sm=0, max_ctas=0, wait_s=0.0, skip_arrival=-1, tile_shape=0):
+        super().__init__(int(ctas_per_sm), int(max_ctas), float(wait_s), int(skip_arrival), int(tile_shape))
+
+    def key(self):
+        """(tile shape, resident CTAs per SM) of these options."""
+        return (int(self.tile_shape), int(self.ctas_per_sm))
 
     def __repr__(self):
         return (f"PersistOpts(ctas_per_sm={self.ctas_per_sm}, max_ctas={self.max_ctas}, wait_s={self.wait_s}, "
-                f"skip_arrival={self.skip_arrival})")
+                f"skip_arrival={self.skip_arrival}, tile_shape={self.tile_shape})")
 
 
 _lib = None
@@ -152,8 +156,8 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
         "emm_persist_workspace_size": ([C.c_int, C.POINTER(_Task), C.POINTER(C.c_size_t),
                                         C.POINTER(C.c_size_t)], C.c_int),
         "emm_forward_persistent": ([C.c_int, C.POINTER(_Task), C.POINTER(PersistOpts), V, C.c_size_t, V], C.c_int),
-        "emm_persist_tune": ([C.c_int, C.POINTER(_Task), V, C.c_size_t, C.c_int, V, C.POINTER(PersistOpts), _D,
-                              _I], C.c_int),
+        "emm_persist_tune": ([C.c_int, C.POINTER(_Task), V, C.c_size_t, C.c_int, V, _I, C.POINTER(PersistOpts), _D,
+                              C.POINTER(PersistOpts)], C.c_int),
         "emm_persist_plan_create": ([C.c_int, C.POINTER(_Task), C.POINTER(PersistOpts), V, C.c_size_t, V,
                                      C.POINTER(V)], C.c_int),
         "emm_persist_plan_run": ([V, V], C.c_int),
@@ -765,21 +769,23 @@ def _persist_check(work: PersistWork, sigmas):
     return sigmas
 
 
-def persist_tune(work: PersistWork, sigmas, steps: int = 40, candidates: int = 8, stream=None):
-    """``emm_persist_tune``: times ``steps`` leapfrog steps with 1, 2, ...
-    resident CTAs per SM and returns (best PersistOpts, {ctas_per_sm: ms})."""
+def persist_tune(work: PersistWork, sigmas, steps: int = 40, candidates: int = 16, stream=None):
+    """``emm_persist_tune``: times ``steps`` leapfrog steps of each tile
+    shape with 1, 2, ... resident CTAs per SM and returns (best PersistOpts,
+    {(tile_shape, ctas_per_sm): ms})."""
     import torch
     sigmas = _persist_check(work, sigmas)
     if stream is None:
         stream = torch.cuda.current_stream(sigmas[0].device)
     arr, keep = work._c(sigmas)
     ms = np.zeros(int(candidates))
+    cands = (PersistOpts * int(candidates))()
     nc = C.c_int(int(candidates))
     best = PersistOpts()
     _check(load_library().emm_persist_tune(len(work.tasks), arr, C.c_void_p(work.ptr), C.c_size_t(work.nbytes),
-                                           int(steps), C.c_void_p(stream.cuda_stream), C.byref(best), _dp(ms),
-                                           C.byref(nc)), "emm_persist_tune")
-    return best, {k + 1: float(ms[k]) for k in range(nc.value)}
+                                           int(steps), C.c_void_p(stream.cuda_stream), C.byref(nc), cands, _dp(ms),
+                                           C.byref(best)), "emm_persist_tune")
+    return best, {cands[k].key(): float(ms[k]) for k in range(nc.value)}
 
 
 def forward_persistent(work: PersistWork, sigmas, opts: Optional[PersistOpts] = None, stream=None,

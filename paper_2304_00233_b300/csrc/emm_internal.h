@@ -134,7 +134,9 @@ struct FieldGeom {
   int org[3], tiles[3], xshift, pitch;
   int psx_hx[2], psx_wx[2], psx_far0[2];  // x-derivative CPML storage: [0] integer, [1] half samples
 };
-FieldGeom field_geom(const emm_grid *g);
+// shape: the stencil tile shape the tiling is for (0: 32 x 8 x 2, 1: 32 x 4 x 4);
+// the memory layout does not depend on it.
+FieldGeom field_geom(const emm_grid *g, int shape = 0);
 
 // Byte layout of the device workspace.
 // The state of transmitter 0 (E[3], H[3], psiE[6], psiH[6]) is one block
@@ -169,7 +171,7 @@ struct Prepared {
   FieldGeom fg;
   dim3 blocks;
   double dt;
-  int sms, rd;
+  int sms, rd, shape;
 };
 
 // Validate, upload the tables, clear the state and compute dt/eps (enqueued
@@ -180,7 +182,8 @@ struct Prepared {
 // the call, so the enqueued work can be captured in a CUDA graph.
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc = 1,
-                    const double *src_pos = nullptr, bool converge = false, bool upload_tables = true);
+                    const double *src_pos = nullptr, bool converge = false, bool upload_tables = true,
+                    int shape = 0);
 // Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te);

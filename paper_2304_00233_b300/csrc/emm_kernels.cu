@@ -60,9 +60,16 @@ namespace emm {
 namespace {
 
 constexpr int TX = 32;  // tile width (x, one warp)
-constexpr int TY = 8;   // tile height (y)
-constexpr int ZC = 2;   // planes per CTA
-constexpr int NT = (TX / 4) * TY * ZC;  // threads: one per quad of 4 x-adjacent cells
+// Tile shapes, 128 threads each (one per quad of 4 x-adjacent cells):
+// shape 0 is 32 (x) by 8 (y) by 2 (z) cells, shape 1 is 32 by 4 by 4.  The
+// plain launches use shape 0; the persistent work list takes the shape its
+// autotuner picks.
+constexpr int kShapes = 2;
+__host__ __device__ constexpr int shape_ty(int S) { return S == 1 ? 4 : 8; }  // tile height (y)
+__host__ __device__ constexpr int shape_zc(int S) { return S == 1 ? 4 : 2; }  // planes per CTA
+constexpr int NT = 128;
+static_assert((TX / 4) * shape_ty(0) * shape_zc(0) == NT && (TX / 4) * shape_ty(1) * shape_zc(1) == NT,
+              "every tile shape has one thread per quad");
 constexpr int XH = 4;   // x halo of the TMA boxes (>= R; keeps box x starts 16-byte aligned)
 constexpr int WX = TX + 2 * XH;
 
@@ -72,8 +79,9 @@ __host__ __device__ constexpr int min_ctas(int R) { return R <= 2 ? 5 : 4; }
 // Shared-memory tiles of one CTA, for either half-step.  "zf" is the source
 // field with z and y halos (Hx / Ex), "xf" the one with z and x halos
 // (Hy / Ey), "xy" the one with x and y halos (Hz / Ez).
-template <int R>
+template <int R, int S = 0>
 struct Tiles {
+  static constexpr int TY = shape_ty(S), ZC = shape_zc(S);
   static constexpr int ZQ = ZC + 2 * R - 1;  // planes of the z-halo boxes
   static constexpr int YH = TY + 2 * R;      // rows of the y-halo boxes
   static constexpr int ZF = ZQ * YH * TX;
@@ -83,8 +91,8 @@ struct Tiles {
   static constexpr int PSI = 6 * NT * 4;  // CPML memory staged per thread: [6 slots][NT] float4
   static constexpr size_t ALL = BYTES + static_cast<size_t>(PSI) * 4;
 };
-template <int R>
-constexpr size_t smem_bytes() { return Tiles<R>::ALL + 144; }  // + alignment pad + mbarrier
+template <int R, int S = 0>
+constexpr size_t smem_bytes() { return Tiles<R, S>::ALL + 144; }  // + alignment pad + mbarrier
 
 // Tensor maps of one launch: the three source fields with their boxes.
 struct TmaSet {
@@ -177,10 +185,10 @@ __device__ __forceinline__ Blk launch_blk() {
 }
 // MULTI: a batch of transmitters (otherwise transmitter 0 alone, and no
 // index arithmetic for it).
-template <bool MULTI>
+template <bool MULTI, int S = 0>
 __device__ __forceinline__ Origin origin_of(const DevParams &p, const Blk &b) {
   const int bx = MULTI ? b.x / p.nsrc : b.x;
-  return Origin{p.org[0] + bx * TX, p.org[1] + b.y * TY, p.org[2] + (b.z - p.rec_layers) * ZC,
+  return Origin{p.org[0] + bx * TX, p.org[1] + b.y * shape_ty(S), p.org[2] + (b.z - p.rec_layers) * shape_zc(S),
                 MULTI ? b.x % p.nsrc : 0};
 }
 template <bool MULTI>
@@ -217,10 +225,10 @@ __device__ __forceinline__ Fields fields_of(const DevParams &p, int src) {
 // tiles initialised it once already: `phase` > 0 counts the tiles before
 // this one) and issue the three copies.  The z-halo boxes start `lead`
 // planes from k0 (-R for D-, -R+1 for D+).
-template <int R>
+template <int R, int S>
 __device__ __forceinline__ void issue_tiles(const TmaSet &tm, float *s, uint64_t *bar, const Origin &o, int lead,
                                             unsigned phase) {
-  using T = Tiles<R>;
+  using T = Tiles<R, S>;
   if (phase == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -254,9 +262,10 @@ __device__ __forceinline__ float *smem_tiles(unsigned char *raw) {
 }
 
 // Does the CTA's box meet the bounding box of the source stencils?
+template <int S>
 __device__ __forceinline__ bool cta_has_source(const SrcDev &sd, const Origin &o) {
-  return sd.any && o.i0 + TX > sd.lo[0] && o.i0 <= sd.hi[0] && o.j0 + TY > sd.lo[1] && o.j0 <= sd.hi[1] &&
-         o.k0 + ZC > sd.lo[2] && o.k0 <= sd.hi[2];
+  return sd.any && o.i0 + TX > sd.lo[0] && o.i0 <= sd.hi[0] && o.j0 + shape_ty(S) > sd.lo[1] &&
+         o.j0 <= sd.hi[1] && o.k0 + shape_zc(S) > sd.lo[2] && o.k0 <= sd.hi[2];
 }
 
 // jw: this transmitter's [3][(2R)^3] stencil weights.
@@ -271,9 +280,9 @@ __device__ __forceinline__ void source_term(const SrcDev &sd, const float *jw, i
 }
 
 // ---------------------------------------------------------------------------
-// Thread layout of a stencil CTA: the tile is 32 (x) x 8 (y) x ZC (z) cells;
-// thread t owns the 4 x-adjacent cells ("quad") q = t % 8 of row r = t / 8 % 8
-// in plane c = t / 64.  A quad starts on a 16-byte boundary of every field
+// Thread layout of a stencil CTA: the tile is 32 (x) x TY (y) x ZC (z) cells;
+// thread t owns the 4 x-adjacent cells ("quad") q = t % 8 of row r = t / 8 % TY
+// in plane c = t / (8 TY).  A quad starts on a 16-byte boundary of every field
 // row, so its samples move as one float4 and its taps as float4 shared-memory
 // reads; derivatives along y and z use paired FP32 FMAs (f32x2).
 // ---------------------------------------------------------------------------
@@ -282,12 +291,13 @@ struct Quad {
   int q, r, c;   // quad, row, plane inside the tile
   int i, j, k;   // grid coordinates of the first cell
 };
+template <int S>
 __device__ __forceinline__ Quad quad_of(const Origin &o) {
   const int t = threadIdx.x;
   Quad u;
   u.q = t & 7;
-  u.r = (t >> 3) & 7;
-  u.c = t >> 6;
+  u.r = (t >> 3) % shape_ty(S);
+  u.c = t / (8 * shape_ty(S));
   u.i = o.i0 + 4 * u.q;
   u.j = o.j0 + u.r;
   u.k = o.k0 + u.c;
@@ -328,15 +338,15 @@ __device__ __forceinline__ void put(float4 &v, int e, float x) {
 
 // Shared-memory views of the three tiles (see Tiles), as float4 at quad
 // granularity: x is a sample column of the box, a multiple of 4.
-template <int R>
+template <int R, int S = 0>
 struct View {
-  using T = Tiles<R>;
+  using T = Tiles<R, S>;
   const float *s;
   __device__ float4 zf(int pz, int y, int x) const {
     return *reinterpret_cast<const float4 *>(s + (pz * T::YH + y) * TX + x);
   }
   __device__ float4 xf(int pz, int y, int x) const {
-    return *reinterpret_cast<const float4 *>(s + T::ZF + (pz * TY + y) * WX + x);
+    return *reinterpret_cast<const float4 *>(s + T::ZF + (pz * T::TY + y) * WX + x);
   }
   __device__ float4 xy(int pz, int y, int x) const {
     return *reinterpret_cast<const float4 *>(s + T::ZF + T::XF + (pz * T::YH + y) * WX + x);
@@ -427,10 +437,11 @@ __device__ __forceinline__ float cpml1(float d, float &psi, float a, float b) {
 // ---------------------------------------------------------------------------
 // Is every cell of the CTA inside the CPML-free region where all D- rows
 // exist (no slab, no boundary test needed)?
+template <int S>
 __device__ __forceinline__ bool interior_E(const DevParams &p, const Origin &o, int R) {
   const int m = max(p.nb, R);
-  return o.i0 >= m && o.i0 + TX - 1 <= p.np[0] - 1 - m && o.j0 >= m && o.j0 + TY - 1 <= p.np[1] - 1 - m &&
-         o.k0 >= m && o.k0 + ZC - 1 <= p.np[2] - 1 - m;
+  return o.i0 >= m && o.i0 + TX - 1 <= p.np[0] - 1 - m && o.j0 >= m && o.j0 + shape_ty(S) - 1 <= p.np[1] - 1 - m &&
+         o.k0 >= m && o.k0 + shape_zc(S) - 1 <= p.np[2] - 1 - m;
 }
 
 // One quad of the E update.  FAST: an interior CTA without the source, where
@@ -461,8 +472,8 @@ __device__ __forceinline__ void load_coef(const float *const *tab, const Quad &u
   }
 }
 
-template <int R, bool FAST>
-__device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
+template <int R, bool FAST, int S>
+__device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, const View<R, S> &v, const Quad &u,
                                        const float4 (&e)[3], const float4 (&w)[3], const float4 *ps, int n,
                                        bool src, const SrcDev *sd, const float *jw, const Coef<R> &cf,
                                        float amp) {
@@ -601,7 +612,7 @@ __device__ __forceinline__ void e_quad(const DevParams &p, const Fields &f, cons
 // One CTA of the E half-step.  CONV: a convergence run (corner DTFT).
 // OUT: E^{n+1} goes to p.Eout (E^n stays where it is).
 // phase: tiles this CTA ran before this one (0 for a CTA of a launch of its own).
-template <int R, bool MULTI, bool CONV, bool OUT>
+template <int R, bool MULTI, bool CONV, bool OUT, int S = 0>
 __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &b,
                                         unsigned phase = 0) {
   if (b.z < p.rec_layers) {
@@ -613,11 +624,11 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of<MULTI>(p, b);
-  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, -R, phase);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R, S>::ALL / 4);
+  const Origin o = origin_of<MULTI, S>(p, b);
+  if (threadIdx.x == 0) issue_tiles<R, S>(tm, s, bar, o, -R, phase);
 
-  const Quad u = quad_of(o);
+  const Quad u = quad_of<S>(o);
   Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
@@ -632,9 +643,9 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   }
   const SrcDev *sd = p.srcs + o.src;
   const float *jw = p.jw + static_cast<size_t>(o.src) * 3 * (2 * R) * (2 * R) * (2 * R);
-  const bool src = p.src_fused && cta_has_source(*sd, o);
-  const bool fast = !src && interior_E(p, o, R);
-  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
+  const bool src = p.src_fused && cta_has_source<S>(*sd, o);
+  const bool fast = !src && interior_E<S>(p, o, R);
+  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R, S>::BYTES / 4);
   if (!fast && live)
     stage_psi(ps, f.psiE[0], f.psiE[1], f.psiE[2], f.psiE[3], f.psiE[4], f.psiE[5], p, u, slab_int(u.j, np1, nb),
               slab_int(u.k, np2, nb),
@@ -645,11 +656,11 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
   const float amp = src ? __ldg(p.amp + n) : 0.f;  // the wavelet at t_{n+1/2}, source CTAs only
   cp_async_wait_all();
   if (!tiles_ready(p, bar, phase) || !live) return;
-  const View<R> v{s};
+  const View<R, S> v{s};
   if (fast)
-    e_quad<R, true>(p, f, v, u, e, w, ps, n, false, sd, jw, cf, 0.f);
+    e_quad<R, true, S>(p, f, v, u, e, w, ps, n, false, sd, jw, cf, 0.f);
   else
-    e_quad<R, false>(p, f, v, u, e, w, ps, n, src, sd, jw, cf, amp);
+    e_quad<R, false, S>(p, f, v, u, e, w, ps, n, src, sd, jw, cf, amp);
 }
 
 // The E half-step of one problem; every launch of a convergence run returns
@@ -667,16 +678,17 @@ __global__ void __launch_bounds__(NT, min_ctas(R))
 // H half-step: H^{n+3/2} = H^{n+1/2} - dt/mu0 curl E^{n+1}
 // ---------------------------------------------------------------------------
 // Is every cell of the CTA inside the CPML-free region where all D+ rows exist?
+template <int S>
 __device__ __forceinline__ bool interior_H(const DevParams &p, const Origin &o, int R) {
   const int lo = max(p.nb, R - 1);
   const int hx = min(p.np[0] - 2 - p.nb, p.np[0] - 1 - R), hy = min(p.np[1] - 2 - p.nb, p.np[1] - 1 - R),
             hz = min(p.np[2] - 2 - p.nb, p.np[2] - 1 - R);
-  return o.i0 >= lo && o.i0 + TX - 1 <= hx && o.j0 >= lo && o.j0 + TY - 1 <= hy && o.k0 >= lo &&
-         o.k0 + ZC - 1 <= hz;
+  return o.i0 >= lo && o.i0 + TX - 1 <= hx && o.j0 >= lo && o.j0 + shape_ty(S) - 1 <= hy && o.k0 >= lo &&
+         o.k0 + shape_zc(S) - 1 <= hz;
 }
 
-template <int R, bool FAST>
-__device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, const View<R> &v, const Quad &u,
+template <int R, bool FAST, int S>
+__device__ __forceinline__ void h_quad(const DevParams &p, const Fields &f, const View<R, S> &v, const Quad &u,
                                        const float4 (&h)[3], const float4 *ps, int n, const Coef<R> &cf) {
   constexpr int M = 2 * R;
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
@@ -817,7 +829,7 @@ __device__ __forceinline__ Blk reversed_tile(const DevParams &p, const Blk &b) {
 }
 
 // One CTA of the H half-step.
-template <int R, bool MULTI, bool CONV>
+template <int R, bool MULTI, bool CONV, int S = 0>
 __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk,
                                         unsigned phase = 0) {
   const Blk b = blk.z < p.rec_layers ? blk : reversed_tile<MULTI>(p, blk);
@@ -830,11 +842,11 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   }
   extern __shared__ unsigned char smem_raw[];
   float *s = smem_tiles(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R>::ALL / 4);
-  const Origin o = origin_of<MULTI>(p, b);
-  if (threadIdx.x == 0) issue_tiles<R>(tm, s, bar, o, 1 - R, phase);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s + Tiles<R, S>::ALL / 4);
+  const Origin o = origin_of<MULTI, S>(p, b);
+  if (threadIdx.x == 0) issue_tiles<R, S>(tm, s, bar, o, 1 - R, phase);
 
-  const Quad u = quad_of(o);
+  const Quad u = quad_of<S>(o);
   const Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
@@ -842,8 +854,8 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
   for (int a = 0; a < 3; ++a) h[a] = live ? *reinterpret_cast<const float4 *>(f.H[a] + id) : float4{};
-  const bool fast = interior_H(p, o, R);
-  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R>::BYTES / 4);
+  const bool fast = interior_H<S>(p, o, R);
+  float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R, S>::BYTES / 4);
   if (!fast && live)
     stage_psi(ps, f.psiH[0], f.psiH[1], f.psiH[2], f.psiH[3], f.psiH[4], f.psiH[5], p, u, slab_half(u.j, np1, nb),
               slab_half(u.k, np2, nb),
@@ -853,11 +865,11 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   load_coef<R>(p.cp, u, live, cf);
   cp_async_wait_all();
   if (!tiles_ready(p, bar, phase) || !live) return;
-  const View<R> v{s};
+  const View<R, S> v{s};
   if (fast)
-    h_quad<R, true>(p, f, v, u, h, ps, n, cf);
+    h_quad<R, true, S>(p, f, v, u, h, ps, n, cf);
   else
-    h_quad<R, false>(p, f, v, u, h, ps, n, cf);
+    h_quad<R, false, S>(p, f, v, u, h, ps, n, cf);
 }
 
 template <int R, bool MULTI, bool CONV>
@@ -995,7 +1007,7 @@ __device__ __forceinline__ bool grid_barrier(const PSet &S, unsigned gen) {
   return __syncthreads_and(go) != 0;
 }
 
-template <int R>
+template <int R, int SH>
 __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_constant__ PSet S) {
   const int total = S.cta0[S.njobs];
   unsigned gen = 0, tiles = 0;  // tiles: stencil tiles this CTA ran (the mbarrier's phase)
@@ -1010,14 +1022,14 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_consta
           const Blk blk{l % J.bx, (l / J.bx) % J.by, l / (J.bx * J.by)};
           if (half == 0) {
             if (J.multi)
-              e_block<R, true, false, false>(J.p, J.tmE, n, blk, tiles);
+              e_block<R, true, false, false, SH>(J.p, J.tmE, n, blk, tiles);
             else
-              e_block<R, false, false, false>(J.p, J.tmE, n, blk, tiles);
+              e_block<R, false, false, false, SH>(J.p, J.tmE, n, blk, tiles);
           } else {
             if (J.multi)
-              h_block<R, true, false>(J.p, J.tmH, n, blk, tiles);
+              h_block<R, true, false, SH>(J.p, J.tmH, n, blk, tiles);
             else
-              h_block<R, false, false>(J.p, J.tmH, n, blk, tiles);
+              h_block<R, false, false, SH>(J.p, J.tmH, n, blk, tiles);
           }
           if (blk.z >= J.p.rec_layers) ++tiles;  // receiver items use no tiles
         }
@@ -1328,11 +1340,11 @@ __global__ void k_corner_check(double *corner, int *halt, volatile int *host, in
 // ---------------------------------------------------------------------------
 // Host side of emm_forward
 // ---------------------------------------------------------------------------
-FieldGeom field_geom(const emm_grid *g) {
+FieldGeom field_geom(const emm_grid *g, int shape) {
   FieldGeom f{};
   const int lo = std::max(g->nb, g->rd);
   const int lo4 = lo & ~3;
-  const int step[3] = {TX, TY, ZC};
+  const int step[3] = {TX, shape_ty(shape), shape_zc(shape)};
   const int first[3] = {lo4, lo, lo};
   for (int a = 0; a < 3; ++a) {
     f.org[a] = first[a] - step[a] * ((first[a] + step[a] - 1) / step[a]);
@@ -1475,11 +1487,11 @@ bool make_map(CUtensorMap *map, const float *base, const DevParams &p, int bx, i
 }
 
 // The boxes of the three source fields (see Tiles).
-template <int R>
+template <int R, int S = 0>
 bool make_tiles(TmaSet *t, float *const *F, const DevParams &p) {
-  using T = Tiles<R>;
-  return make_map(&t->m[0], F[0], p, TX, T::YH, T::ZQ) && make_map(&t->m[1], F[1], p, WX, TY, T::ZQ) &&
-         make_map(&t->m[2], F[2], p, WX, T::YH, ZC);
+  using T = Tiles<R, S>;
+  return make_map(&t->m[0], F[0], p, TX, T::YH, T::ZQ) && make_map(&t->m[1], F[1], p, WX, T::TY, T::ZQ) &&
+         make_map(&t->m[2], F[2], p, WX, T::YH, T::ZC);
 }
 
 // The four air transform passes after a half step (see k_air_fft).
@@ -1586,7 +1598,7 @@ void normalisation(const emm_survey *s, double dt, int nsteps, double *norm) {
 
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc,
-                    const double *src_pos, bool converge, bool upload_tables) {
+                    const double *src_pos, bool converge, bool upload_tables, int shape) {
   int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (!sigma || !ws || (s->nrec > 0 && !rec_out) || (s->volume && !vol_out)) return EMM_EINVAL;
@@ -1795,7 +1807,8 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     p.cp[a] = reinterpret_cast<const float *>(base + L.cp[a]);
     p.pml[a] = reinterpret_cast<const float *>(base + L.pml[a]);
   }
-  const FieldGeom fg = field_geom(g);
+  if (shape < 0 || shape >= kShapes) return EMM_EINVAL;
+  const FieldGeom fg = field_geom(g, shape);
   p.pitch = fg.pitch;
   p.plane = static_cast<size_t>(p.pitch) * p.np[1];
   p.nbe = nbe;
@@ -1892,6 +1905,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
   out->dt = dt;
   out->sms = sms;
   out->rd = rd;
+  out->shape = shape;
   return cudaGetLastError() == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
 
@@ -2113,15 +2127,16 @@ struct PersistRun {
   std::unique_ptr<PSet> S;
   unsigned ctas = 0;
   size_t smem = 0;
-  int rd = 0;
+  int rd = 0, shape = 0;
 };
 
-template <int R>
+template <int R, int SH>
 cudaError_t persist_shape(PersistRun *run, const emm_persist_opts &o) {
-  const size_t sb = smem_bytes<R>();
-  cudaError_t e = cudaFuncSetAttribute(k_persist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  const size_t sb = smem_bytes<R, SH>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_persist<R, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
   int per_sm = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R>, NT, sb);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R, SH>, NT, sb);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
@@ -2132,7 +2147,8 @@ cudaError_t persist_shape(PersistRun *run, const emm_persist_opts &o) {
   run->smem = sb;
   for (int j = 0; j < run->S->njobs; ++j) {
     PJob &J = run->S->job[j];
-    if (!make_tiles<R>(&J.tmE, J.p.H, J.p) || !make_tiles<R>(&J.tmH, J.p.E, J.p)) return cudaErrorInvalidValue;
+    if (!make_tiles<R, SH>(&J.tmE, J.p.H, J.p) || !make_tiles<R, SH>(&J.tmH, J.p.E, J.p))
+      return cudaErrorInvalidValue;
   }
   return cudaSuccess;
 }
@@ -2145,9 +2161,9 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
   size_t total = 0;
   int st = persist_layout(nt, t, &off, &total);
   if (st != EMM_OK) return st;
-  emm_persist_opts o{0, 0, 0.0, -1};
+  emm_persist_opts o{0, 0, 0.0, -1, 0};
   if (opts) o = *opts;
-  if (o.ctas_per_sm < 0 || o.max_ctas < 0) return EMM_EINVAL;
+  if (o.ctas_per_sm < 0 || o.max_ctas < 0 || o.tile_shape < 0 || o.tile_shape >= kShapes) return EMM_EINVAL;
   if (!ws || ws_bytes < total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
   for (int j = 0; j < nt; ++j)
     if (!t[j].sigma || (t[j].survey->nrec > 0 && !t[j].rec_out)) return EMM_EINVAL;
@@ -2161,7 +2177,7 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
   for (int j = 0; j < nt; ++j) {
     const size_t end = j + 1 < nt ? off[j + 1] : total;
     st = prepare_forward(t[j].grid, t[j].survey, t[j].sigma, base + off[j], end - off[j], t[j].rec_out, nullptr, cs,
-                         &run->P[j], t[j].nsrc, t[j].src_pos, false, upload);
+                         &run->P[j], t[j].nsrc, t[j].src_pos, false, upload, o.tile_shape);
     if (st != EMM_OK) return st;
     const Prepared &P = run->P[j];
     PJob &J = S.job[j];
@@ -2184,12 +2200,18 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
   S.wait_ns = static_cast<unsigned long long>((o.wait_s > 0 ? o.wait_s : 1.0) * 1e9);
   S.skip = o.skip_arrival;
   run->rd = run->P[0].rd;
+  run->shape = o.tile_shape;
   cudaError_t e;
-  switch (run->rd) {
-    case 1: e = persist_shape<1>(run, o); break;
-    case 2: e = persist_shape<2>(run, o); break;
-    case 3: e = persist_shape<3>(run, o); break;
-    default: e = persist_shape<4>(run, o); break;
+  const int key = 2 * run->rd + run->shape;
+  switch (key) {
+    case 2: e = persist_shape<1, 0>(run, o); break;
+    case 3: e = persist_shape<1, 1>(run, o); break;
+    case 4: e = persist_shape<2, 0>(run, o); break;
+    case 5: e = persist_shape<2, 1>(run, o); break;
+    case 6: e = persist_shape<3, 0>(run, o); break;
+    case 7: e = persist_shape<3, 1>(run, o); break;
+    case 8: e = persist_shape<4, 0>(run, o); break;
+    default: e = persist_shape<4, 1>(run, o); break;
   }
   return e == cudaSuccess ? EMM_OK : EMM_ECUDA;
 }
@@ -2206,11 +2228,15 @@ cudaError_t persist_launch(const PersistRun &run, cudaStream_t cs) {
   cfg.stream = cs;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  switch (run.rd) {
-    case 1: return cudaLaunchKernelEx(&cfg, k_persist<1>, *run.S);
-    case 2: return cudaLaunchKernelEx(&cfg, k_persist<2>, *run.S);
-    case 3: return cudaLaunchKernelEx(&cfg, k_persist<3>, *run.S);
-    default: return cudaLaunchKernelEx(&cfg, k_persist<4>, *run.S);
+  switch (2 * run.rd + run.shape) {
+    case 2: return cudaLaunchKernelEx(&cfg, k_persist<1, 0>, *run.S);
+    case 3: return cudaLaunchKernelEx(&cfg, k_persist<1, 1>, *run.S);
+    case 4: return cudaLaunchKernelEx(&cfg, k_persist<2, 0>, *run.S);
+    case 5: return cudaLaunchKernelEx(&cfg, k_persist<2, 1>, *run.S);
+    case 6: return cudaLaunchKernelEx(&cfg, k_persist<3, 0>, *run.S);
+    case 7: return cudaLaunchKernelEx(&cfg, k_persist<3, 1>, *run.S);
+    case 8: return cudaLaunchKernelEx(&cfg, k_persist<4, 0>, *run.S);
+    default: return cudaLaunchKernelEx(&cfg, k_persist<4, 1>, *run.S);
   }
 }
 
@@ -2479,15 +2505,22 @@ int emm_forward_persistent(int ntasks, const emm_task *tasks, const emm_persist_
 }
 
 int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_bytes, int steps, emm_stream stream,
-                     emm_persist_opts *best, double *ms, int *ncand) {
-  if (steps < 1 || !best || !ms || !ncand) return EMM_EINVAL;
+                     int *ncand, emm_persist_opts *cands, double *ms, emm_persist_opts *best) {
+  if (steps < 1 || !ncand || *ncand < 1 || !cands || !ms || !best) return EMM_EINVAL;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   emm::PersistRun run;
-  // the candidates: 1 .. the occupancy limit of resident CTAs per SM
-  int st = emm::persist_prepare(ntasks, tasks, nullptr, ws, ws_bytes, cs, true, steps, &run);
+  // the candidates: each tile shape with 1 .. its occupancy limit of
+  // resident CTAs per SM, in that order, at most *ncand of them
+  std::vector<emm_persist_opts> cand;
+  int st = EMM_OK;
+  for (int sh = 0; sh < emm::kShapes && st == EMM_OK; ++sh) {
+    const emm_persist_opts probe{0, 0, 0.0, -1, sh};
+    st = emm::persist_prepare(ntasks, tasks, &probe, ws, ws_bytes, cs, sh == 0, steps, &run);
+    const int top = st == EMM_OK ? static_cast<int>((run.ctas + run.P[0].sms - 1) / run.P[0].sms) : 0;
+    for (int k = 1; k <= top; ++k) cand.push_back(emm_persist_opts{k, 0, 0.0, -1, sh});
+  }
   if (st != EMM_OK) return st;
-  const int top = static_cast<int>((run.ctas + run.P[0].sms - 1) / run.P[0].sms);
-  const int nc = std::min(top, *ncand);
+  const int nc = std::min(static_cast<int>(cand.size()), *ncand);
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess) return EMM_ECUDA;
   if (cudaEventCreate(&b) != cudaSuccess) {
@@ -2496,9 +2529,8 @@ int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_byte
   }
   int bi = -1;
   for (int k = 0; k < nc && st == EMM_OK; ++k) {
-    const emm_persist_opts o{k + 1, 0, 0.0, -1};
     for (int rep = 0; rep < 2 && st == EMM_OK; ++rep) {  // a warm-up run, then the timed one
-      st = emm::persist_prepare(ntasks, tasks, &o, ws, ws_bytes, cs, false, steps, &run);
+      st = emm::persist_prepare(ntasks, tasks, &cand[k], ws, ws_bytes, cs, false, steps, &run);
       if (st == EMM_OK && rep == 1 && cudaEventRecord(a, cs) != cudaSuccess) st = EMM_ECUDA;
       if (st == EMM_OK && emm::persist_launch(run, cs) != cudaSuccess) st = EMM_ECUDA;
       if (st == EMM_OK && rep == 1 && cudaEventRecord(b, cs) != cudaSuccess) st = EMM_ECUDA;
@@ -2506,6 +2538,7 @@ int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_byte
     float t = 0.f;
     if (st == EMM_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess))
       st = EMM_ECUDA;
+    cands[k] = cand[k];
     ms[k] = t;
     if (st == EMM_OK && (bi < 0 || t < ms[bi])) bi = k;
   }
@@ -2513,7 +2546,7 @@ int emm_persist_tune(int ntasks, const emm_task *tasks, void *ws, size_t ws_byte
   cudaEventDestroy(b);
   if (st != EMM_OK) return st;
   *ncand = nc;
-  *best = emm_persist_opts{bi + 1, 0, 0.0, -1};
+  *best = cand[bi];
   return EMM_OK;
 }
 

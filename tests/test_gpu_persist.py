@@ -8,7 +8,9 @@ cooperative launch with grid barriers between the half-steps.
 * One problem against the FP64 oracle within the parity bound.
 * The CUDA-graph plan of the whole solve replays to the same bits, and
   follows new conductivity values written into the bound buffers.
-* The autotuner returns one of the candidates it timed.
+* The autotuner times both tile shapes (32 x 8 x 2 and 32 x 4 x 4 cells)
+  with every resident-CTA count and returns the fastest; both shapes give
+  the same bits.
 * Bounded waits: a two-CTA launch whose second CTA withholds its arrival at
   the first grid barrier (a host-set test option; no fault, trap or endless
   loop) ends with EMM_ETIMEOUT after the short wait bound, and the next
@@ -70,10 +72,12 @@ def test_persistent_equals_single_solves_bitwise(rd):
     ref = _singles(tasks, sigmas)
     for g, r in zip(got, ref):
         assert torch.equal(g, r)
-    # fewer resident CTAs per SM: another walk of the same items, same bits
-    got1 = emm.forward_persistent(work, sigmas, opts=emm.PersistOpts(ctas_per_sm=1))
-    for g, r in zip(got1, ref):
-        assert torch.equal(g, r)
+    # fewer resident CTAs per SM, and the other tile shape: other walks and
+    # other tiles over the same cells, the same arithmetic per cell
+    for opts in (emm.PersistOpts(ctas_per_sm=1), emm.PersistOpts(tile_shape=1), emm.PersistOpts(2, tile_shape=1)):
+        got1 = emm.forward_persistent(work, sigmas, opts=opts)
+        for g, r in zip(got1, ref):
+            assert torch.equal(g, r), opts
 
 
 def test_persistent_against_oracle():
@@ -88,8 +92,10 @@ def test_persistent_against_oracle():
 def test_persistent_graph_plan_and_tuner():
     _, tasks, sigmas = _tasks(2)
     work = emm.PersistWork(tasks)
-    best, ms = emm.persist_tune(work, sigmas, steps=10, candidates=3)
-    assert best.ctas_per_sm in ms and len(ms) >= 1 and all(v > 0 for v in ms.values())
+    best, ms = emm.persist_tune(work, sigmas, steps=10)
+    # every tile shape with every resident-CTA count up to its occupancy limit
+    assert {k[0] for k in ms} == {0, 1} and best.key() in ms and all(v > 0 for v in ms.values())
+    assert min(ms, key=ms.get) == best.key()
     ref = [g.clone() for g in emm.forward_persistent(work, sigmas, opts=best)]
     plan = emm.PersistPlan(work, sigmas, opts=best)
     plan.run_async()
