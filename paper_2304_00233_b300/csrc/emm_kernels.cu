@@ -949,7 +949,7 @@ constexpr int kMaxTasks = 16;
 struct PJob {
   TmaSet tmE, tmH;  // source-field maps of the E half-step (H fields) and of the H half-step (E fields)
   DevParams p;
-  int bx, by, nt, multi;
+  int bx, by, nt;
 };
 struct PSet {
   PJob job[kMaxTasks];
@@ -1020,17 +1020,13 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_consta
         if (n < J.nt) {
           const int l = b - S.cta0[j];
           const Blk blk{l % J.bx, (l / J.bx) % J.by, l / (J.bx * J.by)};
-          if (half == 0) {
-            if (J.multi)
-              e_block<R, true, false, false, SH>(J.p, J.tmE, n, blk, tiles);
-            else
-              e_block<R, false, false, false, SH>(J.p, J.tmE, n, blk, tiles);
-          } else {
-            if (J.multi)
-              h_block<R, true, false, SH>(J.p, J.tmH, n, blk, tiles);
-            else
-              h_block<R, false, false, SH>(J.p, J.tmH, n, blk, tiles);
-          }
+          // the batch form serves single transmitters too (nsrc = 1: the
+          // transmitter index is 0 and its state block is the first), so
+          // one inlined copy of each half-step is enough
+          if (half == 0)
+            e_block<R, true, false, false, SH>(J.p, J.tmE, n, blk, tiles);
+          else
+            h_block<R, true, false, SH>(J.p, J.tmH, n, blk, tiles);
           if (blk.z >= J.p.rec_layers) ++tiles;  // receiver items use no tiles
         }
         __syncthreads();  // the next item reuses the CTA's shared memory
@@ -2185,7 +2181,6 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
     J.bx = static_cast<int>(P.blocks.x);
     J.by = static_cast<int>(P.blocks.y);
     J.nt = steps_cap >= 0 ? std::min(steps_cap, t[j].survey->nt) : t[j].survey->nt;
-    J.multi = P.p.nsrc > 1 ? 1 : 0;
     S.cta0[j] = cta;
     cta += static_cast<int>(P.blocks.x * P.blocks.y * P.blocks.z);
     nmax = std::max(nmax, J.nt);

@@ -143,7 +143,7 @@ def _converged(new, old, tol=1e-5):
 
 @pytest.mark.parametrize("rd", [1, 2])
 def test_corner_stopping_rule(rd):
-    wl = W.small_case(rd=rd, nt=4000, volume=False, nfreq=2)
+    wl = W.small_case(n=(26, 24, 20), rd=rd, nt=4000, volume=False, nfreq=2)
     N = oracle.forward_workload(wl, convergence=True)["nt"]
     assert N < 4000 and (N - 1) % 100 == 0 and N > 201
     flo = int(np.argmin(wl.freqs))
