@@ -338,6 +338,28 @@ int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, siz
 int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
                   double *ms, int *best);
 
+/* ---- Wavefront solve: several time steps in flight, through L2 ----
+ * emm_forward's results (bit for bit) from ONE persistent cooperative
+ * launch that advances z-layers of tiles through `depth` leapfrog steps per
+ * sweep of the grid, so that a layer's fields, read from DRAM once, serve
+ * several half-steps while they sit in the 126 MB L2 (the paper's solver
+ * launches one kernel per half-step and re-reads every field each time,
+ * Sec. 4).  The CTAs claim tiles in a fixed global order and each tile waits
+ * (bounded, 1 s of device time) until the z-layers it reads are complete;
+ * a wait that runs out writes EMM_ETIMEOUT to the status word (emm_status)
+ * and every CTA stops.  One electric point dipole, no volume DTFT, no air
+ * boundary; nt < 2^18.
+ *   depth  time steps per sweep (1 .. 64).
+ *   ws     device workspace of emm_wave_workspace_size bytes, 256-byte
+ *          aligned (the forward workspace, then the tile order and the
+ *          layer counters).
+ * Other arguments as emm_forward.  Asynchronous on `stream`; EMM_EINVAL for
+ * a survey outside the limits above, otherwise the errors of emm_forward;
+ * EMM_ECUDA if the launch fails. */
+int emm_wave_workspace_size(const emm_grid *grid, const emm_survey *survey, int depth, size_t *bytes);
+int emm_forward_wave(const emm_grid *grid, const emm_survey *survey, const float *sigma, int depth, void *ws,
+                     size_t ws_bytes, double *rec_out, emm_stream stream);
+
 /* ---- Persistent work list: many problems in one cooperative launch ----
  * The paper runs one MPI rank per transmitter (Sec. 5); on one GPU the
  * transmitters of a survey and problems on grids of uneven sizes advance

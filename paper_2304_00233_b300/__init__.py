@@ -42,7 +42,8 @@ EXPORTED = ("emm_make_grid", "emm_free_grid", "emm_grid_query", "emm_grid_tables
             "emm_stagger_workspace_size", "emm_stagger_sigma", "emm_stagger_sigma_adjoint",
             "emm_jobs_workspace_size", "emm_forward_jobs", "emm_jobs_tune", "emm_plan_create", "emm_plan_run",
             "emm_plan_destroy", "emm_persist_workspace_size", "emm_forward_persistent", "emm_persist_tune",
-            "emm_persist_plan_create", "emm_persist_plan_run", "emm_persist_plan_destroy")
+            "emm_persist_plan_create", "emm_persist_plan_run", "emm_persist_plan_destroy",
+            "emm_wave_workspace_size", "emm_forward_wave")
 
 
 class EmmError(RuntimeError):
@@ -162,6 +163,8 @@ def load_library(path: str = LIBRARY_PATH) -> C.CDLL:
                                      C.POINTER(V)], C.c_int),
         "emm_persist_plan_run": ([V, V], C.c_int),
         "emm_persist_plan_destroy": ([V], None),
+        "emm_wave_workspace_size": ([V, C.POINTER(_Survey), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "emm_forward_wave": ([V, C.POINTER(_Survey), V, C.c_int, V, C.c_size_t, V, V], C.c_int),
         "emm_plan_create": ([V, C.POINTER(_Survey), V, V, C.c_size_t, V, V, V, C.POINTER(V)], C.c_int),
         "emm_plan_run": ([V, V, V], C.c_int),
         "emm_plan_destroy": ([V], None),
@@ -358,6 +361,49 @@ def forward_async(grid: Grid, survey: Survey, sigma, work: Workspace, stream=Non
         C.c_size_t(work.bytes), C.c_void_p(work.rec.data_ptr()),
         C.c_void_p(0 if work.vol is None else work.vol.data_ptr()), C.c_void_p(stream.cuda_stream))
     _check(code, "emm_forward")
+
+
+class WaveWork:
+    """Device buffers of ``forward_wave`` for one (grid, survey, depth)."""
+
+    def __init__(self, grid: Grid, survey: Survey, depth: int, device=None):
+        import torch
+        self.device = torch.device("cuda" if device is None else device)
+        s, keep = survey._c()
+        n = C.c_size_t(0)
+        _check(load_library().emm_wave_workspace_size(grid.handle, C.byref(s), int(depth), C.byref(n)),
+               "emm_wave_workspace_size")
+        self.depth, self.bytes = int(depth), n.value
+        self.ws = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ptr = self.ws.data_ptr() + (-self.ws.data_ptr()) % 256
+        self.rec = torch.zeros((max(survey.nrec, 1), 6, len(survey.freqs), 2), dtype=torch.float64,
+                               device=self.device)
+
+
+def forward_wave(grid: Grid, survey: Survey, sigma, depth: int = 2, work: Optional[WaveWork] = None,
+                 stream=None, check: bool = True):
+    """``emm_forward_wave``: the forward solve with ``depth`` time steps in
+    flight per sweep of the grid (a persistent launch whose tiles wait on
+    per-layer completion counts).  Returns (G complex128 [nrec][6][nfreq],
+    work); G equals ``forward``'s bit for bit."""
+    import torch
+    _check_sigma(grid, sigma)
+    if stream is None:
+        stream = torch.cuda.current_stream(sigma.device)
+    if work is None or work.depth != int(depth):
+        work = WaveWork(grid, survey, depth, sigma.device)
+    s, keep = survey._c()
+    _check(load_library().emm_forward_wave(grid.handle, C.byref(s), C.c_void_p(sigma.data_ptr()), int(depth),
+                                           C.c_void_p(work.ptr), C.c_size_t(work.bytes),
+                                           C.c_void_p(work.rec.data_ptr()), C.c_void_p(stream.cuda_stream)),
+           "emm_forward_wave")
+    if check:
+        v = C.c_int(0)
+        _check(load_library().emm_status(C.c_void_p(work.ptr), C.byref(v), C.c_void_p(stream.cuda_stream)),
+               "emm_status")
+        if v.value != EMM_OK:
+            raise EmmError(v.value, "emm_forward_wave (device status)")
+    return torch.view_as_complex(work.rec)[: survey.nrec], work
 
 
 def forward_converge(grid: Grid, survey: Survey, sigma, work: Workspace, stream=None) -> int:

@@ -829,10 +829,12 @@ __device__ __forceinline__ Blk reversed_tile(const DevParams &p, const Blk &b) {
 }
 
 // One CTA of the H half-step.
-template <int R, bool MULTI, bool CONV, int S = 0>
+// REV: walk the tiles in reverse launch order (a launch of its own); false
+// where a scheduler hands out the tiles itself.
+template <int R, bool MULTI, bool CONV, int S = 0, bool REV = true>
 __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk,
                                         unsigned phase = 0) {
-  const Blk b = blk.z < p.rec_layers ? blk : reversed_tile<MULTI>(p, blk);
+  const Blk b = (!REV || blk.z < p.rec_layers) ? blk : reversed_tile<MULTI>(p, blk);
   if (b.z < p.rec_layers) {
     const int rs = receiver_source<MULTI>(p, b);
     const Fields f = fields_of<MULTI>(p, rs);
@@ -1032,6 +1034,121 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_consta
         __syncthreads();  // the next item reuses the CTA's shared memory
       }
       if (!grid_barrier(S, ++gen)) return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wavefront solve: every leapfrog step of one problem in ONE persistent
+// launch, with several time steps in flight at once so that a z-layer of
+// tiles (all x-y tiles of one run of planes) is brought from DRAM once and
+// advanced by `depth` steps while it sits in L2.
+//
+// Work unit: a layer item (kind, step s, layer l) = the tiles of z-layer l
+// for the E half-step (kind 0) or the H half-step (kind 1) of step s, or
+// the receiver CTAs of the E half-step (kind 2, H^{s+1/2}) or of the H
+// half-step (kind 3, E^{s+1}); each has `T` CTA items.  The host writes the
+// layer items in a global order (sweeps of `depth` steps; within a sweep
+// the E items of step s0 + d on layer l sit at position l + K d and the H
+// items at l + K d + h), and every CTA claims the next CTA item with an
+// atomic counter.  A claimed item first waits -- thread 0, acquire loads,
+// bounded by wait_ns of %globaltimer -- for the layers it reads to be
+// complete, counted by monotone per-layer completion counters:
+//   E(s, l) reads H^{s+1/2} of layers l-a .. l+a:  cntH[l'] >= s T
+//           (and on receiver layers, R_E(s-1) done:  cntRE >= s RT)
+//   H(s, l) reads E^{s+1} of layers l-a .. l+a:    cntE[l'] >= (s+1) T
+//           (and on receiver layers, R_H(s) done:  cntRH >= (s+1) RT)
+//   R_E(s): cntE[l'] >= (s+1) T on the receiver layers la .. lb
+//   R_H(s): cntH[l'] >= s T on the receiver layers
+// where a = layers of the z halo and RT the CTA items of one step's
+// receivers.  Every dependency lies at an earlier position of the order, so
+// the earliest unfinished item can always proceed (all CTAs are resident:
+// a cooperative launch).  Completion: proxy fence, release fence, add to
+// the item's counter.  Each tile runs e_block / h_block, so the results
+// equal emm_forward's bit for bit.
+// ---------------------------------------------------------------------------
+struct WaveSet {
+  TmaSet tmE, tmH;
+  DevParams p;
+  const unsigned *order;       // layer items: kind | layer << 2 | step << 14
+  long long nitems;            // CTA items in all
+  int T, RT;                   // CTA items of a layer item; of one step's receivers (rec_layers * T)
+  int a, la, lb, L;            // halo layers; receiver layers la .. lb; layers
+  unsigned *cntE, *cntH;       // [L] completed tiles per layer (monotone over the steps)
+  unsigned *cntR;              // [2]: completed receiver items of the E half-steps (kind 2), of the H half-steps (kind 3)
+  unsigned long long *claim;   // next CTA item
+  int *abort, *status;
+  unsigned long long wait_ns;
+};
+
+// Thread 0: wait until counter >= target, bounded; false if the wait ran
+// out (status and abort set) or another CTA gave up.
+__device__ __forceinline__ bool wait_count(const WaveSet &W, const unsigned *c, unsigned target,
+                                           unsigned long long t0) {
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire_u32(c) >= target) return true;
+    if (*reinterpret_cast<volatile const int *>(W.abort)) return false;
+    if ((it & 15u) == 0 && global_ns() - t0 > W.wait_ns) {
+      atomicExch(W.status, EMM_ETIMEOUT);
+      atomicExch(W.abort, 1);
+      return false;
+    }
+    __nanosleep(20);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, min_ctas(R)) k_wave(const __grid_constant__ WaveSet W) {
+  __shared__ long long s_idx;
+  const DevParams &p = W.p;
+  const unsigned T = static_cast<unsigned>(W.T), RT = static_cast<unsigned>(W.RT);
+  unsigned tiles = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = static_cast<long long>(atomicAdd(W.claim, 1ull));
+    __syncthreads();
+    const long long idx = s_idx;
+    if (idx >= W.nitems) return;
+    const unsigned code = W.order[idx / W.T];
+    const int t = static_cast<int>(idx % W.T);
+    const int kind = static_cast<int>(code & 3u), l = static_cast<int>((code >> 2) & 4095u);
+    const int st = static_cast<int>(code >> 14);
+    int ok = 1;
+    if (threadIdx.x == 0) {
+      const unsigned long long t0 = global_ns();
+      const bool rl = l >= W.la && l <= W.lb;
+      if (kind == 0) {
+        // H^{s+1/2} of the halo layers, and (receiver layers) the previous
+        // step's E receivers done before E^{s} is overwritten
+        for (int q = max(0, l - W.a); ok && q <= min(W.L - 1, l + W.a); ++q)
+          ok = wait_count(W, W.cntH + q, static_cast<unsigned>(st) * T, t0);
+        if (ok && rl) ok = wait_count(W, W.cntR + 0, static_cast<unsigned>(st) * RT, t0);
+      } else if (kind == 1) {
+        // E^{s+1} of the halo layers, and (receiver layers) this step's H
+        // receivers done before H^{s+1/2} is overwritten
+        for (int q = max(0, l - W.a); ok && q <= min(W.L - 1, l + W.a); ++q)
+          ok = wait_count(W, W.cntE + q, static_cast<unsigned>(st + 1) * T, t0);
+        if (ok && rl) ok = wait_count(W, W.cntR + 1, static_cast<unsigned>(st + 1) * RT, t0);
+      } else {
+        const unsigned *c = kind == 3 ? W.cntE : W.cntH;
+        const unsigned target = static_cast<unsigned>(kind == 3 ? st + 1 : st) * T;
+        for (int q = W.la; ok && q <= W.lb; ++q) ok = wait_count(W, c + q, target, t0);
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    if (!__syncthreads_and(ok)) return;
+    const Blk b{t % p.tiles_x, t / p.tiles_x, kind >= 2 ? l : p.rec_layers + l};
+    if (kind == 0 || kind == 2)
+      e_block<R, false, false, false, 0>(p, W.tmE, st, b, tiles);
+    else
+      h_block<R, false, false, 0, false>(p, W.tmH, st, b, tiles);
+    if (kind < 2) ++tiles;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __threadfence();
+      // receivers (kinds 2, 3) count in cntR[0] (E^{s+1} read: kind 3) and cntR[1] (kind 2)
+      unsigned *c = kind == 0 ? W.cntE + l : kind == 1 ? W.cntH + l : W.cntR + (kind == 3 ? 0 : 1);
+      red_release_add(c, 1u);
     }
   }
 }
@@ -2243,6 +2360,181 @@ int persist_finalize(const PersistRun &run, int nt, const emm_task *t, cudaStrea
   return EMM_OK;
 }
 
+// ---- wavefront solve (k_wave) ----
+// Workspace: the forward workspace, then the layer-item order (one unsigned
+// per layer item) and the counters (cntE[L], cntH[L], cntR[2], the claim
+// counter), 256-byte aligned.
+struct WaveGeom {
+  int L = 0, T = 0, RT = 0, a = 0, la = 0, lb = -1, K = 0, h = 0, rec_layers = 0;
+  size_t nlayer = 0;
+};
+
+int wave_geom(const emm_grid *g, const emm_survey *s, int depth, WaveGeom *w) {
+  const int st = check_survey(g, s);
+  if (st != EMM_OK) return st;
+  if (depth < 1 || depth > 64 || s->volume || s->airwave || s->src_kind != 0 || s->src_length > 0 ||
+      s->nt >= (1 << 18))
+    return EMM_EINVAL;
+  const FieldGeom fg = field_geom(g, 0);
+  const int rd = g->rd, zc = shape_zc(0);
+  w->L = fg.tiles[2];
+  w->T = fg.tiles[0] * fg.tiles[1];
+  if (w->L > 4095) return EMM_EINVAL;
+  w->a = (rd + zc - 1) / zc;
+  // receiver CTAs (one warp per receiver component, 4 warps a CTA), in
+  // layers of T CTA items, and the z-layers their stencils touch
+  const int rec_blocks = (s->nrec * 3 + NT / 32 - 1) / (NT / 32);
+  w->rec_layers = s->nrec > 0 ? (rec_blocks + w->T - 1) / w->T : 0;
+  w->RT = w->rec_layers * w->T;
+  if (s->nrec > 0) {
+    int kmin = 1 << 30, kmax = -1;
+    std::vector<double> wt(2 * static_cast<size_t>(rd));
+    for (int r = 0; r < s->nrec; ++r)
+      for (int c = 0; c < 6; ++c) {
+        int k0 = 0;
+        const int e = locate_axis(g, 2, kHalf[c][2], s->rec[3 * r + 2], &k0, wt.data());
+        if (e != EMM_OK) return e;
+        kmin = std::min(kmin, k0);
+        kmax = std::max(kmax, k0 + 2 * rd - 1);
+      }
+    w->la = (kmin - fg.org[2]) / zc;
+    w->lb = (kmax - fg.org[2]) / zc;
+  }
+  w->h = w->a + 1;
+  w->K = std::max(2 * w->a + 2, w->lb - w->la + 2);
+  // layer items: per step L E items, L H items and 2 rec_layers receiver items
+  w->nlayer = static_cast<size_t>(s->nt) * (2 * static_cast<size_t>(w->L) + 2 * w->rec_layers);
+  (void)depth;
+  return EMM_OK;
+}
+
+size_t wave_extra_bytes(const WaveGeom &w) {
+  // counters: cntE[L], cntH[L], cntR[2], the 8-byte claim counter, the abort word
+  return align_up(w.nlayer * sizeof(unsigned)) + align_up((2 * static_cast<size_t>(w.L) + 2) * sizeof(unsigned) + 16);
+}
+
+// The global order of the layer items: sweeps of `depth` steps; in a sweep
+// starting at step s0, position q holds (in this order) the H receivers of
+// step s0 + d if q == la + K d + h - 1, E(s0 + d, q - K d), H(s0 + d, q - K d
+// - h) and the E receivers of step s0 + d if q == lb + K d + 1, for every d.
+void wave_order(const WaveGeom &w, int nt, int depth, std::vector<unsigned> *out) {
+  out->clear();
+  out->reserve(w.nlayer);
+  auto put = [&](int kind, int l, int s) {
+    out->push_back(static_cast<unsigned>(kind) | (static_cast<unsigned>(l) << 2) | (static_cast<unsigned>(s) << 14));
+  };
+  for (int s0 = 0; s0 < nt; s0 += depth) {
+    const int D = std::min(depth, nt - s0);
+    const int qmax = w.L - 1 + w.K * (D - 1) + w.h;
+    for (int q = 0; q <= qmax; ++q)
+      for (int d = 0; d < D; ++d) {
+        const int s = s0 + d;
+        if (w.rec_layers && q == w.la + w.K * d + w.h - 1)
+          for (int r = 0; r < w.rec_layers; ++r) put(2, r, s);
+        const int le = q - w.K * d, lh = q - w.K * d - w.h;
+        if (le >= 0 && le < w.L) put(0, le, s);
+        if (lh >= 0 && lh < w.L) put(1, lh, s);
+        if (w.rec_layers && q == w.lb + w.K * d + 1)
+          for (int r = 0; r < w.rec_layers; ++r) put(3, r, s);
+      }
+  }
+}
+
+struct WaveRun {
+  Prepared P;
+  std::unique_ptr<WaveSet> W;
+  unsigned ctas = 0;
+  size_t smem = 0;
+};
+
+template <int R>
+cudaError_t wave_shape(WaveRun *run) {
+  const size_t sb = smem_bytes<R>();
+  cudaError_t e = cudaFuncSetAttribute(k_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<R>, NT, sb);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  run->ctas = static_cast<unsigned>(per_sm * run->P.sms);
+  run->smem = sb;
+  WaveSet &W = *run->W;
+  if (!make_tiles<R>(&W.tmE, W.p.H, W.p) || !make_tiles<R>(&W.tmH, W.p.E, W.p)) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+int wave_prepare(const emm_grid *g, const emm_survey *s, const float *sigma, int depth, void *ws, size_t ws_bytes,
+                 double *rec_out, cudaStream_t cs, WaveRun *run) {
+  WaveGeom w;
+  int st = wave_geom(g, s, depth, &w);
+  if (st != EMM_OK) return st;
+  const size_t fwd = align_up(plan(g, s).total);
+  if (!ws || ws_bytes < fwd + wave_extra_bytes(w) || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return EMM_EWORKSPACE;
+  std::vector<unsigned> order;
+  try {
+    wave_order(w, s->nt, depth, &order);
+  } catch (const std::bad_alloc &) {
+    return EMM_ENOMEM;
+  }
+  if (order.size() != w.nlayer) return EMM_EINVAL;
+  st = prepare_forward(g, s, sigma, ws, fwd, rec_out, nullptr, cs, &run->P);
+  if (st != EMM_OK) return st;
+  if (run->P.p.rec_layers != w.rec_layers || run->P.p.tiles_z != w.L) return EMM_EINVAL;
+  unsigned char *base = static_cast<unsigned char *>(ws) + fwd;
+  unsigned *ord = reinterpret_cast<unsigned *>(base);
+  unsigned *cnt = reinterpret_cast<unsigned *>(base + align_up(w.nlayer * sizeof(unsigned)));
+  const size_t cnt_bytes = (2 * static_cast<size_t>(w.L) + 2) * sizeof(unsigned) + 8 + 8;  // + claim + abort
+  cudaError_t e = cudaMemcpyAsync(ord, order.data(), order.size() * sizeof(unsigned), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, align_up(cnt_bytes), cs);
+  if (e != cudaSuccess) return EMM_ECUDA;
+  run->W.reset(new (std::nothrow) WaveSet{});
+  if (!run->W) return EMM_ENOMEM;
+  WaveSet &W = *run->W;
+  W.p = run->P.p;
+  W.order = ord;
+  W.T = w.T;
+  W.RT = w.RT;
+  W.nitems = static_cast<long long>(w.nlayer) * w.T;
+  W.a = w.a;
+  W.la = w.la;
+  W.lb = w.lb;
+  W.L = w.L;
+  W.cntE = cnt;
+  W.cntH = cnt + w.L;
+  W.cntR = cnt + 2 * w.L;
+  W.claim = reinterpret_cast<unsigned long long *>(cnt + 2 * w.L + 2);
+  W.status = W.p.status;
+  W.abort = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(W.claim) + 8);  // after the claim counter
+  W.p.abort = W.abort;
+  W.wait_ns = 1000000000ull;
+  switch (run->P.rd) {
+    case 1: e = wave_shape<1>(run); break;
+    case 2: e = wave_shape<2>(run); break;
+    case 3: e = wave_shape<3>(run); break;
+    default: e = wave_shape<4>(run); break;
+  }
+  return e == cudaSuccess ? EMM_OK : EMM_ECUDA;
+}
+
+cudaError_t wave_launch(const WaveRun &run, cudaStream_t cs) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(run.ctas);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = run.smem;
+  cfg.stream = cs;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (run.P.rd) {
+    case 1: return cudaLaunchKernelEx(&cfg, k_wave<1>, *run.W);
+    case 2: return cudaLaunchKernelEx(&cfg, k_wave<2>, *run.W);
+    case 3: return cudaLaunchKernelEx(&cfg, k_wave<3>, *run.W);
+    default: return cudaLaunchKernelEx(&cfg, k_wave<4>, *run.W);
+  }
+}
+
 int finalize_forward(const Prepared &P, const emm_survey *s, double *rec_out, double *vol_out, cudaStream_t cs) {
   const int nf = s->nfreq;
   const double *dnorm = reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(P.p.status) -
@@ -2477,6 +2769,25 @@ int emm_forward_jobs(int njobs, const emm_job *jobs, int strategy, void *ws, siz
 int emm_jobs_tune(int njobs, const emm_job *jobs, void *ws, size_t ws_bytes, int steps, emm_stream stream,
                   double *ms, int *best) {
   return emm::jobs_tune(njobs, jobs, ws, ws_bytes, steps, reinterpret_cast<cudaStream_t>(stream), ms, best);
+}
+
+int emm_wave_workspace_size(const emm_grid *g, const emm_survey *s, int depth, size_t *bytes) {
+  if (!bytes) return EMM_EINVAL;
+  emm::WaveGeom w;
+  const int st = emm::wave_geom(g, s, depth, &w);
+  if (st != EMM_OK) return st;
+  *bytes = emm::align_up(emm::plan(g, s).total) + emm::wave_extra_bytes(w);
+  return EMM_OK;
+}
+
+int emm_forward_wave(const emm_grid *g, const emm_survey *s, const float *sigma, int depth, void *ws,
+                     size_t ws_bytes, double *rec_out, emm_stream stream) {
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  emm::WaveRun run;
+  int st = emm::wave_prepare(g, s, sigma, depth, ws, ws_bytes, rec_out, cs, &run);
+  if (st != EMM_OK) return st;
+  if (emm::wave_launch(run, cs) != cudaSuccess) return EMM_ECUDA;
+  return emm::finalize_forward(run.P, s, rec_out, nullptr, cs);
 }
 
 int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes, size_t *offsets) {

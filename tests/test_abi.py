@@ -157,6 +157,28 @@ def test_persistent_work_list_layout_and_errors():
     assert lib.emm_persist_plan_run(None, None) == emm.EMM_EINVAL
 
 
+def test_wave_workspace_and_refusals():
+    from paper_2304_00233_b300 import workloads as W
+    C = emm.C
+    lib = emm.load_library()
+    wl = W.small_case(n=(24, 22, 20), rd=2, nt=30, volume=False)
+    g, s = emm.grid_for(wl), emm.survey_for(wl)
+    n1, n2 = C.c_size_t(0), C.c_size_t(0)
+    sc, k = s._c()
+    assert lib.emm_wave_workspace_size(g.handle, C.byref(sc), 1, C.byref(n1)) == emm.EMM_OK
+    assert lib.emm_wave_workspace_size(g.handle, C.byref(sc), 4, C.byref(n2)) == emm.EMM_OK
+    # the forward workspace, then the tile order and the counters
+    assert n1.value == n2.value > emm.workspace_size(g, s)
+    for depth in (0, 65):
+        assert lib.emm_wave_workspace_size(g.handle, C.byref(sc), depth, C.byref(n1)) == emm.EMM_EINVAL
+    wv = W.small_case(n=(24, 22, 20), rd=2, nt=30, volume=True)
+    sv, kv = emm.survey_for(wv)._c()
+    assert lib.emm_wave_workspace_size(g.handle, C.byref(sv), 2, C.byref(n1)) == emm.EMM_EINVAL
+    # no workspace: refused before anything is enqueued
+    assert lib.emm_forward_wave(g.handle, C.byref(sc), None, 2, None, 0, None, None) in (emm.EMM_EWORKSPACE,
+                                                                                          emm.EMM_EINVAL)
+
+
 def test_new_entry_points_refuse_bad_arguments_on_the_host():
     C = emm.C
     lib = emm.load_library()
