@@ -1081,18 +1081,26 @@ struct WaveSet {
   unsigned long long wait_ns;
 };
 
-// Thread 0: wait until counter >= target, bounded; false if the wait ran
-// out (status and abort set) or another CTA gave up.
-__device__ __forceinline__ bool wait_count(const WaveSet &W, const unsigned *c, unsigned target,
-                                           unsigned long long t0) {
+// Warp 0: wait until every counter a lane names is at least its target
+// (lanes 0 .. n-1 each load one, all in flight at once), bounded; false if
+// the wait ran out (status and abort set) or another CTA gave up.
+__device__ __forceinline__ bool wait_counts(const WaveSet &W, const unsigned *c, unsigned target, int n) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long t0 = global_ns();
   for (unsigned it = 0;; ++it) {
-    if (ld_acquire_u32(c) >= target) return true;
-    if (*reinterpret_cast<volatile const int *>(W.abort)) return false;
-    if ((it & 15u) == 0 && global_ns() - t0 > W.wait_ns) {
-      atomicExch(W.status, EMM_ETIMEOUT);
-      atomicExch(W.abort, 1);
-      return false;
+    const bool sat = lane >= n || ld_acquire_u32(c) >= target;
+    if (__all_sync(0xffffffffu, sat)) return true;
+    int stop = 0;
+    if (lane == 0) {
+      if (*reinterpret_cast<volatile const int *>(W.abort)) {
+        stop = 1;
+      } else if ((it & 15u) == 0 && global_ns() - t0 > W.wait_ns) {
+        atomicExch(W.status, EMM_ETIMEOUT);
+        atomicExch(W.abort, 1);
+        stop = 1;
+      }
     }
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
     __nanosleep(20);
   }
 }
@@ -1103,9 +1111,9 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_wave(const __grid_constant_
   const DevParams &p = W.p;
   const unsigned T = static_cast<unsigned>(W.T), RT = static_cast<unsigned>(W.RT);
   unsigned tiles = 0;
+  if (threadIdx.x == 0) s_idx = static_cast<long long>(atomicAdd(W.claim, 1ull));
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_idx = static_cast<long long>(atomicAdd(W.claim, 1ull));
-    __syncthreads();
     const long long idx = s_idx;
     if (idx >= W.nitems) return;
     const unsigned code = W.order[idx / W.T];
@@ -1113,29 +1121,40 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_wave(const __grid_constant_
     const int kind = static_cast<int>(code & 3u), l = static_cast<int>((code >> 2) & 4095u);
     const int st = static_cast<int>(code >> 14);
     int ok = 1;
-    if (threadIdx.x == 0) {
-      const unsigned long long t0 = global_ns();
-      const bool rl = l >= W.la && l <= W.lb;
-      if (kind == 0) {
-        // H^{s+1/2} of the halo layers, and (receiver layers) the previous
-        // step's E receivers done before E^{s} is overwritten
-        for (int q = max(0, l - W.a); ok && q <= min(W.L - 1, l + W.a); ++q)
-          ok = wait_count(W, W.cntH + q, static_cast<unsigned>(st) * T, t0);
-        if (ok && rl) ok = wait_count(W, W.cntR + 0, static_cast<unsigned>(st) * RT, t0);
-      } else if (kind == 1) {
-        // E^{s+1} of the halo layers, and (receiver layers) this step's H
-        // receivers done before H^{s+1/2} is overwritten
-        for (int q = max(0, l - W.a); ok && q <= min(W.L - 1, l + W.a); ++q)
-          ok = wait_count(W, W.cntE + q, static_cast<unsigned>(st + 1) * T, t0);
-        if (ok && rl) ok = wait_count(W, W.cntR + 1, static_cast<unsigned>(st + 1) * RT, t0);
+    if (threadIdx.x < 32) {
+      // the layers this item reads, one counter per lane:
+      //   E(s, l): H^{s+1/2} of layers l-a .. l+a (cntH >= s T), and on the
+      //            receiver layers the previous step's E receivers (cntR[0] >= s RT)
+      //   H(s, l): E^{s+1} of layers l-a .. l+a (cntE >= (s+1) T), and on the
+      //            receiver layers this step's H receivers (cntR[1] >= (s+1) RT)
+      //   receivers: the receiver layers la .. lb of E^{s+1} (kind 3) or H^{s+1/2} (kind 2)
+      const int lane = threadIdx.x;
+      const unsigned *c = W.cntE;
+      unsigned target = 0;
+      int n = 0;
+      if (kind < 2) {
+        const int lo = max(0, l - W.a), hi = min(W.L - 1, l + W.a);
+        const bool rl = l >= W.la && l <= W.lb;
+        n = hi - lo + 1 + (rl ? 1 : 0);
+        if (lane <= hi - lo) {
+          c = (kind == 0 ? W.cntH : W.cntE) + lo + lane;
+          target = static_cast<unsigned>(kind == 0 ? st : st + 1) * T;
+        } else {
+          c = W.cntR + (kind == 0 ? 0 : 1);
+          target = static_cast<unsigned>(kind == 0 ? st : st + 1) * RT;
+        }
       } else {
-        const unsigned *c = kind == 3 ? W.cntE : W.cntH;
-        const unsigned target = static_cast<unsigned>(kind == 3 ? st + 1 : st) * T;
-        for (int q = W.la; ok && q <= W.lb; ++q) ok = wait_count(W, c + q, target, t0);
+        n = W.lb - W.la + 1;
+        c = (kind == 3 ? W.cntE : W.cntH) + W.la + min(lane, n - 1);
+        target = static_cast<unsigned>(kind == 3 ? st + 1 : st) * T;
       }
-      asm volatile("fence.proxy.async.global;" ::: "memory");
+      ok = wait_counts(W, c, target, n) ? 1 : 0;
+      if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     if (!__syncthreads_and(ok)) return;
+    // the next item is claimed now; its index is needed only after this one
+    unsigned long long nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(W.claim, 1ull);
     const Blk b{t % p.tiles_x, t / p.tiles_x, kind >= 2 ? l : p.rec_layers + l};
     if (kind == 0 || kind == 2)
       e_block<R, false, false, false, 0>(p, W.tmE, st, b, tiles);
@@ -1144,12 +1163,12 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_wave(const __grid_constant_
     if (kind < 2) ++tiles;
     __syncthreads();
     if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      __threadfence();
-      // receivers (kinds 2, 3) count in cntR[0] (E^{s+1} read: kind 3) and cntR[1] (kind 2)
+      // receivers count in cntR[0] (kind 3, E^{s+1}) and cntR[1] (kind 2, H^{s+1/2})
       unsigned *c = kind == 0 ? W.cntE + l : kind == 1 ? W.cntH + l : W.cntR + (kind == 3 ? 0 : 1);
       red_release_add(c, 1u);
+      s_idx = static_cast<long long>(nxt);
     }
+    __syncthreads();
   }
 }
 
