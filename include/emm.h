@@ -164,6 +164,12 @@ typedef struct {
                            positions), through the 2-D DFT of the padded plane.
                            Needs uniform x and y spacing (EMM_EINVAL) and source
                            stencils below the interface (EMM_EOUTSIDE). */
+  int tile_shape;       /* stencil tile of one CTA of the E and H launches, 128
+                           threads each: 0 = 32 x 8 x 2 cells (x, y, z), 1 =
+                           32 x 4 x 4.  Used by emm_forward, emm_forward_timed,
+                           emm_forward_static, emm_forward_batch and the plans;
+                           convergence runs, gradients, work lists and the
+                           wavefront take 0.  Results do not depend on it. */
 } emm_survey;
 
 /* Device workspace bytes emm_forward needs for this grid and survey

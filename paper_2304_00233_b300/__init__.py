@@ -77,7 +77,8 @@ class _Survey(C.Structure):
                 ("src_az", C.c_double), ("src_dip", C.c_double), ("moment", C.c_double),
                 ("nrec", C.c_int), ("rec", _D), ("nfreq", C.c_int), ("freqs", _D),
                 ("volume", C.c_int), ("src_kind", C.c_int),
-                ("src_length", C.c_double), ("src_points", C.c_int), ("airwave", C.c_int)]
+                ("src_length", C.c_double), ("src_points", C.c_int), ("airwave", C.c_int),
+                ("tile_shape", C.c_int)]
 
 
 class _Job(C.Structure):
@@ -288,6 +289,7 @@ class Survey:
     src_length: float = 0.0    # > 0: an antenna of this length (m), as src_points sub-dipoles
     src_points: int = 1
     airwave: bool = False      # air above the top interior node (needs uniform x, y)
+    tile_shape: int = 0        # stencil tile: 0 = 32 x 8 x 2 cells, 1 = 32 x 4 x 4
 
     def _c(self) -> Tuple[_Survey, list]:
         rec = _f64(np.zeros((0, 3)) if self.rec is None else self.rec).reshape(-1, 3)
@@ -305,6 +307,7 @@ class Survey:
         s.src_kind = int(self.src_kind)
         s.src_length, s.src_points = float(self.src_length), int(self.src_points)
         s.airwave = int(bool(self.airwave))
+        s.tile_shape = int(self.tile_shape)
         return s, [rec, freqs]   # the arrays must outlive every use of the struct
 
     @property

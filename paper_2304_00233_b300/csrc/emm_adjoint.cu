@@ -621,7 +621,7 @@ int gradient_impl(const emm_grid *g, const emm_survey *s, const float *sigma, co
   const AdjLayout A = adj_plan(g, s, K, S);
   if (ws_bytes < A.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return EMM_EWORKSPACE;
   Prepared P;
-  st = prepare_forward(g, s, sigma, ws, A.fwd, rec_out, nullptr, cs, &P);
+  st = prepare_forward(g, s, sigma, ws, A.fwd, rec_out, nullptr, cs, &P, 1, nullptr, false, true, 0);
   if (st != EMM_OK) return st;
   unsigned char *base = static_cast<unsigned char *>(ws);
   const Layout &L = P.L;

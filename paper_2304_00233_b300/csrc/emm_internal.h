@@ -180,10 +180,12 @@ struct Prepared {
 // upload_tables false: the tables are already in the workspace (a repeat of
 // an earlier prepare of the same problem); nothing reads host memory after
 // the call, so the enqueued work can be captured in a CUDA graph.
+// shape: the stencil tile shape of the launches (-1: survey->tile_shape; a
+// convergence run takes shape 0).
 int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, void *ws, size_t ws_bytes,
                     double *rec_out, double *vol_out, cudaStream_t cs, Prepared *out, int nsrc = 1,
                     const double *src_pos = nullptr, bool converge = false, bool upload_tables = true,
-                    int shape = 0);
+                    int shape = -1);
 // Enqueue the leapfrog steps n0 .. n1-1 with launch parameters p on grid `blocks`.
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te);

@@ -665,13 +665,13 @@ __device__ __forceinline__ void e_block(const DevParams &p, const TmaSet &tm, co
 
 // The E half-step of one problem; every launch of a convergence run returns
 // at once after the stop.
-template <int R, bool MULTI, bool CONV, bool OUT>
+template <int R, bool MULTI, bool CONV, bool OUT, int S = 0>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_E(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
   if (CONV && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
-  e_block<R, MULTI, CONV, OUT>(p, tm, n, launch_blk());
+  e_block<R, MULTI, CONV, OUT, S>(p, tm, n, launch_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -874,13 +874,13 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
     h_quad<R, false, S>(p, f, v, u, h, ps, n, cf);
 }
 
-template <int R, bool MULTI, bool CONV>
+template <int R, bool MULTI, bool CONV, int S = 0>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
   if (CONV && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
-  h_block<R, MULTI, CONV>(p, tm, n, launch_blk());
+  h_block<R, MULTI, CONV, S>(p, tm, n, launch_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -934,10 +934,10 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_update_H_jobs(const __grid_
 // ---------------------------------------------------------------------------
 // Persistent work list: every leapfrog step of several problems -- each a
 // grid with one transmitter or a batch of them sharing grid and
-// conductivity -- in ONE cooperative launch.  The resident CTAs walk the E
-// half-step's items (every problem's tiles and receiver CTAs; CTA b takes
-// items b, b + G, b + 2G, ...), meet at a grid barrier, walk the H
-// half-step's items, meet again, and so on for every step.  An item runs
+// conductivity -- in ONE cooperative launch.  The resident CTAs take the E
+// half-step's items (every problem's tiles and receiver CTAs) in order from
+// a claim counter, meet at a grid barrier, take the H half-step's items,
+// meet again, and so on for every step.  An item runs
 // the same per-CTA code as the problem's own launch would (e_block /
 // h_block), so each problem's results equal its own solve's bit for bit.
 // The barrier is an arrival counter in the workspace that only grows: a CTA
@@ -958,6 +958,7 @@ struct PSet {
   int cta0[kMaxTasks + 1];  // first item of each problem, then the total
   int njobs, nt_max;
   unsigned *bar;            // arrivals so far (zeroed before the launch)
+  unsigned long long *claim;  // items claimed so far (zeroed before the launch)
   int *abort;               // nonzero once a wait ran out
   int *status;              // the work list's status word
   unsigned long long wait_ns;
@@ -1011,12 +1012,26 @@ __device__ __forceinline__ bool grid_barrier(const PSet &S, unsigned gen) {
 
 template <int R, int SH>
 __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_constant__ PSet S) {
+  __shared__ long long s_b;
   const int total = S.cta0[S.njobs];
   unsigned gen = 0, tiles = 0;  // tiles: stencil tiles this CTA ran (the mbarrier's phase)
+  // Items are claimed in order from one counter (the next one while the
+  // current one runs), so faster CTAs take more of them.  Every CTA's last
+  // claim of a half-step is the one past its end, so half-step k's claims
+  // start at k (total + G).
+  const long long per_phase = static_cast<long long>(total) + gridDim.x;
   for (int n = 0; n < S.nt_max; ++n) {
     for (int half = 0; half < 2; ++half) {
+      const long long base = (2LL * n + half) * per_phase;
+      if (threadIdx.x == 0) s_b = static_cast<long long>(atomicAdd(S.claim, 1ull)) - base;
+      __syncthreads();
       int j = 0;
-      for (int b = static_cast<int>(blockIdx.x); b < total; b += static_cast<int>(gridDim.x)) {
+      for (;;) {
+        const long long bl = s_b;
+        if (bl >= total) break;
+        const int b = static_cast<int>(bl);
+        long long nxt = 0;
+        if (threadIdx.x == 0) nxt = static_cast<long long>(atomicAdd(S.claim, 1ull)) - base;
         while (j + 1 < S.njobs && b >= S.cta0[j + 1]) ++j;
         const PJob &J = S.job[j];
         if (n < J.nt) {
@@ -1032,6 +1047,8 @@ __global__ void __launch_bounds__(NT, min_ctas(R)) k_persist(const __grid_consta
           if (blk.z >= J.p.rec_layers) ++tiles;  // receiver items use no tiles
         }
         __syncthreads();  // the next item reuses the CTA's shared memory
+        if (threadIdx.x == 0) s_b = nxt;
+        __syncthreads();
       }
       if (!grid_barrier(S, ++gen)) return;
     }
@@ -1598,6 +1615,7 @@ int check_survey(const emm_grid *g, const emm_survey *s) {
       (s->src_length > 0 && (s->src_points < 1 || s->src_points > 256)))
     return EMM_EINVAL;
   if (s->airwave != 0 && s->airwave != 1) return EMM_EINVAL;
+  if (s->tile_shape != 0 && s->tile_shape != 1) return EMM_EINVAL;
   return EMM_OK;
 }
 
@@ -1652,20 +1670,20 @@ cudaError_t air_step(const DevParams &p, cudaStream_t st) {
 
 // OUT: one step whose E^{n+1} goes to p.Eout; the launches after the E
 // half-step see it there.
-template <int R, bool MULTI, bool CONV, bool OUT = false>
+template <int R, bool MULTI, bool CONV, bool OUT = false, int S = 0>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   if (OUT && (MULTI || CONV || n1 - n0 != 1)) return cudaErrorInvalidValue;
   DevParams q = p;
   if (OUT)
     for (int a = 0; a < 3; ++a) q.E[a] = p.Eout[a];
   TmaSet tE{}, tH{};
-  if (!make_tiles<R>(&tE, p.H, p) || !make_tiles<R>(&tH, q.E, p)) return cudaErrorInvalidValue;
-  const size_t sb = smem_bytes<R>();
+  if (!make_tiles<R, S>(&tE, p.H, p) || !make_tiles<R, S>(&tH, q.E, p)) return cudaErrorInvalidValue;
+  const size_t sb = smem_bytes<R, S>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_update_E<R, MULTI, CONV, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_update_E<R, MULTI, CONV, OUT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sb));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_update_H<R, MULTI, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_update_H<R, MULTI, CONV, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sb));
   if (e != cudaSuccess) return e;
   // each half-step is launched as a programmatic dependent of the one before
@@ -1677,14 +1695,14 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
     const bool timed = te && te->every > 0 && (n % te->every) == 0 && used + 4 <= te->ev.size();
     if (timed) cudaEventRecord(te->ev[used], st);
-    e = launch_dependent(k_update_E<R, MULTI, CONV, OUT>, blocks, dim3(NT), sb, st, p, tE, n);
+    e = launch_dependent(k_update_E<R, MULTI, CONV, OUT, S>, blocks, dim3(NT), sb, st, p, tE, n);
     if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
       e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(q, st);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
     if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, q, n);
     if (timed) cudaEventRecord(te->ev[used + 2], st);
-    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV>, blocks, dim3(NT), sb, st, q, tH, n);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV, S>, blocks, dim3(NT), sb, st, q, tH, n);
     if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(q, st);
     if (timed) {
@@ -1939,6 +1957,7 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     p.cp[a] = reinterpret_cast<const float *>(base + L.cp[a]);
     p.pml[a] = reinterpret_cast<const float *>(base + L.pml[a]);
   }
+  if (shape < 0) shape = converge ? 0 : s->tile_shape;  // convergence runs keep the 32 x 8 x 2 tiles
   if (shape < 0 || shape >= kShapes) return EMM_EINVAL;
   const FieldGeom fg = field_geom(g, shape);
   p.pitch = fg.pitch;
@@ -2043,21 +2062,26 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
 
 // The launch variants of one order: one transmitter; a batch; a convergence
 // run; one step into another E buffer.
-template <int R>
+template <int R, int S>
 cudaError_t run_order(const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs, StepEvents *te) {
-  if (p.Eout[0]) return launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te);
-  if (p.nsrc > 1) return launch_steps<R, true, false>(p, n0, n1, blocks, cs, te);
-  if (p.corner) return launch_steps<R, false, true>(p, n0, n1, blocks, cs, te);
-  return launch_steps<R, false, false>(p, n0, n1, blocks, cs, te);
+  // the gradient's one-step runs and convergence runs use the 32 x 8 x 2 tiles
+  if (p.Eout[0]) return S == 0 ? launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te) : cudaErrorInvalidValue;
+  if (p.nsrc > 1) return launch_steps<R, true, false, false, S>(p, n0, n1, blocks, cs, te);
+  if (p.corner) return S == 0 ? launch_steps<R, false, true>(p, n0, n1, blocks, cs, te) : cudaErrorInvalidValue;
+  return launch_steps<R, false, false, false, S>(p, n0, n1, blocks, cs, te);
 }
 
 cudaError_t run_steps(const Prepared &P, const DevParams &p, dim3 blocks, int n0, int n1, cudaStream_t cs,
                       StepEvents *te) {
-  switch (P.rd) {
-    case 1: return run_order<1>(p, blocks, n0, n1, cs, te);
-    case 2: return run_order<2>(p, blocks, n0, n1, cs, te);
-    case 3: return run_order<3>(p, blocks, n0, n1, cs, te);
-    default: return run_order<4>(p, blocks, n0, n1, cs, te);
+  switch (2 * P.rd + P.shape) {
+    case 2: return run_order<1, 0>(p, blocks, n0, n1, cs, te);
+    case 3: return run_order<1, 1>(p, blocks, n0, n1, cs, te);
+    case 4: return run_order<2, 0>(p, blocks, n0, n1, cs, te);
+    case 5: return run_order<2, 1>(p, blocks, n0, n1, cs, te);
+    case 6: return run_order<3, 0>(p, blocks, n0, n1, cs, te);
+    case 7: return run_order<3, 1>(p, blocks, n0, n1, cs, te);
+    case 8: return run_order<4, 0>(p, blocks, n0, n1, cs, te);
+    default: return run_order<4, 1>(p, blocks, n0, n1, cs, te);
   }
 }
 
@@ -2171,7 +2195,7 @@ int prepare_jobs(int nj, const emm_job *jobs, void *ws, size_t ws_bytes, cudaStr
   for (int j = 0; j < nj; ++j) {
     const size_t end = j + 1 < nj ? off[j + 1] : total;
     st = prepare_forward(jobs[j].grid, jobs[j].survey, jobs[j].sigma, base + off[j], end - off[j], jobs[j].rec_out,
-                         nullptr, cs, &(*P)[j]);
+                         nullptr, cs, &(*P)[j], 1, nullptr, false, true, 0);
     if (st != EMM_OK) return st;
     (*nts)[j] = jobs[j].survey->nt;
   }
@@ -2234,7 +2258,7 @@ int jobs_tune(int nj, const emm_job *jobs, void *ws, size_t ws_bytes, int steps,
 // Workspace: a 256-byte header (status word at 0, so emm_status(ws) reads
 // the work list's status; abort word; arrival counter), then each task's
 // forward workspace, 256-byte aligned.
-constexpr size_t kPHdrStatus = 0, kPHdrAbort = 4, kPHdrBar = 8;
+constexpr size_t kPHdrStatus = 0, kPHdrAbort = 4, kPHdrBar = 8, kPHdrClaim = 16;
 
 int persist_layout(int nt, const emm_task *t, std::vector<size_t> *off, size_t *total) {
   if (nt < 1 || nt > kMaxTasks || !t) return EMM_EINVAL;
@@ -2327,6 +2351,7 @@ int persist_prepare(int nt, const emm_task *t, const emm_persist_opts *opts, voi
   S.status = reinterpret_cast<int *>(base + kPHdrStatus);
   S.abort = reinterpret_cast<int *>(base + kPHdrAbort);
   S.bar = reinterpret_cast<unsigned *>(base + kPHdrBar);
+  S.claim = reinterpret_cast<unsigned long long *>(base + kPHdrClaim);
   for (int j = 0; j < nt; ++j) S.job[j].p.abort = S.abort;  // a tile wait that runs out stops the run
   S.wait_ns = static_cast<unsigned long long>((o.wait_s > 0 ? o.wait_s : 1.0) * 1e9);
   S.skip = o.skip_arrival;
@@ -2388,7 +2413,10 @@ struct WaveGeom {
   size_t nlayer = 0;
 };
 
-int wave_geom(const emm_grid *g, const emm_survey *s, int depth, WaveGeom *w) {
+// gap: extra positions between an item and the items it waits for, so that
+// with G CTAs in flight (about G / T layer items) a claimed item rarely finds
+// its inputs still being computed; it changes the order, not the sizes.
+int wave_geom(const emm_grid *g, const emm_survey *s, int depth, WaveGeom *w, int gap = 0) {
   const int st = check_survey(g, s);
   if (st != EMM_OK) return st;
   if (depth < 1 || depth > 64 || s->volume || s->airwave || s->src_kind != 0 || s->src_length > 0 ||
@@ -2419,8 +2447,8 @@ int wave_geom(const emm_grid *g, const emm_survey *s, int depth, WaveGeom *w) {
     w->la = (kmin - fg.org[2]) / zc;
     w->lb = (kmax - fg.org[2]) / zc;
   }
-  w->h = w->a + 1;
-  w->K = std::max(2 * w->a + 2, w->lb - w->la + 2);
+  w->h = w->a + 1 + gap;
+  w->K = std::max(w->a + w->h + 1 + gap, w->lb - w->la + 2 + gap);
   // layer items: per step L E items, L H items and 2 rec_layers receiver items
   w->nlayer = static_cast<size_t>(s->nt) * (2 * static_cast<size_t>(w->L) + 2 * w->rec_layers);
   (void)depth;
@@ -2486,6 +2514,16 @@ int wave_prepare(const emm_grid *g, const emm_survey *s, const float *sigma, int
   WaveGeom w;
   int st = wave_geom(g, s, depth, &w);
   if (st != EMM_OK) return st;
+  {
+    // the CTAs in flight cover about G / T layer items, 2 per step of the
+    // sweep and position: keep the waits at least that many positions back
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int G = sms * min_ctas(g->rd), D = std::max(1, std::min(depth, s->nt));
+    const int gap = (G + 2 * D * w.T - 1) / (2 * D * w.T);
+    st = wave_geom(g, s, depth, &w, gap);
+    if (st != EMM_OK) return st;
+  }
   const size_t fwd = align_up(plan(g, s).total);
   if (!ws || ws_bytes < fwd + wave_extra_bytes(w) || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
     return EMM_EWORKSPACE;
@@ -2496,7 +2534,7 @@ int wave_prepare(const emm_grid *g, const emm_survey *s, const float *sigma, int
     return EMM_ENOMEM;
   }
   if (order.size() != w.nlayer) return EMM_EINVAL;
-  st = prepare_forward(g, s, sigma, ws, fwd, rec_out, nullptr, cs, &run->P);
+  st = prepare_forward(g, s, sigma, ws, fwd, rec_out, nullptr, cs, &run->P, 1, nullptr, false, true, 0);
   if (st != EMM_OK) return st;
   if (run->P.p.rec_layers != w.rec_layers || run->P.p.tiles_z != w.L) return EMM_EINVAL;
   unsigned char *base = static_cast<unsigned char *>(ws) + fwd;

@@ -157,3 +157,23 @@ def test_timed_entry_point_matches_forward():
     emm.forward_async(grid, survey, sigma, work)
     torch.cuda.synchronize()
     assert torch.equal(G1, work.rec)
+
+
+@pytest.mark.parametrize("rd", [1, 2, 3, 4])
+def test_tile_shapes_give_the_same_bits(rd):
+    # the same cells in other tiles (32 x 4 x 4 instead of 32 x 8 x 2): the
+    # same arithmetic per cell, so the same bits, volume and batch included
+    import dataclasses
+    wl = W.small_case(n=(38, 34, 30), rd=rd, seed=40 + rd, nt=60, volume=True, nfreq=2)
+    grid = emm.grid_for(wl)
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    s0 = emm.survey_for(wl)
+    s1 = dataclasses.replace(s0, tile_shape=1)
+    G0, v0 = emm.forward(grid, s0, sigma)
+    G1, v1 = emm.forward(grid, s1, sigma)
+    assert torch.equal(G0, G1) and torch.equal(v0, v1)
+    pos = np.array([s0.src, np.array(s0.src) + [30.0, 10.0, -20.0]])
+    b0 = dataclasses.replace(s0, volume=False)
+    B0, _ = emm.forward_batch(grid, b0, sigma, pos)
+    B1, _ = emm.forward_batch(grid, dataclasses.replace(b0, tile_shape=1), sigma, pos)
+    assert torch.equal(B0, B1)
