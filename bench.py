@@ -336,9 +336,14 @@ def gather_to_rank0(t, dist=None, world=1):
     if dist is None:
         return t[None]
     import torch
-    parts = [torch.empty_like(t) for _ in range(world)]
-    dist.all_gather(parts, t)
-    return torch.stack(parts) if dist.get_rank() == 0 else None
+    # complex values travel as their real and imaginary parts
+    src = torch.view_as_real(t).contiguous() if t.is_complex() else t.contiguous()
+    parts = [torch.empty_like(src) for _ in range(world)]
+    dist.all_gather(parts, src)
+    if dist.get_rank() != 0:
+        return None
+    out = torch.stack(parts)
+    return torch.view_as_complex(out) if t.is_complex() else out
 
 
 def aggregate_rate(world, cells, nt, steps, seconds):
