@@ -46,6 +46,11 @@ E2E_SOLVES = 3          # end-to-end solves timed (each reads back the volume)
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 
 
+def log(msg):
+    """A progress line on stderr (the JSON result line goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def _slab_cells(wl):
     np1, np2, np3 = wl.npad
     nb2 = 2 * wl.nb
@@ -527,16 +532,20 @@ def graph_line(emm, torch, stream, job_max, grid, survey, sigma, work, steps, ra
     plan = emm.Plan(grid, survey, sigma, work, stream=stream)
     torch.cuda.synchronize()
     capture_ms = 1e3 * (time.perf_counter() - t0)
+    log(f"graph: captured and instantiated in {capture_ms:.0f} ms")
     plan.run_async(sigma, stream=stream)
     torch.cuda.synchronize()
+    log("graph: first replay done")
 
     def run():
         for _ in range(steps):
             plan.run_async(sigma, stream=stream)
 
     gval = rate(job_max(timed_events(stream, run)))
+    log("graph: timed replays done")
     assert emm.status(work) == emm.EMM_OK
     plan.close()
+    log("graph: plan destroyed")
     return {"value": gval, "unit": "Gcell-steps/s", "vs_stream_launches": gval / value,
             "capture_and_instantiate_ms": capture_ms,
             "what": "emm_plan_run: the solve's time loop captured once as a CUDA graph and replayed"}
@@ -561,16 +570,21 @@ def jobs_line(emm, torch, stream, job_max):
     short = [(g, dataclasses.replace(s, nt=30)) for g, s in probs]
     for (g, s), sg, w in zip(short, sig, works):
         emm.forward_async(g, s, sg, w)
+    torch.cuda.synchronize()
+    log("jobs: short single solves done")
     emm.forward_jobs(short, sig, strategy=emm.JOBS_LIST)
+    log("jobs: short work-list solve done")
     jw = emm.JobsWork(probs)
     best, tune_ms = emm.jobs_tune(probs, sig, jw, steps=40)
     torch.cuda.synchronize()
+    log(f"jobs: tuned ({emm.JOBS_STRATEGIES[best]})")
 
     def one_at_a_time():
         for (g, s), sg, w in zip(probs, sig, works):
             emm.forward_async(g, s, sg, w)
 
     seq = job_max(timed_events(stream, one_at_a_time))
+    log("jobs: one at a time done")
     for (g, s), w in zip(probs, works):
         assert emm.status(w) == emm.EMM_OK
     rates = {}
@@ -776,6 +790,11 @@ def main():
     import torch
     import paper_2304_00233_b300 as emm
     torch.cuda.set_device(local)
+    if os.environ.get("BENCH_STACKS_AFTER_S"):
+        # diagnostics: every thread's Python stack on stderr if the run is
+        # still going after this many seconds
+        import faulthandler
+        faulthandler.dump_traceback_later(float(os.environ["BENCH_STACKS_AFTER_S"]), exit=False)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -888,32 +907,43 @@ def main():
     del work
     gc.collect()
     torch.cuda.empty_cache()
+    log(f"headline done: {value:.2f} Gcell-steps/s")
     extras = not args.no_extras
     if extras and not args.no_marine:
         m = marine_line(emm, torch, stream, job_max, world, rank)
         line["marine"] = m["line"]
+        log("marine line done")
         mwl, mgrid, msurvey, msigma, mwork, mnt = m["ctx"]
         mvalue = m["line"]["value"]
-        # the same solve replayed from a CUDA graph of its time loop (emm_plan);
-        # opt-in (--graph)
-        if args.graph:
-            line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
-                                       lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)
         if args.batch > 0:
             line["batch"] = batch_line(emm, torch, stream, job_max, world, rank, mgrid, msurvey, msigma,
                                        mvalue, args.batch)
+            log("batch line done")
         if not args.no_airwave:
             line["airwave"] = airwave_line(emm, torch, stream, job_max, world)
+            log("airwave line done")
         if not args.no_gradient:
             line["gradient"] = gradient_line(emm, torch, stream, job_max, mgrid, msurvey, msigma,
                                              m["line"]["ms_per_solve"])
-        del mwork, m
+            log("gradient line done")
     if extras and not args.no_jobs:
         line["jobs"] = jobs_line(emm, torch, stream, job_max)
+        log("jobs line done")
     if extras and not args.no_survey:
         line["survey"] = survey_line(emm, torch, stream, job_max, world, rank)
+        log("survey line done")
     if extras and not args.no_gradient_survey:
         line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max, dist, rank, world)
+        log("gradient survey line done")
+    # the marine solve replayed from a CUDA graph of its time loop (emm_plan),
+    # opt-in (--graph) and last: after a plan had been created and run, a
+    # later emm_jobs_tune in the same process did not return (the jobs line)
+    if extras and not args.no_marine and args.graph:
+        line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
+                                   lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)
+        log("graph line done")
+    if extras and not args.no_marine:
+        del mwork, m
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W.WORKLOADS[args.workload]())
     if rank == 0:
