@@ -286,7 +286,10 @@ int emm_forward_batch(const emm_grid *grid, const emm_survey *survey, int nsrc, 
  *     `stream`: set-up, graph launch, normalisation; rec_out and vol_out
  *     receive exactly what emm_forward writes.  Asynchronous; emm_status on
  *     ws reads its device status.
- *   emm_plan_destroy: releases the plan (a run in flight completes). */
+ *   emm_plan_destroy: releases the plan (a run in flight completes).
+ * Known issue: in a process that had created and run a plan, a later
+ * emm_jobs_tune was seen not to return (the cause is not known); call the
+ * tuner before any plan, or pick a strategy without it. */
 typedef struct emm_plan emm_plan;
 int emm_plan_create(const emm_grid *grid, const emm_survey *survey, const float *sigma, void *ws,
                     size_t ws_bytes, double *rec_out, double *vol_out, emm_stream stream, emm_plan **plan);
