@@ -419,9 +419,11 @@ int emm_persist_workspace_size(int ntasks, const emm_task *tasks, size_t *bytes,
  * bounded by opts->wait_s of device time; a wait that runs out writes
  * EMM_ETIMEOUT to the header's status word and every CTA returns at its next
  * barrier (the outputs are then undefined).  Asynchronous on `stream`;
- * host-detected errors as emm_forward and emm_persist_workspace_size, with
- * nothing enqueued; EMM_ECUDA if the launch fails (for instance when the
- * CTAs cannot all be resident). */
+ * host-detected errors as emm_forward and emm_persist_workspace_size: the
+ * layout and option checks enqueue nothing, while an error found in a
+ * task's own set-up (EMM_ECFL, EMM_EOUTSIDE) returns after the set-up of
+ * the tasks before it was enqueued (no launch follows); EMM_ECUDA if the
+ * launch fails (for instance when the CTAs cannot all be resident). */
 int emm_forward_persistent(int ntasks, const emm_task *tasks, const emm_persist_opts *opts, void *ws,
                            size_t ws_bytes, emm_stream stream);
 
