@@ -936,8 +936,7 @@ def main():
         line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max, dist, rank, world)
         log("gradient survey line done")
     # the marine solve replayed from a CUDA graph of its time loop (emm_plan),
-    # opt-in (--graph) and last: after a plan had been created and run, a
-    # later emm_jobs_tune in the same process did not return (the jobs line)
+    # opt-in (--graph), so that the default run stays within its time, and last
     if extras and not args.no_marine and args.graph:
         line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
                                    lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)

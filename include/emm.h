@@ -287,9 +287,8 @@ int emm_forward_batch(const emm_grid *grid, const emm_survey *survey, int nsrc, 
  *     receive exactly what emm_forward writes.  Asynchronous; emm_status on
  *     ws reads its device status.
  *   emm_plan_destroy: releases the plan (a run in flight completes).
- * Known issue: in a process that had created and run a plan, a later
- * emm_jobs_tune was seen not to return (the cause is not known); call the
- * tuner before any plan, or pick a strategy without it. */
+ * A plan and the work-list entry points (emm_forward_jobs, emm_jobs_tune)
+ * may be used in one process in either order. */
 typedef struct emm_plan emm_plan;
 int emm_plan_create(const emm_grid *grid, const emm_survey *survey, const float *sigma, void *ws,
                     size_t ws_bytes, double *rec_out, double *vol_out, emm_stream stream, emm_plan **plan);
@@ -320,7 +319,9 @@ enum {
                                overlap instead of each draining alone */
   EMM_JOBS_SEQUENTIAL = 1,  /* each problem's whole time loop in turn on `stream` */
   EMM_JOBS_STREAMS = 2      /* each problem on a stream of its own, forked from `stream` and
-                               joined back to it (the library creates and releases the streams) */
+                               joined back to it (the library creates and releases the streams);
+                               on these streams each launch waits for the whole launch before
+                               it (no programmatic dependent launches) */
 };
 
 /* Forward solves of up to 16 problems of any grid sizes (one FD order, an

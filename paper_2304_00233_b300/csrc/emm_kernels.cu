@@ -2158,7 +2158,12 @@ cudaError_t run_jobs(const std::vector<Prepared> &P, const std::vector<int> &nts
       if (n0 < ends[j]) e = run_steps(P[j], P[j].p, P[j].blocks, n0, ends[j], cs, nullptr);
     return e;
   }
-  // EMM_JOBS_STREAMS: the streams and events are released once their work is done
+  // EMM_JOBS_STREAMS: the streams and events are released once their work is
+  // done.  The problems' launches on these streams are plain ones, not
+  // programmatic dependents: after a CUDA-graph plan had run in the process,
+  // dependent-launch chains on several such streams at once were seen never
+  // to finish on the eight uneven grids.
+  PlainLaunches plain;
   cudaEvent_t fork;
   cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
   if (e != cudaSuccess) return e;

@@ -91,12 +91,23 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_next_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Host side: while set on a thread, launch_dependent launches plainly (each
+// launch waits for the whole previous one); the kernels' griddepcontrol
+// instructions are then no-ops.  Set for work the library spreads over
+// streams of its own (see run_jobs).
+inline thread_local bool plain_launches = false;
+struct PlainLaunches {
+  bool old;
+  PlainLaunches() : old(plain_launches) { plain_launches = true; }
+  ~PlainLaunches() { plain_launches = old; }
+};
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              Args &&...args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = plain_launches ? 0 : 1;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = block;

@@ -54,3 +54,49 @@ def test_plan_with_air_boundary_equals_forward_and_closes():
     assert torch.equal(G, G_ref) and torch.equal(vol, vol_ref)
     G2, _ = emm.forward(grid, survey, s1, work)
     assert torch.equal(G2, G_ref)
+
+
+_PLAN_THEN_JOBS = r"""
+import dataclasses, sys
+import numpy as np, torch
+import paper_2304_00233_b300 as emm
+from paper_2304_00233_b300 import workloads as W
+wl = W.marine_1d()
+g = emm.grid_for(wl)
+s = emm.survey_for(wl, nt=emm.steps_for(wl, g))
+sg = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+plan = emm.Plan(g, s, sg, emm.Workspace(g, s))
+for _ in range(4):
+    plan.run_async(sg)
+torch.cuda.synchronize()
+plan.close()
+probs, sig = [], []
+for w in W.uneven_jobs():
+    gj = emm.grid_for(w)
+    probs.append((gj, emm.survey_for(w, nt=30)))
+    sig.append(torch.from_numpy(w.sigma.astype(np.float32)).cuda())
+ref, _ = emm.forward_jobs(probs, sig, strategy=emm.JOBS_SEQUENTIAL)
+ref = [r.clone() for r in ref]
+for k in (emm.JOBS_STREAMS, emm.JOBS_LIST):
+    out, _ = emm.forward_jobs(probs, sig, strategy=k)
+    assert all(torch.equal(a, b) for a, b in zip(out, ref)), emm.JOBS_STRATEGIES[k]
+torch.cuda.synchronize()
+print("plan-then-jobs ok")
+"""
+
+
+def test_jobs_after_plan_complete_and_agree():
+    # a full-length marine plan replayed four times, then the eight uneven
+    # grids as work lists in one process: every strategy completes and
+    # gives the sequential strategy's bits.  (With programmatic dependent
+    # launches on the stream-per-problem strategy's own streams this
+    # sequence once never completed; those launches are now plain ones.)
+    # A child process with a time limit turns a recurrence into a failure.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _PLAN_THEN_JOBS], cwd=root, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "plan-then-jobs ok" in r.stdout
