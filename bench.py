@@ -57,27 +57,30 @@ def _slab_cells(wl):
     return nb2 * np2 * np3 + np1 * nb2 * np3 + np1 * np2 * nb2
 
 
-def algorithmic_bytes(wl):
+def algorithmic_bytes(wl, ring):
     """Bytes per leapfrog step the method must move at minimum (FP32):
     6 fields read + written and 3 dt/eps read = 60 B per padded cell, plus
     4 CPML memory arrays read + written (32 B) per cell and per axis whose
-    slab it lies in, plus 32 B per compensated volume-DTFT accumulator."""
+    slab it lies in, plus, with the volume DTFT, 32 B per compensated
+    accumulator (read + written) once per `ring` steps: the DTFT of `ring`
+    steps is added to each accumulator in one pass."""
     cells = int(np.prod(wl.npad))
     b = 60 * cells + 32 * _slab_cells(wl)
     if wl.volume:
-        b += 32 * 6 * len(wl.freqs) * int(np.prod(wl.shape))
+        b += 32 * 6 * len(wl.freqs) * int(np.prod(wl.shape)) // ring
     return b
 
 
-def per_kernel_bytes(wl):
-    """Minimal bytes of each launch of a leapfrog step: the E launch reads H,
+def per_kernel_bytes(wl, ring):
+    """Minimal bytes of each launch, per leapfrog step: the E launch reads H,
     E, dt/eps and writes E (48 B/cell), the H launch reads E, H and writes H
-    (36 B/cell), each with 2 CPML arrays read + written per slab axis; the
-    volume DTFT reads the six fields once (24 B per interior sample) and
-    reads + writes its 6 x nfreq compensated accumulators (32 B each)."""
+    (36 B/cell), each with 2 CPML arrays read + written per slab axis; a
+    volume-DTFT launch reads the six fields of each of its `ring` steps (24 B
+    per interior sample and step) and reads + writes its 6 x nfreq
+    compensated accumulators (32 B each) once."""
     cells = int(np.prod(wl.npad))
     nint = int(np.prod(wl.shape))
-    vol = (24 + 32 * 6 * len(wl.freqs)) * nint if wl.volume else 0
+    vol = (24 * ring + 32 * 6 * len(wl.freqs)) * nint / ring if wl.volume else 0
     return {"k_update_E": 48 * cells + 16 * _slab_cells(wl), "k_update_H": 36 * cells + 16 * _slab_cells(wl),
             "k_volume_dft": vol}
 
@@ -427,7 +430,7 @@ def marine_line(emm, torch, stream, job_max, world, rank, solves=3):
     assert emm.status(work) == emm.EMM_OK
     peak, _ = measured_peaks()
     step_s = float(np.mean(loops)) / nt / 1e3
-    alg = algorithmic_bytes(wl)
+    alg = algorithmic_bytes(wl, emm.VOLUME_RING)
     G = torch.view_as_complex(work.rec)[: survey.nrec].cpu().numpy()
     return {"ctx": (wl, grid, survey, sigma, work, nt),
             "line": {"workload": wl.name, "value": aggregate_rate(world, grid.cells, nt, solves, sec),
@@ -870,13 +873,16 @@ def main():
     e_mean = float(np.mean([t["e_ms"] for t in tims]))
     h_mean = float(np.mean([t["h_ms"] for t in tims]))
     v_mean = float(np.mean([t["v_ms"] for t in tims]))
-    alg = algorithmic_bytes(wl)
-    kb = per_kernel_bytes(wl)
+    alg = algorithmic_bytes(wl, emm.VOLUME_RING)
+    kb = per_kernel_bytes(wl, emm.VOLUME_RING)
     # one leapfrog step as the time loop runs it: E, volume DTFT and H back to
     # back, each launch a programmatic dependent of the one before
     step_s = float(np.mean([t["loop_ms"] for t in tims])) / nt / 1e3
     achieved = alg / step_s / 1e9
-    per_solve = 1 + 2 * nt + (nt if survey.volume else 0) + (1 if survey.nrec else 0) + (1 if survey.volume else 0)
+    # k_prepare, E and H per step, one volume DTFT per VOLUME_RING steps,
+    # the normalisations
+    per_solve = (1 + 2 * nt + (-(-nt // emm.VOLUME_RING) if survey.volume else 0) + (1 if survey.nrec else 0)
+                 + (1 if survey.volume else 0))
     kernels = {"k_update_E": e_mean, "k_update_H": h_mean}
     if survey.volume:
         kernels["k_volume_dft"] = v_mean

@@ -172,8 +172,17 @@ typedef struct {
                            wavefront take 0.  Results do not depend on it. */
 } emm_survey;
 
+/* Leapfrog steps of fields a one-transmitter solve with the volume DTFT
+ * keeps: its half-steps write into a ring of EMM_VOLUME_RING field slots
+ * (E and H), and one volume-DTFT launch adds that many steps' terms to each
+ * accumulator (Eq. 25), in step order, so that the accumulators are read and
+ * written once per EMM_VOLUME_RING steps. */
+#define EMM_VOLUME_RING 8
+
 /* Device workspace bytes emm_forward needs for this grid and survey
- * (fields, CPML memory, 1/eps, tables).  EMM_EINVAL on bad input. */
+ * (fields, CPML memory, 1/eps, tables; with survey->volume the accumulators
+ * and EMM_VOLUME_RING - 1 more copies of E and H, the field ring).
+ * EMM_EINVAL on bad input. */
 int emm_workspace_size(const emm_grid *grid, const emm_survey *survey, size_t *bytes);
 
 /* Run the forward time loop (Algorithm 1 without the airwave step) on
@@ -209,8 +218,11 @@ typedef struct {
   double total_ms; /* out: duration (ms) of the whole enqueued forward run */
   double loop_ms;  /* out: duration (ms) of the time loop alone: every E and H
                       launch back to back, from the first to the last */
-  double v_ms;     /* out: mean duration (ms) of one volume-DTFT launch (0 when
-                      survey->volume is 0) */
+  double v_ms;     /* out: volume-DTFT time (ms) per leapfrog step: the
+                      duration of the timed DTFT launches over the steps they
+                      covered (0 when survey->volume is 0).  With the volume
+                      DTFT one launch covers up to eight steps, and the timed
+                      steps are the last steps of such launches. */
 } emm_timing;
 
 /* emm_forward, with CUDA events recorded on `stream` around the E and H

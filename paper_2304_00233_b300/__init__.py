@@ -29,6 +29,9 @@ LIBRARY_PATH = os.path.join(_HERE, "libemm.so")
 
 (EMM_OK, EMM_EINVAL, EMM_ENOMEM, EMM_EOUTSIDE, EMM_ECFL, EMM_ECUDA, EMM_EWORKSPACE, EMM_EDEVICE,
  EMM_ETIMEOUT) = range(9)
+# EMM_VOLUME_RING: leapfrog steps one volume-DTFT launch covers (the field
+# ring of a one-transmitter solve with the volume DTFT)
+VOLUME_RING = 8
 JOBS_LIST, JOBS_SEQUENTIAL, JOBS_STREAMS = range(3)
 JOBS_STRATEGIES = ("list", "sequential", "streams")
 TAB_NODES, TAB_HALF, TAB_DPLUS, TAB_DMINUS, TAB_SLAB_INT, TAB_SLAB_HALF = range(6)

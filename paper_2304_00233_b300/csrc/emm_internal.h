@@ -94,6 +94,14 @@ struct DevParams {
   float *E[3], *H[3];        // sample (i, j, k) at [k * plane + j * pitch + i]
   float *Eout[3];            // set for a one-step run: the E half-step writes E^{n+1}
                              // here (same layout) and leaves E[] as it was
+  float *Hout[3];            // ring runs: the H half-step writes H^{n+3/2} here
+  // Field ring of a solve with the volume DTFT (ring_k > 1): slot s holds
+  // E^m and H^{m+1/2} for m = s mod ring_k; slot 0 is E[] / H[] of the state,
+  // slot s >= 1 component c (0..2 E, 3..5 H) starts at
+  // ring + ((s - 1) * 6 + c) * ring_comp.  ring_k = 1: the fields stay in place.
+  float *ring;
+  size_t ring_comp;
+  int ring_k;
   const float *ie[3];        // dt / eps = 2 omega0 dt / sigma on the padded grid
   float *psiE[6];            // CPML memory of curl H terms (E update)
   float *psiH[6];            // CPML memory of curl E terms (H update)
@@ -142,7 +150,8 @@ FieldGeom field_geom(const emm_grid *g, int shape = 0);
 // The state of transmitter 0 (E[3], H[3], psiE[6], psiH[6]) is one block
 // at E[0]; transmitter k's block starts sstride bytes further per k.
 struct Layout {
-  size_t status, conv, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, zero_end;
+  size_t status, conv, E[3], H[3], ie[3], psiE[6], psiH[6], sstride, vacc, ring, ring_comp, zero_end;
+  int ring_k;
   size_t cm[3], cp[3], pml[3], srcs, jw, amp, rec_start, rec_w, fE, fH, fE32, fH32, norm;
   size_t air_twx, air_twy, air_decE, air_facH, air_work, total;
 };
@@ -156,11 +165,16 @@ int check_survey(const emm_grid *g, const emm_survey *s);
 // Derivative axis of CPML array c (0..5): 2*comp + 0 -> (comp+1)%3, 2*comp + 1 -> (comp+2)%3.
 inline int psi_axis(int c) { return (c % 2 == 0) ? (c / 2 + 1) % 3 : (c / 2 + 2) % 3; }
 
-// Optional per-launch timing: events before/after the E and H launches of
-// every `every`-th step (3 events per timed step).
+// Optional per-launch timing: events before/after the E, volume DTFT and H
+// launches of every `every`-th step (4 events per timed step).  With a field
+// ring the timed steps are the ends of every (every / ring_k)-th batch, and
+// vsteps[q] is the number of steps the volume DTFT launch of sample q
+// covered (0: none in it); used counts the samples taken.
 struct StepEvents {
   int every = 0;
+  int used = 0;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> vsteps;
   cudaEvent_t loop[2] = {nullptr, nullptr};  // around the whole time loop
 };
 

@@ -106,15 +106,6 @@ __device__ __forceinline__ int slab_half(int i, int np, int nb) {
   return i < nb ? i : ((i >= np - 1 - nb && i <= np - 2) ? nb + np - 2 - i : -1);
 }
 
-// Error-free accumulation (hi, lo) += v  (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
-  const float t = hi + v;
-  const float bp = t - hi;
-  const float err = (hi - (t - bp)) + (v - bp);
-  hi = t;
-  lo += err;
-}
-
 // One warp per (receiver, component): (2R)^3 weighted gather in FP64, warp
 // shuffle reduction, then acc += factor * value for every frequency.
 // CONV: a convergence run, whose extra warp accumulates the corner DTFT.
@@ -831,7 +822,8 @@ __device__ __forceinline__ Blk reversed_tile(const DevParams &p, const Blk &b) {
 // One CTA of the H half-step.
 // REV: walk the tiles in reverse launch order (a launch of its own); false
 // where a scheduler hands out the tiles itself.
-template <int R, bool MULTI, bool CONV, int S = 0, bool REV = true>
+// OUT: H^{n+3/2} goes to p.Hout (H^{n+1/2} stays where it is).
+template <int R, bool MULTI, bool CONV, int S = 0, bool REV = true, bool OUT = false>
 __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, const int n, const Blk &blk,
                                         unsigned phase = 0) {
   const Blk b = (!REV || blk.z < p.rec_layers) ? blk : reversed_tile<MULTI>(p, blk);
@@ -849,13 +841,16 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
   if (threadIdx.x == 0) issue_tiles<R, S>(tm, s, bar, o, 1 - R, phase);
 
   const Quad u = quad_of<S>(o);
-  const Fields f = fields_of<MULTI>(p, o.src);
+  Fields f = fields_of<MULTI>(p, o.src);
   const int np0 = p.np[0], np1 = p.np[1], np2 = p.np[2], nb = p.nb;
   const bool live = u.i >= 0 && u.i < np0 && u.j >= 0 && u.j < np1 && u.k >= 0 && u.k < np2;
   float4 h[3];
   const size_t id = static_cast<size_t>(u.k) * p.plane + static_cast<size_t>(u.j) * p.pitch + u.i;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) h[a] = live ? *reinterpret_cast<const float4 *>(f.H[a] + id) : float4{};
+  for (int a = 0; a < 3; ++a) {
+    h[a] = live ? *reinterpret_cast<const float4 *>(f.H[a] + id) : float4{};
+    if (OUT) f.H[a] = p.Hout[a];  // the whole quad is stored, so Hout gets every sample
+  }
   const bool fast = interior_H<S>(p, o, R);
   float4 *ps = reinterpret_cast<float4 *>(s + Tiles<R, S>::BYTES / 4);
   if (!fast && live)
@@ -874,13 +869,13 @@ __device__ __forceinline__ void h_block(const DevParams &p, const TmaSet &tm, co
     h_quad<R, false, S>(p, f, v, u, h, ps, n, cf);
 }
 
-template <int R, bool MULTI, bool CONV, int S = 0>
+template <int R, bool MULTI, bool CONV, int S = 0, bool OUT = false>
 __global__ void __launch_bounds__(NT, min_ctas(R))
     k_update_H(const DevParams p, const __grid_constant__ TmaSet tm, const int n) {
   wait_prior_grid();
   if (CONV && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
-  h_block<R, MULTI, CONV, S>(p, tm, n, launch_blk());
+  h_block<R, MULTI, CONV, S, true, OUT>(p, tm, n, launch_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -1357,40 +1352,119 @@ __global__ void __launch_bounds__(AFT) k_air_fft(const DevParams p) {
   }
 }
 
-// Volume DTFT of step n (Eq. 25 on every interior sample), after the E
-// launch (and the source and air launches that follow it), when E holds
-// E^{n+1} and H still holds H^{n+1/2}: for the six components and every
-// frequency, acc += factor * value in compensated FP32 (hi + lo pairs of the
-// real and imaginary parts).  One thread per interior sample, i fastest.
-__global__ void k_volume_dft(const DevParams p, const int n) {
+// Steps of fields a solve keeps for its volume DTFT (see ring_depth).
+constexpr int kRing = EMM_VOLUME_RING;
+
+// Slot s of the field ring, component c (0..2 E, 3..5 H); see DevParams.
+inline const float *ring_field(const DevParams &p, int s, int c) {
+  if (s == 0) return c < 3 ? p.E[c] : p.H[c - 3];
+  return p.ring + (static_cast<size_t>(s - 1) * 6 + c) * p.ring_comp;
+}
+
+// The fields one volume-DTFT launch reads: for its step b0 + s, component c,
+// E^{b0+s+1} (c < 3) or H^{b0+s+1/2} (c >= 3).
+struct VolFields {
+  const float *f[kRing][6];
+};
+
+// Pairs of FP32 values (the real and imaginary parts) held in one 64-bit
+// register, for the packed FP32x2 instructions.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(r));
+  return d;
+}
+
+// (hi, lo) += w * (v, v) for two independent sums at once: per lane the
+// product x = w v rounded on its own, then the error-free sum of Knuth's
+// TwoSum: t = hi + x, b = t - hi, e = (hi - (t - b)) + (x - b); hi = t,
+// lo += e.
+__device__ __forceinline__ void two_sum_mul_add2(unsigned long long &hi, unsigned long long &lo,
+                                                 unsigned long long w, unsigned long long vv) {
+  asm("{\n .reg .b64 x, t, b, u, e;\n"
+      " mul.rn.f32x2 x, %2, %3;\n"
+      " add.rn.f32x2 t, %0, x;\n sub.rn.f32x2 b, t, %0;\n sub.rn.f32x2 u, t, b;\n sub.rn.f32x2 u, %0, u;\n"
+      " sub.rn.f32x2 e, x, b;\n add.rn.f32x2 e, u, e;\n add.rn.f32x2 %1, %1, e;\n mov.b64 %0, t;\n}\n"
+      : "+l"(hi), "+l"(lo)
+      : "l"(w), "l"(vv));
+}
+
+// Volume DTFT (Eq. 25 on every interior sample) of the cnt <= kRing steps
+// b0 .. b0+cnt-1, launched after the E launch of the last of them (and the
+// source and air launches that follow it): for each step n the terms of
+// E^{n+1} and H^{n+1/2}, six components and every frequency, acc += factor *
+// value in compensated FP32 (hi + lo pairs of the real and imaginary parts),
+// added to each accumulator step after step.  Each accumulator is read and
+// written once per launch.  One thread per interior sample (i fastest) and
+// component: grid x covers a z plane of samples, y the planes, z the six
+// components.
+__global__ void __launch_bounds__(256) k_volume_dft(const DevParams p, const __grid_constant__ VolFields vf,
+                                                    const int b0, const int cnt) {
   wait_prior_grid();
   if (p.halt && *p.halt) return;  // a convergence run that has stopped
   allow_next_launch();
-  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-  const size_t lin = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (lin >= nint) return;
-  const int ii = static_cast<int>(lin % p.n[0]), jj = static_cast<int>((lin / p.n[0]) % p.n[1]),
-            kk = static_cast<int>(lin / (static_cast<size_t>(p.n[0]) * p.n[1]));
+  const unsigned n0 = static_cast<unsigned>(p.n[0]), nplane = n0 * static_cast<unsigned>(p.n[1]);
+  const unsigned l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nplane) return;
+  const int c = blockIdx.z, kk = blockIdx.y;
+  const int ii = static_cast<int>(l % n0), jj = static_cast<int>(l / n0);
+  const size_t nint = static_cast<size_t>(nplane) * p.n[2];
+  const size_t lin = static_cast<size_t>(kk) * nplane + l;
   const size_t id = static_cast<size_t>(kk + p.nbe) * p.plane + static_cast<size_t>(jj + p.nbe) * p.pitch + (ii + p.nbe);
-  float v[6];
+  unsigned long long vv[kRing];  // (value, value) of each step
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    v[c] = p.E[c][id];
-    v[3 + c] = p.H[c][id];
-  }
-  const float *facE = p.fE32 + static_cast<size_t>(n) * p.nf * 2, *facH = p.fH32 + static_cast<size_t>(n) * p.nf * 2;
-  for (int f = 0; f < p.nf; ++f) {
-    float4 acc[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] = p.vacc[(static_cast<size_t>(c) * p.nf + f) * nint + lin];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const float *fac = c < 3 ? facE : facH;
-      two_sum_add(acc[c].x, acc[c].y, fac[2 * f] * v[c]);
-      two_sum_add(acc[c].z, acc[c].w, fac[2 * f + 1] * v[c]);
-      p.vacc[(static_cast<size_t>(c) * p.nf + f) * nint + lin] = acc[c];
+  for (int s = 0; s < kRing; ++s)
+    if (s < cnt) {
+      const float x = __ldg(vf.f[s][c] + id);
+      vv[s] = pack2(x, x);
     }
+  // factors (re, im) of step b0 + s, frequency f at fac[s * nf + f]
+  const unsigned long long *fac =
+      reinterpret_cast<const unsigned long long *>(c < 3 ? p.fE32 : p.fH32) + static_cast<size_t>(b0) * p.nf;
+  constexpr int FG = 4;  // frequencies per round of accumulator loads
+  for (int f0 = 0; f0 < p.nf; f0 += FG) {
+    float4 *a = p.vacc + (static_cast<size_t>(c) * p.nf + f0) * nint + lin;
+    unsigned long long hi[FG], lo[FG];  // (re, im) pairs
+#pragma unroll
+    for (int g = 0; g < FG; ++g)
+      if (f0 + g < p.nf) {
+        const float4 t = __ldcs(a + g * nint);  // streamed: touched once per launch
+        hi[g] = pack2(t.x, t.z);
+        lo[g] = pack2(t.y, t.w);
+      }
+#pragma unroll
+    for (int s = 0; s < kRing; ++s) {
+      if (s < cnt) {
+#pragma unroll
+        for (int g = 0; g < FG; ++g)
+          if (f0 + g < p.nf) two_sum_mul_add2(hi[g], lo[g], __ldg(fac + s * p.nf + f0 + g), vv[s]);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < FG; ++g)
+      if (f0 + g < p.nf) {
+        const float2 h = unpack2(hi[g]), l = unpack2(lo[g]);
+        __stcs(a + g * nint, make_float4(h.x, l.x, h.y, l.y));
+      }
   }
+}
+
+// The launch of k_volume_dft for steps b0 .. b0+cnt-1, slot(step, c) giving
+// the field of each.
+template <typename Slot>
+cudaError_t launch_volume(const DevParams &p, int b0, int cnt, Slot slot, cudaStream_t st) {
+  VolFields vf{};
+  for (int s = 0; s < cnt; ++s)
+    for (int c = 0; c < 6; ++c) vf.f[s][c] = slot(b0 + s, c);
+  const unsigned nplane = static_cast<unsigned>(p.n[0]) * static_cast<unsigned>(p.n[1]);
+  if (p.n[2] > 65535 || static_cast<size_t>(p.n[0]) * p.n[1] > (1u << 31)) return cudaErrorInvalidValue;
+  const dim3 grid((nplane + 255) / 256, static_cast<unsigned>(p.n[2]), 6);
+  return launch_dependent(k_volume_dft, grid, dim3(256), 0, st, p, vf, b0, cnt);
 }
 
 // dt/eps on the padded grid from the interior staggered conductivity, with
@@ -1550,6 +1624,13 @@ size_t source_stride(const emm_grid *g, const emm_survey *s) {
   return 3 * static_cast<size_t>(ext[0]) * ext[1] * ext[2];
 }
 
+// Steps of fields a solve keeps for its volume DTFT: a one-transmitter solve
+// with the volume DTFT keeps kRing (its half-steps write into a ring of field
+// slots and one DTFT launch adds kRing steps' terms to each accumulator, which
+// is then read and written once per kRing steps instead of every step); any
+// other solve keeps its fields in place.
+int ring_depth(const emm_survey *s, int nsrc) { return (s->volume && nsrc == 1) ? kRing : 1; }
+
 Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   Layout L{};
   size_t off = 0;
@@ -1573,6 +1654,11 @@ Layout plan(const emm_grid *g, const emm_survey *s, int nsrc) {
   L.sstride = off - b0;
   off += static_cast<size_t>(nsrc > 1 ? nsrc - 1 : 0) * L.sstride;
   L.vacc = take(s->volume ? 6 * nf * nint * sizeof(float4) : 0);
+  // field ring of a one-transmitter solve with the volume DTFT: slots 1 ..
+  // ring_k-1 of E and H (slot 0 is the state's), zeroed like the state
+  L.ring_k = ring_depth(s, nsrc);
+  L.ring_comp = align_up(cells * 4);
+  L.ring = take(static_cast<size_t>(L.ring_k - 1) * 6 * L.ring_comp);
   L.zero_end = off;
   for (int c = 0; c < 3; ++c) L.ie[c] = take(cells * 4);
   // air: work planes T, F (3 components) and U (2 rd outputs) per transmitter
@@ -1674,6 +1760,7 @@ template <int R, bool MULTI, bool CONV, bool OUT = false, int S = 0>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
   if (OUT && (MULTI || CONV || n1 - n0 != 1)) return cudaErrorInvalidValue;
   DevParams q = p;
+  q.ring_k = 1;  // the fields stay in place
   if (OUT)
     for (int a = 0; a < 3; ++a) q.E[a] = p.Eout[a];
   TmaSet tE{}, tH{};
@@ -1688,8 +1775,6 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
   if (e != cudaSuccess) return e;
   // each half-step is launched as a programmatic dependent of the one before
   const dim3 inj(static_cast<unsigned>((p.nsrc * p.jstride + 127) / 128));  // k_inject threads
-  const size_t nint = static_cast<size_t>(p.n[0]) * p.n[1] * p.n[2];
-  const dim3 vol_blocks(static_cast<unsigned>((nint + 255) / 256));             // k_volume_dft threads
   size_t used = 0;
   if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
   for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
@@ -1700,14 +1785,101 @@ cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaSt
       e = launch_dependent(k_inject<MULTI, 0>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on && R > 1) e = air_step<MULTI, 0>(q, st);
     if (timed) cudaEventRecord(te->ev[used + 1], st);
-    if (e == cudaSuccess && p.vacc) e = launch_dependent(k_volume_dft, vol_blocks, dim3(256), 0, st, q, n);
-    if (timed) cudaEventRecord(te->ev[used + 2], st);
+    if (e == cudaSuccess && p.vacc)
+      e = launch_volume(q, n, 1, [&](int, int c) -> const float * { return c < 3 ? q.E[c] : q.H[c - 3]; }, st);
+    if (timed) {
+      cudaEventRecord(te->ev[used + 2], st);
+      te->vsteps.push_back(p.vacc ? 1 : 0);
+    }
     if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, CONV, S>, blocks, dim3(NT), sb, st, q, tH, n);
     if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<MULTI, 1>, inj, dim3(128), 0, st, q, n);
     if (e == cudaSuccess && p.air_on) e = air_step<MULTI, 1>(q, st);
     if (timed) {
       cudaEventRecord(te->ev[used + 3], st);
       used += 4;
+      te->used += 1;
+    }
+  }
+  if (te && te->loop[1]) cudaEventRecord(te->loop[1], st);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// A one-transmitter solve with the volume DTFT over a ring of k = p.ring_k
+// field slots (slot m mod k holds E^m and H^{m+1/2}).  The E half-step of
+// step n reads E^n and H^{n+1/2} in slot n mod k and writes E^{n+1} into
+// slot (n+1) mod k; the H half-step reads H^{n+1/2} and E^{n+1} and writes
+// H^{n+3/2} into slot (n+1) mod k.  After the E launch (and the source and
+// air launches after it) of the last step of each batch of at most k steps,
+// and of the run's last step, one k_volume_dft launch adds the batch's
+// terms.  The batch's fields are all still in the ring then: the first
+// launch to overwrite one of its slots (the H launch of the batch's last
+// step, or the E launch after it) follows the DTFT launch in stream order.
+template <int R, int S>
+cudaError_t launch_ring(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
+  const int k = p.ring_k;
+  if (k < 2 || k > kRing || !p.vacc || p.nsrc != 1 || p.corner || p.Eout[0]) return cudaErrorInvalidValue;
+  auto slot = [&](int sl, int c) { return const_cast<float *>(ring_field(p, sl, c)); };
+  // tensor maps per slot: the H boxes the E launch reads, the E boxes the H launch reads
+  TmaSet tE[kRing], tH[kRing];
+  for (int sl = 0; sl < k; ++sl) {
+    float *Hs[3] = {slot(sl, 3), slot(sl, 4), slot(sl, 5)};
+    float *Es[3] = {slot(sl, 0), slot(sl, 1), slot(sl, 2)};
+    if (!make_tiles<R, S>(&tE[sl], Hs, p) || !make_tiles<R, S>(&tH[sl], Es, p)) return cudaErrorInvalidValue;
+  }
+  const size_t sb = smem_bytes<R, S>();
+  cudaError_t e = cudaFuncSetAttribute(k_update_E<R, false, false, true, S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_H<R, false, false, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sb));
+  if (e != cudaSuccess) return e;
+  const dim3 inj(static_cast<unsigned>((p.jstride + 127) / 128));  // k_inject threads
+  // timed samples: the last step of every stride-th batch
+  const int stride = te && te->every > 0 ? std::max(1, te->every / k) : 0;
+  size_t used = 0;
+  int batch = 0, b0 = n0;
+  if (te && te->loop[0]) cudaEventRecord(te->loop[0], st);
+  for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
+    const int so = n % k, sn = (n + 1) % k;
+    const bool flush = n - b0 + 1 == k || n == n1 - 1;
+    const bool timed = flush && stride > 0 && batch % stride == 0 && used + 4 <= te->ev.size();
+    DevParams q = p;  // E half-step: E^n, H^{n+1/2} in slot so; E^{n+1} into slot sn
+    for (int c = 0; c < 3; ++c) {
+      q.E[c] = slot(so, c);
+      q.H[c] = slot(so, 3 + c);
+      q.Eout[c] = slot(sn, c);
+    }
+    if (timed) cudaEventRecord(te->ev[used], st);
+    e = launch_dependent(k_update_E<R, false, false, true, S>, blocks, dim3(NT), sb, st, q, tE[so], n);
+    for (int c = 0; c < 3; ++c) {  // the launches after it see E^{n+1}
+      q.E[c] = slot(sn, c);
+      q.Eout[c] = nullptr;
+    }
+    if (e == cudaSuccess && !p.src_fused && !p.src_magnetic)
+      e = launch_dependent(k_inject<false, 0>, inj, dim3(128), 0, st, q, n);
+    if (e == cudaSuccess && p.air_on && R > 1) e = air_step<false, 0>(q, st);
+    if (timed) cudaEventRecord(te->ev[used + 1], st);
+    if (e == cudaSuccess && flush) {
+      e = launch_volume(p, b0, n - b0 + 1, [&](int m, int c) -> const float * {
+        return c < 3 ? slot((m + 1) % k, c) : slot(m % k, c);  // E^{m+1}, H^{m+1/2}
+      }, st);
+      if (timed) te->vsteps.push_back(n - b0 + 1);
+      b0 = n + 1;
+      ++batch;
+    }
+    if (timed) cudaEventRecord(te->ev[used + 2], st);
+    for (int c = 0; c < 3; ++c) q.Hout[c] = slot(sn, 3 + c);  // H^{n+3/2} into slot sn
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, false, false, S, true>, blocks, dim3(NT), sb, st, q, tH[sn], n);
+    for (int c = 0; c < 3; ++c) {
+      q.H[c] = slot(sn, 3 + c);
+      q.Hout[c] = nullptr;
+    }
+    if (e == cudaSuccess && p.src_magnetic) e = launch_dependent(k_inject<false, 1>, inj, dim3(128), 0, st, q, n);
+    if (e == cudaSuccess && p.air_on) e = air_step<false, 1>(q, st);
+    if (timed) {
+      cudaEventRecord(te->ev[used + 3], st);
+      used += 4;
+      te->used += 1;
     }
   }
   if (te && te->loop[1]) cudaEventRecord(te->loop[1], st);
@@ -1969,6 +2141,11 @@ int prepare_forward(const emm_grid *g, const emm_survey *s, const float *sigma, 
     p.H[c] = reinterpret_cast<float *>(base + L.H[c]) + fg.xshift;
     p.ie[c] = reinterpret_cast<const float *>(base + L.ie[c]) + fg.xshift;
   }
+  // a convergence run keeps its fields in place (its stop step is decided on
+  // the device, so the DTFT of every step must follow that step)
+  p.ring_k = converge ? 1 : L.ring_k;
+  p.ring = reinterpret_cast<float *>(base + L.ring) + fg.xshift;
+  p.ring_comp = L.ring_comp / 4;
   for (int c = 0; c < 6; ++c) {
     // y- and z-derivative arrays share the field rows' x shift
     const int shift = psi_axis(c) == 0 ? 0 : fg.xshift;
@@ -2068,6 +2245,7 @@ cudaError_t run_order(const DevParams &p, dim3 blocks, int n0, int n1, cudaStrea
   if (p.Eout[0]) return S == 0 ? launch_steps<R, false, false, true>(p, n0, n1, blocks, cs, te) : cudaErrorInvalidValue;
   if (p.nsrc > 1) return launch_steps<R, true, false, false, S>(p, n0, n1, blocks, cs, te);
   if (p.corner) return S == 0 ? launch_steps<R, false, true>(p, n0, n1, blocks, cs, te) : cudaErrorInvalidValue;
+  if (p.ring_k > 1) return launch_ring<R, S>(p, n0, n1, blocks, cs, te);
   return launch_steps<R, false, false, false, S>(p, n0, n1, blocks, cs, te);
 }
 
@@ -2711,19 +2889,24 @@ int emm_forward_timed(const emm_grid *g, const emm_survey *s, const float *sigma
   cudaEventRecord(t1, cs);
   if (cudaStreamSynchronize(cs) != cudaSuccess && st == EMM_OK) st = EMM_ECUDA;
   double se = 0, sv = 0, sh = 0;
+  long vsteps = 0;
   float ms = 0.f;
-  for (int q = 0; q < nsamp && st == EMM_OK; ++q) {
+  const int taken = std::min(te.used, nsamp);
+  for (int q = 0; q < taken && st == EMM_OK; ++q) {
     cudaEventElapsedTime(&ms, te.ev[4 * q], te.ev[4 * q + 1]);
     se += ms;
     cudaEventElapsedTime(&ms, te.ev[4 * q + 1], te.ev[4 * q + 2]);
     sv += ms;
+    vsteps += q < static_cast<int>(te.vsteps.size()) ? te.vsteps[q] : 0;
     cudaEventElapsedTime(&ms, te.ev[4 * q + 2], te.ev[4 * q + 3]);
     sh += ms;
   }
-  timing->samples = nsamp;
-  timing->e_ms = nsamp ? se / nsamp : 0.0;
-  timing->v_ms = (nsamp && s->volume) ? sv / nsamp : 0.0;
-  timing->h_ms = nsamp ? sh / nsamp : 0.0;
+  // per step: the E and H launches of the timed steps; the volume DTFT
+  // launches of those steps over the steps they covered
+  timing->samples = taken;
+  timing->e_ms = taken ? se / taken : 0.0;
+  timing->v_ms = (vsteps > 0 && s->volume) ? sv / static_cast<double>(vsteps) : 0.0;
+  timing->h_ms = taken ? sh / taken : 0.0;
   ms = 0.f;
   if (st == EMM_OK) cudaEventElapsedTime(&ms, t0, t1);
   timing->total_ms = ms;

@@ -82,6 +82,25 @@ def test_antenna_workspace_holds_the_union_boxes():
 
 
 
+def test_volume_ring_depth_matches_the_header_and_the_workspace():
+    # EMM_VOLUME_RING in the header, the binding's constant and the field
+    # ring the workspace holds for a solve with the volume DTFT agree
+    hdr = open(os.path.join(ROOT, "include", "emm.h")).read()
+    assert int(re.search(r"#define EMM_VOLUME_RING (\d+)", hdr).group(1)) == emm.VOLUME_RING
+    x = np.arange(1000.0) * 10
+    y = np.arange(6.0) * 10
+    g = emm.make_grid(x, y, y, rd=2, nb=4, ne=3)
+    s0 = emm.Survey(omega0=1.0, fmax=1.0, sigma_min=1.0, nt=10, src=(4995, 25, 25),
+                    rec=np.array([[4000.0, 25.0, 25.0]]), freqs=[1.0, 2.0])
+    s1 = emm.Survey(**{**s0.__dict__, "volume": True})
+    nint = 1000 * 6 * 6
+    acc = 6 * 2 * nint * 16                 # compensated accumulators
+    cells = int(np.prod(g.npad)) * 4        # bytes of one field component (rows unpadded)
+    ring = emm.workspace_size(g, s1) - emm.workspace_size(g, s0) - acc
+    k = emm.VOLUME_RING - 1                 # slots beside the state's own
+    assert k * 6 * cells <= ring <= k * 6 * (cells * 1.07 + 256) + 256
+
+
 def test_work_list_layout_and_errors():
     from paper_2304_00233_b300 import workloads as W
     wls = [W.small_case(n=(20, 18, 16), rd=2, nt=10, volume=False), W.small_case(n=(26, 22, 19), rd=2, nt=12,
