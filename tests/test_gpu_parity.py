@@ -159,6 +159,39 @@ def test_timed_entry_point_matches_forward():
     assert torch.equal(G1, work.rec)
 
 
+@pytest.mark.parametrize("nt", [0, 1, 7, 8, 9, 17])
+def test_volume_dtft_batches_against_oracle(nt):
+    # the volume DTFT adds up to EMM_VOLUME_RING steps per launch: a run
+    # shorter than one batch, exactly one, and a ragged last batch
+    wl = W.small_case(rd=2, n=(25, 23, 21), nt=nt, volume=True, nfreq=2, seed=17)
+    G, vol, _, _ = _run_gpu(wl, nt)
+    if nt == 0:
+        assert np.all(G == 0) and np.all(vol == 0)
+        return
+    ref = oracle.forward_workload(wl, nt=nt)
+    for got, want in ((vol[:3], ref["vol"][:3]), (vol[3:], ref["vol"][3:])):
+        if np.abs(want).max() == 0:    # H^{1/2} of a one-step run
+            assert np.all(got == 0)
+        else:
+            assert rel_l2_masked(got, want) < REL_L2_TOL, nt
+
+
+def test_timed_entry_point_with_volume_matches_forward():
+    # the timed run samples the last steps of volume-DTFT launches; its
+    # outputs equal a plain run's
+    wl = W.small_case(rd=2, nt=72, volume=True, nfreq=2)
+    grid = emm.grid_for(wl)
+    survey = emm.survey_for(wl, nt=72)
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    work = emm.Workspace(grid, survey)
+    t = emm.forward_timed(grid, survey, sigma, work, every=16)
+    assert t["samples"] > 0 and t["v_ms"] > 0 and t["e_ms"] > 0 and t["h_ms"] > 0
+    G1, V1 = work.rec.clone(), work.vol.clone()
+    emm.forward_async(grid, survey, sigma, work)
+    torch.cuda.synchronize()
+    assert torch.equal(G1, work.rec) and torch.equal(V1, work.vol)
+
+
 @pytest.mark.parametrize("rd", [1, 2, 3, 4])
 def test_tile_shapes_give_the_same_bits(rd):
     # the same cells in other tiles (32 x 4 x 4 instead of 32 x 8 x 2): the
