@@ -921,6 +921,14 @@ def main():
         log("marine line done")
         mwl, mgrid, msurvey, msigma, mwork, mnt = m["ctx"]
         mvalue = m["line"]["value"]
+        # the marine solve replayed from a CUDA graph of its time loop
+        # (emm_plan), opt-in (--graph) so that the default run stays within
+        # its time; the work-list lines after it then run in a process that
+        # has created, run and destroyed a plan
+        if args.graph:
+            line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
+                                       lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)
+            log("graph line done")
         if args.batch > 0:
             line["batch"] = batch_line(emm, torch, stream, job_max, world, rank, mgrid, msurvey, msigma,
                                        mvalue, args.batch)
@@ -941,12 +949,6 @@ def main():
     if extras and not args.no_gradient_survey:
         line["gradient_survey"] = gradient_survey_line(emm, torch, stream, job_max, dist, rank, world)
         log("gradient survey line done")
-    # the marine solve replayed from a CUDA graph of its time loop (emm_plan),
-    # opt-in (--graph), so that the default run stays within its time, and last
-    if extras and not args.no_marine and args.graph:
-        line["graph"] = graph_line(emm, torch, stream, job_max, mgrid, msurvey, msigma, mwork, 3,
-                                   lambda sec: aggregate_rate(world, mgrid.cells, mnt, 3, sec), mvalue)
-        log("graph line done")
     if extras and not args.no_marine:
         del mwork, m
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
