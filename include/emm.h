@@ -163,7 +163,15 @@ typedef struct {
                            H_x,y = i k_x,y / |k| H_z, shifted to their own x-y
                            positions), through the 2-D DFT of the padded plane.
                            Needs uniform x and y spacing (EMM_EINVAL) and source
-                           stencils below the interface (EMM_EOUTSIDE). */
+                           stencils below the interface (EMM_EOUTSIDE).  An
+                           electric point-dipole solve without the volume DTFT
+                           runs the layers next to the interface and the air
+                           transforms on a second stream of the library's (one per
+                           host thread and device, of the greatest priority),
+                           forked from `stream` and joined back to it within the
+                           call: work enqueued on `stream` before and after is
+                           ordered with all of it, as with one stream.
+                           emm_forward_timed and convergence runs keep one stream. */
   int tile_shape;       /* stencil tile of one CTA of the E and H launches, 128
                            threads each: 0 = 32 x 8 x 2 cells (x, y, z), 1 =
                            32 x 4 x 4.  Used by emm_forward, emm_forward_timed,

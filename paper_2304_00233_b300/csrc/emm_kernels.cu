@@ -1754,10 +1754,118 @@ cudaError_t air_step(const DevParams &p, cudaStream_t st) {
   return e;
 }
 
+// The second stream of split air runs and its events, one set per host
+// thread and device, created on first use and kept for the life of the
+// thread (a CUDA-graph capture may hold them).
+struct AirSplitStreams {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, et = nullptr, eb = nullptr, ht = nullptr, hb = nullptr;
+};
+
+inline cudaError_t air_split_streams(AirSplitStreams **out) {
+  constexpr int kDevs = 64;
+  thread_local AirSplitStreams sets[kDevs];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+  AirSplitStreams &s = sets[dev];
+  if (!s.side) {
+    // the greatest priority: its CTAs (the critical path) are dispatched
+    // ahead of the bulk launch's queued CTAs as SM slots free up
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s.side, cudaStreamNonBlocking, greatest);
+    cudaEvent_t *ev[6] = {&s.fork, &s.join, &s.et, &s.eb, &s.ht, &s.hb};
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  *out = &s;
+  return cudaSuccess;
+}
+
+// Air runs of an electric point dipole without the volume DTFT: each
+// half-step is launched in two parts, the z-layers of tiles next to the air
+// interface ("top": every cell above ks + R, with the receiver CTAs) and the
+// rest ("bulk"), and the top part with the air transforms runs on a second
+// stream beside the bulk part:
+//   side:   E_top(n) -> air_E(n) -> H_top(n) -> air_H(n) -> E_top(n+1) ...
+//   stream: E_bulk(n) -> H_bulk(n) -> E_bulk(n+1) ...
+// with E_top(n) after H_bulk(n-1), E_bulk(n) after H_top(n-1), H_top(n)
+// after E_bulk(n) and H_bulk(n) after E_top(n) (events).  Bulk cells lie at
+// ks + R or deeper, so they never read the rows the air transforms write
+// (rows above ks); the halo of each part is the other part's cells of the
+// same time level, ordered by those events.  So the air transforms of a
+// half-step overlap the bulk stencil launch of that half-step.  All launches
+// are plain ones but the four air passes after a top launch, which follow
+// it on the side stream as programmatic dependents.  Returns
+// cudaErrorNotSupported (nothing enqueued) when the grid has no bulk layers.
+template <int R, bool MULTI, int S>
+cudaError_t launch_air_split(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st) {
+  constexpr int ZC = shape_zc(S);
+  const int lt = (p.air_ks + R - p.org[2] + ZC - 1) / ZC;  // top tile layers
+  if (lt >= p.tiles_z) return cudaErrorNotSupported;
+  DevParams qt = p, qb = p;
+  qt.tiles_z = lt;  // the receiver layers and tile layers [0, lt)
+  qb.rec_layers = 0;
+  qb.tiles_z = p.tiles_z - lt;
+  qb.org[2] = p.org[2] + lt * ZC;
+  const dim3 gt(blocks.x, blocks.y, static_cast<unsigned>(p.rec_layers + lt));
+  const dim3 gb(blocks.x, blocks.y, static_cast<unsigned>(p.tiles_z - lt));
+  TmaSet tE{}, tH{};
+  if (!make_tiles<R, S>(&tE, p.H, p) || !make_tiles<R, S>(&tH, p.E, p)) return cudaErrorInvalidValue;
+  const size_t sb = smem_bytes<R, S>();
+  cudaError_t e = cudaFuncSetAttribute(k_update_E<R, MULTI, false, false, S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sb));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_H<R, MULTI, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sb));
+  AirSplitStreams *ss = nullptr;
+  if (e == cudaSuccess) e = air_split_streams(&ss);
+  if (e != cudaSuccess) return e;
+  PlainLaunches plain;
+  cudaStream_t sd = ss->side;
+  e = cudaEventRecord(ss->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sd, ss->fork, 0);
+  for (int n = n0; n < n1 && e == cudaSuccess; ++n) {
+    // E half-step
+    if (n > n0) e = cudaStreamWaitEvent(sd, ss->hb, 0);
+    if (e == cudaSuccess) e = launch_dependent(k_update_E<R, MULTI, false, false, S>, gt, dim3(NT), sb, sd, qt, tE, n);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->et, sd);
+    if (e == cudaSuccess && n > n0) e = cudaStreamWaitEvent(st, ss->ht, 0);
+    if (e == cudaSuccess) e = launch_dependent(k_update_E<R, MULTI, false, false, S>, gb, dim3(NT), sb, st, qb, tE, n);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->eb, st);
+    if (e == cudaSuccess && R > 1) {
+      DependentLaunches chain;  // the four passes follow E_top on the side stream
+      e = air_step<MULTI, 0>(p, sd);
+    }
+    // H half-step
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sd, ss->eb, 0);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, false, S>, gt, dim3(NT), sb, sd, qt, tH, n);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->ht, sd);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->et, 0);
+    if (e == cudaSuccess) e = launch_dependent(k_update_H<R, MULTI, false, S>, gb, dim3(NT), sb, st, qb, tH, n);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->hb, st);
+    if (e == cudaSuccess) {
+      DependentLaunches chain;  // the four passes follow H_top on the side stream
+      e = air_step<MULTI, 1>(p, sd);
+    }
+  }
+  // join: the work after the run on `stream` waits for the side stream
+  cudaError_t j = cudaEventRecord(ss->join, sd);
+  if (j == cudaSuccess) j = cudaStreamWaitEvent(st, ss->join, 0);
+  if (e == cudaSuccess) e = j;
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 // OUT: one step whose E^{n+1} goes to p.Eout; the launches after the E
 // half-step see it there.
 template <int R, bool MULTI, bool CONV, bool OUT = false, int S = 0>
 cudaError_t launch_steps(const DevParams &p, int n0, int n1, dim3 blocks, cudaStream_t st, StepEvents *te) {
+  if (!OUT && !CONV && p.air_on && p.src_fused && !p.vacc && !te && n1 > n0) {
+    const cudaError_t e = launch_air_split<R, MULTI, S>(p, n0, n1, blocks, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (OUT && (MULTI || CONV || n1 - n0 != 1)) return cudaErrorInvalidValue;
   DevParams q = p;
   q.ring_k = 1;  // the fields stay in place

@@ -102,6 +102,15 @@ struct PlainLaunches {
   ~PlainLaunches() { plain_launches = old; }
 };
 
+// While alive on a thread inside a PlainLaunches scope: launch_dependent
+// makes programmatic dependents again (for a run of launches that follow
+// one another on one stream with no other dependency between them).
+struct DependentLaunches {
+  bool old;
+  DependentLaunches() : old(plain_launches) { plain_launches = false; }
+  ~DependentLaunches() { plain_launches = old; }
+};
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              Args &&...args) {

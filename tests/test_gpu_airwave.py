@@ -53,6 +53,23 @@ def test_airwave_against_oracle(rd):
     assert np.abs(G0.cpu().numpy() - G.cpu().numpy()).max() > 1e-3 * np.abs(G0.cpu().numpy()).max()
 
 
+@pytest.mark.parametrize("rd", [1, 2, 3, 4])
+def test_split_air_solve_equals_the_sequential_one(rd):
+    # without the volume DTFT an electric-dipole air solve launches each
+    # half-step in two parts on two streams (the tile layers next to the
+    # interface, with the air transforms, beside the rest); with it, one
+    # sequence on one stream.  The same cells by the same arithmetic: the
+    # receivers get the same bits.
+    wl = _air_workload(rd, nt=150)
+    grid = emm.grid_for(wl)
+    sigma = torch.from_numpy(wl.sigma.astype(np.float32)).cuda()
+    G_seq, _ = emm.forward(grid, emm.survey_for(wl, airwave=True), sigma)
+    wl.volume = False
+    G_split, vol = emm.forward(grid, emm.survey_for(wl, airwave=True), sigma)
+    assert vol is None
+    assert torch.equal(G_split, G_seq)
+
+
 def test_airwave_batch_bitwise_equal_to_single_solves():
     wl = _air_workload(2, nt=60)
     wl.volume = False

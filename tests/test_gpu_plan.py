@@ -56,6 +56,23 @@ def test_plan_with_air_boundary_equals_forward_and_closes():
     assert torch.equal(G2, G_ref)
 
 
+def test_plan_of_a_split_air_solve_equals_forward():
+    # without the volume DTFT the air solve runs on two streams; the plan
+    # captures both (forked from and joined back to its stream)
+    from test_gpu_airwave import _air_workload
+    wl = _air_workload(3, nt=70)
+    wl.volume = False
+    grid = emm.grid_for(wl)
+    survey = emm.survey_for(wl, airwave=True)
+    s1 = _sig(wl.sigma)
+    plan = emm.Plan(grid, survey, s1)
+    for _ in range(2):
+        G, _ = plan.run(s1)
+        G_ref, _ = emm.forward(grid, survey, s1)
+        assert torch.equal(G, G_ref)
+    plan.close()
+
+
 _PLAN_THEN_JOBS = r"""
 import dataclasses, sys
 import numpy as np, torch
